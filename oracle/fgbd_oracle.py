@@ -1,0 +1,408 @@
+"""FP64 CPU oracle for the FGBD per-frame path.  TEST INFRASTRUCTURE ONLY.
+
+A plain, slow, NumPy (float64) restatement of the method of Watanabe, Nonaka,
+Pavez, Kobayashi and Ortega, "Fast Graph-Based Denoising for Point Cloud Color
+Information" (ICASSP 2024), written from the paper's definitions:
+
+  step 1  SLG scan-line graph          Section 2.2, Eq. 1-3 (codes), Eq. 4 (weights)
+  step 2  NE-GBP noise estimate        Section 2.3
+  step 3  FSLR filter selection        Section 2.4, Eq. 6 and the limited-region rule
+  step 4  graph low-pass filter        Section 2.4, Eq. 5
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this module.  The CUDA library never calls it, and it
+shares no code with the library: the two meet only at the seeded inputs from
+``paper_2401_09721_gb300.synth`` (which holds none of the method's arithmetic).
+
+Where the paper is silent or ambiguous, the reading taken is stated at the
+function that implements it.  Every function here is pinned by a ``-m "not gpu"``
+test against something other than itself (hand-derived cases, brute force,
+closed forms, spectral identities or statistical recovery).
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+import scipy.sparse as sp
+
+__all__ = [
+    "Params",
+    "scan_line_codes",
+    "scan_orders",
+    "slg_edges",
+    "adjacency_csr",
+    "sigma_g",
+    "edge_weights",
+    "random_walk_weights",
+    "patch_vectors",
+    "patch_covariance",
+    "eigenvalues_desc",
+    "tail_rule",
+    "estimate_noise",
+    "fslr_spread",
+    "fslr_keep",
+    "lowpass_step",
+    "lowpass",
+    "selection_objective",
+    "select_q",
+    "fgbd",
+    "OracleResult",
+]
+
+
+@dataclass
+class Params:
+    bits: int = 10           # b: coordinate bits (Section 2.2)
+    window: int = 1          # linked positions on each side along a scan line (Section 2.2: 1)
+    fslr_factor: float = 2.0  # points with mean patch std > factor * sigma_est are skipped (Section 2.4)
+    q_max: int = 64          # largest filter power searched (the paper gives none; a reading)
+
+
+# --------------------------------------------------------------------------
+# Step 1: SLG graph (Section 2.2)
+# --------------------------------------------------------------------------
+
+def scan_line_codes(g: np.ndarray, bits: int) -> np.ndarray:
+    """Eq. 1-3: the three raster scan-line codes of each voxel.
+
+    C1 = 2^{2b} z + 2^b y + x,  C2 = 2^{2b} x + 2^b z + y,  C3 = 2^{2b} y + 2^b x + z.
+    Returns int64 [3, N].
+    """
+    g = np.asarray(g, dtype=np.int64)
+    x, y, z = g[:, 0], g[:, 1], g[:, 2]
+    s1 = np.int64(2) ** bits
+    s2 = np.int64(2) ** (2 * bits)
+    c1 = s2 * z + s1 * y + x
+    c2 = s2 * x + s1 * z + y
+    c3 = s2 * y + s1 * x + z
+    return np.stack([c1, c2, c3])
+
+
+def scan_orders(codes: np.ndarray) -> np.ndarray:
+    """Section 2.2: points ordered along each scan-line code.
+
+    The paper uses a radix sort; any stable sort yields the same order.  Equal
+    codes (repeated voxels) keep their input order (reading: ties by index).
+    Returns int64 [3, N]; row l lists point indices in ascending code l.
+    """
+    return np.stack([np.argsort(c, kind="stable") for c in codes])
+
+
+def slg_edges(orders: np.ndarray, window: int = 1) -> np.ndarray:
+    """Section 2.2: points consecutive along a code are linked, independently per code.
+
+    With window w, positions k and k+d (1 <= d <= w) are linked; the paper uses
+    w = 1 ("two consecutive points"), giving 2 neighbours per code.
+    Reading: links are taken in the global sorted order, so they also join the
+    end of one scan line to the start of the next (the paper keeps these
+    "distant connections").  Reading: the union over codes is a set, so a pair
+    linked by several codes is one edge.
+    Returns int64 [E, 2] undirected edges (i < j), lexicographically sorted.
+    """
+    parts = []
+    for order in orders:
+        for d in range(1, window + 1):
+            a = order[:-d]
+            b = order[d:]
+            parts.append(np.stack([np.minimum(a, b), np.maximum(a, b)], axis=1))
+    if not parts:
+        return np.zeros((0, 2), np.int64)
+    e = np.concatenate(parts)
+    if e.shape[0] == 0:
+        return np.zeros((0, 2), np.int64)
+    return np.unique(e, axis=0)
+
+
+def adjacency_csr(edges: np.ndarray, n: int):
+    """Symmetric adjacency of the undirected edge set as CSR (rows sorted by column).
+
+    Returns (row_ptr int64 [n+1], col int64 [2E]).
+    """
+    rows = np.concatenate([edges[:, 0], edges[:, 1]])
+    cols = np.concatenate([edges[:, 1], edges[:, 0]])
+    order = np.lexsort((cols, rows))
+    rows = rows[order]
+    cols = cols[order]
+    row_ptr = np.zeros(n + 1, np.int64)
+    np.cumsum(np.bincount(rows, minlength=n), out=row_ptr[1:])
+    return row_ptr, cols
+
+
+def _row_index(row_ptr: np.ndarray) -> np.ndarray:
+    return np.repeat(np.arange(row_ptr.size - 1), np.diff(row_ptr))
+
+
+def _sq_dist(g: np.ndarray, row_ptr: np.ndarray, col: np.ndarray) -> np.ndarray:
+    g = np.asarray(g, dtype=np.int64)
+    diff = g[col] - g[_row_index(row_ptr)]
+    return (diff * diff).sum(axis=1)  # exact integers
+
+
+def sigma_g(g: np.ndarray, row_ptr: np.ndarray, col: np.ndarray) -> float:
+    """Section 2.2: sigma_g, the average Euclidean distance between points and their neighbours.
+
+    Reading: one global scalar, the mean of ||g_i - g_j|| over all directed
+    adjacency entries (equivalently over undirected edges), line-jump edges
+    included.  With no edges the value is 0.
+    """
+    if col.size == 0:
+        return 0.0
+    return float(np.sqrt(_sq_dist(g, row_ptr, col).astype(np.float64)).mean())
+
+
+def edge_weights(g: np.ndarray, row_ptr: np.ndarray, col: np.ndarray, sg: float) -> np.ndarray:
+    """Eq. 4: w_ij = exp(-||g_i - g_j||^2 / sigma_g^2) per adjacency entry (float64).
+
+    Reading: (g_i - g_j)^2 in Eq. 4 is the squared Euclidean norm.  If sigma_g
+    is 0 (every edge has length 0) all weights are 1.  Long edges may underflow
+    to 0 here; ``random_walk_weights`` is the underflow-free row-normalised form.
+    """
+    d2 = _sq_dist(g, row_ptr, col).astype(np.float64)
+    if sg == 0.0:
+        return np.ones_like(d2)
+    return np.exp(-d2 / (sg * sg))
+
+
+def random_walk_weights(g: np.ndarray, row_ptr: np.ndarray, col: np.ndarray, sg: float) -> np.ndarray:
+    """Entries of D^{-1} W (rows of Eq. 4's W divided by their degree d_i = sum_j w_ij).
+
+    Computed as exp(-(d2_ij - min_k d2_ik)/sigma_g^2) / sum_k exp(-(d2_ik - min_k d2_ik)/sigma_g^2),
+    which equals w_ij / d_i exactly in real arithmetic (the common factor
+    exp(-min d2 / sigma_g^2) cancels) and stays defined when every w_ij of a
+    row underflows in floating point.
+    """
+    d2 = _sq_dist(g, row_ptr, col).astype(np.float64)
+    n = row_ptr.size - 1
+    rows = _row_index(row_ptr)
+    if d2.size == 0:
+        return d2
+    dmin = np.full(n, np.inf)
+    np.minimum.at(dmin, rows, d2)
+    shifted = d2 - dmin[rows]
+    e = np.ones_like(shifted) if sg == 0.0 else np.exp(-shifted / (sg * sg))
+    s = np.bincount(rows, weights=e, minlength=n)
+    return e / s[rows]
+
+
+# --------------------------------------------------------------------------
+# Step 2: NE-GBP (Section 2.3)
+# --------------------------------------------------------------------------
+
+def patch_vectors(g: np.ndarray, f: np.ndarray, row_ptr: np.ndarray, col: np.ndarray, k: int):
+    """Section 2.3: graph-based patches a_i, entries ordered by distance from the query point.
+
+    a_i = [f_i, f_{n1}, ..., f_{nk}] with the neighbours in increasing distance.
+    Reading: D = 3 (k + 1) (three colour channels per node, node-major), and only
+    points with exactly k distinct neighbours (k = 6w) give a patch; points with
+    fewer (the ends of the scan orders, pairs linked by two codes) are left out.
+    Reading: equal distances are ordered by the offset g_j - g_i compared as
+    (dz, dy, dx) ascending, then by neighbour index.
+    Returns (A float64 [N', D], idx int64 [N']): the patches and their point indices.
+    """
+    g = np.asarray(g, dtype=np.int64)
+    f = np.asarray(f, dtype=np.float64)
+    deg = np.diff(row_ptr)
+    idx = np.nonzero(deg == k)[0]
+    if idx.size == 0:
+        return np.zeros((0, 3 * (k + 1))), idx
+    nb = col[row_ptr[idx][:, None] + np.arange(k)[None, :]]          # [N', k]
+    off = g[nb] - g[idx][:, None, :]                                  # [N', k, 3]
+    d2 = (off * off).sum(axis=2)
+    # lexicographic (d2, dz, dy, dx, j) inside each row; lexsort keys are given last-major
+    order = np.lexsort((nb, off[:, :, 0], off[:, :, 1], off[:, :, 2], d2), axis=1)
+    nb_sorted = np.take_along_axis(nb, order, axis=1)
+    members = np.concatenate([idx[:, None], nb_sorted], axis=1)        # [N', k+1]
+    A = f[members].reshape(idx.size, 3 * (k + 1))
+    return A, idx
+
+
+def patch_covariance(A: np.ndarray):
+    """Section 2.3: Sigma = (1/N) sum_i (a_i - mu)(a_i - mu)^T with mu the mean patch."""
+    n = A.shape[0]
+    mu = A.mean(axis=0)
+    C = A - mu
+    return (C.T @ C) / n, mu
+
+
+def eigenvalues_desc(S: np.ndarray) -> np.ndarray:
+    """Section 2.3: eigenvalues of the symmetric covariance, lambda_1 >= ... >= lambda_D."""
+    return np.linalg.eigvalsh(S)[::-1].copy()
+
+
+def tail_rule(lam: np.ndarray):
+    """Section 2.3: pick the noise subspace S_H = {lambda_{m+1..D}} and sigma_est = sqrt(tau).
+
+    tau(m) is the mean of lambda_{m+1}..lambda_D.  The paper states the test
+    against the median of the same values following Chen et al. (ICCV 2015):
+    eigenvalues that carry signal lift the mean of the tail above its median,
+    so leading eigenvalues are dropped until that stops.  Reading: m* is the
+    smallest m in [0, D-1] with tau(m) <= median(lambda_{m+1..D}); the mean
+    divides by the D - m values it averages; the median of an even count is the
+    mean of its two middle values.  m = D - 1 always passes.
+    Returns (m*, tau, sigma_est).
+    """
+    lam = np.asarray(lam, dtype=np.float64)
+    D = lam.size
+    for m in range(D):
+        tail = lam[m:]
+        tau = tail.mean()
+        if tau <= np.median(tail):
+            return m, float(tau), float(np.sqrt(max(tau, 0.0)))
+    raise AssertionError("unreachable: a single value is its own median")
+
+
+def estimate_noise(g, f, row_ptr, col, k: int = 6):
+    """NE-GBP (Section 2.3): patches -> covariance -> eigenvalues -> sigma_est.
+
+    With no complete patch the estimate is 0 (reading: nothing to estimate from).
+    Returns a dict with sigma_est, tau, m, eigenvalues, n_patches, covariance.
+    """
+    A, idx = patch_vectors(g, f, row_ptr, col, k)
+    D = 3 * (k + 1)
+    if A.shape[0] == 0:
+        return dict(sigma_est=0.0, tau=0.0, m=0, eigenvalues=np.zeros(D), n_patches=0,
+                    covariance=np.zeros((D, D)), mean=np.zeros(D))
+    S, mu = patch_covariance(A)
+    lam = eigenvalues_desc(S)
+    m, tau, s = tail_rule(lam)
+    return dict(sigma_est=s, tau=tau, m=m, eigenvalues=lam, n_patches=int(A.shape[0]),
+                covariance=S, mean=mu)
+
+
+# --------------------------------------------------------------------------
+# Step 3/4: filter and FSLR selection (Section 2.4)
+# --------------------------------------------------------------------------
+
+def fslr_spread(f: np.ndarray, row_ptr: np.ndarray, col: np.ndarray) -> np.ndarray:
+    """Section 2.4: (sigma_R(i) + sigma_G(i) + sigma_B(i)) / 3 over the patch of point i.
+
+    Reading: the patch of i is i and all its graph neighbours (whatever the
+    degree); each sigma is the population standard deviation (divisor n, as
+    in the covariance of Section 2.3) of that channel over the patch.
+    """
+    f = np.asarray(f, dtype=np.float64)
+    n = f.shape[0]
+    rows = _row_index(row_ptr)
+    cnt = np.diff(row_ptr).astype(np.float64) + 1.0
+    mean = (f + np.stack([np.bincount(rows, weights=f[col, c], minlength=n) for c in range(3)], 1)) / cnt[:, None]
+    dev_self = (f - mean) ** 2
+    dev_nb = (f[col] - mean[rows]) ** 2
+    var = (dev_self + np.stack([np.bincount(rows, weights=dev_nb[:, c], minlength=n) for c in range(3)], 1)) / cnt[:, None]
+    return np.sqrt(var).mean(axis=1)
+
+
+def fslr_keep(spread: np.ndarray, sigma_est: float, factor: float = 2.0) -> np.ndarray:
+    """Section 2.4: points whose spread exceeds factor * sigma_est (factor 2) are not used.
+
+    Reading: if this would leave no point, every point is used.
+    """
+    keep = ~(spread > factor * sigma_est)
+    if not keep.any():
+        keep[:] = True
+    return keep
+
+
+def _rw_matrix(row_ptr, col, rw):
+    n = row_ptr.size - 1
+    return sp.csr_matrix((rw, col, row_ptr), shape=(n, n))
+
+
+def lowpass_step(x: np.ndarray, rwm) -> np.ndarray:
+    """One application of D_g^{-1} W_g with W_g = D + W and D_g = 2 D (Eq. 5).
+
+    D_g^{-1} W_g = (2D)^{-1}(D + W) = I/2 + D^{-1} W / 2.  A point without
+    neighbours (only possible when N = 1) keeps its value.
+    """
+    y = rwm @ x
+    isolated = np.diff(rwm.indptr) == 0
+    y[isolated] = x[isolated]
+    return 0.5 * x + 0.5 * y
+
+
+def lowpass(f_in: np.ndarray, row_ptr, col, rw, q: int) -> np.ndarray:
+    """Eq. 5: f_out = (D_g^{-1} W_g)^q f_in, computed on the vertex domain."""
+    x = np.asarray(f_in, dtype=np.float64).copy()
+    M = _rw_matrix(row_ptr, col, rw)
+    for _ in range(q):
+        x = lowpass_step(x, M)
+    return x
+
+
+def selection_objective(y: np.ndarray, xq: np.ndarray, keep: np.ndarray, sigma_est: float) -> float:
+    """Eq. 6 over the limited region: |sigma_est^2 - (sum y^2 - sum x_q^2) / N|.
+
+    Reading: the signals have three channels and the noise level is per
+    scalar, so the sums run over the kept points and their 3 channels and N is
+    3 times the number of kept points.
+    """
+    y = np.asarray(y, dtype=np.float64)[keep]
+    xq = np.asarray(xq, dtype=np.float64)[keep]
+    lost = ((y - xq) * (y + xq)).sum()
+    return abs(sigma_est * sigma_est - lost / (3.0 * keep.sum()))
+
+
+def select_q(y, row_ptr, col, rw, keep, sigma_est: float, q_max: int = 64):
+    """Section 2.4: the integer q minimising Eq. 6, and x_q.
+
+    Reading: q is searched upward from 0 and the search stops at the first q
+    whose objective is not below the previous one (J(q) >= J(q-1)); q* = q - 1.
+    Equal objectives go to the smaller q.  The search ends at q_max.
+    Returns (q*, x_{q*} float64 [N, 3], J list for q = 0..last evaluated).
+    """
+    y = np.asarray(y, dtype=np.float64)
+    M = _rw_matrix(row_ptr, col, rw)
+    x_prev = y.copy()
+    J = [selection_objective(y, x_prev, keep, sigma_est)]
+    for q in range(1, q_max + 1):
+        x = lowpass_step(x_prev, M)
+        J.append(selection_objective(y, x, keep, sigma_est))
+        if J[q] >= J[q - 1]:
+            return q - 1, x_prev, J
+        x_prev = x
+    return q_max, x_prev, J
+
+
+# --------------------------------------------------------------------------
+# whole path
+# --------------------------------------------------------------------------
+
+@dataclass
+class OracleResult:
+    orders: np.ndarray
+    row_ptr: np.ndarray
+    col: np.ndarray
+    sigma_g: float
+    w: np.ndarray
+    rw: np.ndarray
+    noise: dict
+    spread: np.ndarray
+    keep: np.ndarray
+    q: int
+    J: list
+    out: np.ndarray
+    extra: dict = field(default_factory=dict)
+
+
+def fgbd(g: np.ndarray, f: np.ndarray, params: Params = Params(), q: int | None = None) -> OracleResult:
+    """The four steps of Section 2.1 in order: SLG, NE-GBP, FSLR, low-pass filter.
+
+    With ``q`` given, the filter power is fixed and the selection is skipped.
+    """
+    g = np.asarray(g)
+    n = g.shape[0]
+    codes = scan_line_codes(g, params.bits)
+    orders = scan_orders(codes)
+    edges = slg_edges(orders, params.window)
+    row_ptr, col = adjacency_csr(edges, n)
+    sg = sigma_g(g, row_ptr, col)
+    w = edge_weights(g, row_ptr, col, sg)
+    rw = random_walk_weights(g, row_ptr, col, sg)
+    noise = estimate_noise(g, f, row_ptr, col, k=6 * params.window)
+    spread = fslr_spread(f, row_ptr, col)
+    keep = fslr_keep(spread, noise["sigma_est"], params.fslr_factor)
+    if q is None:
+        qs, out, J = select_q(f, row_ptr, col, rw, keep, noise["sigma_est"], params.q_max)
+    else:
+        qs, out, J = q, lowpass(f, row_ptr, col, rw, q), []
+    return OracleResult(orders, row_ptr, col, sg, w, rw, noise, spread, keep, qs, J, out)
