@@ -1,0 +1,387 @@
+#!/usr/bin/env python3
+"""Throughput of the FGBD per-frame path on one GB300 (or N replicas under torchrun).
+
+One step = one frame through the whole path of Section 2.1 (scan-line graph,
+NE-GBP noise estimate, FSLR selection, Eq. 5 filter written back in input
+order) via ``fgbd_run``.  The workload is the 1M-point plain-method frame:
+a densely voxelized union of 6 ellipsoids and 4 capped cylinders at 10 bits,
+piecewise-smooth uint8 colour, Gaussian colour noise with sigma cycling over
+{10, 20, 30, 40, 50} from step to step (5 noise draws of the same geometry).
+
+Prints one JSON line.  ``--impl reference`` times the FP64 CPU oracle instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Mpoints/s and frames/s at 1M pts/frame (plain vs batched); % HBM roofline"
+SIGMAS = (10.0, 20.0, 30.0, 40.0, 50.0)
+N_POINTS = 1_000_000
+BITS = 10
+L2_FLUSH_BYTES = 512 << 20
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["fgbd", "reference"], default="fgbd")
+    ap.add_argument("--points", type=int, default=N_POINTS)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def make_frames(n_points, seed=0):
+    from paper_2401_09721_gb300 import synth
+    xyz = synth.torso_points(n_points, BITS, seed)
+    clean = synth.piecewise_colors(xyz, BITS, seed)
+    noisy = [synth.add_noise_u8(clean, s, seed + 11 * k) for k, s in enumerate(SIGMAS)]
+    return xyz, clean, noisy
+
+
+# ------------------------------------------------------------------ CPU oracle
+
+def _oracle_child(path, out_path):
+    os.environ.setdefault("OMP_NUM_THREADS", "1")
+    from oracle import fgbd_oracle as orc
+    d = np.load(path)
+    xyz, rgbs = d["xyz"], [d[f"rgb{k}"] for k in range(int(d["k"]))]
+    times = []
+    for rgb in rgbs:
+        t0 = time.perf_counter()
+        orc.fgbd(xyz, rgb, orc.Params(bits=BITS))
+        times.append(time.perf_counter() - t0)
+    with open(out_path, "w") as fh:
+        json.dump({"times": times, "n": int(xyz.shape[0])}, fh)
+
+
+def time_oracle(xyz, rgbs):
+    """Run the oracle in a fresh single-threaded process; return per-frame seconds."""
+    with tempfile.TemporaryDirectory() as td:
+        path = os.path.join(td, "frame.npz")
+        out = os.path.join(td, "t.json")
+        np.savez(path, xyz=xyz, k=len(rgbs), **{f"rgb{k}": r for k, r in enumerate(rgbs)})
+        env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+        code = f"import sys; sys.path.insert(0, {ROOT!r}); import bench; bench._oracle_child({path!r}, {out!r})"
+        subprocess.run([sys.executable, "-c", code], check=True, env=env, cwd=ROOT)
+        with open(out) as fh:
+            return json.load(fh)["times"]
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    # a bounded sample of the workload: a 100k-point frame from the same generator
+    n_sample = min(args.points, 100_000)
+    xyz, _, noisy = make_frames(n_sample)
+    rgbs = [noisy[k % len(noisy)] for k in range(args.warmup + args.steps)]
+    times = time_oracle(xyz, rgbs)[args.warmup:]
+    total = sum(times)
+    value = n_sample * len(times) / total / 1e6
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "Mpoints/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / len(times),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": workload_config(args.points),
+        "cpu_baseline": {"value": value, "unit": "Mpoints/s", "cores": 1, "kind": "oracle",
+                         "sample": f"{n_sample}-point torso frame (same generator, 10-bit), one frame per step, "
+                                   f"sigma cycling 10..50; NumPy float64 oracle, 1 thread"},
+        "e2e": {"value": value, "unit": "Mpoints/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def workload_config(n_points):
+    return {"workload": f"torso_shell_{n_points // 1000}k_b{BITS}_u8_sigma10-50",
+            "points_per_frame": n_points, "frames_per_step": 1, "bits": BITS,
+            "colour": "piecewise-smooth uint8, Gaussian noise sigma in {10,20,30,40,50}",
+            "parallelism": "replicas",
+            "l2": "flushed between timed steps by a 512 MiB write, flush not timed"}
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.proc = None
+        self.index = index
+        self.path = tempfile.mktemp(suffix=".csv")
+
+    def __enter__(self):
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=self.fh, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        if self.proc is None or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as fh:
+            for line in fh:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 7:
+                    continue
+                try:
+                    sm.append(float(parts[0]))
+                    smax.append(float(parts[1]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[3:7]):
+                    if v.lower() == "active":
+                        reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ roofline bookkeeping
+
+def algorithmic_bytes(name, n, q_iters=0, passes=4, out_bytes=3):
+    """Compulsory DRAM bytes of one launch: the per-point figure of each kernel times n."""
+    if name == "slg_hist":
+        return 12 * n
+    if name.startswith("slg_sort_pass"):
+        p = int(name[-1])
+        read = 36 * n if p == 0 else 24 * n  # xyz once per code, or (key, value) of the 3 codes
+        write = 24 * n                       # (key, value) of 3 codes; last pass: 3 orders, codes, 2 ranks
+        return read + write
+    if name == "slg_link":
+        return 48 * n
+    if name == "gather_colors":
+        return 11 * n
+    if name == "ne_moments":
+        return 28 * n
+    if name == "filter_select":
+        return 28 * n + 48 * n * q_iters + (20 + out_bytes) * n
+    return 0
+
+
+def read_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def read_traffic():
+    """DRAM bytes per launch measured by ncu, keyed by kernel and library digest."""
+    path = os.path.join(ROOT, "profiles", "traffic.txt")
+    out = {}
+    try:
+        with open(path) as fh:
+            for line in fh:
+                line = line.strip()
+                if not line or line.startswith("#"):
+                    continue
+                kern, digest, n, b = line.split()
+                out[kern] = (digest, int(n), float(b))
+    except (OSError, ValueError):
+        pass
+    return out
+
+
+# ------------------------------------------------------------------ GPU arm
+
+def run_fgbd(args):
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    from paper_2401_09721_gb300 import build, fgbd
+    build.build()
+
+    xyz, clean, noisy = make_frames(args.points, seed=rank)
+    n = xyz.shape[0]
+    dev = torch.device("cuda", local)
+    x = torch.from_numpy(xyz).to(dev)
+    cols = [torch.from_numpy(c).to(dev) for c in noisy]
+    out = torch.empty((n, 3), dtype=torch.uint8, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    ctx = fgbd.Context(n, bits=BITS)
+    stream = torch.cuda.current_stream()
+
+    def step(k):
+        ctx.run(x, cols[k % len(cols)], out=out)
+
+    for k in range(args.warmup):
+        step(k)
+    ctx.sync()
+
+    # ---- timed region: device events around each step, L2 flushed in between
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    launches0 = ctx.stats()["launches"]
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    wall0 = time.perf_counter()
+    with ClockSampler(local) as clocks:
+        for k in range(args.steps):
+            flush.zero_()
+            starts[k].record(stream)
+            step(args.warmup + k)
+            ends[k].record(stream)
+        torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    if dist:
+        dist.barrier()
+    st = ctx.stats()
+    launches = st["launches"] - launches0
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    total_s = sum(step_ms) / 1e3
+    if dist:
+        t = torch.tensor([total_s], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_s = float(t.item())
+    value = world * n * args.steps / total_s / 1e6
+    fps = world * args.steps / total_s
+
+    # ---- per-kernel timing pass (separate, instrumented)
+    ctx.set_timing(True)
+    per = {}
+    qs = []
+    for k in range(len(cols)):
+        flush.zero_()
+        step(k)
+        qs.append(ctx.stats()["q"])
+        for name, ms in ctx.timings():
+            per.setdefault(name, []).append(ms)
+    ctx.set_timing(False)
+    q_mean = float(np.mean(qs))
+    q_iters = float(np.mean([min(q + 1, 64) for q in qs]))
+    kernels = {}
+    for name, lst in per.items():
+        avg = float(np.mean(lst))
+        b = algorithmic_bytes(name, n, q_iters=q_iters)
+        kernels[name] = {"ms": avg, "launches_per_step": len(lst) / len(cols),
+                         "algo_bytes": b, "gbs": (b / (avg / 1e3) / 1e9) if b and avg > 0 else None}
+    # the kernel with the largest share of the step; the sort passes are one kernel
+    groups = {}
+    for name, kd in kernels.items():
+        g = "slg_sort_pass" if name.startswith("slg_sort_pass") else name
+        groups.setdefault(g, []).append(kd)
+    dom = max(groups, key=lambda g: sum(kd["ms"] * kd["launches_per_step"] for kd in groups[g]))
+    members = groups[dom]
+    dom_ms = float(np.mean([kd["ms"] for kd in members]))
+    dom_bytes = float(np.mean([kd["algo_bytes"] for kd in members]))
+    peak, peak_kind = read_peaks()
+    achieved = dom_bytes / (dom_ms / 1e3) / 1e9
+    traffic = None
+    tr = read_traffic().get(dom)
+    if tr is not None and tr[0] == build._digest()[:16]:
+        traffic = tr[2] * n / tr[1]
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
+                "algo_bytes_per_launch": dom_bytes, "launch_ms": dom_ms}
+    stages = {}
+    for name, kd in kernels.items():
+        stage = ("graph" if name.startswith("slg") else "noise" if name in ("gather_colors", "ne_moments", "ne_finalize")
+                 else "select+filter")
+        stages[stage] = stages.get(stage, 0.0) + kd["ms"] * kd["launches_per_step"]
+
+    # ---- end to end through the public API with host buffers
+    pin_x = torch.from_numpy(xyz).pin_memory()
+    pin_c = [torch.from_numpy(c).pin_memory() for c in noisy]
+    pin_o = torch.empty((n, 3), dtype=torch.uint8).pin_memory()
+    dx = torch.empty_like(x)
+    dc = torch.empty_like(cols[0])
+    e_st = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    e_en = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    for k in range(args.warmup + args.steps):
+        flush.zero_()
+        if k >= args.warmup:
+            e_st[k - args.warmup].record(stream)
+        dx.copy_(pin_x, non_blocking=True)
+        dc.copy_(pin_c[k % len(pin_c)], non_blocking=True)
+        ctx.run(dx, dc, out=out)
+        pin_o.copy_(out, non_blocking=True)
+        if k >= args.warmup:
+            e_en[k - args.warmup].record(stream)
+    torch.cuda.synchronize()
+    e2e_s = sum(a.elapsed_time(b) for a, b in zip(e_st, e_en)) / 1e3
+    if dist:
+        t = torch.tensor([e2e_s], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e = {"value": world * n * args.steps / e2e_s / 1e6, "unit": "Mpoints/s",
+           "h2d_bytes_per_step": int(pin_x.numel() * 4 + pin_c[0].numel()), "d2h_bytes_per_step": int(pin_o.numel())}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        times = time_oracle(xyz, [noisy[2]])
+        cpu = {"value": n / times[0] / 1e6, "unit": "Mpoints/s", "cores": 1, "kind": "oracle",
+               "sample": f"one full {n}-point frame (sigma 30) of this workload; NumPy float64 oracle, 1 thread, "
+                         f"{times[0]:.1f} s"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "Mpoints/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": workload_config(n), "frames_per_s": fps, "e2e": e2e,
+            "gpu_launches": int(launches), "roofline": roofline, "cpu_baseline": cpu,
+            "clocks": clocks.summary(), "stages_ms": stages,
+            "kernels": {k: {"ms": round(v["ms"], 5), "per_step": v["launches_per_step"],
+                            "gbs": None if v["gbs"] is None else round(v["gbs"], 1)} for k, v in kernels.items()},
+            "q_mean": q_mean, "wall_s": wall, "step_ms_min": min(step_ms), "step_ms_max": max(step_ms),
+        }
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_fgbd(args)
+
+
+if __name__ == "__main__":
+    main()

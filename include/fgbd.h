@@ -1,0 +1,205 @@
+/*
+ * fgbd.h - C ABI of the GB300 (sm_103a) implementation of FGBD, the fast
+ * graph-based colour denoiser of Watanabe, Nonaka, Pavez, Kobayashi and Ortega,
+ * "Fast Graph-Based Denoising for Point Cloud Color Information", ICASSP 2024.
+ *
+ * The per-frame path has four steps (Section 2.1):
+ *   fgbd_build_graph     scan-line graph, Section 2.2 (Eq. 1-4)
+ *   fgbd_estimate_noise  NE-GBP noise level, Section 2.3
+ *   fgbd_select_filter   FSLR choice of the filter power q, Section 2.4 (Eq. 6)
+ *   fgbd_denoise         graph low-pass filter, Section 2.4 (Eq. 5)
+ * and fgbd_run chains all four.
+ *
+ * Conventions
+ *  - Every array argument is DEVICE memory on the context's device, owned by
+ *    the caller, unless its name ends in _host.  Point arrays are row-major:
+ *    xyz is int32 [n][3] as (x, y, z); colours are [n][3] as (R, G, B), either
+ *    uint8 (FGBD_U8) or float32 (FGBD_F32) on the 0..255 scale.
+ *  - `stream` is a cudaStream_t (NULL = the legacy default stream).  Calls
+ *    only enqueue work and return; nothing synchronises unless stated.
+ *  - Errors are returned as fgbd_status, never thrown or trapped.  Errors
+ *    found on the device (a coordinate out of range, a bounded device wait
+ *    that gave up) are latched in the context and returned by the next call
+ *    that synchronises (fgbd_sync, fgbd_get_stats, fgbd_graph_csr).
+ *  - A context is not thread-safe; use one per stream.  The context owns all
+ *    scratch memory, allocated once by fgbd_ctx_create for `capacity` points;
+ *    the per-frame calls allocate nothing.
+ */
+#ifndef FGBD_H
+#define FGBD_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define FGBD_ABI_VERSION 1
+#define FGBD_PATCH_DIM 21   /* D = 3 colour channels x (1 point + 6 neighbours), Section 2.3 */
+#define FGBD_Q_CAP 256      /* largest accepted q_max */
+
+typedef enum fgbd_status {
+  FGBD_OK = 0,
+  FGBD_EINVAL = 1,    /* invalid argument: null pointer, n or a parameter out of range */
+  FGBD_ERANGE = 2,    /* a coordinate outside [0, 2^bits) was found on the device */
+  FGBD_ENOMEM = 3,    /* device allocation failed */
+  FGBD_ECUDA = 4,     /* a CUDA runtime call failed; see fgbd_last_error */
+  FGBD_ETIMEOUT = 5,  /* a bounded device-side wait gave up */
+  FGBD_ESTATE = 6,    /* calls out of order (e.g. select before estimate) */
+  FGBD_ENOTIMPL = 7   /* parameter combination not implemented */
+} fgbd_status;
+
+typedef enum fgbd_dtype { FGBD_U8 = 0, FGBD_F32 = 1 } fgbd_dtype;
+
+typedef struct fgbd_params {
+  int32_t bits;         /* b, coordinate bits (Section 2.2); 1..10 so a code fits 32 bits */
+  int32_t window;       /* points linked on each side along a scan line; the paper uses 1 (only 1 is implemented) */
+  double fslr_factor;   /* FSLR skips points whose mean patch std exceeds factor * sigma_est (paper: 2) */
+  int32_t q_max;        /* largest filter power searched, 0..FGBD_Q_CAP (the paper states none; default 64) */
+  int32_t reserved[7];  /* must be zero */
+} fgbd_params;
+
+typedef struct fgbd_stats {
+  int64_t n;                                /* points of the last graph */
+  int64_t n_edges;                          /* distinct undirected SLG edges */
+  double sigma_g;                           /* mean edge length, Eq. 4's bandwidth */
+  int64_t n_patches;                        /* points with exactly 6 neighbours (Section 2.3) */
+  double eigenvalues[FGBD_PATCH_DIM];       /* of the patch covariance, descending */
+  int32_t m;                                /* leading eigenvalues dropped by the tail rule */
+  int32_t q;                                /* selected (or last applied) filter power */
+  double tau;                               /* mean of the noise eigenvalues */
+  double sigma_est;                         /* sqrt(tau) */
+  int64_t n_keep;                           /* points kept by FSLR (0: none, so all were used) */
+  int32_t n_objective;                      /* number of valid entries of objective[] */
+  int32_t valid;                            /* bit 0 graph, bit 1 noise estimate, bit 2 selection */
+  double objective[FGBD_Q_CAP + 1];         /* Eq. 6 over the kept points, J(0..n_objective-1) */
+  int64_t launches;                         /* kernels this context has launched since creation */
+} fgbd_stats;
+
+typedef struct fgbd_ctx fgbd_ctx;
+
+/* ABI version compiled into the library (FGBD_ABI_VERSION). */
+int32_t fgbd_abi_version(void);
+
+/* Human-readable name of a status code (static string). */
+const char* fgbd_status_str(fgbd_status s);
+
+/* Fill `p` with the paper's settings: bits 10, window 1, fslr_factor 2, q_max 64.
+ * Returns FGBD_EINVAL if p is NULL. */
+fgbd_status fgbd_params_default(fgbd_params* p);
+
+/* Create a context on the current CUDA device for frames of up to `capacity`
+ * points (1 <= capacity < 2^30) and allocate all its device memory (about
+ * 140 bytes per point).  `params` may be NULL for the defaults.  On success
+ * *out owns the context; release it with fgbd_ctx_destroy.
+ * Errors: FGBD_EINVAL (bad capacity or parameters), FGBD_ENOMEM, FGBD_ECUDA. */
+fgbd_status fgbd_ctx_create(int64_t capacity, const fgbd_params* params, fgbd_ctx** out);
+
+/* Free a context and its device memory (waits for its work to finish). NULL is ignored. */
+void fgbd_ctx_destroy(fgbd_ctx* ctx);
+
+/* Message of the last FGBD_ECUDA error of this context ("" if none). */
+const char* fgbd_last_error(const fgbd_ctx* ctx);
+
+/* Section 2.2, Eq. 1-4: scan-line graph of n points.  Computes the three
+ * raster codes, radix-sorts the points along each (ties by input index),
+ * links consecutive points of each order, merges the three link sets into
+ * one symmetric graph (a pair linked twice is one edge) and sigma_g, the mean
+ * edge length used by the Gaussian weights of Eq. 4.
+ *   xyz: int32 [n][3] device, each coordinate in [0, 2^bits).
+ *   n:   0 <= n <= capacity.
+ * A coordinate out of range is reported as FGBD_ERANGE by the next
+ * synchronising call.  Errors: FGBD_EINVAL, FGBD_ECUDA. */
+fgbd_status fgbd_build_graph(fgbd_ctx* ctx, const int32_t* xyz, int64_t n, void* stream);
+
+/* Section 2.3 (NE-GBP): noise level of colours on the graph of the last build.
+ * Patches of the points with exactly 6 neighbours (the point then its
+ * neighbours by increasing distance), their covariance, its eigenvalues, and
+ * sigma_est = sqrt(tau) with tau the mean of the eigenvalues left by the tail
+ * rule.  Also computes each point's patch colour spread for FSLR.
+ *   rgb:        colours [n][3] device, dtype FGBD_U8 or FGBD_F32.
+ *   sigma_est:  optional device double receiving sigma_est (may be NULL).
+ * With no complete patch sigma_est is 0.  Errors: FGBD_EINVAL, FGBD_ESTATE
+ * (no graph), FGBD_ECUDA. */
+fgbd_status fgbd_estimate_noise(fgbd_ctx* ctx, const void* rgb, int32_t dtype, double* sigma_est,
+                                void* stream);
+
+/* Section 2.4 (FSLR, Eq. 5-6): the integer filter power q minimising
+ * |sigma_est^2 - (sum y^2 - sum x_q^2)/N| over the points whose mean patch
+ * colour std is at most fslr_factor * sigma_est (all points if none is), with
+ * N = 3 x (points used).  q is searched upward from 0 and the first q whose
+ * objective is not below the previous one ends the search (q* = q - 1), or
+ * q_max.  The filtered colours x_{q*} are kept in the context for
+ * fgbd_denoise with q < 0.
+ *   rgb:        the colours given to fgbd_estimate_noise (same pointer and dtype,
+ *               unchanged contents).
+ *   sigma_est:  device double to use as sigma_est, or NULL for this context's estimate.
+ *   q_out:      optional device int32 receiving q* (may be NULL).
+ * Errors: FGBD_EINVAL, FGBD_ESTATE (no estimate, or other colours), FGBD_ECUDA. */
+fgbd_status fgbd_select_filter(fgbd_ctx* ctx, const void* rgb, int32_t dtype, const double* sigma_est,
+                               int32_t* q_out, void* stream);
+
+/* Eq. 5: f_out = (D_g^{-1} W_g)^q f_in with W_g = D + W, D_g = 2D, i.e. q steps
+ * of x <- x/2 + D^{-1} W x / 2 with W the Gaussian weights of Eq. 4.
+ *   q >= 0:  filter rgb_in (dtype in_dtype) q times (q <= FGBD_Q_CAP).
+ *   q <  0:  write the colours x_{q*} kept by the last fgbd_select_filter;
+ *            rgb_in and in_dtype are ignored (FGBD_ESTATE if there is none).
+ *   rgb_out: [n][3] device, out_dtype FGBD_F32 (exact filter output) or FGBD_U8
+ *            (rounded half to even and clipped to 0..255).
+ * Errors: FGBD_EINVAL, FGBD_ESTATE, FGBD_ECUDA. */
+fgbd_status fgbd_denoise(fgbd_ctx* ctx, const void* rgb_in, int32_t in_dtype, int32_t q, void* rgb_out,
+                         int32_t out_dtype, void* stream);
+
+/* All four steps on one frame (Section 2.1): build, estimate, select, and the
+ * selected filter written to rgb_out.  Same arguments and errors as the four
+ * calls it replaces; rgb_in and rgb_out must not overlap. */
+fgbd_status fgbd_run(fgbd_ctx* ctx, const int32_t* xyz, int64_t n, const void* rgb_in, int32_t in_dtype,
+                     void* rgb_out, int32_t out_dtype, void* stream);
+
+/* Wait for the context's work on `stream` and return any latched device error
+ * (FGBD_ERANGE, FGBD_ETIMEOUT), clearing it. */
+fgbd_status fgbd_sync(fgbd_ctx* ctx, void* stream);
+
+/* Synchronise `stream`, then copy the scalars of the last build, estimate and
+ * selection into *out_host.  Returns latched device errors like fgbd_sync. */
+fgbd_status fgbd_get_stats(fgbd_ctx* ctx, fgbd_stats* out_host, void* stream);
+
+/* The graph of the last build as CSR in input order, rows sorted by column,
+ * with the Eq. 4 weights w_ij = exp(-|g_i - g_j|^2 / sigma_g^2) (float32; long
+ * edges may underflow to 0).  Synchronises `stream`.
+ *   row_ptr:   int64 [n+1] device, or NULL to only query *nnz_host.
+ *   col:       int32 [col_capacity] device (ignored if row_ptr is NULL).
+ *   w:         float32 [col_capacity] device, or NULL.
+ *   nnz_host:  receives the number of stored entries (2 x edges).
+ * Errors: FGBD_EINVAL (col_capacity too small), FGBD_ESTATE, FGBD_ECUDA. */
+fgbd_status fgbd_graph_csr(fgbd_ctx* ctx, int64_t* row_ptr, int32_t* col, float* w, int64_t col_capacity,
+                           int64_t* nnz_host, void* stream);
+
+/* The three scan orders of the last build: orders[l][k] is the input index of
+ * the k-th point along code l+1 (Eq. 1-3).  orders: int32 [3][n] device. */
+fgbd_status fgbd_get_orders(fgbd_ctx* ctx, int32_t* orders, void* stream);
+
+/* FSLR data in input order (Section 2.4): spread[i] = mean over channels of
+ * the population colour std over point i and its neighbours (float32, from
+ * the last estimate) and keep[i] = 1 if point i entered the objective of the
+ * last selection.  Either pointer may be NULL.  FGBD_ESTATE if the context
+ * holds no selection. */
+fgbd_status fgbd_get_fslr(fgbd_ctx* ctx, float* spread, uint8_t* keep, void* stream);
+
+/* Instrumentation (not part of the method).  With timing enabled, every
+ * kernel the context launches is bracketed by two CUDA events recorded on the
+ * launching stream.  fgbd_get_timings synchronises those events, writes up to
+ * `max` entries (kernel name, NUL-padded to FGBD_NAME_LEN bytes, into
+ * names_host; duration in milliseconds into ms_host), sets *count_host to the
+ * number written and clears the list.  Launches beyond FGBD_TIMING_CAP per
+ * list are not timed.  Errors: FGBD_EINVAL, FGBD_ECUDA. */
+#define FGBD_NAME_LEN 32
+#define FGBD_TIMING_CAP 256
+fgbd_status fgbd_set_timing(fgbd_ctx* ctx, int32_t enable);
+fgbd_status fgbd_get_timings(fgbd_ctx* ctx, int32_t max, int32_t* count_host, char* names_host, float* ms_host);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FGBD_H */

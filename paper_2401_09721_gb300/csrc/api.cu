@@ -1,0 +1,539 @@
+// C ABI of the FGBD library (declared in include/fgbd.h).
+//
+// A context owns one device allocation sized for `capacity` points and
+// carved into the buffers below.  Each ABI call validates its arguments on
+// the host, enqueues kernels on the caller's stream and returns; device-side
+// errors are latched in DevScalars::status and surfaced by the synchronising
+// calls.
+#include <algorithm>
+#include <cstddef>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "../../include/fgbd.h"
+#include "fgbd_internal.cuh"
+
+using namespace fgbd;
+
+struct fgbd_ctx {
+  int device = 0;
+  int num_sms = 0;
+  int filter_per_sm = 1;
+  int64_t capacity = 0;
+  fgbd_params params{};
+  void* mem = nullptr;
+  size_t mem_bytes = 0;
+  DevScalars* sc = nullptr;
+  SortBufs sb{};
+  GraphBufs gb{};
+  uint32_t* y8 = nullptr;
+  float4* yf = nullptr;
+  float* spread = nullptr;
+  float4* x0 = nullptr;
+  float4* x1 = nullptr;
+  double* f64part = nullptr;
+  int f64_blocks = 0;
+  int64_t* scan_tmp = nullptr;
+  int max_tiles = 0;
+  // state of the frame held in the context
+  int n = 0;
+  bool has_graph = false;
+  bool has_noise = false;
+  bool has_sel = false;
+  const void* noise_rgb = nullptr;
+  int noise_dtype = -1;
+  std::string err;
+  // instrumentation
+  int64_t launches = 0;
+  bool timing = false;
+  cudaEvent_t ev[2 * FGBD_TIMING_CAP] = {};
+  const char* ev_name[FGBD_TIMING_CAP] = {};
+  int n_timed = 0;
+};
+
+namespace {
+
+struct DeviceGuard {
+  int prev = -1;
+  bool changed = false;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) {
+      changed = cudaSetDevice(dev) == cudaSuccess;
+    }
+  }
+  ~DeviceGuard() {
+    if (changed) cudaSetDevice(prev);
+  }
+};
+
+fgbd_status cuda_fail(fgbd_ctx* ctx, cudaError_t e, const char* where) {
+  if (ctx) {
+    ctx->err = std::string(where) + ": " + cudaGetErrorString(e);
+  }
+  return FGBD_ECUDA;
+}
+
+#define FGBD_CUDA(ctx, expr)                                  \
+  do {                                                        \
+    const cudaError_t e_ = (expr);                            \
+    if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #expr);  \
+  } while (0)
+
+// Record one kernel launch: optional events around it, and the launch count.
+struct LaunchScope {
+  fgbd_ctx* ctx;
+  cudaStream_t st;
+  int slot = -1;
+  LaunchScope(fgbd_ctx* c, const char* name, cudaStream_t s, int kernels = 1) : ctx(c), st(s) {
+    ctx->launches += kernels;
+    if (ctx->timing && ctx->n_timed < FGBD_TIMING_CAP) {
+      slot = ctx->n_timed++;
+      ctx->ev_name[slot] = name;
+      cudaEventRecord(ctx->ev[2 * slot], st);
+    }
+  }
+  ~LaunchScope() {
+    if (slot >= 0) cudaEventRecord(ctx->ev[2 * slot + 1], st);
+  }
+};
+
+#define FGBD_LAUNCH(ctx, name, st, expr)       \
+  do {                                         \
+    LaunchScope scope_(ctx, name, st);         \
+    FGBD_CUDA(ctx, expr);                      \
+  } while (0)
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+int passes_for(int bits) { return (3 * bits + kRadixBits - 1) / kRadixBits; }
+
+bool params_ok(const fgbd_params& p) {
+  if (p.bits < 1 || p.bits > kMaxBits) return false;
+  if (p.window < 1) return false;
+  if (!(p.fslr_factor > 0.0) || p.fslr_factor > 1e30) return false;
+  if (p.q_max < 0 || p.q_max > kQCap) return false;
+  for (int r : p.reserved)
+    if (r != 0) return false;
+  return true;
+}
+
+bool dtype_ok(int32_t d) { return d == FGBD_U8 || d == FGBD_F32; }
+
+cudaStream_t as_stream(void* s) { return static_cast<cudaStream_t>(s); }
+
+void zero_region(fgbd_ctx* ctx, size_t from, size_t to, cudaStream_t st, cudaError_t* e) {
+  if (*e != cudaSuccess) return;
+  *e = cudaMemsetAsync(reinterpret_cast<char*>(ctx->sc) + from, 0, to - from, st);
+}
+
+fgbd_status take_device_status(fgbd_ctx* ctx, cudaStream_t st) {
+  uint32_t status = 0;
+  FGBD_CUDA(ctx, cudaStreamSynchronize(st));
+  FGBD_CUDA(ctx, cudaMemcpy(&status, &ctx->sc->status, sizeof(status), cudaMemcpyDeviceToHost));
+  if (status) {
+    const uint32_t zero = 0;
+    FGBD_CUDA(ctx, cudaMemcpy(&ctx->sc->status, &zero, sizeof(zero), cudaMemcpyHostToDevice));
+    if (status & kFlagTimeout) return FGBD_ETIMEOUT;
+    if (status & kFlagRange) return FGBD_ERANGE;
+  }
+  return FGBD_OK;
+}
+
+FilterArgs filter_args(fgbd_ctx* ctx, int mode, int q_fixed, const double* sigma_src, void* out,
+                       int out_dtype, int dtype) {
+  FilterArgs a{};
+  a.n = ctx->n;
+  a.bits = ctx->params.bits;
+  a.dtype = dtype;
+  a.mode = mode;
+  a.q_fixed = q_fixed;
+  a.q_max = ctx->params.q_max;
+  a.fslr_factor = ctx->params.fslr_factor;
+  a.sigma_src = sigma_src ? sigma_src : &ctx->sc->sigma_est;
+  a.y8 = ctx->y8;
+  a.yf = ctx->yf;
+  a.spread = ctx->spread;
+  a.pk = ctx->gb.pk;
+  a.c4 = ctx->gb.c4;
+  a.rank1 = ctx->gb.rank1;
+  a.xbuf0 = ctx->x0;
+  a.xbuf1 = ctx->x1;
+  a.out = out;
+  a.out_dtype = out_dtype;
+  a.sc = ctx->sc;
+  return a;
+}
+
+int filter_grid_for(const fgbd_ctx* ctx, int n) {
+  const int need = std::max(1, (n + kFilterThreads - 1) / kFilterThreads);
+  return std::max(1, std::min(need, ctx->filter_per_sm * ctx->num_sms));
+}
+
+fgbd_status do_build(fgbd_ctx* ctx, const int32_t* xyz, int64_t n64, cudaStream_t st) {
+  if (n64 < 0 || n64 > ctx->capacity) return FGBD_EINVAL;
+  if (n64 > 0 && !xyz) return FGBD_EINVAL;
+  const int n = int(n64);
+  const int bits = ctx->params.bits;
+  ctx->has_graph = ctx->has_noise = ctx->has_sel = false;
+  ctx->noise_rgb = nullptr;
+  ctx->n = n;
+  cudaError_t e = cudaSuccess;
+  zero_region(ctx, offsetof(DevScalars, n_edges), offsetof(DevScalars, build_end_), st, &e);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "memset");
+  if (n > 0) {
+    ctx->sb.passes = passes_for(bits);
+    ctx->sb.tiles = (n + kSortTile - 1) / kSortTile;
+    const size_t zero_words = size_t(ctx->sb.passes) * 3 * size_t(ctx->sb.tiles) * kRadix;
+    FGBD_LAUNCH(ctx, "slg_hist", st,
+                launch_hist(xyz, n, bits, ctx->sb.passes, ctx->sb.lookback, zero_words, ctx->sc, ctx->num_sms, st));
+    static const char* const kPassNames[kMaxPasses] = {"slg_sort_pass0", "slg_sort_pass1", "slg_sort_pass2",
+                                                       "slg_sort_pass3"};
+    for (int p = 0; p < ctx->sb.passes; ++p)
+      FGBD_LAUNCH(ctx, kPassNames[p], st,
+                  launch_sort_pass(p, ctx->sb.passes, xyz, n, bits, int(ctx->capacity), ctx->sb, ctx->gb, ctx->sc, st));
+    FGBD_LAUNCH(ctx, "slg_link", st, launch_link(n, bits, int(ctx->capacity), ctx->gb, ctx->sc, ctx->num_sms, st));
+  }
+  ctx->has_graph = true;
+  return FGBD_OK;
+}
+
+fgbd_status do_estimate(fgbd_ctx* ctx, const void* rgb, int32_t dtype, double* sigma_out, cudaStream_t st) {
+  if (!ctx->has_graph) return FGBD_ESTATE;
+  if (!dtype_ok(dtype)) return FGBD_EINVAL;
+  if (ctx->n > 0 && !rgb) return FGBD_EINVAL;
+  if (ctx->params.window != 1) return FGBD_ENOTIMPL;
+  const int n = ctx->n;
+  ctx->has_noise = ctx->has_sel = false;
+  cudaError_t e = cudaSuccess;
+  zero_region(ctx, offsetof(DevScalars, n_patches), offsetof(DevScalars, ne_end_), st, &e);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "memset");
+  int nblocks = 0;
+  if (n > 0) {
+    FGBD_LAUNCH(ctx, "gather_colors", st, launch_gather_colors(rgb, dtype, n, ctx->gb.perm, ctx->y8, ctx->yf, st));
+    nblocks = ne_moment_blocks(n, ctx->num_sms);
+    FGBD_LAUNCH(ctx, "ne_moments", st,
+                launch_ne_moments(n, ctx->params.bits, dtype, ctx->gb, ctx->y8, ctx->yf, ctx->spread, ctx->f64part,
+                                  ctx->sc, ctx->num_sms, true, st));
+  }
+  FGBD_LAUNCH(ctx, "ne_finalize", st, launch_ne_finalize(dtype, ctx->f64part, nblocks, ctx->sc, sigma_out, st));
+  ctx->has_noise = true;
+  ctx->noise_rgb = rgb;
+  ctx->noise_dtype = dtype;
+  return FGBD_OK;
+}
+
+fgbd_status do_select(fgbd_ctx* ctx, const void* rgb, int32_t dtype, const double* sigma_est, int32_t* q_out,
+                      void* out, int32_t out_dtype, cudaStream_t st) {
+  if (!ctx->has_noise) return FGBD_ESTATE;
+  if (!dtype_ok(dtype)) return FGBD_EINVAL;
+  if (rgb != ctx->noise_rgb || dtype != ctx->noise_dtype) return FGBD_ESTATE;
+  ctx->has_sel = false;
+  cudaError_t e = cudaSuccess;
+  zero_region(ctx, offsetof(DevScalars, ysq_keep), offsetof(DevScalars, sel_end_), st, &e);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "memset");
+  const FilterArgs a = filter_args(ctx, 0, 0, sigma_est, out, out_dtype, dtype);
+  FGBD_LAUNCH(ctx, "filter_select", st, launch_filter(a, filter_grid_for(ctx, ctx->n), st));
+  if (q_out) FGBD_CUDA(ctx, cudaMemcpyAsync(q_out, &ctx->sc->q_sel, sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
+  ctx->has_sel = true;
+  return FGBD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int32_t fgbd_abi_version(void) { return FGBD_ABI_VERSION; }
+
+const char* fgbd_status_str(fgbd_status s) {
+  switch (s) {
+    case FGBD_OK: return "FGBD_OK";
+    case FGBD_EINVAL: return "FGBD_EINVAL: invalid argument";
+    case FGBD_ERANGE: return "FGBD_ERANGE: coordinate outside [0, 2^bits)";
+    case FGBD_ENOMEM: return "FGBD_ENOMEM: device allocation failed";
+    case FGBD_ECUDA: return "FGBD_ECUDA: CUDA runtime error";
+    case FGBD_ETIMEOUT: return "FGBD_ETIMEOUT: a bounded device wait gave up";
+    case FGBD_ESTATE: return "FGBD_ESTATE: calls out of order";
+    case FGBD_ENOTIMPL: return "FGBD_ENOTIMPL: not implemented";
+  }
+  return "unknown fgbd_status";
+}
+
+fgbd_status fgbd_params_default(fgbd_params* p) {
+  if (!p) return FGBD_EINVAL;
+  std::memset(p, 0, sizeof(*p));
+  p->bits = 10;
+  p->window = 1;
+  p->fslr_factor = 2.0;
+  p->q_max = 64;
+  return FGBD_OK;
+}
+
+fgbd_status fgbd_ctx_create(int64_t capacity, const fgbd_params* params, fgbd_ctx** out) {
+  if (!out) return FGBD_EINVAL;
+  *out = nullptr;
+  if (capacity < 1 || capacity >= (int64_t(1) << 30)) return FGBD_EINVAL;
+  fgbd_params p;
+  if (params) p = *params;
+  else fgbd_params_default(&p);
+  if (!params_ok(p)) return FGBD_EINVAL;
+  fgbd_ctx* ctx = new (std::nothrow) fgbd_ctx();
+  if (!ctx) return FGBD_ENOMEM;
+  ctx->capacity = capacity;
+  ctx->params = p;
+  if (cudaGetDevice(&ctx->device) != cudaSuccess ||
+      cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, ctx->device) != cudaSuccess) {
+    delete ctx;
+    return FGBD_ECUDA;
+  }
+  ctx->filter_per_sm = std::max(1, filter_grid(1 << 30, ctx->num_sms) / ctx->num_sms);
+
+  const size_t C = size_t(capacity);
+  const int tiles = int((C + kSortTile - 1) / kSortTile);
+  ctx->max_tiles = tiles;
+  ctx->f64_blocks = ne_moment_blocks(int(C), ctx->num_sms);
+  const size_t kP = size_t(kD) * kD + kD + 1;
+  struct Item {
+    void** ptr;
+    size_t bytes;
+  };
+  void* keys0 = nullptr;
+  void* keys1 = nullptr;
+  void* vals0 = nullptr;
+  void* vals1 = nullptr;
+  const Item items[] = {
+      {reinterpret_cast<void**>(&ctx->sc), sizeof(DevScalars)},
+      {&keys0, 3 * C * 4},
+      {&keys1, 3 * C * 4},
+      {&vals0, 3 * C * 4},
+      {&vals1, 3 * C * 4},
+      {reinterpret_cast<void**>(&ctx->sb.lookback), size_t(kMaxPasses) * 3 * tiles * kRadix * 4},
+      {reinterpret_cast<void**>(&ctx->gb.perm), 3 * C * 4},
+      {reinterpret_cast<void**>(&ctx->gb.rank1), C * 4},
+      {reinterpret_cast<void**>(&ctx->gb.rank2), C * 4},
+      {reinterpret_cast<void**>(&ctx->gb.pk), C * 4},
+      {reinterpret_cast<void**>(&ctx->gb.c4), C * 16},
+      {reinterpret_cast<void**>(&ctx->y8), C * 4},
+      {reinterpret_cast<void**>(&ctx->yf), C * 16},
+      {reinterpret_cast<void**>(&ctx->spread), C * 4},
+      {reinterpret_cast<void**>(&ctx->x0), C * 16},
+      {reinterpret_cast<void**>(&ctx->x1), C * 16},
+      {reinterpret_cast<void**>(&ctx->f64part), size_t(ctx->f64_blocks) * kP * 8},
+      {reinterpret_cast<void**>(&ctx->scan_tmp), ((C + 1 + 1023) / 1024 + 1) * 8},
+  };
+  size_t total = 0;
+  for (const Item& it : items) total = align_up(total, 256) + it.bytes;
+  total = align_up(total, 256);
+  if (cudaMalloc(&ctx->mem, total) != cudaSuccess) {
+    cudaGetLastError();
+    delete ctx;
+    return FGBD_ENOMEM;
+  }
+  ctx->mem_bytes = total;
+  size_t off = 0;
+  for (const Item& it : items) {
+    off = align_up(off, 256);
+    *it.ptr = static_cast<char*>(ctx->mem) + off;
+    off += it.bytes;
+  }
+  ctx->sb.keys[0] = static_cast<uint32_t*>(keys0);
+  ctx->sb.keys[1] = static_cast<uint32_t*>(keys1);
+  ctx->sb.vals[0] = static_cast<uint32_t*>(vals0);
+  ctx->sb.vals[1] = static_cast<uint32_t*>(vals1);
+  if (cudaMemset(ctx->sc, 0, sizeof(DevScalars)) != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess) {
+    cudaFree(ctx->mem);
+    delete ctx;
+    return FGBD_ECUDA;
+  }
+  *out = ctx;
+  return FGBD_OK;
+}
+
+void fgbd_ctx_destroy(fgbd_ctx* ctx) {
+  if (!ctx) return;
+  DeviceGuard g(ctx->device);
+  cudaDeviceSynchronize();
+  for (cudaEvent_t e : ctx->ev)
+    if (e) cudaEventDestroy(e);
+  cudaFree(ctx->mem);
+  delete ctx;
+}
+
+const char* fgbd_last_error(const fgbd_ctx* ctx) { return ctx ? ctx->err.c_str() : ""; }
+
+fgbd_status fgbd_build_graph(fgbd_ctx* ctx, const int32_t* xyz, int64_t n, void* stream) {
+  if (!ctx) return FGBD_EINVAL;
+  DeviceGuard g(ctx->device);
+  return do_build(ctx, xyz, n, as_stream(stream));
+}
+
+fgbd_status fgbd_estimate_noise(fgbd_ctx* ctx, const void* rgb, int32_t dtype, double* sigma_est, void* stream) {
+  if (!ctx) return FGBD_EINVAL;
+  DeviceGuard g(ctx->device);
+  return do_estimate(ctx, rgb, dtype, sigma_est, as_stream(stream));
+}
+
+fgbd_status fgbd_select_filter(fgbd_ctx* ctx, const void* rgb, int32_t dtype, const double* sigma_est,
+                               int32_t* q_out, void* stream) {
+  if (!ctx) return FGBD_EINVAL;
+  DeviceGuard g(ctx->device);
+  return do_select(ctx, rgb, dtype, sigma_est, q_out, nullptr, FGBD_F32, as_stream(stream));
+}
+
+fgbd_status fgbd_denoise(fgbd_ctx* ctx, const void* rgb_in, int32_t in_dtype, int32_t q, void* rgb_out,
+                         int32_t out_dtype, void* stream) {
+  if (!ctx) return FGBD_EINVAL;
+  DeviceGuard g(ctx->device);
+  const cudaStream_t st = as_stream(stream);
+  if (!ctx->has_graph) return FGBD_ESTATE;
+  if (!dtype_ok(out_dtype)) return FGBD_EINVAL;
+  if (ctx->n > 0 && !rgb_out) return FGBD_EINVAL;
+  if (q < 0) {
+    if (!ctx->has_sel) return FGBD_ESTATE;
+    FGBD_LAUNCH(ctx, "filter_output", st,
+                launch_output(ctx->n, ctx->gb.rank1, ctx->x0, ctx->x1, ctx->sc, rgb_out, out_dtype, st));
+    return FGBD_OK;
+  }
+  if (q > kQCap || !dtype_ok(in_dtype)) return FGBD_EINVAL;
+  if (ctx->n > 0 && !rgb_in) return FGBD_EINVAL;
+  if (ctx->n > 0) {
+    FGBD_LAUNCH(ctx, "gather_colors", st,
+                launch_gather_colors(rgb_in, in_dtype, ctx->n, ctx->gb.perm, ctx->y8, ctx->yf, st));
+  }
+  // the gathered colours and filter buffers now hold this call's data
+  if (rgb_in != ctx->noise_rgb || in_dtype != ctx->noise_dtype) {
+    ctx->has_noise = false;
+    ctx->noise_rgb = nullptr;
+  }
+  ctx->has_sel = false;
+  cudaError_t e = cudaSuccess;
+  zero_region(ctx, offsetof(DevScalars, ysq_keep), offsetof(DevScalars, sel_end_), st, &e);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "memset");
+  const FilterArgs a = filter_args(ctx, 1, q, nullptr, rgb_out, out_dtype, in_dtype);
+  FGBD_LAUNCH(ctx, "filter_fixed", st, launch_filter(a, filter_grid_for(ctx, ctx->n), st));
+  return FGBD_OK;
+}
+
+fgbd_status fgbd_run(fgbd_ctx* ctx, const int32_t* xyz, int64_t n, const void* rgb_in, int32_t in_dtype,
+                     void* rgb_out, int32_t out_dtype, void* stream) {
+  if (!ctx) return FGBD_EINVAL;
+  if (!dtype_ok(in_dtype) || !dtype_ok(out_dtype)) return FGBD_EINVAL;
+  if (n > 0 && (!rgb_in || !rgb_out)) return FGBD_EINVAL;
+  DeviceGuard g(ctx->device);
+  const cudaStream_t st = as_stream(stream);
+  fgbd_status s = do_build(ctx, xyz, n, st);
+  if (s != FGBD_OK) return s;
+  s = do_estimate(ctx, rgb_in, in_dtype, nullptr, st);
+  if (s != FGBD_OK) return s;
+  return do_select(ctx, rgb_in, in_dtype, nullptr, nullptr, rgb_out, out_dtype, st);
+}
+
+fgbd_status fgbd_sync(fgbd_ctx* ctx, void* stream) {
+  if (!ctx) return FGBD_EINVAL;
+  DeviceGuard g(ctx->device);
+  return take_device_status(ctx, as_stream(stream));
+}
+
+fgbd_status fgbd_get_stats(fgbd_ctx* ctx, fgbd_stats* out, void* stream) {
+  if (!ctx || !out) return FGBD_EINVAL;
+  DeviceGuard g(ctx->device);
+  const fgbd_status s = take_device_status(ctx, as_stream(stream));
+  DevScalars h;
+  FGBD_CUDA(ctx, cudaMemcpy(&h, ctx->sc, sizeof(h), cudaMemcpyDeviceToHost));
+  std::memset(out, 0, sizeof(*out));
+  out->n = ctx->n;
+  out->valid = (ctx->has_graph ? 1 : 0) | (ctx->has_noise ? 2 : 0) | (ctx->has_sel ? 4 : 0);
+  if (ctx->has_graph) {
+    out->n_edges = int64_t(h.n_edges);
+    out->sigma_g = h.n_edges ? double(h.dist_fx) / double(1ull << kDistShift) / double(h.n_edges) : 0.0;
+  }
+  if (ctx->has_noise) {
+    out->n_patches = int64_t(h.n_patches);
+    for (int i = 0; i < kD; ++i) out->eigenvalues[i] = h.eig[i];
+    out->m = h.m;
+    out->tau = h.tau;
+    out->sigma_est = h.sigma_est;
+  }
+  out->q = h.q_sel;
+  out->launches = ctx->launches;
+  if (ctx->has_sel) {
+    out->n_keep = int64_t(h.n_keep);
+    out->n_objective = std::min(h.n_J, kQCap + 1);
+    for (int i = 0; i < out->n_objective; ++i) out->objective[i] = h.J[i];
+  }
+  return s;
+}
+
+fgbd_status fgbd_graph_csr(fgbd_ctx* ctx, int64_t* row_ptr, int32_t* col, float* w, int64_t col_capacity,
+                           int64_t* nnz_host, void* stream) {
+  if (!ctx || !nnz_host) return FGBD_EINVAL;
+  DeviceGuard g(ctx->device);
+  const cudaStream_t st = as_stream(stream);
+  if (!ctx->has_graph) return FGBD_ESTATE;
+  const fgbd_status s = take_device_status(ctx, st);
+  if (s != FGBD_OK) return s;
+  unsigned long long edges = 0;
+  FGBD_CUDA(ctx, cudaMemcpy(&edges, &ctx->sc->n_edges, sizeof(edges), cudaMemcpyDeviceToHost));
+  *nnz_host = int64_t(2 * edges);
+  if (!row_ptr) return FGBD_OK;
+  if (col_capacity < *nnz_host || (*nnz_host > 0 && !col)) return FGBD_EINVAL;
+  const int n = ctx->n;
+  FGBD_LAUNCH(ctx, "csr_degree", st, launch_csr_degree(n, ctx->gb, row_ptr, st));
+  FGBD_LAUNCH(ctx, "csr_scan", st, launch_scan_i64(row_ptr, int64_t(n) + 1, ctx->scan_tmp, st));
+  FGBD_LAUNCH(ctx, "csr_fill", st,
+              launch_csr_fill(n, ctx->params.bits, ctx->gb, row_ptr, col, w, col_capacity, ctx->sc, st));
+  FGBD_CUDA(ctx, cudaStreamSynchronize(st));
+  return FGBD_OK;
+}
+
+fgbd_status fgbd_get_orders(fgbd_ctx* ctx, int32_t* orders, void* stream) {
+  if (!ctx) return FGBD_EINVAL;
+  DeviceGuard g(ctx->device);
+  if (!ctx->has_graph) return FGBD_ESTATE;
+  if (ctx->n > 0 && !orders) return FGBD_EINVAL;
+  const cudaStream_t st = as_stream(stream);
+  for (int l = 0; l < 3 && ctx->n > 0; ++l)
+    FGBD_CUDA(ctx, cudaMemcpyAsync(orders + size_t(l) * ctx->n, ctx->gb.perm + size_t(l) * ctx->capacity,
+                                   size_t(ctx->n) * sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
+  return FGBD_OK;
+}
+
+fgbd_status fgbd_get_fslr(fgbd_ctx* ctx, float* spread, uint8_t* keep, void* stream) {
+  if (!ctx) return FGBD_EINVAL;
+  DeviceGuard g(ctx->device);
+  if (!ctx->has_sel) return FGBD_ESTATE;
+  const cudaStream_t st = as_stream(stream);
+  FGBD_LAUNCH(ctx, "fslr_export", st, launch_spread_export(ctx->n, ctx->gb.rank1, ctx->spread, ctx->x0, spread, keep, st));
+  return FGBD_OK;
+}
+
+fgbd_status fgbd_set_timing(fgbd_ctx* ctx, int32_t enable) {
+  if (!ctx) return FGBD_EINVAL;
+  DeviceGuard g(ctx->device);
+  if (enable && !ctx->ev[0]) {
+    for (cudaEvent_t& e : ctx->ev) FGBD_CUDA(ctx, cudaEventCreate(&e));
+  }
+  ctx->timing = enable != 0;
+  ctx->n_timed = 0;
+  return FGBD_OK;
+}
+
+fgbd_status fgbd_get_timings(fgbd_ctx* ctx, int32_t max, int32_t* count, char* names, float* ms) {
+  if (!ctx || !count || max < 0 || (max > 0 && (!names || !ms))) return FGBD_EINVAL;
+  DeviceGuard g(ctx->device);
+  const int k = std::min<int>(max, ctx->n_timed);
+  for (int i = 0; i < k; ++i) {
+    FGBD_CUDA(ctx, cudaEventSynchronize(ctx->ev[2 * i + 1]));
+    float t = 0.f;
+    FGBD_CUDA(ctx, cudaEventElapsedTime(&t, ctx->ev[2 * i], ctx->ev[2 * i + 1]));
+    ms[i] = t;
+    std::memset(names + size_t(i) * FGBD_NAME_LEN, 0, FGBD_NAME_LEN);
+    std::strncpy(names + size_t(i) * FGBD_NAME_LEN, ctx->ev_name[i], FGBD_NAME_LEN - 1);
+  }
+  *count = k;
+  ctx->n_timed = 0;
+  return FGBD_OK;
+}
+
+}  // extern "C"

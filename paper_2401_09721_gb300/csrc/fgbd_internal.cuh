@@ -1,0 +1,234 @@
+// Internal declarations shared by the FGBD CUDA translation units.
+//
+// Index spaces.  The caller's points are in "input order".  Internally every
+// per-point array is kept in "sorted order": the order of the first scan-line
+// code C1 = 2^{2b} z + 2^b y + x (Section 2.2, Eq. 1).  In that order the two
+// code-1 neighbours of point k are simply k-1 and k+1, and the packed C1 code
+// of point k doubles as its coordinates.  Neighbours along C2 and C3
+// (Eq. 2-3) are stored explicitly, four slots per point, with -1 marking an
+// empty slot (the end of a scan order, or a pair already linked by an earlier
+// code, so that the union graph of Section 2.2 is a set).
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace fgbd {
+
+constexpr int kMaxBits = 10;        // three b-bit coordinates fit a 32-bit code
+constexpr int kRadixBits = 8;
+constexpr int kRadix = 1 << kRadixBits;
+constexpr int kSortThreads = 256;
+constexpr int kSortKpt = 16;                       // keys per thread
+constexpr int kSortTile = kSortThreads * kSortKpt;  // 4096 keys per tile
+constexpr int kMaxPasses = 4;                      // ceil(30 / 8)
+constexpr int kK = 6;                              // neighbours per point at window 1
+constexpr int kD = 3 * (kK + 1);                   // patch dimension (Section 2.3)
+constexpr int kQCap = 256;                         // largest q_max accepted
+constexpr int kSqShift = 16;                       // fixed point of squared colours
+constexpr int kDistShift = 20;                     // fixed point of edge lengths
+constexpr int kNeThreads = 256;
+constexpr int kFilterThreads = 256;
+constexpr uint32_t kCoordMask = 0x3FFFFFFFu;       // low 30 bits: packed C1 code
+constexpr uint32_t kKeepBit = 0x80000000u;         // FSLR keep flag beside the code
+
+// latched device error bits
+enum : uint32_t {
+  kFlagRange = 1u,    // a coordinate outside [0, 2^b)
+  kFlagTimeout = 2u,  // a bounded device-side wait gave up
+};
+
+// Device-resident scalars of one context.  Regions are zeroed separately by
+// the call that fills them (see the offsets used in api.cu).
+struct DevScalars {
+  // ---- graph build region
+  unsigned long long n_edges;   // distinct undirected edges E
+  unsigned long long dist_fx;   // sum of edge lengths, fixed point 2^-kDistShift
+  uint32_t hist[3][kMaxPasses][kRadix];
+  uint32_t tile_counter[kMaxPasses];
+  uint32_t build_end_;
+  // ---- noise estimate region
+  unsigned long long n_patches;
+  long long s1[kD];             // sum of (a - 128)
+  long long s2[kD * kD];        // sum of (a - 128)(a - 128)^T (upper triangle filled)
+  uint32_t ne_end_;
+  // ---- results of the noise estimate
+  double eig[kD];               // descending
+  double tau;
+  double sigma_est;
+  int32_t m;
+  int32_t ne_valid;
+  // ---- selection region
+  unsigned long long ysq_keep;  // fixed point 2^-kSqShift
+  unsigned long long ysq_all;
+  unsigned long long n_keep;
+  unsigned long long sumsq[kQCap + 1];
+  uint32_t barrier;
+  uint32_t sel_end_;
+  // ---- results of the selection
+  double J[kQCap + 1];
+  int32_t q_sel;
+  int32_t n_J;
+  int32_t sel_valid;
+  // ---- latched errors (never zeroed by a call; cleared when read)
+  uint32_t status;
+};
+
+// Sort scratch for one build.
+struct SortBufs {
+  uint32_t* keys[2];   // ping-pong [3][cap]
+  uint32_t* vals[2];   // ping-pong [3][cap]
+  uint32_t* lookback;  // [passes][3][tiles][kRadix]
+  int tiles;           // tiles per code at this n
+  int passes;
+};
+
+// Graph in sorted order.
+struct GraphBufs {
+  int32_t* perm;     // [3][cap] input index at each position of each code order
+  int32_t* rank1;    // [cap] position of each input point in the C1 order
+  int32_t* rank2;    // [cap] position of each input point in the C2 order
+  uint32_t* pk;      // [cap] packed C1 code of each sorted point (its coordinates)
+  int4* c4;          // [cap] C2 prev, C2 next, C3 prev, C3 next (sorted ids, -1 empty)
+};
+
+// ---------------------------------------------------------------- launchers
+// Every launcher enqueues on `stream` and returns the launch error.
+
+cudaError_t launch_hist(const int32_t* xyz, int n, int bits, int passes, uint32_t* zero_buf,
+                        size_t zero_words, DevScalars* sc, int num_sms, cudaStream_t stream);
+cudaError_t launch_sort_pass(int pass, int passes, const int32_t* xyz, int n, int bits, int cap,
+                             const SortBufs& sb, const GraphBufs& gb, DevScalars* sc,
+                             cudaStream_t stream);
+cudaError_t launch_link(int n, int bits, int cap, const GraphBufs& gb, DevScalars* sc, int num_sms,
+                        cudaStream_t stream);
+
+cudaError_t launch_gather_colors(const void* rgb, int dtype, int n, const int32_t* perm1,
+                                 uint32_t* y8, float4* yf, cudaStream_t stream);
+cudaError_t launch_ne_moments(int n, int bits, int dtype, const GraphBufs& gb, const uint32_t* y8,
+                              const float4* yf, float* spread, double* f64_partials,
+                              DevScalars* sc, int num_sms, bool moments, cudaStream_t stream);
+cudaError_t launch_ne_finalize(int dtype, const double* f64_partials, int nblocks,
+                               DevScalars* sc, double* sigma_out, cudaStream_t stream);
+int ne_moment_blocks(int n, int num_sms);
+
+struct FilterArgs {
+  int n;
+  int bits;
+  int dtype;             // colours held in y8 (0) or yf (1)
+  int mode;              // 0: select q (Eq. 6), 1: fixed q
+  int q_fixed;           // mode 1
+  int q_max;             // mode 0
+  double fslr_factor;
+  const double* sigma_src;  // sigma_est to use (device)
+  const uint32_t* y8;
+  const float4* yf;
+  const float* spread;
+  const uint32_t* pk;
+  const int4* c4;
+  const int32_t* rank1;
+  float4* xbuf0;
+  float4* xbuf1;
+  void* out;             // input-order output or nullptr
+  int out_dtype;
+  DevScalars* sc;
+};
+cudaError_t launch_filter(const FilterArgs& a, int grid, cudaStream_t stream);
+int filter_grid(int n, int num_sms);
+cudaError_t launch_output(int n, const int32_t* rank1, const float4* xbuf0, const float4* xbuf1,
+                          const DevScalars* sc, void* out, int out_dtype, cudaStream_t stream);
+
+// CSR export in input order
+cudaError_t launch_csr_degree(int n, const GraphBufs& gb, int64_t* deg_out, cudaStream_t stream);
+cudaError_t launch_scan_i64(int64_t* data, int64_t count, int64_t* block_tmp, cudaStream_t stream);
+cudaError_t launch_csr_fill(int n, int bits, const GraphBufs& gb, const int64_t* row_ptr, int32_t* col,
+                            float* w, int64_t col_capacity, const DevScalars* sc, cudaStream_t stream);
+cudaError_t launch_spread_export(int n, const int32_t* rank1, const float* spread, const float4* x0,
+                                 float* spread_out, uint8_t* keep_out, cudaStream_t stream);
+
+// ---------------------------------------------------------------- device helpers
+
+__host__ __device__ inline uint32_t code_of(int which, uint32_t x, uint32_t y, uint32_t z, int b) {
+  // Eq. 1-3 with the three b-bit fields packed high to low
+  switch (which) {
+    case 0: return (z << (2 * b)) | (y << b) | x;
+    case 1: return (x << (2 * b)) | (z << b) | y;
+    default: return (y << (2 * b)) | (x << b) | z;
+  }
+}
+
+// an index read from device memory is used only if it lies in [0, n)
+__device__ __forceinline__ bool in_range(int v, int n) { return unsigned(v) < unsigned(n); }
+
+__device__ __forceinline__ void decode_c1(uint32_t c, int b, int& x, int& y, int& z) {
+  const uint32_t m = (1u << b) - 1u;
+  x = int(c & m);
+  y = int((c >> b) & m);
+  z = int((c >> (2 * b)) & m);
+}
+
+__device__ __forceinline__ int sq_dist_c1(uint32_t a, uint32_t c, int b) {
+  int ax, ay, az, cx, cy, cz;
+  decode_c1(a, b, ax, ay, az);
+  decode_c1(c, b, cx, cy, cz);
+  const int dx = cx - ax, dy = cy - ay, dz = cz - az;
+  return dx * dx + dy * dy + dz * dz;
+}
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+constexpr unsigned long long kWaitLimitNs = 2000000000ull;  // 2 s for any device-side wait
+
+__device__ __forceinline__ uint32_t ld_volatile(const uint32_t* p) {
+  return *reinterpret_cast<const volatile uint32_t*>(p);
+}
+__device__ __forceinline__ void st_volatile(uint32_t* p, uint32_t v) {
+  *reinterpret_cast<volatile uint32_t*>(p) = v;
+}
+
+// round(v^2 * 2^kSqShift) without cancellation: v*v in fp32 plus its exact
+// rounding error from an fma, each scaled and rounded to an integer
+__device__ __forceinline__ unsigned long long sq_fixed(float v) {
+  const float p = v * v;
+  const float e = fmaf(v, v, -p);
+  const float s = float(1 << kSqShift);
+  return (unsigned long long)(__float2ll_rn(p * s) + __float2ll_rn(e * s));
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// block-wide sum of a 64-bit counter, result valid in thread 0
+template <int THREADS>
+__device__ __forceinline__ unsigned long long block_sum_u64(unsigned long long v,
+                                                            unsigned long long* smem) {
+  v = warp_sum(v);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) smem[warp] = v;
+  __syncthreads();
+  unsigned long long t = 0;
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int w = 0; w < THREADS / 32; ++w) t += smem[w];
+  }
+  __syncthreads();
+  return t;
+}
+
+// sigma_g (Section 2.2) from the build sums
+__device__ __forceinline__ double sigma_g_of(const DevScalars* sc) {
+  const unsigned long long e = sc->n_edges;
+  if (e == 0) return 0.0;
+  return double(sc->dist_fx) * (1.0 / double(1ull << kDistShift)) / double(e);
+}
+
+}  // namespace fgbd

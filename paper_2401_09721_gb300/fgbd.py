@@ -1,0 +1,349 @@
+"""Thin ctypes binding of the FGBD C ABI (include/fgbd.h).
+
+Argument marshalling only: every step of the method runs in the CUDA library
+``libfgbd.so``.  Tensors are passed as device pointers; the current PyTorch
+CUDA stream is used unless one is given.  If the library is missing or fails
+to load, every call raises ``RuntimeError``: there is no CPU fallback.
+
+The functions below carry the names of the C entry points.  ``Context`` is a
+small convenience wrapper over them.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libfgbd.so")
+
+FGBD_U8 = 0
+FGBD_F32 = 1
+PATCH_DIM = 21
+Q_CAP = 256
+
+STATUS = {
+    0: "FGBD_OK",
+    1: "FGBD_EINVAL",
+    2: "FGBD_ERANGE",
+    3: "FGBD_ENOMEM",
+    4: "FGBD_ECUDA",
+    5: "FGBD_ETIMEOUT",
+    6: "FGBD_ESTATE",
+    7: "FGBD_ENOTIMPL",
+}
+
+
+class FgbdError(RuntimeError):
+    def __init__(self, status: int, where: str, detail: str = ""):
+        self.status = status
+        msg = f"{where}: {STATUS.get(status, status)}"
+        if detail:
+            msg += f" ({detail})"
+        super().__init__(msg)
+
+
+class Params(ctypes.Structure):
+    _fields_ = [
+        ("bits", ctypes.c_int32),
+        ("window", ctypes.c_int32),
+        ("fslr_factor", ctypes.c_double),
+        ("q_max", ctypes.c_int32),
+        ("reserved", ctypes.c_int32 * 7),
+    ]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [
+        ("n", ctypes.c_int64),
+        ("n_edges", ctypes.c_int64),
+        ("sigma_g", ctypes.c_double),
+        ("n_patches", ctypes.c_int64),
+        ("eigenvalues", ctypes.c_double * PATCH_DIM),
+        ("m", ctypes.c_int32),
+        ("q", ctypes.c_int32),
+        ("tau", ctypes.c_double),
+        ("sigma_est", ctypes.c_double),
+        ("n_keep", ctypes.c_int64),
+        ("n_objective", ctypes.c_int32),
+        ("valid", ctypes.c_int32),
+        ("objective", ctypes.c_double * (Q_CAP + 1)),
+        ("launches", ctypes.c_int64),
+    ]
+
+    def as_dict(self) -> dict:
+        return dict(
+            n=self.n, n_edges=self.n_edges, sigma_g=self.sigma_g, n_patches=self.n_patches,
+            eigenvalues=list(self.eigenvalues), m=self.m, q=self.q, tau=self.tau,
+            sigma_est=self.sigma_est, n_keep=self.n_keep, valid=self.valid,
+            objective=list(self.objective[: self.n_objective]), launches=self.launches,
+        )
+
+
+_lib = None
+
+# name -> (restype, argtypes)
+_P = ctypes.c_void_p
+_SIGS = {
+    "fgbd_abi_version": (ctypes.c_int32, []),
+    "fgbd_status_str": (ctypes.c_char_p, [ctypes.c_int]),
+    "fgbd_params_default": (ctypes.c_int, [ctypes.POINTER(Params)]),
+    "fgbd_ctx_create": (ctypes.c_int, [ctypes.c_int64, ctypes.POINTER(Params), ctypes.POINTER(_P)]),
+    "fgbd_ctx_destroy": (None, [_P]),
+    "fgbd_last_error": (ctypes.c_char_p, [_P]),
+    "fgbd_build_graph": (ctypes.c_int, [_P, _P, ctypes.c_int64, _P]),
+    "fgbd_estimate_noise": (ctypes.c_int, [_P, _P, ctypes.c_int32, _P, _P]),
+    "fgbd_select_filter": (ctypes.c_int, [_P, _P, ctypes.c_int32, _P, _P, _P]),
+    "fgbd_denoise": (ctypes.c_int, [_P, _P, ctypes.c_int32, ctypes.c_int32, _P, ctypes.c_int32, _P]),
+    "fgbd_run": (ctypes.c_int, [_P, _P, ctypes.c_int64, _P, ctypes.c_int32, _P, ctypes.c_int32, _P]),
+    "fgbd_sync": (ctypes.c_int, [_P, _P]),
+    "fgbd_get_stats": (ctypes.c_int, [_P, ctypes.POINTER(Stats), _P]),
+    "fgbd_graph_csr": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64), _P]),
+    "fgbd_get_orders": (ctypes.c_int, [_P, _P, _P]),
+    "fgbd_get_fslr": (ctypes.c_int, [_P, _P, _P, _P]),
+    "fgbd_set_timing": (ctypes.c_int, [_P, ctypes.c_int32]),
+    "fgbd_get_timings": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32), _P, _P]),
+}
+NAME_LEN = 32
+TIMING_CAP = 256
+
+
+def lib() -> ctypes.CDLL:
+    """Load libfgbd.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with paper_2401_09721_gb300.build.build()")
+        handle = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(handle, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = handle
+    return _lib
+
+
+def _check(status: int, where: str, ctx=None):
+    if status != 0:
+        detail = ""
+        if ctx is not None and status == 4:
+            detail = (lib().fgbd_last_error(ctx) or b"").decode(errors="replace")
+        raise FgbdError(status, where, detail)
+
+
+def _stream(stream) -> ctypes.c_void_p:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    if isinstance(stream, torch.cuda.Stream):
+        return ctypes.c_void_p(stream.cuda_stream)
+    return ctypes.c_void_p(int(stream))
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _dtype_code(t: torch.Tensor) -> int:
+    if t.dtype == torch.uint8:
+        return FGBD_U8
+    if t.dtype == torch.float32:
+        return FGBD_F32
+    raise TypeError(f"colours must be uint8 or float32, not {t.dtype}")
+
+
+def _need_cuda(t: torch.Tensor, name: str, shape_n=None):
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if shape_n is not None and tuple(t.shape) != (shape_n, 3):
+        raise ValueError(f"{name} must have shape [{shape_n}, 3], got {tuple(t.shape)}")
+
+
+# ---------------------------------------------------------------- C-named functions
+
+def fgbd_params_default() -> Params:
+    p = Params()
+    _check(lib().fgbd_params_default(ctypes.byref(p)), "fgbd_params_default")
+    return p
+
+
+def fgbd_ctx_create(capacity: int, params: Params | None = None) -> ctypes.c_void_p:
+    out = ctypes.c_void_p()
+    _check(lib().fgbd_ctx_create(int(capacity), ctypes.byref(params) if params else None, ctypes.byref(out)),
+           "fgbd_ctx_create")
+    return out
+
+
+def fgbd_ctx_destroy(ctx) -> None:
+    lib().fgbd_ctx_destroy(ctx)
+
+
+def fgbd_build_graph(ctx, xyz: torch.Tensor, stream=None) -> None:
+    if xyz.dtype != torch.int32:
+        raise TypeError("xyz must be int32")
+    _need_cuda(xyz, "xyz", xyz.shape[0])
+    _check(lib().fgbd_build_graph(ctx, _ptr(xyz), xyz.shape[0], _stream(stream)), "fgbd_build_graph", ctx)
+
+
+def fgbd_estimate_noise(ctx, rgb: torch.Tensor, sigma_out: torch.Tensor | None = None, stream=None) -> None:
+    _need_cuda(rgb, "rgb")
+    if sigma_out is not None and (sigma_out.dtype != torch.float64 or not sigma_out.is_cuda):
+        raise TypeError("sigma_out must be a CUDA float64 tensor")
+    _check(lib().fgbd_estimate_noise(ctx, _ptr(rgb), _dtype_code(rgb), _ptr(sigma_out), _stream(stream)),
+           "fgbd_estimate_noise", ctx)
+
+
+def fgbd_select_filter(ctx, rgb: torch.Tensor, sigma_est: torch.Tensor | None = None,
+                       q_out: torch.Tensor | None = None, stream=None) -> None:
+    _need_cuda(rgb, "rgb")
+    if sigma_est is not None and (sigma_est.dtype != torch.float64 or not sigma_est.is_cuda):
+        raise TypeError("sigma_est must be a CUDA float64 tensor")
+    if q_out is not None and (q_out.dtype != torch.int32 or not q_out.is_cuda):
+        raise TypeError("q_out must be a CUDA int32 tensor")
+    _check(lib().fgbd_select_filter(ctx, _ptr(rgb), _dtype_code(rgb), _ptr(sigma_est), _ptr(q_out),
+                                    _stream(stream)), "fgbd_select_filter", ctx)
+
+
+def fgbd_denoise(ctx, rgb_in: torch.Tensor | None, q: int, rgb_out: torch.Tensor, stream=None) -> None:
+    _need_cuda(rgb_out, "rgb_out")
+    in_code = FGBD_U8
+    if rgb_in is not None:
+        _need_cuda(rgb_in, "rgb_in")
+        in_code = _dtype_code(rgb_in)
+    _check(lib().fgbd_denoise(ctx, _ptr(rgb_in), in_code, int(q), _ptr(rgb_out), _dtype_code(rgb_out),
+                              _stream(stream)), "fgbd_denoise", ctx)
+
+
+def fgbd_run(ctx, xyz: torch.Tensor, rgb_in: torch.Tensor, rgb_out: torch.Tensor, stream=None) -> None:
+    if xyz.dtype != torch.int32:
+        raise TypeError("xyz must be int32")
+    n = xyz.shape[0]
+    _need_cuda(xyz, "xyz", n)
+    _need_cuda(rgb_in, "rgb_in", n)
+    _need_cuda(rgb_out, "rgb_out", n)
+    _check(lib().fgbd_run(ctx, _ptr(xyz), n, _ptr(rgb_in), _dtype_code(rgb_in), _ptr(rgb_out),
+                          _dtype_code(rgb_out), _stream(stream)), "fgbd_run", ctx)
+
+
+def fgbd_sync(ctx, stream=None) -> None:
+    _check(lib().fgbd_sync(ctx, _stream(stream)), "fgbd_sync", ctx)
+
+
+def fgbd_get_stats(ctx, stream=None) -> dict:
+    s = Stats()
+    _check(lib().fgbd_get_stats(ctx, ctypes.byref(s), _stream(stream)), "fgbd_get_stats", ctx)
+    return s.as_dict()
+
+
+def fgbd_graph_csr(ctx, n: int, device, with_weights: bool = True, stream=None):
+    nnz = ctypes.c_int64()
+    _check(lib().fgbd_graph_csr(ctx, None, None, None, 0, ctypes.byref(nnz), _stream(stream)), "fgbd_graph_csr", ctx)
+    row_ptr = torch.empty(n + 1, dtype=torch.int64, device=device)
+    col = torch.empty(max(nnz.value, 1), dtype=torch.int32, device=device)
+    w = torch.empty(max(nnz.value, 1), dtype=torch.float32, device=device) if with_weights else None
+    _check(lib().fgbd_graph_csr(ctx, _ptr(row_ptr), _ptr(col), _ptr(w), col.numel(), ctypes.byref(nnz),
+                                _stream(stream)), "fgbd_graph_csr", ctx)
+    return row_ptr, col[: nnz.value], (w[: nnz.value] if w is not None else None)
+
+
+def fgbd_get_orders(ctx, n: int, device, stream=None) -> torch.Tensor:
+    out = torch.empty((3, max(n, 1)), dtype=torch.int32, device=device)
+    _check(lib().fgbd_get_orders(ctx, _ptr(out), _stream(stream)), "fgbd_get_orders", ctx)
+    return out[:, :n]
+
+
+def fgbd_get_fslr(ctx, n: int, device, stream=None):
+    spread = torch.empty(max(n, 1), dtype=torch.float32, device=device)
+    keep = torch.empty(max(n, 1), dtype=torch.uint8, device=device)
+    _check(lib().fgbd_get_fslr(ctx, _ptr(spread), _ptr(keep), _stream(stream)), "fgbd_get_fslr", ctx)
+    return spread[:n], keep[:n]
+
+
+def fgbd_set_timing(ctx, enable: bool) -> None:
+    _check(lib().fgbd_set_timing(ctx, 1 if enable else 0), "fgbd_set_timing", ctx)
+
+
+def fgbd_get_timings(ctx) -> list:
+    """[(kernel name, milliseconds)] of the launches timed since the last call."""
+    names = ctypes.create_string_buffer(TIMING_CAP * NAME_LEN)
+    ms = (ctypes.c_float * TIMING_CAP)()
+    count = ctypes.c_int32()
+    _check(lib().fgbd_get_timings(ctx, TIMING_CAP, ctypes.byref(count), names, ms), "fgbd_get_timings", ctx)
+    out = []
+    for i in range(count.value):
+        raw = names.raw[i * NAME_LEN:(i + 1) * NAME_LEN].split(b"\0", 1)[0]
+        out.append((raw.decode(), float(ms[i])))
+    return out
+
+
+# ---------------------------------------------------------------- convenience wrapper
+
+class Context:
+    """One FGBD context on the current CUDA device, for frames of up to ``capacity`` points."""
+
+    def __init__(self, capacity: int, bits: int = 10, window: int = 1, fslr_factor: float = 2.0,
+                 q_max: int = 64):
+        p = fgbd_params_default()
+        p.bits, p.window, p.fslr_factor, p.q_max = bits, window, fslr_factor, q_max
+        self.params = p
+        self.capacity = int(capacity)
+        self.device = torch.device("cuda", torch.cuda.current_device())
+        self.handle = fgbd_ctx_create(capacity, p)
+        self.n = 0
+
+    def close(self):
+        if getattr(self, "handle", None):
+            fgbd_ctx_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def build_graph(self, xyz, stream=None):
+        fgbd_build_graph(self.handle, xyz, stream)
+        self.n = xyz.shape[0]
+
+    def estimate_noise(self, rgb, sigma_out=None, stream=None):
+        fgbd_estimate_noise(self.handle, rgb, sigma_out, stream)
+
+    def select_filter(self, rgb, sigma_est=None, q_out=None, stream=None):
+        fgbd_select_filter(self.handle, rgb, sigma_est, q_out, stream)
+
+    def denoise(self, rgb_in, q, out_dtype=torch.float32, out=None, stream=None):
+        if out is None:
+            out = torch.empty((self.n, 3), dtype=out_dtype, device=self.device)
+        fgbd_denoise(self.handle, rgb_in, q, out, stream)
+        return out
+
+    def run(self, xyz, rgb_in, out_dtype=torch.float32, out=None, stream=None):
+        if out is None:
+            out = torch.empty((xyz.shape[0], 3), dtype=out_dtype, device=self.device)
+        fgbd_run(self.handle, xyz, rgb_in, out, stream)
+        self.n = xyz.shape[0]
+        return out
+
+    def sync(self, stream=None):
+        fgbd_sync(self.handle, stream)
+
+    def stats(self, stream=None) -> dict:
+        return fgbd_get_stats(self.handle, stream)
+
+    def graph_csr(self, with_weights=True, stream=None):
+        return fgbd_graph_csr(self.handle, self.n, self.device, with_weights, stream)
+
+    def orders(self, stream=None):
+        return fgbd_get_orders(self.handle, self.n, self.device, stream)
+
+    def fslr(self, stream=None):
+        return fgbd_get_fslr(self.handle, self.n, self.device, stream)
+
+    def set_timing(self, enable: bool):
+        fgbd_set_timing(self.handle, enable)
+
+    def timings(self) -> list:
+        return fgbd_get_timings(self.handle)

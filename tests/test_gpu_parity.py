@@ -1,0 +1,315 @@
+"""CUDA path vs the FP64 oracle, element by element, through the C ABI.
+
+Tolerances (from the method's arithmetic and the required accuracy):
+  scan orders, CSR row pointers and columns   bit-exact (integer work)
+  sigma_g                                     1e-6 relative (float32 sqrt per edge)
+  Eq. 4 weights                               |log w| within 1e-6 * max(1, |log w|)
+  eigenvalues                                 1e-7 of the largest
+  sigma_est                                   1e-5 relative
+  FSLR spread                                 1e-5 relative; keep flags equal except
+                                              within 1e-9 of the threshold
+  J(q)                                        1e-3 + 1e-6 sigma^2 absolute
+  q*                                          equal, or the oracle's J at both q
+                                              within that tolerance (a tie)
+  denoised colours (float32 out)              1e-4 on the [0, 1] scale
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import fgbd_oracle as orc
+from paper_2401_09721_gb300 import build, synth
+
+pytestmark = pytest.mark.gpu
+
+COLOR_TOL = 1e-4 * 255.0
+
+
+@pytest.fixture(scope="module")
+def F():
+    build.build()
+    from paper_2401_09721_gb300 import fgbd
+    assert torch.cuda.is_available(), "these tests need a CUDA GPU"
+    return fgbd
+
+
+def gpu_frame(F, xyz, rgb, bits, q_max=64):
+    ctx = F.Context(max(len(xyz), 1), bits=bits, q_max=q_max)
+    x = torch.from_numpy(np.ascontiguousarray(xyz, dtype=np.int32)).cuda()
+    c = torch.from_numpy(np.ascontiguousarray(rgb)).cuda()
+    ctx.build_graph(x)
+    ctx.estimate_noise(c)
+    ctx.select_filter(c)
+    out = ctx.denoise(None, -1, out_dtype=torch.float32)
+    out8 = ctx.denoise(None, -1, out_dtype=torch.uint8)
+    st = ctx.stats()
+    row_ptr, col, w = ctx.graph_csr()
+    orders = ctx.orders()
+    spread, keep = ctx.fslr()
+    ctx.sync()
+    return ctx, dict(stats=st, out=out.cpu().numpy(), out8=out8.cpu().numpy(), row_ptr=row_ptr.cpu().numpy(),
+                     col=col.cpu().numpy(), w=w.cpu().numpy(), orders=orders.cpu().numpy(),
+                     spread=spread.cpu().numpy(), keep=keep.cpu().numpy().astype(bool), x=x, c=c)
+
+
+def check_graph(g, res, xyz):
+    assert np.array_equal(g["orders"], res.orders), "scan orders differ"
+    assert np.array_equal(g["row_ptr"], res.row_ptr), "CSR row pointers differ"
+    assert np.array_equal(g["col"], res.col.astype(np.int32)), "CSR columns differ"
+    st = g["stats"]
+    assert st["n_edges"] * 2 == res.col.size
+    if res.col.size:
+        assert st["sigma_g"] == pytest.approx(res.sigma_g, rel=1e-6)
+        lw_or = np.log(np.maximum(res.w, 1e-300))
+        ok = res.w > 1e-30
+        lw_gpu = np.log(np.maximum(g["w"].astype(np.float64), 1e-300))
+        err = np.abs(lw_gpu - lw_or)[ok]
+        assert (err <= 1e-6 * np.maximum(1.0, np.abs(lw_or[ok])) + 1e-6).all()
+
+
+def check_noise(g, res):
+    st = g["stats"]
+    nz = res.noise
+    assert st["n_patches"] == nz["n_patches"]
+    if nz["n_patches"] == 0:
+        assert st["sigma_est"] == 0.0
+        return
+    lam = np.array(st["eigenvalues"])
+    assert np.allclose(lam, nz["eigenvalues"], rtol=0, atol=1e-7 * abs(nz["eigenvalues"][0]) + 1e-9)
+    assert st["m"] == nz["m"]
+    assert st["sigma_est"] == pytest.approx(nz["sigma_est"], rel=1e-5)
+
+
+def check_fslr(g, res, factor=2.0):
+    assert np.allclose(g["spread"], res.spread, rtol=1e-5, atol=1e-5)
+    thr = factor * res.noise["sigma_est"]
+    near = np.abs(res.spread - thr) <= 1e-9 * max(thr, 1e-30)
+    raw = ~(res.spread > thr)
+    if not raw[~near].any():
+        return  # no point clearly kept: the selection falls back to all points
+    assert np.array_equal(g["keep"][~near], raw[~near])
+
+
+def check_selection(F, ctx, g, res, y):
+    st = g["stats"]
+    sig2 = res.noise["sigma_est"] ** 2
+    jtol = 1e-3 + 1e-6 * sig2
+    J = np.array(st["objective"])
+    common = min(len(J), len(res.J))
+    assert common >= 1
+    assert np.allclose(J[:common], np.array(res.J[:common]), rtol=0, atol=jtol)
+    if st["q"] == res.q:
+        out = g["out"]
+    else:
+        # the two sides stopped at different q: accept only a tie of the oracle's objective
+        Jq = orc.select_q(y, res.row_ptr, res.col, res.rw, res.keep, res.noise["sigma_est"], max(st["q"], res.q) + 1)[2]
+        assert abs(Jq[st["q"]] - Jq[res.q]) <= jtol
+        out = ctx.denoise(g["c"], res.q, out_dtype=torch.float32).cpu().numpy()
+    assert np.abs(out - res.out).max() <= COLOR_TOL
+    return out
+
+
+def check_u8(out8, ref):
+    r = np.clip(np.rint(ref), 0, 255)
+    diff = np.abs(out8.astype(np.int64) - r.astype(np.int64))
+    frac = np.abs(ref - np.floor(ref) - 0.5)
+    assert (diff[frac > 1e-3] == 0).all()
+    assert diff.max() <= 1
+
+
+def full_check(F, xyz, rgb, bits, q_max=64):
+    res = orc.fgbd(xyz, rgb, orc.Params(bits=bits, q_max=q_max))
+    ctx, g = gpu_frame(F, xyz, rgb, bits, q_max)
+    check_graph(g, res, xyz)
+    check_noise(g, res)
+    check_fslr(g, res)
+    out = check_selection(F, ctx, g, res, rgb)
+    if g["stats"]["q"] == res.q:
+        check_u8(g["out8"], res.out)
+    ctx.close()
+    return res, g
+
+
+# ------------------------------------------------------------------ frames like the paper's
+
+def test_sphere_frame_20k(F):
+    fr = synth.sphere_frame(20500, 9, 20.0, 0)
+    res, g = full_check(F, fr.xyz, fr.noisy, 9)
+    assert g["stats"]["n"] == fr.n and res.q >= 1
+
+
+@pytest.mark.parametrize("sigma", [10.0, 30.0, 50.0])
+def test_dense_shell_frames(F, sigma):
+    xyz = synth.torso_points(60000, 8, 1)
+    clean = synth.piecewise_colors(xyz, 8, 1)
+    noisy = synth.add_noise_u8(clean, sigma, 2)
+    full_check(F, xyz, noisy, 8)
+
+
+def test_float_colours(F):
+    xyz = synth.torso_points(30000, 8, 3)
+    clean = synth.piecewise_colors(xyz, 8, 3, as_float=True)
+    noisy = synth.add_noise_f32(clean, 25.0, 3)
+    full_check(F, xyz, noisy, 8)
+
+
+# ------------------------------------------------------------------ ragged sizes and tiles
+
+@pytest.mark.parametrize("n,bits,seed", [(3, 2, 0), (7, 3, 1), (31, 4, 2), (33, 4, 3), (257, 5, 4),
+                                         (4095, 6, 5), (4096, 6, 6), (4097, 6, 7), (8193, 7, 8),
+                                         (12289, 10, 9), (40000, 9, 10)])
+def test_random_clouds(F, n, bits, seed):
+    rng = np.random.default_rng(seed)
+    xyz = rng.integers(0, 1 << bits, size=(n, 3)).astype(np.int32)   # repeated voxels included
+    rgb = rng.integers(0, 256, size=(n, 3)).astype(np.uint8)
+    full_check(F, xyz, rgb, bits)
+
+
+@pytest.mark.parametrize("bits", [1, 2, 3, 5, 8, 10])
+def test_every_bit_width(F, bits):
+    rng = np.random.default_rng(100 + bits)
+    n = 5000
+    xyz = rng.integers(0, 1 << bits, size=(n, 3)).astype(np.int32)
+    rgb = rng.integers(0, 256, size=(n, 3)).astype(np.uint8)
+    full_check(F, xyz, rgb, bits)
+
+
+# ------------------------------------------------------------------ degenerate cases
+
+def test_empty_frame(F):
+    ctx = F.Context(16, bits=4)
+    x = torch.empty((0, 3), dtype=torch.int32, device="cuda")
+    c = torch.empty((0, 3), dtype=torch.uint8, device="cuda")
+    ctx.build_graph(x)
+    ctx.estimate_noise(c)
+    ctx.select_filter(c)
+    out = ctx.denoise(None, -1)
+    st = ctx.stats()
+    assert out.shape == (0, 3) and st["n"] == 0 and st["n_edges"] == 0 and st["sigma_est"] == 0.0 and st["q"] == 0
+
+
+@pytest.mark.parametrize("n", [1, 2, 6])
+def test_tiny_frames(F, n):
+    rng = np.random.default_rng(n)
+    xyz = rng.integers(0, 16, size=(n, 3)).astype(np.int32)
+    rgb = rng.integers(0, 256, size=(n, 3)).astype(np.uint8)
+    res, g = full_check(F, xyz, rgb, 4)
+    assert g["stats"]["q"] == 0 and np.array_equal(g["out"], rgb.astype(np.float32))
+
+
+def test_all_points_identical(F):
+    xyz = np.full((50, 3), 7, np.int32)
+    rgb = np.random.default_rng(1).integers(0, 256, size=(50, 3)).astype(np.uint8)
+    res, g = full_check(F, xyz, rgb, 4)
+    assert g["stats"]["sigma_g"] == 0.0
+
+
+def test_out_of_range_coordinate_is_reported(F):
+    ctx = F.Context(100, bits=4)
+    xyz = np.random.default_rng(0).integers(0, 16, size=(100, 3)).astype(np.int32)
+    xyz[17, 1] = 16
+    ctx.build_graph(torch.from_numpy(xyz).cuda())
+    with pytest.raises(F.FgbdError) as ei:
+        ctx.sync()
+    assert ei.value.status == 2
+    xyz[17, 1] = -1
+    ctx.build_graph(torch.from_numpy(xyz).cuda())
+    with pytest.raises(F.FgbdError):
+        ctx.sync()
+    xyz[17, 1] = 3
+    ctx.build_graph(torch.from_numpy(xyz).cuda())
+    ctx.sync()
+
+
+def test_call_order_and_arguments(F):
+    ctx = F.Context(100, bits=4)
+    c = torch.zeros((100, 3), dtype=torch.uint8, device="cuda")
+    with pytest.raises(F.FgbdError) as ei:
+        ctx.estimate_noise(c)
+    assert ei.value.status == 6
+    x = torch.from_numpy(np.random.default_rng(0).integers(0, 16, size=(100, 3)).astype(np.int32)).cuda()
+    ctx.build_graph(x)
+    with pytest.raises(F.FgbdError):
+        ctx.select_filter(c)
+    ctx.estimate_noise(c)
+    other = c.clone()
+    with pytest.raises(F.FgbdError):
+        ctx.select_filter(other)           # colours other than the estimate's
+    with pytest.raises(F.FgbdError):
+        ctx.denoise(None, -1)              # nothing selected yet
+    big = torch.zeros((200, 3), dtype=torch.int32, device="cuda")
+    with pytest.raises(F.FgbdError):
+        ctx.build_graph(big)               # above capacity
+
+
+# ------------------------------------------------------------------ fixed q and external sigma
+
+@pytest.mark.parametrize("q", [0, 1, 2, 5, 17])
+def test_fixed_power_filter(F, q):
+    xyz = synth.torso_points(20000, 8, 5)
+    rgb = synth.add_noise_u8(synth.piecewise_colors(xyz, 8, 5), 20.0, 5)
+    codes = orc.scan_line_codes(xyz, 8)
+    row_ptr, col = orc.adjacency_csr(orc.slg_edges(orc.scan_orders(codes)), len(xyz))
+    rw = orc.random_walk_weights(xyz, row_ptr, col, orc.sigma_g(xyz, row_ptr, col))
+    ref = orc.lowpass(rgb, row_ptr, col, rw, q)
+    ctx = F.Context(len(xyz), bits=8)
+    x = torch.from_numpy(xyz).cuda()
+    c = torch.from_numpy(rgb).cuda()
+    ctx.build_graph(x)
+    out = ctx.denoise(c, q).cpu().numpy()
+    assert np.abs(out - ref).max() <= COLOR_TOL
+
+
+def test_external_sigma_and_q_out(F):
+    xyz = synth.torso_points(20000, 8, 6)
+    rgb = synth.add_noise_u8(synth.piecewise_colors(xyz, 8, 6), 30.0, 6)
+    res = orc.fgbd(xyz, rgb, orc.Params(bits=8))
+    ctx = F.Context(len(xyz), bits=8)
+    x = torch.from_numpy(xyz).cuda()
+    c = torch.from_numpy(rgb).cuda()
+    ctx.build_graph(x)
+    sig = torch.zeros(1, dtype=torch.float64, device="cuda")
+    ctx.estimate_noise(c, sigma_out=sig)
+    assert sig.item() == pytest.approx(res.noise["sigma_est"], rel=1e-5)
+    # a caller-chosen sigma drives the selection
+    chosen = 0.5 * res.noise["sigma_est"]
+    keep = orc.fslr_keep(res.spread, chosen)
+    q_ref = orc.select_q(rgb, res.row_ptr, res.col, res.rw, keep, chosen)[0]
+    q_dev = torch.full((1,), -7, dtype=torch.int32, device="cuda")
+    ctx.select_filter(c, sigma_est=torch.tensor([chosen], dtype=torch.float64, device="cuda"), q_out=q_dev)
+    assert q_dev.item() == q_ref
+
+
+def test_q_max_zero(F):
+    xyz = synth.torso_points(10000, 8, 7)
+    rgb = synth.add_noise_u8(synth.piecewise_colors(xyz, 8, 7), 30.0, 7)
+    res, g = full_check(F, xyz, rgb, 8, q_max=0)
+    assert g["stats"]["q"] == 0 and np.array_equal(g["out"], rgb.astype(np.float32))
+
+
+def test_run_matches_separate_calls(F):
+    fr = synth.sphere_frame(20500, 9, 30.0, 4)
+    ctx = F.Context(fr.n, bits=9)
+    x = torch.from_numpy(fr.xyz).cuda()
+    c = torch.from_numpy(fr.noisy).cuda()
+    a = ctx.run(x, c).cpu().numpy()
+    q1 = ctx.stats()["q"]
+    ctx.build_graph(x)
+    ctx.estimate_noise(c)
+    ctx.select_filter(c)
+    b = ctx.denoise(None, -1).cpu().numpy()
+    assert ctx.stats()["q"] == q1
+    assert np.array_equal(a, b)
+
+
+def test_repeated_runs_are_deterministic(F):
+    fr = synth.sphere_frame(20500, 9, 20.0, 8)
+    ctx = F.Context(fr.n, bits=9)
+    x = torch.from_numpy(fr.xyz).cuda()
+    c = torch.from_numpy(fr.noisy).cuda()
+    outs = [ctx.run(x, c).cpu().numpy() for _ in range(3)]
+    stats = [ctx.stats() for _ in range(1)]
+    assert np.array_equal(outs[0], outs[1]) and np.array_equal(outs[1], outs[2])
+    assert stats[0]["q"] >= 0
