@@ -225,9 +225,23 @@ def patch_covariance(A: np.ndarray):
     return (C.T @ C) / n, mu
 
 
+ZERO_EIG_REL = 1e-10
+
+
 def eigenvalues_desc(S: np.ndarray) -> np.ndarray:
-    """Section 2.3: eigenvalues of the symmetric covariance, lambda_1 >= ... >= lambda_D."""
-    return np.linalg.eigvalsh(S)[::-1].copy()
+    """Section 2.3: eigenvalues of the symmetric covariance, lambda_1 >= ... >= lambda_D.
+
+    Reading: an eigenvalue whose magnitude is below 1e-10 max(lambda_1, 1)
+    (colours on the 0..255 scale) is a numerical zero and is returned as
+    exactly 0.  Such values only occur when the covariance is rank-deficient
+    (fewer patches than D, a colour channel without variation, identical
+    patches); any solver returns them as rounding noise of either sign, and
+    the tail rule must not decide on that noise.
+    """
+    lam = np.linalg.eigvalsh(S)[::-1].copy()
+    top = lam[0] if lam.size else 0.0
+    lam[np.abs(lam) < ZERO_EIG_REL * max(top, 1.0)] = 0.0
+    return lam
 
 
 def tail_rule(lam: np.ndarray):

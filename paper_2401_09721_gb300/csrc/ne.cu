@@ -365,6 +365,7 @@ __global__ void __launch_bounds__(kNeThreads)
 
 // ---------------------------------------------------------------- finalize
 
+constexpr double kZeroEigRel = 1e-10;  // relative size below which an eigenvalue is zero
 constexpr int kJ = 22;           // 21 padded to an even size for round-robin pairing
 constexpr int kMaxSweeps = 12;
 
@@ -380,7 +381,6 @@ __global__ void __launch_bounds__(256) k_ne_finalize(int dtype, const double* __
   __shared__ double s_lam[kD];
   __shared__ double s_sorted[kD];
   __shared__ double s_num[kD][kD];
-  __shared__ int s_done;
 
   const int tid = threadIdx.x;
   constexpr int kP = kD * kD + kD + 1;
@@ -424,22 +424,15 @@ __global__ void __launch_bounds__(256) k_ne_finalize(int dtype, const double* __
     A[r][c] = (r < kD && c < kD) ? float(S[r][c]) : 0.f;
     V[r][c] = (r == c) ? 1.f : 0.f;
   }
-  if (tid == 0) s_done = 0;
   __syncthreads();
 
-  // cyclic Jacobi, round-robin order: 11 disjoint rotations per round
+  // cyclic Jacobi, round-robin order: 11 disjoint rotations per round.  A pair
+  // is rotated only while |a_pq| >= 1e-7 sqrt|a_pp a_qq| (float32 resolution);
+  // a sweep that rotates nothing ends the iteration.
   for (int sweep = 0; sweep < kMaxSweeps; ++sweep) {
-    if (tid == 0) {
-      float off = 0.f, dg = 0.f;
-      for (int r = 0; r < kD; ++r) {
-        dg += A[r][r] * A[r][r];
-        for (int c = r + 1; c < kD; ++c) off += A[r][c] * A[r][c];
-      }
-      s_done = (off <= 1e-13f * dg) ? 1 : 0;
-    }
-    __syncthreads();
-    if (s_done) break;
+    int rotated = 0;
     for (int round = 0; round < kJ - 1; ++round) {
+      int did = 0;
       if (tid < kJ / 2) {
         int p, q;
         if (tid == 0) {
@@ -456,18 +449,21 @@ __global__ void __launch_bounds__(256) k_ne_finalize(int dtype, const double* __
         }
         const float apq = A[p][q], app = A[p][p], aqq = A[q][q];
         float c = 1.f, s = 0.f;
-        if (apq != 0.f && fabsf(apq) > 1e-30f * (fabsf(app) + fabsf(aqq))) {
+        if (fabsf(apq) >= 1e-7f * sqrtf(fabsf(app * aqq)) && apq != 0.f) {
           const float theta = (aqq - app) / (2.f * apq);
           const float t = copysignf(1.f, theta) / (fabsf(theta) + sqrtf(theta * theta + 1.f));
           c = rsqrtf(t * t + 1.f);
           s = t * c;
+          did = 1;
         }
         s_p[tid] = p;
         s_q[tid] = q;
         s_c[tid] = c;
         s_s[tid] = s;
       }
-      __syncthreads();
+      const int any = __syncthreads_count(did);
+      rotated += any;
+      if (!any) continue;
       // rows: A <- J^T A
       for (int e = tid; e < (kJ / 2) * kJ; e += blockDim.x) {
         const int pr = e / kJ, j = e % kJ;
@@ -492,6 +488,7 @@ __global__ void __launch_bounds__(256) k_ne_finalize(int dtype, const double* __
       }
       __syncthreads();
     }
+    if (rotated == 0) break;
   }
 
   // float64 Rayleigh quotients of the 21 eigenvector estimates
@@ -509,6 +506,17 @@ __global__ void __launch_bounds__(256) k_ne_finalize(int dtype, const double* __
       den += double(V[r][tid]) * double(V[r][tid]);
     }
     s_lam[tid] = num / den;
+  }
+  __syncthreads();
+  // eigenvalues below 1e-10 max(lambda_1, 1) are numerical zeros (a rank-deficient
+  // covariance); they are set to exactly 0 so the tail rule never decides on rounding noise
+  if (tid < kD) {
+    double top = s_lam[0];
+    for (int j = 1; j < kD; ++j) top = fmax(top, s_lam[j]);
+    const double l = s_lam[tid];
+    const bool zero = fabs(l) < kZeroEigRel * fmax(top, 1.0);
+    __syncwarp(0x1fffffu);
+    if (zero) s_lam[tid] = 0.0;
   }
   __syncthreads();
   if (tid < kD) {

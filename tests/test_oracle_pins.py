@@ -330,6 +330,27 @@ def test_eigen_tail_closed_form_spectrum():
     assert m == 3 and s == pytest.approx(12.0, rel=1e-10)
 
 
+def test_rank_deficient_covariance_gives_exact_zeros():
+    # fewer patches than the patch dimension: Sigma has rank <= N' - 1, and
+    # the remaining eigenvalues are exactly 0, not rounding noise
+    rng = np.random.default_rng(17)
+    A = rng.uniform(0, 255, size=(12, 21))
+    S, _ = orc.patch_covariance(A)
+    lam = orc.eigenvalues_desc(S)
+    assert (lam[11:] == 0.0).all() and (lam[:11] > 0).all()
+    ref = np.linalg.svd(A - A.mean(0), compute_uv=False) ** 2 / 12
+    assert np.allclose(lam[:11], ref[:11], rtol=1e-10)
+    # a channel without variation removes its 7 patch entries
+    B = rng.uniform(0, 255, size=(500, 21))
+    B[:, 1::3] = 77.0
+    lamb = orc.eigenvalues_desc(orc.patch_covariance(B)[0])
+    assert (lamb[14:] == 0.0).all() and (lamb[:14] > 0).all()
+    # all patches equal: every eigenvalue and the estimate are 0
+    C = np.tile(rng.uniform(0, 255, size=(1, 21)), (40, 1))
+    lamc = orc.eigenvalues_desc(orc.patch_covariance(C)[0])
+    assert (lamc == 0).all() and orc.tail_rule(lamc)[2] == 0.0
+
+
 def _noise_recovery(sigma, seed, smooth):
     xyz = synth.sphere_points(20500, 9, seed)
     base = synth.smooth_colors(xyz, 9, seed, as_float=True) if smooth else np.full((len(xyz), 3), 128.0)
