@@ -198,6 +198,34 @@ fgbd_status fgbd_get_fslr(fgbd_ctx* ctx, float* spread, uint8_t* keep, void* str
 fgbd_status fgbd_set_timing(fgbd_ctx* ctx, int32_t enable);
 fgbd_status fgbd_get_timings(fgbd_ctx* ctx, int32_t max, int32_t* count_host, char* names_host, float* ms_host);
 
+/* Allocation-free scan orders.  The paper has no counterpart: this entry
+ * point exists for callers that cannot allocate device memory when they need
+ * the result, such as code running inside a CUDA graph capture or a real-time
+ * frame loop where a cudaMalloc would stall or is not allowed, plug-ins whose
+ * host application owns all device memory, or services held to a fixed
+ * memory budget.  It computes the same three scan orders as fgbd_build_graph
+ * (Eq. 1-3, stable radix sort, ties by input index) without a context.
+ *   xyz:    int32 [n][3] device, coordinates in [0, 2^bits).
+ *   n:      0 <= n <= FGBD_STATIC_MAX_POINTS; larger n returns FGBD_EINVAL.
+ *   bits:   1..10.
+ *   orders: int32 [3][n] device; orders[l][k] is the input index of the k-th
+ *           point along code l+1.
+ *   status: optional device uint32 receiving 0, or the OR of 1 (a coordinate
+ *           out of range) and 2 (a bounded device wait gave up); NULL to skip.
+ * Scratch: one file-scope device array of about 2 MiB (FGBD_STATIC_MAX_POINTS
+ * points) reserved on every GPU that loads the library until the process
+ * exits.  The call allocates and frees nothing.  The first call on a device
+ * looks up the array's device address (cudaGetSymbolAddress) with that device
+ * current; make that first call before any stream capture.  Every call
+ * shares the array and it keeps the previous call's contents; each call clears
+ * what must start at zero, but calls that overlap on the GPU (different
+ * streams or threads without ordering between them) race on it and give wrong
+ * results.  Enqueues on `stream` and returns without synchronising.
+ * Errors: FGBD_EINVAL, FGBD_ECUDA. */
+#define FGBD_STATIC_MAX_POINTS 32768
+fgbd_status fgbd_scan_orders_static(const int32_t* xyz, int64_t n, int32_t bits, int32_t* orders, uint32_t* status,
+                                    void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -104,6 +104,7 @@ _SIGS = {
     "fgbd_get_fslr": (ctypes.c_int, [_P, _P, _P, _P]),
     "fgbd_set_timing": (ctypes.c_int, [_P, ctypes.c_int32]),
     "fgbd_get_timings": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32), _P, _P]),
+    "fgbd_scan_orders_static": (ctypes.c_int, [_P, ctypes.c_int64, ctypes.c_int32, _P, _P, _P]),
 }
 NAME_LEN = 32
 TIMING_CAP = 256
