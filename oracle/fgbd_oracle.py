@@ -225,13 +225,13 @@ def patch_covariance(A: np.ndarray):
     return (C.T @ C) / n, mu
 
 
-ZERO_EIG_REL = 1e-10
+ZERO_EIG_REL = 1e-9
 
 
 def eigenvalues_desc(S: np.ndarray) -> np.ndarray:
     """Section 2.3: eigenvalues of the symmetric covariance, lambda_1 >= ... >= lambda_D.
 
-    Reading: an eigenvalue whose magnitude is below 1e-10 max(lambda_1, 1)
+    Reading: an eigenvalue whose magnitude is below 1e-9 max(lambda_1, 1)
     (colours on the 0..255 scale) is a numerical zero and is returned as
     exactly 0.  Such values only occur when the covariance is rank-deficient
     (fewer patches than D, a colour channel without variation, identical

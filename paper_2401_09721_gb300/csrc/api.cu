@@ -185,9 +185,8 @@ fgbd_status do_build(fgbd_ctx* ctx, const int32_t* xyz, int64_t n64, cudaStream_
   if (n > 0) {
     ctx->sb.passes = passes_for(bits);
     ctx->sb.tiles = (n + kSortTile - 1) / kSortTile;
-    const size_t zero_words = size_t(ctx->sb.passes) * 3 * size_t(ctx->sb.tiles) * kRadix;
     FGBD_LAUNCH(ctx, "slg_hist", st,
-                launch_hist(xyz, n, bits, ctx->sb.passes, ctx->sb.lookback, zero_words, ctx->sc, ctx->num_sms, st));
+                launch_hist(xyz, n, bits, ctx->sb.passes, ctx->sb.tile_counts, 0, ctx->sc, ctx->num_sms, st));
     static const char* const kPassNames[kMaxPasses] = {"slg_sort_pass0", "slg_sort_pass1", "slg_sort_pass2",
                                                        "slg_sort_pass3"};
     for (int p = 0; p < ctx->sb.passes; ++p)
@@ -308,7 +307,7 @@ fgbd_status fgbd_ctx_create(int64_t capacity, const fgbd_params* params, fgbd_ct
       {&keys1, 3 * C * 4},
       {&vals0, 3 * C * 4},
       {&vals1, 3 * C * 4},
-      {reinterpret_cast<void**>(&ctx->sb.lookback), size_t(kMaxPasses) * 3 * tiles * kRadix * 4},
+      {reinterpret_cast<void**>(&ctx->sb.tile_counts), size_t(kMaxPasses) * 3 * tiles * kRadix * 4},
       {reinterpret_cast<void**>(&ctx->gb.perm), 3 * C * 4},
       {reinterpret_cast<void**>(&ctx->gb.rank1), C * 4},
       {reinterpret_cast<void**>(&ctx->gb.rank2), C * 4},

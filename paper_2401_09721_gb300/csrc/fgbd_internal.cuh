@@ -26,10 +26,10 @@ constexpr int kMaxPasses = 4;                      // ceil(30 / 8)
 constexpr int kK = 6;                              // neighbours per point at window 1
 constexpr int kD = 3 * (kK + 1);                   // patch dimension (Section 2.3)
 constexpr int kQCap = 256;                         // largest q_max accepted
-constexpr int kSqShift = 16;                       // fixed point of squared colours
+constexpr int kSqShift = 8;                        // fixed point of squared colours (2^-8)
 constexpr int kDistShift = 20;                     // fixed point of edge lengths
 constexpr int kNeThreads = 256;
-constexpr int kFilterThreads = 256;
+constexpr int kFilterThreads = 512;
 constexpr uint32_t kCoordMask = 0x3FFFFFFFu;       // low 30 bits: packed C1 code
 constexpr uint32_t kKeepBit = 0x80000000u;         // FSLR keep flag beside the code
 
@@ -79,7 +79,7 @@ struct DevScalars {
 struct SortBufs {
   uint32_t* keys[2];   // ping-pong [3][cap]
   uint32_t* vals[2];   // ping-pong [3][cap]
-  uint32_t* lookback;  // [passes][3][tiles][kRadix]
+  uint32_t* tile_counts;  // [passes][3 codes][kRadix digits][tiles]: per-tile digit counts, then offsets
   int tiles;           // tiles per code at this n
   int passes;
 };
@@ -191,14 +191,10 @@ __device__ __forceinline__ void st_volatile(uint32_t* p, uint32_t v) {
   *reinterpret_cast<volatile uint32_t*>(p) = v;
 }
 
-// round(v^2 * 2^kSqShift) without cancellation: v*v in fp32 plus its exact
-// rounding error from an fma, each scaled and rounded to an integer
-__device__ __forceinline__ unsigned long long sq_fixed(float v) {
-  const float p = v * v;
-  const float e = fmaf(v, v, -p);
-  const float s = float(1 << kSqShift);
-  return (unsigned long long)(__float2ll_rn(p * s) + __float2ll_rn(e * s));
-}
+// round(v^2 * 2^kSqShift) as a 32-bit integer: exact for integer colours,
+// within 2^-9 otherwise; colours on the 0..255 scale (|v| < 2896) fit.
+// A 32-bit conversion keeps the per-point work off the float64 pipe.
+__device__ __forceinline__ int sq_fixed(float v) { return __float2int_rn(v * v * float(1 << kSqShift)); }
 
 template <typename T>
 __device__ __forceinline__ T warp_sum(T v) {

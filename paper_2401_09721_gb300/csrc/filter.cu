@@ -15,7 +15,7 @@
 //             J(t) = |sigma^2 - (sum y^2 - sum x_t^2)/(3 N_sel)| and stops at
 //             the first t with J(t) >= J(t-1), keeping q* = t-1.
 //   output    the kept iterate is gathered back to input order (optional).
-// Sums of squares are fixed-point integers (2^-16), so the reduction is exact
+// Sums of squares are fixed-point integers (2^-8), so the reduction is exact
 // and independent of the order in which blocks add.
 // The grid barrier is a counter with a 2 s wait limit; a block that gives up
 // latches kFlagTimeout and every block returns.
@@ -144,7 +144,7 @@ __global__ void __launch_bounds__(kFilterThreads) k_filter(FilterArgs a) {
       if (sp <= t_lo) keep = true;
       else if (sp > t_hi) keep = false;
       else keep = !(spread_f64(a, k) > thr);
-      const unsigned long long q2 = sq_fixed(r) + sq_fixed(g) + sq_fixed(b);
+      const unsigned long long q2 = (unsigned long long)(sq_fixed(r) + sq_fixed(g) + sq_fixed(b));
       ysq_a += q2;
       if (keep) {
         w |= kKeepBit;
@@ -234,7 +234,8 @@ __global__ void __launch_bounds__(kFilterThreads) k_filter(FilterArgs a) {
         xo.z = 0.5f * xk.z + 0.5f * (sb * inv);
       }
       dst[k] = xo;
-      if (select && (keep_all || (wk & kKeepBit))) loc += sq_fixed(xo.x) + sq_fixed(xo.y) + sq_fixed(xo.z);
+      if (select && (keep_all || (wk & kKeepBit)))
+        loc += (unsigned long long)(sq_fixed(xo.x) + sq_fixed(xo.y) + sq_fixed(xo.z));
     }
     if (select) {
       loc = block_sum_u64<kFilterThreads>(loc, s_red);

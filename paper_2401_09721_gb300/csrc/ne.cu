@@ -22,7 +22,6 @@ namespace fgbd {
 namespace {
 
 constexpr int kTiles = 28;  // 3x3 output tiles covering the upper triangle of a 21x21 matrix
-constexpr int kSplits = 8;  // each tile's patch range split over 8 threads
 
 __global__ void __launch_bounds__(256) k_gather_u8(const uint8_t* __restrict__ rgb, int n,
                                                    const int32_t* __restrict__ perm1,
@@ -57,327 +56,462 @@ __device__ __forceinline__ void tile_rc(int tile, int& r0, int& c0) {
   c0 = 3 * (ti + rem);
 }
 
-struct NbKey {
-  unsigned long long key;  // d^2, dz, dy, dx packed so that integer order is lexicographic
-  int idx;                 // sorted id of the neighbour (input order among repeated voxels)
-  float r, g, b;           // its colour, carried through the sort
+// one neighbour of a patch: sort key (d^2, dz, dy, dx packed so that integer
+// order is lexicographic), its sorted id (input order among repeated voxels)
+// and its colour, carried through the sort
+template <int DT>
+struct NbKey;
+template <>
+struct NbKey<0> {
+  unsigned long long key;
+  int idx;
+  uint32_t col;  // packed R, G, B bytes
+};
+template <>
+struct NbKey<1> {
+  unsigned long long key;
+  int idx;
+  float r, g, b;
 };
 
-__device__ __forceinline__ void cswap(NbKey& a, NbKey& b) {
+template <int DT>
+__device__ __forceinline__ void cswap(NbKey<DT>& a, NbKey<DT>& b) {
   const bool sw = (b.key < a.key) || (b.key == a.key && b.idx < a.idx);
   if (sw) {
-    const NbKey t = a;
+    const NbKey<DT> t = a;
     a = b;
     b = t;
   }
 }
 
+constexpr int kNeWarps = kNeThreads / 32;
+constexpr int kRowWords = 9;    // 32 int8 patch entries = 8 words, padded: the 21 rows start in distinct banks
+constexpr int kRowFloats = 33;  // 32 float entries, padded likewise
+constexpr int kFirstLanes = 32 - kTiles;  // lanes 28..31 sum the first moments
+
+// Per point: FSLR spread over the point and its neighbours (written to
+// spread[k]) and, for a point with exactly 6 neighbours, its patch (the point
+// then its neighbours by (d^2, dz, dy, dx, index)) written to column `lane`
+// of the warp's transposed patch block.  Returns whether a patch was written.
+template <int DT>
+__device__ __forceinline__ bool point_patch(int k, int n, int bits, int lane, const uint32_t* __restrict__ pk,
+                                            const int4* __restrict__ c4, const uint32_t* __restrict__ y8,
+                                            const float4* __restrict__ yf, float* __restrict__ spread,
+                                            bool moments, uint8_t* at8, float* atf) {
+  int nb[6];
+  bool v[6];
+  nb[0] = k - 1;
+  v[0] = k > 0;
+  nb[1] = k + 1;
+  v[1] = k + 1 < n;
+  const int4 s = c4[k];
+  nb[2] = s.x;
+  nb[3] = s.y;
+  nb[4] = s.z;
+  nb[5] = s.w;
+  v[2] = in_range(s.x, n);
+  v[3] = in_range(s.y, n);
+  v[4] = in_range(s.z, n);
+  v[5] = in_range(s.w, n);
+  int deg = 0;
+#pragma unroll
+  for (int j = 0; j < 6; ++j) deg += v[j];
+  const bool patch = moments && deg == 6;
+  NbKey<DT> e[6];
+  uint32_t cpk[6];
+#pragma unroll
+  for (int j = 0; j < 6; ++j) {
+    const int q = v[j] ? nb[j] : k;
+    cpk[j] = patch ? pk[q] : 0u;
+    e[j].idx = q;
+    if (DT == 0) {
+      reinterpret_cast<NbKey<0>&>(e[j]).col = y8[q];
+    } else {
+      const float4 c = yf[q];
+      reinterpret_cast<NbKey<1>&>(e[j]).r = c.x;
+      reinterpret_cast<NbKey<1>&>(e[j]).g = c.y;
+      reinterpret_cast<NbKey<1>&>(e[j]).b = c.z;
+    }
+  }
+  float sp;
+  const float cnt = float(deg + 1);
+  uint32_t own8 = 0;
+  float ownr = 0.f, owng = 0.f, ownb = 0.f;
+  if (DT == 0) {
+    own8 = y8[k];
+    int sr = int(own8 & 255u), sg = int((own8 >> 8) & 255u), sb = int((own8 >> 16) & 255u);
+    int qr = sr * sr, qg = sg * sg, qb = sb * sb;
+#pragma unroll
+    for (int j = 0; j < 6; ++j) {
+      if (v[j]) {
+        const uint32_t c = reinterpret_cast<NbKey<0>&>(e[j]).col;
+        const int a = int(c & 255u), b = int((c >> 8) & 255u), d = int((c >> 16) & 255u);
+        sr += a;
+        sg += b;
+        sb += d;
+        qr += a * a;
+        qg += b * b;
+        qb += d * d;
+      }
+    }
+    const int nn = deg + 1;
+    const float vr = float(nn * qr - sr * sr), vg = float(nn * qg - sg * sg), vb = float(nn * qb - sb * sb);
+    sp = (sqrtf(vr) / cnt + sqrtf(vg) / cnt + sqrtf(vb) / cnt) / 3.0f;
+  } else {
+    const float4 o = yf[k];
+    ownr = o.x;
+    owng = o.y;
+    ownb = o.z;
+    float mr = ownr, mg = owng, mb = ownb;
+#pragma unroll
+    for (int j = 0; j < 6; ++j) {
+      if (v[j]) {
+        const NbKey<1>& f = reinterpret_cast<NbKey<1>&>(e[j]);
+        mr += f.r;
+        mg += f.g;
+        mb += f.b;
+      }
+    }
+    mr /= cnt;
+    mg /= cnt;
+    mb /= cnt;
+    float vr = (ownr - mr) * (ownr - mr), vg = (owng - mg) * (owng - mg), vb = (ownb - mb) * (ownb - mb);
+#pragma unroll
+    for (int j = 0; j < 6; ++j) {
+      if (v[j]) {
+        const NbKey<1>& f = reinterpret_cast<NbKey<1>&>(e[j]);
+        vr += (f.r - mr) * (f.r - mr);
+        vg += (f.g - mg) * (f.g - mg);
+        vb += (f.b - mb) * (f.b - mb);
+      }
+    }
+    sp = (sqrtf(vr / cnt) + sqrtf(vg / cnt) + sqrtf(vb / cnt)) / 3.0f;
+  }
+  spread[k] = sp;
+  if (!patch) return false;
+
+  int kx, ky, kz;
+  decode_c1(pk[k], bits, kx, ky, kz);
+#pragma unroll
+  for (int j = 0; j < 6; ++j) {
+    int x, y, z;
+    decode_c1(cpk[j], bits, x, y, z);
+    const int dx = x - kx, dy = y - ky, dz = z - kz;
+    const unsigned long long d2 = (unsigned long long)(dx * dx + dy * dy + dz * dz);
+    e[j].key = (d2 << 33) | ((unsigned long long)(dz + 1024) << 22) | ((unsigned long long)(dy + 1024) << 11) |
+               (unsigned long long)(dx + 1024);
+  }
+  // odd-even transposition sort, 6 rounds
+#pragma unroll
+  for (int round = 0; round < 6; ++round) {
+    if ((round & 1) == 0) {
+      cswap(e[0], e[1]);
+      cswap(e[2], e[3]);
+      cswap(e[4], e[5]);
+    } else {
+      cswap(e[1], e[2]);
+      cswap(e[3], e[4]);
+    }
+  }
+  if (DT == 0) {
+    // entry r of the patch, centred on 128: the colour byte with its top bit flipped, read as int8
+    const int stride = kRowWords * 4;
+    at8[0 * stride + lane] = uint8_t((own8 & 255u) ^ 0x80u);
+    at8[1 * stride + lane] = uint8_t(((own8 >> 8) & 255u) ^ 0x80u);
+    at8[2 * stride + lane] = uint8_t(((own8 >> 16) & 255u) ^ 0x80u);
+#pragma unroll
+    for (int j = 0; j < 6; ++j) {
+      const uint32_t c = reinterpret_cast<NbKey<0>&>(e[j]).col;
+      at8[(3 + 3 * j) * stride + lane] = uint8_t((c & 255u) ^ 0x80u);
+      at8[(4 + 3 * j) * stride + lane] = uint8_t(((c >> 8) & 255u) ^ 0x80u);
+      at8[(5 + 3 * j) * stride + lane] = uint8_t(((c >> 16) & 255u) ^ 0x80u);
+    }
+  } else {
+    atf[0 * kRowFloats + lane] = ownr - 128.f;
+    atf[1 * kRowFloats + lane] = owng - 128.f;
+    atf[2 * kRowFloats + lane] = ownb - 128.f;
+#pragma unroll
+    for (int j = 0; j < 6; ++j) {
+      const NbKey<1>& f = reinterpret_cast<NbKey<1>&>(e[j]);
+      atf[(3 + 3 * j) * kRowFloats + lane] = f.r - 128.f;
+      atf[(4 + 3 * j) * kRowFloats + lane] = f.g - 128.f;
+      atf[(5 + 3 * j) * kRowFloats + lane] = f.b - 128.f;
+    }
+  }
+  return true;
+}
+
+// Warp-synchronous: each warp takes 32 points at a time, stages their patches
+// transposed in its own shared-memory block and accumulates the moments with
+// __syncwarp only.  Lanes 0..27 own one 3x3 tile of the upper triangle of
+// sum a a^T; lanes 28..31 own rows of sum a.  uint8 colours: exact int32 dp4a
+// sums, moved to int64 every 1024 batches; float colours: fp32 sums over 4
+// batches, then float64.  The block combines its warps through shared atomics
+// and adds its totals to the context (uint8) or writes them (float).
 template <int DT>
 __global__ void __launch_bounds__(kNeThreads)
     k_ne_moments(int n, int bits, const uint32_t* __restrict__ pk, const int4* __restrict__ c4,
                  const uint32_t* __restrict__ y8, const float4* __restrict__ yf,
                  float* __restrict__ spread, double* __restrict__ f64_partials, int moments,
                  DevScalars* __restrict__ sc) {
-  // patches of one batch, transposed: row r holds entry r of the 256 patches
-  __shared__ __align__(16) int8_t s_at8[DT == 0 ? kD : 1][kNeThreads];
-  __shared__ __align__(16) float s_atf[DT == 1 ? kD : 1][kNeThreads];
-  __shared__ unsigned long long s_red[kNeThreads / 32];
+  constexpr int kP = kD * kD + kD + 1;
+  __shared__ __align__(16) uint32_t s_at8[DT == 0 ? kNeWarps : 1][kD * kRowWords];
+  __shared__ __align__(16) float s_atf[DT == 1 ? kNeWarps : 1][kD * kRowFloats];
+  __shared__ unsigned long long s_tot8[DT == 0 ? kP : 1];
+  __shared__ double s_totf[DT == 1 ? kP : 1];
 
-  const int tid = threadIdx.x;
-  const int tile = tid / kSplits, split = tid % kSplits;
-  int r0 = 0, c0 = 0;
-  if (tid < kTiles * kSplits) tile_rc(tile, r0, c0);
-  long long acc64[3][3] = {};
-  double accd[3][3] = {};
-  long long s1_64 = 0;
-  double s1_d = 0.0;
-  unsigned long long npatch = 0;
-
-  for (int base = blockIdx.x * kNeThreads; base < n; base += gridDim.x * kNeThreads) {
-    const int k = base + tid;
-    bool has_patch = false;
-    if (k < n) {
-      const uint32_t ck = pk[k];
-      int nb[6];
-      bool v[6];
-      nb[0] = k - 1;
-      v[0] = k > 0;
-      nb[1] = k + 1;
-      v[1] = k + 1 < n;
-      const int4 s = c4[k];
-      nb[2] = s.x;
-      nb[3] = s.y;
-      nb[4] = s.z;
-      nb[5] = s.w;
-      v[2] = in_range(s.x, n);
-      v[3] = in_range(s.y, n);
-      v[4] = in_range(s.z, n);
-      v[5] = in_range(s.w, n);
-      int deg = 0;
-#pragma unroll
-      for (int j = 0; j < 6; ++j) deg += v[j];
-
-      float cr[7], cg[7], cb[7];
-      if (DT == 0) {
-        const uint32_t yk = y8[k];
-        cr[6] = float(yk & 255u);
-        cg[6] = float((yk >> 8) & 255u);
-        cb[6] = float((yk >> 16) & 255u);
-      } else {
-        const float4 yk = yf[k];
-        cr[6] = yk.x;
-        cg[6] = yk.y;
-        cb[6] = yk.z;
-      }
-      // gather neighbour colours (invalid slots repeat the point itself and are skipped below)
-#pragma unroll
-      for (int j = 0; j < 6; ++j) {
-        const int q = v[j] ? nb[j] : k;
-        if (DT == 0) {
-          const uint32_t yq = y8[q];
-          cr[j] = float(yq & 255u);
-          cg[j] = float((yq >> 8) & 255u);
-          cb[j] = float((yq >> 16) & 255u);
-        } else {
-          const float4 yq = yf[q];
-          cr[j] = yq.x;
-          cg[j] = yq.y;
-          cb[j] = yq.z;
-        }
-      }
-
-      // FSLR spread over {k} and its neighbours, population std per channel
-      const float cnt = float(deg + 1);
-      float sp;
-      if (DT == 0) {
-        int sr = int(cr[6]), sg = int(cg[6]), sb = int(cb[6]);
-        int qr = sr * sr, qg = sg * sg, qb = sb * sb;
-#pragma unroll
-        for (int j = 0; j < 6; ++j) {
-          if (v[j]) {
-            const int a = int(cr[j]), b = int(cg[j]), c = int(cb[j]);
-            sr += a;
-            sg += b;
-            sb += c;
-            qr += a * a;
-            qg += b * b;
-            qb += c * c;
-          }
-        }
-        const int nn = deg + 1;
-        const float vr = float(nn * qr - sr * sr), vg = float(nn * qg - sg * sg), vb = float(nn * qb - sb * sb);
-        sp = (sqrtf(vr) / cnt + sqrtf(vg) / cnt + sqrtf(vb) / cnt) / 3.0f;
-      } else {
-        float mr = cr[6], mg = cg[6], mb = cb[6];
-#pragma unroll
-        for (int j = 0; j < 6; ++j) {
-          if (v[j]) {
-            mr += cr[j];
-            mg += cg[j];
-            mb += cb[j];
-          }
-        }
-        mr /= cnt;
-        mg /= cnt;
-        mb /= cnt;
-        float vr = (cr[6] - mr) * (cr[6] - mr), vg = (cg[6] - mg) * (cg[6] - mg), vb = (cb[6] - mb) * (cb[6] - mb);
-#pragma unroll
-        for (int j = 0; j < 6; ++j) {
-          if (v[j]) {
-            vr += (cr[j] - mr) * (cr[j] - mr);
-            vg += (cg[j] - mg) * (cg[j] - mg);
-            vb += (cb[j] - mb) * (cb[j] - mb);
-          }
-        }
-        sp = (sqrtf(vr / cnt) + sqrtf(vg / cnt) + sqrtf(vb / cnt)) / 3.0f;
-      }
-      spread[k] = sp;
-
-      if (moments && deg == 6) {
-        has_patch = true;
-        // order the six neighbours by (d^2, dz, dy, dx, index)
-        int kx, ky, kz;
-        decode_c1(ck, bits, kx, ky, kz);
-        NbKey e[6];
-#pragma unroll
-        for (int j = 0; j < 6; ++j) {
-          int x, y, z;
-          decode_c1(pk[nb[j]], bits, x, y, z);
-          const int dx = x - kx, dy = y - ky, dz = z - kz;
-          const unsigned long long d2 = (unsigned long long)(dx * dx + dy * dy + dz * dz);
-          e[j].key = (d2 << 33) | ((unsigned long long)(dz + 1024) << 22) |
-                     ((unsigned long long)(dy + 1024) << 11) | (unsigned long long)(dx + 1024);
-          e[j].idx = nb[j];
-          e[j].r = cr[j];
-          e[j].g = cg[j];
-          e[j].b = cb[j];
-        }
-        // odd-even transposition sort, 6 rounds
-#pragma unroll
-        for (int round = 0; round < 6; ++round) {
-          if ((round & 1) == 0) {
-            cswap(e[0], e[1]);
-            cswap(e[2], e[3]);
-            cswap(e[4], e[5]);
-          } else {
-            cswap(e[1], e[2]);
-            cswap(e[3], e[4]);
-          }
-        }
-        // write the patch, centred on 128, transposed into shared memory
-        if (DT == 0) {
-          s_at8[0][tid] = int8_t(int(cr[6]) - 128);
-          s_at8[1][tid] = int8_t(int(cg[6]) - 128);
-          s_at8[2][tid] = int8_t(int(cb[6]) - 128);
-#pragma unroll
-          for (int j = 0; j < 6; ++j) {
-            s_at8[3 + 3 * j][tid] = int8_t(int(e[j].r) - 128);
-            s_at8[4 + 3 * j][tid] = int8_t(int(e[j].g) - 128);
-            s_at8[5 + 3 * j][tid] = int8_t(int(e[j].b) - 128);
-          }
-        } else {
-          s_atf[0][tid] = cr[6] - 128.f;
-          s_atf[1][tid] = cg[6] - 128.f;
-          s_atf[2][tid] = cb[6] - 128.f;
-#pragma unroll
-          for (int j = 0; j < 6; ++j) {
-            s_atf[3 + 3 * j][tid] = e[j].r - 128.f;
-            s_atf[4 + 3 * j][tid] = e[j].g - 128.f;
-            s_atf[5 + 3 * j][tid] = e[j].b - 128.f;
-          }
-        }
-      }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (moments) {
+    for (int i = threadIdx.x; i < kP; i += kNeThreads) {
+      if (DT == 0) s_tot8[i] = 0ull;
+      else s_totf[i] = 0.0;
     }
+  }
+  __syncthreads();
+  int r0 = 0, c0 = 0, rb = 0, re = 0;
+  if (lane < kTiles) {
+    tile_rc(lane, r0, c0);
+  } else {
+    rb = ((lane - kTiles) * kD) / kFirstLanes;
+    re = ((lane - kTiles + 1) * kD) / kFirstLanes;
+  }
+  int acc[9] = {};
+  long long acc64[9] = {};
+  float accf[9] = {};
+  double accd[9] = {};
+  unsigned long long npatch = 0;
+  int since_flush = 0;
+  uint8_t* at8 = reinterpret_cast<uint8_t*>(&s_at8[DT == 0 ? warp : 0][0]);
+  float* atf = &s_atf[DT == 1 ? warp : 0][0];
+
+  const int nwarps = gridDim.x * kNeWarps;
+  for (int base = (blockIdx.x * kNeWarps + warp) * 32; base < n; base += nwarps * 32) {
+    const int k = base + lane;
+    bool has = false;
+    if (k < n) has = point_patch<DT>(k, n, bits, lane, pk, c4, y8, yf, spread, moments != 0, at8, atf);
     if (!moments) continue;
-    if (!has_patch) {
+    if (!has) {
 #pragma unroll
       for (int r = 0; r < kD; ++r) {
-        if (DT == 0) s_at8[r][tid] = 0;
-        else s_atf[r][tid] = 0.f;
+        if (DT == 0) at8[r * kRowWords * 4 + lane] = 0;
+        else atf[r * kRowFloats + lane] = 0.f;
       }
     }
-    npatch += has_patch ? 1 : 0;
-    __syncthreads();
-
-    if (tid < kTiles * kSplits) {
-      if (DT == 0) {
-        const int* at = reinterpret_cast<const int*>(&s_at8[0][0]);
-        constexpr int kWordsPerRow = kNeThreads / 4;
-        int acc[3][3] = {};
+    const uint32_t hb = __ballot_sync(0xffffffffu, has);
+    npatch += __popc(hb);
+    __syncwarp();
+    if (DT == 0) {
+      const int* at = reinterpret_cast<const int*>(&s_at8[warp][0]);
+      if (lane < kTiles) {
 #pragma unroll
-        for (int w = split * (kWordsPerRow / kSplits); w < (split + 1) * (kWordsPerRow / kSplits); ++w) {
+        for (int w = 0; w < 8; ++w) {
           int a[3], b[3];
 #pragma unroll
           for (int i = 0; i < 3; ++i) {
-            a[i] = at[(r0 + i) * kWordsPerRow + w];
-            b[i] = at[(c0 + i) * kWordsPerRow + w];
+            a[i] = at[(r0 + i) * kRowWords + w];
+            b[i] = at[(c0 + i) * kRowWords + w];
           }
 #pragma unroll
           for (int i = 0; i < 3; ++i)
 #pragma unroll
-            for (int j = 0; j < 3; ++j) acc[i][j] = __dp4a(a[i], b[j], acc[i][j]);
+            for (int j = 0; j < 3; ++j) acc[3 * i + j] = __dp4a(a[i], b[j], acc[3 * i + j]);
         }
-#pragma unroll
-        for (int i = 0; i < 3; ++i)
-#pragma unroll
-          for (int j = 0; j < 3; ++j) acc64[i][j] += acc[i][j];
       } else {
-        float acc[3][3] = {};
-        constexpr int kPer = kNeThreads / kSplits;
+#pragma unroll
+        for (int t = 0; t < 6; ++t) {
+          const int r = rb + t;
+          if (r < re) {
+#pragma unroll
+            for (int w = 0; w < 8; ++w) acc[t] = __dp4a(at[r * kRowWords + w], 0x01010101, acc[t]);
+          }
+        }
+      }
+      if (++since_flush == 1024) {
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+          acc64[i] += acc[i];
+          acc[i] = 0;
+        }
+        since_flush = 0;
+      }
+    } else {
+      if (lane < kTiles) {
 #pragma unroll 4
-        for (int p = split * kPer; p < (split + 1) * kPer; ++p) {
+        for (int p = 0; p < 32; ++p) {
           float a[3], b[3];
 #pragma unroll
           for (int i = 0; i < 3; ++i) {
-            a[i] = s_atf[r0 + i][p];
-            b[i] = s_atf[c0 + i][p];
+            a[i] = atf[(r0 + i) * kRowFloats + p];
+            b[i] = atf[(c0 + i) * kRowFloats + p];
           }
 #pragma unroll
           for (int i = 0; i < 3; ++i)
 #pragma unroll
-            for (int j = 0; j < 3; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+            for (int j = 0; j < 3; ++j) accf[3 * i + j] = fmaf(a[i], b[j], accf[3 * i + j]);
         }
-#pragma unroll
-        for (int i = 0; i < 3; ++i)
-#pragma unroll
-          for (int j = 0; j < 3; ++j) accd[i][j] += double(acc[i][j]);
-      }
-    } else if (tid < kTiles * kSplits + kD) {
-      const int r = tid - kTiles * kSplits;
-      if (DT == 0) {
-        const int* at = reinterpret_cast<const int*>(&s_at8[0][0]);
-        int acc = 0;
-        for (int w = 0; w < kNeThreads / 4; ++w) acc = __dp4a(at[r * (kNeThreads / 4) + w], 0x01010101, acc);
-        s1_64 += acc;
       } else {
-        float acc = 0.f;
-        for (int p = 0; p < kNeThreads; ++p) acc += s_atf[r][p];
-        s1_d += double(acc);
+#pragma unroll
+        for (int t = 0; t < 6; ++t) {
+          const int r = rb + t;
+          if (r < re) {
+            float sum = 0.f;
+            for (int p = 0; p < 32; ++p) sum += atf[r * kRowFloats + p];
+            accf[t] += sum;
+          }
+        }
+      }
+      if (++since_flush == 4) {
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+          accd[i] += double(accf[i]);
+          accf[i] = 0.f;
+        }
+        since_flush = 0;
       }
     }
-    __syncthreads();
+    __syncwarp();
   }
   if (!moments) return;
-
-  // combine the 8 splits of each tile (8 consecutive lanes)
-  const unsigned long long np = block_sum_u64<kNeThreads>(npatch, s_red);
-  if (tid == 0 && DT == 0 && np) atomicAdd(&sc->n_patches, np);
-  if (tid < kTiles * kSplits) {
+#pragma unroll
+  for (int i = 0; i < 9; ++i) {
+    acc64[i] += acc[i];
+    accd[i] += double(accf[i]);
+  }
+  // combine the warps of the block
+  if (lane < kTiles) {
 #pragma unroll
     for (int i = 0; i < 3; ++i)
 #pragma unroll
       for (int j = 0; j < 3; ++j) {
-        long long v64 = acc64[i][j];
-        double vd = accd[i][j];
-#pragma unroll
-        for (int o = 1; o < kSplits; o <<= 1) {
-          v64 += __shfl_xor_sync(0xffffffffu, v64, o);
-          vd += __shfl_xor_sync(0xffffffffu, vd, o);
-        }
-        acc64[i][j] = v64;
-        accd[i][j] = vd;
+        const int idx = (r0 + i) * kD + (c0 + j);
+        if (DT == 0) atomicAdd(&s_tot8[idx], (unsigned long long)acc64[3 * i + j]);
+        else atomicAdd(&s_totf[idx], accd[3 * i + j]);
       }
-    if (split == 0) {
+  } else {
 #pragma unroll
-      for (int i = 0; i < 3; ++i)
-#pragma unroll
-        for (int j = 0; j < 3; ++j) {
-          const int idx = (r0 + i) * kD + (c0 + j);
-          if (DT == 0) {
-            if (acc64[i][j]) atomicAdd(reinterpret_cast<unsigned long long*>(&sc->s2[idx]),
-                                       (unsigned long long)acc64[i][j]);
-          } else {
-            f64_partials[size_t(blockIdx.x) * (kD * kD + kD + 1) + idx] = accd[i][j];
-          }
-        }
-    }
-  } else if (tid < kTiles * kSplits + kD) {
-    const int r = tid - kTiles * kSplits;
-    if (DT == 0) {
-      if (s1_64) atomicAdd(reinterpret_cast<unsigned long long*>(&sc->s1[r]), (unsigned long long)s1_64);
-    } else {
-      f64_partials[size_t(blockIdx.x) * (kD * kD + kD + 1) + kD * kD + r] = s1_d;
+    for (int t = 0; t < 6; ++t) {
+      const int r = rb + t;
+      if (r < re) {
+        if (DT == 0) atomicAdd(&s_tot8[kD * kD + r], (unsigned long long)acc64[t]);
+        else atomicAdd(&s_totf[kD * kD + r], accd[t]);
+      }
     }
   }
-  if (DT == 1 && tid == 0)
-    f64_partials[size_t(blockIdx.x) * (kD * kD + kD + 1) + kD * kD + kD] = double(np);
+  if (lane == 0) {
+    if (DT == 0) atomicAdd(&s_tot8[kD * kD + kD], npatch);
+    else atomicAdd(&s_totf[kD * kD + kD], double(npatch));
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < kP; i += kNeThreads) {
+    if (DT == 0) {
+      const unsigned long long v = s_tot8[i];
+      if (v == 0) continue;
+      if (i < kD * kD) atomicAdd(reinterpret_cast<unsigned long long*>(&sc->s2[i]), v);
+      else if (i < kD * kD + kD) atomicAdd(reinterpret_cast<unsigned long long*>(&sc->s1[i - kD * kD]), v);
+      else atomicAdd(&sc->n_patches, v);
+    } else {
+      f64_partials[size_t(blockIdx.x) * kP + i] = s_totf[i];
+    }
+  }
 }
 
 // ---------------------------------------------------------------- finalize
 
-constexpr double kZeroEigRel = 1e-10;  // relative size below which an eigenvalue is zero
+constexpr double kZeroEigRel = 1e-9;  // relative size below which an eigenvalue is zero
 constexpr int kJ = 22;           // 21 padded to an even size for round-robin pairing
-constexpr int kMaxSweeps = 12;
+constexpr int kMaxSweeps = 15;
+
+// ---- register-resident Jacobi: one warp, lane i holds row i of A and of V.
+// Circle-method tournament on 22 positions (21 indices + one zero pad): each
+// round rotates the fixed position pairs (2k, 2k+1), then every index except
+// the one at position 0 moves one step along the ring 2 -> 4 -> ... -> 20 ->
+// 21 -> 19 -> ... -> 1 -> 2.  Every pair of indices meets once in 21 rounds,
+// and after a full sweep every index is back at its own position.  Rows move
+// between lanes by shuffles; columns move between registers by a fixed
+// permutation, so every register index is static and the loop stays small.
+__host__ __device__ constexpr int circ_next(int j) {
+  return j == 0 ? 0 : j == 1 ? 2 : j == 20 ? 21 : (j % 2 == 0 ? j + 2 : j - 2);
+}
+__device__ __forceinline__ int circ_prev(int lane) {
+  if (lane >= kJ || lane == 0) return lane;
+  if (lane == 2) return 1;
+  if (lane == 21) return 20;
+  return (lane & 1) ? lane + 2 : lane - 2;
+}
+
+// a[idx] for a runtime idx in [0, 32) without dynamic register indexing
+__device__ __forceinline__ float pick22(const float (&a)[kJ], int idx) {
+  float l0[11], l1[6], l2[3], l3[2];
+#pragma unroll
+  for (int i = 0; i < 11; ++i) l0[i] = (idx & 1) ? a[2 * i + 1] : a[2 * i];
+#pragma unroll
+  for (int i = 0; i < 6; ++i) l1[i] = (idx & 2) ? (2 * i + 1 < 11 ? l0[2 * i + 1] : 0.f) : l0[2 * i];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) l2[i] = (idx & 4) ? l1[2 * i + 1] : l1[2 * i];
+  l3[0] = (idx & 8) ? l2[1] : l2[0];
+  l3[1] = l2[2];
+  return (idx >= kJ) ? 0.f : ((idx & 16) ? l3[1] : l3[0]);
+}
+
+// One round; returns whether any pair was rotated.
+__device__ __forceinline__ bool circle_round(float (&a)[kJ], float (&v)[kJ], int lane, float thr) {
+  constexpr unsigned kFull = 0xffffffffu;
+  const bool is_p = (lane & 1) == 0;
+  const float apq = pick22(a, lane ^ 1);
+  const float dg = pick22(a, lane);
+  const float dq = __shfl_xor_sync(kFull, dg, 1);
+  float c = 1.f, s = 0.f;
+  bool did = false;
+  if (is_p && lane < kJ && fabsf(apq) > thr) {
+    const float theta = __fdividef(dq - dg, 2.f * apq);
+    const float t = copysignf(1.f, theta) / (fabsf(theta) + sqrtf(fmaf(theta, theta, 1.f)));
+    c = rsqrtf(fmaf(t, t, 1.f));
+    s = t * c;
+    did = true;
+  }
+  const bool any = __any_sync(kFull, did);
+  if (any) {
+    const float oc = __shfl_xor_sync(kFull, c, 1), os = __shfl_xor_sync(kFull, s, 1);
+    const float myc = is_p ? c : oc;
+    const float sg = is_p ? -s : os;
+    // rows: A <- J^T A (a lane and its partner lane combine their rows)
+#pragma unroll
+    for (int j = 0; j < kJ; ++j) {
+      const float pr = __shfl_xor_sync(kFull, a[j], 1);
+      a[j] = fmaf(myc, a[j], sg * pr);
+    }
+    // columns: A <- A J, V <- V J
+#pragma unroll
+    for (int k = 0; k < kJ / 2; ++k) {
+      const float ck = __shfl_sync(kFull, c, 2 * k), sk = __shfl_sync(kFull, s, 2 * k);
+      const float ap = a[2 * k], aq = a[2 * k + 1];
+      a[2 * k] = ck * ap - sk * aq;
+      a[2 * k + 1] = sk * ap + ck * aq;
+      const float vp = v[2 * k], vq = v[2 * k + 1];
+      v[2 * k] = ck * vp - sk * vq;
+      v[2 * k + 1] = sk * vp + ck * vq;
+    }
+  }
+  // advance the tournament: A <- P A P^T, V <- V P^T
+  const int src = circ_prev(lane);
+  float t[kJ];
+#pragma unroll
+  for (int j = 0; j < kJ; ++j) t[circ_next(j)] = __shfl_sync(kFull, a[j], src);
+#pragma unroll
+  for (int j = 0; j < kJ; ++j) a[j] = t[j];
+#pragma unroll
+  for (int j = 0; j < kJ; ++j) t[circ_next(j)] = v[j];
+#pragma unroll
+  for (int j = 0; j < kJ; ++j) v[j] = t[j];
+  return any;
+}
 
 __global__ void __launch_bounds__(256) k_ne_finalize(int dtype, const double* __restrict__ f64_partials,
                                                      int nblocks, DevScalars* __restrict__ sc,
                                                      double* __restrict__ sigma_out) {
   __shared__ double S[kD][kD];
   __shared__ double s_sum[kD * kD + kD + 1];
-  __shared__ float A[kJ][kJ + 1];
   __shared__ float V[kJ][kJ + 1];
-  __shared__ float s_c[kJ / 2], s_s[kJ / 2];
-  __shared__ int s_p[kJ / 2], s_q[kJ / 2];
   __shared__ double s_lam[kD];
   __shared__ double s_sorted[kD];
   __shared__ double s_num[kD][kD];
@@ -412,84 +546,41 @@ __global__ void __launch_bounds__(256) k_ne_finalize(int dtype, const double* __
     return;
   }
   // Sigma = S2/N - mu mu^T (upper triangle accumulated; mirror it)
+  const double inv_n = 1.0 / npd;
   for (int e = tid; e < kD * kD; e += blockDim.x) {
     const int r = e / kD, c = e % kD;
     const int rr = min(r, c), cc = max(r, c);
-    const double mr = s_sum[kD * kD + rr] / npd, mc = s_sum[kD * kD + cc] / npd;
-    S[r][c] = s_sum[rr * kD + cc] / npd - mr * mc;
-  }
-  __syncthreads();
-  for (int e = tid; e < kJ * kJ; e += blockDim.x) {
-    const int r = e / kJ, c = e % kJ;
-    A[r][c] = (r < kD && c < kD) ? float(S[r][c]) : 0.f;
-    V[r][c] = (r == c) ? 1.f : 0.f;
+    const double mr = s_sum[kD * kD + rr] * inv_n, mc = s_sum[kD * kD + cc] * inv_n;
+    S[r][c] = s_sum[rr * kD + cc] * inv_n - mr * mc;
   }
   __syncthreads();
 
-  // cyclic Jacobi, round-robin order: 11 disjoint rotations per round.  A pair
-  // is rotated only while |a_pq| >= 1e-7 sqrt|a_pp a_qq| (float32 resolution);
-  // a sweep that rotates nothing ends the iteration.
-  for (int sweep = 0; sweep < kMaxSweeps; ++sweep) {
-    int rotated = 0;
-    for (int round = 0; round < kJ - 1; ++round) {
-      int did = 0;
-      if (tid < kJ / 2) {
-        int p, q;
-        if (tid == 0) {
-          p = round;
-          q = kJ - 1;
-        } else {
-          p = (round + tid) % (kJ - 1);
-          q = (round - tid + (kJ - 1)) % (kJ - 1);
-        }
-        if (p > q) {
-          const int t = p;
-          p = q;
-          q = t;
-        }
-        const float apq = A[p][q], app = A[p][p], aqq = A[q][q];
-        float c = 1.f, s = 0.f;
-        if (fabsf(apq) >= 1e-7f * sqrtf(fabsf(app * aqq)) && apq != 0.f) {
-          const float theta = (aqq - app) / (2.f * apq);
-          const float t = copysignf(1.f, theta) / (fabsf(theta) + sqrtf(theta * theta + 1.f));
-          c = rsqrtf(t * t + 1.f);
-          s = t * c;
-          did = 1;
-        }
-        s_p[tid] = p;
-        s_q[tid] = q;
-        s_c[tid] = c;
-        s_s[tid] = s;
-      }
-      const int any = __syncthreads_count(did);
-      rotated += any;
-      if (!any) continue;
-      // rows: A <- J^T A
-      for (int e = tid; e < (kJ / 2) * kJ; e += blockDim.x) {
-        const int pr = e / kJ, j = e % kJ;
-        const int p = s_p[pr], q = s_q[pr];
-        const float c = s_c[pr], s = s_s[pr];
-        const float ap = A[p][j], aq = A[q][j];
-        A[p][j] = c * ap - s * aq;
-        A[q][j] = s * ap + c * aq;
-      }
-      __syncthreads();
-      // columns: A <- A J, V <- V J
-      for (int e = tid; e < (kJ / 2) * kJ; e += blockDim.x) {
-        const int pr = e / kJ, i = e % kJ;
-        const int p = s_p[pr], q = s_q[pr];
-        const float c = s_c[pr], s = s_s[pr];
-        const float ap = A[i][p], aq = A[i][q];
-        A[i][p] = c * ap - s * aq;
-        A[i][q] = s * ap + c * aq;
-        const float vp = V[i][p], vq = V[i][q];
-        V[i][p] = c * vp - s * vq;
-        V[i][q] = s * vp + c * vq;
-      }
-      __syncthreads();
+  // Cyclic Jacobi in float32 by warp 0, matrix and vectors in registers.  A
+  // pair is rotated only while |a_pq| > 2e-7 ||diag A|| (the float32
+  // resolution of the matrix); a sweep that rotates nothing ends the iteration.
+  if (tid < 32) {
+    const int lane = tid;
+    float a[kJ], v[kJ];
+#pragma unroll
+    for (int j = 0; j < kJ; ++j) {
+      a[j] = (lane < kD && j < kD) ? float(S[lane][j]) : 0.f;
+      v[j] = (j == lane) ? 1.f : 0.f;
     }
-    if (rotated == 0) break;
+    float dsq = lane < kD ? float(S[lane][lane]) * float(S[lane][lane]) : 0.f;
+    dsq = warp_sum(dsq);
+    const float thr = 2e-7f * sqrtf(dsq);
+    for (int sweep = 0; sweep < kMaxSweeps; ++sweep) {
+      bool rotated = false;
+#pragma unroll 1
+      for (int round = 0; round < kJ - 1; ++round) rotated |= circle_round(a, v, lane, thr);
+      if (!rotated) break;
+    }
+    if (lane < kJ) {
+#pragma unroll
+      for (int j = 0; j < kJ; ++j) V[lane][j] = v[j];
+    }
   }
+  __syncthreads();
 
   // float64 Rayleigh quotients of the 21 eigenvector estimates
   for (int e = tid; e < kD * kD; e += blockDim.x) {
@@ -508,7 +599,7 @@ __global__ void __launch_bounds__(256) k_ne_finalize(int dtype, const double* __
     s_lam[tid] = num / den;
   }
   __syncthreads();
-  // eigenvalues below 1e-10 max(lambda_1, 1) are numerical zeros (a rank-deficient
+  // eigenvalues below 1e-9 max(lambda_1, 1) are numerical zeros (a rank-deficient
   // covariance); they are set to exactly 0 so the tail rule never decides on rounding noise
   if (tid < kD) {
     double top = s_lam[0];
@@ -531,7 +622,10 @@ __global__ void __launch_bounds__(256) k_ne_finalize(int dtype, const double* __
   __syncthreads();
   if (tid < kD) sc->eig[tid] = s_sorted[tid];
   if (tid == 0) {
-    // tail rule: smallest m with mean(lambda_{m+1..D}) <= median(lambda_{m+1..D})
+    // tail rule: smallest m with mean(lambda_{m+1..D}) <= median(lambda_{m+1..D}).
+    // The tail sums are accumulated from the smallest value up, so a tail of
+    // exact zeros sums to exactly 0 (a running total minus the dropped values
+    // would leave rounding residue there).
     double suffix[kD + 1];
     suffix[kD] = 0.0;
     for (int i = kD - 1; i >= 0; --i) suffix[i] = suffix[i + 1] + s_sorted[i];
@@ -571,12 +665,21 @@ cudaError_t launch_gather_colors(const void* rgb, int dtype, int n, const int32_
 }
 
 int ne_moment_blocks(int n, int num_sms) {
-  return std::max(1, std::min((n + kNeThreads - 1) / kNeThreads, num_sms * 4));
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ne_moments<0>, kNeThreads, 0) != cudaSuccess ||
+      per_sm < 1)
+    per_sm = 1;
+  int per_sm_f = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_f, k_ne_moments<1>, kNeThreads, 0) != cudaSuccess ||
+      per_sm_f < 1)
+    per_sm_f = 1;
+  per_sm = std::min(per_sm, per_sm_f);
+  return std::max(1, std::min((n + kNeThreads - 1) / kNeThreads, num_sms * per_sm));
 }
 
 cudaError_t launch_ne_moments(int n, int bits, int dtype, const GraphBufs& gb, const uint32_t* y8,
-                                   const float4* yf, float* spread, double* f64_partials,
-                                   DevScalars* sc, int num_sms, bool moments, cudaStream_t stream) {
+                              const float4* yf, float* spread, double* f64_partials,
+                              DevScalars* sc, int num_sms, bool moments, cudaStream_t stream) {
   if (n <= 0) return cudaSuccess;
   const int grid = ne_moment_blocks(n, num_sms);
   if (dtype == 0)

@@ -5,8 +5,8 @@
 // allocation would stall or be illegal, plug-ins whose host application owns
 // all device memory, or services on a GPU with a fixed memory budget.  This
 // entry point runs the same histogram and radix-sort kernels as
-// fgbd_build_graph, but its scratch (key/value ping-pong buffers, look-back
-// words, digit histograms, ranks) lives in one file-scope device array of
+// fgbd_build_graph, but its scratch (key/value ping-pong buffers, per-tile
+// digit counts, digit histograms, ranks) lives in one file-scope device array of
 // fixed size, reserved on every GPU that loads the library until the process
 // exits.  The caller passes the coordinates and the output buffer.
 #include <mutex>
@@ -29,8 +29,8 @@ constexpr size_t kOffKeys0 = align256(kOffScalars + sizeof(DevScalars));
 constexpr size_t kOffKeys1 = align256(kOffKeys0 + 3 * kMaxPts * 4);
 constexpr size_t kOffVals0 = align256(kOffKeys1 + 3 * kMaxPts * 4);
 constexpr size_t kOffVals1 = align256(kOffVals0 + 3 * kMaxPts * 4);
-constexpr size_t kOffLookback = align256(kOffVals1 + 3 * kMaxPts * 4);
-constexpr size_t kOffPk = align256(kOffLookback + size_t(kMaxPasses) * 3 * kMaxTiles * kRadix * 4);
+constexpr size_t kOffTileCounts = align256(kOffVals1 + 3 * kMaxPts * 4);
+constexpr size_t kOffPk = align256(kOffTileCounts + size_t(kMaxPasses) * 3 * kMaxTiles * kRadix * 4);
 constexpr size_t kOffRank1 = align256(kOffPk + kMaxPts * 4);
 constexpr size_t kOffRank2 = align256(kOffRank1 + kMaxPts * 4);
 constexpr size_t kScratchBytes = align256(kOffRank2 + kMaxPts * 4);
@@ -72,9 +72,8 @@ extern "C" fgbd_status fgbd_scan_orders_static(const int32_t* xyz, int64_t n64, 
     return FGBD_ECUDA;
   }
   DevScalars* sc = reinterpret_cast<DevScalars*>(base + kOffScalars);
-  // the array keeps the previous call's contents: clear the status word,
-  // histograms and tile counters (the look-back words are cleared by the
-  // histogram kernel)
+  // the array keeps the previous call's contents: clear the status word and
+  // the digit histograms (the per-tile digit counts are rewritten by every pass)
   if (cudaMemsetAsync(sc, 0, sizeof(DevScalars), st) != cudaSuccess) {
     cudaGetLastError();
     return FGBD_ECUDA;
@@ -93,7 +92,7 @@ extern "C" fgbd_status fgbd_scan_orders_static(const int32_t* xyz, int64_t n64, 
     sb.keys[1] = reinterpret_cast<uint32_t*>(base + kOffKeys1);
     sb.vals[0] = reinterpret_cast<uint32_t*>(base + kOffVals0);
     sb.vals[1] = reinterpret_cast<uint32_t*>(base + kOffVals1);
-    sb.lookback = reinterpret_cast<uint32_t*>(base + kOffLookback);
+    sb.tile_counts = reinterpret_cast<uint32_t*>(base + kOffTileCounts);
     sb.passes = (3 * bits + kRadixBits - 1) / kRadixBits;
     sb.tiles = (n + kSortTile - 1) / kSortTile;
     GraphBufs gb{};
@@ -101,8 +100,7 @@ extern "C" fgbd_status fgbd_scan_orders_static(const int32_t* xyz, int64_t n64, 
     gb.pk = reinterpret_cast<uint32_t*>(base + kOffPk);
     gb.rank1 = reinterpret_cast<int32_t*>(base + kOffRank1);
     gb.rank2 = reinterpret_cast<int32_t*>(base + kOffRank2);
-    const size_t zero_words = size_t(sb.passes) * 3 * size_t(sb.tiles) * kRadix;
-    if (launch_hist(xyz, n, bits, sb.passes, sb.lookback, zero_words, sc, num_sms, st) != cudaSuccess) {
+    if (launch_hist(xyz, n, bits, sb.passes, sb.tile_counts, 0, sc, num_sms, st) != cudaSuccess) {
       cudaGetLastError();
       return FGBD_ECUDA;
     }
