@@ -172,24 +172,32 @@ class ClockSampler:
 
 # ------------------------------------------------------------------ roofline bookkeeping
 
-def algorithmic_bytes(name, n, q_iters=0, passes=4, out_bytes=3):
+def algorithmic_bytes(name, n, q_iters=0, out_bytes=3):
     """Compulsory DRAM bytes of one launch: the per-point figure of each kernel times n."""
-    if name == "slg_hist":
-        return 12 * n
-    if name.startswith("slg_sort_pass"):
-        p = int(name[-1])
-        read = 36 * n if p == 0 else 24 * n  # xyz once per code, or (key, value) of the 3 codes
-        write = 24 * n                       # (key, value) of 3 codes; last pass: 3 orders, codes, 2 ranks
-        return read + write
-    if name == "slg_link":
-        return 48 * n
-    if name == "gather_colors":
-        return 11 * n
-    if name == "ne_moments":
-        return 28 * n
+    per_point = {
+        "slg_hist": 12,                                   # xyz
+        # digit counts: keys once per code slot (pass 0 reads xyz)
+        "slg_counts0": 12, "slg_counts1": 4, "slg_counts2": 4, "slg_counts3": 8, "slg_counts4": 8,
+        # scatter: keys and values in, keys and values (or the final arrays) out
+        "slg_scatter0": 12 + 8, "slg_scatter1": 8 + 8, "slg_scatter2": 8 + 12,
+        "slg_scatter3": 8 + 16, "slg_scatter4": 16 + 12,
+        "slg_link": 40,
+        "gather_colors": 11,
+        "ne_moments": 28,
+    }
+    if name in per_point:
+        return per_point[name] * n
     if name == "filter_select":
         return 28 * n + 48 * n * q_iters + (20 + out_bytes) * n
     return 0
+
+
+def kernel_group(name):
+    """Launches of the same kernel function share one group (the sort passes differ by digit)."""
+    for g in ("slg_counts", "slg_scan", "slg_scatter"):
+        if name.startswith(g):
+            return g
+    return name
 
 
 def read_peaks():
@@ -302,8 +310,7 @@ def run_fgbd(args):
     # the kernel with the largest share of the step; the sort passes are one kernel
     groups = {}
     for name, kd in kernels.items():
-        g = "slg_sort_pass" if name.startswith("slg_sort_pass") else name
-        groups.setdefault(g, []).append(kd)
+        groups.setdefault(kernel_group(name), []).append(kd)
     dom = max(groups, key=lambda g: sum(kd["ms"] * kd["launches_per_step"] for kd in groups[g]))
     members = groups[dom]
     dom_ms = float(np.mean([kd["ms"] for kd in members]))

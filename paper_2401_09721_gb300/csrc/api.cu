@@ -36,7 +36,6 @@ struct fgbd_ctx {
   double* f64part = nullptr;
   int f64_blocks = 0;
   int64_t* scan_tmp = nullptr;
-  int max_tiles = 0;
   // state of the frame held in the context
   int n = 0;
   bool has_graph = false;
@@ -106,8 +105,6 @@ struct LaunchScope {
   } while (0)
 
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
-
-int passes_for(int bits) { return (3 * bits + kRadixBits - 1) / kRadixBits; }
 
 bool params_ok(const fgbd_params& p) {
   if (p.bits < 1 || p.bits > kMaxBits) return false;
@@ -183,15 +180,19 @@ fgbd_status do_build(fgbd_ctx* ctx, const int32_t* xyz, int64_t n64, cudaStream_
   zero_region(ctx, offsetof(DevScalars, n_edges), offsetof(DevScalars, build_end_), st, &e);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "memset");
   if (n > 0) {
-    ctx->sb.passes = passes_for(bits);
-    ctx->sb.tiles = (n + kSortTile - 1) / kSortTile;
-    FGBD_LAUNCH(ctx, "slg_hist", st,
-                launch_hist(xyz, n, bits, ctx->sb.passes, ctx->sb.tile_counts, 0, ctx->sc, ctx->num_sms, st));
-    static const char* const kPassNames[kMaxPasses] = {"slg_sort_pass0", "slg_sort_pass1", "slg_sort_pass2",
-                                                       "slg_sort_pass3"};
-    for (int p = 0; p < ctx->sb.passes; ++p)
-      FGBD_LAUNCH(ctx, kPassNames[p], st,
-                  launch_sort_pass(p, ctx->sb.passes, xyz, n, bits, int(ctx->capacity), ctx->sb, ctx->gb, ctx->sc, st));
+    // kernel names carry the pass: 0-2 = C1 on x, y, z; 3-4 = C2 and C3
+    static const char* const kCounts[kSlgPasses] = {"slg_counts0", "slg_counts1", "slg_counts2", "slg_counts3",
+                                                    "slg_counts4"};
+    static const char* const kScan[kSlgPasses] = {"slg_scan0", "slg_scan1", "slg_scan2", "slg_scan3", "slg_scan4"};
+    static const char* const kScatter[kSlgPasses] = {"slg_scatter0", "slg_scatter1", "slg_scatter2",
+                                                     "slg_scatter3", "slg_scatter4"};
+    FGBD_LAUNCH(ctx, "slg_hist", st, launch_coord_hist(xyz, n, bits, ctx->sc, ctx->num_sms, st));
+    for (int p = 0; p < kSlgPasses; ++p) {
+      const SortPassArgs a = slg_pass_args(p, xyz, n, bits, int(ctx->capacity), ctx->sb, ctx->gb, ctx->sc);
+      FGBD_LAUNCH(ctx, kCounts[p], st, launch_tile_counts(a, st));
+      FGBD_LAUNCH(ctx, kScan[p], st, launch_tile_scan(a, st));
+      FGBD_LAUNCH(ctx, kScatter[p], st, launch_sort_scatter(a, st));
+    }
     FGBD_LAUNCH(ctx, "slg_link", st, launch_link(n, bits, int(ctx->capacity), ctx->gb, ctx->sc, ctx->num_sms, st));
   }
   ctx->has_graph = true;
@@ -210,7 +211,7 @@ fgbd_status do_estimate(fgbd_ctx* ctx, const void* rgb, int32_t dtype, double* s
   if (e != cudaSuccess) return cuda_fail(ctx, e, "memset");
   int nblocks = 0;
   if (n > 0) {
-    FGBD_LAUNCH(ctx, "gather_colors", st, launch_gather_colors(rgb, dtype, n, ctx->gb.perm, ctx->y8, ctx->yf, st));
+    FGBD_LAUNCH(ctx, "gather_colors", st, launch_gather_colors(rgb, dtype, n, ctx->gb.perm1, ctx->y8, ctx->yf, st));
     nblocks = ne_moment_blocks(n, ctx->num_sms);
     FGBD_LAUNCH(ctx, "ne_moments", st,
                 launch_ne_moments(n, ctx->params.bits, dtype, ctx->gb, ctx->y8, ctx->yf, ctx->spread, ctx->f64part,
@@ -290,7 +291,6 @@ fgbd_status fgbd_ctx_create(int64_t capacity, const fgbd_params* params, fgbd_ct
 
   const size_t C = size_t(capacity);
   const int tiles = int((C + kSortTile - 1) / kSortTile);
-  ctx->max_tiles = tiles;
   ctx->f64_blocks = ne_moment_blocks(int(C), ctx->num_sms);
   const size_t kP = size_t(kD) * kD + kD + 1;
   struct Item {
@@ -303,15 +303,16 @@ fgbd_status fgbd_ctx_create(int64_t capacity, const fgbd_params* params, fgbd_ct
   void* vals1 = nullptr;
   const Item items[] = {
       {reinterpret_cast<void**>(&ctx->sc), sizeof(DevScalars)},
-      {&keys0, 3 * C * 4},
-      {&keys1, 3 * C * 4},
-      {&vals0, 3 * C * 4},
-      {&vals1, 3 * C * 4},
-      {reinterpret_cast<void**>(&ctx->sb.tile_counts), size_t(kMaxPasses) * 3 * tiles * kRadix * 4},
-      {reinterpret_cast<void**>(&ctx->gb.perm), 3 * C * 4},
+      {&keys0, 2 * C * 4},
+      {&keys1, 2 * C * 4},
+      {&vals0, 2 * C * 4},
+      {&vals1, 2 * C * 4},
+      {reinterpret_cast<void**>(&ctx->sb.tile_counts), size_t(2) * kMaxRadix * tiles * 4},
+      {reinterpret_cast<void**>(&ctx->gb.perm1), C * 4},
       {reinterpret_cast<void**>(&ctx->gb.rank1), C * 4},
-      {reinterpret_cast<void**>(&ctx->gb.rank2), C * 4},
       {reinterpret_cast<void**>(&ctx->gb.pk), C * 4},
+      {reinterpret_cast<void**>(&ctx->gb.ord23), 2 * C * 4},
+      {reinterpret_cast<void**>(&ctx->gb.rank2), C * 4},
       {reinterpret_cast<void**>(&ctx->gb.c4), C * 16},
       {reinterpret_cast<void**>(&ctx->y8), C * 4},
       {reinterpret_cast<void**>(&ctx->yf), C * 16},
@@ -398,7 +399,7 @@ fgbd_status fgbd_denoise(fgbd_ctx* ctx, const void* rgb_in, int32_t in_dtype, in
   if (ctx->n > 0 && !rgb_in) return FGBD_EINVAL;
   if (ctx->n > 0) {
     FGBD_LAUNCH(ctx, "gather_colors", st,
-                launch_gather_colors(rgb_in, in_dtype, ctx->n, ctx->gb.perm, ctx->y8, ctx->yf, st));
+                launch_gather_colors(rgb_in, in_dtype, ctx->n, ctx->gb.perm1, ctx->y8, ctx->yf, st));
   }
   // the gathered colours and filter buffers now hold this call's data
   if (rgb_in != ctx->noise_rgb || in_dtype != ctx->noise_dtype) {
@@ -492,9 +493,7 @@ fgbd_status fgbd_get_orders(fgbd_ctx* ctx, int32_t* orders, void* stream) {
   if (!ctx->has_graph) return FGBD_ESTATE;
   if (ctx->n > 0 && !orders) return FGBD_EINVAL;
   const cudaStream_t st = as_stream(stream);
-  for (int l = 0; l < 3 && ctx->n > 0; ++l)
-    FGBD_CUDA(ctx, cudaMemcpyAsync(orders + size_t(l) * ctx->n, ctx->gb.perm + size_t(l) * ctx->capacity,
-                                   size_t(ctx->n) * sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
+  FGBD_LAUNCH(ctx, "orders_export", st, launch_orders_export(ctx->n, int(ctx->capacity), ctx->gb, orders, st));
   return FGBD_OK;
 }
 

@@ -16,13 +16,12 @@
 
 namespace fgbd {
 
-constexpr int kMaxBits = 10;        // three b-bit coordinates fit a 32-bit code
-constexpr int kRadixBits = 8;
-constexpr int kRadix = 1 << kRadixBits;
+constexpr int kMaxBits = 10;                       // three b-bit coordinates fit a 32-bit code
+constexpr int kMaxRadix = 1 << kMaxBits;           // radix passes use one coordinate (b bits) as digit
 constexpr int kSortThreads = 256;
 constexpr int kSortKpt = 16;                       // keys per thread
 constexpr int kSortTile = kSortThreads * kSortKpt;  // 4096 keys per tile
-constexpr int kMaxPasses = 4;                      // ceil(30 / 8)
+constexpr int kSlgPasses = 5;                      // 3 for C1, 2 for C2 and C3 together
 constexpr int kK = 6;                              // neighbours per point at window 1
 constexpr int kD = 3 * (kK + 1);                   // patch dimension (Section 2.3)
 constexpr int kQCap = 256;                         // largest q_max accepted
@@ -45,8 +44,7 @@ struct DevScalars {
   // ---- graph build region
   unsigned long long n_edges;   // distinct undirected edges E
   unsigned long long dist_fx;   // sum of edge lengths, fixed point 2^-kDistShift
-  uint32_t hist[3][kMaxPasses][kRadix];
-  uint32_t tile_counter[kMaxPasses];
+  alignas(16) uint32_t chist[3][kMaxRadix];  // histograms of x, y and z (read as uint4)
   uint32_t build_end_;
   // ---- noise estimate region
   unsigned long long n_patches;
@@ -77,30 +75,54 @@ struct DevScalars {
 
 // Sort scratch for one build.
 struct SortBufs {
-  uint32_t* keys[2];   // ping-pong [3][cap]
-  uint32_t* vals[2];   // ping-pong [3][cap]
-  uint32_t* tile_counts;  // [passes][3 codes][kRadix digits][tiles]: per-tile digit counts, then offsets
-  int tiles;           // tiles per code at this n
-  int passes;
+  uint32_t* keys[2];     // ping-pong [2 code slots][cap]
+  uint32_t* vals[2];     // ping-pong [2 code slots][cap]
+  uint32_t* tile_counts; // [2 code slots][kMaxRadix digits][tiles]: per-tile digit counts, then offsets
 };
 
 // Graph in sorted order.
 struct GraphBufs {
-  int32_t* perm;     // [3][cap] input index at each position of each code order
-  int32_t* rank1;    // [cap] position of each input point in the C1 order
-  int32_t* rank2;    // [cap] position of each input point in the C2 order
+  int32_t* perm1;    // [cap] input index of each sorted (C1-order) point
+  int32_t* rank1;    // [cap] sorted id of each input point
   uint32_t* pk;      // [cap] packed C1 code of each sorted point (its coordinates)
+  int32_t* ord23;    // [2][cap] sorted ids along C2 and along C3
+  int32_t* rank2;    // [cap] position of each sorted id in the C2 order
   int4* c4;          // [cap] C2 prev, C2 next, C3 prev, C3 next (sorted ids, -1 empty)
+};
+
+// One radix pass over one or two codes (code slots) whose digit is one
+// coordinate field of the key.
+struct SortPassArgs {
+  int n;
+  int bits;
+  int cap;
+  int tiles;               // tiles per code slot
+  int ncodes;              // 1 or 2
+  int keys_in_shared;      // both slots read the same key array (no slot offset)
+  int shift[2];            // bit offset of the digit in the key
+  int coord[2];            // which coordinate histogram gives the digit totals
+  const int32_t* xyz;      // if set: keys from the coordinates, values = input index
+  const uint32_t* keys_in[2];
+  const uint32_t* vals_in[2];  // null: value = position
+  uint32_t* keys_out[2];       // null: not written
+  uint32_t* vals_out[2];
+  int32_t* rank_out[2];        // rank_out[value] = output position, or null
+  uint32_t* counts;
+  const DevScalars* sc;
 };
 
 // ---------------------------------------------------------------- launchers
 // Every launcher enqueues on `stream` and returns the launch error.
 
-cudaError_t launch_hist(const int32_t* xyz, int n, int bits, int passes, uint32_t* zero_buf,
-                        size_t zero_words, DevScalars* sc, int num_sms, cudaStream_t stream);
-cudaError_t launch_sort_pass(int pass, int passes, const int32_t* xyz, int n, int bits, int cap,
-                             const SortBufs& sb, const GraphBufs& gb, DevScalars* sc,
-                             cudaStream_t stream);
+cudaError_t launch_coord_hist(const int32_t* xyz, int n, int bits, DevScalars* sc, int num_sms, cudaStream_t stream);
+// pass 0..2: C1 on x, y, z; pass 3..4: C2 and C3 over the C1 order
+SortPassArgs slg_pass_args(int pass, const int32_t* xyz, int n, int bits, int cap, const SortBufs& sb,
+                           const GraphBufs& gb, const DevScalars* sc);
+cudaError_t launch_tile_counts(const SortPassArgs& a, cudaStream_t stream);
+cudaError_t launch_tile_scan(const SortPassArgs& a, cudaStream_t stream);
+cudaError_t launch_sort_scatter(const SortPassArgs& a, cudaStream_t stream);
+cudaError_t launch_sort_pass(const SortPassArgs& a, cudaStream_t stream);  // the three above
+cudaError_t launch_orders_export(int n, int cap, const GraphBufs& gb, int32_t* out, cudaStream_t stream);
 cudaError_t launch_link(int n, int bits, int cap, const GraphBufs& gb, DevScalars* sc, int num_sms,
                         cudaStream_t stream);
 

@@ -470,7 +470,7 @@ cudaError_t launch_csr_fill(int n, int bits, const GraphBufs& gb, const int64_t*
                             float* w, int64_t col_capacity, const DevScalars* sc, cudaStream_t stream) {
   if (n <= 0) return cudaSuccess;
   const int grid = std::min((n + 255) / 256, 152 * 16);
-  k_csr_fill<<<grid, 256, 0, stream>>>(n, bits, gb.rank1, gb.perm, gb.pk, gb.c4, row_ptr, col, w, col_capacity, sc);
+  k_csr_fill<<<grid, 256, 0, stream>>>(n, bits, gb.rank1, gb.perm1, gb.pk, gb.c4, row_ptr, col, w, col_capacity, sc);
   return cudaGetLastError();
 }
 

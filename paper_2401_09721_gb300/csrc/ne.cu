@@ -418,103 +418,62 @@ __global__ void __launch_bounds__(kNeThreads)
 // ---------------------------------------------------------------- finalize
 
 constexpr double kZeroEigRel = 1e-9;  // relative size below which an eigenvalue is zero
-constexpr int kJ = 22;           // 21 padded to an even size for round-robin pairing
 constexpr int kMaxSweeps = 15;
+constexpr int kFinThreads = 448;      // 14 warps: one thread per element of the 21 x 21 matrix
 
-// ---- register-resident Jacobi: one warp, lane i holds row i of A and of V.
-// Circle-method tournament on 22 positions (21 indices + one zero pad): each
-// round rotates the fixed position pairs (2k, 2k+1), then every index except
-// the one at position 0 moves one step along the ring 2 -> 4 -> ... -> 20 ->
-// 21 -> 19 -> ... -> 1 -> 2.  Every pair of indices meets once in 21 rounds,
-// and after a full sweep every index is back at its own position.  Rows move
-// between lanes by shuffles; columns move between registers by a fixed
-// permutation, so every register index is static and the loop stays small.
-__host__ __device__ constexpr int circ_next(int j) {
-  return j == 0 ? 0 : j == 1 ? 2 : j == 20 ? 21 : (j % 2 == 0 ? j + 2 : j - 2);
-}
-__device__ __forceinline__ int circ_prev(int lane) {
-  if (lane >= kJ || lane == 0) return lane;
-  if (lane == 2) return 1;
-  if (lane == 21) return 20;
-  return (lane & 1) ? lane + 2 : lane - 2;
+// Parallel cyclic Jacobi schedule on 21 indices: in round r (0..20) index i is
+// paired with (2r - i) mod 21, and index r, which pairs with itself, rests.
+// Every pair {i, j} meets exactly once per sweep, in the round r with
+// 2r = i + j (mod 21).
+__device__ __forceinline__ int jacobi_partner(int i, int r) {
+  int p = 2 * r - i;
+  if (p < 0) p += kD;
+  if (p >= kD) p -= kD;
+  return p;
 }
 
-// a[idx] for a runtime idx in [0, 32) without dynamic register indexing
-__device__ __forceinline__ float pick22(const float (&a)[kJ], int idx) {
-  float l0[11], l1[6], l2[3], l3[2];
-#pragma unroll
-  for (int i = 0; i < 11; ++i) l0[i] = (idx & 1) ? a[2 * i + 1] : a[2 * i];
-#pragma unroll
-  for (int i = 0; i < 6; ++i) l1[i] = (idx & 2) ? (2 * i + 1 < 11 ? l0[2 * i + 1] : 0.f) : l0[2 * i];
-#pragma unroll
-  for (int i = 0; i < 3; ++i) l2[i] = (idx & 4) ? l1[2 * i + 1] : l1[2 * i];
-  l3[0] = (idx & 8) ? l2[1] : l2[0];
-  l3[1] = l2[2];
-  return (idx >= kJ) ? 0.f : ((idx & 16) ? l3[1] : l3[0]);
+// The rotation of round r acting on index x: new row/column x = alpha * old x +
+// beta * old partner.  For the pair p < q with a_pq above the threshold the
+// angle zeroes a_pq: cos 2phi = |a_qq - a_pp| / r, r = sqrt((a_qq - a_pp)^2 +
+// 4 a_pq^2), c = sqrt((1 + cos 2phi) / 2), |s| = |a_pq| / (r c), and s takes
+// the sign of (a_qq - a_pp) a_pq (the smaller of the two angles that zero it).
+// Every thread derives the coefficients from the same three entries with the
+// same operations, so all threads agree on them bit for bit.
+__device__ __forceinline__ bool jacobi_coef(const float* __restrict__ A, int x, int px, float thr, float& alpha,
+                                            float& beta) {
+  alpha = 1.f;
+  beta = 0.f;
+  if (px == x) return false;
+  const int p = min(x, px), q = max(x, px);
+  const float apq = A[p * kD + q];
+  if (!(fabsf(apq) > thr)) return false;
+  const float tau = A[q * kD + q] - A[p * kD + p];
+  const float two_a = 2.f * apq;
+  const float rr = rsqrtf(fmaf(tau, tau, two_a * two_a));
+  const float h = fmaf(0.5f * fabsf(tau), rr, 0.5f);
+  const float ic = rsqrtf(h);
+  const float c = h * ic;
+  float s = fabsf(apq) * rr * ic;
+  if ((tau < 0.f) != (apq < 0.f)) s = -s;
+  alpha = c;
+  beta = (x == p) ? -s : s;
+  return true;
 }
 
-// One round; returns whether any pair was rotated.
-__device__ __forceinline__ bool circle_round(float (&a)[kJ], float (&v)[kJ], int lane, float thr) {
-  constexpr unsigned kFull = 0xffffffffu;
-  const bool is_p = (lane & 1) == 0;
-  const float apq = pick22(a, lane ^ 1);
-  const float dg = pick22(a, lane);
-  const float dq = __shfl_xor_sync(kFull, dg, 1);
-  float c = 1.f, s = 0.f;
-  bool did = false;
-  if (is_p && lane < kJ && fabsf(apq) > thr) {
-    const float theta = __fdividef(dq - dg, 2.f * apq);
-    const float t = copysignf(1.f, theta) / (fabsf(theta) + sqrtf(fmaf(theta, theta, 1.f)));
-    c = rsqrtf(fmaf(t, t, 1.f));
-    s = t * c;
-    did = true;
-  }
-  const bool any = __any_sync(kFull, did);
-  if (any) {
-    const float oc = __shfl_xor_sync(kFull, c, 1), os = __shfl_xor_sync(kFull, s, 1);
-    const float myc = is_p ? c : oc;
-    const float sg = is_p ? -s : os;
-    // rows: A <- J^T A (a lane and its partner lane combine their rows)
-#pragma unroll
-    for (int j = 0; j < kJ; ++j) {
-      const float pr = __shfl_xor_sync(kFull, a[j], 1);
-      a[j] = fmaf(myc, a[j], sg * pr);
-    }
-    // columns: A <- A J, V <- V J
-#pragma unroll
-    for (int k = 0; k < kJ / 2; ++k) {
-      const float ck = __shfl_sync(kFull, c, 2 * k), sk = __shfl_sync(kFull, s, 2 * k);
-      const float ap = a[2 * k], aq = a[2 * k + 1];
-      a[2 * k] = ck * ap - sk * aq;
-      a[2 * k + 1] = sk * ap + ck * aq;
-      const float vp = v[2 * k], vq = v[2 * k + 1];
-      v[2 * k] = ck * vp - sk * vq;
-      v[2 * k + 1] = sk * vp + ck * vq;
-    }
-  }
-  // advance the tournament: A <- P A P^T, V <- V P^T
-  const int src = circ_prev(lane);
-  float t[kJ];
-#pragma unroll
-  for (int j = 0; j < kJ; ++j) t[circ_next(j)] = __shfl_sync(kFull, a[j], src);
-#pragma unroll
-  for (int j = 0; j < kJ; ++j) a[j] = t[j];
-#pragma unroll
-  for (int j = 0; j < kJ; ++j) t[circ_next(j)] = v[j];
-#pragma unroll
-  for (int j = 0; j < kJ; ++j) v[j] = t[j];
-  return any;
-}
-
-__global__ void __launch_bounds__(256) k_ne_finalize(int dtype, const double* __restrict__ f64_partials,
+__global__ void __launch_bounds__(kFinThreads) k_ne_finalize(int dtype, const double* __restrict__ f64_partials,
                                                      int nblocks, DevScalars* __restrict__ sc,
                                                      double* __restrict__ sigma_out) {
   __shared__ double S[kD][kD];
   __shared__ double s_sum[kD * kD + kD + 1];
-  __shared__ float V[kJ][kJ + 1];
+  __shared__ float V[kD][kD + 1];
+  __shared__ float Abuf[2][kD * kD];
+  __shared__ float Vbuf[2][kD * kD];
   __shared__ double s_lam[kD];
   __shared__ double s_sorted[kD];
   __shared__ double s_num[kD][kD];
+  __shared__ double V64[kD][kD + 1];
+  __shared__ double s_suffix[kD + 1];
+  __shared__ int s_pass;
 
   const int tid = threadIdx.x;
   constexpr int kP = kD * kD + kD + 1;
@@ -555,46 +514,71 @@ __global__ void __launch_bounds__(256) k_ne_finalize(int dtype, const double* __
   }
   __syncthreads();
 
-  // Cyclic Jacobi in float32 by warp 0, matrix and vectors in registers.  A
-  // pair is rotated only while |a_pq| > 2e-7 ||diag A|| (the float32
-  // resolution of the matrix); a sweep that rotates nothing ends the iteration.
-  if (tid < 32) {
-    const int lane = tid;
-    float a[kJ], v[kJ];
-#pragma unroll
-    for (int j = 0; j < kJ; ++j) {
-      a[j] = (lane < kD && j < kD) ? float(S[lane][j]) : 0.f;
-      v[j] = (j == lane) ? 1.f : 0.f;
+  // Cyclic Jacobi in float32 over the whole block, matrix and vectors in
+  // shared memory (double-buffered), thread t < 441 owning entry (t / 21,
+  // t % 21) of A and of V.  One barrier per round: each thread derives the
+  // rotations of its row and column indices itself.  A pair is rotated only
+  // while |a_pq| > 2e-7 ||diag A|| (the float32 resolution of the matrix); the
+  // iteration ends at the first barrier where no off-diagonal entry is above
+  // that threshold, since no later round would rotate anything.
+  {
+    const bool owner = tid < kD * kD;
+    const int ei = owner ? tid / kD : 0, ej = owner ? tid % kD : 0;
+    const int lo = min(ei, ej), hi = max(ei, ej);
+    if (owner) {
+      Abuf[0][tid] = float(S[ei][ej]);
+      Vbuf[0][tid] = ei == ej ? 1.f : 0.f;
     }
-    float dsq = lane < kD ? float(S[lane][lane]) * float(S[lane][lane]) : 0.f;
-    dsq = warp_sum(dsq);
+    float dsq = 0.f;
+    for (int i = 0; i < kD; ++i) dsq = fmaf(float(S[i][i]), float(S[i][i]), dsq);
     const float thr = 2e-7f * sqrtf(dsq);
-    for (int sweep = 0; sweep < kMaxSweeps; ++sweep) {
-      bool rotated = false;
-#pragma unroll 1
-      for (int round = 0; round < kJ - 1; ++round) rotated |= circle_round(a, v, lane, thr);
-      if (!rotated) break;
+    int cur = 0;
+    bool big = __syncthreads_or(owner && ei != ej && fabsf(Abuf[0][tid]) > thr);
+    for (int round = 0; big && round < kMaxSweeps * kD; ++round) {
+      const int r = round % kD;
+      const float* A = Abuf[cur];
+      const float* Vc = Vbuf[cur];
+      bool off_big = false;
+      if (owner) {
+        // A' = J^T A J evaluated for (lo, hi) so that both mirror entries get the same bits
+        const int plo = jacobi_partner(lo, r), phi = jacobi_partner(hi, r);
+        float al, bl, ah, bh;
+        jacobi_coef(A, lo, plo, thr, al, bl);
+        jacobi_coef(A, hi, phi, thr, ah, bh);
+        const float row_lo = fmaf(ah, A[lo * kD + hi], bh * A[lo * kD + phi]);
+        const float row_plo = fmaf(ah, A[plo * kD + hi], bh * A[plo * kD + phi]);
+        const float a = fmaf(al, row_lo, bl * row_plo);
+        // V' = V J: column ej of row ei, with the coefficients of index ej
+        const bool j_lo = ej == lo;
+        const float aj = j_lo ? al : ah, bj = j_lo ? bl : bh;
+        const int pj = j_lo ? plo : phi;
+        Abuf[cur ^ 1][tid] = a;
+        Vbuf[cur ^ 1][tid] = fmaf(aj, Vc[ei * kD + ej], bj * Vc[ei * kD + pj]);
+        off_big = ei != ej && fabsf(a) > thr;
+      }
+      cur ^= 1;
+      big = __syncthreads_or(off_big);
     }
-    if (lane < kJ) {
-#pragma unroll
-      for (int j = 0; j < kJ; ++j) V[lane][j] = v[j];
-    }
+    if (owner) V[ei][ej] = Vbuf[cur][tid];
   }
   __syncthreads();
 
   // float64 Rayleigh quotients of the 21 eigenvector estimates
+  for (int e = tid; e < kD * kD; e += blockDim.x) V64[e / kD][e % kD] = double(V[e / kD][e % kD]);
+  __syncthreads();
   for (int e = tid; e < kD * kD; e += blockDim.x) {
     const int k = e / kD, r = e % kD;
     double w = 0.0;
-    for (int c = 0; c < kD; ++c) w += S[r][c] * double(V[c][k]);
-    s_num[k][r] = w * double(V[r][k]);
+#pragma unroll 7
+    for (int c = 0; c < kD; ++c) w = fma(S[r][c], V64[c][k], w);
+    s_num[k][r] = w * V64[r][k];
   }
   __syncthreads();
   if (tid < kD) {
     double num = 0.0, den = 0.0;
     for (int r = 0; r < kD; ++r) {
       num += s_num[tid][r];
-      den += double(V[r][tid]) * double(V[r][tid]);
+      den = fma(V64[r][tid], V64[r][tid], den);
     }
     s_lam[tid] = num / den;
   }
@@ -621,27 +605,33 @@ __global__ void __launch_bounds__(256) k_ne_finalize(int dtype, const double* __
   }
   __syncthreads();
   if (tid < kD) sc->eig[tid] = s_sorted[tid];
+  // tail sums, accumulated from the smallest eigenvalue up so that a tail of
+  // exact zeros sums to exactly 0
   if (tid == 0) {
-    // tail rule: smallest m with mean(lambda_{m+1..D}) <= median(lambda_{m+1..D}).
-    // The tail sums are accumulated from the smallest value up, so a tail of
-    // exact zeros sums to exactly 0 (a running total minus the dropped values
-    // would leave rounding residue there).
-    double suffix[kD + 1];
-    suffix[kD] = 0.0;
-    for (int i = kD - 1; i >= 0; --i) suffix[i] = suffix[i + 1] + s_sorted[i];
-    int m = kD - 1;
-    double tau = s_sorted[kD - 1];
-    for (int mm = 0; mm < kD; ++mm) {
-      const int cnt = kD - mm;
-      const double mean = suffix[mm] / double(cnt);
-      const double med = (cnt & 1) ? s_sorted[mm + cnt / 2]
-                                   : 0.5 * (s_sorted[mm + cnt / 2 - 1] + s_sorted[mm + cnt / 2]);
-      if (mean <= med) {
-        m = mm;
-        tau = mean;
-        break;
-      }
+    s_suffix[kD] = 0.0;
+    for (int i = kD - 1; i >= 0; --i) s_suffix[i] = s_suffix[i + 1] + s_sorted[i];
+  }
+  __syncthreads();
+  // tail rule, every m tested at once: the smallest m with
+  // mean(lambda_{m+1..D}) <= median(lambda_{m+1..D}); m = D - 1 always passes
+  if (tid < 32) {
+    bool pass = false;
+    double mean = 0.0;
+    if (tid < kD) {
+      const int cnt = kD - tid;
+      mean = s_suffix[tid] / double(cnt);
+      const double med = (cnt & 1) ? s_sorted[tid + cnt / 2]
+                                   : 0.5 * (s_sorted[tid + cnt / 2 - 1] + s_sorted[tid + cnt / 2]);
+      pass = mean <= med;
     }
+    const unsigned passing = __ballot_sync(0xffffffffu, pass);
+    const int m = __ffs(passing) - 1;
+    if (tid == m) s_pass = m;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    const int m = s_pass;
+    const double tau = s_suffix[m] / double(kD - m);
     const double sg = sqrt(fmax(tau, 0.0));
     sc->m = m;
     sc->tau = tau;
@@ -693,7 +683,7 @@ cudaError_t launch_ne_moments(int n, int bits, int dtype, const GraphBufs& gb, c
 
 cudaError_t launch_ne_finalize(int dtype, const double* f64_partials, int nblocks, DevScalars* sc,
                                double* sigma_out, cudaStream_t stream) {
-  k_ne_finalize<<<1, 256, 0, stream>>>(dtype, f64_partials, nblocks, sc, sigma_out);
+  k_ne_finalize<<<1, kFinThreads, 0, stream>>>(dtype, f64_partials, nblocks, sc, sigma_out);
   return cudaGetLastError();
 }
 

@@ -1,19 +1,27 @@
 // SLG: scan-line graph construction (Section 2.2).
 //
-// 1. k_hist: scan-line codes C1..C3 (Eq. 1-3) of every point and the digit
-//    histograms of every radix pass of every code, in one read of xyz.
-// 2. one least-significant-digit pass of a stable radix sort over all three
-//    codes at once (8-bit digits, 4096-key tiles), as reduce-then-scan:
-//    k_tile_counts (digit counts per tile), k_tile_scan (each tile's start of
-//    every digit) and k_sort_scatter (stable in-tile rank, write-out in digit
-//    runs).  Ties keep input order, so equal codes are ordered by index.  The
-//    last pass writes the orders, the packed C1 code of each sorted point, and
-//    the C1/C2 rank of each input point.
-// 3. k_link: points consecutive along a code are linked (Section 2.2).  In C1
-//    order the code-1 neighbours are implicit (k-1, k+1); C2/C3 neighbours
-//    are written as slots, a pair already linked by an earlier code is left
-//    out so the union is a set, and each distinct edge's length is summed
-//    for sigma_g.
+// Sorting by a code of Eq. 1-3 is sorting by three b-bit coordinates, most
+// significant first, so a least-significant-digit radix sort whose digits are
+// the coordinates needs three passes of 2^b bins:
+//   C1 = (z, y, x): passes on x, then y, then z, from the input order;
+//   C2 = (x, z, y) and C3 = (y, x, z): stable passes over the C1 order, on z
+//        then x for C2 and on x then y for C3 (among points with equal (x, z)
+//        the C1 order already ranks them by y, and among equal (y, x) by z).
+// Ties keep input order throughout, so equal codes are ordered by index.  The
+// digit histograms of every pass are the three coordinate histograms, taken
+// once (k_coord_hist).  Each pass is reduce-then-scan:
+//   k_tile_counts   digit counts of every 4096-key tile;
+//   k_tile_scan     each tile's global start of every digit;
+//   k_sort_scatter  stable in-tile rank (one ballot per digit bit) and
+//                   write-out in digit runs.
+// The C1 passes carry (code, input index) and end with the packed C1 code of
+// every sorted point, its input index and the rank of every input point; the
+// C2/C3 passes carry (code, sorted id) and end with the sorted ids along C2
+// and C3 and the C2 rank of every sorted id.
+// k_link: points consecutive along a code are linked.  In C1 order the code-1
+// neighbours are implicit (k-1, k+1); C2/C3 neighbours are written as slots;
+// a pair already linked by an earlier code is left out so the union is a set,
+// and each distinct edge's length is summed for sigma_g.
 #include <algorithm>
 
 #include "fgbd_internal.cuh"
@@ -21,283 +29,288 @@
 namespace fgbd {
 namespace {
 
+constexpr int kWarps = kSortThreads / 32;
+constexpr int kDigitsPerThread = kMaxRadix / kSortThreads;  // 4
 
-
-// exclusive scan of one value per thread over a 256-thread block
-__device__ __forceinline__ uint32_t block_exclusive_scan_256(uint32_t v, uint32_t* s_warp) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  uint32_t x = v;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-    if (lane >= o) x += y;
-  }
-  if (lane == 31) s_warp[warp] = x;
-  __syncthreads();
-  uint32_t off = 0;
-#pragma unroll
-  for (int w = 0; w < 8; ++w) off += (w < warp) ? s_warp[w] : 0u;
-  __syncthreads();
-  return off + x - v;
+size_t scatter_smem_bytes() {
+  return sizeof(uint32_t) * (size_t(kWarps) * kMaxRadix + 2 * size_t(kSortTile) + 2 * size_t(kMaxRadix) + kWarps + 1);
 }
 
-__global__ void __launch_bounds__(256) k_hist(const int32_t* __restrict__ xyz, int n, int bits,
-                                              int passes, uint32_t* __restrict__ zero_buf,
-                                              size_t zero_words, DevScalars* __restrict__ sc) {
-  __shared__ uint32_t h[3][kMaxPasses][kRadix];
-  uint32_t* hf = &h[0][0][0];
-  for (int i = threadIdx.x; i < 3 * kMaxPasses * kRadix; i += blockDim.x) hf[i] = 0;
-  const size_t gtid = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  const size_t gstride = size_t(gridDim.x) * blockDim.x;
-  for (size_t i = gtid; i < zero_words; i += gstride) zero_buf[i] = 0;
+__global__ void __launch_bounds__(256) k_coord_hist(const int32_t* __restrict__ xyz, int n, int bits,
+                                                    DevScalars* __restrict__ sc) {
+  __shared__ uint32_t h[3][kMaxRadix];
+  const int radix = 1 << bits;
+  for (int i = threadIdx.x; i < 3 * kMaxRadix; i += blockDim.x) (&h[0][0])[i] = 0;
   __syncthreads();
-  const uint32_t m = (1u << bits) - 1u;
+  const uint32_t m = uint32_t(radix) - 1u;
   bool bad = false;
-  for (size_t i = gtid; i < size_t(n); i += gstride) {
+  const size_t gstride = size_t(gridDim.x) * blockDim.x;
+  for (size_t i = size_t(blockIdx.x) * blockDim.x + threadIdx.x; i < size_t(n); i += gstride) {
     const int xi = xyz[3 * i], yi = xyz[3 * i + 1], zi = xyz[3 * i + 2];
     bad |= (uint32_t(xi) > m) | (uint32_t(yi) > m) | (uint32_t(zi) > m);
-    const uint32_t x = uint32_t(xi) & m, y = uint32_t(yi) & m, z = uint32_t(zi) & m;
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      const uint32_t key = code_of(c, x, y, z, bits);
-      for (int p = 0; p < passes; ++p) atomicAdd(&h[c][p][(key >> (kRadixBits * p)) & (kRadix - 1)], 1u);
-    }
+    atomicAdd(&h[0][uint32_t(xi) & m], 1u);
+    atomicAdd(&h[1][uint32_t(yi) & m], 1u);
+    atomicAdd(&h[2][uint32_t(zi) & m], 1u);
   }
   if (bad) atomicOr(&sc->status, kFlagRange);
   __syncthreads();
-  for (int i = threadIdx.x; i < 3 * kMaxPasses * kRadix; i += blockDim.x) {
-    const uint32_t v = hf[i];
-    if (v) atomicAdd(&sc->hist[0][0][0] + i, v);
-  }
+  for (int c = 0; c < 3; ++c)
+    for (int d = threadIdx.x; d < radix; d += blockDim.x)
+      if (h[c][d]) atomicAdd(&sc->chist[c][d], h[c][d]);
 }
 
-// The keys of tile t of code c at this pass (striped: item j of lane l of warp
-// w is position t*kSortTile + w*32*kSortKpt + j*32 + l, so loads coalesce).
-template <bool FIRST>
-__device__ __forceinline__ void load_tile(const int32_t* __restrict__ xyz, const uint32_t* __restrict__ keys_in,
-                                          const uint32_t* __restrict__ vals_in, int n, int bits, size_t coff,
-                                          int code, int warp_base, int lane, uint32_t (&key)[kSortKpt],
-                                          uint32_t (&val)[kSortKpt], bool with_vals) {
-  const uint32_t m = (1u << bits) - 1u;
+// The keys and values of tile t of code slot c (striped: item j of lane l of
+// warp w is position t*kSortTile + w*32*kSortKpt + j*32 + l, so loads coalesce).
+__device__ __forceinline__ void load_tile(const SortPassArgs& a, int slot, int warp_base, int lane,
+                                          uint32_t (&key)[kSortKpt], uint32_t (&val)[kSortKpt], bool with_vals) {
+  const uint32_t m = (1u << a.bits) - 1u;
+  const size_t off = size_t(slot) * size_t(a.cap);
 #pragma unroll
   for (int j = 0; j < kSortKpt; ++j) {
     const int pos = warp_base + j * 32 + lane;
     key[j] = 0;
     val[j] = 0;
-    if (pos < n) {
-      if (FIRST) {
-        const uint32_t x = uint32_t(xyz[3 * size_t(pos)]) & m;
-        const uint32_t y = uint32_t(xyz[3 * size_t(pos) + 1]) & m;
-        const uint32_t z = uint32_t(xyz[3 * size_t(pos) + 2]) & m;
-        key[j] = code_of(code, x, y, z, bits);
+    if (pos < a.n) {
+      if (a.xyz) {
+        const uint32_t x = uint32_t(a.xyz[3 * size_t(pos)]) & m;
+        const uint32_t y = uint32_t(a.xyz[3 * size_t(pos) + 1]) & m;
+        const uint32_t z = uint32_t(a.xyz[3 * size_t(pos) + 2]) & m;
+        key[j] = code_of(0, x, y, z, a.bits);
         val[j] = uint32_t(pos);
       } else {
-        key[j] = keys_in[coff + pos];
-        if (with_vals) val[j] = vals_in[coff + pos];
+        key[j] = a.keys_in[slot][(a.keys_in_shared ? 0 : off) + pos];
+        if (with_vals) val[j] = a.vals_in[slot] ? a.vals_in[slot][off + pos] : uint32_t(pos);
       }
     }
   }
 }
 
-// Reduce: digit counts of every tile, counts[(code*kRadix + digit)*tiles + tile].
-template <bool FIRST>
-__global__ void __launch_bounds__(kSortThreads)
-    k_tile_counts(const int32_t* __restrict__ xyz, int n, int bits, int cap, int pass, int tiles,
-                  const uint32_t* __restrict__ keys_in, uint32_t* __restrict__ counts) {
-  __shared__ uint32_t s_h[kRadix];
+// Reduce: digit counts of every tile, counts[(slot*radix + digit)*tiles + tile].
+__global__ void __launch_bounds__(kSortThreads) k_tile_counts(SortPassArgs a) {
+  __shared__ uint32_t s_h[kMaxRadix];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int code = blockIdx.x / tiles;
-  const int t = blockIdx.x - code * tiles;
-  s_h[tid] = 0;
+  const int radix = 1 << a.bits;
+  const int slot = blockIdx.x / a.tiles;
+  const int t = blockIdx.x - slot * a.tiles;
+  for (int d = tid; d < radix; d += kSortThreads) s_h[d] = 0;
   __syncthreads();
   uint32_t key[kSortKpt], val[kSortKpt];
-  load_tile<FIRST>(xyz, keys_in, nullptr, n, bits, size_t(code) * size_t(cap), code,
-                   t * kSortTile + warp * (32 * kSortKpt), lane, key, val, false);
-  const int shift = kRadixBits * pass;
+  const int warp_base = t * kSortTile + warp * (32 * kSortKpt);
+  load_tile(a, slot, warp_base, lane, key, val, false);
+  const int shift = a.shift[slot];
+  const uint32_t m = uint32_t(radix) - 1u;
 #pragma unroll
   for (int j = 0; j < kSortKpt; ++j)
-    if (t * kSortTile + warp * (32 * kSortKpt) + j * 32 + lane < n) atomicAdd(&s_h[(key[j] >> shift) & (kRadix - 1)], 1u);
+    if (warp_base + j * 32 + lane < a.n) atomicAdd(&s_h[(key[j] >> shift) & m], 1u);
   __syncthreads();
-  counts[(size_t(code) * kRadix + tid) * tiles + t] = s_h[tid];
+  for (int d = tid; d < radix; d += kSortThreads) a.counts[(size_t(slot) * radix + d) * a.tiles + t] = s_h[d];
 }
 
-// Scan: one warp per (code, digit) row.  offsets[row][t] = start of the
-// digit's bucket (sum of the smaller digits' totals) + counts of tiles < t.
-__global__ void __launch_bounds__(256) k_tile_scan(int tiles, int pass, const DevScalars* __restrict__ sc,
-                                                   uint32_t* __restrict__ counts) {
+// Scan: one warp per (slot, digit) row.  counts become offsets: the start of
+// the digit's bucket (total of the smaller digits) plus the counts of the
+// earlier tiles.  Each lane owns a run of up to 8 consecutive tiles per batch.
+__global__ void __launch_bounds__(256) k_tile_scan(SortPassArgs a) {
   const int lane = threadIdx.x & 31;
+  const int radix = 1 << a.bits;
   const int row = blockIdx.x * 8 + (threadIdx.x >> 5);
-  if (row >= 3 * kRadix) return;
-  const int code = row / kRadix, d = row - code * kRadix;
+  if (row >= a.ncodes * radix) return;
+  const int slot = row / radix, d = row - slot * radix;
+  // the digit's bucket start: lane l sums the histogram entries 32l..32l+31
+  // below d, read as eight independent 16-byte loads
+  const uint4* hist4 = reinterpret_cast<const uint4*>(a.sc->chist[a.coord[slot]]);
   uint32_t base = 0;
-  for (int e = lane; e < d; e += 32) base += sc->hist[code][pass][e];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const int e = lane * 32 + i * 4;
+    if (e < d) {
+      const uint4 h = hist4[e >> 2];
+      base += h.x + (e + 1 < d ? h.y : 0u) + (e + 2 < d ? h.z : 0u) + (e + 3 < d ? h.w : 0u);
+    }
+  }
   base = warp_sum(base);
-  uint32_t* r = counts + size_t(row) * tiles;
-  for (int t0 = 0; t0 < tiles; t0 += 32) {
-    const int t = t0 + lane;
-    const uint32_t c = t < tiles ? r[t] : 0u;
-    uint32_t x = c;
+  uint32_t* r = a.counts + size_t(row) * a.tiles;
+  constexpr int kRun = 8;
+  for (int t0 = 0; t0 < a.tiles; t0 += 32 * kRun) {
+    uint32_t c[kRun];
+    uint32_t own = 0;
+#pragma unroll
+    for (int i = 0; i < kRun; ++i) {
+      const int t = t0 + lane * kRun + i;
+      c[i] = t < a.tiles ? r[t] : 0u;
+      own += c[i];
+    }
+    uint32_t x = own;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
       const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
       if (lane >= o) x += y;
     }
-    if (t < tiles) r[t] = base + x - c;
+    uint32_t run = base + x - own;
+#pragma unroll
+    for (int i = 0; i < kRun; ++i) {
+      const int t = t0 + lane * kRun + i;
+      if (t < a.tiles) r[t] = run;
+      run += c[i];
+    }
     base += __shfl_sync(0xffffffffu, x, 31);
   }
 }
 
 // Scatter: rank each key of the tile among equal digits (stable), then write
-// the tile out in digit runs at the offsets the scan produced.  The last pass
-// writes the orders, the packed C1 codes and the C1/C2 ranks instead.
-template <bool FIRST, bool LAST>
-__global__ void __launch_bounds__(kSortThreads, 3)
-    k_sort_scatter(const int32_t* __restrict__ xyz, int n, int bits, int cap, int pass, int tiles,
-                   const uint32_t* __restrict__ keys_in, const uint32_t* __restrict__ vals_in,
-                   uint32_t* __restrict__ keys_out, uint32_t* __restrict__ vals_out,
-                   const uint32_t* __restrict__ offsets, int32_t* __restrict__ perm, uint32_t* __restrict__ pk,
-                   int32_t* __restrict__ rank1, int32_t* __restrict__ rank2) {
-  constexpr int kWarps = kSortThreads / 32;
-  static_assert(kSortThreads == kRadix, "one thread per digit");
-  __shared__ uint32_t s_whist[kWarps][kRadix];
-  __shared__ uint32_t s_keys[kSortTile];
-  __shared__ uint32_t s_vals[kSortTile];
-  __shared__ uint32_t s_tstart[kRadix];
-  __shared__ uint32_t s_gbase[kRadix];
-  __shared__ uint32_t s_warp[kWarps];
-  __shared__ uint32_t s_count;
+// the tile out in digit runs at the offsets the scan produced.
+__global__ void __launch_bounds__(kSortThreads, 3) k_sort_scatter(SortPassArgs a) {
+  extern __shared__ uint32_t smem[];
+  uint32_t* s_whist = smem;                         // [kWarps][radix]
+  uint32_t* s_keys = s_whist + kWarps * kMaxRadix;  // [kSortTile]
+  uint32_t* s_vals = s_keys + kSortTile;            // [kSortTile]
+  uint32_t* s_tstart = s_vals + kSortTile;          // [radix]
+  uint32_t* s_gbase = s_tstart + kMaxRadix;         // [radix]
+  uint32_t* s_warp = s_gbase + kMaxRadix;           // [kWarps]
+  uint32_t* s_count = s_warp + kWarps;
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int shift = kRadixBits * pass;
-  for (int i = tid; i < kWarps * kRadix; i += kSortThreads) (&s_whist[0][0])[i] = 0;
-  const int code = blockIdx.x / tiles;
-  const int t = blockIdx.x - code * tiles;
+  const int bits = a.bits, radix = 1 << bits;
+  const uint32_t m = uint32_t(radix) - 1u;
+  const int slot = blockIdx.x / a.tiles;
+  const int t = blockIdx.x - slot * a.tiles;
+  const int shift = a.shift[slot];
   const int warp_base = t * kSortTile + warp * (32 * kSortKpt);
-  const size_t coff = size_t(code) * size_t(cap);
+  for (int i = tid; i < kWarps * radix; i += kSortThreads) s_whist[i] = 0;
   // this tile's global start of every digit, known before any key is ranked
-  const uint32_t gbase = offsets[(size_t(code) * kRadix + tid) * tiles + t];
+  for (int d = tid; d < radix; d += kSortThreads) s_gbase[d] = a.counts[(size_t(slot) * radix + d) * a.tiles + t];
 
   uint32_t key[kSortKpt], val[kSortKpt], rnk[kSortKpt];
-  load_tile<FIRST>(xyz, keys_in, vals_in, n, bits, coff, code, warp_base, lane, key, val, true);
+  load_tile(a, slot, warp_base, lane, key, val, true);
   __syncthreads();
 
   // stable rank of each key among equal digits of its warp, in input order:
   // the lanes with the same digit are found with one ballot per digit bit; the
   // lowest of them adds the group size to the warp's digit counter and the
-  // count it returns is the group's base
+  // count it gets back is the group's base
+  uint32_t* wh = s_whist + warp * radix;
   const uint32_t lt = (1u << lane) - 1u;
 #pragma unroll
   for (int j = 0; j < kSortKpt; ++j) {
-    const bool valid = (warp_base + j * 32 + lane) < n;
-    const uint32_t d = (key[j] >> shift) & (kRadix - 1);
+    const bool valid = (warp_base + j * 32 + lane) < a.n;
+    const uint32_t d = (key[j] >> shift) & m;
     uint32_t peers = __ballot_sync(0xffffffffu, valid);
-#pragma unroll
-    for (int b = 0; b < kRadixBits; ++b) {
+    for (int b = 0; b < bits; ++b) {
       const bool bit = (d >> b) & 1u;
       const uint32_t on = __ballot_sync(0xffffffffu, bit);
       peers &= bit ? on : ~on;
     }
     const int leader = peers ? __ffs(peers) - 1 : lane;
     uint32_t old = 0;
-    if (valid && lane == leader) old = atomicAdd(&s_whist[warp][d], uint32_t(__popc(peers)));
+    if (valid && lane == leader) old = atomicAdd(&wh[d], uint32_t(__popc(peers)));
     rnk[j] = __shfl_sync(0xffffffffu, old, leader) + __popc(peers & lt);
     __syncwarp();
   }
   __syncthreads();
 
-  // per digit: offsets of the warps and the tile total
-  const int d = tid;
-  uint32_t total = 0;
+  // per digit (each thread owns kDigitsPerThread consecutive digits): offsets
+  // of the warps, the tile total, and the tile's exclusive digit start
+  uint32_t tot[kDigitsPerThread];
+  uint32_t own = 0;
 #pragma unroll
-  for (int w = 0; w < kWarps; ++w) {
-    const uint32_t c = s_whist[w][d];
-    s_whist[w][d] = total;
-    total += c;
+  for (int i = 0; i < kDigitsPerThread; ++i) {
+    const int d = tid * kDigitsPerThread + i;
+    uint32_t run = 0;
+    if (d < radix) {
+      for (int w = 0; w < kWarps; ++w) {
+        const uint32_t c = s_whist[w * radix + d];
+        s_whist[w * radix + d] = run;
+        run += c;
+      }
+    }
+    tot[i] = run;
+    own += run;
   }
-  const uint32_t tstart = block_exclusive_scan_256(total, s_warp);
-  s_tstart[d] = tstart;
-  s_gbase[d] = gbase;
-  if (d == kRadix - 1) s_count = tstart + total;
+  {
+    uint32_t x = own;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) s_warp[warp] = x;
+    __syncthreads();
+    uint32_t off = 0;
+#pragma unroll
+    for (int w = 0; w < kWarps; ++w) off += (w < warp) ? s_warp[w] : 0u;
+    uint32_t start = off + x - own;
+#pragma unroll
+    for (int i = 0; i < kDigitsPerThread; ++i) {
+      const int d = tid * kDigitsPerThread + i;
+      if (d < radix) s_tstart[d] = start;
+      start += tot[i];
+    }
+    if (tid == kSortThreads - 1) *s_count = start;
+  }
   __syncthreads();
 
   // local sort of the tile by digit, then write out in digit runs
 #pragma unroll
   for (int j = 0; j < kSortKpt; ++j) {
-    if ((warp_base + j * 32 + lane) < n) {
-      const uint32_t dj = (key[j] >> shift) & (kRadix - 1);
-      const uint32_t lp = s_tstart[dj] + s_whist[warp][dj] + rnk[j];
+    if ((warp_base + j * 32 + lane) < a.n) {
+      const uint32_t dj = (key[j] >> shift) & m;
+      const uint32_t lp = s_tstart[dj] + wh[dj] + rnk[j];
       s_keys[lp] = key[j];
       s_vals[lp] = val[j];
     }
   }
   __syncthreads();
-  const uint32_t cnt = s_count;
+  const uint32_t cnt = *s_count;
+  const size_t off = size_t(slot) * size_t(a.cap);
+  uint32_t* ko = a.keys_out[slot];
+  uint32_t* vo = a.vals_out[slot];
+  int32_t* ro = a.rank_out[slot];
   for (uint32_t i = tid; i < cnt; i += kSortThreads) {
     const uint32_t k = s_keys[i], v = s_vals[i];
-    const uint32_t dk = (k >> shift) & (kRadix - 1);
+    const uint32_t dk = (k >> shift) & m;
     const uint32_t g = s_gbase[dk] + (i - s_tstart[dk]);
-    if (g >= uint32_t(n) || v >= uint32_t(n)) continue;
-    if (!LAST) {
-      keys_out[coff + g] = k;
-      vals_out[coff + g] = v;
-    } else {
-      perm[coff + g] = int32_t(v);
-      if (code == 0) {
-        pk[g] = k;
-        rank1[v] = int32_t(g);
-      } else if (code == 1) {
-        rank2[v] = int32_t(g);
-      }
-    }
+    if (g >= uint32_t(a.n) || v >= uint32_t(a.n)) continue;
+    if (ko) ko[off + g] = k;
+    if (vo) vo[off + g] = v;
+    if (ro) ro[v] = int32_t(g);
   }
 }
 
-// One thread per position r of one code's order (blockIdx.y = code).  Each
-// thread resolves its own point only (input index, sorted id, C2 rank and
-// packed code); the values at positions r-1 and r+1 come from the adjacent
-// lanes, with one extra lookup at each end of the warp.
+// One thread per position r of one code's order (blockIdx.y = code).  Code 0
+// is the C1 order itself; codes 1 and 2 read the sorted ids along C2 and C3.
+// The ids at r-1 and r+1 come from the adjacent lanes, with one extra lookup
+// at each end of the warp.
 struct LinkPt {
   int k;       // sorted (C1) id, -1 outside [0, n)
   int r2;      // position in the C2 order (code 2 only)
   uint32_t c;  // packed C1 code
 };
 
-__device__ __forceinline__ LinkPt link_point(int r, int n, int code, const int32_t* __restrict__ pc,
-                                             const int32_t* __restrict__ rank1, const int32_t* __restrict__ rank2,
-                                             const uint32_t* __restrict__ pk) {
+__device__ __forceinline__ LinkPt link_point(int r, int n, int code, const int32_t* __restrict__ ord,
+                                             const int32_t* __restrict__ rank2, const uint32_t* __restrict__ pk) {
   LinkPt q{-1, -1, 0u};
   if (r < 0 || r >= n) return q;
-  if (code == 0) {
-    q.k = r;
-    q.c = pk[r];
-    return q;
-  }
-  const int i = pc[r];
-  if (!in_range(i, n)) return q;
-  const int k = rank1[i];
+  const int k = code == 0 ? r : ord[r];
   if (!in_range(k, n)) return q;
   q.k = k;
   q.c = pk[k];
-  if (code == 2) q.r2 = rank2[i];
+  if (code == 2) q.r2 = rank2[k];
   return q;
 }
 
-__global__ void __launch_bounds__(256) k_link(int n, int bits, int cap, const int32_t* __restrict__ perm,
-                                              const int32_t* __restrict__ rank1,
-                                              const int32_t* __restrict__ rank2,
-                                              const uint32_t* __restrict__ pk, int4* __restrict__ c4,
-                                              DevScalars* __restrict__ sc) {
+__global__ void __launch_bounds__(256) k_link(int n, int bits, int cap, const int32_t* __restrict__ ord23,
+                                              const int32_t* __restrict__ rank2, const uint32_t* __restrict__ pk,
+                                              int4* __restrict__ c4, DevScalars* __restrict__ sc) {
   __shared__ unsigned long long s_red[8];
   const int code = blockIdx.y;
   const int lane = threadIdx.x & 31;
-  const int32_t* pc = perm + size_t(code) * size_t(cap);
+  const int32_t* ord = code == 0 ? nullptr : ord23 + size_t(code - 1) * size_t(cap);
   unsigned long long edges = 0;
   float dist_f = 0.f;  // this thread's few edge lengths; converted to fixed point once
   const int stride = gridDim.x * blockDim.x;
   // whole warps step together so the shuffles see every lane
   for (int base = blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < n; base += stride) {
     const int r = base + lane;
-    const LinkPt me = link_point(r, n, code, pc, rank1, rank2, pk);
+    const LinkPt me = link_point(r, n, code, ord, rank2, pk);
     LinkPt prev, next;
     prev.k = __shfl_up_sync(0xffffffffu, me.k, 1);
     prev.r2 = __shfl_up_sync(0xffffffffu, me.r2, 1);
@@ -305,8 +318,8 @@ __global__ void __launch_bounds__(256) k_link(int n, int bits, int cap, const in
     next.k = __shfl_down_sync(0xffffffffu, me.k, 1);
     next.r2 = __shfl_down_sync(0xffffffffu, me.r2, 1);
     next.c = __shfl_down_sync(0xffffffffu, me.c, 1);
-    if (lane == 0) prev = link_point(r - 1, n, code, pc, rank1, rank2, pk);
-    if (lane == 31) next = link_point(r + 1, n, code, pc, rank1, rank2, pk);
+    if (lane == 0) prev = link_point(r - 1, n, code, ord, rank2, pk);
+    if (lane == 31) next = link_point(r + 1, n, code, ord, rank2, pk);
     if (me.k < 0) continue;
     // the edge to the next position: counted once, unless an earlier code links the pair
     bool dup_next = true;
@@ -336,46 +349,125 @@ __global__ void __launch_bounds__(256) k_link(int n, int bits, int cap, const in
   }
 }
 
+// The three orders in input indices: C1 from perm1, C2 and C3 through perm1.
+__global__ void __launch_bounds__(256) k_orders_export(int n, int cap, const int32_t* __restrict__ perm1,
+                                                       const int32_t* __restrict__ ord23, int32_t* __restrict__ out) {
+  const int stride = gridDim.x * blockDim.x;
+  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += stride) {
+    out[r] = perm1[r];
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      const int k = ord23[size_t(c) * size_t(cap) + r];
+      out[size_t(c + 1) * size_t(n) + r] = in_range(k, n) ? perm1[k] : -1;
+    }
+  }
+}
+
 }  // namespace
 
-cudaError_t launch_hist(const int32_t* xyz, int n, int bits, int passes, uint32_t* zero_buf,
-                        size_t zero_words, DevScalars* sc, int num_sms, cudaStream_t stream) {
-  const size_t work = std::max<size_t>(size_t(n), zero_words);
-  int grid = int(std::min<size_t>((work + 2047) / 2048, size_t(num_sms) * 4));
-  grid = std::max(grid, 1);
-  k_hist<<<grid, 256, 0, stream>>>(xyz, n, bits, passes, zero_buf, zero_words, sc);
+cudaError_t launch_coord_hist(const int32_t* xyz, int n, int bits, DevScalars* sc, int num_sms, cudaStream_t stream) {
+  if (n <= 0) return cudaSuccess;
+  const int grid = std::max(1, std::min((n + 2047) / 2048, num_sms * 4));
+  k_coord_hist<<<grid, 256, 0, stream>>>(xyz, n, bits, sc);
   return cudaGetLastError();
 }
 
-cudaError_t launch_sort_pass(int pass, int passes, const int32_t* xyz, int n, int bits, int cap,
-                             const SortBufs& sb, const GraphBufs& gb, DevScalars* sc,
-                             cudaStream_t stream) {
-  const bool first = pass == 0, last = pass == passes - 1;
-  const uint32_t* kin = first ? nullptr : sb.keys[(pass - 1) & 1];
-  const uint32_t* vin = first ? nullptr : sb.vals[(pass - 1) & 1];
-  uint32_t* kout = sb.keys[pass & 1];
-  uint32_t* vout = sb.vals[pass & 1];
-  uint32_t* counts = sb.tile_counts + size_t(pass) * 3 * size_t(sb.tiles) * kRadix;
-  const dim3 grid(3 * sb.tiles);
-  if (first) k_tile_counts<true><<<grid, kSortThreads, 0, stream>>>(xyz, n, bits, cap, pass, sb.tiles, kin, counts);
-  else k_tile_counts<false><<<grid, kSortThreads, 0, stream>>>(xyz, n, bits, cap, pass, sb.tiles, kin, counts);
-  k_tile_scan<<<(3 * kRadix + 7) / 8, 256, 0, stream>>>(sb.tiles, pass, sc, counts);
-#define FGBD_SCATTER(F, L)                                                                              \
-  k_sort_scatter<F, L><<<grid, kSortThreads, 0, stream>>>(xyz, n, bits, cap, pass, sb.tiles, kin, vin, kout, vout, \
-                                                          counts, gb.perm, gb.pk, gb.rank1, gb.rank2)
-  if (first && last) FGBD_SCATTER(true, true);
-  else if (first) FGBD_SCATTER(true, false);
-  else if (last) FGBD_SCATTER(false, true);
-  else FGBD_SCATTER(false, false);
-#undef FGBD_SCATTER
+cudaError_t launch_tile_counts(const SortPassArgs& a, cudaStream_t stream) {
+  k_tile_counts<<<dim3(a.ncodes * a.tiles), kSortThreads, 0, stream>>>(a);
   return cudaGetLastError();
+}
+
+cudaError_t launch_tile_scan(const SortPassArgs& a, cudaStream_t stream) {
+  k_tile_scan<<<(a.ncodes * (1 << a.bits) + 7) / 8, 256, 0, stream>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sort_scatter(const SortPassArgs& a, cudaStream_t stream) {
+  // the shared-memory limit is a per-device function attribute: set it once per device
+  static unsigned long long configured = 0;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const unsigned long long bit = 1ull << (dev & 63);
+  if (!(configured & bit)) {
+    e = cudaFuncSetAttribute(k_sort_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, int(scatter_smem_bytes()));
+    if (e != cudaSuccess) return e;
+    configured |= bit;
+  }
+  k_sort_scatter<<<dim3(a.ncodes * a.tiles), kSortThreads, scatter_smem_bytes(), stream>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sort_pass(const SortPassArgs& a, cudaStream_t stream) {
+  cudaError_t e = launch_tile_counts(a, stream);
+  if (e == cudaSuccess) e = launch_tile_scan(a, stream);
+  if (e == cudaSuccess) e = launch_sort_scatter(a, stream);
+  return e;
 }
 
 cudaError_t launch_link(int n, int bits, int cap, const GraphBufs& gb, DevScalars* sc, int num_sms,
                         cudaStream_t stream) {
+  if (n <= 0) return cudaSuccess;
   const int gx = std::max(1, std::min((n + 255) / 256, num_sms * 8));
-  k_link<<<dim3(gx, 3), 256, 0, stream>>>(n, bits, cap, gb.perm, gb.rank1, gb.rank2, gb.pk, gb.c4, sc);
+  k_link<<<dim3(gx, 3), 256, 0, stream>>>(n, bits, cap, gb.ord23, gb.rank2, gb.pk, gb.c4, sc);
   return cudaGetLastError();
+}
+
+cudaError_t launch_orders_export(int n, int cap, const GraphBufs& gb, int32_t* out, cudaStream_t stream) {
+  if (n <= 0) return cudaSuccess;
+  const int grid = std::max(1, std::min((n + 255) / 256, 152 * 16));
+  k_orders_export<<<grid, 256, 0, stream>>>(n, cap, gb.perm1, gb.ord23, out);
+  return cudaGetLastError();
+}
+
+SortPassArgs slg_pass_args(int pass, const int32_t* xyz, int n, int bits, int cap, const SortBufs& sb,
+                           const GraphBufs& gb, const DevScalars* sc) {
+  SortPassArgs a{};
+  a.n = n;
+  a.bits = bits;
+  a.cap = cap;
+  a.tiles = (n + kSortTile - 1) / kSortTile;
+  a.counts = sb.tile_counts;
+  a.sc = sc;
+  if (pass < 3) {
+    // C1: digits x, y, z; keys are packed C1 codes (x lowest), values input indices
+    const int p = pass;
+    a.ncodes = 1;
+    a.shift[0] = p * bits;
+    a.coord[0] = p;
+    a.xyz = p == 0 ? xyz : nullptr;
+    a.keys_in[0] = p == 0 ? nullptr : sb.keys[(p - 1) & 1];
+    a.vals_in[0] = p == 0 ? nullptr : sb.vals[(p - 1) & 1];
+    const bool last = p == 2;
+    a.keys_out[0] = last ? gb.pk : sb.keys[p & 1];
+    a.vals_out[0] = last ? reinterpret_cast<uint32_t*>(gb.perm1) : sb.vals[p & 1];
+    a.rank_out[0] = last ? gb.rank1 : nullptr;
+    return a;
+  }
+  // C2 (slot 0): z then x; C3 (slot 1): x then y; both over the C1 order
+  // with the sorted id as value
+  const int p = pass - 3;
+  a.ncodes = 2;
+  a.shift[0] = p == 0 ? 2 * bits : 0;
+  a.coord[0] = p == 0 ? 2 : 0;
+  a.shift[1] = p == 0 ? 0 : bits;
+  a.coord[1] = p == 0 ? 0 : 1;
+  if (p == 0) {
+    a.keys_in[0] = a.keys_in[1] = gb.pk;
+    a.keys_in_shared = 1;
+    a.vals_in[0] = a.vals_in[1] = nullptr;  // value = position = sorted id
+  } else {
+    a.keys_in[0] = a.keys_in[1] = sb.keys[0];
+    a.vals_in[0] = a.vals_in[1] = sb.vals[0];
+  }
+  const bool last = p == 1;
+  for (int s = 0; s < 2; ++s) {
+    a.keys_out[s] = last ? nullptr : sb.keys[0];
+    a.vals_out[s] = last ? reinterpret_cast<uint32_t*>(gb.ord23) : sb.vals[0];
+  }
+  a.rank_out[0] = last ? gb.rank2 : nullptr;
+  a.rank_out[1] = nullptr;
+  return a;
 }
 
 }  // namespace fgbd

@@ -6,7 +6,7 @@
 // all device memory, or services on a GPU with a fixed memory budget.  This
 // entry point runs the same histogram and radix-sort kernels as
 // fgbd_build_graph, but its scratch (key/value ping-pong buffers, per-tile
-// digit counts, digit histograms, ranks) lives in one file-scope device array of
+// digit counts, coordinate histograms, orders, ranks) lives in one file-scope device array of
 // fixed size, reserved on every GPU that loads the library until the process
 // exits.  The caller passes the coordinates and the output buffer.
 #include <mutex>
@@ -26,13 +26,15 @@ constexpr size_t align256(size_t v) { return (v + 255) / 256 * 256; }
 // byte offsets inside the scratch array
 constexpr size_t kOffScalars = 0;
 constexpr size_t kOffKeys0 = align256(kOffScalars + sizeof(DevScalars));
-constexpr size_t kOffKeys1 = align256(kOffKeys0 + 3 * kMaxPts * 4);
-constexpr size_t kOffVals0 = align256(kOffKeys1 + 3 * kMaxPts * 4);
-constexpr size_t kOffVals1 = align256(kOffVals0 + 3 * kMaxPts * 4);
-constexpr size_t kOffTileCounts = align256(kOffVals1 + 3 * kMaxPts * 4);
-constexpr size_t kOffPk = align256(kOffTileCounts + size_t(kMaxPasses) * 3 * kMaxTiles * kRadix * 4);
-constexpr size_t kOffRank1 = align256(kOffPk + kMaxPts * 4);
-constexpr size_t kOffRank2 = align256(kOffRank1 + kMaxPts * 4);
+constexpr size_t kOffKeys1 = align256(kOffKeys0 + 2 * kMaxPts * 4);
+constexpr size_t kOffVals0 = align256(kOffKeys1 + 2 * kMaxPts * 4);
+constexpr size_t kOffVals1 = align256(kOffVals0 + 2 * kMaxPts * 4);
+constexpr size_t kOffTileCounts = align256(kOffVals1 + 2 * kMaxPts * 4);
+constexpr size_t kOffPerm1 = align256(kOffTileCounts + 2 * size_t(kMaxRadix) * kMaxTiles * 4);
+constexpr size_t kOffRank1 = align256(kOffPerm1 + kMaxPts * 4);
+constexpr size_t kOffPk = align256(kOffRank1 + kMaxPts * 4);
+constexpr size_t kOffOrd23 = align256(kOffPk + kMaxPts * 4);
+constexpr size_t kOffRank2 = align256(kOffOrd23 + 2 * kMaxPts * 4);
 constexpr size_t kScratchBytes = align256(kOffRank2 + kMaxPts * 4);
 
 static __device__ __align__(256) unsigned char g_static_scratch[kScratchBytes];
@@ -73,7 +75,7 @@ extern "C" fgbd_status fgbd_scan_orders_static(const int32_t* xyz, int64_t n64, 
   }
   DevScalars* sc = reinterpret_cast<DevScalars*>(base + kOffScalars);
   // the array keeps the previous call's contents: clear the status word and
-  // the digit histograms (the per-tile digit counts are rewritten by every pass)
+  // the coordinate histograms (the per-tile digit counts are rewritten by every pass)
   if (cudaMemsetAsync(sc, 0, sizeof(DevScalars), st) != cudaSuccess) {
     cudaGetLastError();
     return FGBD_ECUDA;
@@ -93,23 +95,27 @@ extern "C" fgbd_status fgbd_scan_orders_static(const int32_t* xyz, int64_t n64, 
     sb.vals[0] = reinterpret_cast<uint32_t*>(base + kOffVals0);
     sb.vals[1] = reinterpret_cast<uint32_t*>(base + kOffVals1);
     sb.tile_counts = reinterpret_cast<uint32_t*>(base + kOffTileCounts);
-    sb.passes = (3 * bits + kRadixBits - 1) / kRadixBits;
-    sb.tiles = (n + kSortTile - 1) / kSortTile;
     GraphBufs gb{};
-    gb.perm = orders;  // the last pass writes the orders straight into the caller's [3][n] array
-    gb.pk = reinterpret_cast<uint32_t*>(base + kOffPk);
+    gb.perm1 = reinterpret_cast<int32_t*>(base + kOffPerm1);
     gb.rank1 = reinterpret_cast<int32_t*>(base + kOffRank1);
+    gb.pk = reinterpret_cast<uint32_t*>(base + kOffPk);
+    gb.ord23 = reinterpret_cast<int32_t*>(base + kOffOrd23);
     gb.rank2 = reinterpret_cast<int32_t*>(base + kOffRank2);
-    if (launch_hist(xyz, n, bits, sb.passes, sb.tile_counts, 0, sc, num_sms, st) != cudaSuccess) {
+    if (launch_coord_hist(xyz, n, bits, sc, num_sms, st) != cudaSuccess) {
       cudaGetLastError();
       return FGBD_ECUDA;
     }
-    for (int p = 0; p < sb.passes; ++p) {
-      // cap = n: the three codes' rows of every buffer are n apart, like the caller's output
-      if (launch_sort_pass(p, sb.passes, xyz, n, bits, n, sb, gb, sc, st) != cudaSuccess) {
+    // cap = n: the code slots of every buffer are n apart
+    for (int p = 0; p < kSlgPasses; ++p) {
+      if (launch_sort_pass(slg_pass_args(p, xyz, n, bits, n, sb, gb, sc), st) != cudaSuccess) {
         cudaGetLastError();
         return FGBD_ECUDA;
       }
+    }
+    // the three orders in input indices, written into the caller's [3][n] array
+    if (launch_orders_export(n, n, gb, orders, st) != cudaSuccess) {
+      cudaGetLastError();
+      return FGBD_ECUDA;
     }
   }
   if (status && cudaMemcpyAsync(status, &sc->status, sizeof(uint32_t), cudaMemcpyDeviceToDevice, st) != cudaSuccess) {
