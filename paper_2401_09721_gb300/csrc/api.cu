@@ -303,11 +303,11 @@ fgbd_status fgbd_ctx_create(int64_t capacity, const fgbd_params* params, fgbd_ct
   void* vals1 = nullptr;
   const Item items[] = {
       {reinterpret_cast<void**>(&ctx->sc), sizeof(DevScalars)},
-      {&keys0, 2 * C * 4},
-      {&keys1, 2 * C * 4},
-      {&vals0, 2 * C * 4},
-      {&vals1, 2 * C * 4},
-      {reinterpret_cast<void**>(&ctx->sb.tile_counts), size_t(2) * kMaxRadix * tiles * 4},
+      {&keys0, C * 4},
+      {&keys1, C * 4},
+      {&vals0, C * 4},
+      {&vals1, C * 4},
+      {reinterpret_cast<void**>(&ctx->sb.tile_counts), size_t(kMaxRadix) * tiles * 4},
       {reinterpret_cast<void**>(&ctx->gb.perm1), C * 4},
       {reinterpret_cast<void**>(&ctx->gb.rank1), C * 4},
       {reinterpret_cast<void**>(&ctx->gb.pk), C * 4},

@@ -75,9 +75,9 @@ struct DevScalars {
 
 // Sort scratch for one build.
 struct SortBufs {
-  uint32_t* keys[2];     // ping-pong [2 code slots][cap]
-  uint32_t* vals[2];     // ping-pong [2 code slots][cap]
-  uint32_t* tile_counts; // [2 code slots][kMaxRadix digits][tiles]: per-tile digit counts, then offsets
+  uint32_t* keys[2];     // ping-pong [cap]
+  uint32_t* vals[2];     // ping-pong [cap]
+  uint32_t* tile_counts; // [kMaxRadix digits][tiles]: per-tile digit counts, then offsets
 };
 
 // Graph in sorted order.
@@ -90,23 +90,19 @@ struct GraphBufs {
   int4* c4;          // [cap] C2 prev, C2 next, C3 prev, C3 next (sorted ids, -1 empty)
 };
 
-// One radix pass over one or two codes (code slots) whose digit is one
-// coordinate field of the key.
+// One stable radix pass whose digit is one coordinate field of the key.
 struct SortPassArgs {
   int n;
   int bits;
-  int cap;
-  int tiles;               // tiles per code slot
-  int ncodes;              // 1 or 2
-  int keys_in_shared;      // both slots read the same key array (no slot offset)
-  int shift[2];            // bit offset of the digit in the key
-  int coord[2];            // which coordinate histogram gives the digit totals
+  int tiles;
+  int shift;               // bit offset of the digit in the key
+  int coord;               // which coordinate histogram gives the digit totals
   const int32_t* xyz;      // if set: keys from the coordinates, values = input index
-  const uint32_t* keys_in[2];
-  const uint32_t* vals_in[2];  // null: value = position
-  uint32_t* keys_out[2];       // null: not written
-  uint32_t* vals_out[2];
-  int32_t* rank_out[2];        // rank_out[value] = output position, or null
+  const uint32_t* keys_in;
+  const uint32_t* vals_in; // null: value = position
+  uint32_t* keys_out;      // null: not written
+  uint32_t* vals_out;
+  int32_t* rank_out;       // rank_out[value] = output position, or null
   uint32_t* counts;
   const DevScalars* sc;
 };
@@ -115,7 +111,7 @@ struct SortPassArgs {
 // Every launcher enqueues on `stream` and returns the launch error.
 
 cudaError_t launch_coord_hist(const int32_t* xyz, int n, int bits, DevScalars* sc, int num_sms, cudaStream_t stream);
-// pass 0..2: C1 on x, y, z; pass 3..4: C2 and C3 over the C1 order
+// pass 0..2: C1 on x, y, z; pass 3: C2 = the C1 order on x; pass 4: C3 = the C2 order on y
 SortPassArgs slg_pass_args(int pass, const int32_t* xyz, int n, int bits, int cap, const SortBufs& sb,
                            const GraphBufs& gb, const DevScalars* sc);
 cudaError_t launch_tile_counts(const SortPassArgs& a, cudaStream_t stream);

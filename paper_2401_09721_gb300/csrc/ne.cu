@@ -419,35 +419,47 @@ __global__ void __launch_bounds__(kNeThreads)
 
 constexpr double kZeroEigRel = 1e-9;  // relative size below which an eigenvalue is zero
 constexpr int kMaxSweeps = 15;
-constexpr int kFinThreads = 448;      // 14 warps: one thread per element of the 21 x 21 matrix
+constexpr int kFinThreads = 384;      // 12 warps: V blocks, A blocks, the rotation predictor
+constexpr int kGroups = 11;           // per round: 10 rotated pairs and one resting index
+constexpr int kVThreads = kD * kGroups;                 // (row of V, group): 231
+constexpr int kAFirst = 256;                            // first thread of the A blocks
+constexpr int kABlocks = kGroups * (kGroups + 1) / 2;   // (group, group) with g <= h: 66
+constexpr int kPredFirst = 352;                         // the predictor warp
 
 // Parallel cyclic Jacobi schedule on 21 indices: in round r (0..20) index i is
 // paired with (2r - i) mod 21, and index r, which pairs with itself, rests.
 // Every pair {i, j} meets exactly once per sweep, in the round r with
-// 2r = i + j (mod 21).
+// 2r = i + j (mod 21).  Group k of round r is {r} for k = 0 and the pair
+// {(r + k) mod 21, (r - k) mod 21} for k = 1..10; the resting index r takes
+// the identity column (alpha, beta) = (1, 0) and is its own partner, so it
+// needs no special case below.
 __device__ __forceinline__ int jacobi_partner(int i, int r) {
   int p = 2 * r - i;
   if (p < 0) p += kD;
   if (p >= kD) p -= kD;
   return p;
 }
+// v mod 21 for v in [-21, 41]
+__device__ __forceinline__ int wrap21(int v) { return v < 0 ? v + kD : (v >= kD ? v - kD : v); }
+// Entry (a, b) after the rotations of round r, whose index i has column
+// co[i] = (alpha_i, beta_i) in J (alpha_i at row i, beta_i at row pa = partner):
+// sum over u in {a, pa}, v in {b, pb} of J[u][a] A[u][v] J[v][b].
+__device__ __forceinline__ float rotated_entry(const float* __restrict__ A, float2 ca, float2 cb, int a, int pa,
+                                               int b, int pb) {
+  const float row_a = fmaf(cb.x, A[a * kD + b], cb.y * A[a * kD + pb]);
+  const float row_pa = fmaf(cb.x, A[pa * kD + b], cb.y * A[pa * kD + pb]);
+  return fmaf(ca.x, row_a, ca.y * row_pa);
+}
 
-// The rotation of round r acting on index x: new row/column x = alpha * old x +
-// beta * old partner.  For the pair p < q with a_pq above the threshold the
-// angle zeroes a_pq: cos 2phi = |a_qq - a_pp| / r, r = sqrt((a_qq - a_pp)^2 +
-// 4 a_pq^2), c = sqrt((1 + cos 2phi) / 2), |s| = |a_pq| / (r c), and s takes
-// the sign of (a_qq - a_pp) a_pq (the smaller of the two angles that zero it).
-// Every thread derives the coefficients from the same three entries with the
-// same operations, so all threads agree on them bit for bit.
-__device__ __forceinline__ bool jacobi_coef(const float* __restrict__ A, int x, int px, float thr, float& alpha,
-                                            float& beta) {
-  alpha = 1.f;
-  beta = 0.f;
-  if (px == x) return false;
-  const int p = min(x, px), q = max(x, px);
-  const float apq = A[p * kD + q];
-  if (!(fabsf(apq) > thr)) return false;
-  const float tau = A[q * kD + q] - A[p * kD + p];
+// The rotation of the pair p < q that zeroes a_pq, as the columns of J for p
+// and for q: (c, -s) and (c, s).  cos 2phi = |a_qq - a_pp| / r with r =
+// sqrt((a_qq - a_pp)^2 + 4 a_pq^2), c = sqrt((1 + cos 2phi) / 2), |s| =
+// |a_pq| / (r c), and s takes the sign of (a_qq - a_pp) a_pq (the smaller of
+// the two angles that zero a_pq).  A pair with |a_pq| <= thr is not rotated.
+__device__ __forceinline__ void jacobi_rotation(float app, float aqq, float apq, float thr, float2& cp, float2& cq) {
+  cp = cq = make_float2(1.f, 0.f);
+  if (!(fabsf(apq) > thr)) return;
+  const float tau = aqq - app;
   const float two_a = 2.f * apq;
   const float rr = rsqrtf(fmaf(tau, tau, two_a * two_a));
   const float h = fmaf(0.5f * fabsf(tau), rr, 0.5f);
@@ -455,9 +467,8 @@ __device__ __forceinline__ bool jacobi_coef(const float* __restrict__ A, int x, 
   const float c = h * ic;
   float s = fabsf(apq) * rr * ic;
   if ((tau < 0.f) != (apq < 0.f)) s = -s;
-  alpha = c;
-  beta = (x == p) ? -s : s;
-  return true;
+  cp = make_float2(c, -s);
+  cq = make_float2(c, s);
 }
 
 __global__ void __launch_bounds__(kFinThreads) k_ne_finalize(int dtype, const double* __restrict__ f64_partials,
@@ -468,12 +479,11 @@ __global__ void __launch_bounds__(kFinThreads) k_ne_finalize(int dtype, const do
   __shared__ float V[kD][kD + 1];
   __shared__ float Abuf[2][kD * kD];
   __shared__ float Vbuf[2][kD * kD];
+  __shared__ float2 s_coef[2][kD];
   __shared__ double s_lam[kD];
   __shared__ double s_sorted[kD];
   __shared__ double s_num[kD][kD];
   __shared__ double V64[kD][kD + 1];
-  __shared__ double s_suffix[kD + 1];
-  __shared__ int s_pass;
 
   const int tid = threadIdx.x;
   constexpr int kP = kD * kD + kD + 1;
@@ -514,130 +524,208 @@ __global__ void __launch_bounds__(kFinThreads) k_ne_finalize(int dtype, const do
   }
   __syncthreads();
 
-  // Cyclic Jacobi in float32 over the whole block, matrix and vectors in
-  // shared memory (double-buffered), thread t < 441 owning entry (t / 21,
-  // t % 21) of A and of V.  One barrier per round: each thread derives the
-  // rotations of its row and column indices itself.  A pair is rotated only
-  // while |a_pq| > 2e-7 ||diag A|| (the float32 resolution of the matrix); the
-  // iteration ends at the first barrier where no off-diagonal entry is above
-  // that threshold, since no later round would rotate anything.
+  // Cyclic Jacobi in float32, matrix and vectors in shared memory
+  // (double-buffered), one barrier per round.  Each round applies the
+  // rotations of round r (coefficients s_coef[r & 1]) by 2x2 blocks: thread
+  // (g, h) of the A blocks computes J_g^T A[g][h] J_h for groups g <= h from
+  // the block's four entries and writes it with its mirror image, thread
+  // (i, h) of the V blocks the entries of row i in the columns of group h.
+  // In the same round the predictor warp evaluates the three entries of
+  // every pair of round r + 1 after this round's rotations and writes that
+  // round's coefficients, so no round waits for a separate coefficient
+  // step.  A pair is rotated only while |a_pq| > 2e-7 ||diag A|| (the
+  // float32 resolution of the matrix); the iteration ends at the first
+  // barrier where no off-diagonal entry is above that threshold, since no
+  // later round would rotate anything.
   {
-    const bool owner = tid < kD * kD;
-    const int ei = owner ? tid / kD : 0, ej = owner ? tid % kD : 0;
-    const int lo = min(ei, ej), hi = max(ei, ej);
-    if (owner) {
-      Abuf[0][tid] = float(S[ei][ej]);
-      Vbuf[0][tid] = ei == ej ? 1.f : 0.f;
+    for (int e = tid; e < kD * kD; e += blockDim.x) {
+      Abuf[0][e] = float(S[e / kD][e % kD]);
+      Vbuf[0][e] = (e / kD == e % kD) ? 1.f : 0.f;
     }
     float dsq = 0.f;
     for (int i = 0; i < kD; ++i) dsq = fmaf(float(S[i][i]), float(S[i][i]), dsq);
     const float thr = 2e-7f * sqrtf(dsq);
+    // roles
+    const bool v_thread = tid < kVThreads;
+    const int vi = tid / kGroups, vh = tid % kGroups;
+    const bool a_thread = tid >= kAFirst && tid < kAFirst + kABlocks;
+    int ag = 0, ah = 0;
+    if (a_thread) {
+      int b = tid - kAFirst;
+      while (b >= kGroups - ag) {
+        b -= kGroups - ag;
+        ++ag;
+      }
+      ah = ag + b;
+    }
+    const bool pred = tid >= kPredFirst && tid < kPredFirst + kGroups;
+    const int pk = tid - kPredFirst;
+    __syncthreads();
+    // coefficients of round 0 from the matrix itself
+    if (pred) {
+      if (pk == 0) {
+        s_coef[0][0] = make_float2(1.f, 0.f);
+      } else {
+        // the pair {pk, -pk mod 21} of round 0
+        const int p = min(pk, kD - pk), q = max(pk, kD - pk);
+        float2 cp, cq;
+        jacobi_rotation(Abuf[0][p * kD + p], Abuf[0][q * kD + q], Abuf[0][p * kD + q], thr, cp, cq);
+        s_coef[0][p] = cp;
+        s_coef[0][q] = cq;
+      }
+    }
+    bool off_big = false;
+    for (int e = tid; e < kD * kD; e += blockDim.x) off_big |= (e / kD != e % kD) && fabsf(Abuf[0][e]) > thr;
+    bool big = __syncthreads_or(off_big);
     int cur = 0;
-    bool big = __syncthreads_or(owner && ei != ej && fabsf(Abuf[0][tid]) > thr);
     for (int round = 0; big && round < kMaxSweeps * kD; ++round) {
       const int r = round % kD;
       const float* A = Abuf[cur];
       const float* Vc = Vbuf[cur];
-      bool off_big = false;
-      if (owner) {
-        // A' = J^T A J evaluated for (lo, hi) so that both mirror entries get the same bits
-        const int plo = jacobi_partner(lo, r), phi = jacobi_partner(hi, r);
-        float al, bl, ah, bh;
-        jacobi_coef(A, lo, plo, thr, al, bl);
-        jacobi_coef(A, hi, phi, thr, ah, bh);
-        const float row_lo = fmaf(ah, A[lo * kD + hi], bh * A[lo * kD + phi]);
-        const float row_plo = fmaf(ah, A[plo * kD + hi], bh * A[plo * kD + phi]);
-        const float a = fmaf(al, row_lo, bl * row_plo);
-        // V' = V J: column ej of row ei, with the coefficients of index ej
-        const bool j_lo = ej == lo;
-        const float aj = j_lo ? al : ah, bj = j_lo ? bl : bh;
-        const int pj = j_lo ? plo : phi;
-        Abuf[cur ^ 1][tid] = a;
-        Vbuf[cur ^ 1][tid] = fmaf(aj, Vc[ei * kD + ej], bj * Vc[ei * kD + pj]);
-        off_big = ei != ej && fabsf(a) > thr;
+      const float2* co = s_coef[round & 1];
+      float* An = Abuf[cur ^ 1];
+      float* Vn = Vbuf[cur ^ 1];
+      off_big = false;
+      if (v_thread) {
+        // row vi, columns y0, y1 of group vh (y0 == y1 == r for the resting group)
+        const int y0 = wrap21(r + vh), y1 = wrap21(r - vh);
+        const float2 c0 = co[y0], c1 = co[y1];
+        const float v0 = Vc[vi * kD + y0], v1 = Vc[vi * kD + y1];
+        Vn[vi * kD + y0] = fmaf(c0.x, v0, c0.y * v1);
+        Vn[vi * kD + y1] = fmaf(c1.x, v1, c1.y * v0);
+      } else if (a_thread) {
+        const int x0 = wrap21(r + ag), x1 = wrap21(r - ag), y0 = wrap21(r + ah), y1 = wrap21(r - ah);
+        const float2 cx0 = co[x0], cx1 = co[x1], cy0 = co[y0], cy1 = co[y1];
+        const float a00 = A[x0 * kD + y0], a01 = A[x0 * kD + y1], a10 = A[x1 * kD + y0], a11 = A[x1 * kD + y1];
+        // T = A_blk J_h, then J_g^T T; J_g = [[alpha_x0, beta_x1], [beta_x0, alpha_x1]]
+        const float t00 = fmaf(a00, cy0.x, a01 * cy0.y), t01 = fmaf(a00, cy1.y, a01 * cy1.x);
+        const float t10 = fmaf(a10, cy0.x, a11 * cy0.y), t11 = fmaf(a10, cy1.y, a11 * cy1.x);
+        const float n00 = fmaf(cx0.x, t00, cx0.y * t10), n01 = fmaf(cx0.x, t01, cx0.y * t11);
+        const float n10 = fmaf(cx1.y, t00, cx1.x * t10), n11 = fmaf(cx1.y, t01, cx1.x * t11);
+        An[x0 * kD + y0] = n00;
+        An[y0 * kD + x0] = n00;
+        An[x1 * kD + y1] = n11;
+        An[y1 * kD + x1] = n11;
+        An[x0 * kD + y1] = n01;
+        An[y1 * kD + x0] = n01;
+        off_big = (x0 != y0 && fabsf(n00) > thr) || (x1 != y1 && fabsf(n11) > thr) || (x0 != y1 && fabsf(n01) > thr);
+        if (ag != ah) {
+          // off the diagonal the fourth entry is distinct; on it, it is the mirror of n01
+          An[x1 * kD + y0] = n10;
+          An[y0 * kD + x1] = n10;
+          off_big |= x1 != y0 && fabsf(n10) > thr;
+        }
+      } else if (pred) {
+        const int rn = r + 1 == kD ? 0 : r + 1;
+        float2* cn = s_coef[(round + 1) & 1];
+        if (pk == 0) {
+          cn[rn] = make_float2(1.f, 0.f);
+        } else {
+          // the pair (p, q) of round r + 1, and the partners of p and q in round r
+          const int u = wrap21(rn + pk), w = wrap21(rn - pk);
+          const int p = min(u, w), q = max(u, w);
+          const int pp = jacobi_partner(p, r), pq = jacobi_partner(q, r);
+          const float2 cp = co[p], cq = co[q];
+          const float app = rotated_entry(A, cp, cp, p, pp, p, pp);
+          const float aqq = rotated_entry(A, cq, cq, q, pq, q, pq);
+          const float apq = rotated_entry(A, cp, cq, p, pp, q, pq);
+          float2 np, nq;
+          jacobi_rotation(app, aqq, apq, thr, np, nq);
+          cn[p] = np;
+          cn[q] = nq;
+        }
       }
       cur ^= 1;
       big = __syncthreads_or(off_big);
     }
-    if (owner) V[ei][ej] = Vbuf[cur][tid];
+    for (int e = tid; e < kD * kD; e += blockDim.x) V[e / kD][e % kD] = Vbuf[cur][e];
   }
   __syncthreads();
 
-  // float64 Rayleigh quotients of the 21 eigenvector estimates
+  // float64 Rayleigh quotients of the 21 eigenvector estimates.  float64 has a
+  // long latency here, so the sums run as three interleaved chains.
   for (int e = tid; e < kD * kD; e += blockDim.x) V64[e / kD][e % kD] = double(V[e / kD][e % kD]);
   __syncthreads();
   for (int e = tid; e < kD * kD; e += blockDim.x) {
     const int k = e / kD, r = e % kD;
-    double w = 0.0;
-#pragma unroll 7
-    for (int c = 0; c < kD; ++c) w = fma(S[r][c], V64[c][k], w);
-    s_num[k][r] = w * V64[r][k];
-  }
-  __syncthreads();
-  if (tid < kD) {
-    double num = 0.0, den = 0.0;
-    for (int r = 0; r < kD; ++r) {
-      num += s_num[tid][r];
-      den = fma(V64[r][tid], V64[r][tid], den);
+    double w0 = 0.0, w1 = 0.0, w2 = 0.0;
+#pragma unroll
+    for (int c = 0; c < kD; c += 3) {
+      w0 = fma(S[r][c], V64[c][k], w0);
+      w1 = fma(S[r][c + 1], V64[c + 1][k], w1);
+      w2 = fma(S[r][c + 2], V64[c + 2][k], w2);
     }
-    s_lam[tid] = num / den;
+    s_num[k][r] = (w0 + w1 + w2) * V64[r][k];
   }
   __syncthreads();
-  // eigenvalues below 1e-9 max(lambda_1, 1) are numerical zeros (a rank-deficient
-  // covariance); they are set to exactly 0 so the tail rule never decides on rounding noise
-  if (tid < kD) {
-    double top = s_lam[0];
-    for (int j = 1; j < kD; ++j) top = fmax(top, s_lam[j]);
-    const double l = s_lam[tid];
-    const bool zero = fabs(l) < kZeroEigRel * fmax(top, 1.0);
-    __syncwarp(0x1fffffu);
-    if (zero) s_lam[tid] = 0.0;
-  }
-  __syncthreads();
-  if (tid < kD) {
-    const double l = s_lam[tid];
-    int rank = 0;
-    for (int j = 0; j < kD; ++j) {
-      const double o = s_lam[j];
-      rank += (o > l) || (o == l && j < tid);
-    }
-    s_sorted[rank] = l;
-  }
-  __syncthreads();
-  if (tid < kD) sc->eig[tid] = s_sorted[tid];
-  // tail sums, accumulated from the smallest eigenvalue up so that a tail of
-  // exact zeros sums to exactly 0
-  if (tid == 0) {
-    s_suffix[kD] = 0.0;
-    for (int i = kD - 1; i >= 0; --i) s_suffix[i] = s_suffix[i + 1] + s_sorted[i];
-  }
-  __syncthreads();
-  // tail rule, every m tested at once: the smallest m with
-  // mean(lambda_{m+1..D}) <= median(lambda_{m+1..D}); m = D - 1 always passes
+  // the rest runs in warp 0, lane j < 21 holding eigenvalue j
   if (tid < 32) {
-    bool pass = false;
-    double mean = 0.0;
-    if (tid < kD) {
-      const int cnt = kD - tid;
-      mean = s_suffix[tid] / double(cnt);
-      const double med = (cnt & 1) ? s_sorted[tid + cnt / 2]
-                                   : 0.5 * (s_sorted[tid + cnt / 2 - 1] + s_sorted[tid + cnt / 2]);
-      pass = mean <= med;
+    constexpr unsigned kFull = 0xffffffffu;
+    const int lane = tid;
+    double lam = 0.0;
+    if (lane < kD) {
+      double n0 = 0.0, n1 = 0.0, n2 = 0.0, d0 = 0.0, d1 = 0.0, d2 = 0.0;
+#pragma unroll
+      for (int r = 0; r < kD; r += 3) {
+        n0 += s_num[lane][r];
+        n1 += s_num[lane][r + 1];
+        n2 += s_num[lane][r + 2];
+        d0 = fma(V64[r][lane], V64[r][lane], d0);
+        d1 = fma(V64[r + 1][lane], V64[r + 1][lane], d1);
+        d2 = fma(V64[r + 2][lane], V64[r + 2][lane], d2);
+      }
+      lam = (n0 + n1 + n2) / (d0 + d1 + d2);
     }
-    const unsigned passing = __ballot_sync(0xffffffffu, pass);
-    const int m = __ffs(passing) - 1;
-    if (tid == m) s_pass = m;
-  }
-  __syncthreads();
-  if (tid == 0) {
-    const int m = s_pass;
-    const double tau = s_suffix[m] / double(kD - m);
-    const double sg = sqrt(fmax(tau, 0.0));
-    sc->m = m;
-    sc->tau = tau;
-    sc->sigma_est = sg;
-    sc->ne_valid = 1;
-    if (sigma_out) *sigma_out = sg;
+    // eigenvalues below 1e-9 max(lambda_1, 1) are numerical zeros (a rank-deficient
+    // covariance); they are set to exactly 0 so the tail rule never decides on rounding noise
+    double top = lane < kD ? lam : -1.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) top = fmax(top, __shfl_xor_sync(kFull, top, o));
+    if (lane < kD && fabs(lam) < kZeroEigRel * fmax(top, 1.0)) lam = 0.0;
+    // descending order (ties by index), by counting the larger values
+    if (lane < kD) s_lam[lane] = lam;
+    __syncwarp();
+    if (lane < kD) {
+      int rank = 0;
+#pragma unroll
+      for (int j = 0; j < kD; ++j) {
+        const double o = s_lam[j];
+        rank += (o > lam) || (o == lam && j < lane);
+      }
+      s_sorted[rank] = lam;
+    }
+    __syncwarp();
+    const double sorted = lane < kD ? s_sorted[lane] : 0.0;
+    if (lane < kD) sc->eig[lane] = sorted;
+    // tail sums lambda_j + ... + lambda_21 by a suffix scan (a tail of exact
+    // zeros sums to exactly 0 in any order)
+    double suffix = sorted;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const double t = __shfl_down_sync(kFull, suffix, o);
+      if (lane + o < kD) suffix += t;
+    }
+    // tail rule, every m tested at once: the smallest m with
+    // mean(lambda_{m+1..D}) <= median(lambda_{m+1..D}), tested as
+    // sum <= median * count; m = D - 1 always passes
+    bool pass = false;
+    if (lane < kD) {
+      const int cnt = kD - lane;
+      const double med = (cnt & 1) ? s_sorted[lane + cnt / 2]
+                                   : 0.5 * (s_sorted[lane + cnt / 2 - 1] + s_sorted[lane + cnt / 2]);
+      pass = suffix <= med * double(cnt);
+    }
+    const int m = __ffs(__ballot_sync(kFull, pass)) - 1;
+    const double tail = __shfl_sync(kFull, suffix, m);
+    if (lane == 0) {
+      const double tau = tail / double(kD - m);
+      const double sg = sqrt(fmax(tau, 0.0));
+      sc->m = m;
+      sc->tau = tau;
+      sc->sigma_est = sg;
+      sc->ne_valid = 1;
+      if (sigma_out) *sigma_out = sg;
+    }
   }
 }
 

@@ -4,12 +4,13 @@
 // significant first, so a least-significant-digit radix sort whose digits are
 // the coordinates needs three passes of 2^b bins:
 //   C1 = (z, y, x): passes on x, then y, then z, from the input order;
-//   C2 = (x, z, y) and C3 = (y, x, z): stable passes over the C1 order, on z
-//        then x for C2 and on x then y for C3 (among points with equal (x, z)
-//        the C1 order already ranks them by y, and among equal (y, x) by z).
+//   C2 = (x, z, y): one stable pass on x over the C1 order (among points
+//        with equal x the C1 order already ranks them by (z, y));
+//   C3 = (y, x, z): one stable pass on y over the C2 order (among points
+//        with equal y the C2 order ranks them by (x, z)).
 // Ties keep input order throughout, so equal codes are ordered by index.  The
-// digit histograms of every pass are the three coordinate histograms, taken
-// once (k_coord_hist).  Each pass is reduce-then-scan:
+// digit totals of every pass are the three coordinate histograms, taken once
+// (k_coord_hist).  Each pass is reduce-then-scan:
 //   k_tile_counts   digit counts of every 4096-key tile;
 //   k_tile_scan     each tile's global start of every digit;
 //   k_sort_scatter  stable in-tile rank (one ballot per digit bit) and
@@ -59,12 +60,11 @@ __global__ void __launch_bounds__(256) k_coord_hist(const int32_t* __restrict__ 
       if (h[c][d]) atomicAdd(&sc->chist[c][d], h[c][d]);
 }
 
-// The keys and values of tile t of code slot c (striped: item j of lane l of
-// warp w is position t*kSortTile + w*32*kSortKpt + j*32 + l, so loads coalesce).
-__device__ __forceinline__ void load_tile(const SortPassArgs& a, int slot, int warp_base, int lane,
-                                          uint32_t (&key)[kSortKpt], uint32_t (&val)[kSortKpt], bool with_vals) {
+// The keys and values of one tile (striped: item j of lane l of warp w is
+// position t*kSortTile + w*32*kSortKpt + j*32 + l, so loads coalesce).
+__device__ __forceinline__ void load_tile(const SortPassArgs& a, int warp_base, int lane, uint32_t (&key)[kSortKpt],
+                                          uint32_t (&val)[kSortKpt], bool with_vals) {
   const uint32_t m = (1u << a.bits) - 1u;
-  const size_t off = size_t(slot) * size_t(a.cap);
 #pragma unroll
   for (int j = 0; j < kSortKpt; ++j) {
     const int pos = warp_base + j * 32 + lane;
@@ -78,46 +78,43 @@ __device__ __forceinline__ void load_tile(const SortPassArgs& a, int slot, int w
         key[j] = code_of(0, x, y, z, a.bits);
         val[j] = uint32_t(pos);
       } else {
-        key[j] = a.keys_in[slot][(a.keys_in_shared ? 0 : off) + pos];
-        if (with_vals) val[j] = a.vals_in[slot] ? a.vals_in[slot][off + pos] : uint32_t(pos);
+        key[j] = a.keys_in[pos];
+        if (with_vals) val[j] = a.vals_in ? a.vals_in[pos] : uint32_t(pos);
       }
     }
   }
 }
 
-// Reduce: digit counts of every tile, counts[(slot*radix + digit)*tiles + tile].
+// Reduce: digit counts of every tile, counts[digit * tiles + tile].
 __global__ void __launch_bounds__(kSortThreads) k_tile_counts(SortPassArgs a) {
   __shared__ uint32_t s_h[kMaxRadix];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int radix = 1 << a.bits;
-  const int slot = blockIdx.x / a.tiles;
-  const int t = blockIdx.x - slot * a.tiles;
+  const int t = blockIdx.x;
   for (int d = tid; d < radix; d += kSortThreads) s_h[d] = 0;
   __syncthreads();
   uint32_t key[kSortKpt], val[kSortKpt];
   const int warp_base = t * kSortTile + warp * (32 * kSortKpt);
-  load_tile(a, slot, warp_base, lane, key, val, false);
-  const int shift = a.shift[slot];
+  load_tile(a, warp_base, lane, key, val, false);
   const uint32_t m = uint32_t(radix) - 1u;
 #pragma unroll
   for (int j = 0; j < kSortKpt; ++j)
-    if (warp_base + j * 32 + lane < a.n) atomicAdd(&s_h[(key[j] >> shift) & m], 1u);
+    if (warp_base + j * 32 + lane < a.n) atomicAdd(&s_h[(key[j] >> a.shift) & m], 1u);
   __syncthreads();
-  for (int d = tid; d < radix; d += kSortThreads) a.counts[(size_t(slot) * radix + d) * a.tiles + t] = s_h[d];
+  for (int d = tid; d < radix; d += kSortThreads) a.counts[size_t(d) * a.tiles + t] = s_h[d];
 }
 
-// Scan: one warp per (slot, digit) row.  counts become offsets: the start of
-// the digit's bucket (total of the smaller digits) plus the counts of the
-// earlier tiles.  Each lane owns a run of up to 8 consecutive tiles per batch.
+// Scan: one warp per digit row.  counts become offsets: the start of the
+// digit's bucket (total of the smaller digits) plus the counts of the earlier
+// tiles.  Each lane owns a run of up to 8 consecutive tiles per batch.
 __global__ void __launch_bounds__(256) k_tile_scan(SortPassArgs a) {
   const int lane = threadIdx.x & 31;
   const int radix = 1 << a.bits;
-  const int row = blockIdx.x * 8 + (threadIdx.x >> 5);
-  if (row >= a.ncodes * radix) return;
-  const int slot = row / radix, d = row - slot * radix;
+  const int d = blockIdx.x * 8 + (threadIdx.x >> 5);
+  if (d >= radix) return;
   // the digit's bucket start: lane l sums the histogram entries 32l..32l+31
   // below d, read as eight independent 16-byte loads
-  const uint4* hist4 = reinterpret_cast<const uint4*>(a.sc->chist[a.coord[slot]]);
+  const uint4* hist4 = reinterpret_cast<const uint4*>(a.sc->chist[a.coord]);
   uint32_t base = 0;
 #pragma unroll
   for (int i = 0; i < 8; ++i) {
@@ -128,7 +125,7 @@ __global__ void __launch_bounds__(256) k_tile_scan(SortPassArgs a) {
     }
   }
   base = warp_sum(base);
-  uint32_t* r = a.counts + size_t(row) * a.tiles;
+  uint32_t* r = a.counts + size_t(d) * a.tiles;
   constexpr int kRun = 8;
   for (int t0 = 0; t0 < a.tiles; t0 += 32 * kRun) {
     uint32_t c[kRun];
@@ -171,16 +168,15 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_sort_scatter(SortPassArgs a
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int bits = a.bits, radix = 1 << bits;
   const uint32_t m = uint32_t(radix) - 1u;
-  const int slot = blockIdx.x / a.tiles;
-  const int t = blockIdx.x - slot * a.tiles;
-  const int shift = a.shift[slot];
+  const int t = blockIdx.x;
+  const int shift = a.shift;
   const int warp_base = t * kSortTile + warp * (32 * kSortKpt);
   for (int i = tid; i < kWarps * radix; i += kSortThreads) s_whist[i] = 0;
   // this tile's global start of every digit, known before any key is ranked
-  for (int d = tid; d < radix; d += kSortThreads) s_gbase[d] = a.counts[(size_t(slot) * radix + d) * a.tiles + t];
+  for (int d = tid; d < radix; d += kSortThreads) s_gbase[d] = a.counts[size_t(d) * a.tiles + t];
 
   uint32_t key[kSortKpt], val[kSortKpt], rnk[kSortKpt];
-  load_tile(a, slot, warp_base, lane, key, val, true);
+  load_tile(a, warp_base, lane, key, val, true);
   __syncthreads();
 
   // stable rank of each key among equal digits of its warp, in input order:
@@ -260,17 +256,16 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_sort_scatter(SortPassArgs a
   }
   __syncthreads();
   const uint32_t cnt = *s_count;
-  const size_t off = size_t(slot) * size_t(a.cap);
-  uint32_t* ko = a.keys_out[slot];
-  uint32_t* vo = a.vals_out[slot];
-  int32_t* ro = a.rank_out[slot];
+  uint32_t* ko = a.keys_out;
+  uint32_t* vo = a.vals_out;
+  int32_t* ro = a.rank_out;
   for (uint32_t i = tid; i < cnt; i += kSortThreads) {
     const uint32_t k = s_keys[i], v = s_vals[i];
     const uint32_t dk = (k >> shift) & m;
     const uint32_t g = s_gbase[dk] + (i - s_tstart[dk]);
     if (g >= uint32_t(a.n) || v >= uint32_t(a.n)) continue;
-    if (ko) ko[off + g] = k;
-    if (vo) vo[off + g] = v;
+    if (ko) ko[g] = k;
+    if (vo) vo[g] = v;
     if (ro) ro[v] = int32_t(g);
   }
 }
@@ -373,12 +368,12 @@ cudaError_t launch_coord_hist(const int32_t* xyz, int n, int bits, DevScalars* s
 }
 
 cudaError_t launch_tile_counts(const SortPassArgs& a, cudaStream_t stream) {
-  k_tile_counts<<<dim3(a.ncodes * a.tiles), kSortThreads, 0, stream>>>(a);
+  k_tile_counts<<<dim3(a.tiles), kSortThreads, 0, stream>>>(a);
   return cudaGetLastError();
 }
 
 cudaError_t launch_tile_scan(const SortPassArgs& a, cudaStream_t stream) {
-  k_tile_scan<<<(a.ncodes * (1 << a.bits) + 7) / 8, 256, 0, stream>>>(a);
+  k_tile_scan<<<((1 << a.bits) + 7) / 8, 256, 0, stream>>>(a);
   return cudaGetLastError();
 }
 
@@ -394,7 +389,7 @@ cudaError_t launch_sort_scatter(const SortPassArgs& a, cudaStream_t stream) {
     if (e != cudaSuccess) return e;
     configured |= bit;
   }
-  k_sort_scatter<<<dim3(a.ncodes * a.tiles), kSortThreads, scatter_smem_bytes(), stream>>>(a);
+  k_sort_scatter<<<dim3(a.tiles), kSortThreads, scatter_smem_bytes(), stream>>>(a);
   return cudaGetLastError();
 }
 
@@ -425,48 +420,41 @@ SortPassArgs slg_pass_args(int pass, const int32_t* xyz, int n, int bits, int ca
   SortPassArgs a{};
   a.n = n;
   a.bits = bits;
-  a.cap = cap;
   a.tiles = (n + kSortTile - 1) / kSortTile;
   a.counts = sb.tile_counts;
   a.sc = sc;
   if (pass < 3) {
     // C1: digits x, y, z; keys are packed C1 codes (x lowest), values input indices
-    const int p = pass;
-    a.ncodes = 1;
-    a.shift[0] = p * bits;
-    a.coord[0] = p;
-    a.xyz = p == 0 ? xyz : nullptr;
-    a.keys_in[0] = p == 0 ? nullptr : sb.keys[(p - 1) & 1];
-    a.vals_in[0] = p == 0 ? nullptr : sb.vals[(p - 1) & 1];
-    const bool last = p == 2;
-    a.keys_out[0] = last ? gb.pk : sb.keys[p & 1];
-    a.vals_out[0] = last ? reinterpret_cast<uint32_t*>(gb.perm1) : sb.vals[p & 1];
-    a.rank_out[0] = last ? gb.rank1 : nullptr;
+    a.shift = pass * bits;
+    a.coord = pass;
+    a.xyz = pass == 0 ? xyz : nullptr;
+    a.keys_in = pass == 0 ? nullptr : sb.keys[(pass - 1) & 1];
+    a.vals_in = pass == 0 ? nullptr : sb.vals[(pass - 1) & 1];
+    const bool last = pass == 2;
+    a.keys_out = last ? gb.pk : sb.keys[pass & 1];
+    a.vals_out = last ? reinterpret_cast<uint32_t*>(gb.perm1) : sb.vals[pass & 1];
+    a.rank_out = last ? gb.rank1 : nullptr;
     return a;
   }
-  // C2 (slot 0): z then x; C3 (slot 1): x then y; both over the C1 order
-  // with the sorted id as value
-  const int p = pass - 3;
-  a.ncodes = 2;
-  a.shift[0] = p == 0 ? 2 * bits : 0;
-  a.coord[0] = p == 0 ? 2 : 0;
-  a.shift[1] = p == 0 ? 0 : bits;
-  a.coord[1] = p == 0 ? 0 : 1;
-  if (p == 0) {
-    a.keys_in[0] = a.keys_in[1] = gb.pk;
-    a.keys_in_shared = 1;
-    a.vals_in[0] = a.vals_in[1] = nullptr;  // value = position = sorted id
-  } else {
-    a.keys_in[0] = a.keys_in[1] = sb.keys[0];
-    a.vals_in[0] = a.vals_in[1] = sb.vals[0];
+  if (pass == 3) {
+    // C2: the C1 order (value = position = sorted id) on x
+    a.shift = 0;
+    a.coord = 0;
+    a.keys_in = gb.pk;
+    a.vals_in = nullptr;
+    a.keys_out = sb.keys[0];
+    a.vals_out = reinterpret_cast<uint32_t*>(gb.ord23);
+    a.rank_out = gb.rank2;
+    return a;
   }
-  const bool last = p == 1;
-  for (int s = 0; s < 2; ++s) {
-    a.keys_out[s] = last ? nullptr : sb.keys[0];
-    a.vals_out[s] = last ? reinterpret_cast<uint32_t*>(gb.ord23) : sb.vals[0];
-  }
-  a.rank_out[0] = last ? gb.rank2 : nullptr;
-  a.rank_out[1] = nullptr;
+  // C3: the C2 order on y
+  a.shift = bits;
+  a.coord = 1;
+  a.keys_in = sb.keys[0];
+  a.vals_in = reinterpret_cast<const uint32_t*>(gb.ord23);
+  a.keys_out = nullptr;
+  a.vals_out = reinterpret_cast<uint32_t*>(gb.ord23 + size_t(cap));
+  a.rank_out = nullptr;
   return a;
 }
 

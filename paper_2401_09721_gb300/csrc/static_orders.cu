@@ -26,11 +26,11 @@ constexpr size_t align256(size_t v) { return (v + 255) / 256 * 256; }
 // byte offsets inside the scratch array
 constexpr size_t kOffScalars = 0;
 constexpr size_t kOffKeys0 = align256(kOffScalars + sizeof(DevScalars));
-constexpr size_t kOffKeys1 = align256(kOffKeys0 + 2 * kMaxPts * 4);
-constexpr size_t kOffVals0 = align256(kOffKeys1 + 2 * kMaxPts * 4);
-constexpr size_t kOffVals1 = align256(kOffVals0 + 2 * kMaxPts * 4);
-constexpr size_t kOffTileCounts = align256(kOffVals1 + 2 * kMaxPts * 4);
-constexpr size_t kOffPerm1 = align256(kOffTileCounts + 2 * size_t(kMaxRadix) * kMaxTiles * 4);
+constexpr size_t kOffKeys1 = align256(kOffKeys0 + kMaxPts * 4);
+constexpr size_t kOffVals0 = align256(kOffKeys1 + kMaxPts * 4);
+constexpr size_t kOffVals1 = align256(kOffVals0 + kMaxPts * 4);
+constexpr size_t kOffTileCounts = align256(kOffVals1 + kMaxPts * 4);
+constexpr size_t kOffPerm1 = align256(kOffTileCounts + size_t(kMaxRadix) * kMaxTiles * 4);
 constexpr size_t kOffRank1 = align256(kOffPerm1 + kMaxPts * 4);
 constexpr size_t kOffPk = align256(kOffRank1 + kMaxPts * 4);
 constexpr size_t kOffOrd23 = align256(kOffPk + kMaxPts * 4);
@@ -105,7 +105,7 @@ extern "C" fgbd_status fgbd_scan_orders_static(const int32_t* xyz, int64_t n64, 
       cudaGetLastError();
       return FGBD_ECUDA;
     }
-    // cap = n: the code slots of every buffer are n apart
+    // cap = n: the C2 and C3 orders lie n apart in the ord23 array
     for (int p = 0; p < kSlgPasses; ++p) {
       if (launch_sort_pass(slg_pass_args(p, xyz, n, bits, n, sb, gb, sc), st) != cudaSuccess) {
         cudaGetLastError();
