@@ -30,11 +30,19 @@
 namespace fgbd {
 namespace {
 
-constexpr int kWarps = kSortThreads / 32;
-constexpr int kDigitsPerThread = kMaxRadix / kSortThreads;  // 4
+// The scatter runs 512 threads on a 4096-key tile (8 keys a thread), twice
+// the threads of the counting pass, so that the per-block serial chains
+// (ranking, write-out) are half as long.  Two warps share one 32-bit digit
+// counter word (16 bits each: a warp ranks at most 256 keys).
+constexpr int kScatterThreads = 512;
+constexpr int kScatterWarps = kScatterThreads / 32;         // 16
+constexpr int kScatterKpt = kSortTile / kScatterThreads;     // 8
+constexpr int kPairWords = kScatterWarps / 2;               // counter words per digit
+constexpr int kDigitsPerThread = kMaxRadix / kScatterThreads;  // 2
 
 size_t scatter_smem_bytes() {
-  return sizeof(uint32_t) * (size_t(kWarps) * kMaxRadix + 2 * size_t(kSortTile) + 2 * size_t(kMaxRadix) + kWarps + 1);
+  return sizeof(uint32_t) *
+         (size_t(kPairWords) * kMaxRadix + 2 * size_t(kSortTile) + 2 * size_t(kMaxRadix) + kScatterWarps + 1);
 }
 
 __global__ void __launch_bounds__(256) k_coord_hist(const int32_t* __restrict__ xyz, int n, int bits,
@@ -155,38 +163,57 @@ __global__ void __launch_bounds__(256) k_tile_scan(SortPassArgs a) {
 
 // Scatter: rank each key of the tile among equal digits (stable), then write
 // the tile out in digit runs at the offsets the scan produced.
-__global__ void __launch_bounds__(kSortThreads, 3) k_sort_scatter(SortPassArgs a) {
+__global__ void __launch_bounds__(kScatterThreads, 2) k_sort_scatter(SortPassArgs a) {
   extern __shared__ uint32_t smem[];
-  uint32_t* s_whist = smem;                         // [kWarps][radix]
-  uint32_t* s_keys = s_whist + kWarps * kMaxRadix;  // [kSortTile]
-  uint32_t* s_vals = s_keys + kSortTile;            // [kSortTile]
-  uint32_t* s_tstart = s_vals + kSortTile;          // [radix]
-  uint32_t* s_gbase = s_tstart + kMaxRadix;         // [radix]
-  uint32_t* s_warp = s_gbase + kMaxRadix;           // [kWarps]
-  uint32_t* s_count = s_warp + kWarps;
+  uint32_t* s_whist = smem;                             // [kPairWords][radix]: warps 2w, 2w+1 in the low, high half
+  uint32_t* s_keys = s_whist + kPairWords * kMaxRadix;  // [kSortTile]
+  uint32_t* s_vals = s_keys + kSortTile;                // [kSortTile]
+  uint32_t* s_tstart = s_vals + kSortTile;              // [radix]
+  uint32_t* s_gbase = s_tstart + kMaxRadix;             // [radix]
+  uint32_t* s_warp = s_gbase + kMaxRadix;               // [kScatterWarps]
+  uint32_t* s_count = s_warp + kScatterWarps;
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int bits = a.bits, radix = 1 << bits;
   const uint32_t m = uint32_t(radix) - 1u;
   const int t = blockIdx.x;
   const int shift = a.shift;
-  const int warp_base = t * kSortTile + warp * (32 * kSortKpt);
-  for (int i = tid; i < kWarps * radix; i += kSortThreads) s_whist[i] = 0;
+  const int warp_base = t * kSortTile + warp * (32 * kScatterKpt);
+  for (int i = tid; i < kPairWords * radix; i += kScatterThreads) s_whist[i] = 0;
   // this tile's global start of every digit, known before any key is ranked
-  for (int d = tid; d < radix; d += kSortThreads) s_gbase[d] = a.counts[size_t(d) * a.tiles + t];
+  for (int d = tid; d < radix; d += kScatterThreads) s_gbase[d] = a.counts[size_t(d) * a.tiles + t];
 
-  uint32_t key[kSortKpt], val[kSortKpt], rnk[kSortKpt];
-  load_tile(a, warp_base, lane, key, val, true);
+  // the keys and values of this warp's 256 positions (striped, so loads coalesce)
+  uint32_t key[kScatterKpt], val[kScatterKpt], rnk[kScatterKpt];
+#pragma unroll
+  for (int j = 0; j < kScatterKpt; ++j) {
+    const int pos = warp_base + j * 32 + lane;
+    key[j] = 0;
+    val[j] = 0;
+    if (pos < a.n) {
+      if (a.xyz) {
+        const uint32_t x = uint32_t(a.xyz[3 * size_t(pos)]) & m;
+        const uint32_t y = uint32_t(a.xyz[3 * size_t(pos) + 1]) & m;
+        const uint32_t z = uint32_t(a.xyz[3 * size_t(pos) + 2]) & m;
+        key[j] = code_of(0, x, y, z, bits);
+        val[j] = uint32_t(pos);
+      } else {
+        key[j] = a.keys_in[pos];
+        val[j] = a.vals_in ? a.vals_in[pos] : uint32_t(pos);
+      }
+    }
+  }
   __syncthreads();
 
   // stable rank of each key among equal digits of its warp, in input order:
   // the lanes with the same digit are found with one ballot per digit bit; the
   // lowest of them adds the group size to the warp's digit counter and the
   // count it gets back is the group's base
-  uint32_t* wh = s_whist + warp * radix;
+  uint32_t* wh = s_whist + (warp >> 1) * radix;
+  const int half = 16 * (warp & 1);
   const uint32_t lt = (1u << lane) - 1u;
 #pragma unroll
-  for (int j = 0; j < kSortKpt; ++j) {
+  for (int j = 0; j < kScatterKpt; ++j) {
     const bool valid = (warp_base + j * 32 + lane) < a.n;
     const uint32_t d = (key[j] >> shift) & m;
     uint32_t peers = __ballot_sync(0xffffffffu, valid);
@@ -197,7 +224,7 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_sort_scatter(SortPassArgs a
     }
     const int leader = peers ? __ffs(peers) - 1 : lane;
     uint32_t old = 0;
-    if (valid && lane == leader) old = atomicAdd(&wh[d], uint32_t(__popc(peers)));
+    if (valid && lane == leader) old = (atomicAdd(&wh[d], uint32_t(__popc(peers)) << half) >> half) & 0xffffu;
     rnk[j] = __shfl_sync(0xffffffffu, old, leader) + __popc(peers & lt);
     __syncwarp();
   }
@@ -212,10 +239,12 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_sort_scatter(SortPassArgs a
     const int d = tid * kDigitsPerThread + i;
     uint32_t run = 0;
     if (d < radix) {
-      for (int w = 0; w < kWarps; ++w) {
+#pragma unroll
+      for (int w = 0; w < kPairWords; ++w) {
         const uint32_t c = s_whist[w * radix + d];
-        s_whist[w * radix + d] = run;
-        run += c;
+        const uint32_t lo = c & 0xffffu, hi = c >> 16;
+        s_whist[w * radix + d] = run | ((run + lo) << 16);
+        run += lo + hi;
       }
     }
     tot[i] = run;
@@ -232,7 +261,7 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_sort_scatter(SortPassArgs a
     __syncthreads();
     uint32_t off = 0;
 #pragma unroll
-    for (int w = 0; w < kWarps; ++w) off += (w < warp) ? s_warp[w] : 0u;
+    for (int w = 0; w < kScatterWarps; ++w) off += (w < warp) ? s_warp[w] : 0u;
     uint32_t start = off + x - own;
 #pragma unroll
     for (int i = 0; i < kDigitsPerThread; ++i) {
@@ -240,16 +269,16 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_sort_scatter(SortPassArgs a
       if (d < radix) s_tstart[d] = start;
       start += tot[i];
     }
-    if (tid == kSortThreads - 1) *s_count = start;
+    if (tid == kScatterThreads - 1) *s_count = start;
   }
   __syncthreads();
 
   // local sort of the tile by digit, then write out in digit runs
 #pragma unroll
-  for (int j = 0; j < kSortKpt; ++j) {
+  for (int j = 0; j < kScatterKpt; ++j) {
     if ((warp_base + j * 32 + lane) < a.n) {
       const uint32_t dj = (key[j] >> shift) & m;
-      const uint32_t lp = s_tstart[dj] + wh[dj] + rnk[j];
+      const uint32_t lp = s_tstart[dj] + ((wh[dj] >> half) & 0xffffu) + rnk[j];
       s_keys[lp] = key[j];
       s_vals[lp] = val[j];
     }
@@ -259,7 +288,7 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_sort_scatter(SortPassArgs a
   uint32_t* ko = a.keys_out;
   uint32_t* vo = a.vals_out;
   int32_t* ro = a.rank_out;
-  for (uint32_t i = tid; i < cnt; i += kSortThreads) {
+  for (uint32_t i = tid; i < cnt; i += kScatterThreads) {
     const uint32_t k = s_keys[i], v = s_vals[i];
     const uint32_t dk = (k >> shift) & m;
     const uint32_t g = s_gbase[dk] + (i - s_tstart[dk]);
@@ -389,7 +418,7 @@ cudaError_t launch_sort_scatter(const SortPassArgs& a, cudaStream_t stream) {
     if (e != cudaSuccess) return e;
     configured |= bit;
   }
-  k_sort_scatter<<<dim3(a.tiles), kSortThreads, scatter_smem_bytes(), stream>>>(a);
+  k_sort_scatter<<<dim3(a.tiles), kScatterThreads, scatter_smem_bytes(), stream>>>(a);
   return cudaGetLastError();
 }
 
