@@ -212,7 +212,7 @@ fgbd_status fgbd_get_timings(fgbd_ctx* ctx, int32_t max, int32_t* count_host, ch
  *           point along code l+1.
  *   status: optional device uint32 receiving 0, or the OR of 1 (a coordinate
  *           out of range) and 2 (a bounded device wait gave up); NULL to skip.
- * Scratch: one file-scope device array of about 2 MiB (FGBD_STATIC_MAX_POINTS
+ * Scratch: one file-scope device array of about 1.3 MiB (FGBD_STATIC_MAX_POINTS
  * points) reserved on every GPU that loads the library until the process
  * exits.  The call allocates and frees nothing.  The first call on a device
  * looks up the array's device address (cudaGetSymbolAddress) with that device
