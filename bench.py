@@ -362,6 +362,28 @@ def run_fgbd(args):
     e2e = {"value": world * n * args.steps / e2e_s / 1e6, "unit": "Mpoints/s",
            "h2d_bytes_per_step": int(pin_x.numel() * 4 + pin_c[0].numel()), "d2h_bytes_per_step": int(pin_o.numel())}
 
+    # ---- ablations of Tables 4 and 5 on the same frames (device-timed like the main steps)
+    ablations = {}
+    for name, variant in (("no_fslr", fgbd.VARIANT_NO_FSLR), ("unsorted_patch", fgbd.VARIANT_UNSORTED_PATCH)):
+        vctx = fgbd.Context(n, bits=BITS, variant=variant)
+        for k in range(3):
+            vctx.run(x, cols[k % len(cols)], out=out)
+        ms, sig, qv = [], [], []
+        for k in range(len(cols)):
+            flush.zero_()
+            a0 = torch.cuda.Event(enable_timing=True)
+            a1 = torch.cuda.Event(enable_timing=True)
+            a0.record(stream)
+            vctx.run(x, cols[k], out=out)
+            a1.record(stream)
+            vst = vctx.stats()
+            ms.append(a0.elapsed_time(a1))
+            sig.append(vst["sigma_est"])
+            qv.append(vst["q"])
+        vctx.close()
+        ablations[name] = {"ms_per_step": float(np.mean(ms)), "value": n / (float(np.mean(ms)) / 1e3) / 1e6,
+                           "unit": "Mpoints/s", "sigma_est": [round(v, 4) for v in sig], "q": qv}
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         times = time_oracle(xyz, [noisy[2]])
@@ -380,6 +402,7 @@ def run_fgbd(args):
             "kernels": {k: {"ms": round(v["ms"], 5), "per_step": v["launches_per_step"],
                             "gbs": None if v["gbs"] is None else round(v["gbs"], 1)} for k, v in kernels.items()},
             "q_mean": q_mean, "wall_s": wall, "step_ms_min": min(step_ms), "step_ms_max": max(step_ms),
+            "ablations": ablations,
         }
         print(json.dumps(line), flush=True)
     ctx.close()

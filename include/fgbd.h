@@ -56,8 +56,19 @@ typedef struct fgbd_params {
   int32_t window;       /* points linked on each side along a scan line; the paper uses 1 (only 1 is implemented) */
   double fslr_factor;   /* FSLR skips points whose mean patch std exceeds factor * sigma_est (paper: 2) */
   int32_t q_max;        /* largest filter power searched, 0..FGBD_Q_CAP (the paper states none; default 64) */
-  int32_t reserved[7];  /* must be zero */
+  int32_t variant;      /* OR of FGBD_VARIANT_* ablation switches; 0 is the method as published */
+  int32_t reserved[6];  /* must be zero */
 } fgbd_params;
+
+/* Ablation switches of Section 3 (Tables 4 and 5), for comparison runs only.
+ *   FGBD_VARIANT_NO_FSLR: "FGBD w/o FSLR" (Table 5): Eq. 6 is evaluated over
+ *     every point; the limited region of Section 2.4 is not applied.
+ *   FGBD_VARIANT_UNSORTED_PATCH: "NE-GBP w/o sort" (Table 4): the neighbours of
+ *     a patch are not ordered by distance (Section 2.3) but taken in the order
+ *     the scan-line graph links them: previous and next along C1, then along C2,
+ *     then along C3. */
+#define FGBD_VARIANT_NO_FSLR 1
+#define FGBD_VARIANT_UNSORTED_PATCH 2
 
 typedef struct fgbd_stats {
   int64_t n;                                /* points of the last graph */

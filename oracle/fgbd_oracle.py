@@ -57,6 +57,9 @@ class Params:
     window: int = 1          # linked positions on each side along a scan line (Section 2.2: 1)
     fslr_factor: float = 2.0  # points with mean patch std > factor * sigma_est are skipped (Section 2.4)
     q_max: int = 64          # largest filter power searched (the paper gives none; a reading)
+    # ablations of Section 3 (Tables 4 and 5); the defaults are the method as published
+    fslr: bool = True             # False: "FGBD w/o FSLR", Eq. 6 over every point
+    sorted_patches: bool = True   # False: "NE-GBP w/o sort", patch entries in link order
 
 
 # --------------------------------------------------------------------------
@@ -189,7 +192,27 @@ def random_walk_weights(g: np.ndarray, row_ptr: np.ndarray, col: np.ndarray, sg:
 # Step 2: NE-GBP (Section 2.3)
 # --------------------------------------------------------------------------
 
-def patch_vectors(g: np.ndarray, f: np.ndarray, row_ptr: np.ndarray, col: np.ndarray, k: int):
+def link_order_neighbours(orders: np.ndarray, idx: np.ndarray) -> np.ndarray:
+    """The neighbours of points idx in the order the scan-line graph links them.
+
+    For each code l = 1, 2, 3 (window 1): the point before and the point after
+    along the order of C_l.  Returns int64 [len(idx), 6].  Used by the "NE-GBP
+    w/o sort" ablation (Section 3 (4), Table 4), whose patch entries are not
+    ordered by distance; reading: "not sorted" is this link order.
+    """
+    n = orders.shape[1]
+    out = np.empty((idx.size, 6), dtype=np.int64)
+    for l in range(3):
+        pos = np.empty(n, dtype=np.int64)
+        pos[orders[l]] = np.arange(n)
+        p = pos[idx]
+        out[:, 2 * l] = orders[l][np.clip(p - 1, 0, n - 1)]
+        out[:, 2 * l + 1] = orders[l][np.clip(p + 1, 0, n - 1)]
+    return out
+
+
+def patch_vectors(g: np.ndarray, f: np.ndarray, row_ptr: np.ndarray, col: np.ndarray, k: int,
+                  orders: np.ndarray | None = None):
     """Section 2.3: graph-based patches a_i, entries ordered by distance from the query point.
 
     a_i = [f_i, f_{n1}, ..., f_{nk}] with the neighbours in increasing distance.
@@ -198,6 +221,8 @@ def patch_vectors(g: np.ndarray, f: np.ndarray, row_ptr: np.ndarray, col: np.nda
     fewer (the ends of the scan orders, pairs linked by two codes) are left out.
     Reading: equal distances are ordered by the offset g_j - g_i compared as
     (dz, dy, dx) ascending, then by neighbour index.
+    With ``orders`` given (window 1 only), the neighbours are not sorted but
+    taken in link order (``link_order_neighbours``): the "w/o sort" ablation.
     Returns (A float64 [N', D], idx int64 [N']): the patches and their point indices.
     """
     g = np.asarray(g, dtype=np.int64)
@@ -206,6 +231,10 @@ def patch_vectors(g: np.ndarray, f: np.ndarray, row_ptr: np.ndarray, col: np.nda
     idx = np.nonzero(deg == k)[0]
     if idx.size == 0:
         return np.zeros((0, 3 * (k + 1))), idx
+    if orders is not None:
+        assert k == 6, "link order is defined for window 1"
+        members = np.concatenate([idx[:, None], link_order_neighbours(orders, idx)], axis=1)
+        return f[members].reshape(idx.size, 3 * (k + 1)), idx
     nb = col[row_ptr[idx][:, None] + np.arange(k)[None, :]]          # [N', k]
     off = g[nb] - g[idx][:, None, :]                                  # [N', k, 3]
     d2 = (off * off).sum(axis=2)
@@ -266,13 +295,14 @@ def tail_rule(lam: np.ndarray):
     raise AssertionError("unreachable: a single value is its own median")
 
 
-def estimate_noise(g, f, row_ptr, col, k: int = 6):
+def estimate_noise(g, f, row_ptr, col, k: int = 6, orders: np.ndarray | None = None):
     """NE-GBP (Section 2.3): patches -> covariance -> eigenvalues -> sigma_est.
 
     With no complete patch the estimate is 0 (reading: nothing to estimate from).
+    ``orders`` selects the unsorted (link-order) patches of the ablation.
     Returns a dict with sigma_est, tau, m, eigenvalues, n_patches, covariance.
     """
-    A, idx = patch_vectors(g, f, row_ptr, col, k)
+    A, idx = patch_vectors(g, f, row_ptr, col, k, orders)
     D = 3 * (k + 1)
     if A.shape[0] == 0:
         return dict(sigma_est=0.0, tau=0.0, m=0, eigenvalues=np.zeros(D), n_patches=0,
@@ -412,9 +442,13 @@ def fgbd(g: np.ndarray, f: np.ndarray, params: Params = Params(), q: int | None 
     sg = sigma_g(g, row_ptr, col)
     w = edge_weights(g, row_ptr, col, sg)
     rw = random_walk_weights(g, row_ptr, col, sg)
-    noise = estimate_noise(g, f, row_ptr, col, k=6 * params.window)
+    noise = estimate_noise(g, f, row_ptr, col, k=6 * params.window,
+                           orders=None if params.sorted_patches else orders)
     spread = fslr_spread(f, row_ptr, col)
-    keep = fslr_keep(spread, noise["sigma_est"], params.fslr_factor)
+    if params.fslr:
+        keep = fslr_keep(spread, noise["sigma_est"], params.fslr_factor)
+    else:
+        keep = np.ones(n, dtype=bool)   # "FGBD w/o FSLR": Eq. 6 over every point
     if q is None:
         qs, out, J = select_q(f, row_ptr, col, rw, keep, noise["sigma_est"], params.q_max)
     else:

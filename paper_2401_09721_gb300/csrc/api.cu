@@ -111,6 +111,7 @@ bool params_ok(const fgbd_params& p) {
   if (p.window < 1) return false;
   if (!(p.fslr_factor > 0.0) || p.fslr_factor > 1e30) return false;
   if (p.q_max < 0 || p.q_max > kQCap) return false;
+  if (p.variant & ~(FGBD_VARIANT_NO_FSLR | FGBD_VARIANT_UNSORTED_PATCH)) return false;
   for (int r : p.reserved)
     if (r != 0) return false;
   return true;
@@ -148,6 +149,7 @@ FilterArgs filter_args(fgbd_ctx* ctx, int mode, int q_fixed, const double* sigma
   a.q_fixed = q_fixed;
   a.q_max = ctx->params.q_max;
   a.fslr_factor = ctx->params.fslr_factor;
+  a.all_points = (ctx->params.variant & FGBD_VARIANT_NO_FSLR) != 0;
   a.sigma_src = sigma_src ? sigma_src : &ctx->sc->sigma_est;
   a.y8 = ctx->y8;
   a.yf = ctx->yf;
@@ -215,7 +217,8 @@ fgbd_status do_estimate(fgbd_ctx* ctx, const void* rgb, int32_t dtype, double* s
     nblocks = ne_moment_blocks(n, ctx->num_sms);
     FGBD_LAUNCH(ctx, "ne_moments", st,
                 launch_ne_moments(n, ctx->params.bits, dtype, ctx->gb, ctx->y8, ctx->yf, ctx->spread, ctx->f64part,
-                                  ctx->sc, ctx->num_sms, true, st));
+                                  ctx->sc, ctx->num_sms, true,
+                                  (ctx->params.variant & FGBD_VARIANT_UNSORTED_PATCH) == 0, st));
   }
   FGBD_LAUNCH(ctx, "ne_finalize", st, launch_ne_finalize(dtype, ctx->f64part, nblocks, ctx->sc, sigma_out, st));
   ctx->has_noise = true;

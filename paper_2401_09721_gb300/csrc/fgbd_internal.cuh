@@ -126,7 +126,8 @@ cudaError_t launch_gather_colors(const void* rgb, int dtype, int n, const int32_
                                  uint32_t* y8, float4* yf, cudaStream_t stream);
 cudaError_t launch_ne_moments(int n, int bits, int dtype, const GraphBufs& gb, const uint32_t* y8,
                               const float4* yf, float* spread, double* f64_partials,
-                              DevScalars* sc, int num_sms, bool moments, cudaStream_t stream);
+                              DevScalars* sc, int num_sms, bool moments, bool sorted_patches,
+                              cudaStream_t stream);
 cudaError_t launch_ne_finalize(int dtype, const double* f64_partials, int nblocks,
                                DevScalars* sc, double* sigma_out, cudaStream_t stream);
 int ne_moment_blocks(int n, int num_sms);
@@ -139,6 +140,7 @@ struct FilterArgs {
   int q_fixed;           // mode 1
   int q_max;             // mode 0
   double fslr_factor;
+  int all_points;        // Eq. 6 over every point (the limited region is off)
   const double* sigma_src;  // sigma_est to use (device)
   const uint32_t* y8;
   const float4* yf;

@@ -141,7 +141,7 @@ __global__ void __launch_bounds__(kFilterThreads) k_filter(FilterArgs a) {
     if (select) {
       const float sp = a.spread[k];
       bool keep;
-      if (sp <= t_lo) keep = true;
+      if (a.all_points || sp <= t_lo) keep = true;
       else if (sp > t_hi) keep = false;
       else keep = !(spread_f64(a, k) > thr);
       const unsigned long long q2 = (unsigned long long)(sq_fixed(r) + sq_fixed(g) + sq_fixed(b));

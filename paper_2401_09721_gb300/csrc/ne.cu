@@ -97,7 +97,7 @@ template <int DT>
 __device__ __forceinline__ bool point_patch(int k, int n, int bits, int lane, const uint32_t* __restrict__ pk,
                                             const int4* __restrict__ c4, const uint32_t* __restrict__ y8,
                                             const float4* __restrict__ yf, float* __restrict__ spread,
-                                            bool moments, uint8_t* at8, float* atf) {
+                                            bool moments, bool sorted_patches, uint8_t* at8, float* atf) {
   int nb[6];
   bool v[6];
   nb[0] = k - 1;
@@ -201,16 +201,20 @@ __device__ __forceinline__ bool point_patch(int k, int n, int bits, int lane, co
     e[j].key = (d2 << 33) | ((unsigned long long)(dz + 1024) << 22) | ((unsigned long long)(dy + 1024) << 11) |
                (unsigned long long)(dx + 1024);
   }
-  // odd-even transposition sort, 6 rounds
+  // odd-even transposition sort, 6 rounds.  Without it (the "w/o sort"
+  // ablation) the entries stay in link order: C1 prev, C1 next, C2 prev, C2
+  // next, C3 prev, C3 next.
+  if (sorted_patches) {
 #pragma unroll
-  for (int round = 0; round < 6; ++round) {
-    if ((round & 1) == 0) {
-      cswap(e[0], e[1]);
-      cswap(e[2], e[3]);
-      cswap(e[4], e[5]);
-    } else {
-      cswap(e[1], e[2]);
-      cswap(e[3], e[4]);
+    for (int round = 0; round < 6; ++round) {
+      if ((round & 1) == 0) {
+        cswap(e[0], e[1]);
+        cswap(e[2], e[3]);
+        cswap(e[4], e[5]);
+      } else {
+        cswap(e[1], e[2]);
+        cswap(e[3], e[4]);
+      }
     }
   }
   if (DT == 0) {
@@ -253,7 +257,7 @@ __global__ void __launch_bounds__(kNeThreads)
     k_ne_moments(int n, int bits, const uint32_t* __restrict__ pk, const int4* __restrict__ c4,
                  const uint32_t* __restrict__ y8, const float4* __restrict__ yf,
                  float* __restrict__ spread, double* __restrict__ f64_partials, int moments,
-                 DevScalars* __restrict__ sc) {
+                 int sorted_patches, DevScalars* __restrict__ sc) {
   constexpr int kP = kD * kD + kD + 1;
   __shared__ __align__(16) uint32_t s_at8[DT == 0 ? kNeWarps : 1][kD * kRowWords];
   __shared__ __align__(16) float s_atf[DT == 1 ? kNeWarps : 1][kD * kRowFloats];
@@ -288,7 +292,8 @@ __global__ void __launch_bounds__(kNeThreads)
   for (int base = (blockIdx.x * kNeWarps + warp) * 32; base < n; base += nwarps * 32) {
     const int k = base + lane;
     bool has = false;
-    if (k < n) has = point_patch<DT>(k, n, bits, lane, pk, c4, y8, yf, spread, moments != 0, at8, atf);
+    if (k < n)
+      has = point_patch<DT>(k, n, bits, lane, pk, c4, y8, yf, spread, moments != 0, sorted_patches != 0, at8, atf);
     if (!moments) continue;
     if (!has) {
 #pragma unroll
@@ -757,15 +762,16 @@ int ne_moment_blocks(int n, int num_sms) {
 
 cudaError_t launch_ne_moments(int n, int bits, int dtype, const GraphBufs& gb, const uint32_t* y8,
                               const float4* yf, float* spread, double* f64_partials,
-                              DevScalars* sc, int num_sms, bool moments, cudaStream_t stream) {
+                              DevScalars* sc, int num_sms, bool moments, bool sorted_patches,
+                              cudaStream_t stream) {
   if (n <= 0) return cudaSuccess;
   const int grid = ne_moment_blocks(n, num_sms);
   if (dtype == 0)
     k_ne_moments<0><<<grid, kNeThreads, 0, stream>>>(n, bits, gb.pk, gb.c4, y8, yf, spread, f64_partials,
-                                                     moments ? 1 : 0, sc);
+                                                     moments ? 1 : 0, sorted_patches ? 1 : 0, sc);
   else
     k_ne_moments<1><<<grid, kNeThreads, 0, stream>>>(n, bits, gb.pk, gb.c4, y8, yf, spread, f64_partials,
-                                                     moments ? 1 : 0, sc);
+                                                     moments ? 1 : 0, sorted_patches ? 1 : 0, sc);
   return cudaGetLastError();
 }
 

@@ -9,6 +9,8 @@ Each function restates one definition of the paper:
                         coordinate tuples (z,y,x), (x,z,y), (y,x,z); ties by index.
 * ``neighbour_sets``    Section 2.2: consecutive points along each order are linked.
 * ``patch_covariance``  Section 2.3: Sigma = 1/N sum (a - mu)(a - mu)^T, element by element.
+* ``link_order_patches`` the "NE-GBP w/o sort" ablation (Table 4): patch entries
+                        in the order the scan lines link them.
 * ``spread``            Section 2.4: mean over channels of the population std in a patch.
 * ``filter_power``      Eq. 5: x <- x/2 + (sum_j w_ij x_j)/(2 sum_j w_ij), q times.
 """
@@ -68,6 +70,35 @@ def patches(points, colors, nb, k=6):
             return (sq_dist(points[i], points[j]), off[2], off[1], off[0], j)
 
         members = [i] + sorted(nb[i], key=key)
+        vec = []
+        for m in members:
+            vec.extend(float(colors[m][c]) for c in range(3))
+        out.append(vec)
+    return out
+
+
+def link_order_patches(points, colors, nb, k=6):
+    """Patch vectors in link order (the "w/o sort" ablation, window 1).
+
+    Members: the point, then its predecessor and successor along C1, along C2
+    and along C3, for the points with exactly k = 6 neighbours.
+    """
+    ords = orders(points)
+    pos = []
+    for order in ords:
+        p = [0] * len(points)
+        for r, i in enumerate(order):
+            p[i] = r
+        pos.append(p)
+    out = []
+    for i in range(len(points)):
+        if len(nb[i]) != k:
+            continue
+        members = [i]
+        for l in range(3):
+            r = pos[l][i]
+            members.append(ords[l][r - 1])
+            members.append(ords[l][r + 1])
         vec = []
         for m in members:
             vec.extend(float(colors[m][c]) for c in range(3))

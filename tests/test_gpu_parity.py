@@ -35,8 +35,8 @@ def F():
     return fgbd
 
 
-def gpu_frame(F, xyz, rgb, bits, q_max=64):
-    ctx = F.Context(max(len(xyz), 1), bits=bits, q_max=q_max)
+def gpu_frame(F, xyz, rgb, bits, q_max=64, variant=0):
+    ctx = F.Context(max(len(xyz), 1), bits=bits, q_max=q_max, variant=variant)
     x = torch.from_numpy(np.ascontiguousarray(xyz, dtype=np.int32)).cuda()
     c = torch.from_numpy(np.ascontiguousarray(rgb)).cuda()
     ctx.build_graph(x)
@@ -82,8 +82,11 @@ def check_noise(g, res):
     assert st["sigma_est"] == pytest.approx(nz["sigma_est"], rel=1e-5)
 
 
-def check_fslr(g, res, factor=2.0):
+def check_fslr(g, res, factor=2.0, all_points=False):
     assert np.allclose(g["spread"], res.spread, rtol=1e-5, atol=1e-5)
+    if all_points:
+        assert g["keep"].all() and res.keep.all()
+        return
     thr = factor * res.noise["sigma_est"]
     near = np.abs(res.spread - thr) <= 1e-9 * max(thr, 1e-30)
     raw = ~(res.spread > thr)
@@ -119,12 +122,15 @@ def check_u8(out8, ref):
     assert diff.max() <= 1
 
 
-def full_check(F, xyz, rgb, bits, q_max=64):
-    res = orc.fgbd(xyz, rgb, orc.Params(bits=bits, q_max=q_max))
-    ctx, g = gpu_frame(F, xyz, rgb, bits, q_max)
+def full_check(F, xyz, rgb, bits, q_max=64, variant=0):
+    no_fslr = bool(variant & F.VARIANT_NO_FSLR)
+    params = orc.Params(bits=bits, q_max=q_max, fslr=not no_fslr,
+                        sorted_patches=not (variant & F.VARIANT_UNSORTED_PATCH))
+    res = orc.fgbd(xyz, rgb, params)
+    ctx, g = gpu_frame(F, xyz, rgb, bits, q_max, variant)
     check_graph(g, res, xyz)
     check_noise(g, res)
-    check_fslr(g, res)
+    check_fslr(g, res, all_points=no_fslr)
     out = check_selection(F, ctx, g, res, rgb)
     if g["stats"]["q"] == res.q:
         check_u8(g["out8"], res.out)
@@ -153,6 +159,31 @@ def test_float_colours(F):
     clean = synth.piecewise_colors(xyz, 8, 3, as_float=True)
     noisy = synth.add_noise_f32(clean, 25.0, 3)
     full_check(F, xyz, noisy, 8)
+
+
+# ------------------------------------------------------------------ ablations (Tables 4 and 5)
+
+@pytest.mark.parametrize("variant", [1, 2, 3])
+def test_ablation_variants_dense_shell(F, variant):
+    xyz = synth.torso_points(60000, 8, 4)
+    clean = synth.piecewise_colors(xyz, 8, 4)
+    noisy = synth.add_noise_u8(clean, 30.0, 5)
+    full_check(F, xyz, noisy, 8, variant=variant)
+
+
+@pytest.mark.parametrize("n,bits,seed", [(4097, 6, 11), (12289, 10, 12)])
+def test_unsorted_patches_random_clouds(F, n, bits, seed):
+    rng = np.random.default_rng(seed)
+    xyz = rng.integers(0, 1 << bits, size=(n, 3)).astype(np.int32)
+    rgb = rng.integers(0, 256, size=(n, 3)).astype(np.uint8)
+    full_check(F, xyz, rgb, bits, variant=2)
+
+
+def test_unsorted_patches_float_colours(F):
+    xyz = synth.torso_points(30000, 8, 6)
+    clean = synth.piecewise_colors(xyz, 8, 6, as_float=True)
+    noisy = synth.add_noise_f32(clean, 20.0, 6)
+    full_check(F, xyz, noisy, 8, variant=3)
 
 
 # ------------------------------------------------------------------ ragged sizes and tiles

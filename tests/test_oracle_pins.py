@@ -271,6 +271,53 @@ def test_spread_hand_example_and_brute_force():
         assert s[i] == pytest.approx(bf.spread(colors.tolist(), nb, i), rel=1e-12, abs=1e-12)
 
 
+# ---------------------------------------------------------------- ablations (Tables 4 and 5)
+
+@pytest.mark.parametrize("seed", range(3))
+def test_unsorted_patches_brute_force(seed):
+    # "NE-GBP w/o sort": the oracle's link-order patches equal the brute-force ones,
+    # they hold the same colours per patch as the sorted ones (a permutation of the
+    # neighbour blocks), and so the mean over the six neighbour blocks of mu agrees
+    rng = np.random.default_rng(300 + seed)
+    xyz = random_cloud(rng, 80, 3, dup_frac=0.05 if seed == 2 else 0.0)
+    colors = rng.integers(0, 256, size=(80, 3))
+    pts = [tuple(int(v) for v in p) for p in xyz]
+    _, orders, _, row_ptr, col = graph_of(xyz, 3)
+    A_u, idx_u = orc.patch_vectors(xyz, colors, row_ptr, col, 6, orders=orders)
+    A_s, idx_s = orc.patch_vectors(xyz, colors, row_ptr, col, 6)
+    nb = bf.neighbour_sets(pts)
+    ref = bf.link_order_patches(pts, colors.tolist(), nb, 6)
+    assert A_u.shape[0] == len(ref) > 5 and np.array_equal(A_u, np.array(ref))
+    assert np.array_equal(idx_u, idx_s)
+    blocks_u = np.sort(A_u[:, 3:].reshape(-1, 6, 3), axis=1)
+    blocks_s = np.sort(A_s[:, 3:].reshape(-1, 6, 3), axis=1)
+    assert np.array_equal(blocks_u, blocks_s)
+    _, mu_u = orc.patch_covariance(A_u)
+    _, mu_s = orc.patch_covariance(A_s)
+    assert np.allclose(mu_u[3:].reshape(6, 3).mean(axis=0), mu_s[3:].reshape(6, 3).mean(axis=0), rtol=1e-12)
+    assert np.allclose(mu_u[:3], mu_s[:3], rtol=0, atol=0)
+
+
+def test_no_fslr_objective_brute_force():
+    # "FGBD w/o FSLR": every point enters Eq. 6; J(q) recomputed from the
+    # brute-force filter over all points with the oracle's sigma_est
+    g = np.array([(x, y, z) for x in range(12) for y in range(6) for z in range(2)], np.int32)
+    rng = np.random.default_rng(7)
+    f = np.where(g[:, 0:1] < 6, 60.0, 190.0) * np.ones((1, 3)) + rng.normal(0, 8, size=(g.shape[0], 3))
+    res = orc.fgbd(g, f, orc.Params(bits=4, fslr=False, q_max=6))
+    full = orc.fgbd(g, f, orc.Params(bits=4, q_max=6))
+    assert res.keep.all() and not full.keep.all()
+    pts = [tuple(int(v) for v in p) for p in g]
+    nb = bf.neighbour_sets(pts)
+    sg = bf.sigma_g(pts, nb)
+    s2 = res.noise["sigma_est"] ** 2
+    y = f.tolist()
+    for q in range(len(res.J)):
+        x = bf.filter_power(pts, y, nb, sg, q)
+        p = sum(y[i][c] ** 2 - x[i][c] ** 2 for i in range(len(pts)) for c in range(3))
+        assert res.J[q] == pytest.approx(abs(s2 - p / (3 * len(pts))), rel=1e-9, abs=1e-9)
+
+
 def test_fslr_keep_rule():
     s = np.array([0.0, 3.9, 4.0, 4.1])
     assert orc.fslr_keep(s, 2.0, 2.0).tolist() == [True, True, True, False]   # strict ">" excludes
