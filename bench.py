@@ -42,6 +42,7 @@ def parse():
     ap.add_argument("--impl", choices=["fgbd", "reference"], default="fgbd")
     ap.add_argument("--points", type=int, default=N_POINTS)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched-path measurement")
     return ap.parse_args()
 
 
@@ -51,6 +52,67 @@ def make_frames(n_points, seed=0):
     clean = synth.piecewise_colors(xyz, BITS, seed)
     noisy = [synth.add_noise_u8(clean, s, seed + 11 * k) for k, s in enumerate(SIGMAS)]
     return xyz, clean, noisy
+
+
+# ------------------------------------------------------------------ batched path
+
+def measure_batched(fgbd, torch, dev, stream, flush, repeats=3):
+    """16 frames of uneven size (200k..1.2M sphere points at b = 10, sigma ~ U[10, 50]):
+    the same frames through 16 sequential fgbd_run calls, one fgbd_run_batch call,
+    and that call replayed from a CUDA graph.  Device time per pass over the 16
+    frames, L2 flushed before each pass (not timed)."""
+    from paper_2401_09721_gb300 import synth
+    frames = synth.batch_frames(16)
+    ctxs = [fgbd.Context(fr.n, bits=10) for fr in frames]
+    xs = [torch.from_numpy(fr.xyz).to(dev) for fr in frames]
+    cs = [torch.from_numpy(fr.noisy).to(dev) for fr in frames]
+    outs = [torch.empty((fr.n, 3), dtype=torch.uint8, device=dev) for fr in frames]
+    total = sum(fr.n for fr in frames)
+
+    def plain():
+        for c, x, ci, co in zip(ctxs, xs, cs, outs):
+            c.run(x, ci, out=co)
+
+    def batched():
+        fgbd.Context.run_batch(ctxs, xs, cs, outs=outs)
+
+    def timed(fn):
+        for _ in range(2):
+            fn()
+        ms = []
+        for _ in range(repeats):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            torch.cuda.synchronize()
+            ms.append(a.elapsed_time(b))
+        return float(np.median(ms))
+
+    res = {"frames": len(frames), "points": total, "sizes": [fr.n for fr in frames],
+           "workload": "16 sphere frames, N ~ U[200k, 1.2M] at b=10, sigma ~ U[10, 50], seeds 1..16"}
+    res["plain_ms"] = timed(plain)
+    plain_outs = [o.clone() for o in outs]
+    res["batched_ms"] = timed(batched)
+    res["identical_to_plain"] = all(torch.equal(a, b) for a, b in zip(outs, plain_outs))
+    try:
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            batched()
+        res["graph_ms"] = timed(g.replay)
+        res["graph_identical_to_plain"] = all(torch.equal(a, b) for a, b in zip(outs, plain_outs))
+    except RuntimeError as e:  # capture refused: report why, keep the other numbers
+        res["graph_ms"] = None
+        res["graph_error"] = str(e).splitlines()[0][:200]
+    for key in ("plain", "batched", "graph"):
+        ms = res[f"{key}_ms"]
+        if ms:
+            res[f"{key}_frames_per_s"] = len(frames) / (ms / 1e3)
+            res[f"{key}_mpoints_per_s"] = total / (ms / 1e3) / 1e6
+    for c in ctxs:
+        c.close()
+    return res
 
 
 # ------------------------------------------------------------------ CPU oracle
@@ -384,6 +446,10 @@ def run_fgbd(args):
         ablations[name] = {"ms_per_step": float(np.mean(ms)), "value": n / (float(np.mean(ms)) / 1e3) / 1e6,
                            "unit": "Mpoints/s", "sigma_est": [round(v, 4) for v in sig], "q": qv}
 
+    batched = None
+    if not args.no_batch:
+        batched = measure_batched(fgbd, torch, dev, stream, flush)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         times = time_oracle(xyz, [noisy[2]])
@@ -402,7 +468,7 @@ def run_fgbd(args):
             "kernels": {k: {"ms": round(v["ms"], 5), "per_step": v["launches_per_step"],
                             "gbs": None if v["gbs"] is None else round(v["gbs"], 1)} for k, v in kernels.items()},
             "q_mean": q_mean, "wall_s": wall, "step_ms_min": min(step_ms), "step_ms_max": max(step_ms),
-            "ablations": ablations,
+            "ablations": ablations, "batched": batched,
         }
         print(json.dumps(line), flush=True)
     ctx.close()

@@ -167,6 +167,29 @@ fgbd_status fgbd_denoise(fgbd_ctx* ctx, const void* rgb_in, int32_t in_dtype, in
 fgbd_status fgbd_run(fgbd_ctx* ctx, const int32_t* xyz, int64_t n, const void* rgb_in, int32_t in_dtype,
                      void* rgb_out, int32_t out_dtype, void* stream);
 
+/* Batched path (no counterpart in the paper, which processes one frame at a
+ * time): fgbd_run on `count` frames, frame f with its own context ctxs[f],
+ * all enqueued in one call and overlapped on the GPU.  A single 1M-point frame
+ * leaves most of the GPU idle in its short, latency-bound kernels; frames run
+ * side by side fill it.
+ *   ctxs, xyz, n, rgb_in, in_dtype, rgb_out, out_dtype: host arrays of
+ *     `count` entries, the fgbd_run arguments of each frame (device buffers).
+ *   count: 0..FGBD_BATCH_MAX; the contexts must be distinct and on one device.
+ * Each context runs its frame on a stream of its own, forked from `stream`
+ * (everything earlier on `stream` finishes first) and joined back into it
+ * (later work on `stream` waits for every frame).  The selection/filter steps,
+ * cooperative launches that use the whole GPU, run one frame after another.
+ * Results, stats and errors are per context, exactly as after fgbd_run (the
+ * outputs are bit-identical).  The call contains no host synchronisation, so
+ * it can be captured into a CUDA graph once the contexts have run a frame (the
+ * first launches set kernel attributes).
+ * Errors: FGBD_EINVAL (any argument) and FGBD_ENOTIMPL (window != 1), both
+ * checked before anything is enqueued; FGBD_ECUDA. */
+#define FGBD_BATCH_MAX 64
+fgbd_status fgbd_run_batch(fgbd_ctx* const* ctxs, const int32_t* const* xyz, const int64_t* n,
+                           const void* const* rgb_in, const int32_t* in_dtype, void* const* rgb_out,
+                           const int32_t* out_dtype, int32_t count, void* stream);
+
 /* Wait for the context's work on `stream` and return any latched device error
  * (FGBD_ERANGE, FGBD_ETIMEOUT), clearing it. */
 fgbd_status fgbd_sync(fgbd_ctx* ctx, void* stream);

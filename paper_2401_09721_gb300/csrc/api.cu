@@ -44,6 +44,11 @@ struct fgbd_ctx {
   const void* noise_rgb = nullptr;
   int noise_dtype = -1;
   std::string err;
+  // batched runs: this context's own stream and the events that order it
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fork = nullptr;    // recorded on the caller's stream (first context of a batch)
+  cudaEvent_t ev_filter = nullptr;  // this frame's cooperative filter has finished
+  cudaEvent_t ev_join = nullptr;    // all of this frame's work has finished
   // instrumentation
   int64_t launches = 0;
   bool timing = false;
@@ -168,6 +173,18 @@ FilterArgs filter_args(fgbd_ctx* ctx, int mode, int q_fixed, const double* sigma
 int filter_grid_for(const fgbd_ctx* ctx, int n) {
   const int need = std::max(1, (n + kFilterThreads - 1) / kFilterThreads);
   return std::max(1, std::min(need, ctx->filter_per_sm * ctx->num_sms));
+}
+
+void release_batch_objects(fgbd_ctx* ctx) {
+  for (cudaEvent_t* e : {&ctx->ev_fork, &ctx->ev_filter, &ctx->ev_join})
+    if (*e) {
+      cudaEventDestroy(*e);
+      *e = nullptr;
+    }
+  if (ctx->side) {
+    cudaStreamDestroy(ctx->side);
+    ctx->side = nullptr;
+  }
 }
 
 fgbd_status do_build(fgbd_ctx* ctx, const int32_t* xyz, int64_t n64, cudaStream_t st) {
@@ -344,7 +361,14 @@ fgbd_status fgbd_ctx_create(int64_t capacity, const fgbd_params* params, fgbd_ct
   ctx->sb.keys[1] = static_cast<uint32_t*>(keys1);
   ctx->sb.vals[0] = static_cast<uint32_t*>(vals0);
   ctx->sb.vals[1] = static_cast<uint32_t*>(vals1);
-  if (cudaMemset(ctx->sc, 0, sizeof(DevScalars)) != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess) {
+  bool ok = cudaMemset(ctx->sc, 0, sizeof(DevScalars)) == cudaSuccess;
+  ok = ok && cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking) == cudaSuccess;
+  for (cudaEvent_t* e : {&ctx->ev_fork, &ctx->ev_filter, &ctx->ev_join})
+    ok = ok && cudaEventCreateWithFlags(e, cudaEventDisableTiming) == cudaSuccess;
+  ok = ok && cudaDeviceSynchronize() == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    release_batch_objects(ctx);
     cudaFree(ctx->mem);
     delete ctx;
     return FGBD_ECUDA;
@@ -359,6 +383,7 @@ void fgbd_ctx_destroy(fgbd_ctx* ctx) {
   cudaDeviceSynchronize();
   for (cudaEvent_t e : ctx->ev)
     if (e) cudaEventDestroy(e);
+  release_batch_objects(ctx);
   cudaFree(ctx->mem);
   delete ctx;
 }
@@ -430,6 +455,52 @@ fgbd_status fgbd_run(fgbd_ctx* ctx, const int32_t* xyz, int64_t n, const void* r
   s = do_estimate(ctx, rgb_in, in_dtype, nullptr, st);
   if (s != FGBD_OK) return s;
   return do_select(ctx, rgb_in, in_dtype, nullptr, nullptr, rgb_out, out_dtype, st);
+}
+
+fgbd_status fgbd_run_batch(fgbd_ctx* const* ctxs, const int32_t* const* xyz, const int64_t* n,
+                           const void* const* rgb_in, const int32_t* in_dtype, void* const* rgb_out,
+                           const int32_t* out_dtype, int32_t count, void* stream) {
+  if (count < 0 || count > FGBD_BATCH_MAX) return FGBD_EINVAL;
+  if (count == 0) return FGBD_OK;
+  if (!ctxs || !xyz || !n || !rgb_in || !in_dtype || !rgb_out || !out_dtype) return FGBD_EINVAL;
+  for (int f = 0; f < count; ++f) {
+    fgbd_ctx* c = ctxs[f];
+    if (!c || c->device != ctxs[0]->device) return FGBD_EINVAL;
+    for (int h = 0; h < f; ++h)
+      if (ctxs[h] == c) return FGBD_EINVAL;  // one frame per context
+    if (!dtype_ok(in_dtype[f]) || !dtype_ok(out_dtype[f])) return FGBD_EINVAL;
+    if (n[f] < 0 || n[f] > c->capacity) return FGBD_EINVAL;
+    if (n[f] > 0 && (!xyz[f] || !rgb_in[f] || !rgb_out[f])) return FGBD_EINVAL;
+    if (c->params.window != 1) return FGBD_ENOTIMPL;
+  }
+  DeviceGuard g(ctxs[0]->device);
+  const cudaStream_t st = as_stream(stream);
+  fgbd_ctx* lead = ctxs[0];
+  // fork: every frame's stream starts after the caller's earlier work
+  FGBD_CUDA(lead, cudaEventRecord(lead->ev_fork, st));
+  for (int f = 0; f < count; ++f) FGBD_CUDA(ctxs[f], cudaStreamWaitEvent(ctxs[f]->side, lead->ev_fork, 0));
+  // graph and noise estimate of every frame, concurrently
+  for (int f = 0; f < count; ++f) {
+    fgbd_ctx* c = ctxs[f];
+    fgbd_status s = do_build(c, xyz[f], n[f], c->side);
+    if (s == FGBD_OK) s = do_estimate(c, rgb_in[f], in_dtype[f], nullptr, c->side);
+    if (s != FGBD_OK) return s;
+  }
+  // selection + filter: cooperative launches, one at a time (frame f waits for
+  // frame f - 1's) so that two of them never compete for residency
+  for (int f = 0; f < count; ++f) {
+    fgbd_ctx* c = ctxs[f];
+    if (f > 0) FGBD_CUDA(c, cudaStreamWaitEvent(c->side, ctxs[f - 1]->ev_filter, 0));
+    const fgbd_status s = do_select(c, rgb_in[f], in_dtype[f], nullptr, nullptr, rgb_out[f], out_dtype[f], c->side);
+    if (s != FGBD_OK) return s;
+    FGBD_CUDA(c, cudaEventRecord(c->ev_filter, c->side));
+  }
+  // join: the caller's stream continues after every frame
+  for (int f = 0; f < count; ++f) {
+    FGBD_CUDA(ctxs[f], cudaEventRecord(ctxs[f]->ev_join, ctxs[f]->side));
+    FGBD_CUDA(ctxs[f], cudaStreamWaitEvent(st, ctxs[f]->ev_join, 0));
+  }
+  return FGBD_OK;
 }
 
 fgbd_status fgbd_sync(fgbd_ctx* ctx, void* stream) {

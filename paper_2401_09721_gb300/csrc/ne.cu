@@ -748,15 +748,16 @@ cudaError_t launch_gather_colors(const void* rgb, int dtype, int n, const int32_
 }
 
 int ne_moment_blocks(int n, int num_sms) {
-  int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ne_moments<0>, kNeThreads, 0) != cudaSuccess ||
-      per_sm < 1)
-    per_sm = 1;
-  int per_sm_f = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_f, k_ne_moments<1>, kNeThreads, 0) != cudaSuccess ||
-      per_sm_f < 1)
-    per_sm_f = 1;
-  per_sm = std::min(per_sm, per_sm_f);
+  // resident blocks per SM, queried once (the same code runs on every device of one build)
+  static const int per_sm = [] {
+    int a = 0, b = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_ne_moments<0>, kNeThreads, 0) != cudaSuccess || a < 1)
+      a = 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_ne_moments<1>, kNeThreads, 0) != cudaSuccess || b < 1)
+      b = 1;
+    cudaGetLastError();
+    return std::min(a, b);
+  }();
   return std::max(1, std::min((n + kNeThreads - 1) / kNeThreads, num_sms * per_sm));
 }
 

@@ -102,6 +102,9 @@ _SIGS = {
     "fgbd_select_filter": (ctypes.c_int, [_P, _P, ctypes.c_int32, _P, _P, _P]),
     "fgbd_denoise": (ctypes.c_int, [_P, _P, ctypes.c_int32, ctypes.c_int32, _P, ctypes.c_int32, _P]),
     "fgbd_run": (ctypes.c_int, [_P, _P, ctypes.c_int64, _P, ctypes.c_int32, _P, ctypes.c_int32, _P]),
+    "fgbd_run_batch": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(ctypes.c_int64),
+                                      ctypes.POINTER(_P), ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(_P),
+                                      ctypes.POINTER(ctypes.c_int32), ctypes.c_int32, _P]),
     "fgbd_sync": (ctypes.c_int, [_P, _P]),
     "fgbd_get_stats": (ctypes.c_int, [_P, ctypes.POINTER(Stats), _P]),
     "fgbd_graph_csr": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64), _P]),
@@ -233,6 +236,34 @@ def fgbd_run(ctx, xyz: torch.Tensor, rgb_in: torch.Tensor, rgb_out: torch.Tensor
                           _dtype_code(rgb_out), _stream(stream)), "fgbd_run", ctx)
 
 
+BATCH_MAX = 64  # FGBD_BATCH_MAX
+
+
+def fgbd_run_batch(ctxs, xyzs, rgbs_in, rgbs_out, stream=None) -> None:
+    """fgbd_run on several frames at once, frame f in context ctxs[f] (handles)."""
+    count = len(ctxs)
+    if not (len(xyzs) == len(rgbs_in) == len(rgbs_out) == count):
+        raise ValueError("one xyz, rgb_in and rgb_out per context")
+    for xyz, ci, co in zip(xyzs, rgbs_in, rgbs_out):
+        if xyz.dtype != torch.int32:
+            raise TypeError("xyz must be int32")
+        n = xyz.shape[0]
+        _need_cuda(xyz, "xyz", n)
+        _need_cuda(ci, "rgb_in", n)
+        _need_cuda(co, "rgb_out", n)
+    def arr(t, vals):
+        return (t * count)(*[v.value if isinstance(v, ctypes.c_void_p) else v for v in vals])
+
+    _check(lib().fgbd_run_batch(arr(_P, ctxs),
+                                arr(_P, [_ptr(x) for x in xyzs]),
+                                arr(ctypes.c_int64, [x.shape[0] for x in xyzs]),
+                                arr(_P, [_ptr(c) for c in rgbs_in]),
+                                arr(ctypes.c_int32, [_dtype_code(c) for c in rgbs_in]),
+                                arr(_P, [_ptr(c) for c in rgbs_out]),
+                                arr(ctypes.c_int32, [_dtype_code(c) for c in rgbs_out]),
+                                count, _stream(stream)), "fgbd_run_batch")
+
+
 def fgbd_sync(ctx, stream=None) -> None:
     _check(lib().fgbd_sync(ctx, _stream(stream)), "fgbd_sync", ctx)
 
@@ -335,6 +366,16 @@ class Context:
 
     def sync(self, stream=None):
         fgbd_sync(self.handle, stream)
+
+    @staticmethod
+    def run_batch(contexts, xyzs, rgbs_in, out_dtype=torch.float32, outs=None, stream=None):
+        """fgbd_run_batch over Context objects; returns the outputs."""
+        if outs is None:
+            outs = [torch.empty((x.shape[0], 3), dtype=out_dtype, device=c.device) for c, x in zip(contexts, xyzs)]
+        fgbd_run_batch([c.handle for c in contexts], xyzs, rgbs_in, outs, stream)
+        for c, x in zip(contexts, xyzs):
+            c.n = x.shape[0]
+        return outs
 
     def stats(self, stream=None) -> dict:
         return fgbd_get_stats(self.handle, stream)

@@ -301,3 +301,26 @@ def torso_frame(target: int = 1_000_000, bits: int = 10, sigma: float = 20.0, se
     clean = piecewise_colors(xyz, bits, seed)
     noisy = add_noise_u8(clean, sigma, seed if noise_seed is None else noise_seed)
     return Frame(xyz, clean, noisy, sigma, bits, f"torso{xyz.shape[0]}_b{bits}_s{sigma:g}")
+
+
+def batch_frames(count: int = 16, lo: int = 200_000, hi: int = 1_200_000, seed: int = 1,
+                 bits: int = 10) -> list:
+    """Frames of uneven sizes for the batched path: frame f (seed seed + f) has
+    N_f ~ U[lo, hi] sphere voxels at `bits` bits (sampled 1.5x, voxelized and
+    trimmed to N_f), smooth colour, and uint8 noise with sigma_f ~ U[10, 50]."""
+    frames = []
+    for f in range(count):
+        s = seed + f
+        rng = np.random.default_rng(s)
+        target = int(rng.integers(lo, hi + 1))
+        sigma = float(rng.uniform(10.0, 50.0))
+        samples = int(target * 1.5) + 1024
+        xyz = sphere_points(samples, bits, s)
+        while xyz.shape[0] < target:
+            samples *= 2
+            xyz = sphere_points(samples, bits, s)
+        xyz = np.ascontiguousarray(xyz[:target])
+        clean = smooth_colors(xyz, bits, s)
+        noisy = add_noise_u8(clean, sigma, s)
+        frames.append(Frame(xyz, clean, noisy, sigma, bits, f"sphere{target}_b{bits}_s{sigma:.1f}"))
+    return frames
