@@ -190,6 +190,36 @@ fgbd_status fgbd_run_batch(fgbd_ctx* const* ctxs, const int32_t* const* xyz, con
                            const void* const* rgb_in, const int32_t* in_dtype, void* const* rgb_out,
                            const int32_t* out_dtype, int32_t count, void* stream);
 
+/* Differentiable filter (no counterpart in the paper; a training extension
+ * of Eq. 5).  With R = D^-1 W, W_ij = exp(-d_ij^2 / sigma^2) on the graph of
+ * the last fgbd_build_graph (Eq. 4), the filter
+ *   x_0 = rgb_in,  x_{t+1} = (1 - alpha) x_t + alpha R x_t,  rgb_out = x_q
+ * is Eq. 5 for alpha = 1/2 and sigma = sigma_g (W_g = D + W, D_g = 2D).
+ *   rgb_in, rgb_out: float32 [n][3] device, input order, 0..255 scale.
+ *   q:          0..FGBD_Q_CAP filter steps.
+ *   alpha:      filter strength (any finite value; 1/2 in the paper).
+ *   sigma:      weight bandwidth; 0 means sigma_g of the graph.
+ *   checkpoint: keep every checkpoint-th iterate for the backward call and
+ *               recompute the others there (0 or 1: keep all); memory about
+ *               (100 + 16 (q / checkpoint + checkpoint + 1)) bytes per point,
+ *               allocated on the first call that needs more (that call
+ *               synchronises the device).
+ * The call records q, alpha, sigma for fgbd_filter_backward.
+ * Errors: FGBD_EINVAL, FGBD_ESTATE (no graph), FGBD_ENOMEM, FGBD_ECUDA. */
+fgbd_status fgbd_filter_forward(fgbd_ctx* ctx, const float* rgb_in, int32_t q, double alpha, double sigma,
+                                int32_t checkpoint, float* rgb_out, void* stream);
+
+/* Adjoint of the last fgbd_filter_forward of this context: given
+ * grad_out = dL/d rgb_out (float32 [n][3], input order) it writes
+ *   grad_in        = dL/d rgb_in = ((1 - alpha) I + alpha W D^-1)^q grad_out,
+ *   grad_params[0] = dL/d alpha,  grad_params[1] = dL/d sigma
+ * (grad_params: device double[2]), summing over the q steps with the stored
+ * or recomputed iterates.  The reductions are float64 in a fixed order.
+ * Errors: FGBD_EINVAL, FGBD_ESTATE (no forward call since the last graph
+ * build), FGBD_ECUDA. */
+fgbd_status fgbd_filter_backward(fgbd_ctx* ctx, const float* grad_out, float* grad_in, double* grad_params,
+                                 void* stream);
+
 /* Wait for the context's work on `stream` and return any latched device error
  * (FGBD_ERANGE, FGBD_ETIMEOUT), clearing it. */
 fgbd_status fgbd_sync(fgbd_ctx* ctx, void* stream);

@@ -373,6 +373,64 @@ def lowpass(f_in: np.ndarray, row_ptr, col, rw, q: int) -> np.ndarray:
     return x
 
 
+# --------------------------------------------------------------------------
+# Differentiable filter (an extension for parameter tuning; Eq. 4-5 generalised)
+# --------------------------------------------------------------------------
+
+def param_filter(g, row_ptr, col, y, q: int, alpha: float, sigma: float):
+    """x_0 = y, x_{t+1} = (1 - alpha) x_t + alpha R x_t with R = D^{-1} W(sigma) of Eq. 4.
+
+    alpha = 1/2 and sigma = sigma_g give Eq. 5 (``lowpass``).  A point without
+    neighbours has R x = x, as in Eq. 5.  Returns the iterates [x_0 .. x_q].
+    """
+    rw = random_walk_weights(g, row_ptr, col, sigma)
+    R = _rw_matrix(row_ptr, col, rw)
+    isolated = np.diff(row_ptr) == 0
+    xs = [np.asarray(y, dtype=np.float64).copy()]
+    for _ in range(q):
+        x = xs[-1]
+        rx = R @ x
+        rx[isolated] = x[isolated]
+        xs.append((1.0 - alpha) * x + alpha * rx)
+    return xs
+
+
+def param_filter_vjp(g, row_ptr, col, y, q: int, alpha: float, sigma: float, grad_out):
+    """Gradient of L(x_q) for ``param_filter``, given grad_out = dL/dx_q.
+
+    With P = (1 - alpha) I + alpha R and u_t = dL/dx_t:
+      u_t = P^T u_{t+1};  dL/dy = u_0;
+      dL/dalpha = sum_t u_{t+1} . (R x_t - x_t);
+      dL/dsigma = sum_t alpha u_{t+1} . (dR/dsigma) x_t,
+    where R_ij = w_ij / sum_k w_ik and w_ij = exp(-d_ij^2 / sigma^2) give
+      dR_ij/dsigma = (2 / sigma^3) R_ij (d_ij^2 - sum_k R_ik d_ik^2).
+    Returns (dL/dy [N, 3], dL/dalpha, dL/dsigma).
+    """
+    xs = param_filter(g, row_ptr, col, y, q, alpha, sigma)
+    rw = random_walk_weights(g, row_ptr, col, sigma)
+    n = row_ptr.size - 1
+    rows = _row_index(row_ptr)
+    d2 = _sq_dist(g, row_ptr, col).astype(np.float64)
+    isolated = np.diff(row_ptr) == 0
+    R = _rw_matrix(row_ptr, col, rw)
+    e = np.bincount(rows, weights=rw * d2, minlength=n)
+    dR = _rw_matrix(row_ptr, col, (2.0 / sigma ** 3) * rw * (d2 - e[rows]))
+    RT = R.T.tocsr()
+    u = np.asarray(grad_out, dtype=np.float64).copy()
+    da = 0.0
+    ds = 0.0
+    for t in range(q - 1, -1, -1):
+        x = xs[t]
+        rx = R @ x
+        rx[isolated] = x[isolated]
+        da += float(np.sum(u * (rx - x)))
+        ds += float(alpha * np.sum(u * (dR @ x)))
+        ru = RT @ u
+        ru[isolated] = u[isolated]
+        u = (1.0 - alpha) * u + alpha * ru
+    return u, da, ds
+
+
 def selection_objective(y: np.ndarray, xq: np.ndarray, keep: np.ndarray, sigma_est: float) -> float:
     """Eq. 6 over the limited region: |sigma_est^2 - (sum y^2 - sum x_q^2) / N|.
 

@@ -6,6 +6,7 @@
 // errors are latched in DevScalars::status and surfaced by the synchronising
 // calls.
 #include <algorithm>
+#include <cmath>
 #include <cstddef>
 #include <cstdio>
 #include <cstring>
@@ -44,6 +45,21 @@ struct fgbd_ctx {
   const void* noise_rgb = nullptr;
   int noise_dtype = -1;
   std::string err;
+  uint64_t graph_gen = 0;  // incremented by every graph build
+  // differentiable filter: workspace (allocated by the first forward call that needs it) and the
+  // state of the last forward call, which the backward call differentiates
+  void* dmem = nullptr;
+  size_t dmem_bytes = 0;
+  DiffBufs db{};
+  float4* d_ckpt = nullptr;   // x_0, x_c, x_2c, ... (c = checkpoint interval)
+  float4* d_seg = nullptr;    // x_{t0+1} .. x_{t0+c-1} of one segment (backward)
+  float4* d_pp[2] = {};       // ping-pong for steps and for the adjoint
+  double* d_part = nullptr;   // per step and block: dL/dalpha, dL/dsigma terms
+  int d_q = -1, d_c = 1, d_n = 0, d_grid = 0;
+  float d_alpha = 0.5f;
+  double d_sigma = 0.0;
+  uint64_t d_gen = 0;
+  bool d_valid = false;
   // batched runs: this context's own stream and the events that order it
   cudaStream_t side = nullptr;
   cudaEvent_t ev_fork = nullptr;    // recorded on the caller's stream (first context of a batch)
@@ -175,6 +191,53 @@ int filter_grid_for(const fgbd_ctx* ctx, int n) {
   return std::max(1, std::min(need, ctx->filter_per_sm * ctx->num_sms));
 }
 
+// Carve the differentiable-filter workspace for n points, q steps, checkpoint
+// interval c; grow the allocation if needed (this synchronises the device).
+fgbd_status diff_workspace(fgbd_ctx* ctx, int n, int q, int c, int grid) {
+  const size_t N = size_t(std::max(n, 1));
+  const size_t nck = size_t(q / c + 1);
+  const size_t sizes[] = {N * kK * 4, N * kK * 4, N * kK * 4, N * kK * 4, N * 4,  // nb, R, RT, d2, e
+                          nck * N * 16, size_t(c > 1 ? c - 1 : 1) * N * 16,     // checkpoints, segment
+                          N * 16, N * 16,                                       // ping-pong
+                          size_t(std::max(q, 1)) * size_t(grid) * 2 * 8};       // partials
+  size_t total = 0;
+  for (size_t b : sizes) total = align_up(total, 256) + b;
+  total = align_up(total, 256);
+  if (total > ctx->dmem_bytes) {
+    if (ctx->dmem) {
+      cudaDeviceSynchronize();
+      cudaFree(ctx->dmem);
+      ctx->dmem = nullptr;
+      ctx->dmem_bytes = 0;
+    }
+    if (cudaMalloc(&ctx->dmem, total) != cudaSuccess) {
+      cudaGetLastError();
+      ctx->dmem = nullptr;
+      return FGBD_ENOMEM;
+    }
+    ctx->dmem_bytes = total;
+  }
+  char* base = static_cast<char*>(ctx->dmem);
+  size_t off = 0;
+  void* ptrs[10];
+  for (int k = 0; k < 10; ++k) {
+    off = align_up(off, 256);
+    ptrs[k] = base + off;
+    off += sizes[k];
+  }
+  ctx->db.nb = static_cast<int32_t*>(ptrs[0]);
+  ctx->db.R = static_cast<float*>(ptrs[1]);
+  ctx->db.RT = static_cast<float*>(ptrs[2]);
+  ctx->db.d2 = static_cast<float*>(ptrs[3]);
+  ctx->db.e = static_cast<float*>(ptrs[4]);
+  ctx->d_ckpt = static_cast<float4*>(ptrs[5]);
+  ctx->d_seg = static_cast<float4*>(ptrs[6]);
+  ctx->d_pp[0] = static_cast<float4*>(ptrs[7]);
+  ctx->d_pp[1] = static_cast<float4*>(ptrs[8]);
+  ctx->d_part = static_cast<double*>(ptrs[9]);
+  return FGBD_OK;
+}
+
 void release_batch_objects(fgbd_ctx* ctx) {
   for (cudaEvent_t* e : {&ctx->ev_fork, &ctx->ev_filter, &ctx->ev_join})
     if (*e) {
@@ -195,6 +258,7 @@ fgbd_status do_build(fgbd_ctx* ctx, const int32_t* xyz, int64_t n64, cudaStream_
   ctx->has_graph = ctx->has_noise = ctx->has_sel = false;
   ctx->noise_rgb = nullptr;
   ctx->n = n;
+  ctx->graph_gen += 1;
   cudaError_t e = cudaSuccess;
   zero_region(ctx, offsetof(DevScalars, n_edges), offsetof(DevScalars, build_end_), st, &e);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "memset");
@@ -384,6 +448,7 @@ void fgbd_ctx_destroy(fgbd_ctx* ctx) {
   for (cudaEvent_t e : ctx->ev)
     if (e) cudaEventDestroy(e);
   release_batch_objects(ctx);
+  cudaFree(ctx->dmem);
   cudaFree(ctx->mem);
   delete ctx;
 }
@@ -500,6 +565,91 @@ fgbd_status fgbd_run_batch(fgbd_ctx* const* ctxs, const int32_t* const* xyz, con
     FGBD_CUDA(ctxs[f], cudaEventRecord(ctxs[f]->ev_join, ctxs[f]->side));
     FGBD_CUDA(ctxs[f], cudaStreamWaitEvent(st, ctxs[f]->ev_join, 0));
   }
+  return FGBD_OK;
+}
+
+fgbd_status fgbd_filter_forward(fgbd_ctx* ctx, const float* rgb_in, int32_t q, double alpha, double sigma,
+                                int32_t checkpoint, float* rgb_out, void* stream) {
+  if (!ctx) return FGBD_EINVAL;
+  if (!ctx->has_graph) return FGBD_ESTATE;
+  if (q < 0 || q > kQCap || checkpoint < 0) return FGBD_EINVAL;
+  if (!std::isfinite(alpha) || !std::isfinite(sigma) || sigma < 0.0) return FGBD_EINVAL;
+  const int n = ctx->n;
+  if (n > 0 && (!rgb_in || !rgb_out)) return FGBD_EINVAL;
+  DeviceGuard g(ctx->device);
+  const cudaStream_t st = as_stream(stream);
+  const int c = std::max(1, std::min(checkpoint == 0 ? 1 : int(checkpoint), std::max(int(q), 1)));
+  const int grid = diff_grid(std::max(n, 1), ctx->num_sms);
+  ctx->d_valid = false;
+  const fgbd_status ws = diff_workspace(ctx, n, q, c, grid);
+  if (ws != FGBD_OK) return ws;
+  const float a = float(alpha);
+  if (n > 0) {
+    FGBD_LAUNCH(ctx, "diff_rows", st, launch_diff_rows(n, ctx->params.bits, sigma, ctx->gb, ctx->sc, ctx->db,
+                                                       ctx->num_sms, st));
+    FGBD_LAUNCH(ctx, "diff_gather", st, launch_diff_gather(n, rgb_in, ctx->gb.perm1, ctx->d_ckpt, ctx->num_sms, st));
+    const float4* cur = ctx->d_ckpt;
+    for (int t = 0; t < q; ++t) {
+      float4* dst = ((t + 1) % c == 0) ? ctx->d_ckpt + size_t((t + 1) / c) * size_t(n) : ctx->d_pp[(t + 1) & 1];
+      FGBD_LAUNCH(ctx, "diff_step", st, launch_diff_step(n, a, ctx->db, cur, dst, ctx->num_sms, st));
+      cur = dst;
+    }
+    FGBD_LAUNCH(ctx, "diff_scatter", st, launch_diff_scatter(n, cur, ctx->gb.perm1, rgb_out, ctx->num_sms, st));
+  }
+  ctx->d_q = q;
+  ctx->d_c = c;
+  ctx->d_n = n;
+  ctx->d_grid = grid;
+  ctx->d_alpha = a;
+  ctx->d_sigma = sigma;
+  ctx->d_gen = ctx->graph_gen;
+  ctx->d_valid = true;
+  return FGBD_OK;
+}
+
+fgbd_status fgbd_filter_backward(fgbd_ctx* ctx, const float* grad_out, float* grad_in, double* grad_params,
+                                 void* stream) {
+  if (!ctx) return FGBD_EINVAL;
+  if (!ctx->d_valid || !ctx->has_graph || ctx->d_gen != ctx->graph_gen) return FGBD_ESTATE;
+  const int n = ctx->d_n;
+  if (n > 0 && (!grad_out || !grad_in)) return FGBD_EINVAL;
+  if (!grad_params) return FGBD_EINVAL;
+  DeviceGuard g(ctx->device);
+  const cudaStream_t st = as_stream(stream);
+  const int q = ctx->d_q, c = ctx->d_c, grid = ctx->d_grid;
+  const float a = ctx->d_alpha;
+  int parts = 0;
+  if (n > 0) {
+    FGBD_LAUNCH(ctx, "diff_gather", st, launch_diff_gather(n, grad_out, ctx->gb.perm1, ctx->d_pp[0], ctx->num_sms, st));
+    int ui = 0;
+    int seg_t0 = -1;  // first step of the segment held in d_seg
+    for (int t = q - 1; t >= 0; --t) {
+      const int t0 = (t / c) * c;
+      const float4* xt;
+      if (t == t0) {
+        xt = ctx->d_ckpt + size_t(t0 / c) * size_t(n);
+      } else {
+        if (seg_t0 != t0) {
+          // recompute x_{t0+1} .. x_t of this segment from its checkpoint
+          const float4* cur = ctx->d_ckpt + size_t(t0 / c) * size_t(n);
+          for (int s = t0; s < t; ++s) {
+            float4* dst = ctx->d_seg + size_t(s - t0) * size_t(n);
+            FGBD_LAUNCH(ctx, "diff_step", st, launch_diff_step(n, a, ctx->db, cur, dst, ctx->num_sms, st));
+            cur = dst;
+          }
+          seg_t0 = t0;
+        }
+        xt = ctx->d_seg + size_t(t - t0 - 1) * size_t(n);
+      }
+      FGBD_LAUNCH(ctx, "diff_back_step", st,
+                  launch_diff_back_step(n, a, ctx->d_sigma, ctx->db, xt, ctx->d_pp[ui], ctx->d_pp[ui ^ 1], ctx->sc,
+                                        ctx->d_part + size_t(t) * size_t(grid) * 2, ctx->num_sms, st));
+      ui ^= 1;
+    }
+    FGBD_LAUNCH(ctx, "diff_scatter", st, launch_diff_scatter(n, ctx->d_pp[ui], ctx->gb.perm1, grad_in, ctx->num_sms, st));
+    parts = q * grid;
+  }
+  FGBD_LAUNCH(ctx, "diff_reduce", st, launch_diff_reduce(parts, ctx->d_part, grad_params, st));
   return FGBD_OK;
 }
 

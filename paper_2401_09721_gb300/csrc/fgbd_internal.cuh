@@ -159,6 +159,28 @@ int filter_grid(int n, int num_sms);
 cudaError_t launch_output(int n, const int32_t* rank1, const float4* xbuf0, const float4* xbuf1,
                           const DevScalars* sc, void* out, int out_dtype, cudaStream_t stream);
 
+// Differentiable filter: rows of R = D^-1 W for given alpha, sigma, and their transpose
+struct DiffBufs {
+  int32_t* nb;  // [n][6] neighbour ids (sorted order), -1 unused
+  float* R;     // [n][6] R_ij
+  float* RT;    // [n][6] R_ji: weight of i in the row of its t-th neighbour
+  float* d2;    // [n][6] squared distances
+  float* e;     // [n] sum_j R_ij d_ij^2
+};
+int diff_grid(int n, int num_sms);
+cudaError_t launch_diff_rows(int n, int bits, double sigma, const GraphBufs& gb, const DevScalars* sc,
+                             const DiffBufs& db, int num_sms, cudaStream_t stream);
+cudaError_t launch_diff_gather(int n, const float* rgb, const int32_t* perm1, float4* x, int num_sms,
+                               cudaStream_t stream);
+cudaError_t launch_diff_scatter(int n, const float4* x, const int32_t* perm1, float* out, int num_sms,
+                                cudaStream_t stream);
+cudaError_t launch_diff_step(int n, float alpha, const DiffBufs& db, const float4* src, float4* dst, int num_sms,
+                             cudaStream_t stream);
+cudaError_t launch_diff_back_step(int n, float alpha, double sigma, const DiffBufs& db, const float4* x,
+                                  const float4* u, float4* u_out, const DevScalars* sc, double* partial,
+                                  int num_sms, cudaStream_t stream);
+cudaError_t launch_diff_reduce(int count, const double* partial, double* grad, cudaStream_t stream);
+
 // CSR export in input order
 cudaError_t launch_csr_degree(int n, const GraphBufs& gb, int64_t* deg_out, cudaStream_t stream);
 cudaError_t launch_scan_i64(int64_t* data, int64_t count, int64_t* block_tmp, cudaStream_t stream);

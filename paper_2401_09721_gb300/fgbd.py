@@ -105,6 +105,9 @@ _SIGS = {
     "fgbd_run_batch": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(ctypes.c_int64),
                                       ctypes.POINTER(_P), ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(_P),
                                       ctypes.POINTER(ctypes.c_int32), ctypes.c_int32, _P]),
+    "fgbd_filter_forward": (ctypes.c_int, [_P, _P, ctypes.c_int32, ctypes.c_double, ctypes.c_double, ctypes.c_int32,
+                                           _P, _P]),
+    "fgbd_filter_backward": (ctypes.c_int, [_P, _P, _P, _P, _P]),
     "fgbd_sync": (ctypes.c_int, [_P, _P]),
     "fgbd_get_stats": (ctypes.c_int, [_P, ctypes.POINTER(Stats), _P]),
     "fgbd_graph_csr": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64), _P]),
@@ -264,6 +267,63 @@ def fgbd_run_batch(ctxs, xyzs, rgbs_in, rgbs_out, stream=None) -> None:
                                 count, _stream(stream)), "fgbd_run_batch")
 
 
+def fgbd_filter_forward(ctx, rgb_in: torch.Tensor, q: int, alpha: float, sigma: float, checkpoint: int,
+                        rgb_out: torch.Tensor, n: int, stream=None) -> None:
+    if rgb_in.dtype != torch.float32 or rgb_out.dtype != torch.float32:
+        raise TypeError("the differentiable filter takes float32 colours")
+    _need_cuda(rgb_in, "rgb_in", n)
+    _need_cuda(rgb_out, "rgb_out", n)
+    _check(lib().fgbd_filter_forward(ctx, _ptr(rgb_in), int(q), float(alpha), float(sigma), int(checkpoint),
+                                     _ptr(rgb_out), _stream(stream)), "fgbd_filter_forward", ctx)
+
+
+def fgbd_filter_backward(ctx, grad_out: torch.Tensor, grad_in: torch.Tensor, grad_params: torch.Tensor, n: int,
+                         stream=None) -> None:
+    if grad_out.dtype != torch.float32 or grad_in.dtype != torch.float32 or grad_params.dtype != torch.float64:
+        raise TypeError("float32 colour gradients and a float64 [2] parameter gradient")
+    _need_cuda(grad_out, "grad_out", n)
+    _need_cuda(grad_in, "grad_in", n)
+    if not grad_params.is_cuda or grad_params.numel() < 2:
+        raise ValueError("grad_params must be a CUDA float64 tensor of 2 entries")
+    _check(lib().fgbd_filter_backward(ctx, _ptr(grad_out), _ptr(grad_in), _ptr(grad_params), _stream(stream)),
+           "fgbd_filter_backward", ctx)
+
+
+class GraphFilter(torch.autograd.Function):
+    """x_q = ((1 - alpha) I + alpha D^-1 W(sigma))^q rgb on a context's graph.
+
+    Differentiable in rgb (float32 [n, 3], input order), alpha and sigma (Python
+    floats or CPU tensors; sigma = 0 means sigma_g).  The backward pass runs
+    the library's adjoint kernels and is valid for the context's last forward
+    call only.
+    """
+
+    @staticmethod
+    def forward(fctx, rgb, alpha, sigma, context, q, checkpoint):
+        a = float(alpha)
+        sg = float(sigma)
+        out = torch.empty_like(rgb)
+        fgbd_filter_forward(context.handle, rgb.contiguous(), q, a, sg, checkpoint, out, context.n)
+        context._diff_token = getattr(context, "_diff_token", 0) + 1
+        fctx.context = context
+        fctx.token = context._diff_token
+        meta = lambda t: (t.device, t.dtype, t.shape) if isinstance(t, torch.Tensor) else None
+        fctx.alpha_meta, fctx.sigma_meta = meta(alpha), meta(sigma)
+        return out
+
+    @staticmethod
+    def backward(fctx, grad_out):
+        context = fctx.context
+        if getattr(context, "_diff_token", None) != fctx.token:
+            raise RuntimeError("the context ran another filter forward since this one; backward needs its state")
+        grad_in = torch.empty_like(grad_out)
+        gp = torch.zeros(2, dtype=torch.float64, device=grad_out.device)
+        fgbd_filter_backward(context.handle, grad_out.contiguous(), grad_in, gp, context.n)
+        like = lambda v, m: None if m is None else v.to(device=m[0], dtype=m[1]).reshape(m[2])
+        ga, gs = like(gp[0], fctx.alpha_meta), like(gp[1], fctx.sigma_meta)
+        return grad_in, ga, gs, None, None, None
+
+
 def fgbd_sync(ctx, stream=None) -> None:
     _check(lib().fgbd_sync(ctx, _stream(stream)), "fgbd_sync", ctx)
 
@@ -366,6 +426,10 @@ class Context:
 
     def sync(self, stream=None):
         fgbd_sync(self.handle, stream)
+
+    def filter(self, rgb, alpha=0.5, sigma=0.0, q=1, checkpoint=1):
+        """Differentiable filter on this context's graph (GraphFilter)."""
+        return GraphFilter.apply(rgb, alpha, sigma, self, q, checkpoint)
 
     @staticmethod
     def run_batch(contexts, xyzs, rgbs_in, out_dtype=torch.float32, outs=None, stream=None):

@@ -473,3 +473,59 @@ def test_fgbd_sparse_sphere_runs():
     assert res.noise["n_patches"] > 15000 and res.q >= 1
     assert res.J[0] == pytest.approx(res.noise["sigma_est"] ** 2, rel=1e-12)
     assert np.isfinite(res.out).all()
+
+
+# ---------------------------------------------------------------- differentiable filter
+
+def _diff_case(seed=0, n=150, bits=4):
+    rng = np.random.default_rng(500 + seed)
+    xyz = random_cloud(rng, n, bits)
+    y = rng.uniform(0, 255, size=(n, 3))
+    _, _, _, row_ptr, col = graph_of(xyz, bits)
+    return xyz, y, row_ptr, col, rng
+
+
+def test_param_filter_reduces_to_eq5():
+    xyz, y, row_ptr, col, _ = _diff_case(0)
+    sg = orc.sigma_g(xyz, row_ptr, col)
+    rw = orc.random_walk_weights(xyz, row_ptr, col, sg)
+    for q in (0, 1, 3):
+        assert np.allclose(orc.param_filter(xyz, row_ptr, col, y, q, 0.5, sg)[-1],
+                           orc.lowpass(y, row_ptr, col, rw, q), rtol=1e-13, atol=1e-11)
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_param_filter_gradient_finite_differences(seed):
+    xyz, y, row_ptr, col, rng = _diff_case(seed)
+    q, alpha = 4, 0.35 + 0.1 * seed
+    sigma = orc.sigma_g(xyz, row_ptr, col) * (0.8 + 0.2 * seed)
+    gout = rng.normal(size=y.shape)
+    loss = lambda yy, a, s: float(np.sum(gout * orc.param_filter(xyz, row_ptr, col, yy, q, a, s)[-1]))
+    gy, da, ds = orc.param_filter_vjp(xyz, row_ptr, col, y, q, alpha, sigma, gout)
+    h = 1e-3
+
+    def central(f, h):   # central differences at steps h and h/2, Richardson-combined (error O(h^4))
+        d1 = (f(h) - f(-h)) / (2 * h)
+        d2 = (f(h / 2) - f(-h / 2)) / h
+        return (4 * d2 - d1) / 3
+
+    fd_a = central(lambda d: loss(y, alpha + d, sigma), h)
+    fd_s = central(lambda d: loss(y, alpha, sigma + d), h)
+    assert da == pytest.approx(fd_a, rel=1e-8, abs=1e-6)
+    assert ds == pytest.approx(fd_s, rel=1e-7, abs=1e-6)
+    for _ in range(16):   # random colour entries
+        i, c = int(rng.integers(len(y))), int(rng.integers(3))
+        yp, ym = y.copy(), y.copy()
+        yp[i, c] += h
+        ym[i, c] -= h
+        assert gy[i, c] == pytest.approx((loss(yp, alpha, sigma) - loss(ym, alpha, sigma)) / (2 * h), rel=1e-6, abs=1e-8)
+
+
+def test_param_filter_adjoint_identity():
+    # <P^q y, g> = <y, (P^T)^q g>: the colour gradient of a linear loss
+    xyz, y, row_ptr, col, rng = _diff_case(3)
+    sg = orc.sigma_g(xyz, row_ptr, col)
+    gout = rng.normal(size=y.shape)
+    xq = orc.param_filter(xyz, row_ptr, col, y, 5, 0.5, sg)[-1]
+    gy, _, _ = orc.param_filter_vjp(xyz, row_ptr, col, y, 5, 0.5, sg, gout)
+    assert np.sum(xq * gout) == pytest.approx(np.sum(y * gy), rel=1e-12)
