@@ -43,6 +43,7 @@ def parse():
     ap.add_argument("--points", type=int, default=N_POINTS)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-path measurement")
+    ap.add_argument("--no-diff", action="store_true", help="skip the differentiable-filter measurement")
     return ap.parse_args()
 
 
@@ -113,6 +114,66 @@ def measure_batched(fgbd, torch, dev, stream, flush, repeats=3):
     for c in ctxs:
         c.close()
     return res
+
+
+# ------------------------------------------------------------------ differentiable filter
+
+def measure_differentiable(fgbd, torch, dev, stream, steps=200, q=4):
+    """Tuning of the filter strength alpha and the bandwidth scale s (sigma = s
+    sigma_g) by Adam on 8 clean/noisy pairs (300k sphere points at b = 9,
+    sigma = 30): loss = mean squared error of the filtered noisy colours against
+    the clean ones, averaged over the pairs.  Reports the device time of one
+    forward + backward pass and the loss before and after."""
+    from paper_2401_09721_gb300 import synth
+    pairs = synth.tuning_pairs()
+    ctxs, ys, cl, sgs = [], [], [], []
+    for fr in pairs:
+        c = fgbd.Context(fr.n, bits=fr.bits)
+        c.build_graph(torch.from_numpy(fr.xyz).to(dev))
+        ctxs.append(c)
+        ys.append(torch.from_numpy(fr.noisy).to(dev))
+        cl.append(torch.from_numpy(fr.clean).to(dev))
+        sgs.append(c.stats()["sigma_g"])
+    alpha = torch.tensor(0.5, dtype=torch.float64, requires_grad=True)
+    scale = torch.tensor(1.0, dtype=torch.float64, requires_grad=True)
+    opt = torch.optim.Adam([alpha, scale], lr=0.02)
+
+    def loss_of(k):
+        out = ctxs[k].filter(ys[k], alpha, scale * sgs[k], q=q)
+        return ((out - cl[k]) ** 2).mean()
+
+    # device time of one forward + backward on one pair
+    for _ in range(3):
+        loss_of(0).backward()
+    ms = []
+    for _ in range(10):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        loss_of(0).backward()
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms.append(a.elapsed_time(b))
+    alpha.grad = None
+    scale.grad = None
+    with torch.no_grad():
+        first = float(np.mean([loss_of(k).item() for k in range(len(pairs))]))
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        opt.zero_grad()
+        total = sum(loss_of(k) for k in range(len(pairs))) / len(pairs)
+        total.backward()
+        opt.step()
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    with torch.no_grad():
+        last = float(np.mean([loss_of(k).item() for k in range(len(pairs))]))
+    for c in ctxs:
+        c.close()
+    return {"workload": "8 pairs, 300k sphere points at b=9, float32 noise sigma=30, seeds 101..108, q=4",
+            "fwd_bwd_ms": float(np.median(ms)), "fwd_bwd_mpoints_per_s": pairs[0].n / (np.median(ms) / 1e3) / 1e6,
+            "adam_steps": steps, "tuning_wall_s": wall, "mse_before": first, "mse_after": last,
+            "psnr_before": 10 * np.log10(255.0 ** 2 / first), "psnr_after": 10 * np.log10(255.0 ** 2 / last),
+            "alpha": float(alpha.item()), "sigma_scale": float(scale.item())}
 
 
 # ------------------------------------------------------------------ CPU oracle
@@ -449,6 +510,9 @@ def run_fgbd(args):
     batched = None
     if not args.no_batch:
         batched = measure_batched(fgbd, torch, dev, stream, flush)
+    differentiable = None
+    if not args.no_diff:
+        differentiable = measure_differentiable(fgbd, torch, dev, stream)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -468,7 +532,7 @@ def run_fgbd(args):
             "kernels": {k: {"ms": round(v["ms"], 5), "per_step": v["launches_per_step"],
                             "gbs": None if v["gbs"] is None else round(v["gbs"], 1)} for k, v in kernels.items()},
             "q_mean": q_mean, "wall_s": wall, "step_ms_min": min(step_ms), "step_ms_max": max(step_ms),
-            "ablations": ablations, "batched": batched,
+            "ablations": ablations, "batched": batched, "differentiable": differentiable,
         }
         print(json.dumps(line), flush=True)
     ctx.close()

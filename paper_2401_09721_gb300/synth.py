@@ -324,3 +324,22 @@ def batch_frames(count: int = 16, lo: int = 200_000, hi: int = 1_200_000, seed: 
         noisy = add_noise_u8(clean, sigma, s)
         frames.append(Frame(xyz, clean, noisy, sigma, bits, f"sphere{target}_b{bits}_s{sigma:.1f}"))
     return frames
+
+
+def tuning_pairs(count: int = 8, n: int = 300_000, sigma: float = 30.0, seed: int = 101, bits: int = 9) -> list:
+    """Clean/noisy pairs for filter-parameter tuning: pair k (seed seed + k) is an
+    n-point sphere frame at `bits` bits with smooth colour and float32 noise of
+    the given sigma (unrounded, unclipped)."""
+    frames = []
+    for k in range(count):
+        s = seed + k
+        samples = int(n * 1.6) + 1024
+        xyz = sphere_points(samples, bits, s)
+        while xyz.shape[0] < n:
+            samples *= 2
+            xyz = sphere_points(samples, bits, s)
+        xyz = np.ascontiguousarray(xyz[:n])
+        clean = smooth_colors(xyz, bits, s, as_float=True)
+        noisy = add_noise_f32(clean, sigma, s)
+        frames.append(Frame(xyz, clean, noisy, sigma, bits, f"sphere{n}_b{bits}_s{sigma:g}_pair{k}"))
+    return frames
