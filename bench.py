@@ -44,6 +44,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-path measurement")
     ap.add_argument("--no-diff", action="store_true", help="skip the differentiable-filter measurement")
+    ap.add_argument("--stream-frames", type=int, default=40, help="frames of the streaming measurement (0: skip)")
     return ap.parse_args()
 
 
@@ -174,6 +175,69 @@ def measure_differentiable(fgbd, torch, dev, stream, steps=200, q=4):
             "adam_steps": steps, "tuning_wall_s": wall, "mse_before": first, "mse_after": last,
             "psnr_before": 10 * np.log10(255.0 ** 2 / first), "psnr_after": 10 * np.log10(255.0 ** 2 / last),
             "alpha": float(alpha.item()), "sigma_scale": float(scale.item())}
+
+
+# ------------------------------------------------------------------ streaming mode
+
+def measure_streaming(fgbd, torch, dev, stream, frames=40):
+    """The first `frames` frames of a 300-frame moving sphere (~1.0M points at
+    b = 10, sigma = 25, synth.StreamSequence): (a) the full method on every
+    frame, (b) the noise estimate and q search on every 10th frame only, the
+    others reusing the previous q (Section 3 (2)), (c) every frame in batches
+    of 4 through the batched path.  Device-timed per frame (per batch in (c));
+    PSNR of the uint8 output against the clean colours."""
+    from paper_2401_09721_gb300 import synth
+    seq = synth.StreamSequence(frames=300)
+    fr = [seq.frame(t) for t in range(frames)]
+    xs = [torch.from_numpy(f.xyz).to(dev) for f in fr]
+    cs = [torch.from_numpy(f.noisy).to(dev) for f in fr]
+    clean = [torch.from_numpy(f.clean).to(dev) for f in fr]
+    cap = max(f.n for f in fr)
+    outs = [torch.empty((f.n, 3), dtype=torch.uint8, device=dev) for f in fr]
+
+    def psnr():
+        mse = [((o.float() - c.float()) ** 2).mean().item() for o, c in zip(outs, clean)]
+        return float(np.mean([10 * np.log10(255.0 ** 2 / m) for m in mse]))
+
+    def summary(lat, n_frames):
+        total = sum(lat)
+        return {"frames_per_s": n_frames / (total / 1e3), "p50_ms": float(np.percentile(lat, 50)),
+                "p99_ms": float(np.percentile(lat, 99)), "psnr_db": psnr()}
+
+    res = {"workload": f"frames 0..{frames - 1} of a 300-frame moving sphere, ~1.0M points at b=10, sigma=25",
+           "points_mean": float(np.mean([f.n for f in fr]))}
+    ctx = fgbd.Context(cap, bits=10)
+    for _ in range(2):
+        ctx.run(xs[0], cs[0], out=outs[0])
+    for mode in ("every_frame", "every_10th"):
+        lat = []
+        for t in range(frames):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            if mode == "every_frame" or t % 10 == 0:
+                ctx.run(xs[t], cs[t], out=outs[t])
+            else:
+                ctx.run_reuse(xs[t], cs[t], out=outs[t])
+            b.record(stream)
+            b.synchronize()
+            lat.append(a.elapsed_time(b))
+        res[mode] = summary(lat, frames)
+    ctx.close()
+    ctxs = [fgbd.Context(cap, bits=10) for _ in range(4)]
+    fgbd.Context.run_batch(ctxs, xs[:4], cs[:4], outs=outs[:4])
+    lat = []
+    for t in range(0, frames - frames % 4, 4):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fgbd.Context.run_batch(ctxs, xs[t:t + 4], cs[t:t + 4], outs=outs[t:t + 4])
+        b.record(stream)
+        b.synchronize()
+        lat.append(a.elapsed_time(b))
+    res["batches_of_4"] = summary(lat, 4 * len(lat))
+    res["batches_of_4"]["latency_is"] = "per batch of 4 frames"
+    for c in ctxs:
+        c.close()
+    return res
 
 
 # ------------------------------------------------------------------ CPU oracle
@@ -513,6 +577,9 @@ def run_fgbd(args):
     differentiable = None
     if not args.no_diff:
         differentiable = measure_differentiable(fgbd, torch, dev, stream)
+    streaming = None
+    if args.stream_frames > 0:
+        streaming = measure_streaming(fgbd, torch, dev, stream, args.stream_frames)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -533,6 +600,7 @@ def run_fgbd(args):
                             "gbs": None if v["gbs"] is None else round(v["gbs"], 1)} for k, v in kernels.items()},
             "q_mean": q_mean, "wall_s": wall, "step_ms_min": min(step_ms), "step_ms_max": max(step_ms),
             "ablations": ablations, "batched": batched, "differentiable": differentiable,
+            "streaming": streaming,
         }
         print(json.dumps(line), flush=True)
     ctx.close()

@@ -167,6 +167,17 @@ fgbd_status fgbd_denoise(fgbd_ctx* ctx, const void* rgb_in, int32_t in_dtype, in
 fgbd_status fgbd_run(fgbd_ctx* ctx, const int32_t* xyz, int64_t n, const void* rgb_in, int32_t in_dtype,
                      void* rgb_out, int32_t out_dtype, void* stream);
 
+/* Streaming mode of Section 3 (2): the noise estimate and the selection run
+ * on some frames only, and the other frames reuse the q of the previous one.
+ * This call builds the graph of the new frame (Section 2.2) and filters it
+ * (Eq. 5) with the q this context selected last (fgbd_select_filter or
+ * fgbd_run), read on the device: no host synchronisation.  The estimate,
+ * FSLR and the q search are skipped; stats keep the last estimate's values.
+ * Arguments as fgbd_run.  Errors: FGBD_ESTATE (this context has never
+ * selected a q), FGBD_EINVAL, FGBD_ECUDA. */
+fgbd_status fgbd_run_reuse(fgbd_ctx* ctx, const int32_t* xyz, int64_t n, const void* rgb_in, int32_t in_dtype,
+                           void* rgb_out, int32_t out_dtype, void* stream);
+
 /* Batched path (no counterpart in the paper, which processes one frame at a
  * time): fgbd_run on `count` frames, frame f with its own context ctxs[f],
  * all enqueued in one call and overlapped on the GPU.  A single 1M-point frame

@@ -46,6 +46,7 @@ struct fgbd_ctx {
   int noise_dtype = -1;
   std::string err;
   uint64_t graph_gen = 0;  // incremented by every graph build
+  bool ever_selected = false;  // sc->q_sel holds a selected q (fgbd_run_reuse may use it)
   // differentiable filter: workspace (allocated by the first forward call that needs it) and the
   // state of the last forward call, which the backward call differentiates
   void* dmem = nullptr;
@@ -321,6 +322,7 @@ fgbd_status do_select(fgbd_ctx* ctx, const void* rgb, int32_t dtype, const doubl
   FGBD_LAUNCH(ctx, "filter_select", st, launch_filter(a, filter_grid_for(ctx, ctx->n), st));
   if (q_out) FGBD_CUDA(ctx, cudaMemcpyAsync(q_out, &ctx->sc->q_sel, sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
   ctx->has_sel = true;
+  ctx->ever_selected = true;
   return FGBD_OK;
 }
 
@@ -520,6 +522,28 @@ fgbd_status fgbd_run(fgbd_ctx* ctx, const int32_t* xyz, int64_t n, const void* r
   s = do_estimate(ctx, rgb_in, in_dtype, nullptr, st);
   if (s != FGBD_OK) return s;
   return do_select(ctx, rgb_in, in_dtype, nullptr, nullptr, rgb_out, out_dtype, st);
+}
+
+fgbd_status fgbd_run_reuse(fgbd_ctx* ctx, const int32_t* xyz, int64_t n, const void* rgb_in, int32_t in_dtype,
+                           void* rgb_out, int32_t out_dtype, void* stream) {
+  if (!ctx) return FGBD_EINVAL;
+  if (!dtype_ok(in_dtype) || !dtype_ok(out_dtype)) return FGBD_EINVAL;
+  if (n > 0 && (!rgb_in || !rgb_out)) return FGBD_EINVAL;
+  if (!ctx->ever_selected) return FGBD_ESTATE;
+  DeviceGuard g(ctx->device);
+  const cudaStream_t st = as_stream(stream);
+  const fgbd_status s = do_build(ctx, xyz, n, st);
+  if (s != FGBD_OK) return s;
+  if (ctx->n > 0)
+    FGBD_LAUNCH(ctx, "gather_colors", st,
+                launch_gather_colors(rgb_in, in_dtype, ctx->n, ctx->gb.perm1, ctx->y8, ctx->yf, st));
+  cudaError_t e = cudaSuccess;
+  zero_region(ctx, offsetof(DevScalars, ysq_keep), offsetof(DevScalars, sel_end_), st, &e);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "memset");
+  FilterArgs a = filter_args(ctx, 1, 0, nullptr, rgb_out, out_dtype, in_dtype);
+  a.q_src = &ctx->sc->q_sel;
+  FGBD_LAUNCH(ctx, "filter_reuse", st, launch_filter(a, filter_grid_for(ctx, ctx->n), st));
+  return FGBD_OK;
 }
 
 fgbd_status fgbd_run_batch(fgbd_ctx* const* ctxs, const int32_t* const* xyz, const int64_t* n,

@@ -138,6 +138,7 @@ struct FilterArgs {
   int dtype;             // colours held in y8 (0) or yf (1)
   int mode;              // 0: select q (Eq. 6), 1: fixed q
   int q_fixed;           // mode 1
+  const int32_t* q_src;  // mode 1: if set, q is read here on the device (and q_sel is left as it is)
   int q_max;             // mode 0
   double fslr_factor;
   int all_points;        // Eq. 6 over every point (the limited region is off)

@@ -182,7 +182,8 @@ __global__ void __launch_bounds__(kFilterThreads) k_filter(FilterArgs a) {
   double J_prev = sigma * sigma;  // J(0): nothing filtered yet
   if (select && gtid == 0) sc->J[0] = J_prev;
   int q_final = 0;
-  const int q_limit = n == 0 ? 0 : (select ? a.q_max : a.q_fixed);
+  const int q_fixed = a.q_src ? min(max(*a.q_src, 0), kQCap) : a.q_fixed;
+  const int q_limit = n == 0 ? 0 : (select ? a.q_max : q_fixed);
   for (int t = 1; t <= q_limit; ++t) {
     const float4* __restrict__ src = (t & 1) ? a.xbuf0 : a.xbuf1;
     float4* __restrict__ dst = (t & 1) ? a.xbuf1 : a.xbuf0;
@@ -263,7 +264,7 @@ __global__ void __launch_bounds__(kFilterThreads) k_filter(FilterArgs a) {
       q_final = t;
     }
   }
-  if (gtid == 0) {
+  if (gtid == 0 && !a.q_src) {
     sc->q_sel = q_final;
     if (select) sc->sel_valid = 1;
     if (select && q_limit == 0) sc->n_J = 1;

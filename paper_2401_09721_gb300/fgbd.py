@@ -102,6 +102,7 @@ _SIGS = {
     "fgbd_select_filter": (ctypes.c_int, [_P, _P, ctypes.c_int32, _P, _P, _P]),
     "fgbd_denoise": (ctypes.c_int, [_P, _P, ctypes.c_int32, ctypes.c_int32, _P, ctypes.c_int32, _P]),
     "fgbd_run": (ctypes.c_int, [_P, _P, ctypes.c_int64, _P, ctypes.c_int32, _P, ctypes.c_int32, _P]),
+    "fgbd_run_reuse": (ctypes.c_int, [_P, _P, ctypes.c_int64, _P, ctypes.c_int32, _P, ctypes.c_int32, _P]),
     "fgbd_run_batch": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(ctypes.c_int64),
                                       ctypes.POINTER(_P), ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(_P),
                                       ctypes.POINTER(ctypes.c_int32), ctypes.c_int32, _P]),
@@ -237,6 +238,17 @@ def fgbd_run(ctx, xyz: torch.Tensor, rgb_in: torch.Tensor, rgb_out: torch.Tensor
     _need_cuda(rgb_out, "rgb_out", n)
     _check(lib().fgbd_run(ctx, _ptr(xyz), n, _ptr(rgb_in), _dtype_code(rgb_in), _ptr(rgb_out),
                           _dtype_code(rgb_out), _stream(stream)), "fgbd_run", ctx)
+
+
+def fgbd_run_reuse(ctx, xyz: torch.Tensor, rgb_in: torch.Tensor, rgb_out: torch.Tensor, stream=None) -> None:
+    if xyz.dtype != torch.int32:
+        raise TypeError("xyz must be int32")
+    n = xyz.shape[0]
+    _need_cuda(xyz, "xyz", n)
+    _need_cuda(rgb_in, "rgb_in", n)
+    _need_cuda(rgb_out, "rgb_out", n)
+    _check(lib().fgbd_run_reuse(ctx, _ptr(xyz), n, _ptr(rgb_in), _dtype_code(rgb_in), _ptr(rgb_out),
+                                _dtype_code(rgb_out), _stream(stream)), "fgbd_run_reuse", ctx)
 
 
 BATCH_MAX = 64  # FGBD_BATCH_MAX
@@ -426,6 +438,14 @@ class Context:
 
     def sync(self, stream=None):
         fgbd_sync(self.handle, stream)
+
+    def run_reuse(self, xyz, rgb_in, out_dtype=torch.float32, out=None, stream=None):
+        """Build this frame's graph and filter it with the last selected q (streaming mode)."""
+        if out is None:
+            out = torch.empty((xyz.shape[0], 3), dtype=out_dtype, device=self.device)
+        fgbd_run_reuse(self.handle, xyz, rgb_in, out, stream)
+        self.n = xyz.shape[0]
+        return out
 
     def filter(self, rgb, alpha=0.5, sigma=0.0, q=1, checkpoint=1):
         """Differentiable filter on this context's graph (GraphFilter)."""

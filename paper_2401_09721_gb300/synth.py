@@ -343,3 +343,62 @@ def tuning_pairs(count: int = 8, n: int = 300_000, sigma: float = 30.0, seed: in
         noisy = add_noise_f32(clean, sigma, s)
         frames.append(Frame(xyz, clean, noisy, sigma, bits, f"sphere{n}_b{bits}_s{sigma:g}_pair{k}"))
     return frames
+
+
+class StreamSequence:
+    """A moving, jittered sphere for the streaming mode: frame t of `frames`.
+
+    The base is `samples` points on a sphere of radius 0.35 (in units of the
+    grid side) around the grid centre.  Frame t rotates it by t * omega about
+    a random axis (omega ~ U[0.2, 0.5] degrees per frame), translates it by
+    40 sin(2 pi t / frames) * d voxels of a 2^10 grid (d a random unit vector;
+    at most about 0.84 voxel per frame), voxelizes at `bits` bits, adds an integer jitter in
+    {-1, 0, 1} to each coordinate and drops repeated voxels.  Colour: the smooth
+    field of ``smooth_colors`` with every phase advanced by 2 pi t / frames;
+    uint8 noise of the given sigma.  Everything is seeded by (seed, t).
+    """
+
+    def __init__(self, frames: int = 300, samples: int = 1_150_000, bits: int = 10, sigma: float = 25.0,
+                 seed: int = 0):
+        self.frames, self.bits, self.sigma, self.seed = frames, bits, sigma, seed
+        rng = np.random.default_rng(seed)
+        v = rng.standard_normal((samples, 3))
+        self.base = v / np.linalg.norm(v, axis=1, keepdims=True) * 0.35
+        axis = rng.standard_normal(3)
+        self.axis = axis / np.linalg.norm(axis)
+        self.omega = np.deg2rad(rng.uniform(0.2, 0.5))
+        d = rng.standard_normal(3)
+        self.dir = d / np.linalg.norm(d)
+        crng = np.random.default_rng(seed + 7919)
+        self.w = crng.uniform(-3.0, 3.0, size=(3, 3, 3))      # [channel, k, xyz]
+        self.phi = crng.uniform(0.0, 2.0 * np.pi, size=(3, 3))
+
+    def _rotation(self, angle):
+        k = self.axis
+        K = np.array([[0, -k[2], k[1]], [k[2], 0, -k[0]], [-k[1], k[0], 0]])
+        return np.eye(3) + np.sin(angle) * K + (1 - np.cos(angle)) * (K @ K)
+
+    def frame(self, t: int) -> Frame:
+        side = 1 << self.bits
+        rng = np.random.default_rng([self.seed, t])
+        p = self.base @ self._rotation(t * self.omega).T
+        shift = 40.0 * (side / 1024.0) * np.sin(2 * np.pi * t / self.frames) * self.dir
+        g = np.floor((p + 0.5) * side + shift).astype(np.int64)
+        g += rng.integers(-1, 2, size=g.shape)
+        np.clip(g, 0, side - 1, out=g)
+        lin = np.sort(np.ravel_multi_index((g[:, 0], g[:, 1], g[:, 2]), (side, side, side)))
+        lin = lin[np.concatenate(([True], lin[1:] != lin[:-1]))]   # drop repeated voxels
+        gx, gy, gz = np.unravel_index(lin, (side, side, side))
+        xyz = np.stack([gx, gy, gz], axis=1).astype(np.int32)
+        xyz = np.ascontiguousarray(xyz[rng.permutation(xyz.shape[0])])
+        gf = xyz.astype(np.float64) / side
+        phase = 2 * np.pi * t / self.frames
+        clean = np.empty(xyz.shape, dtype=np.float64)
+        for c in range(3):
+            acc = np.full(xyz.shape[0], 127.5)
+            for k in range(3):
+                acc += 40.0 * np.sin(2 * np.pi * (gf @ self.w[c, k]) + self.phi[c, k] + phase)
+            clean[:, c] = acc
+        clean = np.clip(np.rint(clean), 0, 255).astype(np.uint8)
+        noisy = add_noise_u8(clean, self.sigma, self.seed * 100003 + t)
+        return Frame(xyz, clean, noisy, self.sigma, self.bits, f"stream{t}_n{xyz.shape[0]}")
