@@ -364,12 +364,13 @@ def algorithmic_bytes(name, n, q_iters=0, out_bytes=3):
     per_point = {
         "slg_hist": 12,                                   # xyz
         # digit counts: the keys of the pass (pass 0 reads xyz)
-        "slg_counts0": 12, "slg_counts1": 4, "slg_counts2": 4, "slg_counts3": 4, "slg_counts4": 4,
+        "slg_counts0": 12, "slg_counts1": 4, "slg_counts2": 4,
         # scatter: keys and values in, keys and values (or the final arrays) out.
-        # pass 2 ends C1 (packed codes, orders, ranks), pass 3 reads the codes
-        # only and writes keys, the C2 order and the C2 ranks, pass 4 the C3 order
-        "slg_scatter0": 12 + 8, "slg_scatter1": 8 + 8, "slg_scatter2": 8 + 12,
-        "slg_scatter3": 4 + 12, "slg_scatter4": 8 + 4,
+        # pass 0 (y-slabs) reads xyz; the slab sort reads the y-ordered pairs and
+        # writes the C3 order; pass 1 (C1 on z) writes packed codes, orders and
+        # ranks; pass 2 (C2 on x) reads the codes only and writes the C2 order
+        # and the C2 ranks
+        "slg_scatter0": 12 + 8, "slg_slab": 8 + 8, "slg_scatter1": 8 + 12, "slg_scatter2": 4 + 8,
         "slg_link": 40,
         "gather_colors": 11,
         "ne_moments": 28,

@@ -264,18 +264,19 @@ fgbd_status do_build(fgbd_ctx* ctx, const int32_t* xyz, int64_t n64, cudaStream_
   zero_region(ctx, offsetof(DevScalars, n_edges), offsetof(DevScalars, build_end_), st, &e);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "memset");
   if (n > 0) {
-    // kernel names carry the pass: 0-2 = C1 on x, y, z; 3-4 = C2 and C3
-    static const char* const kCounts[kSlgPasses] = {"slg_counts0", "slg_counts1", "slg_counts2", "slg_counts3",
-                                                    "slg_counts4"};
-    static const char* const kScan[kSlgPasses] = {"slg_scan0", "slg_scan1", "slg_scan2", "slg_scan3", "slg_scan4"};
-    static const char* const kScatter[kSlgPasses] = {"slg_scatter0", "slg_scatter1", "slg_scatter2",
-                                                     "slg_scatter3", "slg_scatter4"};
+    // kernel names carry the pass: 0 = y-slabs, 1 = C1 (on z, over C3), 2 = C2 (on x, over C1)
+    static const char* const kCounts[kSlgPasses] = {"slg_counts0", "slg_counts1", "slg_counts2"};
+    static const char* const kScan[kSlgPasses] = {"slg_scan0", "slg_scan1", "slg_scan2"};
+    static const char* const kScatter[kSlgPasses] = {"slg_scatter0", "slg_scatter1", "slg_scatter2"};
     FGBD_LAUNCH(ctx, "slg_hist", st, launch_coord_hist(xyz, n, bits, ctx->sc, ctx->num_sms, st));
     for (int p = 0; p < kSlgPasses; ++p) {
       const SortPassArgs a = slg_pass_args(p, xyz, n, bits, int(ctx->capacity), ctx->sb, ctx->gb, ctx->sc);
       FGBD_LAUNCH(ctx, kCounts[p], st, launch_tile_counts(a, st));
       FGBD_LAUNCH(ctx, kScan[p], st, launch_tile_scan(a, st));
       FGBD_LAUNCH(ctx, kScatter[p], st, launch_sort_scatter(a, st));
+      if (p == 0)
+        FGBD_LAUNCH(ctx, "slg_slab", st,
+                    launch_slab_sort(n, bits, int(ctx->capacity), ctx->sb, ctx->gb, ctx->sc, st));
     }
     FGBD_LAUNCH(ctx, "slg_link", st, launch_link(n, bits, int(ctx->capacity), ctx->gb, ctx->sc, ctx->num_sms, st));
   }

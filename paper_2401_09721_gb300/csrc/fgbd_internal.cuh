@@ -21,7 +21,7 @@ constexpr int kMaxRadix = 1 << kMaxBits;           // radix passes use one coord
 constexpr int kSortThreads = 256;
 constexpr int kSortKpt = 16;                       // keys per thread
 constexpr int kSortTile = kSortThreads * kSortKpt;  // 4096 keys per tile
-constexpr int kSlgPasses = 5;                      // 3 for C1, 2 for C2 and C3 together
+constexpr int kSlgPasses = 3;                      // y-slabs (then the slab sort: C3), C1, C2
 constexpr int kK = 6;                              // neighbours per point at window 1
 constexpr int kD = 3 * (kK + 1);                   // patch dimension (Section 2.3)
 constexpr int kQCap = 256;                         // largest q_max accepted
@@ -85,7 +85,7 @@ struct GraphBufs {
   int32_t* perm1;    // [cap] input index of each sorted (C1-order) point
   int32_t* rank1;    // [cap] sorted id of each input point
   uint32_t* pk;      // [cap] packed C1 code of each sorted point (its coordinates)
-  int32_t* ord23;    // [2][cap] sorted ids along C2 and along C3
+  int32_t* ord23;    // [2][cap] sorted ids along C2; input indices along C3
   int32_t* rank2;    // [cap] position of each sorted id in the C2 order
   int4* c4;          // [cap] C2 prev, C2 next, C3 prev, C3 next (sorted ids, -1 empty)
 };
@@ -111,9 +111,13 @@ struct SortPassArgs {
 // Every launcher enqueues on `stream` and returns the launch error.
 
 cudaError_t launch_coord_hist(const int32_t* xyz, int n, int bits, DevScalars* sc, int num_sms, cudaStream_t stream);
-// pass 0..2: C1 on x, y, z; pass 3: C2 = the C1 order on x; pass 4: C3 = the C2 order on y
+// pass 0: y-slabs from the input; (the slab sort then gives C3); pass 1: C1 = the C3 order on z;
+// pass 2: C2 = the C1 order on x
 SortPassArgs slg_pass_args(int pass, const int32_t* xyz, int n, int bits, int cap, const SortBufs& sb,
                            const GraphBufs& gb, const DevScalars* sc);
+// C3 within each y-slab (after pass 0): (x, z) order into keys[1] and ord23[1]
+cudaError_t launch_slab_sort(int n, int bits, int cap, const SortBufs& sb, const GraphBufs& gb,
+                             const DevScalars* sc, cudaStream_t stream);
 cudaError_t launch_tile_counts(const SortPassArgs& a, cudaStream_t stream);
 cudaError_t launch_tile_scan(const SortPassArgs& a, cudaStream_t stream);
 cudaError_t launch_sort_scatter(const SortPassArgs& a, cudaStream_t stream);

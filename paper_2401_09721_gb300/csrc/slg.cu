@@ -1,24 +1,26 @@
 // SLG: scan-line graph construction (Section 2.2).
 //
 // Sorting by a code of Eq. 1-3 is sorting by three b-bit coordinates, most
-// significant first, so a least-significant-digit radix sort whose digits are
-// the coordinates needs three passes of 2^b bins:
-//   C1 = (z, y, x): passes on x, then y, then z, from the input order;
+// significant first.  The digits of the radix passes are the coordinates
+// themselves (2^b bins):
+//   C1 = (z, y, x): one stable pass on z (most significant digit first) puts
+//        every z-slab in place; k_slab_sort then sorts each slab by (y, x) in
+//        shared memory, one block per slab: two stable passes, x then y;
 //   C2 = (x, z, y): one stable pass on x over the C1 order (among points
 //        with equal x the C1 order already ranks them by (z, y));
 //   C3 = (y, x, z): one stable pass on y over the C2 order (among points
 //        with equal y the C2 order ranks them by (x, z)).
 // Ties keep input order throughout, so equal codes are ordered by index.  The
 // digit totals of every pass are the three coordinate histograms, taken once
-// (k_coord_hist).  Each pass is reduce-then-scan:
+// (k_coord_hist).  Each global pass is reduce-then-scan:
 //   k_tile_counts   digit counts of every 4096-key tile;
 //   k_tile_scan     each tile's global start of every digit;
 //   k_sort_scatter  stable in-tile rank (one ballot per digit bit) and
 //                   write-out in digit runs.
-// The C1 passes carry (code, input index) and end with the packed C1 code of
-// every sorted point, its input index and the rank of every input point; the
-// C2/C3 passes carry (code, sorted id) and end with the sorted ids along C2
-// and C3 and the C2 rank of every sorted id.
+// The C1 step ends with the packed C1 code of every sorted point, its input
+// index and the rank of every input point; the C2/C3 passes carry (code,
+// sorted id) and end with the sorted ids along C2 and C3 and the C2 rank of
+// every sorted id.
 // k_link: points consecutive along a code are linked.  In C1 order the code-1
 // neighbours are implicit (k-1, k+1); C2/C3 neighbours are written as slots;
 // a pair already linked by an earlier code is left out so the union is a set,
@@ -299,8 +301,246 @@ __global__ void __launch_bounds__(kScatterThreads, 2) k_sort_scatter(SortPassArg
   }
 }
 
+// ---------------------------------------------------------------- slab sort
+// One block per y-slab of the y-sorted (code, input index) pairs: sort the
+// slab by (x, z) with two stable passes (z, then x), which gives the C3
+// order.  A slab of up to kSlabMax points is held in shared memory and
+// ranked kSlabKpt rounds per warp; warp w owns the contiguous positions
+// [w C, (w + 1) C), so warp order is position order and the ballot ranks
+// inside a warp keep lane order.  A larger slab (a cloud with very many points
+// in one plane) takes the same ranking through global memory, kSlabThreads
+// points at a time, with running digit offsets carried from chunk to chunk.
+constexpr int kSlabThreads = 256;
+constexpr int kSlabWarps = kSlabThreads / 32;
+constexpr int kSlabKpt = 8;
+constexpr int kSlabMax = kSlabThreads * kSlabKpt;  // 4096 points
+constexpr int kSlabPairWords = kSlabWarps / 2;    // digit counter words (two warps each)
+constexpr int kSlabDigits = kMaxRadix / kSlabThreads;  // digits owned by each thread
+
+size_t slab_smem_bytes() {
+  return sizeof(uint32_t) * (size_t(kSlabPairWords) * kMaxRadix + 2 * size_t(kSlabMax) + kMaxRadix + kSlabWarps + 4);
+}
+
+// exclusive scan of one value per thread over the 1024-thread block
+__device__ __forceinline__ uint32_t slab_block_scan(uint32_t v, uint32_t* s_warp, uint32_t* total) {
+  static_assert(kSlabWarps <= 32, "one warp scans the warp totals");
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint32_t x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) s_warp[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    const uint32_t w = lane < kSlabWarps ? s_warp[lane] : 0u;
+    uint32_t wx = w;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, wx, o);
+      if (lane >= o) wx += y;
+    }
+    if (lane < kSlabWarps) s_warp[lane] = wx - w;
+    if (lane == 31 && total) *total = wx;
+  }
+  __syncthreads();
+  const uint32_t r = s_warp[warp] + x - v;
+  __syncthreads();
+  return r;
+}
+
+// Stable rank of one key among the equal digits of its warp (lanes in order),
+// added to the warp's digit counter (16-bit half `half` of the pair word).
+__device__ __forceinline__ uint32_t warp_rank(bool valid, uint32_t d, int bits, uint32_t* wh, int half, int lane) {
+  uint32_t peers = __ballot_sync(0xffffffffu, valid);
+  for (int b = 0; b < bits; ++b) {
+    const bool bit = (d >> b) & 1u;
+    const uint32_t on = __ballot_sync(0xffffffffu, bit);
+    peers &= bit ? on : ~on;
+  }
+  const int leader = peers ? __ffs(peers) - 1 : lane;
+  uint32_t old = 0;
+  if (valid && lane == leader) old = (atomicAdd(&wh[d], uint32_t(__popc(peers)) << half) >> half) & 0xffffu;
+  return __shfl_sync(0xffffffffu, old, leader) + __popc(peers & ((1u << lane) - 1u));
+}
+
+// For digit d (one per thread): the counters of the warps become their
+// exclusive offsets; returns the digit's total.
+__device__ __forceinline__ uint32_t digit_warp_offsets(uint32_t* cnt, int radix, int d) {
+  uint32_t run = 0;
+  if (d < radix) {
+#pragma unroll
+    for (int w = 0; w < kSlabPairWords; ++w) {
+      const uint32_t c = cnt[w * radix + d];
+      const uint32_t lo = c & 0xffffu, hi = c >> 16;
+      cnt[w * radix + d] = run | ((run + lo) << 16);
+      run += lo + hi;
+    }
+  }
+  return run;
+}
+
+__global__ void __launch_bounds__(kSlabThreads, 4)
+    k_slab_sort(int n, int bits, const uint32_t* __restrict__ keys_in, const uint32_t* __restrict__ vals_in,
+                uint32_t* __restrict__ keys_tmp, uint32_t* __restrict__ vals_tmp, uint32_t* __restrict__ keys_out,
+                int32_t* __restrict__ vals_out, const DevScalars* __restrict__ sc) {
+  extern __shared__ uint32_t smem[];
+  uint32_t* cnt = smem;                                   // [kSlabPairWords][radix]
+  uint32_t* s_keys = cnt + kSlabPairWords * kMaxRadix;    // [kSlabMax]
+  uint32_t* s_vals = s_keys + kSlabMax;                   // [kSlabMax]
+  uint32_t* s_start = s_vals + kSlabMax;                  // [radix]
+  uint32_t* s_warp = s_start + kMaxRadix;                 // [kSlabWarps]
+  uint32_t* s_misc = s_warp + kSlabWarps;                 // [4]
+
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int radix = 1 << bits;
+  const uint32_t m = uint32_t(radix) - 1u;
+  const int yv = blockIdx.x;
+  const uint32_t* hy = sc->chist[1];
+  const uint32_t size = hy[yv];
+  if (size == 0) return;
+  // the slab starts after every point of a smaller y
+  uint32_t below = 0;
+  for (int e = tid; e < yv; e += kSlabThreads) below += hy[e];
+  slab_block_scan(below, s_warp, &s_misc[0]);
+  const uint32_t start = s_misc[0];
+  if (uint64_t(start) + size > uint64_t(n)) return;  // inconsistent histogram: leave the slab alone
+  uint32_t* wh = cnt + (warp >> 1) * radix;
+  const int half = 16 * (warp & 1);
+
+  if (size <= uint32_t(kSlabMax)) {
+    for (uint32_t i = tid; i < size; i += kSlabThreads) {
+      s_keys[i] = keys_in[start + i];
+      s_vals[i] = vals_in[start + i];
+    }
+    const int chunk = int((size + 32 * kSlabWarps - 1) / (32 * kSlabWarps)) * 32;  // positions per warp
+    const int rounds = chunk / 32;                                                 // <= kSlabKpt
+    for (int pass = 0; pass < 2; ++pass) {
+      const int shift = pass == 0 ? 2 * bits : 0;  // z, then x
+      for (int i = tid; i < kSlabPairWords * radix; i += kSlabThreads) cnt[i] = 0;
+      __syncthreads();
+      uint32_t k[kSlabKpt], v[kSlabKpt], rk[kSlabKpt];
+#pragma unroll
+      for (int j = 0; j < kSlabKpt; ++j) {
+        k[j] = v[j] = rk[j] = 0;
+        if (j < rounds) {
+          const uint32_t pos = uint32_t(warp * chunk + j * 32 + lane);
+          const bool valid = pos < size;
+          if (valid) {
+            k[j] = s_keys[pos];
+            v[j] = s_vals[pos];
+          }
+          rk[j] = warp_rank(valid, (k[j] >> shift) & m, bits, wh, half, lane);
+          __syncwarp();
+        }
+      }
+      __syncthreads();
+      // each thread owns kSlabDigits consecutive digits
+      uint32_t tot[kSlabDigits], own = 0;
+#pragma unroll
+      for (int i = 0; i < kSlabDigits; ++i) {
+        tot[i] = digit_warp_offsets(cnt, radix, kSlabDigits * tid + i);
+        own += tot[i];
+      }
+      uint32_t ts = slab_block_scan(own, s_warp, nullptr);
+#pragma unroll
+      for (int i = 0; i < kSlabDigits; ++i) {
+        if (kSlabDigits * tid + i < radix) s_start[kSlabDigits * tid + i] = ts;
+        ts += tot[i];
+      }
+      __syncthreads();
+#pragma unroll
+      for (int j = 0; j < kSlabKpt; ++j) {
+        if (j < rounds) {
+          const uint32_t pos = uint32_t(warp * chunk + j * 32 + lane);
+          if (pos < size) {
+            const uint32_t d = (k[j] >> shift) & m;
+            const uint32_t lp = s_start[d] + ((wh[d] >> half) & 0xffffu) + rk[j];
+            if (lp < size) {
+              s_keys[lp] = k[j];
+              s_vals[lp] = v[j];
+            }
+          }
+        }
+      }
+      __syncthreads();
+    }
+    for (uint32_t i = tid; i < size; i += kSlabThreads) {
+      keys_out[start + i] = s_keys[i];
+      vals_out[start + i] = int32_t(s_vals[i]);
+    }
+    return;
+  }
+
+  // ---- a slab larger than shared memory: the same passes, 1024 points at a
+  // time, through global memory (pass 0 into the scratch arrays, pass 1 into
+  // the final arrays)
+  for (int pass = 0; pass < 2; ++pass) {
+    const int shift = pass == 0 ? 2 * bits : 0;  // z, then x
+    const uint32_t* ks = pass == 0 ? keys_in : keys_tmp;
+    const uint32_t* vs = pass == 0 ? vals_in : vals_tmp;
+    // digit histogram of the slab, then each digit's first position
+    for (int d = tid; d < radix; d += kSlabThreads) s_start[d] = 0;
+    __syncthreads();
+    for (uint32_t i = tid; i < size; i += kSlabThreads) atomicAdd(&s_start[(ks[start + i] >> shift) & m], 1u);
+    __syncthreads();
+    // thread t: the next free positions of its kSlabDigits digits
+    uint32_t run[kSlabDigits], own = 0;
+#pragma unroll
+    for (int i = 0; i < kSlabDigits; ++i) {
+      run[i] = kSlabDigits * tid + i < radix ? s_start[kSlabDigits * tid + i] : 0u;
+      own += run[i];
+    }
+    {
+      uint32_t r0 = slab_block_scan(own, s_warp, nullptr);
+#pragma unroll
+      for (int i = 0; i < kSlabDigits; ++i) {
+        const uint32_t h = run[i];
+        run[i] = r0;
+        r0 += h;
+      }
+    }
+    for (uint32_t c0 = 0; c0 < size; c0 += kSlabThreads) {
+      for (int i = tid; i < kSlabPairWords * radix; i += kSlabThreads) cnt[i] = 0;
+#pragma unroll
+      for (int i = 0; i < kSlabDigits; ++i)
+        if (kSlabDigits * tid + i < radix) s_start[kSlabDigits * tid + i] = run[i];
+      __syncthreads();
+      const uint32_t pos = c0 + uint32_t(tid);
+      const bool valid = pos < size;
+      const uint32_t key = valid ? ks[start + pos] : 0u, val = valid ? vs[start + pos] : 0u;
+      const uint32_t d = (key >> shift) & m;
+      const uint32_t rk = warp_rank(valid, d, bits, wh, half, lane);
+      __syncthreads();
+      uint32_t tot[kSlabDigits];
+#pragma unroll
+      for (int i = 0; i < kSlabDigits; ++i) tot[i] = digit_warp_offsets(cnt, radix, kSlabDigits * tid + i);
+      __syncthreads();
+      if (valid) {
+        const uint32_t lp = s_start[d] + ((wh[d] >> half) & 0xffffu) + rk;
+        if (lp < size) {
+          const uint32_t g = start + lp;
+          if (pass == 0) {
+            keys_tmp[g] = key;
+            vals_tmp[g] = val;
+          } else {
+            keys_out[g] = key;
+            vals_out[g] = int32_t(val);
+          }
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < kSlabDigits; ++i) run[i] += tot[i];
+      __syncthreads();
+    }
+    __syncthreads();
+  }
+}
+
 // One thread per position r of one code's order (blockIdx.y = code).  Code 0
-// is the C1 order itself; codes 1 and 2 read the sorted ids along C2 and C3.
+// is the C1 order itself; code 1 reads the sorted ids along C2, code 2 the
+// input indices along C3 (mapped to sorted ids through rank1).
 // The ids at r-1 and r+1 come from the adjacent lanes, with one extra lookup
 // at each end of the warp.
 struct LinkPt {
@@ -310,10 +550,12 @@ struct LinkPt {
 };
 
 __device__ __forceinline__ LinkPt link_point(int r, int n, int code, const int32_t* __restrict__ ord,
-                                             const int32_t* __restrict__ rank2, const uint32_t* __restrict__ pk) {
+                                             const int32_t* __restrict__ rank1, const int32_t* __restrict__ rank2,
+                                             const uint32_t* __restrict__ pk) {
   LinkPt q{-1, -1, 0u};
   if (r < 0 || r >= n) return q;
-  const int k = code == 0 ? r : ord[r];
+  int k = code == 0 ? r : ord[r];
+  if (code == 2) k = in_range(k, n) ? rank1[k] : -1;
   if (!in_range(k, n)) return q;
   q.k = k;
   q.c = pk[k];
@@ -322,8 +564,9 @@ __device__ __forceinline__ LinkPt link_point(int r, int n, int code, const int32
 }
 
 __global__ void __launch_bounds__(256) k_link(int n, int bits, int cap, const int32_t* __restrict__ ord23,
-                                              const int32_t* __restrict__ rank2, const uint32_t* __restrict__ pk,
-                                              int4* __restrict__ c4, DevScalars* __restrict__ sc) {
+                                              const int32_t* __restrict__ rank1, const int32_t* __restrict__ rank2,
+                                              const uint32_t* __restrict__ pk, int4* __restrict__ c4,
+                                              DevScalars* __restrict__ sc) {
   __shared__ unsigned long long s_red[8];
   const int code = blockIdx.y;
   const int lane = threadIdx.x & 31;
@@ -334,7 +577,7 @@ __global__ void __launch_bounds__(256) k_link(int n, int bits, int cap, const in
   // whole warps step together so the shuffles see every lane
   for (int base = blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < n; base += stride) {
     const int r = base + lane;
-    const LinkPt me = link_point(r, n, code, ord, rank2, pk);
+    const LinkPt me = link_point(r, n, code, ord, rank1, rank2, pk);
     LinkPt prev, next;
     prev.k = __shfl_up_sync(0xffffffffu, me.k, 1);
     prev.r2 = __shfl_up_sync(0xffffffffu, me.r2, 1);
@@ -342,8 +585,8 @@ __global__ void __launch_bounds__(256) k_link(int n, int bits, int cap, const in
     next.k = __shfl_down_sync(0xffffffffu, me.k, 1);
     next.r2 = __shfl_down_sync(0xffffffffu, me.r2, 1);
     next.c = __shfl_down_sync(0xffffffffu, me.c, 1);
-    if (lane == 0) prev = link_point(r - 1, n, code, ord, rank2, pk);
-    if (lane == 31) next = link_point(r + 1, n, code, ord, rank2, pk);
+    if (lane == 0) prev = link_point(r - 1, n, code, ord, rank1, rank2, pk);
+    if (lane == 31) next = link_point(r + 1, n, code, ord, rank1, rank2, pk);
     if (me.k < 0) continue;
     // the edge to the next position: counted once, unless an earlier code links the pair
     bool dup_next = true;
@@ -373,17 +616,16 @@ __global__ void __launch_bounds__(256) k_link(int n, int bits, int cap, const in
   }
 }
 
-// The three orders in input indices: C1 from perm1, C2 and C3 through perm1.
+// The three orders in input indices: C1 from perm1, C2 through perm1, C3 as held.
 __global__ void __launch_bounds__(256) k_orders_export(int n, int cap, const int32_t* __restrict__ perm1,
                                                        const int32_t* __restrict__ ord23, int32_t* __restrict__ out) {
   const int stride = gridDim.x * blockDim.x;
   for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += stride) {
     out[r] = perm1[r];
-#pragma unroll
-    for (int c = 0; c < 2; ++c) {
-      const int k = ord23[size_t(c) * size_t(cap) + r];
-      out[size_t(c + 1) * size_t(n) + r] = in_range(k, n) ? perm1[k] : -1;
-    }
+    const int k = ord23[r];
+    out[size_t(n) + r] = in_range(k, n) ? perm1[k] : -1;
+    const int i = ord23[size_t(cap) + r];
+    out[2 * size_t(n) + r] = in_range(i, n) ? i : -1;
   }
 }
 
@@ -429,11 +671,31 @@ cudaError_t launch_sort_pass(const SortPassArgs& a, cudaStream_t stream) {
   return e;
 }
 
+cudaError_t launch_slab_sort(int n, int bits, int cap, const SortBufs& sb, const GraphBufs& gb,
+                             const DevScalars* sc, cudaStream_t stream) {
+  if (n <= 0) return cudaSuccess;
+  static unsigned long long configured = 0;  // the shared-memory limit is set once per device
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const unsigned long long bit = 1ull << (dev & 63);
+  if (!(configured & bit)) {
+    e = cudaFuncSetAttribute(k_slab_sort, cudaFuncAttributeMaxDynamicSharedMemorySize, int(slab_smem_bytes()));
+    if (e != cudaSuccess) return e;
+    configured |= bit;
+  }
+  // scratch for slabs larger than shared memory: the C2 order and C2 ranks, written later
+  k_slab_sort<<<1 << bits, kSlabThreads, slab_smem_bytes(), stream>>>(
+      n, bits, sb.keys[0], sb.vals[0], reinterpret_cast<uint32_t*>(gb.ord23), reinterpret_cast<uint32_t*>(gb.rank2),
+      sb.keys[1], gb.ord23 + size_t(cap), sc);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_link(int n, int bits, int cap, const GraphBufs& gb, DevScalars* sc, int num_sms,
                         cudaStream_t stream) {
   if (n <= 0) return cudaSuccess;
   const int gx = std::max(1, std::min((n + 255) / 256, num_sms * 8));
-  k_link<<<dim3(gx, 3), 256, 0, stream>>>(n, bits, cap, gb.ord23, gb.rank2, gb.pk, gb.c4, sc);
+  k_link<<<dim3(gx, 3), 256, 0, stream>>>(n, bits, cap, gb.ord23, gb.rank1, gb.rank2, gb.pk, gb.c4, sc);
   return cudaGetLastError();
 }
 
@@ -452,38 +714,34 @@ SortPassArgs slg_pass_args(int pass, const int32_t* xyz, int n, int bits, int ca
   a.tiles = (n + kSortTile - 1) / kSortTile;
   a.counts = sb.tile_counts;
   a.sc = sc;
-  if (pass < 3) {
-    // C1: digits x, y, z; keys are packed C1 codes (x lowest), values input indices
-    a.shift = pass * bits;
-    a.coord = pass;
-    a.xyz = pass == 0 ? xyz : nullptr;
-    a.keys_in = pass == 0 ? nullptr : sb.keys[(pass - 1) & 1];
-    a.vals_in = pass == 0 ? nullptr : sb.vals[(pass - 1) & 1];
-    const bool last = pass == 2;
-    a.keys_out = last ? gb.pk : sb.keys[pass & 1];
-    a.vals_out = last ? reinterpret_cast<uint32_t*>(gb.perm1) : sb.vals[pass & 1];
-    a.rank_out = last ? gb.rank1 : nullptr;
-    return a;
-  }
-  if (pass == 3) {
-    // C2: the C1 order (value = position = sorted id) on x
-    a.shift = 0;
-    a.coord = 0;
-    a.keys_in = gb.pk;
-    a.vals_in = nullptr;
+  if (pass == 0) {
+    // y-slabs: keys are packed C1 codes, values input indices
+    a.shift = bits;
+    a.coord = 1;
+    a.xyz = xyz;
     a.keys_out = sb.keys[0];
-    a.vals_out = reinterpret_cast<uint32_t*>(gb.ord23);
-    a.rank_out = gb.rank2;
+    a.vals_out = sb.vals[0];
     return a;
   }
-  // C3: the C2 order on y
-  a.shift = bits;
-  a.coord = 1;
-  a.keys_in = sb.keys[0];
-  a.vals_in = reinterpret_cast<const uint32_t*>(gb.ord23);
+  if (pass == 1) {
+    // C1: the C3 order (from the slab sort) on z; ends with pk, perm1, rank1
+    a.shift = 2 * bits;
+    a.coord = 2;
+    a.keys_in = sb.keys[1];
+    a.vals_in = reinterpret_cast<const uint32_t*>(gb.ord23 + size_t(cap));
+    a.keys_out = gb.pk;
+    a.vals_out = reinterpret_cast<uint32_t*>(gb.perm1);
+    a.rank_out = gb.rank1;
+    return a;
+  }
+  // C2: the C1 order (value = position = sorted id) on x
+  a.shift = 0;
+  a.coord = 0;
+  a.keys_in = gb.pk;
+  a.vals_in = nullptr;
   a.keys_out = nullptr;
-  a.vals_out = reinterpret_cast<uint32_t*>(gb.ord23 + size_t(cap));
-  a.rank_out = nullptr;
+  a.vals_out = reinterpret_cast<uint32_t*>(gb.ord23);
+  a.rank_out = gb.rank2;
   return a;
 }
 

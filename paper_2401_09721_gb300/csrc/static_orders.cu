@@ -107,7 +107,8 @@ extern "C" fgbd_status fgbd_scan_orders_static(const int32_t* xyz, int64_t n64, 
     }
     // cap = n: the C2 and C3 orders lie n apart in the ord23 array
     for (int p = 0; p < kSlgPasses; ++p) {
-      if (launch_sort_pass(slg_pass_args(p, xyz, n, bits, n, sb, gb, sc), st) != cudaSuccess) {
+      if (launch_sort_pass(slg_pass_args(p, xyz, n, bits, n, sb, gb, sc), st) != cudaSuccess ||
+          (p == 0 && launch_slab_sort(n, bits, n, sb, gb, sc, st) != cudaSuccess)) {
         cudaGetLastError();
         return FGBD_ECUDA;
       }
