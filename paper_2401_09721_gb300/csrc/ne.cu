@@ -253,7 +253,7 @@ __device__ __forceinline__ bool point_patch(int k, int n, int bits, int lane, co
 // batches, then float64.  The block combines its warps through shared atomics
 // and adds its totals to the context (uint8) or writes them (float).
 template <int DT>
-__global__ void __launch_bounds__(kNeThreads)
+__global__ void __launch_bounds__(kNeThreads, 4)
     k_ne_moments(int n, int bits, const uint32_t* __restrict__ pk, const int4* __restrict__ c4,
                  const uint32_t* __restrict__ y8, const float4* __restrict__ yf,
                  float* __restrict__ spread, double* __restrict__ f64_partials, int moments,

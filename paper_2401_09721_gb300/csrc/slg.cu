@@ -47,8 +47,8 @@ size_t scatter_smem_bytes() {
          (size_t(kPairWords) * kMaxRadix + 2 * size_t(kSortTile) + 2 * size_t(kMaxRadix) + kScatterWarps + 1);
 }
 
-__global__ void __launch_bounds__(256) k_coord_hist(const int32_t* __restrict__ xyz, int n, int bits,
-                                                    DevScalars* __restrict__ sc) {
+__global__ void __launch_bounds__(1024) k_coord_hist(const int32_t* __restrict__ xyz, int n, int bits,
+                                                     DevScalars* __restrict__ sc) {
   __shared__ uint32_t h[3][kMaxRadix];
   const int radix = 1 << bits;
   for (int i = threadIdx.x; i < 3 * kMaxRadix; i += blockDim.x) (&h[0][0])[i] = 0;
@@ -633,8 +633,9 @@ __global__ void __launch_bounds__(256) k_orders_export(int n, int cap, const int
 
 cudaError_t launch_coord_hist(const int32_t* xyz, int n, int bits, DevScalars* sc, int num_sms, cudaStream_t stream) {
   if (n <= 0) return cudaSuccess;
-  const int grid = std::max(1, std::min((n + 2047) / 2048, num_sms * 4));
-  k_coord_hist<<<grid, 256, 0, stream>>>(xyz, n, bits, sc);
+  // one large block per SM: few blocks keep the global atomics of the final merge few
+  const int grid = std::max(1, std::min((n + 1023) / 1024, num_sms));
+  k_coord_hist<<<grid, 1024, 0, stream>>>(xyz, n, bits, sc);
   return cudaGetLastError();
 }
 
