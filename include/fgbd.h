@@ -163,7 +163,13 @@ fgbd_status fgbd_denoise(fgbd_ctx* ctx, const void* rgb_in, int32_t in_dtype, in
 
 /* All four steps on one frame (Section 2.1): build, estimate, select, and the
  * selected filter written to rgb_out.  Same arguments and errors as the four
- * calls it replaces; rgb_in and rgb_out must not overlap. */
+ * calls it replaces; rgb_in and rgb_out must not overlap.
+ * Repeated calls with the same arguments (buffers, n, dtypes) replay a CUDA
+ * graph of the whole run: the second such call records the kernels into a
+ * graph on the context's own stream, later ones only launch it on `stream`
+ * (the contents of the buffers may change between calls).  Up to 8 argument
+ * sets are kept per context.  Per-kernel timing (fgbd_set_timing) and a
+ * `stream` that is being captured by the caller use the kernels directly. */
 fgbd_status fgbd_run(fgbd_ctx* ctx, const int32_t* xyz, int64_t n, const void* rgb_in, int32_t in_dtype,
                      void* rgb_out, int32_t out_dtype, void* stream);
 
