@@ -18,7 +18,7 @@ CSRC = os.path.join(PKG, "csrc")
 OUT = os.path.join(PKG, "libfgbd.so")
 OBJDIR = os.path.join(PKG, "_build")
 SOURCES = ["slg.cu", "ne.cu", "filter.cu", "diff.cu", "api.cu", "static_orders.cu"]
-HEADERS = [os.path.join(CSRC, "fgbd_internal.cuh"), os.path.join(ROOT, "include", "fgbd.h"),
+HEADERS = [os.path.join(CSRC, "fgbd_internal.cuh"), os.path.join(CSRC, "filter_step.cuh"), os.path.join(ROOT, "include", "fgbd.h"),
            os.path.join(CSRC, "fgbd.map")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",

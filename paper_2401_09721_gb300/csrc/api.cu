@@ -62,6 +62,11 @@ struct fgbd_ctx {
   double d_sigma = 0.0;
   uint64_t d_gen = 0;
   bool d_valid = false;
+  // filter steps stored by the noise-estimate launch (see filter_step.cuh)
+  float4* spec_x = nullptr;   // [kSpecMax][cap]
+  int32_t* spec_z = nullptr;  // [kSpecMax][cap]
+  uint8_t* keep8 = nullptr;   // [cap]
+  int spec_depth = 0;         // steps stored for noise_rgb on the current graph (0: none)
   // fgbd_run replays: CUDA graphs of whole runs, keyed by their arguments
   struct RunKey {
     const void* xyz;
@@ -207,6 +212,11 @@ FilterArgs filter_args(fgbd_ctx* ctx, int mode, int q_fixed, const double* sigma
   a.out = out;
   a.out_dtype = out_dtype;
   a.sc = ctx->sc;
+  a.spec_depth = 0;
+  a.spec_x = ctx->spec_x;
+  a.spec_z = ctx->spec_z;
+  a.cap = int(ctx->capacity);
+  a.keep8 = ctx->keep8;
   return a;
 }
 
@@ -283,6 +293,7 @@ fgbd_status do_build(fgbd_ctx* ctx, const int32_t* xyz, int64_t n64, cudaStream_
   const int n = int(n64);
   const int bits = ctx->params.bits;
   ctx->has_graph = ctx->has_noise = ctx->has_sel = false;
+  ctx->spec_depth = 0;
   ctx->noise_rgb = nullptr;
   ctx->n = n;
   ctx->graph_gen += 1;
@@ -310,7 +321,8 @@ fgbd_status do_build(fgbd_ctx* ctx, const int32_t* xyz, int64_t n64, cudaStream_
   return FGBD_OK;
 }
 
-fgbd_status do_estimate(fgbd_ctx* ctx, const void* rgb, int32_t dtype, double* sigma_out, cudaStream_t st) {
+fgbd_status do_estimate(fgbd_ctx* ctx, const void* rgb, int32_t dtype, double* sigma_out, cudaStream_t st,
+                        bool speculate = true) {
   if (!ctx->has_graph) return FGBD_ESTATE;
   if (!dtype_ok(dtype)) return FGBD_EINVAL;
   if (ctx->n > 0 && !rgb) return FGBD_EINVAL;
@@ -329,7 +341,12 @@ fgbd_status do_estimate(fgbd_ctx* ctx, const void* rgb, int32_t dtype, double* s
                                   ctx->sc, ctx->num_sms, true,
                                   (ctx->params.variant & FGBD_VARIANT_UNSORTED_PATCH) == 0, st));
   }
-  FGBD_LAUNCH(ctx, "ne_finalize", st, launch_ne_finalize(dtype, ctx->f64part, nblocks, ctx->sc, sigma_out, st));
+  // the same launch stores the first filter steps of these colours on the other SMs
+  FilterArgs spec = filter_args(ctx, 0, 0, nullptr, nullptr, 0, dtype);
+  spec.spec_depth = speculate ? std::min(kSpecMax, int(ctx->params.q_max)) : 0;
+  FGBD_LAUNCH(ctx, "ne_finalize", st,
+              launch_ne_finalize(dtype, ctx->f64part, nblocks, ctx->sc, sigma_out, &spec, ctx->num_sms, st));
+  ctx->spec_depth = n > 0 && ctx->num_sms >= 2 ? spec.spec_depth : 0;
   ctx->has_noise = true;
   ctx->noise_rgb = rgb;
   ctx->noise_dtype = dtype;
@@ -345,7 +362,8 @@ fgbd_status do_select(fgbd_ctx* ctx, const void* rgb, int32_t dtype, const doubl
   cudaError_t e = cudaSuccess;
   zero_region(ctx, offsetof(DevScalars, ysq_keep), offsetof(DevScalars, sel_end_), st, &e);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "memset");
-  const FilterArgs a = filter_args(ctx, 0, 0, sigma_est, out, out_dtype, dtype);
+  FilterArgs a = filter_args(ctx, 0, 0, sigma_est, out, out_dtype, dtype);
+  a.spec_depth = ctx->spec_depth;  // the kernel checks that they were all stored
   FGBD_LAUNCH(ctx, "filter_select", st, launch_filter(a, filter_grid_for(ctx, ctx->n), st));
   if (q_out) FGBD_CUDA(ctx, cudaMemcpyAsync(q_out, &ctx->sc->q_sel, sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
   ctx->has_sel = true;
@@ -483,6 +501,9 @@ fgbd_status fgbd_ctx_create(int64_t capacity, const fgbd_params* params, fgbd_ct
       {reinterpret_cast<void**>(&ctx->gb.ord23), 2 * C * 4},
       {reinterpret_cast<void**>(&ctx->gb.rank2), C * 4},
       {reinterpret_cast<void**>(&ctx->gb.c4), C * 16},
+      {reinterpret_cast<void**>(&ctx->spec_x), size_t(kSpecMax) * C * 16},
+      {reinterpret_cast<void**>(&ctx->spec_z), size_t(kSpecMax) * C * 4},
+      {reinterpret_cast<void**>(&ctx->keep8), C},
       {reinterpret_cast<void**>(&ctx->y8), C * 4},
       {reinterpret_cast<void**>(&ctx->yf), C * 16},
       {reinterpret_cast<void**>(&ctx->spread), C * 4},
@@ -571,7 +592,7 @@ fgbd_status fgbd_denoise(fgbd_ctx* ctx, const void* rgb_in, int32_t in_dtype, in
   if (q < 0) {
     if (!ctx->has_sel) return FGBD_ESTATE;
     FGBD_LAUNCH(ctx, "filter_output", st,
-                launch_output(ctx->n, ctx->gb.rank1, ctx->x0, ctx->x1, ctx->sc, rgb_out, out_dtype, st));
+                launch_output(filter_args(ctx, 1, 0, nullptr, rgb_out, out_dtype, ctx->noise_dtype), st));
     return FGBD_OK;
   }
   if (q > kQCap || !dtype_ok(in_dtype)) return FGBD_EINVAL;
@@ -583,6 +604,7 @@ fgbd_status fgbd_denoise(fgbd_ctx* ctx, const void* rgb_in, int32_t in_dtype, in
   // the gathered colours and filter buffers now hold this call's data
   if (rgb_in != ctx->noise_rgb || in_dtype != ctx->noise_dtype) {
     ctx->has_noise = false;
+    ctx->spec_depth = 0;
     ctx->noise_rgb = nullptr;
   }
   ctx->has_sel = false;
@@ -676,7 +698,7 @@ fgbd_status fgbd_run_batch(fgbd_ctx* const* ctxs, const int32_t* const* xyz, con
   for (int f = 0; f < count; ++f) {
     fgbd_ctx* c = ctxs[f];
     fgbd_status s = do_build(c, xyz[f], n[f], c->side);
-    if (s == FGBD_OK) s = do_estimate(c, rgb_in[f], in_dtype[f], nullptr, c->side);
+    if (s == FGBD_OK) s = do_estimate(c, rgb_in[f], in_dtype[f], nullptr, c->side, false);
     if (s != FGBD_OK) return s;
   }
   // selection + filter: cooperative launches, one at a time (frame f waits for
@@ -854,7 +876,8 @@ fgbd_status fgbd_get_fslr(fgbd_ctx* ctx, float* spread, uint8_t* keep, void* str
   DeviceGuard g(ctx->device);
   if (!ctx->has_sel) return FGBD_ESTATE;
   const cudaStream_t st = as_stream(stream);
-  FGBD_LAUNCH(ctx, "fslr_export", st, launch_spread_export(ctx->n, ctx->gb.rank1, ctx->spread, ctx->x0, spread, keep, st));
+  FGBD_LAUNCH(ctx, "fslr_export", st,
+              launch_spread_export(ctx->n, ctx->gb.rank1, ctx->spread, ctx->keep8, spread, keep, st));
   return FGBD_OK;
 }
 

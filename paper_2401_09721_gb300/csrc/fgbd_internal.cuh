@@ -29,6 +29,7 @@ constexpr int kSqShift = 8;                        // fixed point of squared col
 constexpr int kDistShift = 20;                     // fixed point of edge lengths
 constexpr int kNeThreads = 256;
 constexpr int kFilterThreads = 512;
+constexpr int kSpecMax = 2;                        // filter steps taken while sigma_est is computed
 constexpr uint32_t kCoordMask = 0x3FFFFFFFu;       // low 30 bits: packed C1 code
 constexpr uint32_t kKeepBit = 0x80000000u;         // FSLR keep flag beside the code
 
@@ -50,6 +51,8 @@ struct DevScalars {
   unsigned long long n_patches;
   long long s1[kD];             // sum of (a - 128)
   long long s2[kD * kD];        // sum of (a - 128)(a - 128)^T (upper triangle filled)
+  uint32_t spec_barrier;        // grid barrier of the speculative filter steps
+  int32_t spec_done;            // filter steps stored by the noise-estimate kernel
   uint32_t ne_end_;
   // ---- results of the noise estimate
   double eig[kD];               // descending
@@ -62,10 +65,13 @@ struct DevScalars {
   unsigned long long ysq_all;
   unsigned long long n_keep;
   unsigned long long sumsq[kQCap + 1];
+  long long spec_keep[kSpecMax + 1];  // over the kept points: sum of y^2 - x_q^2 (fixed point), q = 1..
+  long long spec_all[kSpecMax + 1];   // the same over every point
   uint32_t barrier;
   uint32_t sel_end_;
   // ---- results of the selection
   double J[kQCap + 1];
+  int32_t kept_buf;             // where x_q is: 0 / 1 the iterate buffers, 2 + q - 1 a stored step, -1 the input
   int32_t q_sel;
   int32_t n_J;
   int32_t sel_valid;
@@ -108,6 +114,7 @@ struct SortPassArgs {
 };
 
 // ---------------------------------------------------------------- launchers
+struct FilterArgs;
 // Every launcher enqueues on `stream` and returns the launch error.
 
 cudaError_t launch_coord_hist(const int32_t* xyz, int n, int bits, DevScalars* sc, int num_sms, cudaStream_t stream);
@@ -132,8 +139,11 @@ cudaError_t launch_ne_moments(int n, int bits, int dtype, const GraphBufs& gb, c
                               const float4* yf, float* spread, double* f64_partials,
                               DevScalars* sc, int num_sms, bool moments, bool sorted_patches,
                               cudaStream_t stream);
+// spec: if not null (and spec->spec_depth > 0), the same launch also takes the
+// first spec_depth filter steps on the other SMs (one block per SM)
 cudaError_t launch_ne_finalize(int dtype, const double* f64_partials, int nblocks,
-                               DevScalars* sc, double* sigma_out, cudaStream_t stream);
+                               DevScalars* sc, double* sigma_out, const FilterArgs* spec, int num_sms,
+                               cudaStream_t stream);
 int ne_moment_blocks(int n, int num_sms);
 
 struct FilterArgs {
@@ -158,11 +168,16 @@ struct FilterArgs {
   void* out;             // input-order output or nullptr
   int out_dtype;
   DevScalars* sc;
+  // select mode: the first spec_depth steps were stored before sigma_est was known
+  int spec_depth;          // 0: none
+  float4* spec_x;          // [kSpecMax][cap]: x_1 .. x_S
+  int32_t* spec_z;         // [kSpecMax][cap]: per point sum_c (y^2 - x_q^2), fixed point
+  int cap;
+  uint8_t* keep8;          // select mode: the FSLR keep flag of every sorted point
 };
 cudaError_t launch_filter(const FilterArgs& a, int grid, cudaStream_t stream);
 int filter_grid(int n, int num_sms);
-cudaError_t launch_output(int n, const int32_t* rank1, const float4* xbuf0, const float4* xbuf1,
-                          const DevScalars* sc, void* out, int out_dtype, cudaStream_t stream);
+cudaError_t launch_output(const FilterArgs& a, cudaStream_t stream);  // the kept iterate, in input order
 
 // Differentiable filter: rows of R = D^-1 W for given alpha, sigma, and their transpose
 struct DiffBufs {
@@ -191,7 +206,7 @@ cudaError_t launch_csr_degree(int n, const GraphBufs& gb, int64_t* deg_out, cuda
 cudaError_t launch_scan_i64(int64_t* data, int64_t count, int64_t* block_tmp, cudaStream_t stream);
 cudaError_t launch_csr_fill(int n, int bits, const GraphBufs& gb, const int64_t* row_ptr, int32_t* col,
                             float* w, int64_t col_capacity, const DevScalars* sc, cudaStream_t stream);
-cudaError_t launch_spread_export(int n, const int32_t* rank1, const float* spread, const float4* x0,
+cudaError_t launch_spread_export(int n, const int32_t* rank1, const float* spread, const uint8_t* keep8,
                                  float* spread_out, uint8_t* keep_out, cudaStream_t stream);
 
 // ---------------------------------------------------------------- device helpers

@@ -1,20 +1,23 @@
 // Graph low-pass filter (Eq. 5) and its FSLR selection (Eq. 6, Section 2.4).
 //
 // k_filter is one cooperative launch over all points, in sorted order:
-//   phase 0   x_0 = y; the FSLR keep flag of each point (spread <= 2 sigma_est)
-//             is stored beside its packed coordinates in x.w; the kept power
-//             sum y^2 and the kept count are reduced.
+//   phase 0   the FSLR keep flag of each point (spread <= 2 sigma_est) goes to
+//             keep8; the kept power sum y^2 and the kept count are reduced;
+//             x_0 = y is written unless the first steps are stored already.
 //   step t    x_t = x_{t-1}/2 + (sum_j e_j x_{t-1}[j]) / (2 sum_j e_j) with
-//             e_j = exp(-(d2_j - min_j d2_j) / sigma_g^2): the rows of
-//             D^{-1} W of Eq. 4, computed on the fly from the neighbours'
-//             coordinates (carried in x.w) so no weight array is read.  The
-//             shift by the row minimum cancels in the ratio and keeps the
-//             largest term at 1 (no underflow of the whole row).
+//             e_j = exp(-(d2_j - min_j d2_j) / sigma_g^2) (eq5_step): the rows
+//             of D^{-1} W of Eq. 4, computed on the fly from the neighbours'
+//             coordinates (carried in x.w), so no weight array is read.
 //             In select mode the kept power sum x_t^2 is reduced and, after a
 //             grid barrier, every block evaluates the same
 //             J(t) = |sigma^2 - (sum y^2 - sum x_t^2)/(3 N_sel)| and stops at
 //             the first t with J(t) >= J(t-1), keeping q* = t-1.
 //   output    the kept iterate is gathered back to input order (optional).
+// The steps do not depend on sigma_est, only the keep flags and J do: the
+// noise-estimate launch stores x_1..x_S and each point's Eq. 6 term
+// y^2 - x_q^2 (speculative_steps), and phase 0 then also reduces those terms
+// over the kept points, so J(1..S) need no step here; ordinary steps continue
+// from x_S only if J still falls there.
 // Sums of squares are fixed-point integers (2^-8), so the reduction is exact
 // and independent of the order in which blocks add.
 // The grid barrier is a counter with a 2 s wait limit; a block that gives up
@@ -22,60 +25,10 @@
 #include <algorithm>
 #include <climits>
 
-#include "fgbd_internal.cuh"
+#include "filter_step.cuh"
 
 namespace fgbd {
 namespace {
-
-__device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long* p) {
-  unsigned long long v;
-  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
-  return v;
-}
-__device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t* p) {
-  uint32_t v;
-  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
-
-__device__ bool grid_barrier(DevScalars* sc, uint32_t& epoch, int* s_ok) {
-  __syncthreads();
-  epoch += 1;
-  if (threadIdx.x == 0) {
-    const uint32_t target = epoch * gridDim.x;
-    __threadfence();
-    atomicAdd(&sc->barrier, 1u);
-    const unsigned long long t0 = global_ns();
-    int ok = 1;
-    while (ld_acquire_u32(&sc->barrier) < target) {
-      if (global_ns() - t0 > kWaitLimitNs) {
-        atomicOr(&sc->status, kFlagTimeout);
-        ok = 0;
-        break;
-      }
-      __nanosleep(64);
-    }
-    __threadfence();
-    if (ld_acquire_u32(&sc->status) & kFlagTimeout) ok = 0;
-    *s_ok = ok;
-  }
-  __syncthreads();
-  return *s_ok != 0;
-}
-
-__device__ __forceinline__ void load_y(const FilterArgs& a, int k, float& r, float& g, float& b) {
-  if (a.dtype == 0) {
-    const uint32_t y = a.y8[k];
-    r = float(y & 255u);
-    g = float((y >> 8) & 255u);
-    b = float((y >> 16) & 255u);
-  } else {
-    const float4 y = a.yf[k];
-    r = y.x;
-    g = y.y;
-    b = y.z;
-  }
-}
 
 // float64 spread of point k, used only where the float32 value is too close to
 // the threshold to decide (Section 2.4: mean of the three population stds)
@@ -110,8 +63,53 @@ __device__ double spread_f64(const FilterArgs& a, int k) {
   return (sqrt(var[0] / cnt) + sqrt(var[1] / cnt) + sqrt(var[2] / cnt)) / 3.0;
 }
 
-__global__ void __launch_bounds__(kFilterThreads) k_filter(FilterArgs a) {
-  __shared__ unsigned long long s_red[kFilterThreads / 32];
+__device__ __forceinline__ void write_out(const FilterArgs& a, int i, float4 x) {
+  if (a.out_dtype == 0) {
+    uint8_t* o = static_cast<uint8_t*>(a.out) + 3 * size_t(i);
+    o[0] = uint8_t(fminf(fmaxf(rintf(x.x), 0.f), 255.f));
+    o[1] = uint8_t(fminf(fmaxf(rintf(x.y), 0.f), 255.f));
+    o[2] = uint8_t(fminf(fmaxf(rintf(x.z), 0.f), 255.f));
+  } else {
+    float* o = static_cast<float*>(a.out) + 3 * size_t(i);
+    o[0] = x.x;
+    o[1] = x.y;
+    o[2] = x.z;
+  }
+}
+
+// x_q of sorted point k, wherever the kept iterate is (kept_buf)
+__device__ __forceinline__ float4 kept_value(const FilterArgs& a, int kept, int k) {
+  if (kept < 0) return x0_of(a, k);
+  if (kept >= 2) return __ldcg(&a.spec_x[size_t(kept - 2) * size_t(a.cap) + k]);
+  return __ldcg(&(kept ? a.xbuf1 : a.xbuf0)[k]);
+}
+
+// Sums of several 64-bit values over the block (two's complement: exact in any order)
+template <int K>
+__device__ __forceinline__ void block_sums(unsigned long long (&v)[K], unsigned long long* s_red) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int i = 0; i < K; ++i) v[i] = warp_sum(v[i]);
+  if (lane == 0) {
+#pragma unroll
+    for (int i = 0; i < K; ++i) s_red[i * (kFilterThreads / 32) + warp] = v[i];
+  }
+  __syncthreads();
+  if (threadIdx.x < K) {
+    unsigned long long t = 0;
+    for (int w = 0; w < kFilterThreads / 32; ++w) t += s_red[threadIdx.x * (kFilterThreads / 32) + w];
+    s_red[K * (kFilterThreads / 32) + threadIdx.x] = t;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < K; ++i) v[i] = s_red[K * (kFilterThreads / 32) + i];
+  __syncthreads();
+}
+
+constexpr int kSums = 3 + 2 * kSpecMax;  // kept y^2, all y^2, kept count, then per stored step kept and all terms
+
+__global__ void __launch_bounds__(kFilterThreads, 2) k_filter(FilterArgs a) {
+  __shared__ unsigned long long s_red[(kSums + 1) * (kFilterThreads / 32)];
   __shared__ int s_ok;
   __shared__ double s_J;
   uint32_t epoch = 0;
@@ -120,6 +118,11 @@ __global__ void __launch_bounds__(kFilterThreads) k_filter(FilterArgs a) {
   const int gstride = gridDim.x * blockDim.x;
   DevScalars* sc = a.sc;
   const bool select = a.mode == 0;
+  // the stored steps count only if the noise-estimate launch finished them
+  const int S = (select && a.spec_depth > 0 &&
+                 ld_acquire_u32(reinterpret_cast<const uint32_t*>(&sc->spec_done)) == uint32_t(a.spec_depth))
+                    ? a.spec_depth
+                    : 0;
 
   double sigma = 0.0;
   float t_lo = 0.f, t_hi = 0.f;
@@ -132,39 +135,56 @@ __global__ void __launch_bounds__(kFilterThreads) k_filter(FilterArgs a) {
     t_hi = float(thr * (1.0 + band));
   }
 
-  // ---- phase 0: x_0 = y with the keep flag
-  unsigned long long ysq_k = 0, ysq_a = 0, nk = 0;
+  // ---- phase 0: keep flags and the Eq. 6 sums; x_0 = y unless the steps are stored
+  unsigned long long acc[kSums] = {};
   for (int k = gtid; k < n; k += gstride) {
-    float r, g, b;
-    load_y(a, k, r, g, b);
-    uint32_t w = a.pk[k];
+    const float4 x0 = x0_of(a, k);
+    if (!S) a.xbuf0[k] = x0;
     if (select) {
       const float sp = a.spread[k];
       bool keep;
       if (a.all_points || sp <= t_lo) keep = true;
       else if (sp > t_hi) keep = false;
       else keep = !(spread_f64(a, k) > thr);
-      const unsigned long long q2 = (unsigned long long)(sq_fixed(r) + sq_fixed(g) + sq_fixed(b));
-      ysq_a += q2;
+      a.keep8[k] = keep ? 1 : 0;
+      const unsigned long long q2 = sq3(x0);
+      acc[1] += q2;
       if (keep) {
-        w |= kKeepBit;
-        nk += 1;
-        ysq_k += q2;
+        acc[0] += q2;
+        acc[2] += 1;
       }
     }
-    a.xbuf0[k] = make_float4(r, g, b, __uint_as_float(w));
   }
-  if (select) {
-    ysq_k = block_sum_u64<kFilterThreads>(ysq_k, s_red);
-    ysq_a = block_sum_u64<kFilterThreads>(ysq_a, s_red);
-    nk = block_sum_u64<kFilterThreads>(nk, s_red);
-    if (threadIdx.x == 0) {
-      if (ysq_k) atomicAdd(&sc->ysq_keep, ysq_k);
-      if (ysq_a) atomicAdd(&sc->ysq_all, ysq_a);
-      if (nk) atomicAdd(&sc->n_keep, nk);
+  // the stored steps' Eq. 6 terms (a second pass: this thread's own keep flags)
+  if (S > 0) {
+    for (int k = gtid; k < n; k += gstride) {
+      const bool keep = a.keep8[k] != 0;
+#pragma unroll
+      for (int q = 0; q < kSpecMax; ++q) {
+        if (q < S) {
+          const unsigned long long z = (unsigned long long)(long long)a.spec_z[size_t(q) * size_t(a.cap) + k];
+          acc[4 + 2 * q] += z;
+          if (keep) acc[3 + 2 * q] += z;
+        }
+      }
     }
   }
-  if (!grid_barrier(sc, epoch, &s_ok)) return;
+  if (select) {
+    block_sums<kSums>(acc, s_red);
+    if (threadIdx.x == 0) {
+      if (acc[0]) atomicAdd(&sc->ysq_keep, acc[0]);
+      if (acc[1]) atomicAdd(&sc->ysq_all, acc[1]);
+      if (acc[2]) atomicAdd(&sc->n_keep, acc[2]);
+#pragma unroll
+      for (int q = 0; q < kSpecMax; ++q) {
+        if (q < S) {
+          atomicAdd(reinterpret_cast<unsigned long long*>(&sc->spec_keep[q + 1]), acc[3 + 2 * q]);
+          atomicAdd(reinterpret_cast<unsigned long long*>(&sc->spec_all[q + 1]), acc[4 + 2 * q]);
+        }
+      }
+    }
+  }
+  if (!grid_barrier(&sc->barrier, &sc->status, gridDim.x, epoch, &s_ok)) return;
 
   bool keep_all = false;
   unsigned long long ysq = 0;
@@ -175,74 +195,47 @@ __global__ void __launch_bounds__(kFilterThreads) k_filter(FilterArgs a) {
     nsel = keep_all ? double(n) : double(nkt);
     ysq = keep_all ? ld_relaxed_u64(&sc->ysq_all) : ld_relaxed_u64(&sc->ysq_keep);
   }
-  const double sg = sigma_g_of(sc);
-  const float cexp = sg > 0.0 ? float(1.4426950408889634 / (sg * sg)) : 0.f;
-  const int bits = a.bits;
+  const float cexp = step_cexp(sc);
 
   double J_prev = sigma * sigma;  // J(0): nothing filtered yet
   if (select && gtid == 0) sc->J[0] = J_prev;
   int q_final = 0;
+  bool stopped = false;
   const int q_fixed = a.q_src ? min(max(*a.q_src, 0), kQCap) : a.q_fixed;
   const int q_limit = n == 0 ? 0 : (select ? a.q_max : q_fixed);
-  for (int t = 1; t <= q_limit; ++t) {
-    const float4* __restrict__ src = (t & 1) ? a.xbuf0 : a.xbuf1;
+  // J(1..S) from the stored terms
+  for (int t = 1; t <= min(S, q_limit); ++t) {
+    const unsigned long long* src = reinterpret_cast<const unsigned long long*>(keep_all ? &sc->spec_all[t]
+                                                                                          : &sc->spec_keep[t]);
+    const double lost = double((long long)ld_relaxed_u64(src)) * (1.0 / double(1 << kSqShift));
+    const double J = fabs(sigma * sigma - lost / (3.0 * nsel));
+    if (gtid == 0) {
+      sc->J[t] = J;
+      sc->n_J = t + 1;
+    }
+    if (J >= J_prev) {
+      q_final = t - 1;
+      stopped = true;
+      break;
+    }
+    J_prev = J;
+    q_final = t;
+  }
+  for (int t = S + 1; t <= q_limit && !stopped; ++t) {
+    const float4* __restrict__ src =
+        (S > 0 && t == S + 1) ? a.spec_x + size_t(S - 1) * size_t(a.cap) : ((t & 1) ? a.xbuf0 : a.xbuf1);
     float4* __restrict__ dst = (t & 1) ? a.xbuf1 : a.xbuf0;
     unsigned long long loc = 0;
     for (int k = gtid; k < n; k += gstride) {
-      const float4 xk = __ldcg(&src[k]);
-      const uint32_t wk = __float_as_uint(xk.w);
-      const uint32_t ck = wk & kCoordMask;
-      int nb[6];
-      bool v[6];
-      nb[0] = k - 1;
-      v[0] = k > 0;
-      nb[1] = k + 1;
-      v[1] = k + 1 < n;
-      const int4 s = a.c4[k];
-      nb[2] = s.x;
-      nb[3] = s.y;
-      nb[4] = s.z;
-      nb[5] = s.w;
-      v[2] = in_range(s.x, n);
-      v[3] = in_range(s.y, n);
-      v[4] = in_range(s.z, n);
-      v[5] = in_range(s.w, n);
-      float4 xn[6];
-      int d2[6];
-      int dmin = INT_MAX;
-#pragma unroll
-      for (int j = 0; j < 6; ++j) {
-        xn[j] = v[j] ? __ldcg(&src[nb[j]]) : xk;
-        d2[j] = v[j] ? sq_dist_c1(ck, __float_as_uint(xn[j].w) & kCoordMask, bits) : INT_MAX;
-        dmin = min(dmin, d2[j]);
-      }
-      float se = 0.f, sr = 0.f, sgc = 0.f, sb = 0.f;
-#pragma unroll
-      for (int j = 0; j < 6; ++j) {
-        if (v[j]) {
-          const float e = exp2f(float(dmin - d2[j]) * cexp);
-          se += e;
-          sr = fmaf(e, xn[j].x, sr);
-          sgc = fmaf(e, xn[j].y, sgc);
-          sb = fmaf(e, xn[j].z, sb);
-        }
-      }
-      float4 xo = xk;
-      if (se > 0.f) {
-        const float inv = 1.f / se;
-        xo.x = 0.5f * xk.x + 0.5f * (sr * inv);
-        xo.y = 0.5f * xk.y + 0.5f * (sgc * inv);
-        xo.z = 0.5f * xk.z + 0.5f * (sb * inv);
-      }
+      const float4 xo = eq5_step(a, src, k, n, cexp);
       dst[k] = xo;
-      if (select && (keep_all || (wk & kKeepBit)))
-        loc += (unsigned long long)(sq_fixed(xo.x) + sq_fixed(xo.y) + sq_fixed(xo.z));
+      if (select && (keep_all || a.keep8[k])) loc += sq3(xo);
     }
     if (select) {
       loc = block_sum_u64<kFilterThreads>(loc, s_red);
       if (threadIdx.x == 0 && loc) atomicAdd(&sc->sumsq[t], loc);
     }
-    if (!grid_barrier(sc, epoch, &s_ok)) return;
+    if (!grid_barrier(&sc->barrier, &sc->status, gridDim.x, epoch, &s_ok)) return;
     if (select) {
       if (threadIdx.x == 0) {
         const unsigned long long ss = ld_relaxed_u64(&sc->sumsq[t]);
@@ -264,53 +257,29 @@ __global__ void __launch_bounds__(kFilterThreads) k_filter(FilterArgs a) {
       q_final = t;
     }
   }
-  if (gtid == 0 && !a.q_src) {
-    sc->q_sel = q_final;
+  // where the kept iterate is
+  const int kept = (S > 0 && q_final <= S) ? (q_final == 0 ? -1 : 2 + q_final - 1) : (q_final & 1);
+  if (gtid == 0) {
+    if (!a.q_src) sc->q_sel = q_final;
+    sc->kept_buf = kept;
     if (select) sc->sel_valid = 1;
     if (select && q_limit == 0) sc->n_J = 1;
   }
   if (a.out) {
-    const float4* res = (q_final & 1) ? a.xbuf1 : a.xbuf0;
     for (int i = gtid; i < n; i += gstride) {
       const int k = a.rank1[i];
       if (!in_range(k, n)) continue;
-      const float4 x = __ldcg(&res[k]);
-      if (a.out_dtype == 0) {
-        uint8_t* o = static_cast<uint8_t*>(a.out) + 3 * size_t(i);
-        o[0] = uint8_t(fminf(fmaxf(rintf(x.x), 0.f), 255.f));
-        o[1] = uint8_t(fminf(fmaxf(rintf(x.y), 0.f), 255.f));
-        o[2] = uint8_t(fminf(fmaxf(rintf(x.z), 0.f), 255.f));
-      } else {
-        float* o = static_cast<float*>(a.out) + 3 * size_t(i);
-        o[0] = x.x;
-        o[1] = x.y;
-        o[2] = x.z;
-      }
+      write_out(a, i, kept_value(a, kept, k));
     }
   }
 }
 
-__global__ void __launch_bounds__(256) k_output(int n, const int32_t* __restrict__ rank1,
-                                                const float4* __restrict__ x0,
-                                                const float4* __restrict__ x1,
-                                                const DevScalars* __restrict__ sc, void* out,
-                                                int out_dtype) {
-  const float4* res = (sc->q_sel & 1) ? x1 : x0;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    const int k = rank1[i];
-    if (!in_range(k, n)) continue;
-    const float4 x = res[k];
-    if (out_dtype == 0) {
-      uint8_t* o = static_cast<uint8_t*>(out) + 3 * size_t(i);
-      o[0] = uint8_t(fminf(fmaxf(rintf(x.x), 0.f), 255.f));
-      o[1] = uint8_t(fminf(fmaxf(rintf(x.y), 0.f), 255.f));
-      o[2] = uint8_t(fminf(fmaxf(rintf(x.z), 0.f), 255.f));
-    } else {
-      float* o = static_cast<float*>(out) + 3 * size_t(i);
-      o[0] = x.x;
-      o[1] = x.y;
-      o[2] = x.z;
-    }
+__global__ void __launch_bounds__(256) k_output(FilterArgs a) {
+  const int kept = a.sc->kept_buf;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += gridDim.x * blockDim.x) {
+    const int k = a.rank1[i];
+    if (!in_range(k, a.n)) continue;
+    write_out(a, i, kept_value(a, kept, k));
   }
 }
 
@@ -416,13 +385,13 @@ __global__ void k_scan_add(int64_t* data, int64_t count, const int64_t* totals) 
 }
 
 __global__ void k_spread_export(int n, const int32_t* __restrict__ rank1, const float* __restrict__ spread,
-                                const float4* __restrict__ x0, float* __restrict__ spread_out,
+                                const uint8_t* __restrict__ keep8, float* __restrict__ spread_out,
                                 uint8_t* __restrict__ keep_out) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     const int k = rank1[i];
     if (!in_range(k, n)) continue;
     if (spread_out) spread_out[i] = spread[k];
-    if (keep_out) keep_out[i] = (__float_as_uint(x0[k].w) & kKeepBit) ? 1 : 0;
+    if (keep_out) keep_out[i] = keep8[k] ? 1 : 0;
   }
 }
 
@@ -444,11 +413,10 @@ cudaError_t launch_filter(const FilterArgs& a, int grid, cudaStream_t stream) {
                                      dim3(kFilterThreads), args, 0, stream);
 }
 
-cudaError_t launch_output(int n, const int32_t* rank1, const float4* xbuf0, const float4* xbuf1,
-                          const DevScalars* sc, void* out, int out_dtype, cudaStream_t stream) {
-  if (n <= 0) return cudaSuccess;
-  const int grid = std::min((n + 255) / 256, 152 * 16);
-  k_output<<<grid, 256, 0, stream>>>(n, rank1, xbuf0, xbuf1, sc, out, out_dtype);
+cudaError_t launch_output(const FilterArgs& a, cudaStream_t stream) {
+  if (a.n <= 0) return cudaSuccess;
+  const int grid = std::min((a.n + 255) / 256, 152 * 16);
+  k_output<<<grid, 256, 0, stream>>>(a);
   return cudaGetLastError();
 }
 
@@ -475,11 +443,11 @@ cudaError_t launch_csr_fill(int n, int bits, const GraphBufs& gb, const int64_t*
   return cudaGetLastError();
 }
 
-cudaError_t launch_spread_export(int n, const int32_t* rank1, const float* spread, const float4* x0,
+cudaError_t launch_spread_export(int n, const int32_t* rank1, const float* spread, const uint8_t* keep8,
                                  float* spread_out, uint8_t* keep_out, cudaStream_t stream) {
   if (n <= 0) return cudaSuccess;
   const int grid = std::min((n + 255) / 256, 152 * 16);
-  k_spread_export<<<grid, 256, 0, stream>>>(n, rank1, spread, x0, spread_out, keep_out);
+  k_spread_export<<<grid, 256, 0, stream>>>(n, rank1, spread, keep8, spread_out, keep_out);
   return cudaGetLastError();
 }
 

@@ -1,0 +1,165 @@
+// One step of the graph low-pass filter (Eq. 5) and the pieces around it that
+// more than one kernel needs: the colours of the sorted points, the bounded
+// grid barrier of the cooperative kernels, and the speculative steps that the
+// noise-estimate kernel takes while its first block computes sigma_est.
+#pragma once
+
+#include <climits>
+
+#include "fgbd_internal.cuh"
+
+namespace fgbd {
+
+__device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t* p) {
+  uint32_t v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Barrier over `members` blocks of a cooperative grid: a counter that each
+// block raises once per barrier, waited on for at most kWaitLimitNs; a block
+// that gives up latches kFlagTimeout, and every block then returns false.
+__device__ __forceinline__ bool grid_barrier(uint32_t* counter, uint32_t* status, uint32_t members, uint32_t& epoch,
+                                             int* s_ok) {
+  __syncthreads();
+  epoch += 1;
+  if (threadIdx.x == 0) {
+    const uint32_t target = epoch * members;
+    __threadfence();
+    atomicAdd(counter, 1u);
+    const unsigned long long t0 = global_ns();
+    int ok = 1;
+    while (ld_acquire_u32(counter) < target) {
+      if (global_ns() - t0 > kWaitLimitNs) {
+        atomicOr(status, kFlagTimeout);
+        ok = 0;
+        break;
+      }
+      __nanosleep(64);
+    }
+    __threadfence();
+    if (ld_acquire_u32(status) & kFlagTimeout) ok = 0;
+    *s_ok = ok;
+  }
+  __syncthreads();
+  return *s_ok != 0;
+}
+
+__device__ __forceinline__ void load_y(const FilterArgs& a, int k, float& r, float& g, float& b) {
+  if (a.dtype == 0) {
+    const uint32_t y = a.y8[k];
+    r = float(y & 255u);
+    g = float((y >> 8) & 255u);
+    b = float((y >> 16) & 255u);
+  } else {
+    const float4 y = a.yf[k];
+    r = y.x;
+    g = y.y;
+    b = y.z;
+  }
+}
+
+// x_0 of sorted point k: its colour, and its packed coordinates in w
+__device__ __forceinline__ float4 x0_of(const FilterArgs& a, int k) {
+  float r, g, b;
+  load_y(a, k, r, g, b);
+  return make_float4(r, g, b, __uint_as_float(a.pk[k]));
+}
+
+// sum over the channels of x^2 in fixed point 2^-kSqShift
+__device__ __forceinline__ unsigned long long sq3(float4 x) {
+  return (unsigned long long)(sq_fixed(x.x) + sq_fixed(x.y) + sq_fixed(x.z));
+}
+
+// The Eq. 4 exponent scale log2(e) / sigma_g^2
+__device__ __forceinline__ float step_cexp(const DevScalars* sc) {
+  const double sg = sigma_g_of(sc);
+  return sg > 0.0 ? float(1.4426950408889634 / (sg * sg)) : 0.f;
+}
+
+// One Eq. 5 step at sorted point k: x_k / 2 + (sum_j e_j x_j) / (2 sum_j e_j)
+// over the neighbours (C1 k - 1, k + 1, the C2/C3 slots) with
+// e_j = exp(-(d2_j - min d2) / sigma_g^2), from the previous iterate `src` (x_0
+// built from the colours when src is null).  Every kernel that takes a step
+// uses this function, so a step gives the same bits in all of them.
+__device__ __forceinline__ float4 eq5_step(const FilterArgs& a, const float4* __restrict__ src, int k, int n,
+                                           float cexp) {
+  const float4 xk = src ? __ldcg(&src[k]) : x0_of(a, k);
+  const uint32_t ck = __float_as_uint(xk.w) & kCoordMask;
+  int nb[6];
+  bool v[6];
+  nb[0] = k - 1;
+  v[0] = k > 0;
+  nb[1] = k + 1;
+  v[1] = k + 1 < n;
+  const int4 s = a.c4[k];
+  nb[2] = s.x;
+  nb[3] = s.y;
+  nb[4] = s.z;
+  nb[5] = s.w;
+  v[2] = in_range(s.x, n);
+  v[3] = in_range(s.y, n);
+  v[4] = in_range(s.z, n);
+  v[5] = in_range(s.w, n);
+  float4 xn[6];
+  int d2[6];
+  int dmin = INT_MAX;
+#pragma unroll
+  for (int j = 0; j < 6; ++j) {
+    xn[j] = v[j] ? (src ? __ldcg(&src[nb[j]]) : x0_of(a, nb[j])) : xk;
+    d2[j] = v[j] ? sq_dist_c1(ck, __float_as_uint(xn[j].w) & kCoordMask, a.bits) : INT_MAX;
+    dmin = min(dmin, d2[j]);
+  }
+  float se = 0.f, sr = 0.f, sgc = 0.f, sb = 0.f;
+#pragma unroll
+  for (int j = 0; j < 6; ++j) {
+    if (v[j]) {
+      const float e = exp2f(float(dmin - d2[j]) * cexp);
+      se += e;
+      sr = fmaf(e, xn[j].x, sr);
+      sgc = fmaf(e, xn[j].y, sgc);
+      sb = fmaf(e, xn[j].z, sb);
+    }
+  }
+  float4 xo = xk;
+  if (se > 0.f) {
+    const float inv = 1.f / se;
+    xo.x = 0.5f * xk.x + 0.5f * (sr * inv);
+    xo.y = 0.5f * xk.y + 0.5f * (sgc * inv);
+    xo.z = 0.5f * xk.z + 0.5f * (sb * inv);
+  }
+  return xo;
+}
+
+// The first `depth` steps x_1..x_depth, each point's Eq. 6 term
+// sum_c (y^2 - x_q^2) in fixed point beside them, by the blocks [first,
+// gridDim.x) of a cooperative grid (they need the graph and the colours
+// only, not sigma_est).  sc->spec_done = depth once every step is stored.
+__device__ __forceinline__ void speculative_steps(const FilterArgs& a, int depth, int first, int* s_ok) {
+  uint32_t epoch = 0;
+  const int n = a.n;
+  const uint32_t members = gridDim.x - uint32_t(first);
+  const int gtid = (blockIdx.x - first) * blockDim.x + threadIdx.x;
+  const int gstride = int(members) * blockDim.x;
+  DevScalars* sc = a.sc;
+  const float cexp = step_cexp(sc);
+  for (int t = 1; t <= depth; ++t) {
+    const float4* src = t == 1 ? nullptr : a.spec_x + size_t(t - 2) * size_t(a.cap);
+    float4* dst = a.spec_x + size_t(t - 1) * size_t(a.cap);
+    int32_t* z = a.spec_z + size_t(t - 1) * size_t(a.cap);
+    for (int k = gtid; k < n; k += gstride) {
+      const float4 xo = eq5_step(a, src, k, n, cexp);
+      dst[k] = xo;
+      z[k] = int32_t((long long)sq3(x0_of(a, k)) - (long long)sq3(xo));
+    }
+    if (!grid_barrier(&sc->spec_barrier, &sc->status, members, epoch, s_ok)) return;
+  }
+  if (gtid == 0) sc->spec_done = depth;
+}
+
+}  // namespace fgbd

@@ -16,7 +16,7 @@
 //   the values are sorted descending and the tail rule gives sigma_est.
 #include <algorithm>
 
-#include "fgbd_internal.cuh"
+#include "filter_step.cuh"
 
 namespace fgbd {
 namespace {
@@ -476,9 +476,23 @@ __device__ __forceinline__ void jacobi_rotation(float app, float aqq, float apq,
   cq = make_float2(c, s);
 }
 
-__global__ void __launch_bounds__(kFinThreads) k_ne_finalize(int dtype, const double* __restrict__ f64_partials,
-                                                     int nblocks, DevScalars* __restrict__ sc,
-                                                     double* __restrict__ sigma_out) {
+// barriers of the first kFinThreads threads of a block (barrier 1; 0 is __syncthreads)
+__device__ __forceinline__ void fin_bar() { asm volatile("bar.sync 1, %0;" ::"n"(kFinThreads) : "memory"); }
+__device__ __forceinline__ bool fin_bar_or(bool v) {
+  uint32_t r;
+  asm volatile(
+      "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 q, %1, 0;\n\tbar.red.or.pred p, 1, %2, q;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(r)
+      : "r"(uint32_t(v)), "n"(kFinThreads)
+      : "memory");
+  return r != 0;
+}
+
+// sigma_est from the patch moments, by the first kFinThreads threads of one
+// block (its barriers count those threads only, so the rest of a larger block
+// may leave at once)
+__device__ __noinline__ void finalize_block(int dtype, const double* __restrict__ f64_partials, int nblocks,
+                                            DevScalars* __restrict__ sc, double* __restrict__ sigma_out) {
   __shared__ double S[kD][kD];
   __shared__ double s_sum[kD * kD + kD + 1];
   __shared__ float V[kD][kD + 1];
@@ -495,17 +509,17 @@ __global__ void __launch_bounds__(kFinThreads) k_ne_finalize(int dtype, const do
   // gather the moments
   double npd;
   if (dtype == 0) {
-    for (int i = tid; i < kD * kD; i += blockDim.x) s_sum[i] = double(sc->s2[i]);
-    for (int i = tid; i < kD; i += blockDim.x) s_sum[kD * kD + i] = double(sc->s1[i]);
+    for (int i = tid; i < kD * kD; i += kFinThreads) s_sum[i] = double(sc->s2[i]);
+    for (int i = tid; i < kD; i += kFinThreads) s_sum[kD * kD + i] = double(sc->s1[i]);
     if (tid == 0) s_sum[kD * kD + kD] = double(sc->n_patches);
   } else {
-    for (int i = tid; i < kP; i += blockDim.x) {
+    for (int i = tid; i < kP; i += kFinThreads) {
       double t = 0.0;
       for (int b = 0; b < nblocks; ++b) t += f64_partials[size_t(b) * kP + i];
       s_sum[i] = t;
     }
   }
-  __syncthreads();
+  fin_bar();
   npd = s_sum[kD * kD + kD];
   if (tid == 0 && dtype == 1) sc->n_patches = (unsigned long long)npd;
   if (npd < 1.0) {
@@ -521,13 +535,13 @@ __global__ void __launch_bounds__(kFinThreads) k_ne_finalize(int dtype, const do
   }
   // Sigma = S2/N - mu mu^T (upper triangle accumulated; mirror it)
   const double inv_n = 1.0 / npd;
-  for (int e = tid; e < kD * kD; e += blockDim.x) {
+  for (int e = tid; e < kD * kD; e += kFinThreads) {
     const int r = e / kD, c = e % kD;
     const int rr = min(r, c), cc = max(r, c);
     const double mr = s_sum[kD * kD + rr] * inv_n, mc = s_sum[kD * kD + cc] * inv_n;
     S[r][c] = s_sum[rr * kD + cc] * inv_n - mr * mc;
   }
-  __syncthreads();
+  fin_bar();
 
   // Cyclic Jacobi in float32, matrix and vectors in shared memory
   // (double-buffered), one barrier per round.  Each round applies the
@@ -543,7 +557,7 @@ __global__ void __launch_bounds__(kFinThreads) k_ne_finalize(int dtype, const do
   // barrier where no off-diagonal entry is above that threshold, since no
   // later round would rotate anything.
   {
-    for (int e = tid; e < kD * kD; e += blockDim.x) {
+    for (int e = tid; e < kD * kD; e += kFinThreads) {
       Abuf[0][e] = float(S[e / kD][e % kD]);
       Vbuf[0][e] = (e / kD == e % kD) ? 1.f : 0.f;
     }
@@ -565,7 +579,7 @@ __global__ void __launch_bounds__(kFinThreads) k_ne_finalize(int dtype, const do
     }
     const bool pred = tid >= kPredFirst && tid < kPredFirst + kGroups;
     const int pk = tid - kPredFirst;
-    __syncthreads();
+    fin_bar();
     // coefficients of round 0 from the matrix itself
     if (pred) {
       if (pk == 0) {
@@ -580,8 +594,8 @@ __global__ void __launch_bounds__(kFinThreads) k_ne_finalize(int dtype, const do
       }
     }
     bool off_big = false;
-    for (int e = tid; e < kD * kD; e += blockDim.x) off_big |= (e / kD != e % kD) && fabsf(Abuf[0][e]) > thr;
-    bool big = __syncthreads_or(off_big);
+    for (int e = tid; e < kD * kD; e += kFinThreads) off_big |= (e / kD != e % kD) && fabsf(Abuf[0][e]) > thr;
+    bool big = fin_bar_or(off_big);
     int cur = 0;
     for (int round = 0; big && round < kMaxSweeps * kD; ++round) {
       const int r = round % kD;
@@ -641,17 +655,17 @@ __global__ void __launch_bounds__(kFinThreads) k_ne_finalize(int dtype, const do
         }
       }
       cur ^= 1;
-      big = __syncthreads_or(off_big);
+      big = fin_bar_or(off_big);
     }
-    for (int e = tid; e < kD * kD; e += blockDim.x) V[e / kD][e % kD] = Vbuf[cur][e];
+    for (int e = tid; e < kD * kD; e += kFinThreads) V[e / kD][e % kD] = Vbuf[cur][e];
   }
-  __syncthreads();
+  fin_bar();
 
   // float64 Rayleigh quotients of the 21 eigenvector estimates.  float64 has a
   // long latency here, so the sums run as three interleaved chains.
-  for (int e = tid; e < kD * kD; e += blockDim.x) V64[e / kD][e % kD] = double(V[e / kD][e % kD]);
-  __syncthreads();
-  for (int e = tid; e < kD * kD; e += blockDim.x) {
+  for (int e = tid; e < kD * kD; e += kFinThreads) V64[e / kD][e % kD] = double(V[e / kD][e % kD]);
+  fin_bar();
+  for (int e = tid; e < kD * kD; e += kFinThreads) {
     const int k = e / kD, r = e % kD;
     double w0 = 0.0, w1 = 0.0, w2 = 0.0;
 #pragma unroll
@@ -662,7 +676,7 @@ __global__ void __launch_bounds__(kFinThreads) k_ne_finalize(int dtype, const do
     }
     s_num[k][r] = (w0 + w1 + w2) * V64[r][k];
   }
-  __syncthreads();
+  fin_bar();
   // the rest runs in warp 0, lane j < 21 holding eigenvalue j
   if (tid < 32) {
     constexpr unsigned kFull = 0xffffffffu;
@@ -734,6 +748,29 @@ __global__ void __launch_bounds__(kFinThreads) k_ne_finalize(int dtype, const do
   }
 }
 
+__global__ void __launch_bounds__(kFinThreads) k_ne_finalize(int dtype, const double* __restrict__ f64_partials,
+                                                           int nblocks, DevScalars* __restrict__ sc,
+                                                           double* __restrict__ sigma_out) {
+  finalize_block(dtype, f64_partials, nblocks, sc, sigma_out);
+}
+
+// One block per SM (the dynamic shared memory keeps a second one out): block 0
+// computes sigma_est on an SM of its own, the others meanwhile take the first
+// filter steps, which need the graph and the colours only.
+constexpr int kSpecThreads = 1024;
+constexpr int kSpecPadBytes = 100 * 1024;  // shared memory that makes a second block not fit on an SM
+
+__global__ void __launch_bounds__(kSpecThreads, 1)
+    k_ne_finalize_spec(int dtype, const double* __restrict__ f64_partials, int nblocks, DevScalars* __restrict__ sc,
+                       double* __restrict__ sigma_out, FilterArgs a) {
+  __shared__ int s_ok;
+  if (blockIdx.x == 0) {
+    if (threadIdx.x < kFinThreads) finalize_block(dtype, f64_partials, nblocks, sc, sigma_out);
+    return;
+  }
+  speculative_steps(a, a.spec_depth, 1, &s_ok);
+}
+
 }  // namespace
 
 cudaError_t launch_gather_colors(const void* rgb, int dtype, int n, const int32_t* perm1,
@@ -777,9 +814,25 @@ cudaError_t launch_ne_moments(int n, int bits, int dtype, const GraphBufs& gb, c
 }
 
 cudaError_t launch_ne_finalize(int dtype, const double* f64_partials, int nblocks, DevScalars* sc,
-                               double* sigma_out, cudaStream_t stream) {
-  k_ne_finalize<<<1, kFinThreads, 0, stream>>>(dtype, f64_partials, nblocks, sc, sigma_out);
-  return cudaGetLastError();
+                               double* sigma_out, const FilterArgs* spec, int num_sms, cudaStream_t stream) {
+  if (!spec || spec->spec_depth <= 0 || spec->n <= 0 || num_sms < 2) {
+    k_ne_finalize<<<1, kFinThreads, 0, stream>>>(dtype, f64_partials, nblocks, sc, sigma_out);
+    return cudaGetLastError();
+  }
+  static unsigned long long configured = 0;  // the shared-memory limit is set once per device
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const unsigned long long bit = 1ull << (dev & 63);
+  if (!(configured & bit)) {
+    e = cudaFuncSetAttribute(k_ne_finalize_spec, cudaFuncAttributeMaxDynamicSharedMemorySize, kSpecPadBytes);
+    if (e != cudaSuccess) return e;
+    configured |= bit;
+  }
+  FilterArgs copy = *spec;
+  void* args[] = {&dtype, &f64_partials, &nblocks, &sc, &sigma_out, &copy};
+  return cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(k_ne_finalize_spec), dim3(num_sms),
+                                     dim3(kSpecThreads), args, kSpecPadBytes, stream);
 }
 
 }  // namespace fgbd
