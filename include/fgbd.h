@@ -101,7 +101,7 @@ fgbd_status fgbd_params_default(fgbd_params* p);
 
 /* Create a context on the current CUDA device for frames of up to `capacity`
  * points (1 <= capacity < 2^30) and allocate all its device memory (about
- * 190 bytes per point).  `params` may be NULL for the defaults.  On success
+ * 180 bytes per point).  `params` may be NULL for the defaults.  On success
  * *out owns the context; release it with fgbd_ctx_destroy.
  * Errors: FGBD_EINVAL (bad capacity or parameters), FGBD_ENOMEM, FGBD_ECUDA. */
 fgbd_status fgbd_ctx_create(int64_t capacity, const fgbd_params* params, fgbd_ctx** out);

@@ -215,7 +215,7 @@ FilterArgs filter_args(fgbd_ctx* ctx, int mode, int q_fixed, const double* sigma
   a.spec_depth = 0;
   a.spec_x = ctx->spec_x;
   a.spec_z = ctx->spec_z;
-  a.cap = int(ctx->capacity);
+  a.cap = int(align_up(size_t(ctx->capacity), 64));  // row stride of spec_x / spec_z
   a.keep8 = ctx->keep8;
   return a;
 }
@@ -501,8 +501,8 @@ fgbd_status fgbd_ctx_create(int64_t capacity, const fgbd_params* params, fgbd_ct
       {reinterpret_cast<void**>(&ctx->gb.ord23), 2 * C * 4},
       {reinterpret_cast<void**>(&ctx->gb.rank2), C * 4},
       {reinterpret_cast<void**>(&ctx->gb.c4), C * 16},
-      {reinterpret_cast<void**>(&ctx->spec_x), size_t(kSpecMax) * C * 16},
-      {reinterpret_cast<void**>(&ctx->spec_z), size_t(kSpecMax) * C * 4},
+      {reinterpret_cast<void**>(&ctx->spec_x), size_t(kSpecMax) * align_up(C, 64) * 16},
+      {reinterpret_cast<void**>(&ctx->spec_z), size_t(kSpecMax) * align_up(C, 64) * 4},
       {reinterpret_cast<void**>(&ctx->keep8), C},
       {reinterpret_cast<void**>(&ctx->y8), C * 4},
       {reinterpret_cast<void**>(&ctx->yf), C * 16},

@@ -29,7 +29,7 @@ constexpr int kSqShift = 8;                        // fixed point of squared col
 constexpr int kDistShift = 20;                     // fixed point of edge lengths
 constexpr int kNeThreads = 256;
 constexpr int kFilterThreads = 512;
-constexpr int kSpecMax = 2;                        // filter steps taken while sigma_est is computed
+constexpr int kSpecMax = 3;                        // filter steps taken while sigma_est is computed
 constexpr uint32_t kCoordMask = 0x3FFFFFFFu;       // low 30 bits: packed C1 code
 constexpr uint32_t kKeepBit = 0x80000000u;         // FSLR keep flag beside the code
 
@@ -172,7 +172,7 @@ struct FilterArgs {
   int spec_depth;          // 0: none
   float4* spec_x;          // [kSpecMax][cap]: x_1 .. x_S
   int32_t* spec_z;         // [kSpecMax][cap]: per point sum_c (y^2 - x_q^2), fixed point
-  int cap;
+  int cap;                 // row stride of spec_x / spec_z, a multiple of 64
   uint8_t* keep8;          // select mode: the FSLR keep flag of every sorted point
 };
 cudaError_t launch_filter(const FilterArgs& a, int grid, cudaStream_t stream);

@@ -84,6 +84,115 @@ __device__ __forceinline__ float4 kept_value(const FilterArgs& a, int kept, int 
   return __ldcg(&(kept ? a.xbuf1 : a.xbuf0)[k]);
 }
 
+// x_0 of the sorted points k0 .. k0 + 3 (k0 a multiple of 4; those at or past
+// n only when `full` is false, and then left unread).  The packed coordinates
+// (x.w) are read only when `with_pk`.
+__device__ __forceinline__ void x0_quad(const FilterArgs& a, int k0, bool full, bool with_pk, float4 (&x)[4]) {
+  uint32_t p[4] = {0u, 0u, 0u, 0u};
+  if (with_pk) {
+    if (full) {
+      const uint4 v = *reinterpret_cast<const uint4*>(a.pk + k0);
+      p[0] = v.x;
+      p[1] = v.y;
+      p[2] = v.z;
+      p[3] = v.w;
+    } else {
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+        if (k0 + i < a.n) p[i] = a.pk[k0 + i];
+    }
+  }
+  if (a.dtype == 0) {
+    uint32_t y[4] = {0u, 0u, 0u, 0u};
+    if (full) {
+      const uint4 v = *reinterpret_cast<const uint4*>(a.y8 + k0);
+      y[0] = v.x;
+      y[1] = v.y;
+      y[2] = v.z;
+      y[3] = v.w;
+    } else {
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+        if (k0 + i < a.n) y[i] = a.y8[k0 + i];
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+      x[i] = make_float4(float(y[i] & 255u), float((y[i] >> 8) & 255u), float((y[i] >> 16) & 255u),
+                         __uint_as_float(p[i]));
+  } else {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const float4 c = (full || k0 + i < a.n) ? a.yf[k0 + i] : make_float4(0.f, 0.f, 0.f, 0.f);
+      x[i] = make_float4(c.x, c.y, c.z, __uint_as_float(p[i]));
+    }
+  }
+}
+
+// colours of the kept iterate at sorted point k (x.w is not meaningful)
+__device__ __forceinline__ float4 kept_rgb(const FilterArgs& a, int kept, int k) {
+  if (kept < 0) {
+    float r, g, b;
+    load_y(a, k, r, g, b);
+    return make_float4(r, g, b, 0.f);
+  }
+  return kept_value(a, kept, k);
+}
+
+// The kept iterate in input order: input points i0 .. i0 + 3 per thread and
+// trip, their sorted positions read as one int4 and the four gathers issued
+// together; uint8 / float32 output as 32- / 128-bit stores where aligned.
+__device__ __forceinline__ void output_quads(const FilterArgs& a, int kept, int gtid, int gstride) {
+  const int n = a.n;
+  const bool u8 = a.out_dtype == 0;
+  const bool wide = (reinterpret_cast<uintptr_t>(a.out) & (u8 ? 3u : 15u)) == 0;
+  for (int i0 = 4 * gtid; i0 < n; i0 += 4 * gstride) {
+    const bool full = i0 + 4 <= n;
+    int kk[4] = {-1, -1, -1, -1};
+    if (full) {
+      const int4 v = *reinterpret_cast<const int4*>(a.rank1 + i0);
+      kk[0] = v.x;
+      kk[1] = v.y;
+      kk[2] = v.z;
+      kk[3] = v.w;
+    } else {
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+        if (i0 + i < n) kk[i] = a.rank1[i0 + i];
+    }
+    float4 v[4];
+    bool ok[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      ok[i] = in_range(kk[i], n);
+      v[i] = ok[i] ? kept_rgb(a, kept, kk[i]) : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    if (full && wide && ok[0] && ok[1] && ok[2] && ok[3]) {
+      if (u8) {
+        uint32_t b[12];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          b[3 * i + 0] = uint32_t(fminf(fmaxf(rintf(v[i].x), 0.f), 255.f));
+          b[3 * i + 1] = uint32_t(fminf(fmaxf(rintf(v[i].y), 0.f), 255.f));
+          b[3 * i + 2] = uint32_t(fminf(fmaxf(rintf(v[i].z), 0.f), 255.f));
+        }
+        uint32_t* o = reinterpret_cast<uint32_t*>(static_cast<uint8_t*>(a.out) + 3 * size_t(i0));
+#pragma unroll
+        for (int w = 0; w < 3; ++w)
+          o[w] = b[4 * w] | (b[4 * w + 1] << 8) | (b[4 * w + 2] << 16) | (b[4 * w + 3] << 24);
+      } else {
+        float4* o = reinterpret_cast<float4*>(static_cast<float*>(a.out) + 3 * size_t(i0));
+        o[0] = make_float4(v[0].x, v[0].y, v[0].z, v[1].x);
+        o[1] = make_float4(v[1].y, v[1].z, v[2].x, v[2].y);
+        o[2] = make_float4(v[2].z, v[3].x, v[3].y, v[3].z);
+      }
+    } else {
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+        if (ok[i] && i0 + i < n) write_out(a, i0 + i, v[i]);
+    }
+  }
+}
+
 // Sums of several 64-bit values over the block (two's complement: exact in any order)
 template <int K>
 __device__ __forceinline__ void block_sums(unsigned long long (&v)[K], unsigned long long* s_red) {
@@ -135,36 +244,98 @@ __global__ void __launch_bounds__(kFilterThreads, 2) k_filter(FilterArgs a) {
     t_hi = float(thr * (1.0 + band));
   }
 
-  // ---- phase 0: keep flags and the Eq. 6 sums; x_0 = y unless the steps are stored
+  // ---- phase 0: keep flags and the Eq. 6 sums; x_0 = y unless the steps are stored.
+  // Four consecutive points per thread and trip, read with 16-byte loads that
+  // are all issued before the first is used.
   unsigned long long acc[kSums] = {};
-  for (int k = gtid; k < n; k += gstride) {
-    const float4 x0 = x0_of(a, k);
-    if (!S) a.xbuf0[k] = x0;
+  for (int k0 = 4 * gtid; k0 < n; k0 += 4 * gstride) {
+    const bool full = k0 + 4 <= n;
+    float4 x[4];
+    x0_quad(a, k0, full, !S, x);
+    float sp[4] = {0.f, 0.f, 0.f, 0.f};
     if (select) {
-      const float sp = a.spread[k];
-      bool keep;
-      if (a.all_points || sp <= t_lo) keep = true;
-      else if (sp > t_hi) keep = false;
-      else keep = !(spread_f64(a, k) > thr);
-      a.keep8[k] = keep ? 1 : 0;
-      const unsigned long long q2 = sq3(x0);
-      acc[1] += q2;
-      if (keep) {
-        acc[0] += q2;
-        acc[2] += 1;
+      if (full) {
+        const float4 v = *reinterpret_cast<const float4*>(a.spread + k0);
+        sp[0] = v.x;
+        sp[1] = v.y;
+        sp[2] = v.z;
+        sp[3] = v.w;
+      } else {
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+          if (k0 + i < n) sp[i] = a.spread[k0 + i];
+      }
+    }
+    if (!S) {
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+        if (full || k0 + i < n) a.xbuf0[k0 + i] = x[i];
+    }
+    if (select) {
+      uint32_t kw = 0;
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        if (!full && k0 + i >= n) continue;
+        bool keep;
+        if (a.all_points || sp[i] <= t_lo) keep = true;
+        else if (sp[i] > t_hi) keep = false;
+        else keep = !(spread_f64(a, k0 + i) > thr);
+        kw |= uint32_t(keep) << (8 * i);
+        const unsigned long long q2 = sq3(x[i]);
+        acc[1] += q2;
+        if (keep) {
+          acc[0] += q2;
+          acc[2] += 1;
+        }
+      }
+      if (full) {
+        *reinterpret_cast<uint32_t*>(a.keep8 + k0) = kw;
+      } else {
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+          if (k0 + i < n) a.keep8[k0 + i] = uint8_t((kw >> (8 * i)) & 1u);
       }
     }
   }
-  // the stored steps' Eq. 6 terms (a second pass: this thread's own keep flags)
+  // the stored steps' Eq. 6 terms (a second pass over this thread's own points and keep flags)
   if (S > 0) {
-    for (int k = gtid; k < n; k += gstride) {
-      const bool keep = a.keep8[k] != 0;
+    for (int k0 = 4 * gtid; k0 < n; k0 += 4 * gstride) {
+      const bool full = k0 + 4 <= n;
+      uint32_t kw = 0;
+      int32_t z[kSpecMax][4] = {};
+      if (full) kw = *reinterpret_cast<const uint32_t*>(a.keep8 + k0);
 #pragma unroll
       for (int q = 0; q < kSpecMax; ++q) {
         if (q < S) {
-          const unsigned long long z = (unsigned long long)(long long)a.spec_z[size_t(q) * size_t(a.cap) + k];
-          acc[4 + 2 * q] += z;
-          if (keep) acc[3 + 2 * q] += z;
+          const int32_t* zr = a.spec_z + size_t(q) * size_t(a.cap) + k0;
+          if (full) {
+            const int4 v = *reinterpret_cast<const int4*>(zr);
+            z[q][0] = v.x;
+            z[q][1] = v.y;
+            z[q][2] = v.z;
+            z[q][3] = v.w;
+          } else {
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+              if (k0 + i < n) z[q][i] = zr[i];
+          }
+        }
+      }
+      if (!full) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+          if (k0 + i < n) kw |= uint32_t(a.keep8[k0 + i] != 0) << (8 * i);
+      }
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const bool keep = (kw >> (8 * i)) & 1u;
+#pragma unroll
+        for (int q = 0; q < kSpecMax; ++q) {
+          if (q < S) {
+            const unsigned long long zz = (unsigned long long)(long long)z[q][i];
+            acc[4 + 2 * q] += zz;
+            if (keep) acc[3 + 2 * q] += zz;
+          }
         }
       }
     }
@@ -265,22 +436,11 @@ __global__ void __launch_bounds__(kFilterThreads, 2) k_filter(FilterArgs a) {
     if (select) sc->sel_valid = 1;
     if (select && q_limit == 0) sc->n_J = 1;
   }
-  if (a.out) {
-    for (int i = gtid; i < n; i += gstride) {
-      const int k = a.rank1[i];
-      if (!in_range(k, n)) continue;
-      write_out(a, i, kept_value(a, kept, k));
-    }
-  }
+  if (a.out) output_quads(a, kept, gtid, gstride);
 }
 
 __global__ void __launch_bounds__(256) k_output(FilterArgs a) {
-  const int kept = a.sc->kept_buf;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += gridDim.x * blockDim.x) {
-    const int k = a.rank1[i];
-    if (!in_range(k, a.n)) continue;
-    write_out(a, i, kept_value(a, kept, k));
-  }
+  output_quads(a, a.sc->kept_buf, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
 }
 
 // ---------------------------------------------------------------- export

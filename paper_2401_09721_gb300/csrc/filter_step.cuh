@@ -89,7 +89,7 @@ __device__ __forceinline__ float step_cexp(const DevScalars* sc) {
 // uses this function, so a step gives the same bits in all of them.
 __device__ __forceinline__ float4 eq5_step(const FilterArgs& a, const float4* __restrict__ src, int k, int n,
                                            float cexp) {
-  const float4 xk = src ? __ldcg(&src[k]) : x0_of(a, k);
+  const float4 xk = src ? __ldca(&src[k]) : x0_of(a, k);
   const uint32_t ck = __float_as_uint(xk.w) & kCoordMask;
   int nb[6];
   bool v[6];
@@ -111,7 +111,7 @@ __device__ __forceinline__ float4 eq5_step(const FilterArgs& a, const float4* __
   int dmin = INT_MAX;
 #pragma unroll
   for (int j = 0; j < 6; ++j) {
-    xn[j] = v[j] ? (src ? __ldcg(&src[nb[j]]) : x0_of(a, nb[j])) : xk;
+    xn[j] = v[j] ? (src ? __ldca(&src[nb[j]]) : x0_of(a, nb[j])) : xk;
     d2[j] = v[j] ? sq_dist_c1(ck, __float_as_uint(xn[j].w) & kCoordMask, a.bits) : INT_MAX;
     dmin = min(dmin, d2[j]);
   }
