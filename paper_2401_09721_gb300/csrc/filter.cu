@@ -30,9 +30,49 @@
 namespace fgbd {
 namespace {
 
-// float64 spread of point k, used only where the float32 value is too close to
-// the threshold to decide (Section 2.4: mean of the three population stds)
-__device__ double spread_f64(const FilterArgs& a, int k) {
+// ---- float-float arithmetic (an unevaluated sum hi + lo of two floats,
+// about 44 significant bits): the error-free transformations TwoSum (Knuth)
+// and TwoProduct through a fused multiply-add, as in Dekker's double-length
+// arithmetic.  Float64 is slow on this GPU; this stands in for it in the rare
+// FSLR decisions that float32 cannot take.
+struct FF {
+  float hi, lo;
+};
+__device__ __forceinline__ FF ff_fast_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ FF ff_add(FF x, FF y) {
+  const float s = __fadd_rn(x.hi, y.hi);
+  const float bb = __fsub_rn(s, x.hi);
+  const float e = __fadd_rn(__fsub_rn(x.hi, __fsub_rn(s, bb)), __fsub_rn(y.hi, bb));
+  return ff_fast_two_sum(s, __fadd_rn(e, __fadd_rn(x.lo, y.lo)));
+}
+__device__ __forceinline__ FF ff_neg(FF x) { return {-x.hi, -x.lo}; }
+__device__ __forceinline__ FF ff_mul(FF x, FF y) {
+  const float p = __fmul_rn(x.hi, y.hi);
+  const float e = fmaf(x.hi, y.hi, -p);
+  return ff_fast_two_sum(p, fmaf(x.hi, y.lo, fmaf(x.lo, y.hi, e)));
+}
+__device__ __forceinline__ FF ff_div_int(FF x, int k) {
+  const float kf = float(k);
+  const float q1 = __fdiv_rn(x.hi, kf);
+  const FF r = ff_add(x, ff_neg(ff_mul({q1, 0.f}, {kf, 0.f})));
+  return ff_fast_two_sum(q1, __fdiv_rn(r.hi, kf));
+}
+__device__ __forceinline__ FF ff_sqrt(FF x) {
+  if (!(x.hi > 0.f)) return {0.f, 0.f};
+  const float s = __fsqrt_rn(x.hi);
+  const FF r = ff_add(x, ff_neg(ff_mul({s, 0.f}, {s, 0.f})));
+  return ff_fast_two_sum(s, __fdiv_rn(r.hi, __fmul_rn(2.f, s)));
+}
+
+// The FSLR keep decision of Section 2.4, spread <= threshold, for a point whose
+// float32 spread is too close to the threshold to decide: the mean of the
+// three population standard deviations over the point and its neighbours,
+// two-pass (mean, then squared deviations) in float-float, compared with the
+// threshold given as float-float.
+__device__ __noinline__ bool keep_ff(const FilterArgs& a, int k, FF thr) {
   int nb[7];
   int cnt = 0;
   nb[cnt++] = k;
@@ -43,24 +83,23 @@ __device__ double spread_f64(const FilterArgs& a, int k) {
   if (in_range(s.y, a.n)) nb[cnt++] = s.y;
   if (in_range(s.z, a.n)) nb[cnt++] = s.z;
   if (in_range(s.w, a.n)) nb[cnt++] = s.w;
-  double mean[3] = {0.0, 0.0, 0.0};
-  for (int j = 0; j < cnt; ++j) {
-    float r, g, b;
-    load_y(a, nb[j], r, g, b);
-    mean[0] += r;
-    mean[1] += g;
-    mean[2] += b;
+  float col[3][7];
+  for (int j = 0; j < cnt; ++j) load_y(a, nb[j], col[0][j], col[1][j], col[2][j]);
+  FF total = {0.f, 0.f};
+  for (int c = 0; c < 3; ++c) {
+    FF sum = {0.f, 0.f};
+    for (int j = 0; j < cnt; ++j) sum = ff_add(sum, {col[c][j], 0.f});
+    const FF mean = ff_div_int(sum, cnt);
+    FF ss = {0.f, 0.f};
+    for (int j = 0; j < cnt; ++j) {
+      const FF d = ff_add({col[c][j], 0.f}, ff_neg(mean));
+      ss = ff_add(ss, ff_mul(d, d));
+    }
+    total = ff_add(total, ff_sqrt(ff_div_int(ss, cnt)));
   }
-  for (int c = 0; c < 3; ++c) mean[c] /= double(cnt);
-  double var[3] = {0.0, 0.0, 0.0};
-  for (int j = 0; j < cnt; ++j) {
-    float r, g, b;
-    load_y(a, nb[j], r, g, b);
-    var[0] += (r - mean[0]) * (r - mean[0]);
-    var[1] += (g - mean[1]) * (g - mean[1]);
-    var[2] += (b - mean[2]) * (b - mean[2]);
-  }
-  return (sqrt(var[0] / cnt) + sqrt(var[1] / cnt) + sqrt(var[2] / cnt)) / 3.0;
+  // mean of the three <= thr  <=>  their sum - 3 thr <= 0
+  const FF d = ff_add(total, ff_neg(ff_mul(thr, {3.f, 0.f})));
+  return d.hi < 0.f || (d.hi == 0.f && d.lo <= 0.f);
 }
 
 __device__ __forceinline__ void write_out(const FilterArgs& a, int i, float4 x) {
@@ -220,28 +259,39 @@ constexpr int kSums = 3 + 2 * kSpecMax;  // kept y^2, all y^2, kept count, then 
 __global__ void __launch_bounds__(kFilterThreads, 2) k_filter(FilterArgs a) {
   __shared__ unsigned long long s_red[(kSums + 1) * (kFilterThreads / 32)];
   __shared__ int s_ok;
-  __shared__ double s_J;
   uint32_t epoch = 0;
   const int n = a.n;
   const int gtid = blockIdx.x * blockDim.x + threadIdx.x;
   const int gstride = gridDim.x * blockDim.x;
   DevScalars* sc = a.sc;
   const bool select = a.mode == 0;
-  // the stored steps count only if the noise-estimate launch finished them
-  const int S = (select && a.spec_depth > 0 &&
-                 ld_acquire_u32(reinterpret_cast<const uint32_t*>(&sc->spec_done)) == uint32_t(a.spec_depth))
-                    ? a.spec_depth
-                    : 0;
-
-  double sigma = 0.0;
+  // Block-uniform scalars, computed by thread 0: the stored steps count only if
+  // the noise-estimate launch finished them; the FSLR threshold 2 sigma_est as
+  // a float32 band [t_lo, t_hi] (outside it float32 decides) and as float-float.
+  __shared__ int s_S;
+  __shared__ float s_thr[4];
+  if (threadIdx.x == 0) {
+    s_S = (select && a.spec_depth > 0 &&
+           ld_acquire_u32(reinterpret_cast<const uint32_t*>(&sc->spec_done)) == uint32_t(a.spec_depth))
+              ? a.spec_depth
+              : 0;
+    if (select) {
+      const double thr = a.fslr_factor * *a.sigma_src;
+      const double band = a.dtype == 0 ? 2e-6 : 5e-5;
+      s_thr[0] = float(thr * (1.0 - band));
+      s_thr[1] = float(thr * (1.0 + band));
+      s_thr[2] = float(thr);
+      s_thr[3] = float(thr - double(s_thr[2]));
+    }
+  }
+  __syncthreads();
+  const int S = s_S;
   float t_lo = 0.f, t_hi = 0.f;
-  double thr = 0.0;
+  FF thr = {0.f, 0.f};
   if (select) {
-    sigma = *a.sigma_src;
-    thr = a.fslr_factor * sigma;
-    const double band = a.dtype == 0 ? 2e-6 : 5e-5;
-    t_lo = float(thr * (1.0 - band));
-    t_hi = float(thr * (1.0 + band));
+    t_lo = s_thr[0];
+    t_hi = s_thr[1];
+    thr = {s_thr[2], s_thr[3]};
   }
 
   // ---- phase 0: keep flags and the Eq. 6 sums; x_0 = y unless the steps are stored.
@@ -279,7 +329,7 @@ __global__ void __launch_bounds__(kFilterThreads, 2) k_filter(FilterArgs a) {
         bool keep;
         if (a.all_points || sp[i] <= t_lo) keep = true;
         else if (sp[i] > t_hi) keep = false;
-        else keep = !(spread_f64(a, k0 + i) > thr);
+        else keep = keep_ff(a, k0 + i, thr);
         kw |= uint32_t(keep) << (8 * i);
         const unsigned long long q2 = sq3(x[i]);
         acc[1] += q2;
@@ -357,41 +407,54 @@ __global__ void __launch_bounds__(kFilterThreads, 2) k_filter(FilterArgs a) {
   }
   if (!grid_barrier(&sc->barrier, &sc->status, gridDim.x, epoch, &s_ok)) return;
 
-  bool keep_all = false;
+  // J(0..S) from the stored terms, by thread 0 of each block (every block
+  // reaches the same values: the sums are exact integers)
+  __shared__ int s_ctl[4];  // keep_all, q_limit, q_final, stop
+  __shared__ float s_cexp;
+  double sigma = 0.0, nsel = 1.0, J_prev = 0.0;  // thread 0 only
   unsigned long long ysq = 0;
-  double nsel = 1.0;
-  if (select) {
-    const unsigned long long nkt = ld_relaxed_u64(&sc->n_keep);
-    keep_all = nkt == 0;  // no point left: every point is used
-    nsel = keep_all ? double(n) : double(nkt);
-    ysq = keep_all ? ld_relaxed_u64(&sc->ysq_all) : ld_relaxed_u64(&sc->ysq_keep);
-  }
-  const float cexp = step_cexp(sc);
-
-  double J_prev = sigma * sigma;  // J(0): nothing filtered yet
-  if (select && gtid == 0) sc->J[0] = J_prev;
-  int q_final = 0;
-  bool stopped = false;
-  const int q_fixed = a.q_src ? min(max(*a.q_src, 0), kQCap) : a.q_fixed;
-  const int q_limit = n == 0 ? 0 : (select ? a.q_max : q_fixed);
-  // J(1..S) from the stored terms
-  for (int t = 1; t <= min(S, q_limit); ++t) {
-    const unsigned long long* src = reinterpret_cast<const unsigned long long*>(keep_all ? &sc->spec_all[t]
-                                                                                          : &sc->spec_keep[t]);
-    const double lost = double((long long)ld_relaxed_u64(src)) * (1.0 / double(1 << kSqShift));
-    const double J = fabs(sigma * sigma - lost / (3.0 * nsel));
-    if (gtid == 0) {
-      sc->J[t] = J;
-      sc->n_J = t + 1;
+  if (threadIdx.x == 0) {
+    s_cexp = step_cexp(sc);
+    const int q_fixed = a.q_src ? min(max(*a.q_src, 0), kQCap) : a.q_fixed;
+    const int q_limit = n == 0 ? 0 : (select ? a.q_max : q_fixed);
+    int keep_all = 0, q_final = 0, stopped = 0;
+    if (select) {
+      sigma = *a.sigma_src;
+      const unsigned long long nkt = ld_relaxed_u64(&sc->n_keep);
+      keep_all = nkt == 0;  // no point left: every point is used
+      nsel = keep_all ? double(n) : double(nkt);
+      ysq = keep_all ? ld_relaxed_u64(&sc->ysq_all) : ld_relaxed_u64(&sc->ysq_keep);
+      J_prev = sigma * sigma;  // J(0): nothing filtered yet
+      if (blockIdx.x == 0) sc->J[0] = J_prev;
+      for (int t = 1; t <= min(S, q_limit); ++t) {
+        const unsigned long long* src = reinterpret_cast<const unsigned long long*>(
+            keep_all ? &sc->spec_all[t] : &sc->spec_keep[t]);
+        const double lost = double((long long)ld_relaxed_u64(src)) * (1.0 / double(1 << kSqShift));
+        const double J = fabs(sigma * sigma - lost / (3.0 * nsel));
+        if (blockIdx.x == 0) {
+          sc->J[t] = J;
+          sc->n_J = t + 1;
+        }
+        if (J >= J_prev) {
+          q_final = t - 1;
+          stopped = 1;
+          break;
+        }
+        J_prev = J;
+        q_final = t;
+      }
     }
-    if (J >= J_prev) {
-      q_final = t - 1;
-      stopped = true;
-      break;
-    }
-    J_prev = J;
-    q_final = t;
+    s_ctl[0] = keep_all;
+    s_ctl[1] = q_limit;
+    s_ctl[2] = q_final;
+    s_ctl[3] = stopped;
   }
+  __syncthreads();
+  const float cexp = s_cexp;
+  const bool keep_all = s_ctl[0] != 0;
+  const int q_limit = s_ctl[1];
+  int q_final = s_ctl[2];
+  const bool stopped = s_ctl[3] != 0;
   for (int t = S + 1; t <= q_limit && !stopped; ++t) {
     const float4* __restrict__ src =
         (S > 0 && t == S + 1) ? a.spec_x + size_t(S - 1) * size_t(a.cap) : ((t & 1) ? a.xbuf0 : a.xbuf1);
@@ -406,24 +469,26 @@ __global__ void __launch_bounds__(kFilterThreads, 2) k_filter(FilterArgs a) {
       loc = block_sum_u64<kFilterThreads>(loc, s_red);
       if (threadIdx.x == 0 && loc) atomicAdd(&sc->sumsq[t], loc);
     }
+    // (the barrier starts with __syncthreads: every thread has read s_ctl[3])
     if (!grid_barrier(&sc->barrier, &sc->status, gridDim.x, epoch, &s_ok)) return;
     if (select) {
       if (threadIdx.x == 0) {
         const unsigned long long ss = ld_relaxed_u64(&sc->sumsq[t]);
         const double lost = double((long long)(ysq - ss)) * (1.0 / double(1 << kSqShift));
-        s_J = fabs(sigma * sigma - lost / (3.0 * nsel));
+        const double J = fabs(sigma * sigma - lost / (3.0 * nsel));
+        if (blockIdx.x == 0) {
+          sc->J[t] = J;
+          sc->n_J = t + 1;
+        }
+        s_ctl[3] = J >= J_prev;
+        if (!(J >= J_prev)) J_prev = J;
       }
       __syncthreads();
-      const double J = s_J;
-      if (gtid == 0) sc->J[t] = J;
-      if (J >= J_prev) {
+      if (s_ctl[3]) {
         q_final = t - 1;
-        if (gtid == 0) sc->n_J = t + 1;
         break;
       }
-      J_prev = J;
       q_final = t;
-      if (gtid == 0) sc->n_J = t + 1;
     } else {
       q_final = t;
     }

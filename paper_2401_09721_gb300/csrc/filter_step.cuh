@@ -82,6 +82,14 @@ __device__ __forceinline__ float step_cexp(const DevScalars* sc) {
   return sg > 0.0 ? float(1.4426950408889634 / (sg * sg)) : 0.f;
 }
 
+// The same, computed once per block by thread 0 and shared: float64 work is
+// slow on this GPU, and every thread computing it costs microseconds.
+__device__ __forceinline__ float block_cexp(const DevScalars* sc, float* s_cexp) {
+  if (threadIdx.x == 0) *s_cexp = step_cexp(sc);
+  __syncthreads();
+  return *s_cexp;
+}
+
 // One Eq. 5 step at sorted point k: x_k / 2 + (sum_j e_j x_j) / (2 sum_j e_j)
 // over the neighbours (C1 k - 1, k + 1, the C2/C3 slots) with
 // e_j = exp(-(d2_j - min d2) / sigma_g^2), from the previous iterate `src` (x_0
@@ -140,14 +148,15 @@ __device__ __forceinline__ float4 eq5_step(const FilterArgs& a, const float4* __
 // sum_c (y^2 - x_q^2) in fixed point beside them, by the blocks [first,
 // gridDim.x) of a cooperative grid (they need the graph and the colours
 // only, not sigma_est).  sc->spec_done = depth once every step is stored.
-__device__ __forceinline__ void speculative_steps(const FilterArgs& a, int depth, int first, int* s_ok) {
+__device__ __forceinline__ void speculative_steps(const FilterArgs& a, int depth, int first, int* s_ok,
+                                                  float* s_cexp) {
   uint32_t epoch = 0;
   const int n = a.n;
   const uint32_t members = gridDim.x - uint32_t(first);
   const int gtid = (blockIdx.x - first) * blockDim.x + threadIdx.x;
   const int gstride = int(members) * blockDim.x;
   DevScalars* sc = a.sc;
-  const float cexp = step_cexp(sc);
+  const float cexp = block_cexp(sc, s_cexp);
   for (int t = 1; t <= depth; ++t) {
     const float4* src = t == 1 ? nullptr : a.spec_x + size_t(t - 2) * size_t(a.cap);
     float4* dst = a.spec_x + size_t(t - 1) * size_t(a.cap);

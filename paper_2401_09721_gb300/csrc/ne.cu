@@ -764,11 +764,12 @@ __global__ void __launch_bounds__(kSpecThreads, 1)
     k_ne_finalize_spec(int dtype, const double* __restrict__ f64_partials, int nblocks, DevScalars* __restrict__ sc,
                        double* __restrict__ sigma_out, FilterArgs a) {
   __shared__ int s_ok;
+  __shared__ float s_cexp;
   if (blockIdx.x == 0) {
     if (threadIdx.x < kFinThreads) finalize_block(dtype, f64_partials, nblocks, sc, sigma_out);
     return;
   }
-  speculative_steps(a, a.spec_depth, 1, &s_ok);
+  speculative_steps(a, a.spec_depth, 1, &s_ok, &s_cexp);
 }
 
 }  // namespace
