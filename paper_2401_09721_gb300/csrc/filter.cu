@@ -68,36 +68,81 @@ __device__ __forceinline__ FF ff_sqrt(FF x) {
 }
 
 // The FSLR keep decision of Section 2.4, spread <= threshold, for a point whose
-// float32 spread is too close to the threshold to decide: the mean of the
-// three population standard deviations over the point and its neighbours,
-// two-pass (mean, then squared deviations) in float-float, compared with the
-// threshold given as float-float.
+// float32 spread is too close to the threshold to decide.  The spread is the
+// mean of the three population standard deviations over the point and its
+// neighbours; the decision compares their sum with 3 thr (thr as float-float).
+// uint8 colours: cnt^2 times each variance is the integer cnt sum x^2 - (sum x)^2
+// (below 2^22, exact in float32), so only the three square roots need float-float.
+// float colours: two-pass (mean, then squared deviations) in float-float.
 __device__ __noinline__ bool keep_ff(const FilterArgs& a, int k, FF thr) {
   int nb[7];
-  int cnt = 0;
-  nb[cnt++] = k;
-  if (k > 0) nb[cnt++] = k - 1;
-  if (k + 1 < a.n) nb[cnt++] = k + 1;
+  bool v[7];
+  nb[0] = k;
+  v[0] = true;
+  nb[1] = k - 1;
+  v[1] = k > 0;
+  nb[2] = k + 1;
+  v[2] = k + 1 < a.n;
   const int4 s = a.c4[k];
-  if (in_range(s.x, a.n)) nb[cnt++] = s.x;
-  if (in_range(s.y, a.n)) nb[cnt++] = s.y;
-  if (in_range(s.z, a.n)) nb[cnt++] = s.z;
-  if (in_range(s.w, a.n)) nb[cnt++] = s.w;
-  float col[3][7];
-  for (int j = 0; j < cnt; ++j) load_y(a, nb[j], col[0][j], col[1][j], col[2][j]);
+  nb[3] = s.x;
+  nb[4] = s.y;
+  nb[5] = s.z;
+  nb[6] = s.w;
+#pragma unroll
+  for (int j = 3; j < 7; ++j) v[j] = in_range(nb[j], a.n);
+  int cnt = 0;
+#pragma unroll
+  for (int j = 0; j < 7; ++j) cnt += v[j];
   FF total = {0.f, 0.f};
-  for (int c = 0; c < 3; ++c) {
+  if (a.dtype == 0) {
+    uint32_t c[7];
+#pragma unroll
+    for (int j = 0; j < 7; ++j) c[j] = v[j] ? a.y8[nb[j]] : 0u;
+#pragma unroll
+    for (int ch = 0; ch < 3; ++ch) {
+      int sx = 0, sq = 0;
+#pragma unroll
+      for (int j = 0; j < 7; ++j) {
+        const int x = int((c[j] >> (8 * ch)) & 255u);
+        sx += x;
+        sq += x * x;
+      }
+      const int V = cnt * sq - sx * sx;  // cnt^2 var; absent neighbours read as 0 and add nothing
+      total = ff_add(total, ff_sqrt({float(V), 0.f}));
+    }
+    // sum_c sqrt(V_c) / cnt against 3 thr
+    const FF d = ff_add(total, ff_neg(ff_mul(thr, {3.f * float(cnt), 0.f})));
+    return d.hi < 0.f || (d.hi == 0.f && d.lo <= 0.f);
+  }
+  float col[3][7];
+#pragma unroll
+  for (int j = 0; j < 7; ++j) {
+    if (v[j]) {
+      const float4 y = a.yf[nb[j]];
+      col[0][j] = y.x;
+      col[1][j] = y.y;
+      col[2][j] = y.z;
+    } else {
+      col[0][j] = col[1][j] = col[2][j] = 0.f;
+    }
+  }
+#pragma unroll
+  for (int ch = 0; ch < 3; ++ch) {
     FF sum = {0.f, 0.f};
-    for (int j = 0; j < cnt; ++j) sum = ff_add(sum, {col[c][j], 0.f});
+#pragma unroll
+    for (int j = 0; j < 7; ++j)
+      if (v[j]) sum = ff_add(sum, {col[ch][j], 0.f});
     const FF mean = ff_div_int(sum, cnt);
     FF ss = {0.f, 0.f};
-    for (int j = 0; j < cnt; ++j) {
-      const FF d = ff_add({col[c][j], 0.f}, ff_neg(mean));
-      ss = ff_add(ss, ff_mul(d, d));
+#pragma unroll
+    for (int j = 0; j < 7; ++j) {
+      if (v[j]) {
+        const FF d = ff_add({col[ch][j], 0.f}, ff_neg(mean));
+        ss = ff_add(ss, ff_mul(d, d));
+      }
     }
     total = ff_add(total, ff_sqrt(ff_div_int(ss, cnt)));
   }
-  // mean of the three <= thr  <=>  their sum - 3 thr <= 0
   const FF d = ff_add(total, ff_neg(ff_mul(thr, {3.f, 0.f})));
   return d.hi < 0.f || (d.hi == 0.f && d.lo <= 0.f);
 }

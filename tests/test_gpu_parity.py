@@ -344,3 +344,32 @@ def test_repeated_runs_are_deterministic(F):
     stats = [ctx.stats() for _ in range(1)]
     assert np.array_equal(outs[0], outs[1]) and np.array_equal(outs[1], outs[2])
     assert stats[0]["q"] >= 0
+
+
+@pytest.mark.parametrize("dtype", ["u8", "f32"])
+def test_fslr_band_decisions(F, dtype):
+    """Section 2.4's keep rule where float32 cannot decide: thresholds 1e-9
+    (relative) above and below a point's spread put that point inside the
+    kernel's float32 uncertainty band, so the exact path decides it; the
+    oracle's float64 spread says which way."""
+    xyz = synth.torso_points(20000, 8, 9)
+    clean = synth.piecewise_colors(xyz, 8, 9)
+    rgb = synth.add_noise_u8(clean, 20.0, 9) if dtype == "u8" else synth.add_noise_f32(clean, 20.0, 9)
+    res = orc.fgbd(xyz, rgb, orc.Params(bits=8))
+    ctx = F.Context(len(xyz), bits=8)
+    x = torch.from_numpy(xyz).cuda()
+    c = torch.from_numpy(np.ascontiguousarray(rgb)).cuda()
+    ctx.build_graph(x)
+    ctx.estimate_noise(c)
+    sp = res.spread
+    order = np.argsort(sp, kind="stable")
+    picks = order[[len(sp) // 5, len(sp) // 3, len(sp) // 2, 2 * len(sp) // 3]]
+    for p in picks:
+        for sign in (+1.0, -1.0):
+            thr = sp[p] * (1.0 + sign * 1e-9)
+            ctx.select_filter(c, sigma_est=torch.tensor([thr / 2.0], dtype=torch.float64, device="cuda"))
+            _, keep = ctx.fslr()
+            keep = keep.cpu().numpy().astype(bool)
+            assert keep[p] == (sign > 0), (p, sign)
+            near = np.abs(sp - thr) <= 1e-11 * thr
+            assert np.array_equal(keep[~near], ~(sp > thr)[~near])
