@@ -315,7 +315,7 @@ fgbd_status do_build(fgbd_ctx* ctx, const int32_t* xyz, int64_t n64, cudaStream_
         FGBD_LAUNCH(ctx, "slg_slab", st,
                     launch_slab_sort(n, bits, int(ctx->capacity), ctx->sb, ctx->gb, ctx->sc, st));
     }
-    FGBD_LAUNCH(ctx, "slg_link", st, launch_link(n, bits, int(ctx->capacity), ctx->gb, ctx->sc, ctx->num_sms, st));
+    FGBD_LAUNCH(ctx, "slg_link", st, launch_link(n, bits, int(ctx->capacity), ctx->gb, ctx->sb, ctx->sc, ctx->num_sms, st));
   }
   ctx->has_graph = true;
   return FGBD_OK;

@@ -91,7 +91,7 @@ struct GraphBufs {
   int32_t* perm1;    // [cap] input index of each sorted (C1-order) point
   int32_t* rank1;    // [cap] sorted id of each input point
   uint32_t* pk;      // [cap] packed C1 code of each sorted point (its coordinates)
-  int32_t* ord23;    // [2][cap] sorted ids along C2; input indices along C3
+  int32_t* ord23;    // [2][cap] sorted ids along C2, then along C3
   int32_t* rank2;    // [cap] position of each sorted id in the C2 order
   int4* c4;          // [cap] C2 prev, C2 next, C3 prev, C3 next (sorted ids, -1 empty)
 };
@@ -109,6 +109,7 @@ struct SortPassArgs {
   uint32_t* keys_out;      // null: not written
   uint32_t* vals_out;
   int32_t* rank_out;       // rank_out[value] = output position, or null
+  int32_t* pos_out;        // pos_out[input position] = output position, or null
   uint32_t* counts;
   const DevScalars* sc;
 };
@@ -130,8 +131,8 @@ cudaError_t launch_tile_scan(const SortPassArgs& a, cudaStream_t stream);
 cudaError_t launch_sort_scatter(const SortPassArgs& a, cudaStream_t stream);
 cudaError_t launch_sort_pass(const SortPassArgs& a, cudaStream_t stream);  // the three above
 cudaError_t launch_orders_export(int n, int cap, const GraphBufs& gb, int32_t* out, cudaStream_t stream);
-cudaError_t launch_link(int n, int bits, int cap, const GraphBufs& gb, DevScalars* sc, int num_sms,
-                        cudaStream_t stream);
+cudaError_t launch_link(int n, int bits, int cap, const GraphBufs& gb, const SortBufs& sb, DevScalars* sc,
+                        int num_sms, cudaStream_t stream);
 
 cudaError_t launch_gather_colors(const void* rgb, int dtype, int n, const int32_t* perm1,
                                  uint32_t* y8, float4* yf, cudaStream_t stream);

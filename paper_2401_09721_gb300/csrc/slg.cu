@@ -2,25 +2,26 @@
 //
 // Sorting by a code of Eq. 1-3 is sorting by three b-bit coordinates, most
 // significant first.  The digits of the radix passes are the coordinates
-// themselves (2^b bins):
-//   C1 = (z, y, x): one stable pass on z (most significant digit first) puts
-//        every z-slab in place; k_slab_sort then sorts each slab by (y, x) in
-//        shared memory, one block per slab: two stable passes, x then y;
-//   C2 = (x, z, y): one stable pass on x over the C1 order (among points
-//        with equal x the C1 order already ranks them by (z, y));
-//   C3 = (y, x, z): one stable pass on y over the C2 order (among points
-//        with equal y the C2 order ranks them by (x, z)).
-// Ties keep input order throughout, so equal codes are ordered by index.  The
-// digit totals of every pass are the three coordinate histograms, taken once
-// (k_coord_hist).  Each global pass is reduce-then-scan:
+// themselves (2^b bins), and ties keep input order throughout, so equal codes
+// are ordered by index:
+//   pass 0   one stable pass on y over the input puts every y-slab in place;
+//   slab     k_slab_sort sorts each y-slab by (x, z) in shared memory, one
+//            block per slab (two stable passes, z then x): the C3 = (y, x, z)
+//            order;
+//   pass 1   C1 = (z, y, x): one stable pass on z over the C3 order (among
+//            points with equal z the C3 order already ranks them by (y, x));
+//   pass 2   C2 = (x, z, y): one stable pass on x over the C1 order (among
+//            points with equal x the C1 order ranks them by (z, y)).
+// The digit totals of every pass are the three coordinate histograms, taken
+// once (k_coord_hist).  Each global pass is reduce-then-scan:
 //   k_tile_counts   digit counts of every 4096-key tile;
 //   k_tile_scan     each tile's global start of every digit;
 //   k_sort_scatter  stable in-tile rank (one ballot per digit bit) and
 //                   write-out in digit runs.
-// The C1 step ends with the packed C1 code of every sorted point, its input
-// index and the rank of every input point; the C2/C3 passes carry (code,
-// sorted id) and end with the sorted ids along C2 and C3 and the C2 rank of
-// every sorted id.
+// Keys are the packed C1 codes in every pass.  Pass 1 ends with the packed
+// code of every sorted (C1) point, its input index, the rank of every input
+// point, and the C3 order rewritten as sorted ids; pass 2 ends with the sorted
+// ids along C2, their packed codes, and the C2 rank of every sorted id.
 // k_link: points consecutive along a code are linked.  In C1 order the code-1
 // neighbours are implicit (k-1, k+1); C2/C3 neighbours are written as slots;
 // a pair already linked by an earlier code is left out so the union is a set,
@@ -283,6 +284,10 @@ __global__ void __launch_bounds__(kScatterThreads, 2) k_sort_scatter(SortPassArg
       const uint32_t lp = s_tstart[dj] + ((wh[dj] >> half) & 0xffffu) + rnk[j];
       s_keys[lp] = key[j];
       s_vals[lp] = val[j];
+      if (a.pos_out) {
+        const uint32_t g = s_gbase[dj] + (lp - s_tstart[dj]);
+        if (g < uint32_t(a.n)) a.pos_out[warp_base + j * 32 + lane] = int32_t(g);
+      }
     }
   }
   __syncthreads();
@@ -539,8 +544,9 @@ __global__ void __launch_bounds__(kSlabThreads, 4)
 }
 
 // One thread per position r of one code's order (blockIdx.y = code).  Code 0
-// is the C1 order itself; code 1 reads the sorted ids along C2, code 2 the
-// input indices along C3 (mapped to sorted ids through rank1).
+// is the C1 order itself; codes 1 and 2 read the sorted ids along C2 and C3
+// and the packed C1 codes in the same order (keys of the C2 pass; keys of the
+// slab sort for C3), so only the C2 rank of a C3 point is a gather.
 // The ids at r-1 and r+1 come from the adjacent lanes, with one extra lookup
 // at each end of the warp.
 struct LinkPt {
@@ -550,34 +556,35 @@ struct LinkPt {
 };
 
 __device__ __forceinline__ LinkPt link_point(int r, int n, int code, const int32_t* __restrict__ ord,
-                                             const int32_t* __restrict__ rank1, const int32_t* __restrict__ rank2,
+                                             const uint32_t* __restrict__ keys, const int32_t* __restrict__ rank2,
                                              const uint32_t* __restrict__ pk) {
   LinkPt q{-1, -1, 0u};
   if (r < 0 || r >= n) return q;
-  int k = code == 0 ? r : ord[r];
-  if (code == 2) k = in_range(k, n) ? rank1[k] : -1;
+  const int k = code == 0 ? r : ord[r];
   if (!in_range(k, n)) return q;
   q.k = k;
-  q.c = pk[k];
+  q.c = code == 0 ? pk[r] : keys[r];
   if (code == 2) q.r2 = rank2[k];
   return q;
 }
 
 __global__ void __launch_bounds__(256) k_link(int n, int bits, int cap, const int32_t* __restrict__ ord23,
-                                              const int32_t* __restrict__ rank1, const int32_t* __restrict__ rank2,
-                                              const uint32_t* __restrict__ pk, int4* __restrict__ c4,
-                                              DevScalars* __restrict__ sc) {
+                                              const uint32_t* __restrict__ keys_c2,
+                                              const uint32_t* __restrict__ keys_c3,
+                                              const int32_t* __restrict__ rank2, const uint32_t* __restrict__ pk,
+                                              int4* __restrict__ c4, DevScalars* __restrict__ sc) {
   __shared__ unsigned long long s_red[8];
   const int code = blockIdx.y;
   const int lane = threadIdx.x & 31;
   const int32_t* ord = code == 0 ? nullptr : ord23 + size_t(code - 1) * size_t(cap);
+  const uint32_t* keys = code == 1 ? keys_c2 : keys_c3;
   unsigned long long edges = 0;
   float dist_f = 0.f;  // this thread's few edge lengths; converted to fixed point once
   const int stride = gridDim.x * blockDim.x;
   // whole warps step together so the shuffles see every lane
   for (int base = blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < n; base += stride) {
     const int r = base + lane;
-    const LinkPt me = link_point(r, n, code, ord, rank1, rank2, pk);
+    const LinkPt me = link_point(r, n, code, ord, keys, rank2, pk);
     LinkPt prev, next;
     prev.k = __shfl_up_sync(0xffffffffu, me.k, 1);
     prev.r2 = __shfl_up_sync(0xffffffffu, me.r2, 1);
@@ -585,8 +592,8 @@ __global__ void __launch_bounds__(256) k_link(int n, int bits, int cap, const in
     next.k = __shfl_down_sync(0xffffffffu, me.k, 1);
     next.r2 = __shfl_down_sync(0xffffffffu, me.r2, 1);
     next.c = __shfl_down_sync(0xffffffffu, me.c, 1);
-    if (lane == 0) prev = link_point(r - 1, n, code, ord, rank1, rank2, pk);
-    if (lane == 31) next = link_point(r + 1, n, code, ord, rank1, rank2, pk);
+    if (lane == 0) prev = link_point(r - 1, n, code, ord, keys, rank2, pk);
+    if (lane == 31) next = link_point(r + 1, n, code, ord, keys, rank2, pk);
     if (me.k < 0) continue;
     // the edge to the next position: counted once, unless an earlier code links the pair
     bool dup_next = true;
@@ -616,7 +623,7 @@ __global__ void __launch_bounds__(256) k_link(int n, int bits, int cap, const in
   }
 }
 
-// The three orders in input indices: C1 from perm1, C2 through perm1, C3 as held.
+// The three orders in input indices: C1 from perm1, C2 and C3 through perm1.
 __global__ void __launch_bounds__(256) k_orders_export(int n, int cap, const int32_t* __restrict__ perm1,
                                                        const int32_t* __restrict__ ord23, int32_t* __restrict__ out) {
   const int stride = gridDim.x * blockDim.x;
@@ -624,8 +631,8 @@ __global__ void __launch_bounds__(256) k_orders_export(int n, int cap, const int
     out[r] = perm1[r];
     const int k = ord23[r];
     out[size_t(n) + r] = in_range(k, n) ? perm1[k] : -1;
-    const int i = ord23[size_t(cap) + r];
-    out[2 * size_t(n) + r] = in_range(i, n) ? i : -1;
+    const int k3 = ord23[size_t(cap) + r];
+    out[2 * size_t(n) + r] = in_range(k3, n) ? perm1[k3] : -1;
   }
 }
 
@@ -692,11 +699,12 @@ cudaError_t launch_slab_sort(int n, int bits, int cap, const SortBufs& sb, const
   return cudaGetLastError();
 }
 
-cudaError_t launch_link(int n, int bits, int cap, const GraphBufs& gb, DevScalars* sc, int num_sms,
-                        cudaStream_t stream) {
+cudaError_t launch_link(int n, int bits, int cap, const GraphBufs& gb, const SortBufs& sb, DevScalars* sc,
+                        int num_sms, cudaStream_t stream) {
   if (n <= 0) return cudaSuccess;
   const int gx = std::max(1, std::min((n + 255) / 256, num_sms * 8));
-  k_link<<<dim3(gx, 3), 256, 0, stream>>>(n, bits, cap, gb.ord23, gb.rank1, gb.rank2, gb.pk, gb.c4, sc);
+  k_link<<<dim3(gx, 3), 256, 0, stream>>>(n, bits, cap, gb.ord23, sb.keys[0], sb.keys[1], gb.rank2, gb.pk, gb.c4,
+                                          sc);
   return cudaGetLastError();
 }
 
@@ -725,7 +733,8 @@ SortPassArgs slg_pass_args(int pass, const int32_t* xyz, int n, int bits, int ca
     return a;
   }
   if (pass == 1) {
-    // C1: the C3 order (from the slab sort) on z; ends with pk, perm1, rank1
+    // C1: the C3 order (from the slab sort) on z; ends with pk, perm1, rank1 and the C3
+    // order as sorted ids
     a.shift = 2 * bits;
     a.coord = 2;
     a.keys_in = sb.keys[1];
@@ -733,6 +742,7 @@ SortPassArgs slg_pass_args(int pass, const int32_t* xyz, int n, int bits, int ca
     a.keys_out = gb.pk;
     a.vals_out = reinterpret_cast<uint32_t*>(gb.perm1);
     a.rank_out = gb.rank1;
+    a.pos_out = gb.ord23 + size_t(cap);  // the C3 order now as sorted ids (over the input indices read here)
     return a;
   }
   // C2: the C1 order (value = position = sorted id) on x
@@ -740,7 +750,7 @@ SortPassArgs slg_pass_args(int pass, const int32_t* xyz, int n, int bits, int ca
   a.coord = 0;
   a.keys_in = gb.pk;
   a.vals_in = nullptr;
-  a.keys_out = nullptr;
+  a.keys_out = sb.keys[0];  // the packed codes along C2, for the link step
   a.vals_out = reinterpret_cast<uint32_t*>(gb.ord23);
   a.rank_out = gb.rank2;
   return a;
