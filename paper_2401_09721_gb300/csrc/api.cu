@@ -156,6 +156,10 @@ struct LaunchScope {
 
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
+// distance between the C2 and C3 halves of ord23: a multiple of 64 points, so
+// both halves start 256-byte aligned
+int ord_stride(const fgbd_ctx* ctx) { return int(align_up(size_t(ctx->capacity), 64)); }
+
 bool params_ok(const fgbd_params& p) {
   if (p.bits < 1 || p.bits > kMaxBits) return false;
   if (p.window < 1) return false;
@@ -307,15 +311,15 @@ fgbd_status do_build(fgbd_ctx* ctx, const int32_t* xyz, int64_t n64, cudaStream_
     static const char* const kScatter[kSlgPasses] = {"slg_scatter0", "slg_scatter1", "slg_scatter2"};
     FGBD_LAUNCH(ctx, "slg_hist", st, launch_coord_hist(xyz, n, bits, ctx->sc, ctx->num_sms, st));
     for (int p = 0; p < kSlgPasses; ++p) {
-      const SortPassArgs a = slg_pass_args(p, xyz, n, bits, int(ctx->capacity), ctx->sb, ctx->gb, ctx->sc);
+      const SortPassArgs a = slg_pass_args(p, xyz, n, bits, ord_stride(ctx), ctx->sb, ctx->gb, ctx->sc);
       FGBD_LAUNCH(ctx, kCounts[p], st, launch_tile_counts(a, st));
       FGBD_LAUNCH(ctx, kScan[p], st, launch_tile_scan(a, st));
       FGBD_LAUNCH(ctx, kScatter[p], st, launch_sort_scatter(a, st));
       if (p == 0)
         FGBD_LAUNCH(ctx, "slg_slab", st,
-                    launch_slab_sort(n, bits, int(ctx->capacity), ctx->sb, ctx->gb, ctx->sc, st));
+                    launch_slab_sort(n, bits, ord_stride(ctx), ctx->sb, ctx->gb, ctx->sc, st));
     }
-    FGBD_LAUNCH(ctx, "slg_link", st, launch_link(n, bits, int(ctx->capacity), ctx->gb, ctx->sb, ctx->sc, ctx->num_sms, st));
+    FGBD_LAUNCH(ctx, "slg_link", st, launch_link(n, bits, ord_stride(ctx), ctx->gb, ctx->sb, ctx->sc, ctx->num_sms, st));
   }
   ctx->has_graph = true;
   return FGBD_OK;
@@ -498,7 +502,7 @@ fgbd_status fgbd_ctx_create(int64_t capacity, const fgbd_params* params, fgbd_ct
       {reinterpret_cast<void**>(&ctx->gb.perm1), C * 4},
       {reinterpret_cast<void**>(&ctx->gb.rank1), C * 4},
       {reinterpret_cast<void**>(&ctx->gb.pk), C * 4},
-      {reinterpret_cast<void**>(&ctx->gb.ord23), 2 * C * 4},
+      {reinterpret_cast<void**>(&ctx->gb.ord23), 2 * align_up(C, 64) * 4},
       {reinterpret_cast<void**>(&ctx->gb.rank2), C * 4},
       {reinterpret_cast<void**>(&ctx->gb.c4), C * 16},
       {reinterpret_cast<void**>(&ctx->spec_x), size_t(kSpecMax) * align_up(C, 64) * 16},
@@ -867,7 +871,7 @@ fgbd_status fgbd_get_orders(fgbd_ctx* ctx, int32_t* orders, void* stream) {
   if (!ctx->has_graph) return FGBD_ESTATE;
   if (ctx->n > 0 && !orders) return FGBD_EINVAL;
   const cudaStream_t st = as_stream(stream);
-  FGBD_LAUNCH(ctx, "orders_export", st, launch_orders_export(ctx->n, int(ctx->capacity), ctx->gb, orders, st));
+  FGBD_LAUNCH(ctx, "orders_export", st, launch_orders_export(ctx->n, ord_stride(ctx), ctx->gb, orders, st));
   return FGBD_OK;
 }
 

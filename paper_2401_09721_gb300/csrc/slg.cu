@@ -543,12 +543,13 @@ __global__ void __launch_bounds__(kSlabThreads, 4)
   }
 }
 
-// One thread per position r of one code's order (blockIdx.y = code).  Code 0
-// is the C1 order itself; codes 1 and 2 read the sorted ids along C2 and C3
-// and the packed C1 codes in the same order (keys of the C2 pass; keys of the
-// slab sort for C3), so only the C2 rank of a C3 point is a gather.
-// The ids at r-1 and r+1 come from the adjacent lanes, with one extra lookup
-// at each end of the warp.
+// One code's order per grid row (blockIdx.y = code).  Code 0 is the C1 order
+// itself; codes 1 and 2 read the sorted ids along C2 and C3 and the packed C1
+// codes in the same order (keys of the C2 pass; keys of the slab sort for C3),
+// so only the C2 rank of a C3 point is a gather.  Each lane takes four
+// consecutive positions (16-byte loads, the C2 rank gathers issued together);
+// the neighbours across lanes come from shuffles, with one extra lookup at
+// each end of the warp.
 struct LinkPt {
   int k;       // sorted (C1) id, -1 outside [0, n)
   int r2;      // position in the C2 order (code 2 only)
@@ -556,67 +557,117 @@ struct LinkPt {
 };
 
 __device__ __forceinline__ LinkPt link_point(int r, int n, int code, const int32_t* __restrict__ ord,
-                                             const uint32_t* __restrict__ keys, const int32_t* __restrict__ rank2,
-                                             const uint32_t* __restrict__ pk) {
+                                             const uint32_t* __restrict__ keys, const int32_t* __restrict__ rank2) {
   LinkPt q{-1, -1, 0u};
   if (r < 0 || r >= n) return q;
   const int k = code == 0 ? r : ord[r];
   if (!in_range(k, n)) return q;
   q.k = k;
-  q.c = code == 0 ? pk[r] : keys[r];
+  q.c = keys[r];
   if (code == 2) q.r2 = rank2[k];
   return q;
 }
 
-__global__ void __launch_bounds__(256) k_link(int n, int bits, int cap, const int32_t* __restrict__ ord23,
-                                              const uint32_t* __restrict__ keys_c2,
-                                              const uint32_t* __restrict__ keys_c3,
-                                              const int32_t* __restrict__ rank2, const uint32_t* __restrict__ pk,
-                                              int4* __restrict__ c4, DevScalars* __restrict__ sc) {
+__device__ __forceinline__ LinkPt shfl_pt(LinkPt p, int delta, bool up) {
+  LinkPt q;
+  q.k = up ? __shfl_up_sync(0xffffffffu, p.k, delta) : __shfl_down_sync(0xffffffffu, p.k, delta);
+  q.r2 = up ? __shfl_up_sync(0xffffffffu, p.r2, delta) : __shfl_down_sync(0xffffffffu, p.r2, delta);
+  q.c = up ? __shfl_up_sync(0xffffffffu, p.c, delta) : __shfl_down_sync(0xffffffffu, p.c, delta);
+  return q;
+}
+
+constexpr int kLinkThreads = 256;
+constexpr int kLinkPerLane = 4;
+
+__global__ void __launch_bounds__(kLinkThreads, 6) k_link(int n, int bits, int cap, const int32_t* __restrict__ ord23,
+                                                       const uint32_t* __restrict__ keys_c2,
+                                                       const uint32_t* __restrict__ keys_c3,
+                                                       const int32_t* __restrict__ rank2,
+                                                       const uint32_t* __restrict__ pk, int4* __restrict__ c4,
+                                                       DevScalars* __restrict__ sc) {
   __shared__ unsigned long long s_red[8];
   const int code = blockIdx.y;
   const int lane = threadIdx.x & 31;
   const int32_t* ord = code == 0 ? nullptr : ord23 + size_t(code - 1) * size_t(cap);
-  const uint32_t* keys = code == 1 ? keys_c2 : keys_c3;
+  const uint32_t* keys = code == 0 ? pk : (code == 1 ? keys_c2 : keys_c3);
+  const bool vec = ((reinterpret_cast<uintptr_t>(ord) | reinterpret_cast<uintptr_t>(keys)) & 15u) == 0;
   unsigned long long edges = 0;
   float dist_f = 0.f;  // this thread's few edge lengths; converted to fixed point once
-  const int stride = gridDim.x * blockDim.x;
+  constexpr int kSpan = 32 * kLinkPerLane;
+  const int warps = gridDim.x * (kLinkThreads / 32);
   // whole warps step together so the shuffles see every lane
-  for (int base = blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < n; base += stride) {
-    const int r = base + lane;
-    const LinkPt me = link_point(r, n, code, ord, keys, rank2, pk);
-    LinkPt prev, next;
-    prev.k = __shfl_up_sync(0xffffffffu, me.k, 1);
-    prev.r2 = __shfl_up_sync(0xffffffffu, me.r2, 1);
-    prev.c = __shfl_up_sync(0xffffffffu, me.c, 1);
-    next.k = __shfl_down_sync(0xffffffffu, me.k, 1);
-    next.r2 = __shfl_down_sync(0xffffffffu, me.r2, 1);
-    next.c = __shfl_down_sync(0xffffffffu, me.c, 1);
-    if (lane == 0) prev = link_point(r - 1, n, code, ord, keys, rank2, pk);
-    if (lane == 31) next = link_point(r + 1, n, code, ord, keys, rank2, pk);
-    if (me.k < 0) continue;
-    // the edge to the next position: counted once, unless an earlier code links the pair
-    bool dup_next = true;
-    if (next.k >= 0) {
-      dup_next = code > 0 && abs(me.k - next.k) == 1;
-      if (code == 2) dup_next |= abs(me.r2 - next.r2) == 1;
-      if (!dup_next) {
-        edges += 1;
-        dist_f += sqrtf(float(sq_dist_c1(me.c, next.c, bits)));
+  for (int base = (blockIdx.x * (kLinkThreads / 32) + (threadIdx.x >> 5)) * kSpan; base < n; base += warps * kSpan) {
+    const int r0 = base + kLinkPerLane * lane;
+    int kk[kLinkPerLane];
+    uint32_t cc[kLinkPerLane];
+    if (vec && r0 + kLinkPerLane <= n) {
+      const uint4 kv = *reinterpret_cast<const uint4*>(keys + r0);
+      cc[0] = kv.x;
+      cc[1] = kv.y;
+      cc[2] = kv.z;
+      cc[3] = kv.w;
+      if (code == 0) {
+#pragma unroll
+        for (int i = 0; i < kLinkPerLane; ++i) kk[i] = r0 + i;
+      } else {
+        const int4 ov = *reinterpret_cast<const int4*>(ord + r0);
+        kk[0] = ov.x;
+        kk[1] = ov.y;
+        kk[2] = ov.z;
+        kk[3] = ov.w;
+      }
+    } else {
+#pragma unroll
+      for (int i = 0; i < kLinkPerLane; ++i) {
+        const int r = r0 + i;
+        kk[i] = -1;
+        cc[i] = 0u;
+        if (r < n) {
+          kk[i] = code == 0 ? r : ord[r];
+          cc[i] = keys[r];
+        }
       }
     }
-    if (code == 0) continue;
-    bool dup_prev = true;
-    if (prev.k >= 0) {
-      dup_prev = abs(me.k - prev.k) == 1;
-      if (code == 2) dup_prev |= abs(me.r2 - prev.r2) == 1;
+    LinkPt p[kLinkPerLane];
+#pragma unroll
+    for (int i = 0; i < kLinkPerLane; ++i) {
+      p[i].k = in_range(kk[i], n) ? kk[i] : -1;
+      p[i].c = cc[i];
+      p[i].r2 = (code == 2 && p[i].k >= 0) ? rank2[p[i].k] : -1;
     }
-    int2* slot = reinterpret_cast<int2*>(c4 + me.k) + (code - 1);
-    *slot = make_int2(dup_prev ? -1 : prev.k, dup_next ? -1 : next.k);
+    LinkPt before = shfl_pt(p[kLinkPerLane - 1], 1, true);
+    LinkPt after = shfl_pt(p[0], 1, false);
+    if (lane == 0) before = link_point(r0 - 1, n, code, ord, keys, rank2);
+    if (lane == 31) after = link_point(r0 + kLinkPerLane, n, code, ord, keys, rank2);
+#pragma unroll
+    for (int i = 0; i < kLinkPerLane; ++i) {
+      const LinkPt me = p[i];
+      const LinkPt prev = i == 0 ? before : p[i - 1];
+      const LinkPt next = i == kLinkPerLane - 1 ? after : p[i + 1];
+      if (me.k < 0) continue;
+      // the edge to the next position: counted once, unless an earlier code links the pair
+      bool dup_next = true;
+      if (next.k >= 0) {
+        dup_next = code > 0 && abs(me.k - next.k) == 1;
+        if (code == 2) dup_next |= abs(me.r2 - next.r2) == 1;
+        if (!dup_next) {
+          edges += 1;
+          dist_f += sqrtf(float(sq_dist_c1(me.c, next.c, bits)));
+        }
+      }
+      if (code == 0) continue;
+      bool dup_prev = true;
+      if (prev.k >= 0) {
+        dup_prev = abs(me.k - prev.k) == 1;
+        if (code == 2) dup_prev |= abs(me.r2 - prev.r2) == 1;
+      }
+      int2* slot = reinterpret_cast<int2*>(c4 + me.k) + (code - 1);
+      *slot = make_int2(dup_prev ? -1 : prev.k, dup_next ? -1 : next.k);
+    }
   }
   unsigned long long dist = (unsigned long long)__float2ull_rn(dist_f * float(1u << kDistShift));
-  edges = block_sum_u64<256>(edges, s_red);
-  dist = block_sum_u64<256>(dist, s_red);
+  edges = block_sum_u64<kLinkThreads>(edges, s_red);
+  dist = block_sum_u64<kLinkThreads>(dist, s_red);
   if (threadIdx.x == 0) {
     if (edges) atomicAdd(&sc->n_edges, edges);
     if (dist) atomicAdd(&sc->dist_fx, dist);
@@ -702,8 +753,10 @@ cudaError_t launch_slab_sort(int n, int bits, int cap, const SortBufs& sb, const
 cudaError_t launch_link(int n, int bits, int cap, const GraphBufs& gb, const SortBufs& sb, DevScalars* sc,
                         int num_sms, cudaStream_t stream) {
   if (n <= 0) return cudaSuccess;
-  const int gx = std::max(1, std::min((n + 255) / 256, num_sms * 8));
-  k_link<<<dim3(gx, 3), 256, 0, stream>>>(n, bits, cap, gb.ord23, sb.keys[0], sb.keys[1], gb.rank2, gb.pk, gb.c4,
+  // the three codes' blocks together fill the GPU once (6 resident blocks of 256 threads per SM)
+  const int gx = std::max(1, std::min((n + kLinkThreads * kLinkPerLane - 1) / (kLinkThreads * kLinkPerLane),
+                                      num_sms * 2));
+  k_link<<<dim3(gx, 3), kLinkThreads, 0, stream>>>(n, bits, cap, gb.ord23, sb.keys[0], sb.keys[1], gb.rank2, gb.pk, gb.c4,
                                           sc);
   return cudaGetLastError();
 }
