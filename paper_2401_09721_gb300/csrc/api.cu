@@ -177,7 +177,7 @@ cudaStream_t as_stream(void* s) { return static_cast<cudaStream_t>(s); }
 
 void zero_region(fgbd_ctx* ctx, size_t from, size_t to, cudaStream_t st, cudaError_t* e) {
   if (*e != cudaSuccess) return;
-  *e = cudaMemsetAsync(reinterpret_cast<char*>(ctx->sc) + from, 0, to - from, st);
+  *e = launch_zero_words(reinterpret_cast<uint32_t*>(reinterpret_cast<char*>(ctx->sc) + from), (to - from) / 4, st);
 }
 
 fgbd_status take_device_status(fgbd_ctx* ctx, cudaStream_t st) {

@@ -36,6 +36,7 @@ __global__ void __launch_bounds__(kDiffThreads)
     k_diff_rows(int n, int bits, double sigma_in, const uint32_t* __restrict__ pk, const int4* __restrict__ c4,
                 const DevScalars* __restrict__ sc, int32_t* __restrict__ nb, float* __restrict__ R,
                 float* __restrict__ d2f, float* __restrict__ e) {
+  pdl_wait();
   const double sg = diff_sigma(sigma_in, sc);
   const float cexp = sg > 0.0 ? float(1.4426950408889634 / (sg * sg)) : 0.f;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
@@ -87,6 +88,7 @@ __global__ void __launch_bounds__(kDiffThreads)
 // its neighbour's row (the graph is symmetric, so the slot exists).
 __global__ void __launch_bounds__(kDiffThreads)
     k_diff_rows_t(int n, const int32_t* __restrict__ nb, const float* __restrict__ R, float* __restrict__ RT) {
+  pdl_wait();
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
 #pragma unroll
     for (int t = 0; t < kK; ++t) {
@@ -105,6 +107,7 @@ __global__ void __launch_bounds__(kDiffThreads)
 // x[k] = rgb[perm1[k]] (input order -> sorted order)
 __global__ void __launch_bounds__(kDiffThreads)
     k_diff_gather(int n, const float* __restrict__ rgb, const int32_t* __restrict__ perm1, float4* __restrict__ x) {
+  pdl_wait();
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
     const int i = perm1[k];
     float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -116,6 +119,7 @@ __global__ void __launch_bounds__(kDiffThreads)
 // out[perm1[k]] = x[k] (sorted order -> input order)
 __global__ void __launch_bounds__(kDiffThreads)
     k_diff_scatter(int n, const float4* __restrict__ x, const int32_t* __restrict__ perm1, float* __restrict__ out) {
+  pdl_wait();
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
     const int i = perm1[k];
     if (!in_range(i, n)) continue;
@@ -130,6 +134,7 @@ __global__ void __launch_bounds__(kDiffThreads)
 __global__ void __launch_bounds__(kDiffThreads)
     k_diff_step(int n, float alpha, const int32_t* __restrict__ nb, const float* __restrict__ R,
                 const float4* __restrict__ src, float4* __restrict__ dst) {
+  pdl_wait();
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     float rx = 0.f, ry = 0.f, rz = 0.f;
 #pragma unroll
@@ -156,6 +161,7 @@ __global__ void __launch_bounds__(kDiffThreads)
                      const float* __restrict__ R, const float* __restrict__ RT, const float* __restrict__ d2f,
                      const float* __restrict__ e, const float4* __restrict__ x, const float4* __restrict__ u,
                      float4* __restrict__ u_out, const DevScalars* __restrict__ sc, double* __restrict__ partial) {
+  pdl_wait();
   __shared__ double s_red[2][kDiffThreads / 32];
   const double sg = diff_sigma(sigma_in, sc);
   const float c3 = sg > 0.0 ? float(2.0 / (sg * sg * sg)) : 0.f;
@@ -219,6 +225,7 @@ __global__ void __launch_bounds__(kDiffThreads)
 // grad[0..1] = the sums of `count` (dalpha, dsigma) partials, in a fixed order
 __global__ void __launch_bounds__(256) k_diff_reduce(int count, const double* __restrict__ partial,
                                                      double* __restrict__ grad) {
+  pdl_wait();
   __shared__ double s[2][256];
   double a = 0.0, b = 0.0;
   for (int i = threadIdx.x; i < count; i += blockDim.x) {
@@ -249,46 +256,47 @@ cudaError_t launch_diff_rows(int n, int bits, double sigma, const GraphBufs& gb,
                              const DiffBufs& db, int num_sms, cudaStream_t stream) {
   if (n <= 0) return cudaSuccess;
   const int grid = diff_grid(n, num_sms);
-  k_diff_rows<<<grid, kDiffThreads, 0, stream>>>(n, bits, sigma, gb.pk, gb.c4, sc, db.nb, db.R, db.d2, db.e);
+  {
+    const cudaError_t le = launch_kernel(k_diff_rows, dim3(grid), dim3(kDiffThreads), 0, stream, false, n, bits,
+                                         sigma, gb.pk, gb.c4, sc, db.nb, db.R, db.d2, db.e);
+    if (le != cudaSuccess) return le;
+  }
   cudaError_t err = cudaGetLastError();
   if (err != cudaSuccess) return err;
-  k_diff_rows_t<<<grid, kDiffThreads, 0, stream>>>(n, db.nb, db.R, db.RT);
-  return cudaGetLastError();
+  return launch_kernel(k_diff_rows_t, dim3(grid), dim3(kDiffThreads), 0, stream, false, n, db.nb, db.R, db.RT);
 }
 
 cudaError_t launch_diff_gather(int n, const float* rgb, const int32_t* perm1, float4* x, int num_sms,
                                cudaStream_t stream) {
   if (n <= 0) return cudaSuccess;
-  k_diff_gather<<<diff_grid(n, num_sms), kDiffThreads, 0, stream>>>(n, rgb, perm1, x);
-  return cudaGetLastError();
+  return launch_kernel(k_diff_gather, dim3(diff_grid(n, num_sms)), dim3(kDiffThreads), 0, stream, false, n, rgb,
+                       perm1, x);
 }
 
 cudaError_t launch_diff_scatter(int n, const float4* x, const int32_t* perm1, float* out, int num_sms,
                                 cudaStream_t stream) {
   if (n <= 0) return cudaSuccess;
-  k_diff_scatter<<<diff_grid(n, num_sms), kDiffThreads, 0, stream>>>(n, x, perm1, out);
-  return cudaGetLastError();
+  return launch_kernel(k_diff_scatter, dim3(diff_grid(n, num_sms)), dim3(kDiffThreads), 0, stream, false, n, x, perm1,
+                       out);
 }
 
 cudaError_t launch_diff_step(int n, float alpha, const DiffBufs& db, const float4* src, float4* dst, int num_sms,
                              cudaStream_t stream) {
   if (n <= 0) return cudaSuccess;
-  k_diff_step<<<diff_grid(n, num_sms), kDiffThreads, 0, stream>>>(n, alpha, db.nb, db.R, src, dst);
-  return cudaGetLastError();
+  return launch_kernel(k_diff_step, dim3(diff_grid(n, num_sms)), dim3(kDiffThreads), 0, stream, false, n, alpha,
+                       db.nb, db.R, src, dst);
 }
 
 cudaError_t launch_diff_back_step(int n, float alpha, double sigma, const DiffBufs& db, const float4* x,
                                   const float4* u, float4* u_out, const DevScalars* sc, double* partial,
                                   int num_sms, cudaStream_t stream) {
   if (n <= 0) return cudaSuccess;
-  k_diff_back_step<<<diff_grid(n, num_sms), kDiffThreads, 0, stream>>>(n, alpha, sigma, db.nb, db.R, db.RT, db.d2,
-                                                                       db.e, x, u, u_out, sc, partial);
-  return cudaGetLastError();
+  return launch_kernel(k_diff_back_step, dim3(diff_grid(n, num_sms)), dim3(kDiffThreads), 0, stream, false, n, alpha,
+                       sigma, db.nb, db.R, db.RT, db.d2, db.e, x, u, u_out, sc, partial);
 }
 
 cudaError_t launch_diff_reduce(int count, const double* partial, double* grad, cudaStream_t stream) {
-  k_diff_reduce<<<1, 256, 0, stream>>>(count, partial, grad);
-  return cudaGetLastError();
+  return launch_kernel(k_diff_reduce, dim3(1), dim3(256), 0, stream, false, count, partial, grad);
 }
 
 }  // namespace fgbd

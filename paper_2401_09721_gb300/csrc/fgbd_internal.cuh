@@ -79,6 +79,12 @@ struct DevScalars {
   uint32_t status;
 };
 
+// the regions are zeroed as 32-bit words
+static_assert(offsetof(DevScalars, n_edges) % 4 == 0 && offsetof(DevScalars, build_end_) % 4 == 0 &&
+                  offsetof(DevScalars, n_patches) % 4 == 0 && offsetof(DevScalars, ne_end_) % 4 == 0 &&
+                  offsetof(DevScalars, ysq_keep) % 4 == 0 && offsetof(DevScalars, sel_end_) % 4 == 0,
+              "DevScalars regions must be whole 32-bit words");
+
 // Sort scratch for one build.
 struct SortBufs {
   uint32_t* keys[2];     // ping-pong [cap]
@@ -289,5 +295,46 @@ __device__ __forceinline__ double sigma_g_of(const DevScalars* sc) {
   if (e == 0) return 0.0;
   return double(sc->dist_fx) * (1.0 / double(1ull << kDistShift)) / double(e);
 }
+
+// ---------------------------------------------------------------- launches
+// Programmatic dependent launch (opt-in): with FGBD_PDL set in the
+// environment, consecutive kernels are launched with programmatic stream
+// serialization.  Every kernel starts with pdl_wait(), which then returns once
+// the kernel it depends on has completed and its writes are visible; under an
+// ordinary launch it returns at once.  Measured on the 1M-point frame it
+// gained nothing (0.2635 vs 0.2632 ms), and letting the next kernel launch at
+// the start of each kernel cost 12 us (waiting blocks held resources the
+// multi-wave kernels needed), so ordinary launches are the default.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+bool pdl_enabled();  // true if the environment sets FGBD_PDL
+
+// Launch `kernel` on `stream`: cooperative (all blocks resident, for the grid
+// barriers) or with programmatic stream serialization.
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_kernel(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t stream,
+                                 bool cooperative, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = stream;
+  cudaLaunchAttribute attrs[1];
+  cfg.attrs = attrs;
+  cfg.numAttrs = 0;
+  if (cooperative) {
+    attrs[0].id = cudaLaunchAttributeCooperative;
+    attrs[0].val.cooperative = 1;
+    cfg.numAttrs = 1;
+  } else if (pdl_enabled()) {
+    attrs[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attrs[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.numAttrs = 1;
+  }
+  return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
+// zero [p, p + words) on `stream` (a kernel, so it joins the programmatic chain)
+cudaError_t launch_zero_words(uint32_t* p, size_t words, cudaStream_t stream);
 
 }  // namespace fgbd

@@ -302,6 +302,7 @@ __device__ __forceinline__ void block_sums(unsigned long long (&v)[K], unsigned 
 constexpr int kSums = 3 + 2 * kSpecMax;  // kept y^2, all y^2, kept count, then per stored step kept and all terms
 
 __global__ void __launch_bounds__(kFilterThreads, 2) k_filter(FilterArgs a) {
+  pdl_wait();
   __shared__ unsigned long long s_red[(kSums + 1) * (kFilterThreads / 32)];
   __shared__ int s_ok;
   uint32_t epoch = 0;
@@ -550,6 +551,7 @@ __global__ void __launch_bounds__(kFilterThreads, 2) k_filter(FilterArgs a) {
 }
 
 __global__ void __launch_bounds__(256) k_output(FilterArgs a) {
+  pdl_wait();
   output_quads(a, a.sc->kept_buf, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
 }
 
@@ -570,6 +572,7 @@ __device__ __forceinline__ int gather_row(int k, int n, const int4* c4, int nb[6
 
 __global__ void k_csr_degree(int n, const int32_t* __restrict__ rank1, const int4* __restrict__ c4,
                              int64_t* __restrict__ deg) {
+  pdl_wait();
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i <= n; i += gridDim.x * blockDim.x) {
     if (i == n) {
       deg[i] = 0;
@@ -585,6 +588,7 @@ __global__ void k_csr_fill(int n, int bits, const int32_t* __restrict__ rank1,
                            const int4* __restrict__ c4, const int64_t* __restrict__ row_ptr,
                            int32_t* __restrict__ col, float* __restrict__ w, int64_t col_capacity,
                            const DevScalars* __restrict__ sc) {
+  pdl_wait();
   const double sg = sigma_g_of(sc);
   const float inv2 = sg > 0.0 ? float(1.0 / (sg * sg)) : 0.f;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
@@ -623,6 +627,7 @@ __global__ void k_csr_fill(int n, int bits, const int32_t* __restrict__ rank1,
 constexpr int kScanBlock = 1024;
 
 __global__ void k_scan_blocks(int64_t* data, int64_t count, int64_t* totals) {
+  pdl_wait();
   __shared__ int64_t s[kScanBlock];
   const int64_t i = int64_t(blockIdx.x) * kScanBlock + threadIdx.x;
   const int64_t v = i < count ? data[i] : 0;
@@ -639,6 +644,7 @@ __global__ void k_scan_blocks(int64_t* data, int64_t count, int64_t* totals) {
 }
 
 __global__ void k_scan_totals(int64_t* totals, int nb) {
+  pdl_wait();
   if (threadIdx.x == 0 && blockIdx.x == 0) {
     int64_t run = 0;
     for (int b = 0; b < nb; ++b) {
@@ -650,6 +656,7 @@ __global__ void k_scan_totals(int64_t* totals, int nb) {
 }
 
 __global__ void k_scan_add(int64_t* data, int64_t count, const int64_t* totals) {
+  pdl_wait();
   const int64_t i = int64_t(blockIdx.x) * kScanBlock + threadIdx.x;
   if (i < count) data[i] += totals[blockIdx.x];
 }
@@ -657,6 +664,7 @@ __global__ void k_scan_add(int64_t* data, int64_t count, const int64_t* totals) 
 __global__ void k_spread_export(int n, const int32_t* __restrict__ rank1, const float* __restrict__ spread,
                                 const uint8_t* __restrict__ keep8, float* __restrict__ spread_out,
                                 uint8_t* __restrict__ keep_out) {
+  pdl_wait();
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     const int k = rank1[i];
     if (!in_range(k, n)) continue;
@@ -677,48 +685,49 @@ int filter_grid(int n, int num_sms) {
 }
 
 cudaError_t launch_filter(const FilterArgs& a, int grid, cudaStream_t stream) {
-  FilterArgs copy = a;
-  void* args[] = {&copy};
-  return cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(k_filter), dim3(grid),
-                                     dim3(kFilterThreads), args, 0, stream);
+  return launch_kernel(k_filter, dim3(grid), dim3(kFilterThreads), 0, stream, true, a);
 }
 
 cudaError_t launch_output(const FilterArgs& a, cudaStream_t stream) {
   if (a.n <= 0) return cudaSuccess;
   const int grid = std::min((a.n + 255) / 256, 152 * 16);
-  k_output<<<grid, 256, 0, stream>>>(a);
-  return cudaGetLastError();
+  return launch_kernel(k_output, dim3(grid), dim3(256), 0, stream, false, a);
 }
 
 cudaError_t launch_csr_degree(int n, const GraphBufs& gb, int64_t* deg_out, cudaStream_t stream) {
   const int grid = std::max(1, std::min((n + 256) / 256, 152 * 16));
-  k_csr_degree<<<grid, 256, 0, stream>>>(n, gb.rank1, gb.c4, deg_out);
-  return cudaGetLastError();
+  return launch_kernel(k_csr_degree, dim3(grid), dim3(256), 0, stream, false, n, gb.rank1, gb.c4, deg_out);
 }
 
 cudaError_t launch_scan_i64(int64_t* data, int64_t count, int64_t* block_tmp, cudaStream_t stream) {
   if (count <= 0) return cudaSuccess;
   const int nb = int((count + kScanBlock - 1) / kScanBlock);
-  k_scan_blocks<<<nb, kScanBlock, 0, stream>>>(data, count, block_tmp);
-  k_scan_totals<<<1, 32, 0, stream>>>(block_tmp, nb);
-  k_scan_add<<<nb, kScanBlock, 0, stream>>>(data, count, block_tmp);
-  return cudaGetLastError();
+  {
+    const cudaError_t le = launch_kernel(k_scan_blocks, dim3(nb), dim3(kScanBlock), 0, stream, false, data, count,
+                                         block_tmp);
+    if (le != cudaSuccess) return le;
+  }
+  {
+    const cudaError_t le = launch_kernel(k_scan_totals, dim3(1), dim3(32), 0, stream, false, block_tmp, nb);
+    if (le != cudaSuccess) return le;
+  }
+  return launch_kernel(k_scan_add, dim3(nb), dim3(kScanBlock), 0, stream, false, data, count, block_tmp);
 }
 
 cudaError_t launch_csr_fill(int n, int bits, const GraphBufs& gb, const int64_t* row_ptr, int32_t* col,
                             float* w, int64_t col_capacity, const DevScalars* sc, cudaStream_t stream) {
   if (n <= 0) return cudaSuccess;
   const int grid = std::min((n + 255) / 256, 152 * 16);
-  k_csr_fill<<<grid, 256, 0, stream>>>(n, bits, gb.rank1, gb.perm1, gb.pk, gb.c4, row_ptr, col, w, col_capacity, sc);
-  return cudaGetLastError();
+  return launch_kernel(k_csr_fill, dim3(grid), dim3(256), 0, stream, false, n, bits, gb.rank1, gb.perm1, gb.pk, gb.c4,
+                       row_ptr, col, w, col_capacity, sc);
 }
 
 cudaError_t launch_spread_export(int n, const int32_t* rank1, const float* spread, const uint8_t* keep8,
                                  float* spread_out, uint8_t* keep_out, cudaStream_t stream) {
   if (n <= 0) return cudaSuccess;
   const int grid = std::min((n + 255) / 256, 152 * 16);
-  k_spread_export<<<grid, 256, 0, stream>>>(n, rank1, spread, keep8, spread_out, keep_out);
-  return cudaGetLastError();
+  return launch_kernel(k_spread_export, dim3(grid), dim3(256), 0, stream, false, n, rank1, spread, keep8, spread_out,
+                       keep_out);
 }
 
 }  // namespace fgbd

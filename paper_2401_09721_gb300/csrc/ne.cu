@@ -26,6 +26,7 @@ constexpr int kTiles = 28;  // 3x3 output tiles covering the upper triangle of a
 __global__ void __launch_bounds__(256) k_gather_u8(const uint8_t* __restrict__ rgb, int n,
                                                    const int32_t* __restrict__ perm1,
                                                    uint32_t* __restrict__ y8) {
+  pdl_wait();
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
     const int pi = perm1[k];
     if (!in_range(pi, n)) continue;
@@ -37,6 +38,7 @@ __global__ void __launch_bounds__(256) k_gather_u8(const uint8_t* __restrict__ r
 __global__ void __launch_bounds__(256) k_gather_f32(const float* __restrict__ rgb, int n,
                                                     const int32_t* __restrict__ perm1,
                                                     float4* __restrict__ yf) {
+  pdl_wait();
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
     const int pi = perm1[k];
     if (!in_range(pi, n)) continue;
@@ -258,6 +260,7 @@ __global__ void __launch_bounds__(kNeThreads, 4)
                  const uint32_t* __restrict__ y8, const float4* __restrict__ yf,
                  float* __restrict__ spread, double* __restrict__ f64_partials, int moments,
                  int sorted_patches, DevScalars* __restrict__ sc) {
+  pdl_wait();
   constexpr int kP = kD * kD + kD + 1;
   __shared__ __align__(16) uint32_t s_at8[DT == 0 ? kNeWarps : 1][kD * kRowWords];
   __shared__ __align__(16) float s_atf[DT == 1 ? kNeWarps : 1][kD * kRowFloats];
@@ -751,6 +754,7 @@ __device__ __noinline__ void finalize_block(int dtype, const double* __restrict_
 __global__ void __launch_bounds__(kFinThreads) k_ne_finalize(int dtype, const double* __restrict__ f64_partials,
                                                            int nblocks, DevScalars* __restrict__ sc,
                                                            double* __restrict__ sigma_out) {
+  pdl_wait();
   finalize_block(dtype, f64_partials, nblocks, sc, sigma_out);
 }
 
@@ -763,6 +767,7 @@ constexpr int kSpecPadBytes = 100 * 1024;  // shared memory that makes a second 
 __global__ void __launch_bounds__(kSpecThreads, 1)
     k_ne_finalize_spec(int dtype, const double* __restrict__ f64_partials, int nblocks, DevScalars* __restrict__ sc,
                        double* __restrict__ sigma_out, FilterArgs a) {
+  pdl_wait();
   __shared__ int s_ok;
   __shared__ float s_cexp;
   if (blockIdx.x == 0) {
@@ -779,10 +784,10 @@ cudaError_t launch_gather_colors(const void* rgb, int dtype, int n, const int32_
   if (n <= 0) return cudaSuccess;
   const int grid = std::min((n + 255) / 256, 152 * 16);
   if (dtype == 0)
-    k_gather_u8<<<grid, 256, 0, stream>>>(static_cast<const uint8_t*>(rgb), n, perm1, y8);
-  else
-    k_gather_f32<<<grid, 256, 0, stream>>>(static_cast<const float*>(rgb), n, perm1, yf);
-  return cudaGetLastError();
+    return launch_kernel(k_gather_u8, dim3(grid), dim3(256), 0, stream, false, static_cast<const uint8_t*>(rgb), n,
+                         perm1, y8);
+  return launch_kernel(k_gather_f32, dim3(grid), dim3(256), 0, stream, false, static_cast<const float*>(rgb), n,
+                       perm1, yf);
 }
 
 int ne_moment_blocks(int n, int num_sms) {
@@ -806,20 +811,17 @@ cudaError_t launch_ne_moments(int n, int bits, int dtype, const GraphBufs& gb, c
   if (n <= 0) return cudaSuccess;
   const int grid = ne_moment_blocks(n, num_sms);
   if (dtype == 0)
-    k_ne_moments<0><<<grid, kNeThreads, 0, stream>>>(n, bits, gb.pk, gb.c4, y8, yf, spread, f64_partials,
-                                                     moments ? 1 : 0, sorted_patches ? 1 : 0, sc);
-  else
-    k_ne_moments<1><<<grid, kNeThreads, 0, stream>>>(n, bits, gb.pk, gb.c4, y8, yf, spread, f64_partials,
-                                                     moments ? 1 : 0, sorted_patches ? 1 : 0, sc);
-  return cudaGetLastError();
+    return launch_kernel(k_ne_moments<0>, dim3(grid), dim3(kNeThreads), 0, stream, false, n, bits, gb.pk, gb.c4, y8,
+                         yf, spread, f64_partials, moments ? 1 : 0, sorted_patches ? 1 : 0, sc);
+  return launch_kernel(k_ne_moments<1>, dim3(grid), dim3(kNeThreads), 0, stream, false, n, bits, gb.pk, gb.c4, y8, yf,
+                       spread, f64_partials, moments ? 1 : 0, sorted_patches ? 1 : 0, sc);
 }
 
 cudaError_t launch_ne_finalize(int dtype, const double* f64_partials, int nblocks, DevScalars* sc,
                                double* sigma_out, const FilterArgs* spec, int num_sms, cudaStream_t stream) {
-  if (!spec || spec->spec_depth <= 0 || spec->n <= 0 || num_sms < 2) {
-    k_ne_finalize<<<1, kFinThreads, 0, stream>>>(dtype, f64_partials, nblocks, sc, sigma_out);
-    return cudaGetLastError();
-  }
+  if (!spec || spec->spec_depth <= 0 || spec->n <= 0 || num_sms < 2)
+    return launch_kernel(k_ne_finalize, dim3(1), dim3(kFinThreads), 0, stream, false, dtype, f64_partials, nblocks,
+                         sc, sigma_out);
   static unsigned long long configured = 0;  // the shared-memory limit is set once per device
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -830,10 +832,8 @@ cudaError_t launch_ne_finalize(int dtype, const double* f64_partials, int nblock
     if (e != cudaSuccess) return e;
     configured |= bit;
   }
-  FilterArgs copy = *spec;
-  void* args[] = {&dtype, &f64_partials, &nblocks, &sc, &sigma_out, &copy};
-  return cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(k_ne_finalize_spec), dim3(num_sms),
-                                     dim3(kSpecThreads), args, kSpecPadBytes, stream);
+  return launch_kernel(k_ne_finalize_spec, dim3(num_sms), dim3(kSpecThreads), kSpecPadBytes, stream, true, dtype,
+                       f64_partials, nblocks, sc, sigma_out, *spec);
 }
 
 }  // namespace fgbd

@@ -27,6 +27,7 @@
 // a pair already linked by an earlier code is left out so the union is a set,
 // and each distinct edge's length is summed for sigma_g.
 #include <algorithm>
+#include <cstdlib>
 
 #include "fgbd_internal.cuh"
 
@@ -50,6 +51,7 @@ size_t scatter_smem_bytes() {
 
 __global__ void __launch_bounds__(1024) k_coord_hist(const int32_t* __restrict__ xyz, int n, int bits,
                                                      DevScalars* __restrict__ sc) {
+  pdl_wait();
   __shared__ uint32_t h[3][kMaxRadix];
   const int radix = 1 << bits;
   for (int i = threadIdx.x; i < 3 * kMaxRadix; i += blockDim.x) (&h[0][0])[i] = 0;
@@ -98,6 +100,7 @@ __device__ __forceinline__ void load_tile(const SortPassArgs& a, int warp_base, 
 
 // Reduce: digit counts of every tile, counts[digit * tiles + tile].
 __global__ void __launch_bounds__(kSortThreads) k_tile_counts(SortPassArgs a) {
+  pdl_wait();
   __shared__ uint32_t s_h[kMaxRadix];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int radix = 1 << a.bits;
@@ -119,6 +122,7 @@ __global__ void __launch_bounds__(kSortThreads) k_tile_counts(SortPassArgs a) {
 // digit's bucket (total of the smaller digits) plus the counts of the earlier
 // tiles.  Each lane owns a run of up to 8 consecutive tiles per batch.
 __global__ void __launch_bounds__(256) k_tile_scan(SortPassArgs a) {
+  pdl_wait();
   const int lane = threadIdx.x & 31;
   const int radix = 1 << a.bits;
   const int d = blockIdx.x * 8 + (threadIdx.x >> 5);
@@ -167,6 +171,7 @@ __global__ void __launch_bounds__(256) k_tile_scan(SortPassArgs a) {
 // Scatter: rank each key of the tile among equal digits (stable), then write
 // the tile out in digit runs at the offsets the scan produced.
 __global__ void __launch_bounds__(kScatterThreads, 2) k_sort_scatter(SortPassArgs a) {
+  pdl_wait();
   extern __shared__ uint32_t smem[];
   uint32_t* s_whist = smem;                             // [kPairWords][radix]: warps 2w, 2w+1 in the low, high half
   uint32_t* s_keys = s_whist + kPairWords * kMaxRadix;  // [kSortTile]
@@ -390,6 +395,7 @@ __global__ void __launch_bounds__(kSlabThreads, 4)
     k_slab_sort(int n, int bits, const uint32_t* __restrict__ keys_in, const uint32_t* __restrict__ vals_in,
                 uint32_t* __restrict__ keys_tmp, uint32_t* __restrict__ vals_tmp, uint32_t* __restrict__ keys_out,
                 int32_t* __restrict__ vals_out, const DevScalars* __restrict__ sc) {
+  pdl_wait();
   extern __shared__ uint32_t smem[];
   uint32_t* cnt = smem;                                   // [kSlabPairWords][radix]
   uint32_t* s_keys = cnt + kSlabPairWords * kMaxRadix;    // [kSlabMax]
@@ -585,6 +591,7 @@ __global__ void __launch_bounds__(kLinkThreads, 6) k_link(int n, int bits, int c
                                                        const int32_t* __restrict__ rank2,
                                                        const uint32_t* __restrict__ pk, int4* __restrict__ c4,
                                                        DevScalars* __restrict__ sc) {
+  pdl_wait();
   __shared__ unsigned long long s_red[8];
   const int code = blockIdx.y;
   const int lane = threadIdx.x & 31;
@@ -677,6 +684,7 @@ __global__ void __launch_bounds__(kLinkThreads, 6) k_link(int n, int bits, int c
 // The three orders in input indices: C1 from perm1, C2 and C3 through perm1.
 __global__ void __launch_bounds__(256) k_orders_export(int n, int cap, const int32_t* __restrict__ perm1,
                                                        const int32_t* __restrict__ ord23, int32_t* __restrict__ out) {
+  pdl_wait();
   const int stride = gridDim.x * blockDim.x;
   for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += stride) {
     out[r] = perm1[r];
@@ -693,18 +701,15 @@ cudaError_t launch_coord_hist(const int32_t* xyz, int n, int bits, DevScalars* s
   if (n <= 0) return cudaSuccess;
   // one large block per SM: few blocks keep the global atomics of the final merge few
   const int grid = std::max(1, std::min((n + 1023) / 1024, num_sms));
-  k_coord_hist<<<grid, 1024, 0, stream>>>(xyz, n, bits, sc);
-  return cudaGetLastError();
+  return launch_kernel(k_coord_hist, dim3(grid), dim3(1024), 0, stream, false, xyz, n, bits, sc);
 }
 
 cudaError_t launch_tile_counts(const SortPassArgs& a, cudaStream_t stream) {
-  k_tile_counts<<<dim3(a.tiles), kSortThreads, 0, stream>>>(a);
-  return cudaGetLastError();
+  return launch_kernel(k_tile_counts, dim3(a.tiles), dim3(kSortThreads), 0, stream, false, a);
 }
 
 cudaError_t launch_tile_scan(const SortPassArgs& a, cudaStream_t stream) {
-  k_tile_scan<<<((1 << a.bits) + 7) / 8, 256, 0, stream>>>(a);
-  return cudaGetLastError();
+  return launch_kernel(k_tile_scan, dim3(((1 << a.bits) + 7) / 8), dim3(256), 0, stream, false, a);
 }
 
 cudaError_t launch_sort_scatter(const SortPassArgs& a, cudaStream_t stream) {
@@ -719,8 +724,7 @@ cudaError_t launch_sort_scatter(const SortPassArgs& a, cudaStream_t stream) {
     if (e != cudaSuccess) return e;
     configured |= bit;
   }
-  k_sort_scatter<<<dim3(a.tiles), kScatterThreads, scatter_smem_bytes(), stream>>>(a);
-  return cudaGetLastError();
+  return launch_kernel(k_sort_scatter, dim3(a.tiles), dim3(kScatterThreads), scatter_smem_bytes(), stream, false, a);
 }
 
 cudaError_t launch_sort_pass(const SortPassArgs& a, cudaStream_t stream) {
@@ -744,10 +748,9 @@ cudaError_t launch_slab_sort(int n, int bits, int cap, const SortBufs& sb, const
     configured |= bit;
   }
   // scratch for slabs larger than shared memory: the C2 order and C2 ranks, written later
-  k_slab_sort<<<1 << bits, kSlabThreads, slab_smem_bytes(), stream>>>(
-      n, bits, sb.keys[0], sb.vals[0], reinterpret_cast<uint32_t*>(gb.ord23), reinterpret_cast<uint32_t*>(gb.rank2),
-      sb.keys[1], gb.ord23 + size_t(cap), sc);
-  return cudaGetLastError();
+  return launch_kernel(k_slab_sort, dim3(1 << bits), dim3(kSlabThreads), slab_smem_bytes(), stream, false, n, bits,
+                       sb.keys[0], sb.vals[0], reinterpret_cast<uint32_t*>(gb.ord23),
+                       reinterpret_cast<uint32_t*>(gb.rank2), sb.keys[1], gb.ord23 + size_t(cap), sc);
 }
 
 cudaError_t launch_link(int n, int bits, int cap, const GraphBufs& gb, const SortBufs& sb, DevScalars* sc,
@@ -756,16 +759,14 @@ cudaError_t launch_link(int n, int bits, int cap, const GraphBufs& gb, const Sor
   // the three codes' blocks together fill the GPU once (6 resident blocks of 256 threads per SM)
   const int gx = std::max(1, std::min((n + kLinkThreads * kLinkPerLane - 1) / (kLinkThreads * kLinkPerLane),
                                       num_sms * 2));
-  k_link<<<dim3(gx, 3), kLinkThreads, 0, stream>>>(n, bits, cap, gb.ord23, sb.keys[0], sb.keys[1], gb.rank2, gb.pk, gb.c4,
-                                          sc);
-  return cudaGetLastError();
+  return launch_kernel(k_link, dim3(gx, 3), dim3(kLinkThreads), 0, stream, false, n, bits, cap, gb.ord23, sb.keys[0],
+                       sb.keys[1], gb.rank2, gb.pk, gb.c4, sc);
 }
 
 cudaError_t launch_orders_export(int n, int cap, const GraphBufs& gb, int32_t* out, cudaStream_t stream) {
   if (n <= 0) return cudaSuccess;
   const int grid = std::max(1, std::min((n + 255) / 256, 152 * 16));
-  k_orders_export<<<grid, 256, 0, stream>>>(n, cap, gb.perm1, gb.ord23, out);
-  return cudaGetLastError();
+  return launch_kernel(k_orders_export, dim3(grid), dim3(256), 0, stream, false, n, cap, gb.perm1, gb.ord23, out);
 }
 
 SortPassArgs slg_pass_args(int pass, const int32_t* xyz, int n, int bits, int cap, const SortBufs& sb,
@@ -807,6 +808,27 @@ SortPassArgs slg_pass_args(int pass, const int32_t* xyz, int n, int bits, int ca
   a.vals_out = reinterpret_cast<uint32_t*>(gb.ord23);
   a.rank_out = gb.rank2;
   return a;
+}
+
+// ---------------------------------------------------------------- shared launch pieces
+
+bool pdl_enabled() {
+  static const bool on = std::getenv("FGBD_PDL") != nullptr;
+  return on;
+}
+
+namespace {
+__global__ void __launch_bounds__(256) k_zero_words(uint32_t* __restrict__ p, size_t words) {
+  pdl_wait();
+  for (size_t i = size_t(blockIdx.x) * blockDim.x + threadIdx.x; i < words; i += size_t(gridDim.x) * blockDim.x)
+    p[i] = 0u;
+}
+}  // namespace
+
+cudaError_t launch_zero_words(uint32_t* p, size_t words, cudaStream_t stream) {
+  if (words == 0) return cudaSuccess;
+  const int grid = int(std::min<size_t>((words + 255) / 256, 64));
+  return launch_kernel(k_zero_words, dim3(grid), dim3(256), 0, stream, false, p, words);
 }
 
 }  // namespace fgbd
