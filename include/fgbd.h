@@ -57,8 +57,18 @@ typedef struct fgbd_params {
   double fslr_factor;   /* FSLR skips points whose mean patch std exceeds factor * sigma_est (paper: 2) */
   int32_t q_max;        /* largest filter power searched, 0..FGBD_Q_CAP (the paper states none; default 64) */
   int32_t variant;      /* OR of FGBD_VARIANT_* ablation switches; 0 is the method as published */
-  int32_t reserved[6];  /* must be zero */
+  int32_t flags;        /* OR of FGBD_FLAG_* execution choices (same results); 0 is the default */
+  int32_t reserved[5];  /* must be zero */
 } fgbd_params;
+
+/* Execution choices that do not change any result.
+ *   FGBD_FLAG_FUSED_SELECT: fgbd_run takes the FSLR selection and the filter
+ *     inside the noise-estimate launch (the blocks that take the speculative
+ *     filter steps continue once sigma_est is published) instead of a second
+ *     cooperative launch.  It pays off only while sigma_est arrives before the
+ *     speculative steps end; on the 1M-point frame it is 4 us slower, so it is
+ *     off by default. */
+#define FGBD_FLAG_FUSED_SELECT 1
 
 /* Ablation switches of Section 3 (Tables 4 and 5), for comparison runs only.
  *   FGBD_VARIANT_NO_FSLR: "FGBD w/o FSLR" (Table 5): Eq. 6 is evaluated over

@@ -166,6 +166,7 @@ bool params_ok(const fgbd_params& p) {
   if (!(p.fslr_factor > 0.0) || p.fslr_factor > 1e30) return false;
   if (p.q_max < 0 || p.q_max > kQCap) return false;
   if (p.variant & ~(FGBD_VARIANT_NO_FSLR | FGBD_VARIANT_UNSORTED_PATCH)) return false;
+  if (p.flags & ~FGBD_FLAG_FUSED_SELECT) return false;
   for (int r : p.reserved)
     if (r != 0) return false;
   return true;
@@ -325,8 +326,11 @@ fgbd_status do_build(fgbd_ctx* ctx, const int32_t* xyz, int64_t n64, cudaStream_
   return FGBD_OK;
 }
 
+// With `fuse`, the estimate launch also selects q and writes the filtered
+// colours to fuse_out (what do_select with the estimated sigma would do).
 fgbd_status do_estimate(fgbd_ctx* ctx, const void* rgb, int32_t dtype, double* sigma_out, cudaStream_t st,
-                        bool speculate = true) {
+                        bool speculate = true, bool fuse = false, void* fuse_out = nullptr,
+                        int32_t fuse_out_dtype = FGBD_U8) {
   if (!ctx->has_graph) return FGBD_ESTATE;
   if (!dtype_ok(dtype)) return FGBD_EINVAL;
   if (ctx->n > 0 && !rgb) return FGBD_EINVAL;
@@ -346,14 +350,24 @@ fgbd_status do_estimate(fgbd_ctx* ctx, const void* rgb, int32_t dtype, double* s
                                   (ctx->params.variant & FGBD_VARIANT_UNSORTED_PATCH) == 0, st));
   }
   // the same launch stores the first filter steps of these colours on the other SMs
-  FilterArgs spec = filter_args(ctx, 0, 0, nullptr, nullptr, 0, dtype);
+  FilterArgs spec = filter_args(ctx, 0, 0, nullptr, fuse ? fuse_out : nullptr, fuse ? fuse_out_dtype : 0, dtype);
   spec.spec_depth = speculate ? std::min(kSpecMax, int(ctx->params.q_max)) : 0;
+  ctx->spec_depth = n > 0 && ctx->num_sms >= 2 ? spec.spec_depth : 0;
+  const bool fused = fuse && ctx->spec_depth > 0;
+  spec.fuse = fused ? 1 : 0;
+  if (fused) {
+    zero_region(ctx, offsetof(DevScalars, ysq_keep), offsetof(DevScalars, sel_end_), st, &e);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "memset");
+  }
   FGBD_LAUNCH(ctx, "ne_finalize", st,
               launch_ne_finalize(dtype, ctx->f64part, nblocks, ctx->sc, sigma_out, &spec, ctx->num_sms, st));
-  ctx->spec_depth = n > 0 && ctx->num_sms >= 2 ? spec.spec_depth : 0;
   ctx->has_noise = true;
   ctx->noise_rgb = rgb;
   ctx->noise_dtype = dtype;
+  if (fused) {
+    ctx->has_sel = true;
+    ctx->ever_selected = true;
+  }
   return FGBD_OK;
 }
 
@@ -378,8 +392,11 @@ fgbd_status do_select(fgbd_ctx* ctx, const void* rgb, int32_t dtype, const doubl
 fgbd_status direct_run(fgbd_ctx* ctx, const fgbd_ctx::RunKey& k, cudaStream_t st) {
   fgbd_status s = do_build(ctx, static_cast<const int32_t*>(k.xyz), k.n, st);
   if (s != FGBD_OK) return s;
-  s = do_estimate(ctx, k.rgb_in, k.in_dtype, nullptr, st);
+  // with FGBD_FLAG_FUSED_SELECT the estimate launch selects and filters too
+  const bool fuse = (ctx->params.flags & FGBD_FLAG_FUSED_SELECT) != 0;
+  s = do_estimate(ctx, k.rgb_in, k.in_dtype, nullptr, st, true, fuse, k.rgb_out, k.out_dtype);
   if (s != FGBD_OK) return s;
+  if (ctx->has_sel) return FGBD_OK;
   return do_select(ctx, k.rgb_in, k.in_dtype, nullptr, nullptr, k.rgb_out, k.out_dtype, st);
 }
 

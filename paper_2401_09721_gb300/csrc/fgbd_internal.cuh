@@ -53,6 +53,8 @@ struct DevScalars {
   long long s2[kD * kD];        // sum of (a - 128)(a - 128)^T (upper triangle filled)
   uint32_t spec_barrier;        // grid barrier of the speculative filter steps
   int32_t spec_done;            // filter steps stored by the noise-estimate kernel
+  uint32_t sigma_ready;         // set (release) once sigma_est of this estimate is written
+  uint32_t spec_go[kSpecMax + 1];  // after stored step t: 1 to take another before selecting
   uint32_t ne_end_;
   // ---- results of the noise estimate
   double eig[kD];               // descending
@@ -180,6 +182,7 @@ struct FilterArgs {
   float4* spec_x;          // [kSpecMax][cap]: x_1 .. x_S
   int32_t* spec_z;         // [kSpecMax][cap]: per point sum_c (y^2 - x_q^2), fixed point
   int cap;                 // row stride of spec_x / spec_z, a multiple of 64
+  int fuse;                // noise-estimate launch: select and filter too, once sigma_est is known
   uint8_t* keep8;          // select mode: the FSLR keep flag of every sorted point
 };
 cudaError_t launch_filter(const FilterArgs& a, int grid, cudaStream_t stream);

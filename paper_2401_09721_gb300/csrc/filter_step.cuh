@@ -97,7 +97,7 @@ __device__ __forceinline__ float block_cexp(const DevScalars* sc, float* s_cexp)
 // uses this function, so a step gives the same bits in all of them.
 __device__ __forceinline__ float4 eq5_step(const FilterArgs& a, const float4* __restrict__ src, int k, int n,
                                            float cexp) {
-  const float4 xk = src ? __ldca(&src[k]) : x0_of(a, k);
+  const float4 xk = src ? __ldcg(&src[k]) : x0_of(a, k);
   const uint32_t ck = __float_as_uint(xk.w) & kCoordMask;
   int nb[6];
   bool v[6];
@@ -119,7 +119,7 @@ __device__ __forceinline__ float4 eq5_step(const FilterArgs& a, const float4* __
   int dmin = INT_MAX;
 #pragma unroll
   for (int j = 0; j < 6; ++j) {
-    xn[j] = v[j] ? (src ? __ldca(&src[nb[j]]) : x0_of(a, nb[j])) : xk;
+    xn[j] = v[j] ? (src ? __ldcg(&src[nb[j]]) : x0_of(a, nb[j])) : xk;
     d2[j] = v[j] ? sq_dist_c1(ck, __float_as_uint(xn[j].w) & kCoordMask, a.bits) : INT_MAX;
     dmin = min(dmin, d2[j]);
   }
@@ -144,19 +144,23 @@ __device__ __forceinline__ float4 eq5_step(const FilterArgs& a, const float4* __
   return xo;
 }
 
-// The first `depth` steps x_1..x_depth, each point's Eq. 6 term
-// sum_c (y^2 - x_q^2) in fixed point beside them, by the blocks [first,
-// gridDim.x) of a cooperative grid (they need the graph and the colours
-// only, not sigma_est).  sc->spec_done = depth once every step is stored.
-__device__ __forceinline__ void speculative_steps(const FilterArgs& a, int depth, int first, int* s_ok,
-                                                  float* s_cexp) {
-  uint32_t epoch = 0;
+// The first steps x_1, x_2, ... and each point's Eq. 6 term sum_c (y^2 - x_q^2)
+// in fixed point beside them, by the blocks [first, gridDim.x) of a
+// cooperative grid (they need the graph and the colours only, not sigma_est):
+// `depth` steps, or, with `until_sigma`, fewer once sigma_est is published
+// (sc->sigma_ready).  Block `first` reads that flag before each grid barrier
+// and leaves its answer in sc->spec_go[t], which every block reads after the
+// barrier, so all blocks stop after the same step.  sc->spec_done = the steps
+// stored; returns that number, or -1 after a barrier timeout.
+__device__ __forceinline__ int speculative_steps(const FilterArgs& a, int depth, int first, bool until_sigma,
+                                                 uint32_t& epoch, int* s_ok, float* s_cexp, int* s_go) {
   const int n = a.n;
   const uint32_t members = gridDim.x - uint32_t(first);
   const int gtid = (blockIdx.x - first) * blockDim.x + threadIdx.x;
   const int gstride = int(members) * blockDim.x;
   DevScalars* sc = a.sc;
   const float cexp = block_cexp(sc, s_cexp);
+  int stored = depth;
   for (int t = 1; t <= depth; ++t) {
     const float4* src = t == 1 ? nullptr : a.spec_x + size_t(t - 2) * size_t(a.cap);
     float4* dst = a.spec_x + size_t(t - 1) * size_t(a.cap);
@@ -166,9 +170,22 @@ __device__ __forceinline__ void speculative_steps(const FilterArgs& a, int depth
       dst[k] = xo;
       z[k] = int32_t((long long)sq3(x0_of(a, k)) - (long long)sq3(xo));
     }
-    if (!grid_barrier(&sc->spec_barrier, &sc->status, members, epoch, s_ok)) return;
+    const bool ask = until_sigma && t < depth;
+    if (ask && blockIdx.x == first && threadIdx.x == 0) sc->spec_go[t] = ld_acquire_u32(&sc->sigma_ready) ? 0u : 1u;
+    if (!grid_barrier(&sc->spec_barrier, &sc->status, members, epoch, s_ok)) return -1;
+    if (ask) {
+      if (threadIdx.x == 0) *s_go = int(ld_acquire_u32(&sc->spec_go[t]));
+      __syncthreads();
+      const bool go = *s_go != 0;
+      __syncthreads();
+      if (!go) {
+        stored = t;
+        break;
+      }
+    }
   }
-  if (gtid == 0) sc->spec_done = depth;
+  if (gtid == 0) sc->spec_done = stored;
+  return stored;
 }
 
 }  // namespace fgbd

@@ -16,7 +16,7 @@
 //   the values are sorted descending and the tail rule gives sigma_est.
 #include <algorithm>
 
-#include "filter_step.cuh"
+#include "select.cuh"
 
 namespace fgbd {
 namespace {
@@ -479,6 +479,70 @@ __device__ __forceinline__ void jacobi_rotation(float app, float aqq, float apq,
   cq = make_float2(c, s);
 }
 
+// Entry (i, k) of the Helmert basis of R^7: column 0 is uniform, column k >= 1
+// is (1, ..., 1, -k, 0, ..., 0) / sqrt(k (k + 1)) with k ones.
+__device__ __forceinline__ float helmert7(int i, int k) {
+  if (k == 0) return 0.37796447300922722f;  // 1 / sqrt(7)
+  const float inv = rsqrtf(float(k * (k + 1)));
+  return i < k ? inv : (i == k ? -float(k) * inv : 0.f);
+}
+
+// Eigenvectors of the symmetric 3x3 matrix m (in place: its columns on
+// return), by cyclic Jacobi in float32 (a few sweeps converge for 3x3).
+__device__ __noinline__ void colour_basis(float (*m)[3]) {
+  float a[3][3], v[3][3];
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      a[i][j] = m[i][j];
+      v[i][j] = i == j ? 1.f : 0.f;
+    }
+  const float scale = fabsf(a[0][0]) + fabsf(a[1][1]) + fabsf(a[2][2]);
+  for (int sweep = 0; sweep < 8; ++sweep) {
+    if (!(fabsf(a[0][1]) + fabsf(a[0][2]) + fabsf(a[1][2]) > 1e-7f * scale)) break;
+    for (int pair = 0; pair < 3; ++pair) {
+      const int p = pair == 2 ? 1 : 0, q = pair == 0 ? 1 : 2;
+      float2 cp, cq;
+      jacobi_rotation(a[p][p], a[q][q], a[p][q], 1e-7f * scale, cp, cq);
+      const float c = cp.x, s = cq.y;  // column p = (c, -s) at rows (p, q), column q = (s, c)
+      if (s == 0.f) continue;
+      for (int k = 0; k < 3; ++k) {  // A J
+        const float akp = a[k][p], akq = a[k][q];
+        a[k][p] = c * akp - s * akq;
+        a[k][q] = s * akp + c * akq;
+      }
+      for (int k = 0; k < 3; ++k) {  // J^T A
+        const float apk = a[p][k], aqk = a[q][k];
+        a[p][k] = c * apk - s * aqk;
+        a[q][k] = s * apk + c * aqk;
+      }
+      for (int k = 0; k < 3; ++k) {  // V J
+        const float vkp = v[k][p], vkq = v[k][q];
+        v[k][p] = c * vkp - s * vkq;
+        v[k][q] = s * vkp + c * vkq;
+      }
+    }
+  }
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) m[i][j] = v[i][j];
+}
+
+// a / b in float64 from a float32 reciprocal and Newton steps (fused
+// multiply-adds only; the library division is much longer on this GPU).
+// Within an ulp or two of the rounded quotient for b > 0.
+__device__ __forceinline__ double div_newton(double a, double b) {
+  double r = double(__frcp_rn(float(b)));
+  r = fma(r, fma(-b, r, 1.0), r);
+  r = fma(r, fma(-b, r, 1.0), r);
+  const double q = a * r;
+  return fma(r, fma(-b, q, a), q);
+}
+
+// 64-bit integer whose signed order is the numeric order of the double x
+__device__ __forceinline__ long long order_key(double x) {
+  const long long b = __double_as_longlong(x);
+  return b < 0 ? (b ^ 0x7fffffffffffffffLL) : b;
+}
+
 // barriers of the first kFinThreads threads of a block (barrier 1; 0 is __syncthreads)
 __device__ __forceinline__ void fin_bar() { asm volatile("bar.sync 1, %0;" ::"n"(kFinThreads) : "memory"); }
 __device__ __forceinline__ bool fin_bar_or(bool v) {
@@ -497,12 +561,13 @@ __device__ __forceinline__ bool fin_bar_or(bool v) {
 __device__ __noinline__ void finalize_block(int dtype, const double* __restrict__ f64_partials, int nblocks,
                                             DevScalars* __restrict__ sc, double* __restrict__ sigma_out) {
   __shared__ double S[kD][kD];
+  __shared__ float Sf[kD][kD];  // Sigma rounded to float32 once, for the float32 work
   __shared__ double s_sum[kD * kD + kD + 1];
   __shared__ float V[kD][kD + 1];
   __shared__ float Abuf[2][kD * kD];
   __shared__ float Vbuf[2][kD * kD];
   __shared__ float2 s_coef[2][kD];
-  __shared__ double s_lam[kD];
+  __shared__ long long s_key[kD];
   __shared__ double s_sorted[kD];
   __shared__ double s_num[kD][kD];
   __shared__ double V64[kD][kD + 1];
@@ -533,6 +598,8 @@ __device__ __noinline__ void finalize_block(int dtype, const double* __restrict_
       sc->m = 0;
       sc->ne_valid = 1;
       if (sigma_out) *sigma_out = 0.0;
+      __threadfence();
+      atomicExch(&sc->sigma_ready, 1u);
     }
     return;
   }
@@ -542,7 +609,9 @@ __device__ __noinline__ void finalize_block(int dtype, const double* __restrict_
     const int r = e / kD, c = e % kD;
     const int rr = min(r, c), cc = max(r, c);
     const double mr = s_sum[kD * kD + rr] * inv_n, mc = s_sum[kD * kD + cc] * inv_n;
-    S[r][c] = s_sum[rr * kD + cc] * inv_n - mr * mc;
+    const double v = s_sum[rr * kD + cc] * inv_n - mr * mc;
+    S[r][c] = v;
+    Sf[r][c] = float(v);
   }
   fin_bar();
 
@@ -560,12 +629,58 @@ __device__ __noinline__ void finalize_block(int dtype, const double* __restrict_
   // barrier where no off-diagonal entry is above that threshold, since no
   // later round would rotate anything.
   {
-    for (int e = tid; e < kD * kD; e += kFinThreads) {
-      Abuf[0][e] = float(S[e / kD][e % kD]);
-      Vbuf[0][e] = (e / kD == e % kD) ? 1.f : 0.f;
+    // Start from V0 = H7 (x) Qc instead of the identity (entry 3 i + a of a
+    // patch is channel a of its point i): Qc diagonalises the 3x3 colour
+    // covariance averaged over the seven points, H7 is the Helmert basis of
+    // the seven points (first vector uniform).  A0 = V0^T Sigma V0 has much
+    // less off-diagonal mass, so the iteration needs about half the rounds;
+    // the eigenvalues still come from float64 Rayleigh quotients of the final
+    // vectors, so the start changes only the work, not the accuracy.
+    __shared__ float s_qc[3][3];
+    if (tid < 9) {
+      const int a = tid / 3, b = tid % 3;
+      float c = 0.f;
+      for (int i = 0; i < 7; ++i) c += Sf[3 * i + a][3 * i + b];
+      reinterpret_cast<float*>(s_qc)[tid] = c * (1.f / 7.f);
     }
+    fin_bar();
+    if (tid == 0) colour_basis(s_qc);
+    fin_bar();
+    for (int e = tid; e < kD * kD; e += kFinThreads) {
+      const int r = e / kD, c = e % kD;
+      Vbuf[0][e] = helmert7(r / 3, c / 3) * s_qc[r % 3][c % 3];
+    }
+    fin_bar();
+    // T = Sigma V0 into Vbuf[1] (scratch here), then the upper triangle of V0^T T, mirrored
+    for (int e = tid; e < kD * kD; e += kFinThreads) {
+      const int r = e / kD, c = e % kD;
+      float t0 = 0.f, t1 = 0.f, t2 = 0.f;
+#pragma unroll
+      for (int k = 0; k < kD; k += 3) {
+        t0 = fmaf(Sf[r][k], Vbuf[0][k * kD + c], t0);
+        t1 = fmaf(Sf[r][k + 1], Vbuf[0][(k + 1) * kD + c], t1);
+        t2 = fmaf(Sf[r][k + 2], Vbuf[0][(k + 2) * kD + c], t2);
+      }
+      Vbuf[1][e] = t0 + t1 + t2;
+    }
+    fin_bar();
+    for (int e = tid; e < kD * kD; e += kFinThreads) {
+      const int r = e / kD, c = e % kD;
+      if (r > c) continue;
+      float t0 = 0.f, t1 = 0.f, t2 = 0.f;
+#pragma unroll
+      for (int k = 0; k < kD; k += 3) {
+        t0 = fmaf(Vbuf[0][k * kD + r], Vbuf[1][k * kD + c], t0);
+        t1 = fmaf(Vbuf[0][(k + 1) * kD + r], Vbuf[1][(k + 1) * kD + c], t1);
+        t2 = fmaf(Vbuf[0][(k + 2) * kD + r], Vbuf[1][(k + 2) * kD + c], t2);
+      }
+      const float v = t0 + t1 + t2;
+      Abuf[0][r * kD + c] = v;
+      Abuf[0][c * kD + r] = v;
+    }
+    fin_bar();
     float dsq = 0.f;
-    for (int i = 0; i < kD; ++i) dsq = fmaf(float(S[i][i]), float(S[i][i]), dsq);
+    for (int i = 0; i < kD; ++i) dsq = fmaf(Abuf[0][i * kD + i], Abuf[0][i * kD + i], dsq);
     const float thr = 2e-7f * sqrtf(dsq);
     // roles
     const bool v_thread = tid < kVThreads;
@@ -696,7 +811,7 @@ __device__ __noinline__ void finalize_block(int dtype, const double* __restrict_
         d1 = fma(V64[r + 1][lane], V64[r + 1][lane], d1);
         d2 = fma(V64[r + 2][lane], V64[r + 2][lane], d2);
       }
-      lam = (n0 + n1 + n2) / (d0 + d1 + d2);
+      lam = div_newton(n0 + n1 + n2, d0 + d1 + d2);
     }
     // eigenvalues below 1e-9 max(lambda_1, 1) are numerical zeros (a rank-deficient
     // covariance); they are set to exactly 0 so the tail rule never decides on rounding noise
@@ -705,14 +820,17 @@ __device__ __noinline__ void finalize_block(int dtype, const double* __restrict_
     for (int o = 16; o > 0; o >>= 1) top = fmax(top, __shfl_xor_sync(kFull, top, o));
     if (lane < kD && fabs(lam) < kZeroEigRel * fmax(top, 1.0)) lam = 0.0;
     // descending order (ties by index), by counting the larger values
-    if (lane < kD) s_lam[lane] = lam;
+    // (float64 compares are slow here: the values are compared through
+    // order-preserving 64-bit integer keys of their bit patterns)
+    if (lane < kD) s_key[lane] = order_key(lam);
     __syncwarp();
     if (lane < kD) {
+      const long long mine = order_key(lam);
       int rank = 0;
 #pragma unroll
       for (int j = 0; j < kD; ++j) {
-        const double o = s_lam[j];
-        rank += (o > lam) || (o == lam && j < lane);
+        const long long o = s_key[j];
+        rank += (o > mine) || (o == mine && j < lane);
       }
       s_sorted[rank] = lam;
     }
@@ -740,13 +858,15 @@ __device__ __noinline__ void finalize_block(int dtype, const double* __restrict_
     const int m = __ffs(__ballot_sync(kFull, pass)) - 1;
     const double tail = __shfl_sync(kFull, suffix, m);
     if (lane == 0) {
-      const double tau = tail / double(kD - m);
+      const double tau = div_newton(tail, double(kD - m));
       const double sg = sqrt(fmax(tau, 0.0));
       sc->m = m;
       sc->tau = tau;
       sc->sigma_est = sg;
       sc->ne_valid = 1;
       if (sigma_out) *sigma_out = sg;
+      __threadfence();
+      atomicExch(&sc->sigma_ready, 1u);
     }
   }
 }
@@ -760,7 +880,10 @@ __global__ void __launch_bounds__(kFinThreads) k_ne_finalize(int dtype, const do
 
 // One block per SM (the dynamic shared memory keeps a second one out): block 0
 // computes sigma_est on an SM of its own, the others meanwhile take the first
-// filter steps, which need the graph and the colours only.
+// filter steps, which need the graph and the colours only.  With a.fuse they
+// then also select and filter: they stop stepping once sigma_est is published
+// (or after kSpecMax steps, then waiting for it) and run the selection over
+// the stored steps (select_filter), so no second launch follows.
 constexpr int kSpecThreads = 1024;
 constexpr int kSpecPadBytes = 100 * 1024;  // shared memory that makes a second block not fit on an SM
 
@@ -769,12 +892,32 @@ __global__ void __launch_bounds__(kSpecThreads, 1)
                        double* __restrict__ sigma_out, FilterArgs a) {
   pdl_wait();
   __shared__ int s_ok;
+  __shared__ int s_go;
   __shared__ float s_cexp;
   if (blockIdx.x == 0) {
     if (threadIdx.x < kFinThreads) finalize_block(dtype, f64_partials, nblocks, sc, sigma_out);
     return;
   }
-  speculative_steps(a, a.spec_depth, 1, &s_ok, &s_cexp);
+  uint32_t epoch = 0;
+  const int S = speculative_steps(a, a.spec_depth, 1, a.fuse != 0, epoch, &s_ok, &s_cexp, &s_go);
+  if (!a.fuse || S < 0) return;
+  // sigma_est of block 0 (a bounded wait)
+  if (threadIdx.x == 0) {
+    const unsigned long long t0 = global_ns();
+    int ok = 1;
+    while (!ld_acquire_u32(&sc->sigma_ready)) {
+      if (global_ns() - t0 > kWaitLimitNs) {
+        atomicOr(&sc->status, kFlagTimeout);
+        ok = 0;
+        break;
+      }
+      __nanosleep(128);
+    }
+    s_ok = ok;
+  }
+  __syncthreads();
+  if (!s_ok) return;
+  select_filter<kSpecThreads>(a, S, 1, gridDim.x - 1, &sc->spec_barrier, epoch);
 }
 
 }  // namespace

@@ -51,12 +51,14 @@ class Params(ctypes.Structure):
         ("fslr_factor", ctypes.c_double),
         ("q_max", ctypes.c_int32),
         ("variant", ctypes.c_int32),
-        ("reserved", ctypes.c_int32 * 6),
+        ("flags", ctypes.c_int32),
+        ("reserved", ctypes.c_int32 * 5),
     ]
 
 
 VARIANT_NO_FSLR = 1          # FGBD_VARIANT_NO_FSLR
 VARIANT_UNSORTED_PATCH = 2   # FGBD_VARIANT_UNSORTED_PATCH
+FLAG_FUSED_SELECT = 1        # FGBD_FLAG_FUSED_SELECT
 
 
 class Stats(ctypes.Structure):
@@ -393,9 +395,10 @@ class Context:
     """One FGBD context on the current CUDA device, for frames of up to ``capacity`` points."""
 
     def __init__(self, capacity: int, bits: int = 10, window: int = 1, fslr_factor: float = 2.0,
-                 q_max: int = 64, variant: int = 0):
+                 q_max: int = 64, variant: int = 0, flags: int = 0):
         p = fgbd_params_default()
         p.bits, p.window, p.fslr_factor, p.q_max, p.variant = bits, window, fslr_factor, q_max, variant
+        p.flags = flags
         self.params = p
         self.capacity = int(capacity)
         self.device = torch.device("cuda", torch.cuda.current_device())

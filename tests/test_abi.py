@@ -75,6 +75,9 @@ def test_host_side_checks_without_gpu(so):
     assert lib.fgbd_ctx_create(100, ctypes.byref(bad), ctypes.byref(out)) == 1
     bad.variant, bad.reserved[0] = 0, 1                                     # reserved must stay zero
     assert lib.fgbd_ctx_create(100, ctypes.byref(bad), ctypes.byref(out)) == 1
+    bad.reserved[0], bad.flags = 0, 2                                       # no such execution flag
+    assert lib.fgbd_ctx_create(100, ctypes.byref(bad), ctypes.byref(out)) == 1
+    assert p.flags == 0 and fgbd.FLAG_FUSED_SELECT == 1
     assert p.variant == 0 and fgbd.VARIANT_NO_FSLR == 1 and fgbd.VARIANT_UNSORTED_PATCH == 2
     assert lib.fgbd_ctx_create(100, None, None) == 1
     assert lib.fgbd_build_graph(None, None, 0, None) == 1

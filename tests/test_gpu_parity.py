@@ -335,6 +335,24 @@ def test_run_matches_separate_calls(F):
     assert np.array_equal(a, b)
 
 
+@pytest.mark.parametrize("sigma,seed", [(10.0, 21), (30.0, 22), (60.0, 23)])
+def test_fused_select_matches_default(F, sigma, seed):
+    """FGBD_FLAG_FUSED_SELECT changes where the selection runs, not what it
+    computes: outputs, q, J and sigma_est are identical to the default path."""
+    fr = synth.sphere_frame(60000, 9, sigma, seed)
+    x = torch.from_numpy(fr.xyz).cuda()
+    c = torch.from_numpy(fr.noisy).cuda()
+    res = []
+    for flags in (0, F.FLAG_FUSED_SELECT):
+        ctx = F.Context(fr.n, bits=9, flags=flags)
+        out = ctx.run(x, c).cpu().numpy()
+        res.append((out, ctx.stats()))
+    (a, sa), (b, sb) = res
+    assert np.array_equal(a, b)
+    assert sa["q"] == sb["q"] and sa["sigma_est"] == sb["sigma_est"] and sa["n_keep"] == sb["n_keep"]
+    assert sa["objective"] == sb["objective"]
+
+
 def test_repeated_runs_are_deterministic(F):
     fr = synth.sphere_frame(20500, 9, 20.0, 8)
     ctx = F.Context(fr.n, bits=9)
