@@ -156,9 +156,13 @@ __device__ __forceinline__ bool point_patch(int k, int n, int bits, int lane, co
         qb += d * d;
       }
     }
+    // cnt^2 times each population variance is an exact integer; the mean of
+    // the three standard deviations is (sum of their roots) / (3 cnt), with one
+    // rounded reciprocal instead of four divisions (a few ulp in all, far
+    // inside the band in which the selection decides exactly)
     const int nn = deg + 1;
     const float vr = float(nn * qr - sr * sr), vg = float(nn * qg - sg * sg), vb = float(nn * qb - sb * sb);
-    sp = (sqrtf(vr) / cnt + sqrtf(vg) / cnt + sqrtf(vb) / cnt) / 3.0f;
+    sp = (sqrtf(vr) + sqrtf(vg) + sqrtf(vb)) * __frcp_rn(3.0f * cnt);
   } else {
     const float4 o = yf[k];
     ownr = o.x;
@@ -174,9 +178,10 @@ __device__ __forceinline__ bool point_patch(int k, int n, int bits, int lane, co
         mb += f.b;
       }
     }
-    mr /= cnt;
-    mg /= cnt;
-    mb /= cnt;
+    const float icnt = __frcp_rn(cnt);
+    mr *= icnt;
+    mg *= icnt;
+    mb *= icnt;
     float vr = (ownr - mr) * (ownr - mr), vg = (owng - mg) * (owng - mg), vb = (ownb - mb) * (ownb - mb);
 #pragma unroll
     for (int j = 0; j < 6; ++j) {
@@ -187,7 +192,7 @@ __device__ __forceinline__ bool point_patch(int k, int n, int bits, int lane, co
         vb += (f.b - mb) * (f.b - mb);
       }
     }
-    sp = (sqrtf(vr / cnt) + sqrtf(vg / cnt) + sqrtf(vb / cnt)) / 3.0f;
+    sp = (sqrtf(vr * icnt) + sqrtf(vg * icnt) + sqrtf(vb * icnt)) * (1.0f / 3.0f);
   }
   spread[k] = sp;
   if (!patch) return false;
@@ -203,21 +208,23 @@ __device__ __forceinline__ bool point_patch(int k, int n, int bits, int lane, co
     e[j].key = (d2 << 33) | ((unsigned long long)(dz + 1024) << 22) | ((unsigned long long)(dy + 1024) << 11) |
                (unsigned long long)(dx + 1024);
   }
-  // odd-even transposition sort, 6 rounds.  Without it (the "w/o sort"
-  // ablation) the entries stay in link order: C1 prev, C1 next, C2 prev, C2
-  // next, C3 prev, C3 next.
+  // a sorting network for 6 elements with 12 comparators in 5 layers (the
+  // keys with their index are a strict order, so the result is the unique
+  // sorted one).  Without it (the "w/o sort" ablation) the entries stay in
+  // link order: C1 prev, C1 next, C2 prev, C2 next, C3 prev, C3 next.
   if (sorted_patches) {
-#pragma unroll
-    for (int round = 0; round < 6; ++round) {
-      if ((round & 1) == 0) {
-        cswap(e[0], e[1]);
-        cswap(e[2], e[3]);
-        cswap(e[4], e[5]);
-      } else {
-        cswap(e[1], e[2]);
-        cswap(e[3], e[4]);
-      }
-    }
+    cswap(e[0], e[5]);
+    cswap(e[1], e[3]);
+    cswap(e[2], e[4]);
+    cswap(e[1], e[2]);
+    cswap(e[3], e[4]);
+    cswap(e[0], e[3]);
+    cswap(e[2], e[5]);
+    cswap(e[0], e[1]);
+    cswap(e[2], e[3]);
+    cswap(e[4], e[5]);
+    cswap(e[1], e[2]);
+    cswap(e[3], e[4]);
   }
   if (DT == 0) {
     // entry r of the patch, centred on 128: the colour byte with its top bit flipped, read as int8
