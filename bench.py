@@ -31,6 +31,7 @@ SIGMAS = (10.0, 20.0, 30.0, 40.0, 50.0)
 N_POINTS = 1_000_000
 BITS = 10
 L2_FLUSH_BYTES = 512 << 20
+SPEC_STEPS = 3          # filter steps the noise-estimate launch stores (kSpecMax)
 FALLBACK_HBM_GBS = 6800.0
 
 
@@ -367,24 +368,27 @@ def algorithmic_bytes(name, n, extra_steps=0.0, out_bytes=3):
         "slg_counts0": 12, "slg_counts1": 4, "slg_counts2": 4,
         # scatter: keys and values in, keys and values (or the final arrays) out.
         # pass 0 (y-slabs) reads xyz; the slab sort reads the y-ordered pairs and
-        # writes the C3 order; pass 1 (C1 on z) writes packed codes, orders and
-        # ranks; pass 2 (C2 on x) reads the codes only and writes the C2 order
-        # and the C2 ranks
-        "slg_scatter0": 12 + 8, "slg_slab": 8 + 8, "slg_scatter1": 8 + 12, "slg_scatter2": 4 + 8,
-        "slg_link": 40,
+        # writes the C3 order; pass 1 (C1 on z) writes packed codes, input
+        # indices, ranks and the C3 order as sorted ids; pass 2 (C2 on x) reads
+        # the codes only and writes the C2 order, the C2 ranks and the codes
+        # along C2
+        "slg_scatter0": 12 + 8, "slg_slab": 8 + 8, "slg_scatter1": 8 + 16, "slg_scatter2": 4 + 12,
+        # link: codes along C1, ids and codes along C2 and C3, C2 ranks of the C3
+        # points; the neighbour slots out
+        "slg_link": 4 + 8 + 12 + 16,
         "gather_colors": 11,
         "ne_moments": 28,
     }
     if name in per_point:
         return per_point[name] * n
     if name == "ne_finalize":
-        # the two filter steps stored by the estimate launch (its eigen block moves no bytes):
+        # the filter steps stored by the estimate launch (its eigen block moves no bytes):
         # per step x in 16 (or y 4 + codes 4), c4 16, x out 16, Eq. 6 term 4, y 4
-        return 2 * 56 * n
+        return SPEC_STEPS * 56 * n
     if name == "filter_select":
-        # keep flags: y 4, codes 4, spread 4, keep 1; stored Eq. 6 terms 2 x 4 and keep 1;
-        # ordinary steps beyond the two stored ones 48 each; output: rank 4, x 16, colours out
-        return (22 + 48 * extra_steps + 20 + out_bytes) * n
+        # keep flags: y 4, spread 4, keep 1; the stored steps' Eq. 6 terms 4 each and keep 1;
+        # ordinary steps beyond the stored ones 48 each; output: rank 4, x 16, colours out
+        return (9 + 4 * SPEC_STEPS + 1 + 48 * extra_steps + 20 + out_bytes) * n
     return 0
 
 
@@ -500,8 +504,8 @@ def run_fgbd(args):
             per.setdefault(name, []).append(ms)
     ctx.set_timing(False)
     q_mean = float(np.mean(qs))
-    # steps the selection takes itself: J(q* + 1) decides, two steps come stored
-    extra_steps = float(np.mean([max(0, min(q + 1, 64) - 2) for q in qs]))
+    # steps the selection takes itself: J(q* + 1) decides, SPEC_STEPS come stored
+    extra_steps = float(np.mean([max(0, min(q + 1, 64) - SPEC_STEPS) for q in qs]))
     kernels = {}
     for name, lst in per.items():
         avg = float(np.mean(lst))

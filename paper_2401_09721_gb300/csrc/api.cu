@@ -178,6 +178,7 @@ cudaStream_t as_stream(void* s) { return static_cast<cudaStream_t>(s); }
 
 void zero_region(fgbd_ctx* ctx, size_t from, size_t to, cudaStream_t st, cudaError_t* e) {
   if (*e != cudaSuccess) return;
+  if (to > from) ctx->launches += 1;  // one k_zero_words launch
   *e = launch_zero_words(reinterpret_cast<uint32_t*>(reinterpret_cast<char*>(ctx->sc) + from), (to - from) / 4, st);
 }
 
