@@ -37,8 +37,14 @@ __global__ void __launch_bounds__(kDiffThreads)
                 const DevScalars* __restrict__ sc, int32_t* __restrict__ nb, float* __restrict__ R,
                 float* __restrict__ d2f, float* __restrict__ e) {
   pdl_wait();
-  const double sg = diff_sigma(sigma_in, sc);
-  const float cexp = sg > 0.0 ? float(1.4426950408889634 / (sg * sg)) : 0.f;
+  // the exponent scale once per block (float64 is slow on this GPU)
+  __shared__ float s_cexp;
+  if (threadIdx.x == 0) {
+    const double sg = diff_sigma(sigma_in, sc);
+    s_cexp = sg > 0.0 ? float(1.4426950408889634 / (sg * sg)) : 0.f;
+  }
+  __syncthreads();
+  const float cexp = s_cexp;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     int j[kK];
     j[0] = i > 0 ? i - 1 : -1;
@@ -154,18 +160,46 @@ __global__ void __launch_bounds__(kDiffThreads)
   }
 }
 
+// Float-float accumulator (hi + lo): TwoSum (Knuth) and the TwoProduct of a
+// fused multiply-add keep products and sums of float32 values exact to about
+// 44 bits without float64, which is slow on this GPU.
+struct FF2 {
+  float hi, lo;
+};
+__device__ __forceinline__ FF2 ff2_add(FF2 x, FF2 y) {
+  const float s = __fadd_rn(x.hi, y.hi);
+  const float bb = __fsub_rn(s, x.hi);
+  const float err = __fadd_rn(__fsub_rn(x.hi, __fsub_rn(s, bb)), __fsub_rn(y.hi, bb));
+  const float lo = __fadd_rn(err, __fadd_rn(x.lo, y.lo));
+  const float h = __fadd_rn(s, lo);
+  return {h, __fsub_rn(lo, __fsub_rn(h, s))};
+}
+// x += a * b, the product exact
+__device__ __forceinline__ FF2 ff2_fma(FF2 x, float a, float b) {
+  const float p = __fmul_rn(a, b);
+  return ff2_add(x, {p, fmaf(a, b, -p)});
+}
+__device__ __forceinline__ FF2 ff2_shfl_down(FF2 x, int o) {
+  return {__shfl_down_sync(0xffffffffu, x.hi, o), __shfl_down_sync(0xffffffffu, x.lo, o)};
+}
+
 // One adjoint step: u_out = P^T u, and this step's terms of dL/dalpha and
-// dL/dsigma (per block, float64) at partial[2 * blockIdx.x + {0, 1}].
+// dL/dsigma (per block, float64) at partial[2 * blockIdx.x + {0, 1}].  The
+// per-point terms are accumulated in float-float and only the block's warp
+// sums are combined in float64.
 __global__ void __launch_bounds__(kDiffThreads)
     k_diff_back_step(int n, float alpha, double sigma_in, const int32_t* __restrict__ nb,
                      const float* __restrict__ R, const float* __restrict__ RT, const float* __restrict__ d2f,
                      const float* __restrict__ e, const float4* __restrict__ x, const float4* __restrict__ u,
                      float4* __restrict__ u_out, const DevScalars* __restrict__ sc, double* __restrict__ partial) {
   pdl_wait();
-  __shared__ double s_red[2][kDiffThreads / 32];
-  const double sg = diff_sigma(sigma_in, sc);
-  const float c3 = sg > 0.0 ? float(2.0 / (sg * sg * sg)) : 0.f;
-  double da = 0.0, ds = 0.0;
+  __shared__ FF2 s_red[2][kDiffThreads / 32];
+  __shared__ double s_scale;  // alpha * 2 / sigma^3
+  if (threadIdx.x == 0) {
+    const double sg = diff_sigma(sigma_in, sc);
+    s_scale = sg > 0.0 ? double(alpha) * (2.0 / (sg * sg * sg)) : 0.0;
+  }
+  FF2 da = {0.f, 0.f}, ds = {0.f, 0.f};
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     float ux = 0.f, uy = 0.f, uz = 0.f;  // (W D^-1 u)_i
     float rx = 0.f, ry = 0.f, rz = 0.f;  // (R x)_i
@@ -195,16 +229,15 @@ __global__ void __launch_bounds__(kDiffThreads)
     const float4 xi = x[i];
     const float a = 1.f - alpha;
     u_out[i] = make_float4(fmaf(a, ui.x, alpha * ux), fmaf(a, ui.y, alpha * uy), fmaf(a, ui.z, alpha * uz), 0.f);
-    da += double(ui.x) * double(rx - xi.x) + double(ui.y) * double(ry - xi.y) + double(ui.z) * double(rz - xi.z);
-    ds += double(ui.x) * double(gx) + double(ui.y) * double(gy) + double(ui.z) * double(gz);
+    da = ff2_fma(ff2_fma(ff2_fma(da, ui.x, rx - xi.x), ui.y, ry - xi.y), ui.z, rz - xi.z);
+    ds = ff2_fma(ff2_fma(ff2_fma(ds, ui.x, gx), ui.y, gy), ui.z, gz);
   }
-  ds *= double(alpha) * double(c3);
   // block sums in a fixed order
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
-    da += __shfl_down_sync(0xffffffffu, da, o);
-    ds += __shfl_down_sync(0xffffffffu, ds, o);
+    da = ff2_add(da, ff2_shfl_down(da, o));
+    ds = ff2_add(ds, ff2_shfl_down(ds, o));
   }
   if (lane == 0) {
     s_red[0][warp] = da;
@@ -214,11 +247,11 @@ __global__ void __launch_bounds__(kDiffThreads)
   if (threadIdx.x == 0) {
     double a0 = 0.0, a1 = 0.0;
     for (int w = 0; w < kDiffThreads / 32; ++w) {
-      a0 += s_red[0][w];
-      a1 += s_red[1][w];
+      a0 += double(s_red[0][w].hi) + double(s_red[0][w].lo);
+      a1 += double(s_red[1][w].hi) + double(s_red[1][w].lo);
     }
     partial[2 * blockIdx.x] = a0;
-    partial[2 * blockIdx.x + 1] = a1;
+    partial[2 * blockIdx.x + 1] = a1 * s_scale;
   }
 }
 
