@@ -293,7 +293,8 @@ void release_batch_objects(fgbd_ctx* ctx) {
     }
 }
 
-fgbd_status do_build(fgbd_ctx* ctx, const int32_t* xyz, int64_t n64, cudaStream_t st) {
+// `zeroed`: the caller has already zeroed the scalar regions this call fills
+fgbd_status do_build(fgbd_ctx* ctx, const int32_t* xyz, int64_t n64, cudaStream_t st, bool zeroed = false) {
   if (n64 < 0 || n64 > ctx->capacity) return FGBD_EINVAL;
   if (n64 > 0 && !xyz) return FGBD_EINVAL;
   const int n = int(n64);
@@ -304,7 +305,7 @@ fgbd_status do_build(fgbd_ctx* ctx, const int32_t* xyz, int64_t n64, cudaStream_
   ctx->n = n;
   ctx->graph_gen += 1;
   cudaError_t e = cudaSuccess;
-  zero_region(ctx, offsetof(DevScalars, n_edges), offsetof(DevScalars, build_end_), st, &e);
+  if (!zeroed) zero_region(ctx, offsetof(DevScalars, n_edges), offsetof(DevScalars, build_end_), st, &e);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "memset");
   if (n > 0) {
     // kernel names carry the pass: 0 = y-slabs, 1 = C1 (on z, over C3), 2 = C2 (on x, over C1)
@@ -331,7 +332,7 @@ fgbd_status do_build(fgbd_ctx* ctx, const int32_t* xyz, int64_t n64, cudaStream_
 // colours to fuse_out (what do_select with the estimated sigma would do).
 fgbd_status do_estimate(fgbd_ctx* ctx, const void* rgb, int32_t dtype, double* sigma_out, cudaStream_t st,
                         bool speculate = true, bool fuse = false, void* fuse_out = nullptr,
-                        int32_t fuse_out_dtype = FGBD_U8) {
+                        int32_t fuse_out_dtype = FGBD_U8, bool zeroed = false) {
   if (!ctx->has_graph) return FGBD_ESTATE;
   if (!dtype_ok(dtype)) return FGBD_EINVAL;
   if (ctx->n > 0 && !rgb) return FGBD_EINVAL;
@@ -339,7 +340,7 @@ fgbd_status do_estimate(fgbd_ctx* ctx, const void* rgb, int32_t dtype, double* s
   const int n = ctx->n;
   ctx->has_noise = ctx->has_sel = false;
   cudaError_t e = cudaSuccess;
-  zero_region(ctx, offsetof(DevScalars, n_patches), offsetof(DevScalars, ne_end_), st, &e);
+  if (!zeroed) zero_region(ctx, offsetof(DevScalars, n_patches), offsetof(DevScalars, ne_end_), st, &e);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "memset");
   int nblocks = 0;
   if (n > 0) {
@@ -356,7 +357,7 @@ fgbd_status do_estimate(fgbd_ctx* ctx, const void* rgb, int32_t dtype, double* s
   ctx->spec_depth = n > 0 && ctx->num_sms >= 2 ? spec.spec_depth : 0;
   const bool fused = fuse && ctx->spec_depth > 0;
   spec.fuse = fused ? 1 : 0;
-  if (fused) {
+  if (fused && !zeroed) {
     zero_region(ctx, offsetof(DevScalars, ysq_keep), offsetof(DevScalars, sel_end_), st, &e);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "memset");
   }
@@ -373,13 +374,13 @@ fgbd_status do_estimate(fgbd_ctx* ctx, const void* rgb, int32_t dtype, double* s
 }
 
 fgbd_status do_select(fgbd_ctx* ctx, const void* rgb, int32_t dtype, const double* sigma_est, int32_t* q_out,
-                      void* out, int32_t out_dtype, cudaStream_t st) {
+                      void* out, int32_t out_dtype, cudaStream_t st, bool zeroed = false) {
   if (!ctx->has_noise) return FGBD_ESTATE;
   if (!dtype_ok(dtype)) return FGBD_EINVAL;
   if (rgb != ctx->noise_rgb || dtype != ctx->noise_dtype) return FGBD_ESTATE;
   ctx->has_sel = false;
   cudaError_t e = cudaSuccess;
-  zero_region(ctx, offsetof(DevScalars, ysq_keep), offsetof(DevScalars, sel_end_), st, &e);
+  if (!zeroed) zero_region(ctx, offsetof(DevScalars, ysq_keep), offsetof(DevScalars, sel_end_), st, &e);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "memset");
   FilterArgs a = filter_args(ctx, 0, 0, sigma_est, out, out_dtype, dtype);
   a.spec_depth = ctx->spec_depth;  // the kernel checks that they were all stored
@@ -391,14 +392,19 @@ fgbd_status do_select(fgbd_ctx* ctx, const void* rgb, int32_t dtype, const doubl
 }
 
 fgbd_status direct_run(fgbd_ctx* ctx, const fgbd_ctx::RunKey& k, cudaStream_t st) {
-  fgbd_status s = do_build(ctx, static_cast<const int32_t*>(k.xyz), k.n, st);
+  if (k.n < 0 || k.n > ctx->capacity) return FGBD_EINVAL;
+  // the build, noise and selection regions of the scalars are adjacent: one launch zeroes them
+  cudaError_t e = cudaSuccess;
+  zero_region(ctx, offsetof(DevScalars, n_edges), offsetof(DevScalars, sel_end_), st, &e);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "memset");
+  fgbd_status s = do_build(ctx, static_cast<const int32_t*>(k.xyz), k.n, st, true);
   if (s != FGBD_OK) return s;
   // with FGBD_FLAG_FUSED_SELECT the estimate launch selects and filters too
   const bool fuse = (ctx->params.flags & FGBD_FLAG_FUSED_SELECT) != 0;
-  s = do_estimate(ctx, k.rgb_in, k.in_dtype, nullptr, st, true, fuse, k.rgb_out, k.out_dtype);
+  s = do_estimate(ctx, k.rgb_in, k.in_dtype, nullptr, st, true, fuse, k.rgb_out, k.out_dtype, true);
   if (s != FGBD_OK) return s;
   if (ctx->has_sel) return FGBD_OK;
-  return do_select(ctx, k.rgb_in, k.in_dtype, nullptr, nullptr, k.rgb_out, k.out_dtype, st);
+  return do_select(ctx, k.rgb_in, k.in_dtype, nullptr, nullptr, k.rgb_out, k.out_dtype, st, true);
 }
 
 // host state after a replayed run: what a direct run of the same arguments leaves

@@ -86,6 +86,10 @@ static_assert(offsetof(DevScalars, n_edges) % 4 == 0 && offsetof(DevScalars, bui
                   offsetof(DevScalars, n_patches) % 4 == 0 && offsetof(DevScalars, ne_end_) % 4 == 0 &&
                   offsetof(DevScalars, ysq_keep) % 4 == 0 && offsetof(DevScalars, sel_end_) % 4 == 0,
               "DevScalars regions must be whole 32-bit words");
+static_assert(offsetof(DevScalars, n_edges) < offsetof(DevScalars, build_end_) &&
+                  offsetof(DevScalars, build_end_) < offsetof(DevScalars, n_patches) &&
+                  offsetof(DevScalars, ne_end_) < offsetof(DevScalars, ysq_keep),
+              "the build, noise and selection regions are zeroed as one range by fgbd_run");
 
 // Sort scratch for one build.
 struct SortBufs {

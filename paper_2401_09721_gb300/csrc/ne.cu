@@ -23,15 +23,44 @@ namespace {
 
 constexpr int kTiles = 28;  // 3x3 output tiles covering the upper triangle of a 21x21 matrix
 
+// Colours into sorted order: four consecutive sorted points per thread, their
+// input indices read as one int4 and the twelve colour loads issued together.
+__device__ __forceinline__ void perm_quad(const int32_t* __restrict__ perm1, int k0, int n, int (&pi)[4]) {
+  if (k0 + 4 <= n) {
+    const int4 v = *reinterpret_cast<const int4*>(perm1 + k0);
+    pi[0] = v.x;
+    pi[1] = v.y;
+    pi[2] = v.z;
+    pi[3] = v.w;
+  } else {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) pi[i] = k0 + i < n ? perm1[k0 + i] : -1;
+  }
+}
+
 __global__ void __launch_bounds__(256) k_gather_u8(const uint8_t* __restrict__ rgb, int n,
                                                    const int32_t* __restrict__ perm1,
                                                    uint32_t* __restrict__ y8) {
   pdl_wait();
-  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
-    const int pi = perm1[k];
-    if (!in_range(pi, n)) continue;
-    const size_t i = size_t(pi);
-    y8[k] = uint32_t(rgb[3 * i]) | (uint32_t(rgb[3 * i + 1]) << 8) | (uint32_t(rgb[3 * i + 2]) << 16);
+  for (int k0 = 4 * (blockIdx.x * blockDim.x + threadIdx.x); k0 < n; k0 += 4 * gridDim.x * blockDim.x) {
+    int pi[4];
+    perm_quad(perm1, k0, n, pi);
+    uint32_t c[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      c[i] = 0u;
+      if (in_range(pi[i], n)) {
+        const size_t b = 3 * size_t(pi[i]);
+        c[i] = uint32_t(__ldg(rgb + b)) | (uint32_t(__ldg(rgb + b + 1)) << 8) | (uint32_t(__ldg(rgb + b + 2)) << 16);
+      }
+    }
+    if (k0 + 4 <= n) {
+      *reinterpret_cast<uint4*>(y8 + k0) = make_uint4(c[0], c[1], c[2], c[3]);
+    } else {
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+        if (k0 + i < n) y8[k0 + i] = c[i];
+    }
   }
 }
 
@@ -39,11 +68,21 @@ __global__ void __launch_bounds__(256) k_gather_f32(const float* __restrict__ rg
                                                     const int32_t* __restrict__ perm1,
                                                     float4* __restrict__ yf) {
   pdl_wait();
-  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
-    const int pi = perm1[k];
-    if (!in_range(pi, n)) continue;
-    const size_t i = size_t(pi);
-    yf[k] = make_float4(rgb[3 * i], rgb[3 * i + 1], rgb[3 * i + 2], 0.f);
+  for (int k0 = 4 * (blockIdx.x * blockDim.x + threadIdx.x); k0 < n; k0 += 4 * gridDim.x * blockDim.x) {
+    int pi[4];
+    perm_quad(perm1, k0, n, pi);
+    float4 c[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      c[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (in_range(pi[i], n)) {
+        const size_t b = 3 * size_t(pi[i]);
+        c[i] = make_float4(__ldg(rgb + b), __ldg(rgb + b + 1), __ldg(rgb + b + 2), 0.f);
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+      if (k0 + i < n) yf[k0 + i] = c[i];
   }
 }
 
@@ -932,7 +971,7 @@ __global__ void __launch_bounds__(kSpecThreads, 1)
 cudaError_t launch_gather_colors(const void* rgb, int dtype, int n, const int32_t* perm1,
                                  uint32_t* y8, float4* yf, cudaStream_t stream) {
   if (n <= 0) return cudaSuccess;
-  const int grid = std::min((n + 255) / 256, 152 * 16);
+  const int grid = std::min((n + 1023) / 1024, 152 * 8);  // four points a thread
   if (dtype == 0)
     return launch_kernel(k_gather_u8, dim3(grid), dim3(256), 0, stream, false, static_cast<const uint8_t*>(rgb), n,
                          perm1, y8);
