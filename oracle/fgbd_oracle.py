@@ -60,6 +60,8 @@ class Params:
     # ablations of Section 3 (Tables 4 and 5); the defaults are the method as published
     fslr: bool = True             # False: "FGBD w/o FSLR", Eq. 6 over every point
     sorted_patches: bool = True   # False: "NE-GBP w/o sort", patch entries in link order
+    # a reading, not the paper's: links only between points of the same scan line
+    same_line: bool = False       # True: no link joins the end of one scan line to the next
 
 
 # --------------------------------------------------------------------------
@@ -92,7 +94,8 @@ def scan_orders(codes: np.ndarray) -> np.ndarray:
     return np.stack([np.argsort(c, kind="stable") for c in codes])
 
 
-def slg_edges(orders: np.ndarray, window: int = 1) -> np.ndarray:
+def slg_edges(orders: np.ndarray, window: int = 1, codes: np.ndarray | None = None,
+              bits: int | None = None) -> np.ndarray:
     """Section 2.2: points consecutive along a code are linked, independently per code.
 
     With window w, positions k and k+d (1 <= d <= w) are linked; the paper uses
@@ -101,13 +104,20 @@ def slg_edges(orders: np.ndarray, window: int = 1) -> np.ndarray:
     end of one scan line to the start of the next (the paper keeps these
     "distant connections").  Reading: the union over codes is a set, so a pair
     linked by several codes is one edge.
+    With ``codes`` and ``bits`` given (the same-line ablation), a pair is linked
+    along code l only if both points lie on the same scan line of that code,
+    i.e. their codes agree in all but the low b bits (the minor coordinate).
     Returns int64 [E, 2] undirected edges (i < j), lexicographically sorted.
     """
     parts = []
-    for order in orders:
+    for l, order in enumerate(orders):
         for d in range(1, window + 1):
             a = order[:-d]
             b = order[d:]
+            if codes is not None:
+                line = codes[l] >> bits
+                same = line[a] == line[b]
+                a, b = a[same], b[same]
             parts.append(np.stack([np.minimum(a, b), np.maximum(a, b)], axis=1))
     if not parts:
         return np.zeros((0, 2), np.int64)
@@ -495,7 +505,7 @@ def fgbd(g: np.ndarray, f: np.ndarray, params: Params = Params(), q: int | None 
     n = g.shape[0]
     codes = scan_line_codes(g, params.bits)
     orders = scan_orders(codes)
-    edges = slg_edges(orders, params.window)
+    edges = slg_edges(orders, params.window, codes if params.same_line else None, params.bits)
     row_ptr, col = adjacency_csr(edges, n)
     sg = sigma_g(g, row_ptr, col)
     w = edge_weights(g, row_ptr, col, sg)

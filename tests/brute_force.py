@@ -7,7 +7,8 @@ Each function restates one definition of the paper:
 
 * ``orders``            Section 2.2, Eq. 1-3: sorting by C1/C2/C3 is sorting by the
                         coordinate tuples (z,y,x), (x,z,y), (y,x,z); ties by index.
-* ``neighbour_sets``    Section 2.2: consecutive points along each order are linked.
+* ``neighbour_sets``    Section 2.2: consecutive points along each order are linked
+                        (optionally only within one scan line: the same-line ablation).
 * ``patch_covariance``  Section 2.3: Sigma = 1/N sum (a - mu)(a - mu)^T, element by element.
 * ``link_order_patches`` the "NE-GBP w/o sort" ablation (Table 4): patch entries
                         in the order the scan lines link them.
@@ -30,14 +31,22 @@ def orders(points, window=1):
     return [sorted(range(n), key=k) for k in keys]
 
 
-def neighbour_sets(points, window=1):
+# the two coordinates a scan line of each code holds fixed: C1 (z, y), C2 (x, z), C3 (y, x)
+LINE_AXES = [(2, 1), (0, 2), (1, 0)]
+
+
+def neighbour_sets(points, window=1, same_line=False):
+    """With same_line, two points are linked along a code only if they lie on
+    one scan line of it (equal in that code's two major coordinates)."""
     n = len(points)
     nb = [set() for _ in range(n)]
-    for order in orders(points):
+    for l, order in enumerate(orders(points)):
         for k in range(n):
             for d in range(1, window + 1):
                 if k + d < n:
                     a, b = order[k], order[k + d]
+                    if same_line and any(points[a][ax] != points[b][ax] for ax in LINE_AXES[l]):
+                        continue
                     if a != b:
                         nb[a].add(b)
                         nb[b].add(a)

@@ -63,6 +63,32 @@ def test_codes_orders_edges_hand_example():
     assert orc.sigma_g(xyz, row_ptr, col) == pytest.approx(expect, rel=1e-15)
 
 
+def test_same_line_links_hand_example():
+    """Four points on a 2x2 square in the z = 0 plane: along C1 and C3 the
+    middle pair (1, 2) is a jump to the next scan line, along C2 the pair
+    (2, 1); with the jumps kept the graph is the square plus the diagonal 1-2,
+    without them the square alone."""
+    xyz = np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0], [1, 1, 0]], dtype=np.int32)
+    codes = orc.scan_line_codes(xyz, 2)
+    orders = orc.scan_orders(codes)
+    assert orders.tolist() == [[0, 1, 2, 3], [0, 2, 1, 3], [0, 1, 2, 3]]
+    assert orc.slg_edges(orders).tolist() == [[0, 1], [0, 2], [1, 2], [1, 3], [2, 3]]
+    assert orc.slg_edges(orders, 1, codes, 2).tolist() == [[0, 1], [0, 2], [1, 3], [2, 3]]
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_same_line_graph_matches_brute_force(seed):
+    rng = np.random.default_rng(100 + seed)
+    n = int(rng.integers(2, 60))
+    bits = int(rng.integers(1, 4))
+    xyz = random_cloud(rng, n, bits, dup_frac=0.15 if seed % 2 else 0.0)
+    pts = [tuple(int(v) for v in p) for p in xyz]
+    codes = orc.scan_line_codes(xyz, bits)
+    edges = orc.slg_edges(orc.scan_orders(codes), 1, codes, bits)
+    row_ptr, col = orc.adjacency_csr(edges, n)
+    assert csr_sets(row_ptr, col) == bf.neighbour_sets(pts, 1, same_line=True)
+
+
 @pytest.mark.parametrize("seed", range(12))
 def test_graph_matches_brute_force(seed):
     rng = np.random.default_rng(seed)
