@@ -14,6 +14,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -566,13 +567,16 @@ def run_fgbd(args):
     e2e = {"value": world * n * args.steps / e2e_s / 1e6, "unit": "Mpoints/s",
            "h2d_bytes_per_step": int(pin_x.numel() * 4 + pin_c[0].numel()), "d2h_bytes_per_step": int(pin_o.numel())}
 
-    # ---- ablations of Tables 4 and 5 on the same frames (device-timed like the main steps)
+    # ---- ablations of Tables 4 and 5 (and the same-line reading) on the same frames,
+    # device-timed like the main steps; PSNR of the output against the clean colours
     ablations = {}
-    for name, variant in (("no_fslr", fgbd.VARIANT_NO_FSLR), ("unsorted_patch", fgbd.VARIANT_UNSORTED_PATCH)):
+    clean_d = torch.from_numpy(clean).to(dev).float()
+    for name, variant in (("as_published", 0), ("no_fslr", fgbd.VARIANT_NO_FSLR),
+                          ("unsorted_patch", fgbd.VARIANT_UNSORTED_PATCH), ("same_line", fgbd.VARIANT_SAME_LINE)):
         vctx = fgbd.Context(n, bits=BITS, variant=variant)
         for k in range(3):
             vctx.run(x, cols[k % len(cols)], out=out)
-        ms, sig, qv = [], [], []
+        ms, sig, qv, ps = [], [], [], []
         for k in range(len(cols)):
             flush.zero_()
             a0 = torch.cuda.Event(enable_timing=True)
@@ -584,9 +588,12 @@ def run_fgbd(args):
             ms.append(a0.elapsed_time(a1))
             sig.append(vst["sigma_est"])
             qv.append(vst["q"])
+            mse = float(((out.float() - clean_d) ** 2).mean().item())
+            ps.append(round(10.0 * math.log10(255.0 ** 2 / max(mse, 1e-12)), 3))
         vctx.close()
         ablations[name] = {"ms_per_step": float(np.mean(ms)), "value": n / (float(np.mean(ms)) / 1e3) / 1e6,
-                           "unit": "Mpoints/s", "sigma_est": [round(v, 4) for v in sig], "q": qv}
+                           "unit": "Mpoints/s", "sigma": list(SIGMAS), "sigma_est": [round(v, 4) for v in sig],
+                           "q": qv, "psnr_db": ps}
 
     batched = None
     if not args.no_batch:

@@ -79,6 +79,12 @@ typedef struct fgbd_params {
  *     then along C3. */
 #define FGBD_VARIANT_NO_FSLR 1
 #define FGBD_VARIANT_UNSORTED_PATCH 2
+/*   FGBD_VARIANT_SAME_LINE: links only join points of the same scan line of a
+ *     code (equal in its two major coordinates).  The method as published links
+ *     consecutive points of the global sorted order, so the last point of one
+ *     scan line is also linked to the first of the next (Section 2.2); this
+ *     switch drops those links, to measure what they contribute. */
+#define FGBD_VARIANT_SAME_LINE 4
 
 typedef struct fgbd_stats {
   int64_t n;                                /* points of the last graph */

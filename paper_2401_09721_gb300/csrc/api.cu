@@ -165,7 +165,7 @@ bool params_ok(const fgbd_params& p) {
   if (p.window < 1) return false;
   if (!(p.fslr_factor > 0.0) || p.fslr_factor > 1e30) return false;
   if (p.q_max < 0 || p.q_max > kQCap) return false;
-  if (p.variant & ~(FGBD_VARIANT_NO_FSLR | FGBD_VARIANT_UNSORTED_PATCH)) return false;
+  if (p.variant & ~(FGBD_VARIANT_NO_FSLR | FGBD_VARIANT_UNSORTED_PATCH | FGBD_VARIANT_SAME_LINE)) return false;
   if (p.flags & ~FGBD_FLAG_FUSED_SELECT) return false;
   for (int r : p.reserved)
     if (r != 0) return false;
@@ -322,7 +322,8 @@ fgbd_status do_build(fgbd_ctx* ctx, const int32_t* xyz, int64_t n64, cudaStream_
         FGBD_LAUNCH(ctx, "slg_slab", st,
                     launch_slab_sort(n, bits, ord_stride(ctx), ctx->sb, ctx->gb, ctx->sc, st));
     }
-    FGBD_LAUNCH(ctx, "slg_link", st, launch_link(n, bits, ord_stride(ctx), ctx->gb, ctx->sb, ctx->sc, ctx->num_sms, st));
+    FGBD_LAUNCH(ctx, "slg_link", st, launch_link(n, bits, ord_stride(ctx), (ctx->params.variant & FGBD_VARIANT_SAME_LINE) != 0, ctx->gb,
+                                                 ctx->sb, ctx->sc, ctx->num_sms, st));
   }
   ctx->has_graph = true;
   return FGBD_OK;

@@ -47,14 +47,14 @@ __global__ void __launch_bounds__(kDiffThreads)
   const float cexp = s_cexp;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     int j[kK];
-    j[0] = i > 0 ? i - 1 : -1;
-    j[1] = i + 1 < n ? i + 1 : -1;
+    const uint32_t ci = pk[i];  // packed code, with the same-line variant's missing-C1-link bits
+    j[0] = c1_prev_linked(ci, i) ? i - 1 : -1;
+    j[1] = c1_next_linked(ci, i, n) ? i + 1 : -1;
     const int4 s = c4[i];
     j[2] = in_range(s.x, n) ? s.x : -1;
     j[3] = in_range(s.y, n) ? s.y : -1;
     j[4] = in_range(s.z, n) ? s.z : -1;
     j[5] = in_range(s.w, n) ? s.w : -1;
-    const uint32_t ci = pk[i];
     int d2[kK];
     int dmin = INT_MAX;
 #pragma unroll

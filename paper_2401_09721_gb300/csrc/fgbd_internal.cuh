@@ -31,6 +31,11 @@ constexpr int kNeThreads = 256;
 constexpr int kFilterThreads = 512;
 constexpr int kSpecMax = 3;                        // filter steps taken while sigma_est is computed
 constexpr uint32_t kCoordMask = 0x3FFFFFFFu;       // low 30 bits: packed C1 code
+// The two high bits of a sorted point's packed code (pk, and x.w of an iterate)
+// mark a missing link to its C1 neighbour k - 1 / k + 1: set by the link step
+// only under the same-line variant, zero otherwise.
+constexpr uint32_t kNoPrevLink = 1u << 30;
+constexpr uint32_t kNoNextLink = 1u << 31;
 constexpr uint32_t kKeepBit = 0x80000000u;         // FSLR keep flag beside the code
 
 // latched device error bits
@@ -143,8 +148,8 @@ cudaError_t launch_tile_scan(const SortPassArgs& a, cudaStream_t stream);
 cudaError_t launch_sort_scatter(const SortPassArgs& a, cudaStream_t stream);
 cudaError_t launch_sort_pass(const SortPassArgs& a, cudaStream_t stream);  // the three above
 cudaError_t launch_orders_export(int n, int cap, const GraphBufs& gb, int32_t* out, cudaStream_t stream);
-cudaError_t launch_link(int n, int bits, int cap, const GraphBufs& gb, const SortBufs& sb, DevScalars* sc,
-                        int num_sms, cudaStream_t stream);
+cudaError_t launch_link(int n, int bits, int cap, bool same_line, const GraphBufs& gb, const SortBufs& sb,
+                        DevScalars* sc, int num_sms, cudaStream_t stream);
 
 cudaError_t launch_gather_colors(const void* rgb, int dtype, int n, const int32_t* perm1,
                                  uint32_t* y8, float4* yf, cudaStream_t stream);
@@ -243,6 +248,10 @@ __device__ __forceinline__ void decode_c1(uint32_t c, int b, int& x, int& y, int
   y = int((c >> b) & m);
   z = int((c >> (2 * b)) & m);
 }
+
+// whether sorted point k is linked to k - 1 / k + 1 (C1 neighbours), from its packed-code word
+__device__ __forceinline__ bool c1_prev_linked(uint32_t pkw, int k) { return k > 0 && !(pkw & kNoPrevLink); }
+__device__ __forceinline__ bool c1_next_linked(uint32_t pkw, int k, int n) { return k + 1 < n && !(pkw & kNoNextLink); }
 
 __device__ __forceinline__ int sq_dist_c1(uint32_t a, uint32_t c, int b) {
   int ax, ay, az, cx, cy, cz;

@@ -29,11 +29,12 @@ __global__ void __launch_bounds__(256) k_output(FilterArgs a) {
 
 // ---------------------------------------------------------------- export
 
-__device__ __forceinline__ int gather_row(int k, int n, const int4* c4, int nb[6]) {
+__device__ __forceinline__ int gather_row(int k, int n, const uint32_t* pk, const int4* c4, int nb[6]) {
   int cnt = 0;
   if (!in_range(k, n)) return 0;
-  if (k > 0) nb[cnt++] = k - 1;
-  if (k + 1 < n) nb[cnt++] = k + 1;
+  const uint32_t pkk = pk[k];
+  if (c1_prev_linked(pkk, k)) nb[cnt++] = k - 1;
+  if (c1_next_linked(pkk, k, n)) nb[cnt++] = k + 1;
   const int4 s = c4[k];
   if (in_range(s.x, n)) nb[cnt++] = s.x;
   if (in_range(s.y, n)) nb[cnt++] = s.y;
@@ -42,7 +43,8 @@ __device__ __forceinline__ int gather_row(int k, int n, const int4* c4, int nb[6
   return cnt;
 }
 
-__global__ void k_csr_degree(int n, const int32_t* __restrict__ rank1, const int4* __restrict__ c4,
+__global__ void k_csr_degree(int n, const int32_t* __restrict__ rank1, const uint32_t* __restrict__ pk,
+                             const int4* __restrict__ c4,
                              int64_t* __restrict__ deg) {
   pdl_wait();
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i <= n; i += gridDim.x * blockDim.x) {
@@ -51,7 +53,7 @@ __global__ void k_csr_degree(int n, const int32_t* __restrict__ rank1, const int
       continue;
     }
     int nb[6];
-    deg[i] = gather_row(rank1[i], n, c4, nb);
+    deg[i] = gather_row(rank1[i], n, pk, c4, nb);
   }
 }
 
@@ -66,7 +68,7 @@ __global__ void k_csr_fill(int n, int bits, const int32_t* __restrict__ rank1,
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     const int k = rank1[i];
     int nb[6];
-    const int cnt = gather_row(k, n, c4, nb);
+    const int cnt = gather_row(k, n, pk, c4, nb);
     if (cnt == 0) continue;
     int orig[6];
     float wv[6];
@@ -168,7 +170,8 @@ cudaError_t launch_output(const FilterArgs& a, cudaStream_t stream) {
 
 cudaError_t launch_csr_degree(int n, const GraphBufs& gb, int64_t* deg_out, cudaStream_t stream) {
   const int grid = std::max(1, std::min((n + 256) / 256, 152 * 16));
-  return launch_kernel(k_csr_degree, dim3(grid), dim3(256), 0, stream, false, n, gb.rank1, gb.c4, deg_out);
+  return launch_kernel(k_csr_degree, dim3(grid), dim3(256), 0, stream, false, n, gb.rank1, gb.pk, gb.c4,
+                       deg_out);
 }
 
 cudaError_t launch_scan_i64(int64_t* data, int64_t count, int64_t* block_tmp, cudaStream_t stream) {

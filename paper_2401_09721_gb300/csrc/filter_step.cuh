@@ -98,13 +98,14 @@ __device__ __forceinline__ float block_cexp(const DevScalars* sc, float* s_cexp)
 __device__ __forceinline__ float4 eq5_step(const FilterArgs& a, const float4* __restrict__ src, int k, int n,
                                            float cexp) {
   const float4 xk = src ? __ldcg(&src[k]) : x0_of(a, k);
-  const uint32_t ck = __float_as_uint(xk.w) & kCoordMask;
+  const uint32_t wk = __float_as_uint(xk.w);  // packed code and the missing-C1-link bits
+  const uint32_t ck = wk & kCoordMask;
   int nb[6];
   bool v[6];
   nb[0] = k - 1;
-  v[0] = k > 0;
+  v[0] = c1_prev_linked(wk, k);
   nb[1] = k + 1;
-  v[1] = k + 1 < n;
+  v[1] = c1_next_linked(wk, k, n);
   const int4 s = a.c4[k];
   nb[2] = s.x;
   nb[3] = s.y;

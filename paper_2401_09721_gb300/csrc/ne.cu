@@ -141,10 +141,11 @@ __device__ __forceinline__ bool point_patch(int k, int n, int bits, int lane, co
                                             bool moments, bool sorted_patches, uint8_t* at8, float* atf) {
   int nb[6];
   bool v[6];
+  const uint32_t pkk = pk[k];  // packed code, with the same-line variant's missing-C1-link bits
   nb[0] = k - 1;
-  v[0] = k > 0;
+  v[0] = c1_prev_linked(pkk, k);
   nb[1] = k + 1;
-  v[1] = k + 1 < n;
+  v[1] = c1_next_linked(pkk, k, n);
   const int4 s = c4[k];
   nb[2] = s.x;
   nb[3] = s.y;
@@ -237,7 +238,7 @@ __device__ __forceinline__ bool point_patch(int k, int n, int bits, int lane, co
   if (!patch) return false;
 
   int kx, ky, kz;
-  decode_c1(pk[k], bits, kx, ky, kz);
+  decode_c1(pkk, bits, kx, ky, kz);
 #pragma unroll
   for (int j = 0; j < 6; ++j) {
     int x, y, z;

@@ -81,12 +81,13 @@ __device__ __forceinline__ FF ff_sqrt(FF x) {
 __device__ __noinline__ bool keep_ff(const FilterArgs& a, int k, FF thr) {
   int nb[7];
   bool v[7];
+  const uint32_t pkk = a.pk[k];
   nb[0] = k;
   v[0] = true;
   nb[1] = k - 1;
-  v[1] = k > 0;
+  v[1] = c1_prev_linked(pkk, k);
   nb[2] = k + 1;
-  v[2] = k + 1 < a.n;
+  v[2] = c1_next_linked(pkk, k, a.n);
   const int4 s = a.c4[k];
   nb[3] = s.x;
   nb[4] = s.y;

@@ -563,7 +563,7 @@ struct LinkPt {
 };
 
 __device__ __forceinline__ LinkPt link_point(int r, int n, int code, const int32_t* __restrict__ ord,
-                                             const uint32_t* __restrict__ keys, const int32_t* __restrict__ rank2) {
+                                             const uint32_t* keys, const int32_t* __restrict__ rank2) {
   LinkPt q{-1, -1, 0u};
   if (r < 0 || r >= n) return q;
   const int k = code == 0 ? r : ord[r];
@@ -585,12 +585,25 @@ __device__ __forceinline__ LinkPt shfl_pt(LinkPt p, int delta, bool up) {
 constexpr int kLinkThreads = 256;
 constexpr int kLinkPerLane = 4;
 
-__global__ void __launch_bounds__(kLinkThreads, 6) k_link(int n, int bits, int cap, const int32_t* __restrict__ ord23,
+// whether two points lie on one scan line of `code` (equal in its two major coordinates)
+__device__ __forceinline__ bool same_scan_line(int code, uint32_t a, uint32_t c, int b) {
+  int ax, ay, az, cx, cy, cz;
+  decode_c1(a, b, ax, ay, az);
+  decode_c1(c, b, cx, cy, cz);
+  if (code == 0) return az == cz && ay == cy;
+  if (code == 1) return ax == cx && az == cz;
+  return ay == cy && ax == cx;
+}
+
+// Under the same-line variant (same_line) a pair is linked along a code only on
+// one scan line of it, and the C1 pass records the missing C1 links of every
+// sorted point in the high bits of its packed code (kNoPrevLink, kNoNextLink).
+__global__ void __launch_bounds__(kLinkThreads, 6) k_link(int n, int bits, int cap, int same_line,
+                                                       const int32_t* __restrict__ ord23,
                                                        const uint32_t* __restrict__ keys_c2,
                                                        const uint32_t* __restrict__ keys_c3,
-                                                       const int32_t* __restrict__ rank2,
-                                                       const uint32_t* __restrict__ pk, int4* __restrict__ c4,
-                                                       DevScalars* __restrict__ sc) {
+                                                       const int32_t* __restrict__ rank2, uint32_t* pk,
+                                                       int4* __restrict__ c4, DevScalars* __restrict__ sc) {
   pdl_wait();
   __shared__ unsigned long long s_red[8];
   const int code = blockIdx.y;
@@ -652,21 +665,28 @@ __global__ void __launch_bounds__(kLinkThreads, 6) k_link(int n, int bits, int c
       const LinkPt prev = i == 0 ? before : p[i - 1];
       const LinkPt next = i == kLinkPerLane - 1 ? after : p[i + 1];
       if (me.k < 0) continue;
+      const bool sl = same_line != 0;
+      const bool next_ok = next.k >= 0 && (!sl || same_scan_line(code, me.c, next.c, bits));
+      const bool prev_ok = prev.k >= 0 && (!sl || same_scan_line(code, me.c, prev.c, bits));
       // the edge to the next position: counted once, unless an earlier code links the pair
+      // (C1: adjacent sorted ids; C2: adjacent C2 positions; each on one line under the variant)
       bool dup_next = true;
-      if (next.k >= 0) {
-        dup_next = code > 0 && abs(me.k - next.k) == 1;
-        if (code == 2) dup_next |= abs(me.r2 - next.r2) == 1;
+      if (next_ok) {
+        dup_next = code > 0 && abs(me.k - next.k) == 1 && (!sl || same_scan_line(0, me.c, next.c, bits));
+        if (code == 2) dup_next |= abs(me.r2 - next.r2) == 1 && (!sl || same_scan_line(1, me.c, next.c, bits));
         if (!dup_next) {
           edges += 1;
           dist_f += sqrtf(float(sq_dist_c1(me.c, next.c, bits)));
         }
       }
-      if (code == 0) continue;
+      if (code == 0) {
+        if (sl) pk[me.k] = (me.c & kCoordMask) | (prev_ok ? 0u : kNoPrevLink) | (next_ok ? 0u : kNoNextLink);
+        continue;
+      }
       bool dup_prev = true;
-      if (prev.k >= 0) {
-        dup_prev = abs(me.k - prev.k) == 1;
-        if (code == 2) dup_prev |= abs(me.r2 - prev.r2) == 1;
+      if (prev_ok) {
+        dup_prev = abs(me.k - prev.k) == 1 && (!sl || same_scan_line(0, me.c, prev.c, bits));
+        if (code == 2) dup_prev |= abs(me.r2 - prev.r2) == 1 && (!sl || same_scan_line(1, me.c, prev.c, bits));
       }
       int2* slot = reinterpret_cast<int2*>(c4 + me.k) + (code - 1);
       *slot = make_int2(dup_prev ? -1 : prev.k, dup_next ? -1 : next.k);
@@ -753,14 +773,14 @@ cudaError_t launch_slab_sort(int n, int bits, int cap, const SortBufs& sb, const
                        reinterpret_cast<uint32_t*>(gb.rank2), sb.keys[1], gb.ord23 + size_t(cap), sc);
 }
 
-cudaError_t launch_link(int n, int bits, int cap, const GraphBufs& gb, const SortBufs& sb, DevScalars* sc,
-                        int num_sms, cudaStream_t stream) {
+cudaError_t launch_link(int n, int bits, int cap, bool same_line, const GraphBufs& gb, const SortBufs& sb,
+                        DevScalars* sc, int num_sms, cudaStream_t stream) {
   if (n <= 0) return cudaSuccess;
   // the three codes' blocks together fill the GPU once (6 resident blocks of 256 threads per SM)
   const int gx = std::max(1, std::min((n + kLinkThreads * kLinkPerLane - 1) / (kLinkThreads * kLinkPerLane),
                                       num_sms * 2));
-  return launch_kernel(k_link, dim3(gx, 3), dim3(kLinkThreads), 0, stream, false, n, bits, cap, gb.ord23, sb.keys[0],
-                       sb.keys[1], gb.rank2, gb.pk, gb.c4, sc);
+  return launch_kernel(k_link, dim3(gx, 3), dim3(kLinkThreads), 0, stream, false, n, bits, cap, same_line ? 1 : 0,
+                       gb.ord23, sb.keys[0], sb.keys[1], gb.rank2, gb.pk, gb.c4, sc);
 }
 
 cudaError_t launch_orders_export(int n, int cap, const GraphBufs& gb, int32_t* out, cudaStream_t stream) {

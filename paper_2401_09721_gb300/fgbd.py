@@ -58,6 +58,7 @@ class Params(ctypes.Structure):
 
 VARIANT_NO_FSLR = 1          # FGBD_VARIANT_NO_FSLR
 VARIANT_UNSORTED_PATCH = 2   # FGBD_VARIANT_UNSORTED_PATCH
+VARIANT_SAME_LINE = 4        # FGBD_VARIANT_SAME_LINE
 FLAG_FUSED_SELECT = 1        # FGBD_FLAG_FUSED_SELECT
 
 

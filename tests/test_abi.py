@@ -71,7 +71,7 @@ def test_host_side_checks_without_gpu(so):
     assert lib.fgbd_ctx_create(100, ctypes.byref(bad), ctypes.byref(out)) == 1
     bad.bits, bad.q_max = 10, 257
     assert lib.fgbd_ctx_create(100, ctypes.byref(bad), ctypes.byref(out)) == 1
-    bad.q_max, bad.variant = 64, 4                                          # no such ablation switch
+    bad.q_max, bad.variant = 64, 8                                          # no such ablation switch
     assert lib.fgbd_ctx_create(100, ctypes.byref(bad), ctypes.byref(out)) == 1
     bad.variant, bad.reserved[0] = 0, 1                                     # reserved must stay zero
     assert lib.fgbd_ctx_create(100, ctypes.byref(bad), ctypes.byref(out)) == 1
@@ -79,6 +79,7 @@ def test_host_side_checks_without_gpu(so):
     assert lib.fgbd_ctx_create(100, ctypes.byref(bad), ctypes.byref(out)) == 1
     assert p.flags == 0 and fgbd.FLAG_FUSED_SELECT == 1
     assert p.variant == 0 and fgbd.VARIANT_NO_FSLR == 1 and fgbd.VARIANT_UNSORTED_PATCH == 2
+    assert fgbd.VARIANT_SAME_LINE == 4
     assert lib.fgbd_ctx_create(100, None, None) == 1
     assert lib.fgbd_build_graph(None, None, 0, None) == 1
     assert lib.fgbd_sync(None, None) == 1

@@ -125,7 +125,8 @@ def check_u8(out8, ref):
 def full_check(F, xyz, rgb, bits, q_max=64, variant=0):
     no_fslr = bool(variant & F.VARIANT_NO_FSLR)
     params = orc.Params(bits=bits, q_max=q_max, fslr=not no_fslr,
-                        sorted_patches=not (variant & F.VARIANT_UNSORTED_PATCH))
+                        sorted_patches=not (variant & F.VARIANT_UNSORTED_PATCH),
+                        same_line=bool(variant & F.VARIANT_SAME_LINE))
     res = orc.fgbd(xyz, rgb, params)
     ctx, g = gpu_frame(F, xyz, rgb, bits, q_max, variant)
     check_graph(g, res, xyz)
@@ -163,7 +164,7 @@ def test_float_colours(F):
 
 # ------------------------------------------------------------------ ablations (Tables 4 and 5)
 
-@pytest.mark.parametrize("variant", [1, 2, 3])
+@pytest.mark.parametrize("variant", [1, 2, 3, 4, 6, 7])
 def test_ablation_variants_dense_shell(F, variant):
     xyz = synth.torso_points(60000, 8, 4)
     clean = synth.piecewise_colors(xyz, 8, 4)
@@ -177,6 +178,23 @@ def test_unsorted_patches_random_clouds(F, n, bits, seed):
     xyz = rng.integers(0, 1 << bits, size=(n, 3)).astype(np.int32)
     rgb = rng.integers(0, 256, size=(n, 3)).astype(np.uint8)
     full_check(F, xyz, rgb, bits, variant=2)
+
+
+@pytest.mark.parametrize("n,bits,seed,variant", [(4097, 6, 13, 4), (12289, 10, 14, 4), (9000, 5, 15, 6)])
+def test_same_line_links_random_clouds(F, n, bits, seed, variant):
+    """Links only within a scan line (a reading's ablation): random clouds with
+    repeated voxels, many short lines and line ends."""
+    rng = np.random.default_rng(seed)
+    xyz = rng.integers(0, 1 << bits, size=(n, 3)).astype(np.int32)
+    rgb = rng.integers(0, 256, size=(n, 3)).astype(np.uint8)
+    full_check(F, xyz, rgb, bits, variant=variant)
+
+
+def test_same_line_float_colours(F):
+    xyz = synth.torso_points(30000, 8, 7)
+    clean = synth.piecewise_colors(xyz, 8, 7, as_float=True)
+    noisy = synth.add_noise_f32(clean, 20.0, 7)
+    full_check(F, xyz, noisy, 8, variant=4)
 
 
 def test_unsorted_patches_float_colours(F):
