@@ -322,8 +322,10 @@ fgbd_status do_build(fgbd_ctx* ctx, const int32_t* xyz, int64_t n64, cudaStream_
         FGBD_LAUNCH(ctx, "slg_slab", st,
                     launch_slab_sort(n, bits, ord_stride(ctx), ctx->sb, ctx->gb, ctx->sc, st));
     }
-    FGBD_LAUNCH(ctx, "slg_link", st, launch_link(n, bits, ord_stride(ctx), (ctx->params.variant & FGBD_VARIANT_SAME_LINE) != 0, ctx->gb,
-                                                 ctx->sb, ctx->sc, ctx->num_sms, st));
+    const bool same_line = (ctx->params.variant & FGBD_VARIANT_SAME_LINE) != 0;
+    FGBD_LAUNCH(ctx, "slg_link", st,
+                launch_link(n, bits, ord_stride(ctx), same_line, ctx->gb, ctx->sb, ctx->sc, ctx->num_sms, st));
+    if (same_line) ctx->launches += 1;  // and k_c1_line_flags
   }
   ctx->has_graph = true;
   return FGBD_OK;

@@ -596,14 +596,15 @@ __device__ __forceinline__ bool same_scan_line(int code, uint32_t a, uint32_t c,
 }
 
 // Under the same-line variant (same_line) a pair is linked along a code only on
-// one scan line of it, and the C1 pass records the missing C1 links of every
-// sorted point in the high bits of its packed code (kNoPrevLink, kNoNextLink).
-__global__ void __launch_bounds__(kLinkThreads, 6) k_link(int n, int bits, int cap, int same_line,
+// one scan line of it (k_c1_line_flags then records the missing C1 links).
+template <bool SAME_LINE>
+__global__ void __launch_bounds__(kLinkThreads, 6) k_link(int n, int bits, int cap,
                                                        const int32_t* __restrict__ ord23,
                                                        const uint32_t* __restrict__ keys_c2,
                                                        const uint32_t* __restrict__ keys_c3,
-                                                       const int32_t* __restrict__ rank2, uint32_t* pk,
-                                                       int4* __restrict__ c4, DevScalars* __restrict__ sc) {
+                                                       const int32_t* __restrict__ rank2,
+                                                       const uint32_t* __restrict__ pk, int4* __restrict__ c4,
+                                                       DevScalars* __restrict__ sc) {
   pdl_wait();
   __shared__ unsigned long long s_red[8];
   const int code = blockIdx.y;
@@ -665,7 +666,7 @@ __global__ void __launch_bounds__(kLinkThreads, 6) k_link(int n, int bits, int c
       const LinkPt prev = i == 0 ? before : p[i - 1];
       const LinkPt next = i == kLinkPerLane - 1 ? after : p[i + 1];
       if (me.k < 0) continue;
-      const bool sl = same_line != 0;
+      constexpr bool sl = SAME_LINE;
       const bool next_ok = next.k >= 0 && (!sl || same_scan_line(code, me.c, next.c, bits));
       const bool prev_ok = prev.k >= 0 && (!sl || same_scan_line(code, me.c, prev.c, bits));
       // the edge to the next position: counted once, unless an earlier code links the pair
@@ -679,10 +680,7 @@ __global__ void __launch_bounds__(kLinkThreads, 6) k_link(int n, int bits, int c
           dist_f += sqrtf(float(sq_dist_c1(me.c, next.c, bits)));
         }
       }
-      if (code == 0) {
-        if (sl) pk[me.k] = (me.c & kCoordMask) | (prev_ok ? 0u : kNoPrevLink) | (next_ok ? 0u : kNoNextLink);
-        continue;
-      }
+      if (code == 0) continue;
       bool dup_prev = true;
       if (prev_ok) {
         dup_prev = abs(me.k - prev.k) == 1 && (!sl || same_scan_line(0, me.c, prev.c, bits));
@@ -698,6 +696,21 @@ __global__ void __launch_bounds__(kLinkThreads, 6) k_link(int n, int bits, int c
   if (threadIdx.x == 0) {
     if (edges) atomicAdd(&sc->n_edges, edges);
     if (dist) atomicAdd(&sc->dist_fx, dist);
+  }
+}
+
+// Same-line variant: the missing links of every sorted point to its C1
+// neighbours k - 1, k + 1 (not on its C1 scan line) go into the high bits of
+// its packed code, where every kernel that takes k +- 1 as neighbours looks.
+// (A neighbour's word may already carry its own bits when read: the
+// coordinates are decoded through masks, so that does not matter.)
+__global__ void __launch_bounds__(256) k_c1_line_flags(int n, int bits, uint32_t* pk) {
+  pdl_wait();
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+    const uint32_t c = pk[k] & kCoordMask;
+    const bool prev_ok = k > 0 && same_scan_line(0, c, pk[k - 1], bits);
+    const bool next_ok = k + 1 < n && same_scan_line(0, c, pk[k + 1], bits);
+    pk[k] = c | (prev_ok ? 0u : kNoPrevLink) | (next_ok ? 0u : kNoNextLink);
   }
 }
 
@@ -779,8 +792,14 @@ cudaError_t launch_link(int n, int bits, int cap, bool same_line, const GraphBuf
   // the three codes' blocks together fill the GPU once (6 resident blocks of 256 threads per SM)
   const int gx = std::max(1, std::min((n + kLinkThreads * kLinkPerLane - 1) / (kLinkThreads * kLinkPerLane),
                                       num_sms * 2));
-  return launch_kernel(k_link, dim3(gx, 3), dim3(kLinkThreads), 0, stream, false, n, bits, cap, same_line ? 1 : 0,
-                       gb.ord23, sb.keys[0], sb.keys[1], gb.rank2, gb.pk, gb.c4, sc);
+  if (!same_line)
+    return launch_kernel(k_link<false>, dim3(gx, 3), dim3(kLinkThreads), 0, stream, false, n, bits, cap, gb.ord23,
+                         sb.keys[0], sb.keys[1], gb.rank2, gb.pk, gb.c4, sc);
+  const cudaError_t e = launch_kernel(k_link<true>, dim3(gx, 3), dim3(kLinkThreads), 0, stream, false, n, bits, cap,
+                                      gb.ord23, sb.keys[0], sb.keys[1], gb.rank2, gb.pk, gb.c4, sc);
+  if (e != cudaSuccess) return e;
+  return launch_kernel(k_c1_line_flags, dim3(std::min((n + 255) / 256, num_sms * 8)), dim3(256), 0, stream, false, n,
+                       bits, gb.pk);
 }
 
 cudaError_t launch_orders_export(int n, int cap, const GraphBufs& gb, int32_t* out, cudaStream_t stream) {
