@@ -189,6 +189,25 @@ fgbd_status fgbd_denoise(fgbd_ctx* ctx, const void* rgb_in, int32_t in_dtype, in
 fgbd_status fgbd_run(fgbd_ctx* ctx, const int32_t* xyz, int64_t n, const void* rgb_in, int32_t in_dtype,
                      void* rgb_out, int32_t out_dtype, void* stream);
 
+/* fgbd_run on HOST buffers (no counterpart in the paper): the coordinates and
+ * colours are copied into one of two device staging slots owned by the
+ * context, the run takes place on `stream` exactly as fgbd_run, and the result
+ * is copied back into rgb_out.  The copies run on two copy streams of the
+ * context, so consecutive calls pipeline: a call's input copy overlaps the
+ * previous call's device work, and its output copy overlaps the next call's.
+ *   xyz [n][3], rgb_in [n][3], rgb_out [n][3]: host memory, page-locked
+ *     (cudaHostAlloc / cudaHostRegister) for the copies to be asynchronous;
+ *     pageable memory also works, with synchronous copies.
+ * Ownership: the host buffers of a call are read / written asynchronously.
+ * They are free again (inputs no longer read, output complete) once
+ * fgbd_sync(ctx, stream) has returned, or once the call after the next one on
+ * this context has returned (it waits for this call's output copy before it
+ * reuses its staging slot).  The first call allocates the staging memory
+ * (about 72 bytes per point of capacity) and synchronises the device once.
+ * Errors: as fgbd_run; FGBD_ENOMEM if the staging memory cannot be had. */
+fgbd_status fgbd_run_host(fgbd_ctx* ctx, const int32_t* xyz, int64_t n, const void* rgb_in, int32_t in_dtype,
+                          void* rgb_out, int32_t out_dtype, void* stream);
+
 /* Streaming mode of Section 3 (2): the noise estimate and the selection run
  * on some frames only, and the other frames reuse the q of the previous one.
  * This call builds the graph of the new frame (Section 2.2) and filters it
@@ -253,8 +272,9 @@ fgbd_status fgbd_filter_forward(fgbd_ctx* ctx, const float* rgb_in, int32_t q, d
 fgbd_status fgbd_filter_backward(fgbd_ctx* ctx, const float* grad_out, float* grad_in, double* grad_params,
                                  void* stream);
 
-/* Wait for the context's work on `stream` and return any latched device error
- * (FGBD_ERANGE, FGBD_ETIMEOUT), clearing it. */
+/* Wait for the context's work on `stream` (and for the output copies of
+ * fgbd_run_host) and return any latched device error (FGBD_ERANGE,
+ * FGBD_ETIMEOUT), clearing it. */
 fgbd_status fgbd_sync(fgbd_ctx* ctx, void* stream);
 
 /* Synchronise `stream`, then copy the scalars of the last build, estimate and

@@ -94,6 +94,14 @@ struct fgbd_ctx {
   cudaEvent_t ev_fork = nullptr;    // recorded on the caller's stream (first context of a batch)
   cudaEvent_t ev_filter = nullptr;  // this frame's cooperative filter has finished
   cudaEvent_t ev_join = nullptr;    // all of this frame's work has finished
+  // fgbd_run_host: two staging slots (coordinates, colours in, colours out) and
+  // the copy streams and events that pipeline consecutive calls
+  void* stage = nullptr;
+  size_t stage_bytes = 0;
+  int stage_next = 0;
+  bool stage_used[2] = {false, false};
+  cudaStream_t h2d = nullptr, d2h = nullptr;
+  cudaEvent_t ev_in[2] = {}, ev_run[2] = {}, ev_out[2] = {};
   // instrumentation
   int64_t launches = 0;
   bool timing = false;
@@ -586,6 +594,12 @@ void fgbd_ctx_destroy(fgbd_ctx* ctx) {
   for (cudaEvent_t e : ctx->ev)
     if (e) cudaEventDestroy(e);
   release_batch_objects(ctx);
+  for (int i = 0; i < 2; ++i)
+    for (cudaEvent_t e : {ctx->ev_in[i], ctx->ev_run[i], ctx->ev_out[i]})
+      if (e) cudaEventDestroy(e);
+  for (cudaStream_t st : {ctx->h2d, ctx->d2h})
+    if (st) cudaStreamDestroy(st);
+  cudaFree(ctx->stage);
   cudaFree(ctx->dmem);
   cudaFree(ctx->mem);
   delete ctx;
@@ -679,6 +693,62 @@ fgbd_status fgbd_run(fgbd_ctx* ctx, const int32_t* xyz, int64_t n, const void* r
     if (ctx->run_seen.size() > 16) ctx->run_seen.erase(ctx->run_seen.begin());
   }
   return direct_run(ctx, key, st);
+}
+
+fgbd_status fgbd_run_host(fgbd_ctx* ctx, const int32_t* xyz, int64_t n, const void* rgb_in, int32_t in_dtype,
+                          void* rgb_out, int32_t out_dtype, void* stream) {
+  if (!ctx) return FGBD_EINVAL;
+  if (!dtype_ok(in_dtype) || !dtype_ok(out_dtype)) return FGBD_EINVAL;
+  if (n < 0 || n > ctx->capacity) return FGBD_EINVAL;
+  if (n > 0 && (!xyz || !rgb_in || !rgb_out)) return FGBD_EINVAL;
+  DeviceGuard g(ctx->device);
+  const cudaStream_t st = as_stream(stream);
+  const size_t C = size_t(ctx->capacity);
+  const size_t xyz_b = align_up(C * 12, 256), col_b = align_up(C * 12, 256);  // float colours are the larger
+  const size_t slot_b = xyz_b + 2 * col_b;
+  if (!ctx->stage) {
+    // first call: the staging slots, copy streams and events (this synchronises the device once)
+    if (cudaMalloc(&ctx->stage, 2 * slot_b) != cudaSuccess) {
+      cudaGetLastError();
+      ctx->stage = nullptr;
+      return FGBD_ENOMEM;
+    }
+    ctx->stage_bytes = 2 * slot_b;
+    FGBD_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->h2d, cudaStreamNonBlocking));
+    FGBD_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->d2h, cudaStreamNonBlocking));
+    for (int i = 0; i < 2; ++i) {
+      FGBD_CUDA(ctx, cudaEventCreateWithFlags(&ctx->ev_in[i], cudaEventDisableTiming));
+      FGBD_CUDA(ctx, cudaEventCreateWithFlags(&ctx->ev_run[i], cudaEventDisableTiming));
+      FGBD_CUDA(ctx, cudaEventCreateWithFlags(&ctx->ev_out[i], cudaEventDisableTiming));
+    }
+  }
+  const int slot = ctx->stage_next;
+  ctx->stage_next ^= 1;
+  // the call before the previous one used this slot: its output copy must be done
+  // (so its host buffers are free again) before the slot is refilled
+  if (ctx->stage_used[slot]) FGBD_CUDA(ctx, cudaEventSynchronize(ctx->ev_out[slot]));
+  char* base = static_cast<char*>(ctx->stage) + size_t(slot) * slot_b;
+  int32_t* dxyz = reinterpret_cast<int32_t*>(base);
+  void* din = base + xyz_b;
+  void* dout = base + xyz_b + col_b;
+  const size_t in_b = size_t(n) * (in_dtype == FGBD_U8 ? 3 : 12);
+  const size_t out_b = size_t(n) * (out_dtype == FGBD_U8 ? 3 : 12);
+  // inputs on the copy stream, at once: they overlap the previous call's device work
+  if (n > 0) {
+    FGBD_CUDA(ctx, cudaMemcpyAsync(dxyz, xyz, size_t(n) * 12, cudaMemcpyHostToDevice, ctx->h2d));
+    FGBD_CUDA(ctx, cudaMemcpyAsync(din, rgb_in, in_b, cudaMemcpyHostToDevice, ctx->h2d));
+  }
+  FGBD_CUDA(ctx, cudaEventRecord(ctx->ev_in[slot], ctx->h2d));
+  FGBD_CUDA(ctx, cudaStreamWaitEvent(st, ctx->ev_in[slot], 0));
+  ctx->stage_used[slot] = true;
+  const fgbd_status s = fgbd_run(ctx, dxyz, n, din, in_dtype, dout, out_dtype, stream);
+  if (s != FGBD_OK) return s;
+  // the output on the other copy stream, after the run
+  FGBD_CUDA(ctx, cudaEventRecord(ctx->ev_run[slot], st));
+  FGBD_CUDA(ctx, cudaStreamWaitEvent(ctx->d2h, ctx->ev_run[slot], 0));
+  if (n > 0) FGBD_CUDA(ctx, cudaMemcpyAsync(rgb_out, dout, out_b, cudaMemcpyDeviceToHost, ctx->d2h));
+  FGBD_CUDA(ctx, cudaEventRecord(ctx->ev_out[slot], ctx->d2h));
+  return FGBD_OK;
 }
 
 fgbd_status fgbd_run_reuse(fgbd_ctx* ctx, const int32_t* xyz, int64_t n, const void* rgb_in, int32_t in_dtype,
@@ -837,6 +907,8 @@ fgbd_status fgbd_filter_backward(fgbd_ctx* ctx, const float* grad_out, float* gr
 fgbd_status fgbd_sync(fgbd_ctx* ctx, void* stream) {
   if (!ctx) return FGBD_EINVAL;
   DeviceGuard g(ctx->device);
+  // the output copies of fgbd_run_host run on the context's own copy stream
+  if (ctx->d2h) FGBD_CUDA(ctx, cudaStreamSynchronize(ctx->d2h));
   return take_device_status(ctx, as_stream(stream));
 }
 

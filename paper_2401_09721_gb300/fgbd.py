@@ -106,6 +106,7 @@ _SIGS = {
     "fgbd_denoise": (ctypes.c_int, [_P, _P, ctypes.c_int32, ctypes.c_int32, _P, ctypes.c_int32, _P]),
     "fgbd_run": (ctypes.c_int, [_P, _P, ctypes.c_int64, _P, ctypes.c_int32, _P, ctypes.c_int32, _P]),
     "fgbd_run_reuse": (ctypes.c_int, [_P, _P, ctypes.c_int64, _P, ctypes.c_int32, _P, ctypes.c_int32, _P]),
+    "fgbd_run_host": (ctypes.c_int, [_P, _P, ctypes.c_int64, _P, ctypes.c_int32, _P, ctypes.c_int32, _P]),
     "fgbd_run_batch": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(ctypes.c_int64),
                                       ctypes.POINTER(_P), ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(_P),
                                       ctypes.POINTER(ctypes.c_int32), ctypes.c_int32, _P]),
@@ -252,6 +253,24 @@ def fgbd_run_reuse(ctx, xyz: torch.Tensor, rgb_in: torch.Tensor, rgb_out: torch.
     _need_cuda(rgb_out, "rgb_out", n)
     _check(lib().fgbd_run_reuse(ctx, _ptr(xyz), n, _ptr(rgb_in), _dtype_code(rgb_in), _ptr(rgb_out),
                                 _dtype_code(rgb_out), _stream(stream)), "fgbd_run_reuse", ctx)
+
+
+def _need_host(t: torch.Tensor, name: str, n: int) -> None:
+    if t.device.type != "cpu" or not t.is_contiguous() or tuple(t.shape) != (n, 3):
+        raise ValueError(f"{name} must be a contiguous [n, 3] CPU tensor")
+
+
+def fgbd_run_host(ctx, xyz: torch.Tensor, rgb_in: torch.Tensor, rgb_out: torch.Tensor, stream=None) -> None:
+    """fgbd_run on host tensors (pin them for asynchronous copies); see fgbd_run_host in fgbd.h
+    for when the buffers are free again."""
+    if xyz.dtype != torch.int32:
+        raise TypeError("xyz must be int32")
+    n = xyz.shape[0]
+    _need_host(xyz, "xyz", n)
+    _need_host(rgb_in, "rgb_in", n)
+    _need_host(rgb_out, "rgb_out", n)
+    _check(lib().fgbd_run_host(ctx, _ptr(xyz), n, _ptr(rgb_in), _dtype_code(rgb_in), _ptr(rgb_out),
+                               _dtype_code(rgb_out), _stream(stream)), "fgbd_run_host", ctx)
 
 
 BATCH_MAX = 64  # FGBD_BATCH_MAX
@@ -442,6 +461,12 @@ class Context:
 
     def sync(self, stream=None):
         fgbd_sync(self.handle, stream)
+
+    def run_host(self, xyz, rgb_in, out, stream=None):
+        """fgbd_run on host (CPU) tensors; `out` is complete after sync() or two calls later."""
+        fgbd_run_host(self.handle, xyz, rgb_in, out, stream)
+        self.n = xyz.shape[0]
+        return out
 
     def run_reuse(self, xyz, rgb_in, out_dtype=torch.float32, out=None, stream=None):
         """Build this frame's graph and filter it with the last selected q (streaming mode)."""
