@@ -409,3 +409,33 @@ def test_fslr_band_decisions(F, dtype):
             assert keep[p] == (sign > 0), (p, sign)
             near = np.abs(sp - thr) <= 1e-11 * thr
             assert np.array_equal(keep[~near], ~(sp > thr)[~near])
+
+
+# ------------------------------------------------------------------ the full-size workload
+
+@pytest.mark.parametrize("sigma", [10.0, 30.0, 50.0])
+def test_full_size_torso_frame_through_fgbd_run(F, sigma):
+    """The benchmarked 1M-point torso frame (b = 10) in the launch configuration
+    the benchmark times: fgbd_run, whose second call replays the CUDA graph
+    captured from the first.  The whole frame is compared with the oracle: the
+    graph bit for bit, sigma_est, q, the FSLR flags and every output colour."""
+    xyz = synth.torso_points(1_000_000, 10, 0)
+    clean = synth.piecewise_colors(xyz, 10, 0)
+    noisy = synth.add_noise_u8(clean, sigma, 11 * int(sigma // 10 - 1))
+    res = orc.fgbd(xyz, noisy, orc.Params(bits=10))
+    ctx = F.Context(len(xyz), bits=10)
+    x = torch.from_numpy(xyz).cuda()
+    c = torch.from_numpy(noisy).cuda()
+    outs = [ctx.run(x, c, out_dtype=torch.float32).cpu().numpy() for _ in range(3)]
+    assert np.array_equal(outs[0], outs[1]) and np.array_equal(outs[1], outs[2])
+    st = ctx.stats()
+    row_ptr, col, w = ctx.graph_csr()
+    spread, keep = ctx.fslr()
+    g = dict(stats=st, out=outs[2], row_ptr=row_ptr.cpu().numpy(), col=col.cpu().numpy(), w=w.cpu().numpy(),
+             orders=ctx.orders().cpu().numpy(), spread=spread.cpu().numpy(),
+             keep=keep.cpu().numpy().astype(bool), x=x, c=c)
+    check_graph(g, res, xyz)
+    check_noise(g, res)
+    check_fslr(g, res)
+    check_selection(F, ctx, g, res, noisy)
+    ctx.close()
