@@ -271,6 +271,23 @@ def time_oracle(xyz, rgbs):
             return json.load(fh)["times"]
 
 
+def max_over_ranks(values, dist=None, device="cpu"):
+    """Each of `values` maximised over the ranks of the job (the slowest rank
+    sets the job's time); the values themselves when there is one rank."""
+    if dist is None:
+        return [float(v) for v in values]
+    import torch
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t.tolist()]
+
+
+def job_throughput(world, n_points, steps, seconds):
+    """Whole-job Mpoints/s and frames/s: every rank takes one n_points frame per step
+    (replicas), and the job's time is the slowest rank's."""
+    return world * n_points * steps / seconds / 1e6, world * steps / seconds
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -485,13 +502,8 @@ def run_fgbd(args):
     st = ctx.stats()
     launches = st["launches"] - launches0
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
-    total_s = sum(step_ms) / 1e3
-    if dist:
-        t = torch.tensor([total_s], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_s = float(t.item())
-    value = world * n * args.steps / total_s / 1e6
-    fps = world * args.steps / total_s
+    total_s = max_over_ranks([sum(step_ms) / 1e3], dist, dev)[0]
+    value, fps = job_throughput(world, n, args.steps, total_s)
 
     # ---- per-kernel timing pass (separate, instrumented)
     ctx.set_timing(True)
@@ -577,14 +589,11 @@ def run_fgbd(args):
             e_en[k - args.warmup].record(stream)
     torch.cuda.synchronize()
     serial_s = sum(a.elapsed_time(b) for a, b in zip(e_st, e_en)) / 1e3
-    if dist:
-        t = torch.tensor([e2e_s, serial_s], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s, serial_s = float(t[0].item()), float(t[1].item())
-    e2e = {"value": world * n * args.steps / e2e_s / 1e6, "unit": "Mpoints/s",
+    e2e_s, serial_s = max_over_ranks([e2e_s, serial_s], dist, dev)
+    e2e = {"value": job_throughput(world, n, args.steps, e2e_s)[0], "unit": "Mpoints/s",
            "h2d_bytes_per_step": int(pin_x.numel() * 4 + pin_c[0].numel()), "d2h_bytes_per_step": int(pin_o[0].numel()),
            "api": "fgbd_run_host (pinned host buffers, two steps in flight), host wall clock",
-           "serial": {"value": world * n * args.steps / serial_s / 1e6,
+           "serial": {"value": job_throughput(world, n, args.steps, serial_s)[0],
                       "how": "copies and run in order on one stream, L2 flushed between steps, CUDA events"}}
 
     # ---- ablations of Tables 4 and 5 (and the same-line reading) on the same frames,
