@@ -272,6 +272,16 @@ fgbd_status fgbd_filter_forward(fgbd_ctx* ctx, const float* rgb_in, int32_t q, d
 fgbd_status fgbd_filter_backward(fgbd_ctx* ctx, const float* grad_out, float* grad_in, double* grad_params,
                                  void* stream);
 
+/* Testing / fault injection: the time in nanoseconds after which every
+ * device-side wait of this context (the grid barriers of the filter and of the
+ * speculative steps, the fused selection's wait for sigma_est) gives up,
+ * latches FGBD_ETIMEOUT and lets its kernel return; 2 s by default.  With 0 a
+ * barrier gives up as soon as it is not already complete, which tests use to
+ * check that a timeout is reported by the next synchronising call and that the
+ * context then works again.  Waits for the context's earlier work first.
+ * Errors: FGBD_EINVAL (ns < 0), FGBD_ECUDA. */
+fgbd_status fgbd_debug_set_wait_limit(fgbd_ctx* ctx, int64_t ns);
+
 /* Wait for the context's work on `stream` (and for the output copies of
  * fgbd_run_host) and return any latched device error (FGBD_ERANGE,
  * FGBD_ETIMEOUT), clearing it. */

@@ -571,6 +571,8 @@ fgbd_status fgbd_ctx_create(int64_t capacity, const fgbd_params* params, fgbd_ct
   ctx->sb.vals[0] = static_cast<uint32_t*>(vals0);
   ctx->sb.vals[1] = static_cast<uint32_t*>(vals1);
   bool ok = cudaMemset(ctx->sc, 0, sizeof(DevScalars)) == cudaSuccess;
+  const unsigned long long limit = kWaitLimitNs;
+  ok = ok && cudaMemcpy(&ctx->sc->wait_limit_ns, &limit, sizeof(limit), cudaMemcpyHostToDevice) == cudaSuccess;
   ok = ok && cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking) == cudaSuccess;
   ok = ok && cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking) == cudaSuccess;
   for (cudaEvent_t* e : {&ctx->ev_fork, &ctx->ev_filter, &ctx->ev_join})
@@ -901,6 +903,16 @@ fgbd_status fgbd_filter_backward(fgbd_ctx* ctx, const float* grad_out, float* gr
     parts = q * grid;
   }
   FGBD_LAUNCH(ctx, "diff_reduce", st, launch_diff_reduce(parts, ctx->d_part, grad_params, st));
+  return FGBD_OK;
+}
+
+fgbd_status fgbd_debug_set_wait_limit(fgbd_ctx* ctx, int64_t ns) {
+  if (!ctx || ns < 0) return FGBD_EINVAL;
+  DeviceGuard g(ctx->device);
+  const unsigned long long v = ns > 0 ? (unsigned long long)ns : 0ull;
+  // the context's work finishes first, so no wait in flight sees the value change
+  FGBD_CUDA(ctx, cudaDeviceSynchronize());
+  FGBD_CUDA(ctx, cudaMemcpy(&ctx->sc->wait_limit_ns, &v, sizeof(v), cudaMemcpyHostToDevice));
   return FGBD_OK;
 }
 

@@ -84,6 +84,8 @@ struct DevScalars {
   int32_t sel_valid;
   // ---- latched errors (never zeroed by a call; cleared when read)
   uint32_t status;
+  // ---- settings (set at context creation)
+  unsigned long long wait_limit_ns;  // any device-side wait gives up after this long
 };
 
 // the regions are zeroed as 32-bit words

@@ -22,10 +22,11 @@ __device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t* p) {
 }
 
 // Barrier over `members` blocks of a cooperative grid: a counter that each
-// block raises once per barrier, waited on for at most kWaitLimitNs; a block
-// that gives up latches kFlagTimeout, and every block then returns false.
+// block raises once per barrier, waited on for at most sc->wait_limit_ns (2 s
+// unless a test lowers it); a block that gives up latches kFlagTimeout, and
+// every block then returns false.
 __device__ __forceinline__ bool grid_barrier(uint32_t* counter, uint32_t* status, uint32_t members, uint32_t& epoch,
-                                             int* s_ok) {
+                                             int* s_ok, const DevScalars* sc) {
   __syncthreads();
   epoch += 1;
   if (threadIdx.x == 0) {
@@ -33,9 +34,10 @@ __device__ __forceinline__ bool grid_barrier(uint32_t* counter, uint32_t* status
     __threadfence();
     atomicAdd(counter, 1u);
     const unsigned long long t0 = global_ns();
+    const unsigned long long limit = sc->wait_limit_ns;
     int ok = 1;
     while (ld_acquire_u32(counter) < target) {
-      if (global_ns() - t0 > kWaitLimitNs) {
+      if (global_ns() - t0 > limit) {
         atomicOr(status, kFlagTimeout);
         ok = 0;
         break;
@@ -173,7 +175,7 @@ __device__ __forceinline__ int speculative_steps(const FilterArgs& a, int depth,
     }
     const bool ask = until_sigma && t < depth;
     if (ask && blockIdx.x == first && threadIdx.x == 0) sc->spec_go[t] = ld_acquire_u32(&sc->sigma_ready) ? 0u : 1u;
-    if (!grid_barrier(&sc->spec_barrier, &sc->status, members, epoch, s_ok)) return -1;
+    if (!grid_barrier(&sc->spec_barrier, &sc->status, members, epoch, s_ok, sc)) return -1;
     if (ask) {
       if (threadIdx.x == 0) *s_go = int(ld_acquire_u32(&sc->spec_go[t]));
       __syncthreads();

@@ -951,9 +951,10 @@ __global__ void __launch_bounds__(kSpecThreads, 1)
   // sigma_est of block 0 (a bounded wait)
   if (threadIdx.x == 0) {
     const unsigned long long t0 = global_ns();
+    const unsigned long long limit = sc->wait_limit_ns;
     int ok = 1;
     while (!ld_acquire_u32(&sc->sigma_ready)) {
-      if (global_ns() - t0 > kWaitLimitNs) {
+      if (global_ns() - t0 > limit) {
         atomicOr(&sc->status, kFlagTimeout);
         ok = 0;
         break;

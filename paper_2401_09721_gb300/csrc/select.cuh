@@ -450,7 +450,7 @@ __device__ __forceinline__ void select_filter(const FilterArgs& a, int S, int fi
       }
     }
   }
-  if (!grid_barrier(bar, &sc->status, members, epoch, &s_ok)) return;
+  if (!grid_barrier(bar, &sc->status, members, epoch, &s_ok, sc)) return;
 
   // J(0..S) from the stored terms, by thread 0 of each block (every block
   // reaches the same values: the sums are exact integers)
@@ -515,7 +515,7 @@ __device__ __forceinline__ void select_filter(const FilterArgs& a, int S, int fi
       if (threadIdx.x == 0 && loc) atomicAdd(&sc->sumsq[t], loc);
     }
     // (the barrier starts with __syncthreads: every thread has read s_ctl[3])
-    if (!grid_barrier(bar, &sc->status, members, epoch, &s_ok)) return;
+    if (!grid_barrier(bar, &sc->status, members, epoch, &s_ok, sc)) return;
     if (select) {
       if (threadIdx.x == 0) {
         const unsigned long long ss = ld_relaxed_u64(&sc->sumsq[t]);

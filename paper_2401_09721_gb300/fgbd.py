@@ -107,6 +107,7 @@ _SIGS = {
     "fgbd_run": (ctypes.c_int, [_P, _P, ctypes.c_int64, _P, ctypes.c_int32, _P, ctypes.c_int32, _P]),
     "fgbd_run_reuse": (ctypes.c_int, [_P, _P, ctypes.c_int64, _P, ctypes.c_int32, _P, ctypes.c_int32, _P]),
     "fgbd_run_host": (ctypes.c_int, [_P, _P, ctypes.c_int64, _P, ctypes.c_int32, _P, ctypes.c_int32, _P]),
+    "fgbd_debug_set_wait_limit": (ctypes.c_int, [_P, ctypes.c_int64]),
     "fgbd_run_batch": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(ctypes.c_int64),
                                       ctypes.POINTER(_P), ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(_P),
                                       ctypes.POINTER(ctypes.c_int32), ctypes.c_int32, _P]),
@@ -461,6 +462,10 @@ class Context:
 
     def sync(self, stream=None):
         fgbd_sync(self.handle, stream)
+
+    def set_wait_limit(self, ns: int):
+        """Testing: the time after which every device-side wait gives up (FGBD_ETIMEOUT)."""
+        _check(lib().fgbd_debug_set_wait_limit(self.handle, int(ns)), "fgbd_debug_set_wait_limit", self.handle)
 
     def run_host(self, xyz, rgb_in, out, stream=None):
         """fgbd_run on host (CPU) tensors; `out` is complete after sync() or two calls later."""

@@ -85,3 +85,4 @@ def test_host_side_checks_without_gpu(so):
     assert lib.fgbd_sync(None, None) == 1
     assert lib.fgbd_status_str(0) == b"FGBD_OK"
     assert lib.fgbd_status_str(5).startswith(b"FGBD_ETIMEOUT")
+    assert lib.fgbd_debug_set_wait_limit(None, 0) == 1
