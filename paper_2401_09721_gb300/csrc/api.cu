@@ -14,6 +14,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/fgbd.h"
 #include "fgbd_internal.cuh"
 
@@ -111,6 +113,12 @@ struct fgbd_ctx {
 };
 
 namespace {
+
+// NVTX range over one API call (header-only NVTX 3: no cost unless a profiler is attached)
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+};
 
 struct DeviceGuard {
   int prev = -1;
@@ -610,12 +618,14 @@ void fgbd_ctx_destroy(fgbd_ctx* ctx) {
 const char* fgbd_last_error(const fgbd_ctx* ctx) { return ctx ? ctx->err.c_str() : ""; }
 
 fgbd_status fgbd_build_graph(fgbd_ctx* ctx, const int32_t* xyz, int64_t n, void* stream) {
+  NvtxRange nvtx_("fgbd_build_graph");
   if (!ctx) return FGBD_EINVAL;
   DeviceGuard g(ctx->device);
   return do_build(ctx, xyz, n, as_stream(stream));
 }
 
 fgbd_status fgbd_estimate_noise(fgbd_ctx* ctx, const void* rgb, int32_t dtype, double* sigma_est, void* stream) {
+  NvtxRange nvtx_("fgbd_estimate_noise");
   if (!ctx) return FGBD_EINVAL;
   DeviceGuard g(ctx->device);
   return do_estimate(ctx, rgb, dtype, sigma_est, as_stream(stream));
@@ -623,6 +633,7 @@ fgbd_status fgbd_estimate_noise(fgbd_ctx* ctx, const void* rgb, int32_t dtype, d
 
 fgbd_status fgbd_select_filter(fgbd_ctx* ctx, const void* rgb, int32_t dtype, const double* sigma_est,
                                int32_t* q_out, void* stream) {
+  NvtxRange nvtx_("fgbd_select_filter");
   if (!ctx) return FGBD_EINVAL;
   DeviceGuard g(ctx->device);
   return do_select(ctx, rgb, dtype, sigma_est, q_out, nullptr, FGBD_F32, as_stream(stream));
@@ -630,6 +641,7 @@ fgbd_status fgbd_select_filter(fgbd_ctx* ctx, const void* rgb, int32_t dtype, co
 
 fgbd_status fgbd_denoise(fgbd_ctx* ctx, const void* rgb_in, int32_t in_dtype, int32_t q, void* rgb_out,
                          int32_t out_dtype, void* stream) {
+  NvtxRange nvtx_("fgbd_denoise");
   if (!ctx) return FGBD_EINVAL;
   DeviceGuard g(ctx->device);
   const cudaStream_t st = as_stream(stream);
@@ -665,6 +677,7 @@ fgbd_status fgbd_denoise(fgbd_ctx* ctx, const void* rgb_in, int32_t in_dtype, in
 
 fgbd_status fgbd_run(fgbd_ctx* ctx, const int32_t* xyz, int64_t n, const void* rgb_in, int32_t in_dtype,
                      void* rgb_out, int32_t out_dtype, void* stream) {
+  NvtxRange nvtx_("fgbd_run");
   if (!ctx) return FGBD_EINVAL;
   if (!dtype_ok(in_dtype) || !dtype_ok(out_dtype)) return FGBD_EINVAL;
   if (n > 0 && (!rgb_in || !rgb_out)) return FGBD_EINVAL;
@@ -699,6 +712,7 @@ fgbd_status fgbd_run(fgbd_ctx* ctx, const int32_t* xyz, int64_t n, const void* r
 
 fgbd_status fgbd_run_host(fgbd_ctx* ctx, const int32_t* xyz, int64_t n, const void* rgb_in, int32_t in_dtype,
                           void* rgb_out, int32_t out_dtype, void* stream) {
+  NvtxRange nvtx_("fgbd_run_host");
   if (!ctx) return FGBD_EINVAL;
   if (!dtype_ok(in_dtype) || !dtype_ok(out_dtype)) return FGBD_EINVAL;
   if (n < 0 || n > ctx->capacity) return FGBD_EINVAL;
@@ -755,6 +769,7 @@ fgbd_status fgbd_run_host(fgbd_ctx* ctx, const int32_t* xyz, int64_t n, const vo
 
 fgbd_status fgbd_run_reuse(fgbd_ctx* ctx, const int32_t* xyz, int64_t n, const void* rgb_in, int32_t in_dtype,
                            void* rgb_out, int32_t out_dtype, void* stream) {
+  NvtxRange nvtx_("fgbd_run_reuse");
   if (!ctx) return FGBD_EINVAL;
   if (!dtype_ok(in_dtype) || !dtype_ok(out_dtype)) return FGBD_EINVAL;
   if (n > 0 && (!rgb_in || !rgb_out)) return FGBD_EINVAL;
@@ -778,6 +793,7 @@ fgbd_status fgbd_run_reuse(fgbd_ctx* ctx, const int32_t* xyz, int64_t n, const v
 fgbd_status fgbd_run_batch(fgbd_ctx* const* ctxs, const int32_t* const* xyz, const int64_t* n,
                            const void* const* rgb_in, const int32_t* in_dtype, void* const* rgb_out,
                            const int32_t* out_dtype, int32_t count, void* stream) {
+  NvtxRange nvtx_("fgbd_run_batch");
   if (count < 0 || count > FGBD_BATCH_MAX) return FGBD_EINVAL;
   if (count == 0) return FGBD_OK;
   if (!ctxs || !xyz || !n || !rgb_in || !in_dtype || !rgb_out || !out_dtype) return FGBD_EINVAL;
@@ -823,6 +839,7 @@ fgbd_status fgbd_run_batch(fgbd_ctx* const* ctxs, const int32_t* const* xyz, con
 
 fgbd_status fgbd_filter_forward(fgbd_ctx* ctx, const float* rgb_in, int32_t q, double alpha, double sigma,
                                 int32_t checkpoint, float* rgb_out, void* stream) {
+  NvtxRange nvtx_("fgbd_filter_forward");
   if (!ctx) return FGBD_EINVAL;
   if (!ctx->has_graph) return FGBD_ESTATE;
   if (q < 0 || q > kQCap || checkpoint < 0) return FGBD_EINVAL;
@@ -862,6 +879,7 @@ fgbd_status fgbd_filter_forward(fgbd_ctx* ctx, const float* rgb_in, int32_t q, d
 
 fgbd_status fgbd_filter_backward(fgbd_ctx* ctx, const float* grad_out, float* grad_in, double* grad_params,
                                  void* stream) {
+  NvtxRange nvtx_("fgbd_filter_backward");
   if (!ctx) return FGBD_EINVAL;
   if (!ctx->d_valid || !ctx->has_graph || ctx->d_gen != ctx->graph_gen) return FGBD_ESTATE;
   const int n = ctx->d_n;
