@@ -234,7 +234,9 @@ fgbd_status fgbd_run_reuse(fgbd_ctx* ctx, const int32_t* xyz, int64_t n, const v
  * Results, stats and errors are per context, exactly as after fgbd_run (the
  * outputs are bit-identical).  The call contains no host synchronisation, so
  * it can be captured into a CUDA graph once the contexts have run a frame (the
- * first launches set kernel attributes).
+ * first launches set kernel attributes).  Like fgbd_run, the second call with
+ * the same contexts and buffers records a CUDA graph of the whole batch (kept
+ * by ctxs[0], up to 4 of them) and later calls launch it.
  * Errors: FGBD_EINVAL (any argument) and FGBD_ENOTIMPL (window != 1), both
  * checked before anything is enqueued; FGBD_ECUDA. */
 #define FGBD_BATCH_MAX 64

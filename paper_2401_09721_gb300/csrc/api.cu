@@ -6,6 +6,7 @@
 // errors are latched in DevScalars::status and surfaced by the synchronising
 // calls.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstddef>
 #include <cstdio>
@@ -22,6 +23,7 @@
 using namespace fgbd;
 
 struct fgbd_ctx {
+  uint64_t uid = 0;  // unique over the process: a destroyed context's id never comes back
   int device = 0;
   int num_sms = 0;
   int filter_per_sm = 1;
@@ -89,6 +91,17 @@ struct fgbd_ctx {
   };
   std::vector<RunGraph> run_graphs;  // most recent last
   std::vector<RunKey> run_seen;      // keys run once directly (the next call captures)
+  // fgbd_run_batch replays (held by the batch's first context): per frame its
+  // context and arguments, and the launches the capture counted for it
+  struct BatchGraph {
+    std::vector<fgbd_ctx*> ctxs;
+    std::vector<uint64_t> uids;  // the contexts' ids: a graph of a destroyed context never matches
+    std::vector<RunKey> keys;
+    std::vector<int64_t> launches;
+    cudaGraphExec_t exec;
+  };
+  std::vector<BatchGraph> batch_graphs;  // most recent last
+  std::vector<std::pair<std::vector<uint64_t>, std::vector<RunKey>>> batch_seen;
   cudaStream_t cap_stream = nullptr;
   bool graphs_on = true;
   // batched runs: this context's own stream and the events that order it
@@ -302,6 +315,8 @@ void release_batch_objects(fgbd_ctx* ctx) {
     }
   for (auto& g : ctx->run_graphs) cudaGraphExecDestroy(g.exec);
   ctx->run_graphs.clear();
+  for (auto& g : ctx->batch_graphs) cudaGraphExecDestroy(g.exec);
+  ctx->batch_graphs.clear();
   for (cudaStream_t* st : {&ctx->side, &ctx->cap_stream})
     if (*st) {
       cudaStreamDestroy(*st);
@@ -474,6 +489,82 @@ fgbd_status capture_run(fgbd_ctx* ctx, const fgbd_ctx::RunKey& k, cudaStream_t s
   return FGBD_OK;
 }
 
+// The batch of fgbd_run_batch, enqueued directly: every frame on its context's
+// own stream, forked from `st` and joined back into it; the selection/filter
+// launches (cooperative, each using the whole GPU) one frame after another.
+fgbd_status direct_batch(const std::vector<fgbd_ctx*>& ctxs, const std::vector<fgbd_ctx::RunKey>& keys,
+                         cudaStream_t st) {
+  const int count = int(ctxs.size());
+  fgbd_ctx* lead = ctxs[0];
+  // fork: every frame's stream starts after the caller's earlier work
+  FGBD_CUDA(lead, cudaEventRecord(lead->ev_fork, st));
+  for (int f = 0; f < count; ++f) FGBD_CUDA(ctxs[f], cudaStreamWaitEvent(ctxs[f]->side, lead->ev_fork, 0));
+  // graph and noise estimate of every frame, concurrently
+  for (int f = 0; f < count; ++f) {
+    fgbd_ctx* c = ctxs[f];
+    const fgbd_ctx::RunKey& k = keys[f];
+    fgbd_status s = do_build(c, static_cast<const int32_t*>(k.xyz), k.n, c->side);
+    if (s == FGBD_OK) s = do_estimate(c, k.rgb_in, k.in_dtype, nullptr, c->side, false);
+    if (s != FGBD_OK) return s;
+  }
+  // selection + filter: cooperative launches, one at a time (frame f waits for
+  // frame f - 1's) so that two of them never compete for residency
+  for (int f = 0; f < count; ++f) {
+    fgbd_ctx* c = ctxs[f];
+    const fgbd_ctx::RunKey& k = keys[f];
+    if (f > 0) FGBD_CUDA(c, cudaStreamWaitEvent(c->side, ctxs[f - 1]->ev_filter, 0));
+    const fgbd_status s = do_select(c, k.rgb_in, k.in_dtype, nullptr, nullptr, k.rgb_out, k.out_dtype, c->side);
+    if (s != FGBD_OK) return s;
+    FGBD_CUDA(c, cudaEventRecord(c->ev_filter, c->side));
+  }
+  // join: the caller's stream continues after every frame
+  for (int f = 0; f < count; ++f) {
+    FGBD_CUDA(ctxs[f], cudaEventRecord(ctxs[f]->ev_join, ctxs[f]->side));
+    FGBD_CUDA(ctxs[f], cudaStreamWaitEvent(st, ctxs[f]->ev_join, 0));
+  }
+  return FGBD_OK;
+}
+
+// Record the batch into a CUDA graph on the first context's capture stream (the
+// frames' own streams join the capture through the fork event), then launch it.
+// If the capture fails the batch runs directly and the first context stops capturing.
+fgbd_status capture_batch(fgbd_ctx* lead, const std::vector<fgbd_ctx*>& ctxs,
+                          const std::vector<fgbd_ctx::RunKey>& keys, cudaStream_t st) {
+  const cudaStream_t cs = lead->cap_stream;
+  std::vector<int64_t> launches0;
+  for (fgbd_ctx* c : ctxs) launches0.push_back(c->launches);
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    cudaGetLastError();
+    lead->graphs_on = false;
+    return direct_batch(ctxs, keys, st);
+  }
+  const fgbd_status s = direct_batch(ctxs, keys, cs);
+  const cudaError_t ce = cudaStreamEndCapture(cs, &graph);
+  bool ok = s == FGBD_OK && ce == cudaSuccess && graph;
+  ok = ok && cudaGraphInstantiate(&exec, graph, 0) == cudaSuccess;
+  if (graph) cudaGraphDestroy(graph);
+  if (!ok) {
+    cudaGetLastError();
+    if (exec) cudaGraphExecDestroy(exec);
+    for (size_t f = 0; f < ctxs.size(); ++f) ctxs[f]->launches = launches0[f];
+    lead->graphs_on = false;
+    if (s != FGBD_OK && s != FGBD_ECUDA) return s;
+    return direct_batch(ctxs, keys, st);
+  }
+  FGBD_CUDA(lead, cudaGraphLaunch(exec, st));
+  if (lead->batch_graphs.size() >= 4) {
+    cudaGraphExecDestroy(lead->batch_graphs.front().exec);
+    lead->batch_graphs.erase(lead->batch_graphs.begin());
+  }
+  fgbd_ctx::BatchGraph bg{ctxs, {}, keys, {}, exec};
+  for (fgbd_ctx* c : ctxs) bg.uids.push_back(c->uid);
+  for (size_t f = 0; f < ctxs.size(); ++f) bg.launches.push_back(ctxs[f]->launches - launches0[f]);
+  lead->batch_graphs.push_back(bg);
+  return FGBD_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -514,6 +605,8 @@ fgbd_status fgbd_ctx_create(int64_t capacity, const fgbd_params* params, fgbd_ct
   if (!params_ok(p)) return FGBD_EINVAL;
   fgbd_ctx* ctx = new (std::nothrow) fgbd_ctx();
   if (!ctx) return FGBD_ENOMEM;
+  static std::atomic<uint64_t> next_uid{1};
+  ctx->uid = next_uid.fetch_add(1);
   ctx->capacity = capacity;
   ctx->params = p;
   if (cudaGetDevice(&ctx->device) != cudaSuccess ||
@@ -810,31 +903,35 @@ fgbd_status fgbd_run_batch(fgbd_ctx* const* ctxs, const int32_t* const* xyz, con
   DeviceGuard g(ctxs[0]->device);
   const cudaStream_t st = as_stream(stream);
   fgbd_ctx* lead = ctxs[0];
-  // fork: every frame's stream starts after the caller's earlier work
-  FGBD_CUDA(lead, cudaEventRecord(lead->ev_fork, st));
-  for (int f = 0; f < count; ++f) FGBD_CUDA(ctxs[f], cudaStreamWaitEvent(ctxs[f]->side, lead->ev_fork, 0));
-  // graph and noise estimate of every frame, concurrently
-  for (int f = 0; f < count; ++f) {
-    fgbd_ctx* c = ctxs[f];
-    fgbd_status s = do_build(c, xyz[f], n[f], c->side);
-    if (s == FGBD_OK) s = do_estimate(c, rgb_in[f], in_dtype[f], nullptr, c->side, false);
-    if (s != FGBD_OK) return s;
+  std::vector<fgbd_ctx*> cv(ctxs, ctxs + count);
+  std::vector<uint64_t> uids;
+  for (int f = 0; f < count; ++f) uids.push_back(ctxs[f]->uid);
+  std::vector<fgbd_ctx::RunKey> keys;
+  for (int f = 0; f < count; ++f) keys.push_back({xyz[f], n[f], rgb_in[f], in_dtype[f], rgb_out[f], out_dtype[f]});
+  bool timing = false;
+  for (int f = 0; f < count; ++f) timing |= ctxs[f]->timing;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cap) != cudaSuccess) {
+    cudaGetLastError();
+    cap = cudaStreamCaptureStatusActive;
   }
-  // selection + filter: cooperative launches, one at a time (frame f waits for
-  // frame f - 1's) so that two of them never compete for residency
-  for (int f = 0; f < count; ++f) {
-    fgbd_ctx* c = ctxs[f];
-    if (f > 0) FGBD_CUDA(c, cudaStreamWaitEvent(c->side, ctxs[f - 1]->ev_filter, 0));
-    const fgbd_status s = do_select(c, rgb_in[f], in_dtype[f], nullptr, nullptr, rgb_out[f], out_dtype[f], c->side);
-    if (s != FGBD_OK) return s;
-    FGBD_CUDA(c, cudaEventRecord(c->ev_filter, c->side));
+  // like fgbd_run: the second call with the same contexts and arguments records a
+  // CUDA graph of the whole batch, later calls launch it
+  if (lead->graphs_on && !timing && cap == cudaStreamCaptureStatusNone) {
+    for (size_t i = 0; i < lead->batch_graphs.size(); ++i) {
+      const fgbd_ctx::BatchGraph& bg = lead->batch_graphs[i];
+      if (bg.uids != uids || bg.ctxs != cv || !(bg.keys == keys)) continue;
+      FGBD_CUDA(lead, cudaGraphLaunch(bg.exec, st));
+      for (int f = 0; f < count; ++f) mark_run_done(ctxs[f], keys[f], bg.launches[f]);
+      return FGBD_OK;
+    }
+    bool seen = false;
+    for (const auto& e : lead->batch_seen) seen |= e.first == uids && e.second == keys;
+    if (seen) return capture_batch(lead, cv, keys, st);
+    lead->batch_seen.push_back({uids, keys});
+    if (lead->batch_seen.size() > 8) lead->batch_seen.erase(lead->batch_seen.begin());
   }
-  // join: the caller's stream continues after every frame
-  for (int f = 0; f < count; ++f) {
-    FGBD_CUDA(ctxs[f], cudaEventRecord(ctxs[f]->ev_join, ctxs[f]->side));
-    FGBD_CUDA(ctxs[f], cudaStreamWaitEvent(st, ctxs[f]->ev_join, 0));
-  }
-  return FGBD_OK;
+  return direct_batch(cv, keys, st);
 }
 
 fgbd_status fgbd_filter_forward(fgbd_ctx* ctx, const float* rgb_in, int32_t q, double alpha, double sigma,

@@ -131,3 +131,35 @@ def test_batch_captured_in_a_cuda_graph(F):
         assert np.array_equal(out.cpu().numpy(), ref_out)
         assert ctx.stats()["q"] == ref_st["q"]
         ctx.close()
+
+
+def test_repeated_batches_replay_their_graph(F):
+    """The second call with the same contexts and buffers records a CUDA graph of
+    the batch and later calls launch it: new contents in the same buffers give
+    the plain results every time; a context destroyed and replaced (its address
+    may come back) never meets a graph recorded for the old one."""
+    frames = _frames()[:3]
+    ctxs = [F.Context(len(x), bits=b) for x, _, b in frames]
+    xs = [_dev(x.astype(np.int32)) for x, _, _ in frames]
+    cs = [_dev(c) for _, c, _ in frames]
+    outs = [torch.empty((len(x), 3), dtype=torch.float32, device="cuda") for x, _, _ in frames]
+    for call in range(4):
+        new = []
+        for k, (xyz, rgb, bits) in enumerate(frames):
+            noisy = (synth.add_noise_u8(rgb, 8.0, 70 + 10 * call + k) if rgb.dtype == np.uint8
+                     else synth.add_noise_f32(rgb, 8.0, 70 + 10 * call + k))
+            cs[k].copy_(_dev(noisy))
+            new.append(noisy)
+        if call == 3:
+            # replace the middle context by a new one of the same shape
+            ctxs[1].close()
+            ctxs[1] = F.Context(len(frames[1][0]), bits=frames[1][2])
+        F.Context.run_batch(ctxs, xs, cs, outs=outs)
+        torch.cuda.synchronize()
+        for ctx, out, (xyz, _, bits), noisy in zip(ctxs, outs, frames, new):
+            ctx.sync()
+            ref_out, ref_st, _ = _plain(F, xyz, noisy, bits)
+            assert np.array_equal(out.cpu().numpy(), ref_out), call
+            assert ctx.stats()["q"] == ref_st["q"]
+    for ctx in ctxs:
+        ctx.close()
