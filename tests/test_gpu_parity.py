@@ -225,6 +225,22 @@ def test_every_bit_width(F, bits):
     full_check(F, xyz, rgb, bits)
 
 
+@pytest.mark.parametrize("sizes", [(4096, 10), (4097, 300), (15000, 15000, 7)])
+def test_large_y_slabs(F, sizes):
+    """Clouds concentrated on a few y planes: y-slabs at, just above and far
+    above the slab sort's shared-memory capacity (4096 points), where it ranks
+    through global memory instead."""
+    rng = np.random.default_rng(sum(sizes))
+    parts = []
+    for i, m in enumerate(sizes):
+        xz = rng.integers(0, 256, size=(m, 2))
+        parts.append(np.stack([xz[:, 0], np.full(m, 5 + 90 * i), xz[:, 1]], axis=1))
+    xyz = np.concatenate(parts).astype(np.int32)
+    xyz = xyz[rng.permutation(len(xyz))]
+    rgb = rng.integers(0, 256, size=(len(xyz), 3)).astype(np.uint8)
+    full_check(F, xyz, rgb, 8)
+
+
 # ------------------------------------------------------------------ degenerate cases
 
 def test_empty_frame(F):
