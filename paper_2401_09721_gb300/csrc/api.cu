@@ -324,8 +324,12 @@ void release_batch_objects(fgbd_ctx* ctx) {
     }
 }
 
-// `zeroed`: the caller has already zeroed the scalar regions this call fills
-fgbd_status do_build(fgbd_ctx* ctx, const int32_t* xyz, int64_t n64, cudaStream_t st, bool zeroed = false) {
+// `zeroed`: the caller has already zeroed the scalar regions this call fills.
+// `rgb_gather` (fgbd_run): the colours of the frame, gathered into sorted order
+// on the context's side stream as soon as the C1 order exists, beside the C2
+// pass and the link step, which do not touch them (do_estimate then joins it).
+fgbd_status do_build(fgbd_ctx* ctx, const int32_t* xyz, int64_t n64, cudaStream_t st, bool zeroed = false,
+                     const void* rgb_gather = nullptr, int32_t gather_dtype = FGBD_U8) {
   if (n64 < 0 || n64 > ctx->capacity) return FGBD_EINVAL;
   if (n64 > 0 && !xyz) return FGBD_EINVAL;
   const int n = int(n64);
@@ -352,6 +356,13 @@ fgbd_status do_build(fgbd_ctx* ctx, const int32_t* xyz, int64_t n64, cudaStream_
       if (p == 0)
         FGBD_LAUNCH(ctx, "slg_slab", st,
                     launch_slab_sort(n, bits, ord_stride(ctx), ctx->sb, ctx->gb, ctx->sc, st));
+      if (p == 1 && rgb_gather) {
+        FGBD_CUDA(ctx, cudaEventRecord(ctx->ev_fork, st));
+        FGBD_CUDA(ctx, cudaStreamWaitEvent(ctx->side, ctx->ev_fork, 0));
+        FGBD_LAUNCH(ctx, "gather_colors", ctx->side,
+                    launch_gather_colors(rgb_gather, gather_dtype, n, ctx->gb.perm1, ctx->y8, ctx->yf, ctx->side));
+        FGBD_CUDA(ctx, cudaEventRecord(ctx->ev_join, ctx->side));
+      }
     }
     const bool same_line = (ctx->params.variant & FGBD_VARIANT_SAME_LINE) != 0;
     FGBD_LAUNCH(ctx, "slg_link", st,
@@ -366,7 +377,7 @@ fgbd_status do_build(fgbd_ctx* ctx, const int32_t* xyz, int64_t n64, cudaStream_
 // colours to fuse_out (what do_select with the estimated sigma would do).
 fgbd_status do_estimate(fgbd_ctx* ctx, const void* rgb, int32_t dtype, double* sigma_out, cudaStream_t st,
                         bool speculate = true, bool fuse = false, void* fuse_out = nullptr,
-                        int32_t fuse_out_dtype = FGBD_U8, bool zeroed = false) {
+                        int32_t fuse_out_dtype = FGBD_U8, bool zeroed = false, bool pregathered = false) {
   if (!ctx->has_graph) return FGBD_ESTATE;
   if (!dtype_ok(dtype)) return FGBD_EINVAL;
   if (ctx->n > 0 && !rgb) return FGBD_EINVAL;
@@ -378,7 +389,11 @@ fgbd_status do_estimate(fgbd_ctx* ctx, const void* rgb, int32_t dtype, double* s
   if (e != cudaSuccess) return cuda_fail(ctx, e, "memset");
   int nblocks = 0;
   if (n > 0) {
-    FGBD_LAUNCH(ctx, "gather_colors", st, launch_gather_colors(rgb, dtype, n, ctx->gb.perm1, ctx->y8, ctx->yf, st));
+    if (pregathered)
+      FGBD_CUDA(ctx, cudaStreamWaitEvent(st, ctx->ev_join, 0));  // the gather do_build started
+    else
+      FGBD_LAUNCH(ctx, "gather_colors", st,
+                  launch_gather_colors(rgb, dtype, n, ctx->gb.perm1, ctx->y8, ctx->yf, st));
     nblocks = ne_moment_blocks(n, ctx->num_sms);
     FGBD_LAUNCH(ctx, "ne_moments", st,
                 launch_ne_moments(n, ctx->params.bits, dtype, ctx->gb, ctx->y8, ctx->yf, ctx->spread, ctx->f64part,
@@ -431,11 +446,11 @@ fgbd_status direct_run(fgbd_ctx* ctx, const fgbd_ctx::RunKey& k, cudaStream_t st
   cudaError_t e = cudaSuccess;
   zero_region(ctx, offsetof(DevScalars, n_edges), offsetof(DevScalars, sel_end_), st, &e);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "memset");
-  fgbd_status s = do_build(ctx, static_cast<const int32_t*>(k.xyz), k.n, st, true);
+  fgbd_status s = do_build(ctx, static_cast<const int32_t*>(k.xyz), k.n, st, true, k.rgb_in, k.in_dtype);
   if (s != FGBD_OK) return s;
   // with FGBD_FLAG_FUSED_SELECT the estimate launch selects and filters too
   const bool fuse = (ctx->params.flags & FGBD_FLAG_FUSED_SELECT) != 0;
-  s = do_estimate(ctx, k.rgb_in, k.in_dtype, nullptr, st, true, fuse, k.rgb_out, k.out_dtype, true);
+  s = do_estimate(ctx, k.rgb_in, k.in_dtype, nullptr, st, true, fuse, k.rgb_out, k.out_dtype, true, k.n > 0);
   if (s != FGBD_OK) return s;
   if (ctx->has_sel) return FGBD_OK;
   return do_select(ctx, k.rgb_in, k.in_dtype, nullptr, nullptr, k.rgb_out, k.out_dtype, st, true);
