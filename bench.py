@@ -600,9 +600,10 @@ def run_fgbd(args):
     # device-timed like the main steps; PSNR of the output against the clean colours
     ablations = {}
     clean_d = torch.from_numpy(clean).to(dev).float()
-    for name, variant in (("as_published", 0), ("no_fslr", fgbd.VARIANT_NO_FSLR),
-                          ("unsorted_patch", fgbd.VARIANT_UNSORTED_PATCH), ("same_line", fgbd.VARIANT_SAME_LINE)):
-        vctx = fgbd.Context(n, bits=BITS, variant=variant)
+    for name, variant, window in (("as_published", 0, 1), ("no_fslr", fgbd.VARIANT_NO_FSLR, 1),
+                                  ("unsorted_patch", fgbd.VARIANT_UNSORTED_PATCH, 1),
+                                  ("same_line", fgbd.VARIANT_SAME_LINE, 1), ("window2", 0, 2), ("window3", 0, 3)):
+        vctx = fgbd.Context(n, bits=BITS, variant=variant, window=window)
         for k in range(2 * len(cols)):  # every frame's graph is captured before the timed runs
             vctx.run(x, cols[k % len(cols)], out=out)
         ms, sig, qv, ps = [], [], [], []
@@ -621,7 +622,8 @@ def run_fgbd(args):
             ps.append(round(10.0 * math.log10(255.0 ** 2 / max(mse, 1e-12)), 3))
         vctx.close()
         ablations[name] = {"ms_per_step": float(np.mean(ms)), "value": n / (float(np.mean(ms)) / 1e3) / 1e6,
-                           "unit": "Mpoints/s", "sigma": list(SIGMAS), "sigma_est": [round(v, 4) for v in sig],
+                           "unit": "Mpoints/s", "window": window, "sigma": list(SIGMAS),
+                           "sigma_est": [round(v, 4) for v in sig],
                            "q": qv, "psnr_db": ps}
 
     batched = None

@@ -34,8 +34,10 @@
 extern "C" {
 #endif
 
-#define FGBD_ABI_VERSION 1
-#define FGBD_PATCH_DIM 21   /* D = 3 colour channels x (1 point + 6 neighbours), Section 2.3 */
+#define FGBD_ABI_VERSION 2
+#define FGBD_PATCH_DIM 21   /* D = 3 colour channels x (1 point + 6 neighbours), Section 2.3, window 1 */
+#define FGBD_MAX_WINDOW 3   /* largest window implemented */
+#define FGBD_PATCH_DIM_MAX 57  /* D = 3 (6 w + 1) at window FGBD_MAX_WINDOW */
 #define FGBD_Q_CAP 256      /* largest accepted q_max */
 
 typedef enum fgbd_status {
@@ -53,7 +55,7 @@ typedef enum fgbd_dtype { FGBD_U8 = 0, FGBD_F32 = 1 } fgbd_dtype;
 
 typedef struct fgbd_params {
   int32_t bits;         /* b, coordinate bits (Section 2.2); 1..10 so a code fits 32 bits */
-  int32_t window;       /* points linked on each side along a scan line; the paper uses 1 (only 1 is implemented) */
+  int32_t window;       /* w: points linked on each side along a scan line, 1..FGBD_MAX_WINDOW (paper: 1) */
   double fslr_factor;   /* FSLR skips points whose mean patch std exceeds factor * sigma_est (paper: 2) */
   int32_t q_max;        /* largest filter power searched, 0..FGBD_Q_CAP (the paper states none; default 64) */
   int32_t variant;      /* OR of FGBD_VARIANT_* ablation switches; 0 is the method as published */
@@ -90,8 +92,9 @@ typedef struct fgbd_stats {
   int64_t n;                                /* points of the last graph */
   int64_t n_edges;                          /* distinct undirected SLG edges */
   double sigma_g;                           /* mean edge length, Eq. 4's bandwidth */
-  int64_t n_patches;                        /* points with exactly 6 neighbours (Section 2.3) */
-  double eigenvalues[FGBD_PATCH_DIM];       /* of the patch covariance, descending */
+  int64_t n_patches;                        /* points with exactly 6 w neighbours (Section 2.3) */
+  int32_t patch_dim;                        /* D = 3 (6 w + 1): valid entries of eigenvalues[] */
+  double eigenvalues[FGBD_PATCH_DIM_MAX];   /* of the patch covariance, descending */
   int32_t m;                                /* leading eigenvalues dropped by the tail rule */
   int32_t q;                                /* selected (or last applied) filter power */
   double tau;                               /* mean of the noise eigenvalues */
@@ -118,8 +121,11 @@ fgbd_status fgbd_params_default(fgbd_params* p);
 /* Create a context on the current CUDA device for frames of up to `capacity`
  * points (1 <= capacity < 2^30) and allocate all its device memory (about
  * 180 bytes per point).  `params` may be NULL for the defaults.  On success
- * *out owns the context; release it with fgbd_ctx_destroy.
- * Errors: FGBD_EINVAL (bad capacity or parameters), FGBD_ENOMEM, FGBD_ECUDA. */
+ * *out owns the context; release it with fgbd_ctx_destroy.  A window w > 1
+ * adds 24 (w - 1) bytes per point and a few MB of noise-estimate scratch.
+ * Errors: FGBD_EINVAL (bad capacity or parameters), FGBD_ENOTIMPL (window
+ * above FGBD_MAX_WINDOW, or FGBD_VARIANT_UNSORTED_PATCH with window > 1),
+ * FGBD_ENOMEM, FGBD_ECUDA. */
 fgbd_status fgbd_ctx_create(int64_t capacity, const fgbd_params* params, fgbd_ctx** out);
 
 /* Free a context and its device memory (waits for its work to finish). NULL is ignored. */
@@ -130,7 +136,8 @@ const char* fgbd_last_error(const fgbd_ctx* ctx);
 
 /* Section 2.2, Eq. 1-4: scan-line graph of n points.  Computes the three
  * raster codes, radix-sorts the points along each (ties by input index),
- * links consecutive points of each order, merges the three link sets into
+ * links consecutive points of each order (with window w, each point to the w
+ * before and the w after it), merges the three link sets into
  * one symmetric graph (a pair linked twice is one edge) and sigma_g, the mean
  * edge length used by the Gaussian weights of Eq. 4.
  *   xyz: int32 [n][3] device, each coordinate in [0, 2^bits).
@@ -140,8 +147,9 @@ const char* fgbd_last_error(const fgbd_ctx* ctx);
 fgbd_status fgbd_build_graph(fgbd_ctx* ctx, const int32_t* xyz, int64_t n, void* stream);
 
 /* Section 2.3 (NE-GBP): noise level of colours on the graph of the last build.
- * Patches of the points with exactly 6 neighbours (the point then its
- * neighbours by increasing distance), their covariance, its eigenvalues, and
+ * Patches of the points with exactly 6 w neighbours (the point then its
+ * neighbours by increasing distance; D = 3 (6 w + 1) entries), their
+ * covariance, its eigenvalues, and
  * sigma_est = sqrt(tau) with tau the mean of the eigenvalues left by the tail
  * rule.  Also computes each point's patch colour spread for FSLR.
  *   rgb:        colours [n][3] device, dtype FGBD_U8 or FGBD_F32.
@@ -259,7 +267,8 @@ fgbd_status fgbd_run_batch(fgbd_ctx* const* ctxs, const int32_t* const* xyz, con
  *               allocated on the first call that needs more (that call
  *               synchronises the device).
  * The call records q, alpha, sigma for fgbd_filter_backward.
- * Errors: FGBD_EINVAL, FGBD_ESTATE (no graph), FGBD_ENOMEM, FGBD_ECUDA. */
+ * Errors: FGBD_EINVAL, FGBD_ESTATE (no graph), FGBD_ENOTIMPL (window != 1),
+ * FGBD_ENOMEM, FGBD_ECUDA. */
 fgbd_status fgbd_filter_forward(fgbd_ctx* ctx, const float* rgb_in, int32_t q, double alpha, double sigma,
                                 int32_t checkpoint, float* rgb_out, void* stream);
 

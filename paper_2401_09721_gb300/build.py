@@ -17,9 +17,10 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 OUT = os.path.join(PKG, "libfgbd.so")
 OBJDIR = os.path.join(PKG, "_build")
-SOURCES = ["slg.cu", "ne.cu", "filter.cu", "diff.cu", "api.cu", "static_orders.cu"]
-HEADERS = [os.path.join(CSRC, "fgbd_internal.cuh"), os.path.join(CSRC, "filter_step.cuh"), os.path.join(ROOT, "include", "fgbd.h"),
-           os.path.join(CSRC, "fgbd.map")]
+SOURCES = ["slg.cu", "ne.cu", "ne_wide.cu", "filter.cu", "diff.cu", "api.cu", "static_orders.cu"]
+# every header of csrc (sorted, so the digest does not depend on directory order)
+HEADERS = [os.path.join(CSRC, f) for f in sorted(os.listdir(CSRC)) if f.endswith(".cuh")] + [
+    os.path.join(ROOT, "include", "fgbd.h"), os.path.join(CSRC, "fgbd.map")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "-Xptxas", "-warn-spills"]

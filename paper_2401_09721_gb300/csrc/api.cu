@@ -41,6 +41,7 @@ struct fgbd_ctx {
   float4* x1 = nullptr;
   double* f64part = nullptr;
   int f64_blocks = 0;
+  WideNe wne{};  // noise-estimate scratch of windows w > 1 (unused at window 1)
   int64_t* scan_tmp = nullptr;
   // state of the frame held in the context
   int n = 0;
@@ -252,6 +253,9 @@ FilterArgs filter_args(fgbd_ctx* ctx, int mode, int q_fixed, const double* sigma
   a.spec_z = ctx->spec_z;
   a.cap = int(align_up(size_t(ctx->capacity), 64));  // row stride of spec_x / spec_z
   a.keep8 = ctx->keep8;
+  a.cx = ctx->gb.cx;
+  a.nx = ctx->gb.nx;
+  a.cx_stride = ctx->gb.cx_stride;
   return a;
 }
 
@@ -365,8 +369,13 @@ fgbd_status do_build(fgbd_ctx* ctx, const int32_t* xyz, int64_t n64, cudaStream_
       }
     }
     const bool same_line = (ctx->params.variant & FGBD_VARIANT_SAME_LINE) != 0;
-    FGBD_LAUNCH(ctx, "slg_link", st,
-                launch_link(n, bits, ord_stride(ctx), same_line, ctx->gb, ctx->sb, ctx->sc, ctx->num_sms, st));
+    if (ctx->params.window == 1)
+      FGBD_LAUNCH(ctx, "slg_link", st,
+                  launch_link(n, bits, ord_stride(ctx), same_line, ctx->gb, ctx->sb, ctx->sc, ctx->num_sms, st));
+    else
+      FGBD_LAUNCH(ctx, "slg_link", st,
+                  launch_link_wide(n, bits, ord_stride(ctx), ctx->params.window, same_line, ctx->gb, ctx->sb,
+                                   ctx->sc, ctx->num_sms, st));
     if (same_line) ctx->launches += 1;  // and k_c1_line_flags
   }
   ctx->has_graph = true;
@@ -381,12 +390,31 @@ fgbd_status do_estimate(fgbd_ctx* ctx, const void* rgb, int32_t dtype, double* s
   if (!ctx->has_graph) return FGBD_ESTATE;
   if (!dtype_ok(dtype)) return FGBD_EINVAL;
   if (ctx->n > 0 && !rgb) return FGBD_EINVAL;
-  if (ctx->params.window != 1) return FGBD_ENOTIMPL;
   const int n = ctx->n;
   ctx->has_noise = ctx->has_sel = false;
   cudaError_t e = cudaSuccess;
   if (!zeroed) zero_region(ctx, offsetof(DevScalars, n_patches), offsetof(DevScalars, ne_end_), st, &e);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "memset");
+  if (ctx->params.window > 1) {
+    // wider windows: moments, their reduction, the Jacobi block, the Rayleigh
+    // quotients with the tail rule; no filter steps are taken beside them
+    if (n > 0) {
+      if (pregathered)
+        FGBD_CUDA(ctx, cudaStreamWaitEvent(st, ctx->ev_join, 0));
+      else
+        FGBD_LAUNCH(ctx, "gather_colors", st,
+                    launch_gather_colors(rgb, dtype, n, ctx->gb.perm1, ctx->y8, ctx->yf, st));
+    }
+    FGBD_LAUNCH(ctx, "ne_wide", st,
+                launch_ne_wide(n, ctx->params.bits, ctx->params.window, dtype, ctx->gb, ctx->y8, ctx->yf,
+                               ctx->spread, ctx->wne, ctx->sc, sigma_out, ctx->num_sms, st));
+    ctx->launches += n > 0 ? 3 : 2;  // the one counted above and the others of the estimate
+    ctx->spec_depth = 0;
+    ctx->has_noise = true;
+    ctx->noise_rgb = rgb;
+    ctx->noise_dtype = dtype;
+    return FGBD_OK;
+  }
   int nblocks = 0;
   if (n > 0) {
     if (pregathered)
@@ -449,7 +477,7 @@ fgbd_status direct_run(fgbd_ctx* ctx, const fgbd_ctx::RunKey& k, cudaStream_t st
   fgbd_status s = do_build(ctx, static_cast<const int32_t*>(k.xyz), k.n, st, true, k.rgb_in, k.in_dtype);
   if (s != FGBD_OK) return s;
   // with FGBD_FLAG_FUSED_SELECT the estimate launch selects and filters too
-  const bool fuse = (ctx->params.flags & FGBD_FLAG_FUSED_SELECT) != 0;
+  const bool fuse = (ctx->params.flags & FGBD_FLAG_FUSED_SELECT) != 0 && ctx->params.window == 1;
   s = do_estimate(ctx, k.rgb_in, k.in_dtype, nullptr, st, true, fuse, k.rgb_out, k.out_dtype, true, k.n > 0);
   if (s != FGBD_OK) return s;
   if (ctx->has_sel) return FGBD_OK;
@@ -618,6 +646,9 @@ fgbd_status fgbd_ctx_create(int64_t capacity, const fgbd_params* params, fgbd_ct
   if (params) p = *params;
   else fgbd_params_default(&p);
   if (!params_ok(p)) return FGBD_EINVAL;
+  // windows 2..3 are built; the unsorted-patch ablation is defined for window 1 only
+  if (p.window > kMaxWindow) return FGBD_ENOTIMPL;
+  if (p.window > 1 && (p.variant & FGBD_VARIANT_UNSORTED_PATCH)) return FGBD_ENOTIMPL;
   fgbd_ctx* ctx = new (std::nothrow) fgbd_ctx();
   if (!ctx) return FGBD_ENOMEM;
   static std::atomic<uint64_t> next_uid{1};
@@ -629,12 +660,18 @@ fgbd_status fgbd_ctx_create(int64_t capacity, const fgbd_params* params, fgbd_ct
     delete ctx;
     return FGBD_ECUDA;
   }
-  ctx->filter_per_sm = std::max(1, filter_grid(1 << 30, ctx->num_sms) / ctx->num_sms);
+  const int nx = extra_slots(p.window);
+  ctx->filter_per_sm = std::max(1, filter_grid(1 << 30, ctx->num_sms, nx) / ctx->num_sms);
 
   const size_t C = size_t(capacity);
   const int tiles = int((C + kSortTile - 1) / kSortTile);
   ctx->f64_blocks = ne_moment_blocks(int(C), ctx->num_sms);
   const size_t kP = size_t(kD) * kD + kD + 1;
+  // wider windows: the further neighbour slots and the noise-estimate scratch
+  const bool wide = p.window > 1;
+  const size_t wD = size_t(3 * (6 * p.window + 1));
+  const int w_blocks = ne_wide_blocks(int(C), ctx->num_sms);
+  const size_t wP = ne_wide_part_entries(p.window);
   struct Item {
     void** ptr;
     size_t bytes;
@@ -666,6 +703,13 @@ fgbd_status fgbd_ctx_create(int64_t capacity, const fgbd_params* params, fgbd_ct
       {reinterpret_cast<void**>(&ctx->x1), C * 16},
       {reinterpret_cast<void**>(&ctx->f64part), size_t(ctx->f64_blocks) * kP * 8},
       {reinterpret_cast<void**>(&ctx->scan_tmp), ((C + 1 + 1023) / 1024 + 1) * 8},
+      {reinterpret_cast<void**>(&ctx->gb.cx), size_t(nx) * align_up(C, 64) * 4},
+      {reinterpret_cast<void**>(&ctx->wne.part), wide ? size_t(w_blocks) * wP * 8 : 0},
+      {reinterpret_cast<void**>(&ctx->wne.tot), wide ? wP * 8 : 0},
+      {reinterpret_cast<void**>(&ctx->wne.S), wide ? wD * wD * 8 : 0},
+      {reinterpret_cast<void**>(&ctx->wne.V), wide ? wD * wD * 4 : 0},
+      {reinterpret_cast<void**>(&ctx->wne.lam), wide ? wD * 8 : 0},
+      {reinterpret_cast<void**>(&ctx->wne.done), wide ? 4 : 0},
   };
   size_t total = 0;
   for (const Item& it : items) total = align_up(total, 256) + it.bytes;
@@ -686,7 +730,15 @@ fgbd_status fgbd_ctx_create(int64_t capacity, const fgbd_params* params, fgbd_ct
   ctx->sb.keys[1] = static_cast<uint32_t*>(keys1);
   ctx->sb.vals[0] = static_cast<uint32_t*>(vals0);
   ctx->sb.vals[1] = static_cast<uint32_t*>(vals1);
+  ctx->gb.nx = nx;
+  ctx->gb.cx_stride = int(align_up(C, 64));
+  if (!wide) {
+    ctx->gb.cx = nullptr;
+    ctx->wne = WideNe{};
+  }
+  ctx->wne.blocks = wide ? w_blocks : 0;
   bool ok = cudaMemset(ctx->sc, 0, sizeof(DevScalars)) == cudaSuccess;
+  if (wide) ok = ok && cudaMemset(ctx->wne.done, 0, 4) == cudaSuccess;
   const unsigned long long limit = kWaitLimitNs;
   ok = ok && cudaMemcpy(&ctx->sc->wait_limit_ns, &limit, sizeof(limit), cudaMemcpyHostToDevice) == cudaSuccess;
   ok = ok && cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking) == cudaSuccess;
@@ -953,6 +1005,7 @@ fgbd_status fgbd_filter_forward(fgbd_ctx* ctx, const float* rgb_in, int32_t q, d
                                 int32_t checkpoint, float* rgb_out, void* stream) {
   NvtxRange nvtx_("fgbd_filter_forward");
   if (!ctx) return FGBD_EINVAL;
+  if (ctx->params.window != 1) return FGBD_ENOTIMPL;  // the adjoint rows hold six neighbours
   if (!ctx->has_graph) return FGBD_ESTATE;
   if (q < 0 || q > kQCap || checkpoint < 0) return FGBD_EINVAL;
   if (!std::isfinite(alpha) || !std::isfinite(sigma) || sigma < 0.0) return FGBD_EINVAL;
@@ -1069,7 +1122,8 @@ fgbd_status fgbd_get_stats(fgbd_ctx* ctx, fgbd_stats* out, void* stream) {
   }
   if (ctx->has_noise) {
     out->n_patches = int64_t(h.n_patches);
-    for (int i = 0; i < kD; ++i) out->eigenvalues[i] = h.eig[i];
+    out->patch_dim = 3 * (6 * ctx->params.window + 1);
+    for (int i = 0; i < out->patch_dim; ++i) out->eigenvalues[i] = h.eig[i];
     out->m = h.m;
     out->tau = h.tau;
     out->sigma_est = h.sigma_est;

@@ -7,7 +7,9 @@
 // of point k doubles as its coordinates.  Neighbours along C2 and C3
 // (Eq. 2-3) are stored explicitly, four slots per point, with -1 marking an
 // empty slot (the end of a scan order, or a pair already linked by an earlier
-// code, so that the union graph of Section 2.2 is a set).
+// code, so that the union graph of Section 2.2 is a set).  With a window
+// w > 1 the points d = 2..w positions away along each code are stored in
+// 6 (w - 1) further slots per point (GraphBufs::cx).
 #pragma once
 
 #include <cstddef>
@@ -24,6 +26,8 @@ constexpr int kSortTile = kSortThreads * kSortKpt;  // 4096 keys per tile
 constexpr int kSlgPasses = 3;                      // y-slabs (then the slab sort: C3), C1, C2
 constexpr int kK = 6;                              // neighbours per point at window 1
 constexpr int kD = 3 * (kK + 1);                   // patch dimension (Section 2.3)
+constexpr int kMaxWindow = 3;                      // windows 1..3: K = 6w neighbours per point
+constexpr int kDMax = 3 * (6 * kMaxWindow + 1);    // largest patch dimension (57)
 constexpr int kQCap = 256;                         // largest q_max accepted
 constexpr int kSqShift = 8;                        // fixed point of squared colours (2^-8)
 constexpr int kDistShift = 20;                     // fixed point of edge lengths
@@ -62,7 +66,7 @@ struct DevScalars {
   uint32_t spec_go[kSpecMax + 1];  // after stored step t: 1 to take another before selecting
   uint32_t ne_end_;
   // ---- results of the noise estimate
-  double eig[kD];               // descending
+  double eig[kDMax];            // descending (the first D = 3 (6w + 1) are used)
   double tau;
   double sigma_est;
   int32_t m;
@@ -113,7 +117,16 @@ struct GraphBufs {
   int32_t* ord23;    // [2][cap] sorted ids along C2, then along C3
   int32_t* rank2;    // [cap] position of each sorted id in the C2 order
   int4* c4;          // [cap] C2 prev, C2 next, C3 prev, C3 next (sorted ids, -1 empty)
+  // windows w > 1: [6 (w - 1)][cap stride] the points d = 2..w positions away;
+  // slot 6 (d - 2) + 2 l + s holds code l's point d before (s = 0) / after (s = 1)
+  // the point (sorted ids, -1 empty or linked by an earlier code)
+  int32_t* cx;
+  int nx;            // 6 (w - 1)
+  int cx_stride;     // row stride of cx, a multiple of 64
 };
+
+// number of further neighbour slots at window w
+__host__ __device__ constexpr int extra_slots(int w) { return 6 * (w - 1); }
 
 // One stable radix pass whose digit is one coordinate field of the key.
 struct SortPassArgs {
@@ -152,6 +165,10 @@ cudaError_t launch_sort_pass(const SortPassArgs& a, cudaStream_t stream);  // th
 cudaError_t launch_orders_export(int n, int cap, const GraphBufs& gb, int32_t* out, cudaStream_t stream);
 cudaError_t launch_link(int n, int bits, int cap, bool same_line, const GraphBufs& gb, const SortBufs& sb,
                         DevScalars* sc, int num_sms, cudaStream_t stream);
+// windows w > 1: every link of the window (C2/C3 d = 1 into c4, d >= 2 into cx)
+// and the edge sums; then k_c1_line_flags under the same-line variant
+cudaError_t launch_link_wide(int n, int bits, int cap, int window, bool same_line, const GraphBufs& gb,
+                             const SortBufs& sb, DevScalars* sc, int num_sms, cudaStream_t stream);
 
 cudaError_t launch_gather_colors(const void* rgb, int dtype, int n, const int32_t* perm1,
                                  uint32_t* y8, float4* yf, cudaStream_t stream);
@@ -165,6 +182,24 @@ cudaError_t launch_ne_finalize(int dtype, const double* f64_partials, int nblock
                                DevScalars* sc, double* sigma_out, const FilterArgs* spec, int num_sms,
                                cudaStream_t stream);
 int ne_moment_blocks(int n, int num_sms);
+
+// Noise estimate at windows w > 1 (patch dimension D = 3 (6w + 1)): per-block
+// moment partials, their reduction, the one-block float32 Jacobi, and float64
+// Rayleigh quotients with the tail rule.
+struct WideNe {
+  double* part;   // [blocks][D*D + D + 1] per-block moments (int64 bit patterns for uint8 colours)
+  double* tot;    // [D*D + D + 1] the totals: sum a a^T (upper triangle), sum a, patch count
+  double* S;      // [D][D] the covariance
+  float* V;       // [D][D] its eigenvector estimates (columns)
+  double* lam;    // [D] Rayleigh quotients
+  uint32_t* done; // blocks of the Rayleigh launch finished (reset by the last)
+  int blocks;     // moment blocks (the rows of part)
+};
+int ne_wide_blocks(int n, int num_sms);
+size_t ne_wide_part_entries(int window);  // D*D + D + 1
+cudaError_t launch_ne_wide(int n, int bits, int window, int dtype, const GraphBufs& gb, const uint32_t* y8,
+                           const float4* yf, float* spread, const WideNe& w, DevScalars* sc, double* sigma_out,
+                           int num_sms, cudaStream_t stream);
 
 struct FilterArgs {
   int n;
@@ -195,9 +230,13 @@ struct FilterArgs {
   int cap;                 // row stride of spec_x / spec_z, a multiple of 64
   int fuse;                // noise-estimate launch: select and filter too, once sigma_est is known
   uint8_t* keep8;          // select mode: the FSLR keep flag of every sorted point
+  // windows w > 1: the further neighbour slots (GraphBufs::cx), nx = 6 (w - 1)
+  const int32_t* cx;
+  int nx;
+  int cx_stride;
 };
 cudaError_t launch_filter(const FilterArgs& a, int grid, cudaStream_t stream);
-int filter_grid(int n, int num_sms);
+int filter_grid(int n, int num_sms, int nx = 0);
 cudaError_t launch_output(const FilterArgs& a, cudaStream_t stream);  // the kept iterate, in input order
 
 // Differentiable filter: rows of R = D^-1 W for given alpha, sigma, and their transpose
@@ -254,6 +293,25 @@ __device__ __forceinline__ void decode_c1(uint32_t c, int b, int& x, int& y, int
 // whether sorted point k is linked to k - 1 / k + 1 (C1 neighbours), from its packed-code word
 __device__ __forceinline__ bool c1_prev_linked(uint32_t pkw, int k) { return k > 0 && !(pkw & kNoPrevLink); }
 __device__ __forceinline__ bool c1_next_linked(uint32_t pkw, int k, int n) { return k + 1 < n && !(pkw & kNoNextLink); }
+
+// Neighbour j (0 .. 5 + nx) of sorted point k in link order: 0 / 1 the C1
+// points k - 1 / k + 1 (pkw: k's packed-code word with the missing-link
+// bits), 2..5 the c4 slots s, then the further slots of a window w > 1.
+// Returns its sorted id, or -1 for an empty slot.
+__device__ __forceinline__ int neighbour_of(int j, int k, int n, uint32_t pkw, int4 s, const int32_t* __restrict__ cx,
+                                            int cx_stride) {
+  int v;
+  switch (j) {
+    case 0: return c1_prev_linked(pkw, k) ? k - 1 : -1;
+    case 1: return c1_next_linked(pkw, k, n) ? k + 1 : -1;
+    case 2: v = s.x; break;
+    case 3: v = s.y; break;
+    case 4: v = s.z; break;
+    case 5: v = s.w; break;
+    default: v = cx[size_t(j - 6) * size_t(cx_stride) + k]; break;
+  }
+  return in_range(v, n) ? v : -1;
+}
 
 __device__ __forceinline__ int sq_dist_c1(uint32_t a, uint32_t c, int b) {
   int ax, ay, az, cx, cy, cz;

@@ -9,6 +9,8 @@
 namespace fgbd {
 namespace {
 
+// NX further neighbour slots per point: 0 at window 1, 6 (w - 1) at window w
+template <int NX>
 __global__ void __launch_bounds__(kFilterThreads, 2) k_filter(FilterArgs a) {
   pdl_wait();
   // the stored steps count only if the noise-estimate launch finished them
@@ -19,7 +21,7 @@ __global__ void __launch_bounds__(kFilterThreads, 2) k_filter(FilterArgs a) {
   }
   __syncthreads();
   uint32_t epoch = 0;
-  select_filter<kFilterThreads>(a, s_S, 0, gridDim.x, &a.sc->barrier, epoch);
+  select_filter<kFilterThreads, NX>(a, s_S, 0, gridDim.x, &a.sc->barrier, epoch);
 }
 
 __global__ void __launch_bounds__(256) k_output(FilterArgs a) {
@@ -29,52 +31,49 @@ __global__ void __launch_bounds__(256) k_output(FilterArgs a) {
 
 // ---------------------------------------------------------------- export
 
-__device__ __forceinline__ int gather_row(int k, int n, const uint32_t* pk, const int4* c4, int nb[6]) {
+constexpr int kMaxDegree = 6 * kMaxWindow;
+
+__device__ __forceinline__ int gather_row(int k, int n, const GraphBufs& gb, int nb[kMaxDegree]) {
   int cnt = 0;
   if (!in_range(k, n)) return 0;
-  const uint32_t pkk = pk[k];
-  if (c1_prev_linked(pkk, k)) nb[cnt++] = k - 1;
-  if (c1_next_linked(pkk, k, n)) nb[cnt++] = k + 1;
-  const int4 s = c4[k];
-  if (in_range(s.x, n)) nb[cnt++] = s.x;
-  if (in_range(s.y, n)) nb[cnt++] = s.y;
-  if (in_range(s.z, n)) nb[cnt++] = s.z;
-  if (in_range(s.w, n)) nb[cnt++] = s.w;
+  const uint32_t pkk = gb.pk[k];
+  const int4 s = gb.c4[k];
+  const int slots = 6 + gb.nx;
+  for (int j = 0; j < slots && j < kMaxDegree; ++j) {
+    const int o = neighbour_of(j, k, n, pkk, s, gb.cx, gb.cx_stride);
+    if (o >= 0) nb[cnt++] = o;
+  }
   return cnt;
 }
 
-__global__ void k_csr_degree(int n, const int32_t* __restrict__ rank1, const uint32_t* __restrict__ pk,
-                             const int4* __restrict__ c4,
-                             int64_t* __restrict__ deg) {
+__global__ void k_csr_degree(int n, GraphBufs gb, int64_t* __restrict__ deg) {
   pdl_wait();
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i <= n; i += gridDim.x * blockDim.x) {
     if (i == n) {
       deg[i] = 0;
       continue;
     }
-    int nb[6];
-    deg[i] = gather_row(rank1[i], n, pk, c4, nb);
+    int nb[kMaxDegree];
+    deg[i] = gather_row(gb.rank1[i], n, gb, nb);
   }
 }
 
-__global__ void k_csr_fill(int n, int bits, const int32_t* __restrict__ rank1,
-                           const int32_t* __restrict__ perm1, const uint32_t* __restrict__ pk,
-                           const int4* __restrict__ c4, const int64_t* __restrict__ row_ptr,
+__global__ void k_csr_fill(int n, int bits, GraphBufs gb, const int64_t* __restrict__ row_ptr,
                            int32_t* __restrict__ col, float* __restrict__ w, int64_t col_capacity,
                            const DevScalars* __restrict__ sc) {
   pdl_wait();
   const double sg = sigma_g_of(sc);
   const float inv2 = sg > 0.0 ? float(1.0 / (sg * sg)) : 0.f;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    const int k = rank1[i];
-    int nb[6];
-    const int cnt = gather_row(k, n, pk, c4, nb);
+    const int k = gb.rank1[i];
+    int nb[kMaxDegree];
+    const int cnt = gather_row(k, n, gb, nb);
     if (cnt == 0) continue;
-    int orig[6];
-    float wv[6];
+    int orig[kMaxDegree];
+    float wv[kMaxDegree];
     for (int j = 0; j < cnt; ++j) {
-      orig[j] = perm1[nb[j]];
-      wv[j] = expf(-float(sq_dist_c1(pk[k], pk[nb[j]], bits)) * inv2);
+      orig[j] = gb.perm1[nb[j]];
+      wv[j] = expf(-float(sq_dist_c1(gb.pk[k], gb.pk[nb[j]], bits)) * inv2);
     }
     for (int a = 1; a < cnt; ++a) {  // insertion sort by input index
       const int o = orig[a];
@@ -149,17 +148,24 @@ __global__ void k_spread_export(int n, const int32_t* __restrict__ rank1, const 
 
 }  // namespace
 
-int filter_grid(int n, int num_sms) {
+int filter_grid(int n, int num_sms, int nx) {
   int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_filter, kFilterThreads, 0) != cudaSuccess ||
-      per_sm < 1)
-    per_sm = 1;
+  cudaError_t e;
+  if (nx == extra_slots(3)) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_filter<extra_slots(3)>, kFilterThreads, 0);
+  else if (nx == extra_slots(2)) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_filter<extra_slots(2)>, kFilterThreads, 0);
+  else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_filter<0>, kFilterThreads, 0);
+  if (e != cudaSuccess || per_sm < 1) per_sm = 1;
   const int need = std::max(1, (n + kFilterThreads - 1) / kFilterThreads);
   return std::max(1, std::min(need, per_sm * num_sms));
 }
 
 cudaError_t launch_filter(const FilterArgs& a, int grid, cudaStream_t stream) {
-  return launch_kernel(k_filter, dim3(grid), dim3(kFilterThreads), 0, stream, true, a);
+  if (a.nx == extra_slots(2))
+    return launch_kernel(k_filter<extra_slots(2)>, dim3(grid), dim3(kFilterThreads), 0, stream, true, a);
+  if (a.nx == extra_slots(3))
+    return launch_kernel(k_filter<extra_slots(3)>, dim3(grid), dim3(kFilterThreads), 0, stream, true, a);
+  if (a.nx != 0) return cudaErrorInvalidValue;
+  return launch_kernel(k_filter<0>, dim3(grid), dim3(kFilterThreads), 0, stream, true, a);
 }
 
 cudaError_t launch_output(const FilterArgs& a, cudaStream_t stream) {
@@ -170,8 +176,7 @@ cudaError_t launch_output(const FilterArgs& a, cudaStream_t stream) {
 
 cudaError_t launch_csr_degree(int n, const GraphBufs& gb, int64_t* deg_out, cudaStream_t stream) {
   const int grid = std::max(1, std::min((n + 256) / 256, 152 * 16));
-  return launch_kernel(k_csr_degree, dim3(grid), dim3(256), 0, stream, false, n, gb.rank1, gb.pk, gb.c4,
-                       deg_out);
+  return launch_kernel(k_csr_degree, dim3(grid), dim3(256), 0, stream, false, n, gb, deg_out);
 }
 
 cudaError_t launch_scan_i64(int64_t* data, int64_t count, int64_t* block_tmp, cudaStream_t stream) {
@@ -193,8 +198,8 @@ cudaError_t launch_csr_fill(int n, int bits, const GraphBufs& gb, const int64_t*
                             float* w, int64_t col_capacity, const DevScalars* sc, cudaStream_t stream) {
   if (n <= 0) return cudaSuccess;
   const int grid = std::min((n + 255) / 256, 152 * 16);
-  return launch_kernel(k_csr_fill, dim3(grid), dim3(256), 0, stream, false, n, bits, gb.rank1, gb.perm1, gb.pk, gb.c4,
-                       row_ptr, col, w, col_capacity, sc);
+  return launch_kernel(k_csr_fill, dim3(grid), dim3(256), 0, stream, false, n, bits, gb, row_ptr, col, w,
+                       col_capacity, sc);
 }
 
 cudaError_t launch_spread_export(int n, const int32_t* rank1, const float* spread, const uint8_t* keep8,

@@ -147,6 +147,53 @@ __device__ __forceinline__ float4 eq5_step(const FilterArgs& a, const float4* __
   return xo;
 }
 
+// The same step at a window w > 1, over the 6 + NX neighbours (NX = 6 (w - 1)
+// further slots): a first pass finds min d2 from the packed codes, a second
+// accumulates, so no per-neighbour array is held in registers.
+template <int NX>
+__device__ __forceinline__ float4 eq5_step_wide(const FilterArgs& a, const float4* __restrict__ src, int k, int n,
+                                                float cexp) {
+  const float4 xk = src ? __ldcg(&src[k]) : x0_of(a, k);
+  const uint32_t wk = __float_as_uint(xk.w);
+  const uint32_t ck = wk & kCoordMask;
+  const int4 s = a.c4[k];
+  int dmin = INT_MAX;
+#pragma unroll 1
+  for (int j = 0; j < 6 + NX; ++j) {
+    const int o = neighbour_of(j, k, n, wk, s, a.cx, a.cx_stride);
+    if (o >= 0) dmin = min(dmin, sq_dist_c1(ck, a.pk[o] & kCoordMask, a.bits));
+  }
+  float se = 0.f, sr = 0.f, sgc = 0.f, sb = 0.f;
+#pragma unroll 1
+  for (int j = 0; j < 6 + NX; ++j) {
+    const int o = neighbour_of(j, k, n, wk, s, a.cx, a.cx_stride);
+    if (o < 0) continue;
+    const float4 xo = src ? __ldcg(&src[o]) : x0_of(a, o);
+    const int d2 = sq_dist_c1(ck, __float_as_uint(xo.w) & kCoordMask, a.bits);
+    const float e = exp2f(float(dmin - d2) * cexp);
+    se += e;
+    sr = fmaf(e, xo.x, sr);
+    sgc = fmaf(e, xo.y, sgc);
+    sb = fmaf(e, xo.z, sb);
+  }
+  float4 xo = xk;
+  if (se > 0.f) {
+    const float inv = 1.f / se;
+    xo.x = 0.5f * xk.x + 0.5f * (sr * inv);
+    xo.y = 0.5f * xk.y + 0.5f * (sgc * inv);
+    xo.z = 0.5f * xk.z + 0.5f * (sb * inv);
+  }
+  return xo;
+}
+
+// one Eq. 5 step at window 1 (NX = 0) or wider
+template <int NX>
+__device__ __forceinline__ float4 eq5_step_nx(const FilterArgs& a, const float4* __restrict__ src, int k, int n,
+                                              float cexp) {
+  if constexpr (NX == 0) return eq5_step(a, src, k, n, cexp);
+  else return eq5_step_wide<NX>(a, src, k, n, cexp);
+}
+
 // The first steps x_1, x_2, ... and each point's Eq. 6 term sum_c (y^2 - x_q^2)
 // in fixed point beside them, by the blocks [first, gridDim.x) of a
 // cooperative grid (they need the graph and the colours only, not sigma_est):

@@ -16,6 +16,7 @@
 //   the values are sorted descending and the tail rule gives sigma_est.
 #include <algorithm>
 
+#include "eigen.cuh"
 #include "select.cuh"
 
 namespace fgbd {
@@ -472,7 +473,6 @@ __global__ void __launch_bounds__(kNeThreads, 4)
 
 // ---------------------------------------------------------------- finalize
 
-constexpr double kZeroEigRel = 1e-9;  // relative size below which an eigenvalue is zero
 constexpr int kMaxSweeps = 15;
 constexpr int kFinThreads = 384;      // 12 warps: V blocks, A blocks, the rotation predictor
 constexpr int kGroups = 11;           // per round: 10 rotated pairs and one resting index
@@ -504,26 +504,6 @@ __device__ __forceinline__ float rotated_entry(const float* __restrict__ A, floa
   const float row_a = fmaf(cb.x, A[a * kD + b], cb.y * A[a * kD + pb]);
   const float row_pa = fmaf(cb.x, A[pa * kD + b], cb.y * A[pa * kD + pb]);
   return fmaf(ca.x, row_a, ca.y * row_pa);
-}
-
-// The rotation of the pair p < q that zeroes a_pq, as the columns of J for p
-// and for q: (c, -s) and (c, s).  cos 2phi = |a_qq - a_pp| / r with r =
-// sqrt((a_qq - a_pp)^2 + 4 a_pq^2), c = sqrt((1 + cos 2phi) / 2), |s| =
-// |a_pq| / (r c), and s takes the sign of (a_qq - a_pp) a_pq (the smaller of
-// the two angles that zero a_pq).  A pair with |a_pq| <= thr is not rotated.
-__device__ __forceinline__ void jacobi_rotation(float app, float aqq, float apq, float thr, float2& cp, float2& cq) {
-  cp = cq = make_float2(1.f, 0.f);
-  if (!(fabsf(apq) > thr)) return;
-  const float tau = aqq - app;
-  const float two_a = 2.f * apq;
-  const float rr = rsqrtf(fmaf(tau, tau, two_a * two_a));
-  const float h = fmaf(0.5f * fabsf(tau), rr, 0.5f);
-  const float ic = rsqrtf(h);
-  const float c = h * ic;
-  float s = fabsf(apq) * rr * ic;
-  if ((tau < 0.f) != (apq < 0.f)) s = -s;
-  cp = make_float2(c, -s);
-  cq = make_float2(c, s);
 }
 
 // Entry (i, k) of the Helmert basis of R^7: column 0 is uniform, column k >= 1
@@ -571,23 +551,6 @@ __device__ __noinline__ void colour_basis(float (*m)[3]) {
   }
   for (int i = 0; i < 3; ++i)
     for (int j = 0; j < 3; ++j) m[i][j] = v[i][j];
-}
-
-// a / b in float64 from a float32 reciprocal and Newton steps (fused
-// multiply-adds only; the library division is much longer on this GPU).
-// Within an ulp or two of the rounded quotient for b > 0.
-__device__ __forceinline__ double div_newton(double a, double b) {
-  double r = double(__frcp_rn(float(b)));
-  r = fma(r, fma(-b, r, 1.0), r);
-  r = fma(r, fma(-b, r, 1.0), r);
-  const double q = a * r;
-  return fma(r, fma(-b, q, a), q);
-}
-
-// 64-bit integer whose signed order is the numeric order of the double x
-__device__ __forceinline__ long long order_key(double x) {
-  const long long b = __double_as_longlong(x);
-  return b < 0 ? (b ^ 0x7fffffffffffffffLL) : b;
 }
 
 // barriers of the first kFinThreads threads of a block (barrier 1; 0 is __syncthreads)

@@ -1,0 +1,596 @@
+// NE-GBP (Section 2.3) at windows w > 1.  With w points linked on each side
+// along each of the three codes (Section 2.2), a point has up to K = 6w
+// neighbours, and the points with exactly K give patches of D = 3 (K + 1)
+// entries: the point, then its neighbours by increasing distance (ties by the
+// offset (dz, dy, dx), then by index), three colour channels each.  The FSLR
+// spread of every point (Section 2.4) comes from the same pass.  Four launches:
+//
+//   k_ne_moments_wide  batches of points staged as a transposed patch block in
+//                      shared memory; each thread owns one 3x3 tile (node a,
+//                      node b >= a) of sum a a^T or the three sums a of one
+//                      node.  uint8 colours: int8 entries c - 128 and exact
+//                      dp4a sums in int64; float colours: float32 sums per
+//                      batch, then float64.  Each block writes its partial
+//                      sums (no atomics, so the totals do not depend on timing).
+//   k_ne_wide_reduce   the partials summed entry by entry in block order.
+//   k_ne_wide_jacobi   one block: Sigma = S2/N - mu mu^T in float64, then a
+//                      cyclic Jacobi in float32 (round-robin order: in round r
+//                      index i pairs with 2r - i mod D), one coefficient step
+//                      and one update step per round.
+//   k_ne_wide_tail     one block per eigenvector: the float64 Rayleigh quotient
+//                      v^T Sigma v / v^T v (second order in the eigenvector
+//                      error); the last block to finish sorts the values, sets
+//                      numerical zeros to 0 and applies the tail rule.
+#include <algorithm>
+
+#include "eigen.cuh"
+
+namespace fgbd {
+namespace {
+
+constexpr int kWThreads = 256;        // moments: threads per block
+constexpr int kWJacobiThreads = 512;
+constexpr int kWTailThreads = 64;     // D <= 57 eigenvector entries, one per thread
+constexpr int kWMaxSweeps = 30;
+
+template <int W>
+constexpr int patch_dim() {
+  return 3 * (6 * W + 1);
+}
+
+// compare-exchange of two (key, sorted id) pairs: ascending key, then id
+__device__ __forceinline__ void cmp_swap(unsigned long long& ka, int& ia, unsigned long long& kb, int& ib) {
+  const bool sw = (kb < ka) || (kb == ka && ib < ia);
+  const unsigned long long k0 = sw ? kb : ka, k1 = sw ? ka : kb;
+  const int i0 = sw ? ib : ia, i1 = sw ? ia : ib;
+  ka = k0;
+  kb = k1;
+  ia = i0;
+  ib = i1;
+}
+
+// Sorted point k: its FSLR spread over itself and all its neighbours
+// (spread[k]) and, if it has exactly K = 6W neighbours, its patch written to
+// column `col` of the transposed batch block `rows` (row stride `rw` words;
+// uint8: byte entries c ^ 0x80, i.e. c - 128 as int8; float: c - 128).
+// Returns whether a patch was written.
+template <int W, int DT>
+__device__ __forceinline__ bool wide_patch(int k, int n, int bits, const GraphBufs& gb, const uint32_t* __restrict__ y8,
+                                           const float4* __restrict__ yf, float* __restrict__ spread, int col,
+                                           uint32_t* rows, int rw) {
+  constexpr int K = 6 * W;
+  const uint32_t pkk = gb.pk[k];
+  const int4 s = gb.c4[k];
+  int id[K];
+  int deg = 0;
+#pragma unroll
+  for (int j = 0; j < K; ++j) {
+    id[j] = neighbour_of(j, k, n, pkk, s, gb.cx, gb.cx_stride);
+    deg += id[j] >= 0;
+  }
+  const int nn = deg + 1;
+  float sp;
+  if (DT == 0) {
+    const uint32_t own = y8[k];
+    int sr = int(own & 255u), sg = int((own >> 8) & 255u), sb = int((own >> 16) & 255u);
+    int qr = sr * sr, qg = sg * sg, qb = sb * sb;
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+      if (id[j] < 0) continue;
+      const uint32_t c = y8[id[j]];
+      const int a = int(c & 255u), b = int((c >> 8) & 255u), d = int((c >> 16) & 255u);
+      sr += a;
+      sg += b;
+      sb += d;
+      qr += a * a;
+      qg += b * b;
+      qb += d * d;
+    }
+    // nn^2 times each population variance is an exact integer (as at window 1)
+    const float vr = float(nn * qr - sr * sr), vg = float(nn * qg - sg * sg), vb = float(nn * qb - sb * sb);
+    sp = (sqrtf(vr) + sqrtf(vg) + sqrtf(vb)) * __frcp_rn(3.0f * float(nn));
+  } else {
+    const float4 o = yf[k];
+    float mr = o.x, mg = o.y, mb = o.z;
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+      if (id[j] < 0) continue;
+      const float4 c = yf[id[j]];
+      mr += c.x;
+      mg += c.y;
+      mb += c.z;
+    }
+    const float icnt = __frcp_rn(float(nn));
+    mr *= icnt;
+    mg *= icnt;
+    mb *= icnt;
+    float vr = (o.x - mr) * (o.x - mr), vg = (o.y - mg) * (o.y - mg), vb = (o.z - mb) * (o.z - mb);
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+      if (id[j] < 0) continue;
+      const float4 c = yf[id[j]];
+      vr += (c.x - mr) * (c.x - mr);
+      vg += (c.y - mg) * (c.y - mg);
+      vb += (c.z - mb) * (c.z - mb);
+    }
+    sp = (sqrtf(vr * icnt) + sqrtf(vg * icnt) + sqrtf(vb * icnt)) * (1.0f / 3.0f);
+  }
+  spread[k] = sp;
+  if (deg != K) return false;
+
+  // sort keys: d^2, then the offset (dz, dy, dx), packed so that integer order is lexicographic
+  int kx, ky, kz;
+  decode_c1(pkk, bits, kx, ky, kz);
+  unsigned long long key[K];
+#pragma unroll
+  for (int j = 0; j < K; ++j) {
+    int x, y, z;
+    decode_c1(gb.pk[id[j]], bits, x, y, z);
+    const int dx = x - kx, dy = y - ky, dz = z - kz;
+    const unsigned long long d2 = (unsigned long long)(dx * dx + dy * dy + dz * dz);
+    key[j] = (d2 << 33) | ((unsigned long long)(dz + 1024) << 22) | ((unsigned long long)(dy + 1024) << 11) |
+             (unsigned long long)(dx + 1024);
+  }
+  // odd-even transposition sort: K rounds order K elements (keys with their
+  // id are a strict order, so the result is the unique sorted one)
+#pragma unroll
+  for (int round = 0; round < K; ++round) {
+#pragma unroll
+    for (int i = round & 1; i + 1 < K; i += 2) cmp_swap(key[i], id[i], key[i + 1], id[i + 1]);
+  }
+  if (DT == 0) {
+    uint8_t* b = reinterpret_cast<uint8_t*>(rows);
+    const int stride = rw * 4;
+    const uint32_t own = y8[k];
+    b[0 * stride + col] = uint8_t((own & 255u) ^ 0x80u);
+    b[1 * stride + col] = uint8_t(((own >> 8) & 255u) ^ 0x80u);
+    b[2 * stride + col] = uint8_t(((own >> 16) & 255u) ^ 0x80u);
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+      const uint32_t c = y8[id[j]];
+      b[(3 + 3 * j) * stride + col] = uint8_t((c & 255u) ^ 0x80u);
+      b[(4 + 3 * j) * stride + col] = uint8_t(((c >> 8) & 255u) ^ 0x80u);
+      b[(5 + 3 * j) * stride + col] = uint8_t(((c >> 16) & 255u) ^ 0x80u);
+    }
+  } else {
+    float* f = reinterpret_cast<float*>(rows);
+    const float4 own = yf[k];
+    f[0 * rw + col] = own.x - 128.f;
+    f[1 * rw + col] = own.y - 128.f;
+    f[2 * rw + col] = own.z - 128.f;
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+      const float4 c = yf[id[j]];
+      f[(3 + 3 * j) * rw + col] = c.x - 128.f;
+      f[(4 + 3 * j) * rw + col] = c.y - 128.f;
+      f[(5 + 3 * j) * rw + col] = c.z - 128.f;
+    }
+  }
+  return true;
+}
+
+// Per block: batches of B points (B = 256 uint8 / 128 float), one per thread
+// of the first B; partial sums to part[blockIdx.x][D*D + D + 1] (second
+// moments at r*D + c for the computed tiles, first moments at D*D + r, the
+// patch count last; uint8 sums as int64 bit patterns).
+template <int W, int DT>
+__global__ void __launch_bounds__(kWThreads) k_ne_moments_wide(int n, int bits, GraphBufs gb,
+                                                               const uint32_t* __restrict__ y8,
+                                                               const float4* __restrict__ yf,
+                                                               float* __restrict__ spread, double* __restrict__ part) {
+  pdl_wait();
+  constexpr int T = 6 * W + 1;  // points of a patch
+  constexpr int D = 3 * T;
+  constexpr int B = DT == 0 ? 256 : 128;
+  constexpr int RW = DT == 0 ? B / 4 + 1 : B + 1;  // row stride in words, odd: rows start in distinct banks
+  constexpr int NT = T * (T + 1) / 2;              // tiles (a, b), a <= b
+  constexpr int P = D * D + D + 1;
+  static_assert(NT + T <= kWThreads && B <= kWThreads, "one tile or one first-moment node per thread");
+  static_assert(D * RW * 4 <= 48 * 1024, "the batch block fits static shared memory");
+  __shared__ __align__(16) uint32_t rows[D * RW];
+
+  const int tid = threadIdx.x;
+  int ta = -1, tb = -1;  // tile (ta, tb), or the first moments of node ta (tb = -1)
+  if (tid < NT) {
+    int t = tid, a = 0;
+    while (t >= T - a) {
+      t -= T - a;
+      ++a;
+    }
+    ta = a;
+    tb = a + t;
+  } else if (tid < NT + T) {
+    ta = tid - NT;
+  }
+  long long acc64[9] = {};
+  double accd[9] = {};
+  unsigned long long npatch = 0;
+  for (int base = blockIdx.x * B; base < n; base += gridDim.x * B) {
+    bool has = false;
+    if (tid < B) {
+      const int k = base + tid;
+      if (k < n) has = wide_patch<W, DT>(k, n, bits, gb, y8, yf, spread, tid, rows, RW);
+      if (!has) {
+        if (DT == 0) {
+          uint8_t* b = reinterpret_cast<uint8_t*>(rows);
+#pragma unroll 3
+          for (int r = 0; r < D; ++r) b[r * RW * 4 + tid] = 0;
+        } else {
+          float* f = reinterpret_cast<float*>(rows);
+#pragma unroll 3
+          for (int r = 0; r < D; ++r) f[r * RW + tid] = 0.f;
+        }
+      }
+    }
+    npatch += (unsigned long long)__syncthreads_count(has);
+    if (DT == 0) {
+      const int* ri = reinterpret_cast<const int*>(rows);
+      if (tb >= 0) {
+        int acc[9] = {};
+#pragma unroll 4
+        for (int w = 0; w < B / 4; ++w) {
+          int a[3], b[3];
+#pragma unroll
+          for (int i = 0; i < 3; ++i) {
+            a[i] = ri[(3 * ta + i) * RW + w];
+            b[i] = ri[(3 * tb + i) * RW + w];
+          }
+#pragma unroll
+          for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int j = 0; j < 3; ++j) acc[3 * i + j] = __dp4a(a[i], b[j], acc[3 * i + j]);
+        }
+#pragma unroll
+        for (int i = 0; i < 9; ++i) acc64[i] += acc[i];
+      } else if (ta >= 0) {
+        int acc[3] = {};
+#pragma unroll 4
+        for (int w = 0; w < B / 4; ++w)
+#pragma unroll
+          for (int i = 0; i < 3; ++i) acc[i] = __dp4a(ri[(3 * ta + i) * RW + w], 0x01010101, acc[i]);
+#pragma unroll
+        for (int i = 0; i < 3; ++i) acc64[i] += acc[i];
+      }
+    } else {
+      const float* rf = reinterpret_cast<const float*>(rows);
+      if (tb >= 0) {
+        float accf[9] = {};
+#pragma unroll 4
+        for (int p = 0; p < B; ++p) {
+          float a[3], b[3];
+#pragma unroll
+          for (int i = 0; i < 3; ++i) {
+            a[i] = rf[(3 * ta + i) * RW + p];
+            b[i] = rf[(3 * tb + i) * RW + p];
+          }
+#pragma unroll
+          for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int j = 0; j < 3; ++j) accf[3 * i + j] = fmaf(a[i], b[j], accf[3 * i + j]);
+        }
+#pragma unroll
+        for (int i = 0; i < 9; ++i) accd[i] += double(accf[i]);
+      } else if (ta >= 0) {
+        float accf[3] = {};
+#pragma unroll 4
+        for (int p = 0; p < B; ++p)
+#pragma unroll
+          for (int i = 0; i < 3; ++i) accf[i] += rf[(3 * ta + i) * RW + p];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) accd[i] += double(accf[i]);
+      }
+    }
+    __syncthreads();
+  }
+  double* out = part + size_t(blockIdx.x) * P;
+  long long* outi = reinterpret_cast<long long*>(out);
+  if (tb >= 0) {
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        const int idx = (3 * ta + i) * D + 3 * tb + j;
+        if (DT == 0) outi[idx] = acc64[3 * i + j];
+        else out[idx] = accd[3 * i + j];
+      }
+  } else if (ta >= 0) {
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      if (DT == 0) outi[D * D + 3 * ta + i] = acc64[i];
+      else out[D * D + 3 * ta + i] = accd[i];
+    }
+  }
+  if (tid == 0) {
+    if (DT == 0) outi[D * D + D] = (long long)npatch;
+    else out[D * D + D] = double(npatch);
+  }
+}
+
+// the totals: entry i summed over the blocks' partials in block order; second
+// moments outside the computed tiles (below the diagonal blocks) are 0
+template <int DT>
+__global__ void __launch_bounds__(256) k_ne_wide_reduce(const double* __restrict__ part, int blocks, int D,
+                                                        double* __restrict__ tot) {
+  pdl_wait();
+  const int P = D * D + D + 1;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= P) return;
+  const bool used = i >= D * D || (i / D) / 3 <= (i % D) / 3;
+  if (DT == 0) {
+    long long t = 0;
+    if (used)
+      for (int b = 0; b < blocks; ++b) t += reinterpret_cast<const long long*>(part)[size_t(b) * P + i];
+    tot[i] = double(t);  // below 2^53 for any capacity: exact
+  } else {
+    double t = 0.0;
+    if (used)
+      for (int b = 0; b < blocks; ++b) t += part[size_t(b) * P + i];
+    tot[i] = t;
+  }
+}
+
+template <int D>
+__device__ __forceinline__ int round_partner(int i, int r) {
+  int p = 2 * r - i;
+  if (p < 0) p += D;
+  if (p >= D) p -= D;
+  return p;
+}
+
+// One block: the covariance, then the float32 Jacobi.  D is odd, so in round
+// r every pair {i, j} with i + j = 2r (mod D) is rotated and index r rests;
+// each pair meets once per sweep.  A pair is rotated while |a_pq| > 2e-7
+// ||diag A|| (the float32 resolution of the matrix); the iteration ends at the
+// first round after which no off-diagonal entry is above that, or after
+// kWMaxSweeps sweeps.  Without patches the results are written here (zero).
+template <int D>
+__global__ void __launch_bounds__(kWJacobiThreads) k_ne_wide_jacobi(const double* __restrict__ tot,
+                                                                    double* __restrict__ S,
+                                                                    float* __restrict__ Vout,
+                                                                    DevScalars* __restrict__ sc,
+                                                                    double* __restrict__ sigma_out) {
+  pdl_wait();
+  static_assert(D & 1, "the round-robin schedule assumes an odd dimension");
+  __shared__ float Ab[2][D * D];
+  __shared__ float V[D * D];
+  __shared__ float2 co[D];
+  const int tid = threadIdx.x;
+  const double npd = tot[D * D + D];
+  if (tid == 0) sc->n_patches = (unsigned long long)npd;
+  if (!(npd >= 1.0)) {
+    for (int i = tid; i < D; i += kWJacobiThreads) sc->eig[i] = 0.0;
+    if (tid == 0) {
+      sc->tau = 0.0;
+      sc->sigma_est = 0.0;
+      sc->m = 0;
+      sc->ne_valid = 1;
+      if (sigma_out) *sigma_out = 0.0;
+      __threadfence();
+      atomicExch(&sc->sigma_ready, 1u);
+    }
+    return;
+  }
+  const double inv_n = 1.0 / npd;
+  for (int e = tid; e < D * D; e += kWJacobiThreads) {
+    const int r = e / D, c = e % D;
+    const int rr = min(r, c), cc = max(r, c);
+    const double mr = tot[D * D + rr] * inv_n, mc = tot[D * D + cc] * inv_n;
+    const double v = tot[rr * D + cc] * inv_n - mr * mc;
+    S[e] = v;
+    Ab[0][e] = float(v);
+    V[e] = r == c ? 1.f : 0.f;
+  }
+  __syncthreads();
+  float dsq = 0.f;
+  for (int i = 0; i < D; ++i) dsq = fmaf(Ab[0][i * D + i], Ab[0][i * D + i], dsq);
+  const float thr = 2e-7f * sqrtf(dsq);
+  bool off = false;
+  for (int e = tid; e < D * D; e += kWJacobiThreads) off |= (e / D != e % D) && fabsf(Ab[0][e]) > thr;
+  bool big = __syncthreads_or(off) != 0;
+  int cur = 0;
+  for (int round = 0; big && round < kWMaxSweeps * D; ++round) {
+    const int r = round % D;
+    const float* A = Ab[cur];
+    float* An = Ab[cur ^ 1];
+    if (tid < D) {
+      const int i = tid, pi = round_partner<D>(i, r);
+      float2 c = make_float2(1.f, 0.f);
+      if (pi != i) {
+        const int p = min(i, pi), q = max(i, pi);
+        float2 cp, cq;
+        jacobi_rotation(A[p * D + p], A[q * D + q], A[p * D + q], thr, cp, cq);
+        c = i == p ? cp : cq;
+      }
+      co[i] = c;  // column i of J: alpha_i at row i, beta_i at row pi
+    }
+    __syncthreads();
+    off = false;
+    // J^T A J entry by entry: sum over u in {i, pi}, v in {j, pj} of J[u][i] A[u][v] J[v][j].
+    // Only i <= j is computed and mirrored: the two roundings of a_ij and a_ji
+    // would differ, and a pair whose a_pq sat just above the threshold with
+    // a_qp just below would then never be rotated again.
+    for (int e = tid; e < D * D; e += kWJacobiThreads) {
+      const int i = e / D, j = e % D;
+      if (i > j) continue;
+      const int pi = round_partner<D>(i, r), pj = round_partner<D>(j, r);
+      const float2 ci = co[i], cj = co[j];
+      const float row_i = fmaf(cj.x, A[i * D + j], cj.y * A[i * D + pj]);
+      const float row_pi = fmaf(cj.x, A[pi * D + j], cj.y * A[pi * D + pj]);
+      const float v = fmaf(ci.x, row_i, ci.y * row_pi);
+      An[i * D + j] = v;
+      An[j * D + i] = v;
+      off |= i != j && fabsf(v) > thr;
+    }
+    // V J in place: the thread of (row x, i < pi) owns both entries it changes
+    for (int e = tid; e < D * D; e += kWJacobiThreads) {
+      const int x = e / D, i = e % D;
+      const int pi = round_partner<D>(i, r);
+      if (pi <= i) continue;
+      const float2 ci = co[i], cp = co[pi];
+      const float vi = V[x * D + i], vp = V[x * D + pi];
+      V[x * D + i] = fmaf(ci.x, vi, ci.y * vp);
+      V[x * D + pi] = fmaf(cp.x, vp, cp.y * vi);
+    }
+    big = __syncthreads_or(off) != 0;
+    cur ^= 1;
+  }
+  for (int e = tid; e < D * D; e += kWJacobiThreads) Vout[e] = V[e];
+}
+
+// Block k: lambda_k = v_k^T Sigma v_k / v_k^T v_k in float64.  The last block
+// to finish (a counter; no block waits for another) sorts the D values
+// descending, sets those below 1e-9 max(lambda_1, 1) to 0 and applies the tail
+// rule: m* is the smallest m with mean(lambda_{m+1..D}) <= median(lambda_{m+1..D}),
+// sigma_est = sqrt(tau(m*)).
+template <int D>
+__global__ void __launch_bounds__(kWTailThreads) k_ne_wide_tail(const double* __restrict__ tot,
+                                                                const double* __restrict__ S,
+                                                                const float* __restrict__ V,
+                                                                double* __restrict__ lam, uint32_t* __restrict__ done,
+                                                                DevScalars* __restrict__ sc,
+                                                                double* __restrict__ sigma_out) {
+  pdl_wait();
+  static_assert(D <= kWTailThreads, "one eigenvalue per thread in the last block");
+  __shared__ double s_v[D];
+  __shared__ double s_red[2][2];
+  __shared__ int s_last;
+  __shared__ long long s_key[D];
+  __shared__ double s_sorted[D];
+  __shared__ double s_suffix[D];
+  __shared__ double s_top[2];
+  __shared__ int s_m;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (!(tot[D * D + D] >= 1.0)) return;  // no patches: the Jacobi launch wrote the results
+  const int k = blockIdx.x;
+  if (tid < D) s_v[tid] = double(V[tid * D + k]);
+  __syncthreads();
+  double num = 0.0, den = 0.0;
+  if (tid < D) {
+    const double* row = S + size_t(tid) * D;
+    double u0 = 0.0, u1 = 0.0, u2 = 0.0;
+#pragma unroll
+    for (int c = 0; c < D; c += 3) {
+      u0 = fma(row[c], s_v[c], u0);
+      u1 = fma(row[c + 1], s_v[c + 1], u1);
+      u2 = fma(row[c + 2], s_v[c + 2], u2);
+    }
+    num = s_v[tid] * (u0 + u1 + u2);
+    den = s_v[tid] * s_v[tid];
+  }
+  num = warp_sum(num);
+  den = warp_sum(den);
+  if (lane == 0) {
+    s_red[warp][0] = num;
+    s_red[warp][1] = den;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    const double nn = s_red[0][0] + s_red[1][0], dd = s_red[0][1] + s_red[1][1];
+    lam[k] = dd > 0.0 ? nn / dd : 0.0;
+    __threadfence();
+    s_last = atomicAdd(done, 1u) == unsigned(D - 1);
+  }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  double l = tid < D ? __ldcg(&lam[tid]) : 0.0;
+  double top = tid < D ? l : -1.0;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) top = fmax(top, __shfl_xor_sync(0xffffffffu, top, o));
+  if (lane == 0) s_top[warp] = top;
+  if (tid == 0) s_m = D - 1;  // m = D - 1 always passes
+  __syncthreads();
+  top = fmax(s_top[0], s_top[1]);
+  if (tid < D && fabs(l) < kZeroEigRel * fmax(top, 1.0)) l = 0.0;
+  if (tid < D) s_key[tid] = order_key(l);
+  __syncthreads();
+  if (tid < D) {
+    const long long mine = s_key[tid];
+    int rank = 0;
+    for (int j = 0; j < D; ++j) {
+      const long long o = s_key[j];
+      rank += (o > mine) || (o == mine && j < tid);
+    }
+    s_sorted[rank] = l;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    double acc = 0.0;
+    for (int j = D - 1; j >= 0; --j) {
+      acc += s_sorted[j];
+      s_suffix[j] = acc;
+    }
+  }
+  __syncthreads();
+  if (tid < D) {
+    const int cnt = D - tid;
+    const double med = (cnt & 1) ? s_sorted[tid + cnt / 2]
+                                 : 0.5 * (s_sorted[tid + cnt / 2 - 1] + s_sorted[tid + cnt / 2]);
+    if (s_suffix[tid] <= med * double(cnt)) atomicMin(&s_m, tid);
+    sc->eig[tid] = s_sorted[tid];
+  }
+  __syncthreads();
+  if (tid == 0) {
+    const int m = s_m;
+    const double tau = s_suffix[m] / double(D - m);
+    const double sg = sqrt(fmax(tau, 0.0));
+    sc->m = m;
+    sc->tau = tau;
+    sc->sigma_est = sg;
+    sc->ne_valid = 1;
+    if (sigma_out) *sigma_out = sg;
+    *done = 0u;  // ready for the next estimate
+    __threadfence();
+    atomicExch(&sc->sigma_ready, 1u);
+  }
+}
+
+template <int W>
+cudaError_t launch_wide(int n, int bits, int dtype, const GraphBufs& gb, const uint32_t* y8, const float4* yf,
+                        float* spread, const WideNe& w, DevScalars* sc, double* sigma_out, int num_sms,
+                        cudaStream_t stream) {
+  constexpr int D = patch_dim<W>();
+  const int P = D * D + D + 1;
+  const int blocks = std::min(ne_wide_blocks(n, num_sms), w.blocks);
+  cudaError_t e = cudaSuccess;
+  if (n > 0) {
+    e = dtype == 0 ? launch_kernel(k_ne_moments_wide<W, 0>, dim3(blocks), dim3(kWThreads), 0, stream, false, n, bits,
+                                   gb, y8, yf, spread, w.part)
+                   : launch_kernel(k_ne_moments_wide<W, 1>, dim3(blocks), dim3(kWThreads), 0, stream, false, n, bits,
+                                   gb, y8, yf, spread, w.part);
+    if (e != cudaSuccess) return e;
+  }
+  const int used = n > 0 ? blocks : 0;
+  e = dtype == 0 ? launch_kernel(k_ne_wide_reduce<0>, dim3((P + 255) / 256), dim3(256), 0, stream, false,
+                                 static_cast<const double*>(w.part), used, D, w.tot)
+                 : launch_kernel(k_ne_wide_reduce<1>, dim3((P + 255) / 256), dim3(256), 0, stream, false,
+                                 static_cast<const double*>(w.part), used, D, w.tot);
+  if (e != cudaSuccess) return e;
+  e = launch_kernel(k_ne_wide_jacobi<D>, dim3(1), dim3(kWJacobiThreads), 0, stream, false,
+                    static_cast<const double*>(w.tot), w.S, w.V, sc, sigma_out);
+  if (e != cudaSuccess) return e;
+  return launch_kernel(k_ne_wide_tail<D>, dim3(D), dim3(kWTailThreads), 0, stream, false,
+                       static_cast<const double*>(w.tot), static_cast<const double*>(w.S),
+                       static_cast<const float*>(w.V), w.lam, w.done, sc, sigma_out);
+}
+
+}  // namespace
+
+int ne_wide_blocks(int n, int num_sms) { return std::max(1, std::min((n + 127) / 128, 2 * num_sms)); }
+
+size_t ne_wide_part_entries(int window) {
+  const size_t D = size_t(3 * (6 * window + 1));
+  return D * D + D + 1;
+}
+
+cudaError_t launch_ne_wide(int n, int bits, int window, int dtype, const GraphBufs& gb, const uint32_t* y8,
+                           const float4* yf, float* spread, const WideNe& w, DevScalars* sc, double* sigma_out,
+                           int num_sms, cudaStream_t stream) {
+  if (gb.nx != extra_slots(window) || !w.part || !w.tot || !w.S || !w.V || !w.lam || !w.done)
+    return cudaErrorInvalidValue;
+  if (window == 2) return launch_wide<2>(n, bits, dtype, gb, y8, yf, spread, w, sc, sigma_out, num_sms, stream);
+  if (window == 3) return launch_wide<3>(n, bits, dtype, gb, y8, yf, spread, w, sc, sigma_out, num_sms, stream);
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace fgbd

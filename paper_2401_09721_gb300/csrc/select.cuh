@@ -152,6 +152,75 @@ __device__ __noinline__ bool keep_ff(const FilterArgs& a, int k, FF thr) {
   return d.hi < 0.f || (d.hi == 0.f && d.lo <= 0.f);
 }
 
+// The same decision at a window w > 1: the point and its 6 + NX neighbour
+// slots, in loops (only the few points in the float32 band come here).
+template <int NX>
+__device__ __noinline__ bool keep_ff_wide(const FilterArgs& a, int k, FF thr) {
+  const int n = a.n;
+  const uint32_t pkk = a.pk[k];
+  const int4 s = a.c4[k];
+  FF total = {0.f, 0.f};
+  int cnt = 1;
+#pragma unroll 1
+  for (int j = 0; j < 6 + NX; ++j) cnt += neighbour_of(j, k, n, pkk, s, a.cx, a.cx_stride) >= 0;
+  if (a.dtype == 0) {
+    int sx[3], sq[3];
+    const uint32_t own = a.y8[k];
+#pragma unroll
+    for (int ch = 0; ch < 3; ++ch) {
+      const int x = int((own >> (8 * ch)) & 255u);
+      sx[ch] = x;
+      sq[ch] = x * x;
+    }
+#pragma unroll 1
+    for (int j = 0; j < 6 + NX; ++j) {
+      const int o = neighbour_of(j, k, n, pkk, s, a.cx, a.cx_stride);
+      if (o < 0) continue;
+      const uint32_t c = a.y8[o];
+#pragma unroll
+      for (int ch = 0; ch < 3; ++ch) {
+        const int x = int((c >> (8 * ch)) & 255u);
+        sx[ch] += x;
+        sq[ch] += x * x;
+      }
+    }
+    // cnt^2 var <= 19^2 127.5^2 < 2^24: exact in float32
+#pragma unroll
+    for (int ch = 0; ch < 3; ++ch) total = ff_add(total, ff_sqrt({float(cnt * sq[ch] - sx[ch] * sx[ch]), 0.f}));
+    const FF d = ff_add(total, ff_neg(ff_mul(thr, {3.f * float(cnt), 0.f})));
+    return d.hi < 0.f || (d.hi == 0.f && d.lo <= 0.f);
+  }
+#pragma unroll 1
+  for (int ch = 0; ch < 3; ++ch) {
+    const float* own = reinterpret_cast<const float*>(&a.yf[k]);
+    FF sum = {own[ch], 0.f};
+#pragma unroll 1
+    for (int j = 0; j < 6 + NX; ++j) {
+      const int o = neighbour_of(j, k, n, pkk, s, a.cx, a.cx_stride);
+      if (o >= 0) sum = ff_add(sum, {reinterpret_cast<const float*>(&a.yf[o])[ch], 0.f});
+    }
+    const FF mean = ff_div_int(sum, cnt);
+    FF dd = ff_add({own[ch], 0.f}, ff_neg(mean));
+    FF ss = ff_mul(dd, dd);
+#pragma unroll 1
+    for (int j = 0; j < 6 + NX; ++j) {
+      const int o = neighbour_of(j, k, n, pkk, s, a.cx, a.cx_stride);
+      if (o < 0) continue;
+      dd = ff_add({reinterpret_cast<const float*>(&a.yf[o])[ch], 0.f}, ff_neg(mean));
+      ss = ff_add(ss, ff_mul(dd, dd));
+    }
+    total = ff_add(total, ff_sqrt(ff_div_int(ss, cnt)));
+  }
+  const FF d = ff_add(total, ff_neg(ff_mul(thr, {3.f, 0.f})));
+  return d.hi < 0.f || (d.hi == 0.f && d.lo <= 0.f);
+}
+
+template <int NX>
+__device__ __forceinline__ bool keep_ff_nx(const FilterArgs& a, int k, FF thr) {
+  if constexpr (NX == 0) return keep_ff(a, k, thr);
+  else return keep_ff_wide<NX>(a, k, thr);
+}
+
 __device__ __forceinline__ void write_out(const FilterArgs& a, int i, float4 x) {
   if (a.out_dtype == 0) {
     uint8_t* o = static_cast<uint8_t*>(a.out) + 3 * size_t(i);
@@ -308,8 +377,9 @@ constexpr int kSums = 3 + 2 * kSpecMax;  // kept y^2, all y^2, kept count, then 
 
 // The selection and filter for the blocks [first, first + members) of a
 // cooperative grid of THREADS-thread blocks, from S stored steps (0: none),
-// grid barriers on *bar (epoch: the barriers this grid has passed on it).
-template <int THREADS>
+// grid barriers on *bar (epoch: the barriers this grid has passed on it);
+// NX further neighbour slots per point (window w > 1: NX = 6 (w - 1)).
+template <int THREADS, int NX = 0>
 __device__ __forceinline__ void select_filter(const FilterArgs& a, int S, int first, uint32_t members,
                                               uint32_t* bar, uint32_t& epoch) {
   __shared__ unsigned long long s_red[(kSums + 1) * (THREADS / 32)];
@@ -374,7 +444,7 @@ __device__ __forceinline__ void select_filter(const FilterArgs& a, int S, int fi
         bool keep;
         if (a.all_points || sp[i] <= t_lo) keep = true;
         else if (sp[i] > t_hi) keep = false;
-        else keep = keep_ff(a, k0 + i, thr);
+        else keep = keep_ff_nx<NX>(a, k0 + i, thr);
         kw |= uint32_t(keep) << (8 * i);
         const unsigned long long q2 = sq3(x[i]);
         acc[1] += q2;
@@ -506,7 +576,7 @@ __device__ __forceinline__ void select_filter(const FilterArgs& a, int S, int fi
     float4* __restrict__ dst = (t & 1) ? a.xbuf1 : a.xbuf0;
     unsigned long long loc = 0;
     for (int k = gtid; k < n; k += gstride) {
-      const float4 xo = eq5_step(a, src, k, n, cexp);
+      const float4 xo = eq5_step_nx<NX>(a, src, k, n, cexp);
       dst[k] = xo;
       if (select && (keep_all || __ldcg(a.keep8 + k))) loc += sq3(xo);
     }

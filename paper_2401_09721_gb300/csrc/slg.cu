@@ -714,6 +714,78 @@ __global__ void __launch_bounds__(256) k_c1_line_flags(int n, int bits, uint32_t
   }
 }
 
+// Windows w > 1 (Section 2.2 with w points linked on each side): one thread
+// per (code l, position r) fills the slots of the point at r for code l, the
+// points d = 1..w positions before and after it: C2/C3 d = 1 into c4, every
+// code's d >= 2 into cx (C1 d = 1 stays implicit: k - 1, k + 1).  A pair that
+// an earlier code links (C1: sorted ids at most w apart; C2: C2 positions at
+// most w apart; each on one scan line under the same-line variant) is left
+// out of the later code's slots, so the union graph is a set.  The decision
+// is a function of the pair and the code, so both ends reach the same one.
+// Each undirected edge is counted (and its length summed) once, from the
+// earlier position.
+__global__ void __launch_bounds__(256) k_link_wide(int n, int bits, int cap, int window, int same_line,
+                                                  const int32_t* __restrict__ ord23,
+                                                  const uint32_t* __restrict__ keys_c2,
+                                                  const uint32_t* __restrict__ keys_c3,
+                                                  const int32_t* __restrict__ rank2, const uint32_t* __restrict__ pk,
+                                                  int4* __restrict__ c4, int32_t* __restrict__ cx, int cx_stride,
+                                                  DevScalars* __restrict__ sc) {
+  pdl_wait();
+  __shared__ unsigned long long s_red[8];
+  const int code = blockIdx.y;
+  const int32_t* ord = code == 0 ? nullptr : ord23 + size_t(code - 1) * size_t(cap);
+  const uint32_t* keys = code == 0 ? pk : (code == 1 ? keys_c2 : keys_c3);
+  const bool sl = same_line != 0;
+  unsigned long long edges = 0;
+  float dist_f = 0.f;
+  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
+    const int k = code == 0 ? r : ord[r];
+    if (!in_range(k, n)) continue;
+    const uint32_t c = keys[r] & kCoordMask;
+    const int r2 = code == 2 ? rank2[k] : -1;
+    for (int d = 1; d <= window; ++d) {
+      int slot[2];
+#pragma unroll
+      for (int side = 0; side < 2; ++side) {
+        slot[side] = -1;
+        const int rr = side ? r + d : r - d;
+        if (rr < 0 || rr >= n) continue;
+        const int o = code == 0 ? rr : ord[rr];
+        if (!in_range(o, n)) continue;
+        const uint32_t oc = keys[rr] & kCoordMask;
+        if (sl && !same_scan_line(code, c, oc, bits)) continue;
+        bool dup = false;
+        if (code >= 1) dup = abs(k - o) <= window && (!sl || same_scan_line(0, c, oc, bits));
+        if (code == 2 && !dup) {
+          const int o2 = rank2[o];
+          dup = abs(r2 - o2) <= window && (!sl || same_scan_line(1, c, oc, bits));
+        }
+        if (dup) continue;
+        slot[side] = o;
+        if (side) {
+          edges += 1;
+          dist_f += sqrtf(float(sq_dist_c1(c, oc, bits)));
+        }
+      }
+      if (d == 1) {
+        if (code > 0) reinterpret_cast<int2*>(c4 + k)[code - 1] = make_int2(slot[0], slot[1]);
+      } else {
+        const int s0 = 6 * (d - 2) + 2 * code;
+        cx[size_t(s0) * size_t(cx_stride) + k] = slot[0];
+        cx[size_t(s0 + 1) * size_t(cx_stride) + k] = slot[1];
+      }
+    }
+  }
+  unsigned long long dist = (unsigned long long)__float2ull_rn(dist_f * float(1u << kDistShift));
+  edges = block_sum_u64<256>(edges, s_red);
+  dist = block_sum_u64<256>(dist, s_red);
+  if (threadIdx.x == 0) {
+    if (edges) atomicAdd(&sc->n_edges, edges);
+    if (dist) atomicAdd(&sc->dist_fx, dist);
+  }
+}
+
 // The three orders in input indices: C1 from perm1, C2 and C3 through perm1.
 __global__ void __launch_bounds__(256) k_orders_export(int n, int cap, const int32_t* __restrict__ perm1,
                                                        const int32_t* __restrict__ ord23, int32_t* __restrict__ out) {
@@ -798,6 +870,19 @@ cudaError_t launch_link(int n, int bits, int cap, bool same_line, const GraphBuf
   const cudaError_t e = launch_kernel(k_link<true>, dim3(gx, 3), dim3(kLinkThreads), 0, stream, false, n, bits, cap,
                                       gb.ord23, sb.keys[0], sb.keys[1], gb.rank2, gb.pk, gb.c4, sc);
   if (e != cudaSuccess) return e;
+  return launch_kernel(k_c1_line_flags, dim3(std::min((n + 255) / 256, num_sms * 8)), dim3(256), 0, stream, false, n,
+                       bits, gb.pk);
+}
+
+cudaError_t launch_link_wide(int n, int bits, int cap, int window, bool same_line, const GraphBufs& gb,
+                             const SortBufs& sb, DevScalars* sc, int num_sms, cudaStream_t stream) {
+  if (n <= 0) return cudaSuccess;
+  if (window < 2 || window > kMaxWindow || gb.nx != extra_slots(window) || !gb.cx) return cudaErrorInvalidValue;
+  const int gx = std::max(1, std::min((n + 255) / 256, num_sms * 4));
+  const cudaError_t e = launch_kernel(k_link_wide, dim3(gx, 3), dim3(256), 0, stream, false, n, bits, cap, window,
+                                      same_line ? 1 : 0, gb.ord23, sb.keys[0], sb.keys[1], gb.rank2, gb.pk, gb.c4,
+                                      gb.cx, gb.cx_stride, sc);
+  if (e != cudaSuccess || !same_line) return e;
   return launch_kernel(k_c1_line_flags, dim3(std::min((n + 255) / 256, num_sms * 8)), dim3(256), 0, stream, false, n,
                        bits, gb.pk);
 }

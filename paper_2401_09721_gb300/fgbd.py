@@ -20,8 +20,11 @@ LIB_PATH = os.path.join(_HERE, "libfgbd.so")
 
 FGBD_U8 = 0
 FGBD_F32 = 1
-PATCH_DIM = 21
+PATCH_DIM = 21        # FGBD_PATCH_DIM (window 1)
+MAX_WINDOW = 3        # FGBD_MAX_WINDOW
+PATCH_DIM_MAX = 57    # FGBD_PATCH_DIM_MAX
 Q_CAP = 256
+ABI_VERSION = 2
 
 STATUS = {
     0: "FGBD_OK",
@@ -68,7 +71,8 @@ class Stats(ctypes.Structure):
         ("n_edges", ctypes.c_int64),
         ("sigma_g", ctypes.c_double),
         ("n_patches", ctypes.c_int64),
-        ("eigenvalues", ctypes.c_double * PATCH_DIM),
+        ("patch_dim", ctypes.c_int32),
+        ("eigenvalues", ctypes.c_double * PATCH_DIM_MAX),
         ("m", ctypes.c_int32),
         ("q", ctypes.c_int32),
         ("tau", ctypes.c_double),
@@ -83,7 +87,8 @@ class Stats(ctypes.Structure):
     def as_dict(self) -> dict:
         return dict(
             n=self.n, n_edges=self.n_edges, sigma_g=self.sigma_g, n_patches=self.n_patches,
-            eigenvalues=list(self.eigenvalues), m=self.m, q=self.q, tau=self.tau,
+            patch_dim=self.patch_dim,
+            eigenvalues=list(self.eigenvalues[: self.patch_dim]), m=self.m, q=self.q, tau=self.tau,
             sigma_est=self.sigma_est, n_keep=self.n_keep, valid=self.valid,
             objective=list(self.objective[: self.n_objective]), launches=self.launches,
         )
@@ -138,6 +143,9 @@ def lib() -> ctypes.CDLL:
             fn = getattr(handle, name)
             fn.restype = res
             fn.argtypes = args
+        if handle.fgbd_abi_version() != ABI_VERSION:
+            raise RuntimeError(f"{LIB_PATH} has ABI {handle.fgbd_abi_version()}, this binding expects "
+                               f"{ABI_VERSION}: rebuild it")
         _lib = handle
     return _lib
 

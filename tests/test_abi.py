@@ -57,7 +57,7 @@ def test_only_the_abi_is_exported():
 def test_host_side_checks_without_gpu(so):
     from paper_2401_09721_gb300 import fgbd
     lib = fgbd.lib()
-    assert lib.fgbd_abi_version() == 1
+    assert lib.fgbd_abi_version() == fgbd.ABI_VERSION == 2
     p = fgbd.Params()
     assert lib.fgbd_params_default(ctypes.byref(p)) == 0
     assert (p.bits, p.window, p.fslr_factor, p.q_max) == (10, 1, 2.0, 64)
@@ -77,6 +77,13 @@ def test_host_side_checks_without_gpu(so):
     assert lib.fgbd_ctx_create(100, ctypes.byref(bad), ctypes.byref(out)) == 1
     bad.reserved[0], bad.flags = 0, 2                                       # no such execution flag
     assert lib.fgbd_ctx_create(100, ctypes.byref(bad), ctypes.byref(out)) == 1
+    bad.flags, bad.window = 0, 0                                            # window < 1
+    assert lib.fgbd_ctx_create(100, ctypes.byref(bad), ctypes.byref(out)) == 1
+    bad.window = fgbd.MAX_WINDOW + 1                                        # wider than built
+    assert lib.fgbd_ctx_create(100, ctypes.byref(bad), ctypes.byref(out)) == 7
+    bad.window, bad.variant = 2, fgbd.VARIANT_UNSORTED_PATCH                # link order defined at w = 1 only
+    assert lib.fgbd_ctx_create(100, ctypes.byref(bad), ctypes.byref(out)) == 7
+    assert (fgbd.MAX_WINDOW, fgbd.PATCH_DIM_MAX) == (3, 57)
     assert p.flags == 0 and fgbd.FLAG_FUSED_SELECT == 1
     assert p.variant == 0 and fgbd.VARIANT_NO_FSLR == 1 and fgbd.VARIANT_UNSORTED_PATCH == 2
     assert fgbd.VARIANT_SAME_LINE == 4

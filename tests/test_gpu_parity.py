@@ -35,8 +35,8 @@ def F():
     return fgbd
 
 
-def gpu_frame(F, xyz, rgb, bits, q_max=64, variant=0):
-    ctx = F.Context(max(len(xyz), 1), bits=bits, q_max=q_max, variant=variant)
+def gpu_frame(F, xyz, rgb, bits, q_max=64, variant=0, window=1):
+    ctx = F.Context(max(len(xyz), 1), bits=bits, q_max=q_max, variant=variant, window=window)
     x = torch.from_numpy(np.ascontiguousarray(xyz, dtype=np.int32)).cuda()
     c = torch.from_numpy(np.ascontiguousarray(rgb)).cuda()
     ctx.build_graph(x)
@@ -122,13 +122,13 @@ def check_u8(out8, ref):
     assert diff.max() <= 1
 
 
-def full_check(F, xyz, rgb, bits, q_max=64, variant=0):
+def full_check(F, xyz, rgb, bits, q_max=64, variant=0, window=1):
     no_fslr = bool(variant & F.VARIANT_NO_FSLR)
-    params = orc.Params(bits=bits, q_max=q_max, fslr=not no_fslr,
+    params = orc.Params(bits=bits, window=window, q_max=q_max, fslr=not no_fslr,
                         sorted_patches=not (variant & F.VARIANT_UNSORTED_PATCH),
                         same_line=bool(variant & F.VARIANT_SAME_LINE))
     res = orc.fgbd(xyz, rgb, params)
-    ctx, g = gpu_frame(F, xyz, rgb, bits, q_max, variant)
+    ctx, g = gpu_frame(F, xyz, rgb, bits, q_max, variant, window)
     check_graph(g, res, xyz)
     check_noise(g, res)
     check_fslr(g, res, all_points=no_fslr)
@@ -202,6 +202,90 @@ def test_unsorted_patches_float_colours(F):
     clean = synth.piecewise_colors(xyz, 8, 6, as_float=True)
     noisy = synth.add_noise_f32(clean, 20.0, 6)
     full_check(F, xyz, noisy, 8, variant=3)
+
+
+# ------------------------------------------------------------------ windows w > 1 (K = 6w, D = 3 (6w + 1))
+
+@pytest.mark.parametrize("window", [2, 3])
+def test_wider_windows_sphere_frame(F, window):
+    fr = synth.sphere_frame(20500, 9, 20.0, 0)
+    res, g = full_check(F, fr.xyz, fr.noisy, 9, window=window)
+    assert g["stats"]["patch_dim"] == 3 * (6 * window + 1) and res.noise["n_patches"] > 0
+
+
+@pytest.mark.parametrize("window,sigma", [(2, 10.0), (2, 40.0), (3, 25.0)])
+def test_wider_windows_dense_shell(F, window, sigma):
+    xyz = synth.torso_points(60000, 8, 21)
+    clean = synth.piecewise_colors(xyz, 8, 21)
+    noisy = synth.add_noise_u8(clean, sigma, 22)
+    full_check(F, xyz, noisy, 8, window=window)
+
+
+@pytest.mark.parametrize("window,n,bits,seed", [(2, 7, 3, 30), (3, 33, 4, 31), (2, 4097, 6, 32),
+                                                (3, 8193, 7, 33), (2, 12289, 10, 34), (3, 40000, 9, 35)])
+def test_wider_windows_random_clouds(F, window, n, bits, seed):
+    rng = np.random.default_rng(seed)
+    xyz = rng.integers(0, 1 << bits, size=(n, 3)).astype(np.int32)   # repeated voxels included
+    rgb = rng.integers(0, 256, size=(n, 3)).astype(np.uint8)
+    full_check(F, xyz, rgb, bits, window=window)
+
+
+@pytest.mark.parametrize("window", [2, 3])
+def test_wider_windows_float_colours(F, window):
+    xyz = synth.torso_points(30000, 8, 23)
+    clean = synth.piecewise_colors(xyz, 8, 23, as_float=True)
+    noisy = synth.add_noise_f32(clean, 25.0, 23)
+    full_check(F, xyz, noisy, 8, window=window)
+
+
+@pytest.mark.parametrize("window,variant", [(2, 4), (3, 5)])
+def test_wider_windows_variants(F, window, variant):
+    """Same-line links (and without FSLR) at wider windows, on random clouds
+    with many short scan lines."""
+    rng = np.random.default_rng(40 + window)
+    xyz = rng.integers(0, 1 << 5, size=(9000, 3)).astype(np.int32)
+    rgb = rng.integers(0, 256, size=(9000, 3)).astype(np.uint8)
+    full_check(F, xyz, rgb, 5, variant=variant, window=window)
+
+
+def test_wider_window_empty_and_tiny(F):
+    for n in (0, 1, 2, 13):
+        rng = np.random.default_rng(n)
+        xyz = rng.integers(0, 16, size=(n, 3)).astype(np.int32)
+        rgb = rng.integers(0, 256, size=(n, 3)).astype(np.uint8)
+        if n == 0:
+            ctx = F.Context(16, bits=4, window=2)
+            x = torch.empty((0, 3), dtype=torch.int32, device="cuda")
+            c = torch.empty((0, 3), dtype=torch.uint8, device="cuda")
+            ctx.build_graph(x)
+            ctx.estimate_noise(c)
+            ctx.select_filter(c)
+            st = ctx.stats()
+            assert st["n"] == 0 and st["sigma_est"] == 0.0 and st["q"] == 0
+            ctx.close()
+        else:
+            full_check(F, xyz, rgb, 4, window=2)
+
+
+def test_wider_window_run_matches_separate_calls(F):
+    xyz = synth.torso_points(50000, 9, 24)
+    noisy = synth.add_noise_u8(synth.piecewise_colors(xyz, 9, 24), 20.0, 24)
+    ctx, g = gpu_frame(F, xyz, noisy, 9, window=2)
+    run = F.Context(len(xyz), bits=9, window=2)
+    x = torch.from_numpy(xyz.astype(np.int32)).cuda()
+    c = torch.from_numpy(noisy).cuda()
+    outs = [run.run(x, c, out_dtype=torch.uint8).cpu().numpy() for _ in range(3)]  # direct, captured, replayed
+    st = run.stats()
+    assert st["q"] == g["stats"]["q"] and st["sigma_est"] == g["stats"]["sigma_est"]
+    for o in outs:
+        assert np.array_equal(o, g["out8"])
+    # the differentiable filter keeps six neighbours a row: refused at w > 1
+    z = torch.zeros((len(xyz), 3), dtype=torch.float32, device="cuda")
+    with pytest.raises(F.FgbdError) as e:
+        F.fgbd_filter_forward(run.handle, z, 2, 0.5, 0.0, 1, torch.empty_like(z), len(xyz))
+    assert e.value.status == 7
+    ctx.close()
+    run.close()
 
 
 # ------------------------------------------------------------------ ragged sizes and tiles

@@ -383,6 +383,26 @@ def test_patches_and_covariance_brute_force(seed):
     assert np.allclose(mu, muref, rtol=1e-14)
 
 
+@pytest.mark.parametrize("window,seed", [(2, 0), (2, 1), (3, 2), (3, 3)])
+def test_patches_wider_windows_brute_force(window, seed):
+    """Windows w > 1: K = 6w neighbours, D = 3 (6w + 1) patch entries, each
+    patch in increasing distance order, against the brute-force construction."""
+    rng = np.random.default_rng(200 + seed)
+    xyz = random_cloud(rng, 150, 3, dup_frac=0.05 if seed % 2 else 0.0)
+    colors = rng.integers(0, 256, size=(150, 3))
+    pts = [tuple(int(v) for v in p) for p in xyz]
+    _, _, _, row_ptr, col = graph_of(xyz, 3, window)
+    k = 6 * window
+    A, idx = orc.patch_vectors(xyz, colors, row_ptr, col, k)
+    nb = bf.neighbour_sets(pts, window)
+    ref = bf.patches(pts, colors.tolist(), nb, k)
+    assert A.shape[1] == 3 * (k + 1)
+    assert len(ref) == A.shape[0] and A.shape[0] > 5
+    assert np.array_equal(A, np.array(ref))
+    res = orc.fgbd(xyz, colors.astype(np.uint8), orc.Params(bits=3, window=window))
+    assert res.noise["n_patches"] == A.shape[0] and len(res.noise["eigenvalues"]) == 3 * (k + 1)
+
+
 def test_tail_rule_hand_cases():
     for case in load("tail_rule.json")["cases"]:
         m, tau, s = orc.tail_rule(np.array(case["lambda"], float))
