@@ -405,10 +405,11 @@ fgbd_status do_estimate(fgbd_ctx* ctx, const void* rgb, int32_t dtype, double* s
         FGBD_LAUNCH(ctx, "gather_colors", st,
                     launch_gather_colors(rgb, dtype, n, ctx->gb.perm1, ctx->y8, ctx->yf, st));
     }
-    FGBD_LAUNCH(ctx, "ne_wide", st,
-                launch_ne_wide(n, ctx->params.bits, ctx->params.window, dtype, ctx->gb, ctx->y8, ctx->yf,
-                               ctx->spread, ctx->wne, ctx->sc, sigma_out, ctx->num_sms, st));
-    ctx->launches += n > 0 ? 3 : 2;  // the one counted above and the others of the estimate
+    static const char* const kStage[4] = {"ne_wide_moments", "ne_wide_reduce", "ne_wide_jacobi", "ne_wide_tail"};
+    for (int stage = n > 0 ? 0 : 1; stage < 4; ++stage)
+      FGBD_LAUNCH(ctx, kStage[stage], st,
+                  launch_ne_wide(stage, n, ctx->params.bits, ctx->params.window, dtype, ctx->gb, ctx->y8, ctx->yf,
+                                 ctx->spread, ctx->wne, ctx->sc, sigma_out, ctx->num_sms, st));
     ctx->spec_depth = 0;
     ctx->has_noise = true;
     ctx->noise_rgb = rgb;

@@ -197,9 +197,10 @@ struct WideNe {
 };
 int ne_wide_blocks(int n, int num_sms);
 size_t ne_wide_part_entries(int window);  // D*D + D + 1
-cudaError_t launch_ne_wide(int n, int bits, int window, int dtype, const GraphBufs& gb, const uint32_t* y8,
-                           const float4* yf, float* spread, const WideNe& w, DevScalars* sc, double* sigma_out,
-                           int num_sms, cudaStream_t stream);
+// stage 0 the moments (nothing at n = 0), 1 their reduction, 2 the Jacobi block, 3 the tail rule
+cudaError_t launch_ne_wide(int stage, int n, int bits, int window, int dtype, const GraphBufs& gb,
+                           const uint32_t* y8, const float4* yf, float* spread, const WideNe& w, DevScalars* sc,
+                           double* sigma_out, int num_sms, cudaStream_t stream);
 
 struct FilterArgs {
   int n;

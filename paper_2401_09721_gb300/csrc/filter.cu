@@ -151,9 +151,12 @@ __global__ void k_spread_export(int n, const int32_t* __restrict__ rank1, const 
 int filter_grid(int n, int num_sms, int nx) {
   int per_sm = 0;
   cudaError_t e;
-  if (nx == extra_slots(3)) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_filter<extra_slots(3)>, kFilterThreads, 0);
-  else if (nx == extra_slots(2)) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_filter<extra_slots(2)>, kFilterThreads, 0);
-  else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_filter<0>, kFilterThreads, 0);
+  if (nx == extra_slots(3))
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_filter<extra_slots(3)>, kFilterThreads, 0);
+  else if (nx == extra_slots(2))
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_filter<extra_slots(2)>, kFilterThreads, 0);
+  else
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_filter<0>, kFilterThreads, 0);
   if (e != cudaSuccess || per_sm < 1) per_sm = 1;
   const int need = std::max(1, (n + kFilterThreads - 1) / kFilterThreads);
   return std::max(1, std::min(need, per_sm * num_sms));

@@ -147,9 +147,26 @@ __device__ __forceinline__ float4 eq5_step(const FilterArgs& a, const float4* __
   return xo;
 }
 
+// Slot group g of sorted point k as sorted ids (-1 empty): g = 0 the six
+// window-1 slots (C1 k - 1, k + 1, the c4 slots), g >= 1 the further slots
+// 6 (g - 1) .. 6 (g - 1) + 5 of a window w > 1.
+__device__ __forceinline__ void slot_group(const FilterArgs& a, int k, int n, uint32_t wk, int4 s, int g, int (&o)[6]) {
+  if (g == 0) {
+#pragma unroll
+    for (int i = 0; i < 6; ++i) o[i] = neighbour_of(i, k, n, wk, s, nullptr, 0);
+  } else {
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+      const int v = a.cx[size_t(6 * (g - 1) + i) * size_t(a.cx_stride) + k];
+      o[i] = in_range(v, n) ? v : -1;
+    }
+  }
+}
+
 // The same step at a window w > 1, over the 6 + NX neighbours (NX = 6 (w - 1)
-// further slots): a first pass finds min d2 from the packed codes, a second
-// accumulates, so no per-neighbour array is held in registers.
+// further slots), six at a time so that the loads of a group are issued
+// together: a first pass finds min d2 from the packed codes, a second
+// accumulates.
 template <int NX>
 __device__ __forceinline__ float4 eq5_step_wide(const FilterArgs& a, const float4* __restrict__ src, int k, int n,
                                                 float cexp) {
@@ -159,22 +176,35 @@ __device__ __forceinline__ float4 eq5_step_wide(const FilterArgs& a, const float
   const int4 s = a.c4[k];
   int dmin = INT_MAX;
 #pragma unroll 1
-  for (int j = 0; j < 6 + NX; ++j) {
-    const int o = neighbour_of(j, k, n, wk, s, a.cx, a.cx_stride);
-    if (o >= 0) dmin = min(dmin, sq_dist_c1(ck, a.pk[o] & kCoordMask, a.bits));
+  for (int g = 0; g <= NX / 6; ++g) {
+    int o[6];
+    slot_group(a, k, n, wk, s, g, o);
+    uint32_t c[6];
+#pragma unroll
+    for (int i = 0; i < 6; ++i) c[i] = o[i] >= 0 ? a.pk[o[i]] : 0u;
+#pragma unroll
+    for (int i = 0; i < 6; ++i)
+      if (o[i] >= 0) dmin = min(dmin, sq_dist_c1(ck, c[i] & kCoordMask, a.bits));
   }
   float se = 0.f, sr = 0.f, sgc = 0.f, sb = 0.f;
 #pragma unroll 1
-  for (int j = 0; j < 6 + NX; ++j) {
-    const int o = neighbour_of(j, k, n, wk, s, a.cx, a.cx_stride);
-    if (o < 0) continue;
-    const float4 xo = src ? __ldcg(&src[o]) : x0_of(a, o);
-    const int d2 = sq_dist_c1(ck, __float_as_uint(xo.w) & kCoordMask, a.bits);
-    const float e = exp2f(float(dmin - d2) * cexp);
-    se += e;
-    sr = fmaf(e, xo.x, sr);
-    sgc = fmaf(e, xo.y, sgc);
-    sb = fmaf(e, xo.z, sb);
+  for (int g = 0; g <= NX / 6; ++g) {
+    int o[6];
+    slot_group(a, k, n, wk, s, g, o);
+    float4 xo[6];
+#pragma unroll
+    for (int i = 0; i < 6; ++i)
+      xo[i] = o[i] >= 0 ? (src ? __ldcg(&src[o[i]]) : x0_of(a, o[i])) : xk;
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+      if (o[i] < 0) continue;
+      const int d2 = sq_dist_c1(ck, __float_as_uint(xo[i].w) & kCoordMask, a.bits);
+      const float e = exp2f(float(dmin - d2) * cexp);
+      se += e;
+      sr = fmaf(e, xo[i].x, sr);
+      sgc = fmaf(e, xo[i].y, sgc);
+      sb = fmaf(e, xo[i].z, sb);
+    }
   }
   float4 xo = xk;
   if (se > 0.f) {

@@ -12,11 +12,12 @@
 //                      dp4a sums in int64; float colours: float32 sums per
 //                      batch, then float64.  Each block writes its partial
 //                      sums (no atomics, so the totals do not depend on timing).
-//   k_ne_wide_reduce   the partials summed entry by entry in block order.
+//   k_ne_wide_reduce   the partials summed entry by entry in a fixed order.
 //   k_ne_wide_jacobi   one block: Sigma = S2/N - mu mu^T in float64, then a
 //                      cyclic Jacobi in float32 (round-robin order: in round r
-//                      index i pairs with 2r - i mod D), one coefficient step
-//                      and one update step per round.
+//                      index i pairs with 2r - i mod D) from a Helmert x colour
+//                      warm start, one coefficient step and one update step
+//                      by 2x2 blocks per round.
 //   k_ne_wide_tail     one block per eigenvector: the float64 Rayleigh quotient
 //                      v^T Sigma v / v^T v (second order in the eigenvector
 //                      error); the last block to finish sorts the values, sets
@@ -306,26 +307,45 @@ __global__ void __launch_bounds__(kWThreads) k_ne_moments_wide(int n, int bits, 
   }
 }
 
-// the totals: entry i summed over the blocks' partials in block order; second
-// moments outside the computed tiles (below the diagonal blocks) are 0
+// The totals: block (32 entries) x 8 warps; warp w sums the partial rows
+// w, w + 8, ... of its lane's entry, and the eight warp sums are added in warp
+// order, so the result does not depend on timing.  Second moments outside the
+// computed tiles (below the diagonal blocks) are 0.
+constexpr int kReduceWarps = 8;
+
 template <int DT>
-__global__ void __launch_bounds__(256) k_ne_wide_reduce(const double* __restrict__ part, int blocks, int D,
-                                                        double* __restrict__ tot) {
+__global__ void __launch_bounds__(32 * kReduceWarps) k_ne_wide_reduce(const double* __restrict__ part, int blocks,
+                                                                      int D, double* __restrict__ tot) {
   pdl_wait();
+  __shared__ double s_f[kReduceWarps][32];
+  __shared__ long long s_i[kReduceWarps][32];
   const int P = D * D + D + 1;
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= P) return;
-  const bool used = i >= D * D || (i / D) / 3 <= (i % D) / 3;
-  if (DT == 0) {
-    long long t = 0;
-    if (used)
-      for (int b = 0; b < blocks; ++b) t += reinterpret_cast<const long long*>(part)[size_t(b) * P + i];
-    tot[i] = double(t);  // below 2^53 for any capacity: exact
-  } else {
-    double t = 0.0;
-    if (used)
-      for (int b = 0; b < blocks; ++b) t += part[size_t(b) * P + i];
-    tot[i] = t;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int i = blockIdx.x * 32 + lane;
+  const bool used = i < P && (i >= D * D || (i / D) / 3 <= (i % D) / 3);
+  long long ti = 0;
+  double tf = 0.0;
+  if (used) {
+    if (DT == 0) {
+      const long long* pi = reinterpret_cast<const long long*>(part);
+#pragma unroll 4
+      for (int b = warp; b < blocks; b += kReduceWarps) ti += pi[size_t(b) * P + i];
+    } else {
+#pragma unroll 4
+      for (int b = warp; b < blocks; b += kReduceWarps) tf += part[size_t(b) * P + i];
+    }
+  }
+  s_i[warp][lane] = ti;
+  s_f[warp][lane] = tf;
+  __syncthreads();
+  if (warp == 0 && i < P) {
+    long long a = 0;
+    double f = 0.0;
+    for (int w = 0; w < kReduceWarps; ++w) {
+      a += s_i[w][lane];
+      f += s_f[w][lane];
+    }
+    tot[i] = DT == 0 ? double(a) : f;  // integer totals stay below 2^53 for any capacity: exact
   }
 }
 
@@ -336,13 +356,34 @@ __device__ __forceinline__ int round_partner(int i, int r) {
   if (p >= D) p -= D;
   return p;
 }
+// v mod D for v in (-D, 2D)
+template <int D>
+__device__ __forceinline__ int wrap_d(int v) {
+  return v < 0 ? v + D : (v >= D ? v - D : v);
+}
+
+// Entry (i, k) of the Helmert basis of R^T: column 0 is uniform, column k >= 1
+// is (1, ..., 1, -k, 0, ..., 0) / sqrt(k (k + 1)) with k ones.
+__device__ __forceinline__ float helmert(int i, int k, int T) {
+  if (k == 0) return rsqrtf(float(T));
+  const float inv = rsqrtf(float(k * (k + 1)));
+  return i < k ? inv : (i == k ? -float(k) * inv : 0.f);
+}
 
 // One block: the covariance, then the float32 Jacobi.  D is odd, so in round
 // r every pair {i, j} with i + j = 2r (mod D) is rotated and index r rests;
-// each pair meets once per sweep.  A pair is rotated while |a_pq| > 2e-7
-// ||diag A|| (the float32 resolution of the matrix); the iteration ends at the
-// first round after which no off-diagonal entry is above that, or after
-// kWMaxSweeps sweeps.  Without patches the results are written here (zero).
+// each pair meets once per sweep.  Group g of round r is {r} for g = 0 and the
+// pair {r + g, r - g} (mod D) for g >= 1; a round updates A by (group, group)
+// blocks with g <= h (each written with its mirror image, so A stays exactly
+// symmetric: separate roundings of a_ij and a_ji could leave a pair whose
+// a_pq sits above the threshold and a_qp below it unrotated for ever) and V by
+// (row, group).  The start is V0 = H_T (x) Qc (T = D / 3 patch points; H_T
+// their Helmert basis, Qc the eigenvectors of the mean 3x3 colour covariance),
+// which removes about a quarter of the rounds.  A pair is rotated while
+// |a_pq| > 2e-7 ||diag A|| (the float32 resolution of the matrix); the
+// iteration ends at the first round after which no off-diagonal entry is
+// above that, or after kWMaxSweeps sweeps.  Without patches the results are
+// written here (zero).
 template <int D>
 __global__ void __launch_bounds__(kWJacobiThreads) k_ne_wide_jacobi(const double* __restrict__ tot,
                                                                     double* __restrict__ S,
@@ -350,10 +391,16 @@ __global__ void __launch_bounds__(kWJacobiThreads) k_ne_wide_jacobi(const double
                                                                     DevScalars* __restrict__ sc,
                                                                     double* __restrict__ sigma_out) {
   pdl_wait();
-  static_assert(D & 1, "the round-robin schedule assumes an odd dimension");
+  static_assert(D % 6 == 3, "D = 3 T with T odd: the round-robin schedule needs an odd dimension");
+  constexpr int T = D / 3;
+  constexpr int G = (D + 1) / 2;       // groups of a round: the resting index and (D - 1) / 2 pairs
+  constexpr int NA = G * (G + 1) / 2;  // (group, group) blocks with g <= h
+  constexpr int NV = D * G;            // (row of V, group)
   __shared__ float Ab[2][D * D];
   __shared__ float V[D * D];
   __shared__ float2 co[D];
+  __shared__ uint16_t s_blk[NA];
+  __shared__ float s_qc[3][3];
   const int tid = threadIdx.x;
   const double npd = tot[D * D + D];
   if (tid == 0) sc->n_patches = (unsigned long long)npd;
@@ -371,14 +418,64 @@ __global__ void __launch_bounds__(kWJacobiThreads) k_ne_wide_jacobi(const double
     return;
   }
   const double inv_n = 1.0 / npd;
+  float* Sf = Ab[0];  // Sigma in float32 until the warm start replaces it
   for (int e = tid; e < D * D; e += kWJacobiThreads) {
     const int r = e / D, c = e % D;
     const int rr = min(r, c), cc = max(r, c);
     const double mr = tot[D * D + rr] * inv_n, mc = tot[D * D + cc] * inv_n;
     const double v = tot[rr * D + cc] * inv_n - mr * mc;
     S[e] = v;
-    Ab[0][e] = float(v);
-    V[e] = r == c ? 1.f : 0.f;
+    Sf[e] = float(v);
+  }
+  for (int t = tid; t < NA; t += kWJacobiThreads) {
+    int b = t, g = 0;
+    while (b >= G - g) {
+      b -= G - g;
+      ++g;
+    }
+    s_blk[t] = uint16_t((g << 8) | (g + b));
+  }
+  __syncthreads();
+  if (tid < 9) {
+    const int a = tid / 3, b = tid % 3;
+    float c = 0.f;
+    for (int i = 0; i < T; ++i) c += Sf[(3 * i + a) * D + 3 * i + b];
+    s_qc[a][b] = c * (1.f / float(T));
+  }
+  __syncthreads();
+  if (tid == 0) colour_basis(s_qc);
+  __syncthreads();
+  for (int e = tid; e < D * D; e += kWJacobiThreads) {
+    const int r = e / D, c = e % D;
+    V[e] = helmert(r / 3, c / 3, T) * s_qc[r % 3][c % 3];
+  }
+  __syncthreads();
+  // A0 = V0^T Sigma V0: Sigma V0 into Ab[1], then the upper triangle of V0^T (Sigma V0), mirrored
+  for (int e = tid; e < D * D; e += kWJacobiThreads) {
+    const int r = e / D, c = e % D;
+    float t0 = 0.f, t1 = 0.f, t2 = 0.f;
+#pragma unroll 3
+    for (int k = 0; k < D; k += 3) {
+      t0 = fmaf(Sf[r * D + k], V[k * D + c], t0);
+      t1 = fmaf(Sf[r * D + k + 1], V[(k + 1) * D + c], t1);
+      t2 = fmaf(Sf[r * D + k + 2], V[(k + 2) * D + c], t2);
+    }
+    Ab[1][e] = t0 + t1 + t2;
+  }
+  __syncthreads();
+  for (int e = tid; e < D * D; e += kWJacobiThreads) {
+    const int r = e / D, c = e % D;
+    if (r > c) continue;
+    float t0 = 0.f, t1 = 0.f, t2 = 0.f;
+#pragma unroll 3
+    for (int k = 0; k < D; k += 3) {
+      t0 = fmaf(V[k * D + r], Ab[1][k * D + c], t0);
+      t1 = fmaf(V[(k + 1) * D + r], Ab[1][(k + 1) * D + c], t1);
+      t2 = fmaf(V[(k + 2) * D + r], Ab[1][(k + 2) * D + c], t2);
+    }
+    const float v = t0 + t1 + t2;
+    Ab[0][r * D + c] = v;
+    Ab[0][c * D + r] = v;
   }
   __syncthreads();
   float dsq = 0.f;
@@ -405,31 +502,40 @@ __global__ void __launch_bounds__(kWJacobiThreads) k_ne_wide_jacobi(const double
     }
     __syncthreads();
     off = false;
-    // J^T A J entry by entry: sum over u in {i, pi}, v in {j, pj} of J[u][i] A[u][v] J[v][j].
-    // Only i <= j is computed and mirrored: the two roundings of a_ij and a_ji
-    // would differ, and a pair whose a_pq sat just above the threshold with
-    // a_qp just below would then never be rotated again.
-    for (int e = tid; e < D * D; e += kWJacobiThreads) {
-      const int i = e / D, j = e % D;
-      if (i > j) continue;
-      const int pi = round_partner<D>(i, r), pj = round_partner<D>(j, r);
-      const float2 ci = co[i], cj = co[j];
-      const float row_i = fmaf(cj.x, A[i * D + j], cj.y * A[i * D + pj]);
-      const float row_pi = fmaf(cj.x, A[pi * D + j], cj.y * A[pi * D + pj]);
-      const float v = fmaf(ci.x, row_i, ci.y * row_pi);
-      An[i * D + j] = v;
-      An[j * D + i] = v;
-      off |= i != j && fabsf(v) > thr;
-    }
-    // V J in place: the thread of (row x, i < pi) owns both entries it changes
-    for (int e = tid; e < D * D; e += kWJacobiThreads) {
-      const int x = e / D, i = e % D;
-      const int pi = round_partner<D>(i, r);
-      if (pi <= i) continue;
-      const float2 ci = co[i], cp = co[pi];
-      const float vi = V[x * D + i], vp = V[x * D + pi];
-      V[x * D + i] = fmaf(ci.x, vi, ci.y * vp);
-      V[x * D + pi] = fmaf(cp.x, vp, cp.y * vi);
+    for (int t = tid; t < NA + NV; t += kWJacobiThreads) {
+      if (t < NA) {
+        // block (g, h): T = A_blk J_h, then J_g^T T; J_g = [[alpha_x0, beta_x1], [beta_x0, alpha_x1]]
+        const int ag = s_blk[t] >> 8, ah = s_blk[t] & 255;
+        const int x0 = wrap_d<D>(r + ag), x1 = wrap_d<D>(r - ag), y0 = wrap_d<D>(r + ah), y1 = wrap_d<D>(r - ah);
+        const float2 cx0 = co[x0], cx1 = co[x1], cy0 = co[y0], cy1 = co[y1];
+        const float a00 = A[x0 * D + y0], a01 = A[x0 * D + y1], a10 = A[x1 * D + y0], a11 = A[x1 * D + y1];
+        const float t00 = fmaf(a00, cy0.x, a01 * cy0.y), t01 = fmaf(a00, cy1.y, a01 * cy1.x);
+        const float t10 = fmaf(a10, cy0.x, a11 * cy0.y), t11 = fmaf(a10, cy1.y, a11 * cy1.x);
+        const float n00 = fmaf(cx0.x, t00, cx0.y * t10), n01 = fmaf(cx0.x, t01, cx0.y * t11);
+        const float n10 = fmaf(cx1.y, t00, cx1.x * t10), n11 = fmaf(cx1.y, t01, cx1.x * t11);
+        An[x0 * D + y0] = n00;
+        An[y0 * D + x0] = n00;
+        An[x1 * D + y1] = n11;
+        An[y1 * D + x1] = n11;
+        An[x0 * D + y1] = n01;
+        An[y1 * D + x0] = n01;
+        off |= (x0 != y0 && fabsf(n00) > thr) || (x1 != y1 && fabsf(n11) > thr) || (x0 != y1 && fabsf(n01) > thr);
+        if (ag != ah) {
+          // off the diagonal the fourth entry is distinct; on it, it is the mirror of n01
+          An[x1 * D + y0] = n10;
+          An[y0 * D + x1] = n10;
+          off |= x1 != y0 && fabsf(n10) > thr;
+        }
+      } else {
+        // row x of V in the columns of group h (the resting column, h = 0, is unchanged)
+        const int v = t - NA, x = v / G, h = v % G;
+        if (h == 0) continue;
+        const int y0 = wrap_d<D>(r + h), y1 = wrap_d<D>(r - h);
+        const float2 c0 = co[y0], c1 = co[y1];
+        const float v0 = V[x * D + y0], v1 = V[x * D + y1];
+        V[x * D + y0] = fmaf(c0.x, v0, c0.y * v1);
+        V[x * D + y1] = fmaf(c1.x, v1, c1.y * v0);
+      }
     }
     big = __syncthreads_or(off) != 0;
     cur ^= 1;
@@ -546,32 +652,37 @@ __global__ void __launch_bounds__(kWTailThreads) k_ne_wide_tail(const double* __
 }
 
 template <int W>
-cudaError_t launch_wide(int n, int bits, int dtype, const GraphBufs& gb, const uint32_t* y8, const float4* yf,
-                        float* spread, const WideNe& w, DevScalars* sc, double* sigma_out, int num_sms,
-                        cudaStream_t stream) {
+cudaError_t launch_wide(int stage, int n, int bits, int dtype, const GraphBufs& gb, const uint32_t* y8,
+                        const float4* yf, float* spread, const WideNe& w, DevScalars* sc, double* sigma_out,
+                        int num_sms, cudaStream_t stream) {
   constexpr int D = patch_dim<W>();
   const int P = D * D + D + 1;
   const int blocks = std::min(ne_wide_blocks(n, num_sms), w.blocks);
-  cudaError_t e = cudaSuccess;
-  if (n > 0) {
-    e = dtype == 0 ? launch_kernel(k_ne_moments_wide<W, 0>, dim3(blocks), dim3(kWThreads), 0, stream, false, n, bits,
-                                   gb, y8, yf, spread, w.part)
-                   : launch_kernel(k_ne_moments_wide<W, 1>, dim3(blocks), dim3(kWThreads), 0, stream, false, n, bits,
-                                   gb, y8, yf, spread, w.part);
-    if (e != cudaSuccess) return e;
+  switch (stage) {
+    case 0:
+      if (n <= 0) return cudaSuccess;
+      return dtype == 0 ? launch_kernel(k_ne_moments_wide<W, 0>, dim3(blocks), dim3(kWThreads), 0, stream, false, n,
+                                        bits, gb, y8, yf, spread, w.part)
+                        : launch_kernel(k_ne_moments_wide<W, 1>, dim3(blocks), dim3(kWThreads), 0, stream, false, n,
+                                        bits, gb, y8, yf, spread, w.part);
+    case 1: {
+      const int used = n > 0 ? blocks : 0;
+      const dim3 rgrid((P + 31) / 32), rblock(32 * kReduceWarps);
+      return dtype == 0 ? launch_kernel(k_ne_wide_reduce<0>, rgrid, rblock, 0, stream, false,
+                                        static_cast<const double*>(w.part), used, D, w.tot)
+                        : launch_kernel(k_ne_wide_reduce<1>, rgrid, rblock, 0, stream, false,
+                                        static_cast<const double*>(w.part), used, D, w.tot);
+    }
+    case 2:
+      return launch_kernel(k_ne_wide_jacobi<D>, dim3(1), dim3(kWJacobiThreads), 0, stream, false,
+                           static_cast<const double*>(w.tot), w.S, w.V, sc, sigma_out);
+    case 3:
+      return launch_kernel(k_ne_wide_tail<D>, dim3(D), dim3(kWTailThreads), 0, stream, false,
+                           static_cast<const double*>(w.tot), static_cast<const double*>(w.S),
+                           static_cast<const float*>(w.V), w.lam, w.done, sc, sigma_out);
+    default:
+      return cudaErrorInvalidValue;
   }
-  const int used = n > 0 ? blocks : 0;
-  e = dtype == 0 ? launch_kernel(k_ne_wide_reduce<0>, dim3((P + 255) / 256), dim3(256), 0, stream, false,
-                                 static_cast<const double*>(w.part), used, D, w.tot)
-                 : launch_kernel(k_ne_wide_reduce<1>, dim3((P + 255) / 256), dim3(256), 0, stream, false,
-                                 static_cast<const double*>(w.part), used, D, w.tot);
-  if (e != cudaSuccess) return e;
-  e = launch_kernel(k_ne_wide_jacobi<D>, dim3(1), dim3(kWJacobiThreads), 0, stream, false,
-                    static_cast<const double*>(w.tot), w.S, w.V, sc, sigma_out);
-  if (e != cudaSuccess) return e;
-  return launch_kernel(k_ne_wide_tail<D>, dim3(D), dim3(kWTailThreads), 0, stream, false,
-                       static_cast<const double*>(w.tot), static_cast<const double*>(w.S),
-                       static_cast<const float*>(w.V), w.lam, w.done, sc, sigma_out);
 }
 
 }  // namespace
@@ -583,13 +694,15 @@ size_t ne_wide_part_entries(int window) {
   return D * D + D + 1;
 }
 
-cudaError_t launch_ne_wide(int n, int bits, int window, int dtype, const GraphBufs& gb, const uint32_t* y8,
-                           const float4* yf, float* spread, const WideNe& w, DevScalars* sc, double* sigma_out,
-                           int num_sms, cudaStream_t stream) {
+cudaError_t launch_ne_wide(int stage, int n, int bits, int window, int dtype, const GraphBufs& gb,
+                           const uint32_t* y8, const float4* yf, float* spread, const WideNe& w, DevScalars* sc,
+                           double* sigma_out, int num_sms, cudaStream_t stream) {
   if (gb.nx != extra_slots(window) || !w.part || !w.tot || !w.S || !w.V || !w.lam || !w.done)
     return cudaErrorInvalidValue;
-  if (window == 2) return launch_wide<2>(n, bits, dtype, gb, y8, yf, spread, w, sc, sigma_out, num_sms, stream);
-  if (window == 3) return launch_wide<3>(n, bits, dtype, gb, y8, yf, spread, w, sc, sigma_out, num_sms, stream);
+  if (window == 2)
+    return launch_wide<2>(stage, n, bits, dtype, gb, y8, yf, spread, w, sc, sigma_out, num_sms, stream);
+  if (window == 3)
+    return launch_wide<3>(stage, n, bits, dtype, gb, y8, yf, spread, w, sc, sigma_out, num_sms, stream);
   return cudaErrorInvalidValue;
 }
 
