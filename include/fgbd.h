@@ -245,8 +245,9 @@ fgbd_status fgbd_run_reuse(fgbd_ctx* ctx, const int32_t* xyz, int64_t n, const v
  * first launches set kernel attributes).  Like fgbd_run, the second call with
  * the same contexts and buffers records a CUDA graph of the whole batch (kept
  * by ctxs[0], up to 4 of them) and later calls launch it.
- * Errors: FGBD_EINVAL (any argument) and FGBD_ENOTIMPL (window != 1), both
- * checked before anything is enqueued; FGBD_ECUDA. */
+ * Contexts of any window may share a batch.
+ * Errors: FGBD_EINVAL (any argument), checked before anything is enqueued;
+ * FGBD_ECUDA. */
 #define FGBD_BATCH_MAX 64
 fgbd_status fgbd_run_batch(fgbd_ctx* const* ctxs, const int32_t* const* xyz, const int64_t* n,
                            const void* const* rgb_in, const int32_t* in_dtype, void* const* rgb_out,

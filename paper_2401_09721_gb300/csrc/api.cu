@@ -966,7 +966,6 @@ fgbd_status fgbd_run_batch(fgbd_ctx* const* ctxs, const int32_t* const* xyz, con
     if (!dtype_ok(in_dtype[f]) || !dtype_ok(out_dtype[f])) return FGBD_EINVAL;
     if (n[f] < 0 || n[f] > c->capacity) return FGBD_EINVAL;
     if (n[f] > 0 && (!xyz[f] || !rgb_in[f] || !rgb_out[f])) return FGBD_EINVAL;
-    if (c->params.window != 1) return FGBD_ENOTIMPL;
   }
   DeviceGuard g(ctxs[0]->device);
   const cudaStream_t st = as_stream(stream);

@@ -42,8 +42,8 @@ def _dev(a):
     return torch.from_numpy(np.ascontiguousarray(a)).cuda()
 
 
-def _plain(F, xyz, rgb, bits):
-    ctx = F.Context(max(len(xyz), 1), bits=bits)
+def _plain(F, xyz, rgb, bits, window=1):
+    ctx = F.Context(max(len(xyz), 1), bits=bits, window=window)
     out = ctx.run(_dev(xyz.astype(np.int32)), _dev(rgb), out_dtype=torch.float32)
     ctx.sync()
     res = (out.cpu().numpy(), ctx.stats(), ctx.orders().cpu().numpy())
@@ -67,6 +67,32 @@ def test_batch_equals_plain_runs(F):
             assert st[key] == ref_st[key], key
         if len(xyz):
             assert np.array_equal(ctx.orders().cpu().numpy(), ref_orders)
+    for ctx in ctxs:
+        ctx.close()
+
+
+def test_batch_of_mixed_windows_equals_plain_runs(F):
+    """Contexts of windows 1, 2 and 3 in one batch, run directly, then recorded
+    and replayed: every frame equals its own plain run bit for bit."""
+    frames = _frames()[:4]
+    windows = [2, 3, 1, 2]
+    ctxs = [F.Context(len(x), bits=b, window=w) for (x, _, b), w in zip(frames, windows)]
+    xs = [_dev(x.astype(np.int32)) for x, _, _ in frames]
+    cs = [_dev(c) for _, c, _ in frames]
+    outs = [torch.empty((len(x), 3), dtype=torch.float32, device="cuda") for x, _, _ in frames]
+    refs = [_plain(F, xyz, rgb, bits, w) for (xyz, rgb, bits), w in zip(frames, windows)]
+    for _ in range(3):   # direct, recorded, replayed
+        for o in outs:
+            o.fill_(-1.0)
+        F.Context.run_batch(ctxs, xs, cs, outs=outs)
+        torch.cuda.synchronize()
+        for ctx, out, (ref_out, ref_st, _), w in zip(ctxs, outs, refs, windows):
+            ctx.sync()
+            st = ctx.stats()
+            assert np.array_equal(out.cpu().numpy(), ref_out), w
+            assert st["patch_dim"] == 3 * (6 * w + 1)
+            for key in ("n_edges", "n_patches", "m", "q", "sigma_est", "n_keep"):
+                assert st[key] == ref_st[key], (w, key)
     for ctx in ctxs:
         ctx.close()
 
