@@ -93,3 +93,33 @@ def test_host_side_checks_without_gpu(so):
     assert lib.fgbd_status_str(0) == b"FGBD_OK"
     assert lib.fgbd_status_str(5).startswith(b"FGBD_ETIMEOUT")
     assert lib.fgbd_debug_set_wait_limit(None, 0) == 1
+
+
+def test_binding_structs_match_the_header_layout(tmp_path):
+    """The ctypes structures have the size and field offsets that a C compiler
+    gives the header's structs (a field added on one side only fails here)."""
+    import shutil
+    import subprocess
+    from paper_2401_09721_gb300 import fgbd
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = {"fgbd_params": fgbd.Params, "fgbd_stats": fgbd.Stats}
+    lines = ["#include <stddef.h>", "#include <stdio.h>", '#include "fgbd.h"', "int main(void) {"]
+    for cname, py in structs.items():
+        lines.append(f'  printf("{cname} size %zu\\n", sizeof({cname}));')
+        for field, _ in py._fields_:
+            lines.append(f'  printf("{cname} {field} %zu\\n", offsetof({cname}, {field}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    r = subprocess.run([cc, "-std=c99", "-I", os.path.dirname(HEADER), str(src), "-o", str(exe)],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")
+    got = {tuple(line.split()[:2]): int(line.split()[2]) for line in out if line.strip()}
+    for cname, py in structs.items():
+        assert got[(cname, "size")] == ctypes.sizeof(py), cname
+        for field, _ in py._fields_:
+            assert got[(cname, field)] == getattr(py, field).offset, (cname, field)
