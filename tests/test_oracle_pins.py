@@ -104,17 +104,18 @@ def test_graph_matches_brute_force(seed):
     assert orc.sigma_g(xyz, row_ptr, col) == pytest.approx(bf.sigma_g(pts, nb), rel=1e-12)
 
 
-def test_graph_invariants():
+@pytest.mark.parametrize("window", [1, 2, 3])
+def test_graph_invariants(window):
     rng = np.random.default_rng(5)
     xyz = random_cloud(rng, 400, 5, dup_frac=0.05)
-    _, _, edges, row_ptr, col = graph_of(xyz, 5)
+    _, _, edges, row_ptr, col = graph_of(xyz, 5, window)
     n = len(xyz)
     A = np.zeros((n, n), int)
     rows = np.repeat(np.arange(n), np.diff(row_ptr))
     A[rows, col] = 1
     assert (A == A.T).all()                 # symmetric
     assert np.trace(A) == 0                 # no self loops
-    assert np.diff(row_ptr).max() <= 6      # at most 2 neighbours x 3 codes
+    assert np.diff(row_ptr).max() <= 6 * window   # at most 2w neighbours x 3 codes
     assert (np.diff(row_ptr) >= 1).all()    # n >= 2: every point is linked
     for i in range(n):                      # rows sorted by column
         r = col[row_ptr[i]:row_ptr[i + 1]]
