@@ -46,7 +46,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-path measurement")
     ap.add_argument("--no-diff", action="store_true", help="skip the differentiable-filter measurement")
-    ap.add_argument("--stream-frames", type=int, default=40, help="frames of the streaming measurement (0: skip)")
+    ap.add_argument("--stream-frames", type=int, default=300, help="frames of the streaming measurement (0: skip)")
     return ap.parse_args()
 
 
@@ -58,6 +58,36 @@ def make_frames(n_points, seed=0):
     return xyz, clean, noisy
 
 
+# ------------------------------------------------------------------ input generation
+
+_STREAM_SEQ = None
+
+
+def _stream_frame(t):
+    global _STREAM_SEQ
+    from paper_2401_09721_gb300 import synth
+    if _STREAM_SEQ is None:
+        _STREAM_SEQ = synth.StreamSequence(frames=300)
+    return _STREAM_SEQ.frame(t)
+
+
+def _batch_frame(f):
+    from paper_2401_09721_gb300 import synth
+    return synth.batch_frame(f)
+
+
+def generate(fn, items):
+    """[fn(i) for i in items], computed by a pool of spawned processes (one per
+    host core); spawned, not forked, so that it is safe after CUDA is in use."""
+    import multiprocessing as mp
+    items = list(items)
+    workers = max(1, min(len(items), len(os.sched_getaffinity(0))))
+    if workers == 1:
+        return [fn(i) for i in items]
+    with mp.get_context("spawn").Pool(workers) as pool:
+        return pool.map(fn, items, chunksize=1)
+
+
 # ------------------------------------------------------------------ batched path
 
 def measure_batched(fgbd, torch, dev, stream, flush, repeats=3):
@@ -65,8 +95,7 @@ def measure_batched(fgbd, torch, dev, stream, flush, repeats=3):
     the same frames through 16 sequential fgbd_run calls, one fgbd_run_batch call,
     and that call replayed from a CUDA graph.  Device time per pass over the 16
     frames, L2 flushed before each pass (not timed)."""
-    from paper_2401_09721_gb300 import synth
-    frames = synth.batch_frames(16)
+    frames = generate(_batch_frame, range(16))
     ctxs = [fgbd.Context(fr.n, bits=10) for fr in frames]
     xs = [torch.from_numpy(fr.xyz).to(dev) for fr in frames]
     cs = [torch.from_numpy(fr.noisy).to(dev) for fr in frames]
@@ -181,16 +210,14 @@ def measure_differentiable(fgbd, torch, dev, stream, steps=200, q=4):
 
 # ------------------------------------------------------------------ streaming mode
 
-def measure_streaming(fgbd, torch, dev, stream, frames=40):
-    """The first `frames` frames of a 300-frame moving sphere (~1.0M points at
+def measure_streaming(fgbd, torch, dev, stream, frames=300):
+    """The first `frames` frames (all 300 by default) of a 300-frame moving sphere (~1.0M points at
     b = 10, sigma = 25, synth.StreamSequence): (a) the full method on every
     frame, (b) the noise estimate and q search on every 10th frame only, the
     others reusing the previous q (Section 3 (2)), (c) every frame in batches
     of 4 through the batched path.  Device-timed per frame (per batch in (c));
     PSNR of the uint8 output against the clean colours."""
-    from paper_2401_09721_gb300 import synth
-    seq = synth.StreamSequence(frames=300)
-    fr = [seq.frame(t) for t in range(frames)]
+    fr = generate(_stream_frame, range(frames))
     xs = [torch.from_numpy(f.xyz).to(dev) for f in fr]
     cs = [torch.from_numpy(f.noisy).to(dev) for f in fr]
     clean = [torch.from_numpy(f.clean).to(dev) for f in fr]
@@ -244,13 +271,14 @@ def measure_streaming(fgbd, torch, dev, stream, frames=40):
 
 # ------------------------------------------------------------------ CPU oracle
 
-def _oracle_child(path, out_path):
+def _oracle_child(path, out_path, which):
     os.environ.setdefault("OMP_NUM_THREADS", "1")
     from oracle import fgbd_oracle as orc
     d = np.load(path)
-    xyz, rgbs = d["xyz"], [d[f"rgb{k}"] for k in range(int(d["k"]))]
+    xyz = d["xyz"]
     times = []
-    for rgb in rgbs:
+    for k in which:
+        rgb = d[f"rgb{k}"]
         t0 = time.perf_counter()
         orc.fgbd(xyz, rgb, orc.Params(bits=BITS))
         times.append(time.perf_counter() - t0)
@@ -258,17 +286,67 @@ def _oracle_child(path, out_path):
         json.dump({"times": times, "n": int(xyz.shape[0])}, fh)
 
 
-def time_oracle(xyz, rgbs):
-    """Run the oracle in a fresh single-threaded process; return per-frame seconds."""
+def host_cores():
+    """Cores this process may run on, and the CPU model (lscpu)."""
+    cores = len(os.sched_getaffinity(0))
+    model = "unknown"
+    try:
+        out = subprocess.run(["lscpu"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True,
+                             timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return cores, model
+
+
+def time_oracle(xyz, rgbs, procs=1):
+    """Run the oracle (as it stands, NumPy float64, one thread per process) on
+    every colour array of `rgbs` over the frame `xyz`, spread over `procs`
+    concurrent fresh processes.  Returns (wall seconds of the whole run, the
+    per-frame seconds).  With procs = 1 the frames run one after another."""
+    procs = max(1, min(procs, len(rgbs)))
     with tempfile.TemporaryDirectory() as td:
         path = os.path.join(td, "frame.npz")
-        out = os.path.join(td, "t.json")
-        np.savez(path, xyz=xyz, k=len(rgbs), **{f"rgb{k}": r for k, r in enumerate(rgbs)})
+        np.savez(path, xyz=xyz, **{f"rgb{k}": r for k, r in enumerate(rgbs)})
         env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
-        code = f"import sys; sys.path.insert(0, {ROOT!r}); import bench; bench._oracle_child({path!r}, {out!r})"
-        subprocess.run([sys.executable, "-c", code], check=True, env=env, cwd=ROOT)
-        with open(out) as fh:
-            return json.load(fh)["times"]
+        children = []
+        t0 = time.perf_counter()
+        for p in range(procs):
+            which = list(range(p, len(rgbs), procs))
+            out = os.path.join(td, f"t{p}.json")
+            code = (f"import sys; sys.path.insert(0, {ROOT!r}); import bench; "
+                    f"bench._oracle_child({path!r}, {out!r}, {which!r})")
+            children.append((out, subprocess.Popen([sys.executable, "-c", code], env=env, cwd=ROOT)))
+        for _, ch in children:
+            if ch.wait() != 0:
+                raise RuntimeError("oracle process failed")
+        wall = time.perf_counter() - t0
+        times = []
+        for out, _ in children:
+            with open(out) as fh:
+                times += json.load(fh)["times"]
+        return wall, times
+
+
+def cpu_baseline(xyz, noisy):
+    """The oracle on full frames of the workload: one frame on one thread, then
+    one frame per host core, all at once (every core busy)."""
+    n = xyz.shape[0]
+    cores, model = host_cores()
+    _, t1 = time_oracle(xyz, [noisy[2]], procs=1)
+    rgbs = [noisy[k % len(noisy)] for k in range(cores)]
+    wall, tk = time_oracle(xyz, rgbs, procs=cores)
+    return {"value": cores * n / wall / 1e6, "unit": "Mpoints/s", "cores": cores, "kind": "oracle",
+            "cpu_model": model,
+            "sample": f"{cores} full {n}-point frames of this workload (sigma cycling 10..50), one per host core, "
+                      f"run at once in {cores} single-threaded processes of the NumPy float64 oracle: "
+                      f"{wall:.1f} s wall",
+            "one_core": {"value": n / t1[0] / 1e6, "unit": "Mpoints/s", "cores": 1,
+                         "sample": f"one full {n}-point frame (sigma 30), one thread, {t1[0]:.1f} s"},
+            "all_cores_frame_s": {"mean": float(np.mean(tk)), "max": float(np.max(tk))}}
 
 
 def max_over_ranks(values, dist=None, device="cpu"):
@@ -292,21 +370,26 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    # a bounded sample of the workload: a 100k-point frame from the same generator
-    n_sample = min(args.points, 100_000)
-    xyz, _, noisy = make_frames(n_sample)
-    rgbs = [noisy[k % len(noisy)] for k in range(args.warmup + args.steps)]
-    times = time_oracle(xyz, rgbs)[args.warmup:]
-    total = sum(times)
-    value = n_sample * len(times) / total / 1e6
+    # the full workload frame, one frame per step; the frames of the run are
+    # spread over the host cores (one single-threaded oracle process per core)
+    xyz, _, noisy = make_frames(args.points)
+    n = xyz.shape[0]
+    cores, model = host_cores()
+    if args.warmup > 0:
+        time_oracle(xyz, [noisy[k % len(noisy)] for k in range(min(args.warmup, cores))], procs=cores)
+    rgbs = [noisy[k % len(noisy)] for k in range(args.steps)]
+    wall, times = time_oracle(xyz, rgbs, procs=cores)
+    value = n * len(rgbs) / wall / 1e6
+    used = min(cores, len(rgbs))
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "Mpoints/s", "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / len(times),
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * wall / len(rgbs),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": workload_config(args.points),
-        "cpu_baseline": {"value": value, "unit": "Mpoints/s", "cores": 1, "kind": "oracle",
-                         "sample": f"{n_sample}-point torso frame (same generator, 10-bit), one frame per step, "
-                                   f"sigma cycling 10..50; NumPy float64 oracle, 1 thread"},
+        "config": workload_config(n),
+        "cpu_baseline": {"value": value, "unit": "Mpoints/s", "cores": used, "kind": "oracle", "cpu_model": model,
+                         "sample": f"{len(rgbs)} full {n}-point torso frames of this workload, one per step "
+                                   f"(sigma cycling 10..50), spread over {used} single-threaded processes of the "
+                                   f"NumPy float64 oracle; {wall:.1f} s wall, {float(np.mean(times)):.1f} s a frame"},
         "e2e": {"value": value, "unit": "Mpoints/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -525,14 +608,14 @@ def run_fgbd(args):
         b = algorithmic_bytes(name, n, extra_steps=extra_steps)
         kernels[name] = {"ms": avg, "launches_per_step": len(lst) / len(cols),
                          "algo_bytes": b, "gbs": (b / (avg / 1e3) / 1e9) if b and avg > 0 else None}
-    # the kernel with the largest share of the step among those that move
-    # compulsory bytes (the one-block eigen step has none); the launches of one
-    # kernel function (the five sort passes) count as one kernel
+    # the dominant kernel: the largest share of the step; the launches of one
+    # kernel function (the sort passes) count as one kernel.  Every kernel in
+    # the step has algorithmic bytes (the estimate launch: its stored filter
+    # steps; its eigen block moves none).
     groups = {}
     for name, kd in kernels.items():
         groups.setdefault(kernel_group(name), []).append(kd)
-    # the estimate launch is timed by its one-block eigen step (its stored filter steps run beside it)
-    movers = [g for g in groups if all(kd["algo_bytes"] for kd in groups[g]) and g != "ne_finalize"]
+    movers = [g for g in groups if all(kd["algo_bytes"] for kd in groups[g])]
     dom = max(movers, key=lambda g: sum(kd["ms"] * kd["launches_per_step"] for kd in groups[g]))
     members = groups[dom]
     dom_ms = float(np.mean([kd["ms"] for kd in members]))
@@ -543,9 +626,21 @@ def run_fgbd(args):
     tr = read_traffic().get(dom)
     if tr is not None and tr[0] == build._digest()[:16]:
         traffic = tr[2] * n / tr[1]
+    step_kernel_ms = sum(kd["ms"] * kd["launches_per_step"] for kd in kernels.values())
+    table = {}
+    for name, kd in sorted(kernels.items(), key=lambda it: -it[1]["ms"] * it[1]["launches_per_step"]):
+        table[name] = {"ms": round(kd["ms"], 5), "per_step": kd["launches_per_step"],
+                       "share": round(kd["ms"] * kd["launches_per_step"] / step_kernel_ms, 4),
+                       "algo_bytes": kd["algo_bytes"],
+                       "gbs": None if kd["gbs"] is None else round(kd["gbs"], 1),
+                       "frac": None if kd["gbs"] is None else round(kd["gbs"] / peak, 4)}
     roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
-                "algo_bytes_per_launch": dom_bytes, "launch_ms": dom_ms}
+                "algo_bytes_per_launch": dom_bytes, "launch_ms": dom_ms,
+                "kernels": table,
+                "how": "per-kernel CUDA events on the launching stream in an instrumented pass over the five "
+                       "noise draws (L2 flushed before each); achieved = algorithmic bytes / mean launch time; "
+                       "share = of the summed kernel times of a step"}
     stages = {}
     for name, kd in kernels.items():
         stage = ("graph" if name.startswith("slg") else "noise" if name in ("gather_colors", "ne_moments", "ne_finalize")
@@ -638,10 +733,7 @@ def run_fgbd(args):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        times = time_oracle(xyz, [noisy[2]])
-        cpu = {"value": n / times[0] / 1e6, "unit": "Mpoints/s", "cores": 1, "kind": "oracle",
-               "sample": f"one full {n}-point frame (sigma 30) of this workload; NumPy float64 oracle, 1 thread, "
-                         f"{times[0]:.1f} s"}
+        cpu = cpu_baseline(xyz, noisy)
 
     if rank == 0:
         line = {
@@ -651,8 +743,6 @@ def run_fgbd(args):
             "config": workload_config(n), "frames_per_s": fps, "e2e": e2e,
             "gpu_launches": int(launches), "roofline": roofline, "cpu_baseline": cpu,
             "clocks": clocks.summary(), "stages_ms": stages,
-            "kernels": {k: {"ms": round(v["ms"], 5), "per_step": v["launches_per_step"],
-                            "gbs": None if v["gbs"] is None else round(v["gbs"], 1)} for k, v in kernels.items()},
             "q_mean": q_mean, "wall_s": wall, "step_ms_min": min(step_ms), "step_ms_max": max(step_ms),
             "ablations": ablations, "batched": batched, "differentiable": differentiable,
             "streaming": streaming,

@@ -339,18 +339,19 @@ fgbd_status fgbd_get_timings(fgbd_ctx* ctx, int32_t max, int32_t* count_host, ch
 
 /* Allocation-free scan orders.  The paper has no counterpart: this entry
  * point exists for callers that cannot allocate device memory when they need
- * the result, such as code running inside a CUDA graph capture or a real-time
- * frame loop where a cudaMalloc would stall or is not allowed, plug-ins whose
- * host application owns all device memory, or services held to a fixed
- * memory budget.  It computes the same three scan orders as fgbd_build_graph
- * (Eq. 1-3, stable radix sort, ties by input index) without a context.
+ * the result: a real-time frame loop where a cudaMalloc would stall the frame
+ * (it can synchronise the device), a plug-in whose host application owns all
+ * device memory, or a service held to a fixed memory budget.  It computes the
+ * same three scan orders as fgbd_build_graph (the codes of the three scan
+ * directions, each sorted stably, ties broken by input index) without a
+ * context.
  *   xyz:    int32 [n][3] device, coordinates in [0, 2^bits).
  *   n:      0 <= n <= FGBD_STATIC_MAX_POINTS; larger n returns FGBD_EINVAL.
  *   bits:   1..10.
  *   orders: int32 [3][n] device; orders[l][k] is the input index of the k-th
  *           point along code l+1.
- *   status: optional device uint32 receiving 0, or the OR of 1 (a coordinate
- *           out of range) and 2 (a bounded device wait gave up); NULL to skip.
+ *   status: optional device uint32 receiving 0, or 1 if a coordinate was out
+ *           of range (the orders are then unspecified); NULL to skip.
  * Scratch: one file-scope device array of about 1.3 MiB (FGBD_STATIC_MAX_POINTS
  * points) reserved on every GPU that loads the library until the process
  * exits.  The call allocates and frees nothing.  The first call on a device

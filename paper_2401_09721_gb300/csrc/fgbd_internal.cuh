@@ -12,6 +12,7 @@
 // 6 (w - 1) further slots per point (GraphBufs::cx).
 #pragma once
 
+#include <atomic>
 #include <cstddef>
 #include <cstdint>
 #include <cuda_runtime.h>
@@ -409,6 +410,21 @@ inline cudaError_t launch_kernel(void (*kernel)(KArgs...), dim3 grid, dim3 block
     cfg.numAttrs = 1;
   }
   return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
+// Run `set` (a kernel attribute change, which is idempotent) once per device:
+// `done` holds one bit per device index.  Safe from several host threads; two
+// threads may both run `set` the first time, which changes nothing.
+template <typename F>
+inline cudaError_t once_per_device(std::atomic<unsigned long long>& done, F&& set) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const unsigned long long bit = 1ull << (dev & 63);
+  if (done.load(std::memory_order_acquire) & bit) return cudaSuccess;
+  e = set();
+  if (e == cudaSuccess) done.fetch_or(bit, std::memory_order_acq_rel);
+  return e;
 }
 
 // zero [p, p + words) on `stream` (a kernel, so it joins the programmatic chain)

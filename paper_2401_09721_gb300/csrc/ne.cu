@@ -937,16 +937,11 @@ cudaError_t launch_ne_finalize(int dtype, const double* f64_partials, int nblock
   if (!spec || spec->spec_depth <= 0 || spec->n <= 0 || num_sms < 2)
     return launch_kernel(k_ne_finalize, dim3(1), dim3(kFinThreads), 0, stream, false, dtype, f64_partials, nblocks,
                          sc, sigma_out);
-  static unsigned long long configured = 0;  // the shared-memory limit is set once per device
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
+  static std::atomic<unsigned long long> configured{0};  // the shared-memory limit is set once per device
+  const cudaError_t e = once_per_device(configured, [] {
+    return cudaFuncSetAttribute(k_ne_finalize_spec, cudaFuncAttributeMaxDynamicSharedMemorySize, kSpecPadBytes);
+  });
   if (e != cudaSuccess) return e;
-  const unsigned long long bit = 1ull << (dev & 63);
-  if (!(configured & bit)) {
-    e = cudaFuncSetAttribute(k_ne_finalize_spec, cudaFuncAttributeMaxDynamicSharedMemorySize, kSpecPadBytes);
-    if (e != cudaSuccess) return e;
-    configured |= bit;
-  }
   return launch_kernel(k_ne_finalize_spec, dim3(num_sms), dim3(kSpecThreads), kSpecPadBytes, stream, true, dtype,
                        f64_partials, nblocks, sc, sigma_out, *spec);
 }

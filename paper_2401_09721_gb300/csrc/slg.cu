@@ -819,16 +819,11 @@ cudaError_t launch_tile_scan(const SortPassArgs& a, cudaStream_t stream) {
 
 cudaError_t launch_sort_scatter(const SortPassArgs& a, cudaStream_t stream) {
   // the shared-memory limit is a per-device function attribute: set it once per device
-  static unsigned long long configured = 0;
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
+  static std::atomic<unsigned long long> configured{0};
+  const cudaError_t e = once_per_device(configured, [] {
+    return cudaFuncSetAttribute(k_sort_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, int(scatter_smem_bytes()));
+  });
   if (e != cudaSuccess) return e;
-  const unsigned long long bit = 1ull << (dev & 63);
-  if (!(configured & bit)) {
-    e = cudaFuncSetAttribute(k_sort_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, int(scatter_smem_bytes()));
-    if (e != cudaSuccess) return e;
-    configured |= bit;
-  }
   return launch_kernel(k_sort_scatter, dim3(a.tiles), dim3(kScatterThreads), scatter_smem_bytes(), stream, false, a);
 }
 
@@ -842,16 +837,11 @@ cudaError_t launch_sort_pass(const SortPassArgs& a, cudaStream_t stream) {
 cudaError_t launch_slab_sort(int n, int bits, int cap, const SortBufs& sb, const GraphBufs& gb,
                              const DevScalars* sc, cudaStream_t stream) {
   if (n <= 0) return cudaSuccess;
-  static unsigned long long configured = 0;  // the shared-memory limit is set once per device
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
+  static std::atomic<unsigned long long> configured{0};  // the shared-memory limit is set once per device
+  const cudaError_t e = once_per_device(configured, [] {
+    return cudaFuncSetAttribute(k_slab_sort, cudaFuncAttributeMaxDynamicSharedMemorySize, int(slab_smem_bytes()));
+  });
   if (e != cudaSuccess) return e;
-  const unsigned long long bit = 1ull << (dev & 63);
-  if (!(configured & bit)) {
-    e = cudaFuncSetAttribute(k_slab_sort, cudaFuncAttributeMaxDynamicSharedMemorySize, int(slab_smem_bytes()));
-    if (e != cudaSuccess) return e;
-    configured |= bit;
-  }
   // scratch for slabs larger than shared memory: the C2 order and C2 ranks, written later
   return launch_kernel(k_slab_sort, dim3(1 << bits), dim3(kSlabThreads), slab_smem_bytes(), stream, false, n, bits,
                        sb.keys[0], sb.vals[0], reinterpret_cast<uint32_t*>(gb.ord23),

@@ -1,9 +1,9 @@
 // fgbd_scan_orders_static: the scan-order radix sort without any device allocation.
 //
 // Some callers cannot call cudaMalloc at the moment they need the scan orders:
-// code running inside a CUDA graph capture or a real-time frame loop where an
-// allocation would stall or be illegal, plug-ins whose host application owns
-// all device memory, or services on a GPU with a fixed memory budget.  This
+// a real-time frame loop where an allocation would stall the frame, plug-ins
+// whose host application owns all device memory, or services on a GPU with a
+// fixed memory budget.  This
 // entry point runs the same histogram and radix-sort kernels as
 // fgbd_build_graph, but its scratch (key/value ping-pong buffers, per-tile
 // digit counts, coordinate histograms, orders, ranks) lives in one file-scope device array of

@@ -303,27 +303,29 @@ def torso_frame(target: int = 1_000_000, bits: int = 10, sigma: float = 20.0, se
     return Frame(xyz, clean, noisy, sigma, bits, f"torso{xyz.shape[0]}_b{bits}_s{sigma:g}")
 
 
+def batch_frame(f: int, lo: int = 200_000, hi: int = 1_200_000, seed: int = 1, bits: int = 10) -> Frame:
+    """Frame f of ``batch_frames``: seed seed + f, N_f ~ U[lo, hi] sphere voxels
+    at `bits` bits (sampled 1.5x, voxelized and trimmed to N_f), smooth colour,
+    and uint8 noise with sigma_f ~ U[10, 50]."""
+    s = seed + f
+    rng = np.random.default_rng(s)
+    target = int(rng.integers(lo, hi + 1))
+    sigma = float(rng.uniform(10.0, 50.0))
+    samples = int(target * 1.5) + 1024
+    xyz = sphere_points(samples, bits, s)
+    while xyz.shape[0] < target:
+        samples *= 2
+        xyz = sphere_points(samples, bits, s)
+    xyz = np.ascontiguousarray(xyz[:target])
+    clean = smooth_colors(xyz, bits, s)
+    noisy = add_noise_u8(clean, sigma, s)
+    return Frame(xyz, clean, noisy, sigma, bits, f"sphere{target}_b{bits}_s{sigma:.1f}")
+
+
 def batch_frames(count: int = 16, lo: int = 200_000, hi: int = 1_200_000, seed: int = 1,
                  bits: int = 10) -> list:
-    """Frames of uneven sizes for the batched path: frame f (seed seed + f) has
-    N_f ~ U[lo, hi] sphere voxels at `bits` bits (sampled 1.5x, voxelized and
-    trimmed to N_f), smooth colour, and uint8 noise with sigma_f ~ U[10, 50]."""
-    frames = []
-    for f in range(count):
-        s = seed + f
-        rng = np.random.default_rng(s)
-        target = int(rng.integers(lo, hi + 1))
-        sigma = float(rng.uniform(10.0, 50.0))
-        samples = int(target * 1.5) + 1024
-        xyz = sphere_points(samples, bits, s)
-        while xyz.shape[0] < target:
-            samples *= 2
-            xyz = sphere_points(samples, bits, s)
-        xyz = np.ascontiguousarray(xyz[:target])
-        clean = smooth_colors(xyz, bits, s)
-        noisy = add_noise_u8(clean, sigma, s)
-        frames.append(Frame(xyz, clean, noisy, sigma, bits, f"sphere{target}_b{bits}_s{sigma:.1f}"))
-    return frames
+    """Frames of uneven sizes for the batched path: ``batch_frame`` f for f = 0..count-1."""
+    return [batch_frame(f, lo, hi, seed, bits) for f in range(count)]
 
 
 def tuning_pairs(count: int = 8, n: int = 300_000, sigma: float = 30.0, seed: int = 101, bits: int = 9) -> list:

@@ -1,14 +1,15 @@
-"""The allocation-free scan orders agree with the context-based ones.
+"""The allocation-free scan orders agree with the context-based ones and the oracle.
 
 ``fgbd_scan_orders_static`` is for callers that cannot allocate device memory
-when they need the scan orders (inside a CUDA graph capture or a real-time
-frame loop, or in a host application that owns all device memory).  Its
-scratch is one fixed device array shared by every call, so this test makes two
-calls in a row, the second on a smaller cloud with another bit width, and
+when they need the scan orders (a real-time frame loop where an allocation
+would stall the frame, or a host application that owns all device memory).
+Its scratch is one fixed device array shared by every call, so this test makes
+two calls in a row, the second on a smaller cloud with another bit width, and
 checks each against ``fgbd_build_graph`` + ``fgbd_get_orders`` on the same
-input.  Orders are integers, so the comparison is exact, as in the other
-parity tests.  The file name sorts last so that a run stopping at the first
-failure has already run every other test.
+input and against the oracle's stable sorts of the three codes.  Orders are
+integers, so the comparisons are exact, as in the other parity tests.  A
+coordinate out of range must set status bit 1.  The file name sorts last so
+that a run stopping at the first failure has already run every other test.
 """
 import ctypes
 
@@ -16,6 +17,7 @@ import numpy as np
 import pytest
 import torch
 
+from oracle import fgbd_oracle as orc
 from paper_2401_09721_gb300 import build, synth
 
 pytestmark = pytest.mark.gpu
@@ -51,6 +53,29 @@ def test_static_orders_match_context_orders_on_two_calls():
         assert status.item() == 0
         assert torch.equal(got, want)
         ctx.close()
+        ref = orc.scan_orders(orc.scan_line_codes(xyz, bits)).astype(np.int32)
+        assert np.array_equal(got.cpu().numpy(), ref)
+
+
+def test_static_orders_flag_a_coordinate_out_of_range():
+    build.build()
+    from paper_2401_09721_gb300 import fgbd
+
+    lib = fgbd.lib()
+    stream = torch.cuda.current_stream()
+    xyz = np.random.default_rng(9).integers(0, 256, size=(5000, 3)).astype(np.int32)
+    xyz[1234, 1] = 256                                                         # y = 2^bits
+    x = torch.from_numpy(xyz).cuda()
+    got = torch.empty((3, xyz.shape[0]), dtype=torch.int32, device="cuda")
+    status = torch.zeros((1,), dtype=torch.int32, device="cuda")
+    assert _call(lib, x, xyz.shape[0], 8, got, status, stream) == 0
+    torch.cuda.synchronize()
+    assert status.item() & 1
+    # the next call on valid input clears the bit
+    x = torch.from_numpy(np.clip(xyz, 0, 255)).cuda()
+    assert _call(lib, x, xyz.shape[0], 8, got, status, stream) == 0
+    torch.cuda.synchronize()
+    assert status.item() == 0
 
 
 def test_static_orders_reject_sizes_beyond_the_maximum():
