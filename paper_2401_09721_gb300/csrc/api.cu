@@ -396,7 +396,7 @@ fgbd_status do_estimate(fgbd_ctx* ctx, const void* rgb, int32_t dtype, double* s
   if (!zeroed) zero_region(ctx, offsetof(DevScalars, n_patches), offsetof(DevScalars, ne_end_), st, &e);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "memset");
   if (ctx->params.window > 1) {
-    // wider windows: moments, their reduction, the Jacobi block, the Rayleigh
+    // wider windows: moments, their reduction, the eigenvector block, the Rayleigh
     // quotients with the tail rule; no filter steps are taken beside them
     if (n > 0) {
       if (pregathered)
@@ -405,7 +405,7 @@ fgbd_status do_estimate(fgbd_ctx* ctx, const void* rgb, int32_t dtype, double* s
         FGBD_LAUNCH(ctx, "gather_colors", st,
                     launch_gather_colors(rgb, dtype, n, ctx->gb.perm1, ctx->y8, ctx->yf, st));
     }
-    static const char* const kStage[4] = {"ne_wide_moments", "ne_wide_reduce", "ne_wide_jacobi", "ne_wide_tail"};
+    static const char* const kStage[4] = {"ne_wide_moments", "ne_wide_reduce", "ne_wide_eigvec", "ne_wide_tail"};
     for (int stage = n > 0 ? 0 : 1; stage < 4; ++stage)
       FGBD_LAUNCH(ctx, kStage[stage], st,
                   launch_ne_wide(stage, n, ctx->params.bits, ctx->params.window, dtype, ctx->gb, ctx->y8, ctx->yf,
@@ -708,7 +708,7 @@ fgbd_status fgbd_ctx_create(int64_t capacity, const fgbd_params* params, fgbd_ct
       {reinterpret_cast<void**>(&ctx->wne.part), wide ? size_t(w_blocks) * wP * 8 : 0},
       {reinterpret_cast<void**>(&ctx->wne.tot), wide ? wP * 8 : 0},
       {reinterpret_cast<void**>(&ctx->wne.S), wide ? wD * wD * 8 : 0},
-      {reinterpret_cast<void**>(&ctx->wne.V), wide ? wD * wD * 4 : 0},
+      {reinterpret_cast<void**>(&ctx->wne.V), wide ? (wD * wD + wD) * 4 : 0},
       {reinterpret_cast<void**>(&ctx->wne.lam), wide ? wD * 8 : 0},
       {reinterpret_cast<void**>(&ctx->wne.done), wide ? 4 : 0},
   };

@@ -185,20 +185,20 @@ cudaError_t launch_ne_finalize(int dtype, const double* f64_partials, int nblock
 int ne_moment_blocks(int n, int num_sms);
 
 // Noise estimate at windows w > 1 (patch dimension D = 3 (6w + 1)): per-block
-// moment partials, their reduction, the one-block float32 Jacobi, and float64
+// moment partials, their reduction, the one-block float32 eigenvectors, and float64
 // Rayleigh quotients with the tail rule.
 struct WideNe {
   double* part;   // [blocks][D*D + D + 1] per-block moments (int64 bit patterns for uint8 colours)
   double* tot;    // [D*D + D + 1] the totals: sum a a^T (upper triangle), sum a, patch count
   double* S;      // [D][D] the covariance
-  float* V;       // [D][D] its eigenvector estimates (columns)
+  float* V;       // [D][D] its eigenvector estimates (columns), then their D float32 eigenvalues
   double* lam;    // [D] Rayleigh quotients
   uint32_t* done; // blocks of the Rayleigh launch finished (reset by the last)
   int blocks;     // moment blocks (the rows of part)
 };
 int ne_wide_blocks(int n, int num_sms);
 size_t ne_wide_part_entries(int window);  // D*D + D + 1
-// stage 0 the moments (nothing at n = 0), 1 their reduction, 2 the Jacobi block, 3 the tail rule
+// stage 0 the moments (nothing at n = 0), 1 their reduction, 2 the eigenvector block, 3 the tail rule
 cudaError_t launch_ne_wide(int stage, int n, int bits, int window, int dtype, const GraphBufs& gb,
                            const uint32_t* y8, const float4* yf, float* spread, const WideNe& w, DevScalars* sc,
                            double* sigma_out, int num_sms, cudaStream_t stream);

@@ -9,15 +9,17 @@
 //   index), to the first and second moments sum a and sum a a^T.  uint8
 //   colours are centred on 128 and kept as int8, so the moments are exact
 //   integer sums (dp4a over 4 patches per instruction, int64 accumulation).
-// k_ne_finalize: one block.  Sigma = S2/N - mu mu^T in float64; a cyclic
-//   Jacobi in float32 (parallel round-robin order) gives approximate
-//   eigenvectors; each eigenvalue is then the float64 Rayleigh quotient
-//   v^T Sigma v / v^T v, whose error is second order in the eigenvector error;
-//   the values are sorted descending and the tail rule gives sigma_est.
+// k_ne_finalize: one block.  Sigma = S2/N - mu mu^T in float64; float32
+//   eigenvector estimates from a Householder tridiagonalisation, Sturm
+//   multisection and inverse iteration (tridiag.cuh); each eigenvalue is then
+//   the float64 Rayleigh quotient v^T Sigma v / v^T v, whose error is second
+//   order in the eigenvector error; the values are sorted descending and the
+//   tail rule gives sigma_est.
 #include <algorithm>
 
 #include "eigen.cuh"
 #include "select.cuh"
+#include "tridiag.cuh"
 
 namespace fgbd {
 namespace {
@@ -473,58 +475,14 @@ __global__ void __launch_bounds__(kNeThreads, 4)
 
 // ---------------------------------------------------------------- finalize
 
-constexpr int kMaxSweeps = 15;
-constexpr int kFinThreads = 384;      // 12 warps: V blocks, A blocks, the rotation predictor
-constexpr int kGroups = 11;           // per round: 10 rotated pairs and one resting index
-constexpr int kVThreads = kD * kGroups;                 // (row of V, group): 231
-constexpr int kAFirst = 256;                            // first thread of the A blocks
-constexpr int kABlocks = kGroups * (kGroups + 1) / 2;   // (group, group) with g <= h: 66
-constexpr int kPredFirst = 352;                         // the predictor warp
-
-// Parallel cyclic Jacobi schedule on 21 indices: in round r (0..20) index i is
-// paired with (2r - i) mod 21, and index r, which pairs with itself, rests.
-// Every pair {i, j} meets exactly once per sweep, in the round r with
-// 2r = i + j (mod 21).  Group k of round r is {r} for k = 0 and the pair
-// {(r + k) mod 21, (r - k) mod 21} for k = 1..10; the resting index r takes
-// the identity column (alpha, beta) = (1, 0) and is its own partner, so it
-// needs no special case below.
-__device__ __forceinline__ int jacobi_partner(int i, int r) {
-  int p = 2 * r - i;
-  if (p < 0) p += kD;
-  if (p >= kD) p -= kD;
-  return p;
-}
-// v mod 21 for v in [-21, 41]
-__device__ __forceinline__ int wrap21(int v) { return v < 0 ? v + kD : (v >= kD ? v - kD : v); }
-// Entry (a, b) after the rotations of round r, whose index i has column
-// co[i] = (alpha_i, beta_i) in J (alpha_i at row i, beta_i at row pa = partner):
-// sum over u in {a, pa}, v in {b, pb} of J[u][a] A[u][v] J[v][b].
-__device__ __forceinline__ float rotated_entry(const float* __restrict__ A, float2 ca, float2 cb, int a, int pa,
-                                               int b, int pb) {
-  const float row_a = fmaf(cb.x, A[a * kD + b], cb.y * A[a * kD + pb]);
-  const float row_pa = fmaf(cb.x, A[pa * kD + b], cb.y * A[pa * kD + pb]);
-  return fmaf(ca.x, row_a, ca.y * row_pa);
-}
-
-// Entry (i, k) of the Helmert basis of R^7: column 0 is uniform, column k >= 1
-// is (1, ..., 1, -k, 0, ..., 0) / sqrt(k (k + 1)) with k ones.
-__device__ __forceinline__ float helmert7(int i, int k) {
-  if (k == 0) return 0.37796447300922722f;  // 1 / sqrt(7)
-  const float inv = rsqrtf(float(k * (k + 1)));
-  return i < k ? inv : (i == k ? -float(k) * inv : 0.f);
-}
+constexpr int kFinThreads = 384;      // 12 warps
 
 // barriers of the first kFinThreads threads of a block (barrier 1; 0 is __syncthreads)
 __device__ __forceinline__ void fin_bar() { asm volatile("bar.sync 1, %0;" ::"n"(kFinThreads) : "memory"); }
-__device__ __forceinline__ bool fin_bar_or(bool v) {
-  uint32_t r;
-  asm volatile(
-      "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 q, %1, 0;\n\tbar.red.or.pred p, 1, %2, q;\n\tselp.u32 %0, 1, 0, p;\n\t}"
-      : "=r"(r)
-      : "r"(uint32_t(v)), "n"(kFinThreads)
-      : "memory");
-  return r != 0;
-}
+
+struct FinBar {
+  __device__ void operator()() const { fin_bar(); }
+};
 
 // sigma_est from the patch moments, by the first kFinThreads threads of one
 // block (its barriers count those threads only, so the rest of a larger block
@@ -534,10 +492,9 @@ __device__ __noinline__ void finalize_block(int dtype, const double* __restrict_
   __shared__ double S[kD][kD];
   __shared__ float Sf[kD][kD];  // Sigma rounded to float32 once, for the float32 work
   __shared__ double s_sum[kD * kD + kD + 1];
-  __shared__ float V[kD][kD + 1];
-  __shared__ float Abuf[2][kD * kD];
-  __shared__ float Vbuf[2][kD * kD];
-  __shared__ float2 s_coef[2][kD];
+  __shared__ float V[kD * kD];  // eigenvector estimates (columns)
+  __shared__ float s_mu[kD];    // their float32 eigenvalues (the fallback of a non-finite quotient)
+  __shared__ TridiagSmem<kD, kFinThreads> tw;
   __shared__ long long s_key[kD];
   __shared__ double s_sorted[kD];
   __shared__ double s_num[kD][kD];
@@ -586,173 +543,13 @@ __device__ __noinline__ void finalize_block(int dtype, const double* __restrict_
   }
   fin_bar();
 
-  // Cyclic Jacobi in float32, matrix and vectors in shared memory
-  // (double-buffered), one barrier per round.  Each round applies the
-  // rotations of round r (coefficients s_coef[r & 1]) by 2x2 blocks: thread
-  // (g, h) of the A blocks computes J_g^T A[g][h] J_h for groups g <= h from
-  // the block's four entries and writes it with its mirror image, thread
-  // (i, h) of the V blocks the entries of row i in the columns of group h.
-  // In the same round the predictor warp evaluates the three entries of
-  // every pair of round r + 1 after this round's rotations and writes that
-  // round's coefficients, so no round waits for a separate coefficient
-  // step.  A pair is rotated only while |a_pq| > 2e-7 ||diag A|| (the
-  // float32 resolution of the matrix); the iteration ends at the first
-  // barrier where no off-diagonal entry is above that threshold, since no
-  // later round would rotate anything.
-  {
-    // Start from V0 = H7 (x) Qc instead of the identity (entry 3 i + a of a
-    // patch is channel a of its point i): Qc diagonalises the 3x3 colour
-    // covariance averaged over the seven points, H7 is the Helmert basis of
-    // the seven points (first vector uniform).  A0 = V0^T Sigma V0 has much
-    // less off-diagonal mass, so the iteration needs about half the rounds;
-    // the eigenvalues still come from float64 Rayleigh quotients of the final
-    // vectors, so the start changes only the work, not the accuracy.
-    __shared__ float s_qc[3][3];
-    if (tid < 9) {
-      const int a = tid / 3, b = tid % 3;
-      float c = 0.f;
-      for (int i = 0; i < 7; ++i) c += Sf[3 * i + a][3 * i + b];
-      reinterpret_cast<float*>(s_qc)[tid] = c * (1.f / 7.f);
-    }
-    fin_bar();
-    if (tid == 0) colour_basis(s_qc);
-    fin_bar();
-    for (int e = tid; e < kD * kD; e += kFinThreads) {
-      const int r = e / kD, c = e % kD;
-      Vbuf[0][e] = helmert7(r / 3, c / 3) * s_qc[r % 3][c % 3];
-    }
-    fin_bar();
-    // T = Sigma V0 into Vbuf[1] (scratch here), then the upper triangle of V0^T T, mirrored
-    for (int e = tid; e < kD * kD; e += kFinThreads) {
-      const int r = e / kD, c = e % kD;
-      float t0 = 0.f, t1 = 0.f, t2 = 0.f;
-#pragma unroll
-      for (int k = 0; k < kD; k += 3) {
-        t0 = fmaf(Sf[r][k], Vbuf[0][k * kD + c], t0);
-        t1 = fmaf(Sf[r][k + 1], Vbuf[0][(k + 1) * kD + c], t1);
-        t2 = fmaf(Sf[r][k + 2], Vbuf[0][(k + 2) * kD + c], t2);
-      }
-      Vbuf[1][e] = t0 + t1 + t2;
-    }
-    fin_bar();
-    for (int e = tid; e < kD * kD; e += kFinThreads) {
-      const int r = e / kD, c = e % kD;
-      if (r > c) continue;
-      float t0 = 0.f, t1 = 0.f, t2 = 0.f;
-#pragma unroll
-      for (int k = 0; k < kD; k += 3) {
-        t0 = fmaf(Vbuf[0][k * kD + r], Vbuf[1][k * kD + c], t0);
-        t1 = fmaf(Vbuf[0][(k + 1) * kD + r], Vbuf[1][(k + 1) * kD + c], t1);
-        t2 = fmaf(Vbuf[0][(k + 2) * kD + r], Vbuf[1][(k + 2) * kD + c], t2);
-      }
-      const float v = t0 + t1 + t2;
-      Abuf[0][r * kD + c] = v;
-      Abuf[0][c * kD + r] = v;
-    }
-    fin_bar();
-    float dsq = 0.f;
-    for (int i = 0; i < kD; ++i) dsq = fmaf(Abuf[0][i * kD + i], Abuf[0][i * kD + i], dsq);
-    const float thr = 2e-7f * sqrtf(dsq);
-    // roles
-    const bool v_thread = tid < kVThreads;
-    const int vi = tid / kGroups, vh = tid % kGroups;
-    const bool a_thread = tid >= kAFirst && tid < kAFirst + kABlocks;
-    int ag = 0, ah = 0;
-    if (a_thread) {
-      int b = tid - kAFirst;
-      while (b >= kGroups - ag) {
-        b -= kGroups - ag;
-        ++ag;
-      }
-      ah = ag + b;
-    }
-    const bool pred = tid >= kPredFirst && tid < kPredFirst + kGroups;
-    const int pk = tid - kPredFirst;
-    fin_bar();
-    // coefficients of round 0 from the matrix itself
-    if (pred) {
-      if (pk == 0) {
-        s_coef[0][0] = make_float2(1.f, 0.f);
-      } else {
-        // the pair {pk, -pk mod 21} of round 0
-        const int p = min(pk, kD - pk), q = max(pk, kD - pk);
-        float2 cp, cq;
-        jacobi_rotation(Abuf[0][p * kD + p], Abuf[0][q * kD + q], Abuf[0][p * kD + q], thr, cp, cq);
-        s_coef[0][p] = cp;
-        s_coef[0][q] = cq;
-      }
-    }
-    bool off_big = false;
-    for (int e = tid; e < kD * kD; e += kFinThreads) off_big |= (e / kD != e % kD) && fabsf(Abuf[0][e]) > thr;
-    bool big = fin_bar_or(off_big);
-    int cur = 0;
-    for (int round = 0; big && round < kMaxSweeps * kD; ++round) {
-      const int r = round % kD;
-      const float* A = Abuf[cur];
-      const float* Vc = Vbuf[cur];
-      const float2* co = s_coef[round & 1];
-      float* An = Abuf[cur ^ 1];
-      float* Vn = Vbuf[cur ^ 1];
-      off_big = false;
-      if (v_thread) {
-        // row vi, columns y0, y1 of group vh (y0 == y1 == r for the resting group)
-        const int y0 = wrap21(r + vh), y1 = wrap21(r - vh);
-        const float2 c0 = co[y0], c1 = co[y1];
-        const float v0 = Vc[vi * kD + y0], v1 = Vc[vi * kD + y1];
-        Vn[vi * kD + y0] = fmaf(c0.x, v0, c0.y * v1);
-        Vn[vi * kD + y1] = fmaf(c1.x, v1, c1.y * v0);
-      } else if (a_thread) {
-        const int x0 = wrap21(r + ag), x1 = wrap21(r - ag), y0 = wrap21(r + ah), y1 = wrap21(r - ah);
-        const float2 cx0 = co[x0], cx1 = co[x1], cy0 = co[y0], cy1 = co[y1];
-        const float a00 = A[x0 * kD + y0], a01 = A[x0 * kD + y1], a10 = A[x1 * kD + y0], a11 = A[x1 * kD + y1];
-        // T = A_blk J_h, then J_g^T T; J_g = [[alpha_x0, beta_x1], [beta_x0, alpha_x1]]
-        const float t00 = fmaf(a00, cy0.x, a01 * cy0.y), t01 = fmaf(a00, cy1.y, a01 * cy1.x);
-        const float t10 = fmaf(a10, cy0.x, a11 * cy0.y), t11 = fmaf(a10, cy1.y, a11 * cy1.x);
-        const float n00 = fmaf(cx0.x, t00, cx0.y * t10), n01 = fmaf(cx0.x, t01, cx0.y * t11);
-        const float n10 = fmaf(cx1.y, t00, cx1.x * t10), n11 = fmaf(cx1.y, t01, cx1.x * t11);
-        An[x0 * kD + y0] = n00;
-        An[y0 * kD + x0] = n00;
-        An[x1 * kD + y1] = n11;
-        An[y1 * kD + x1] = n11;
-        An[x0 * kD + y1] = n01;
-        An[y1 * kD + x0] = n01;
-        off_big = (x0 != y0 && fabsf(n00) > thr) || (x1 != y1 && fabsf(n11) > thr) || (x0 != y1 && fabsf(n01) > thr);
-        if (ag != ah) {
-          // off the diagonal the fourth entry is distinct; on it, it is the mirror of n01
-          An[x1 * kD + y0] = n10;
-          An[y0 * kD + x1] = n10;
-          off_big |= x1 != y0 && fabsf(n10) > thr;
-        }
-      } else if (pred) {
-        const int rn = r + 1 == kD ? 0 : r + 1;
-        float2* cn = s_coef[(round + 1) & 1];
-        if (pk == 0) {
-          cn[rn] = make_float2(1.f, 0.f);
-        } else {
-          // the pair (p, q) of round r + 1, and the partners of p and q in round r
-          const int u = wrap21(rn + pk), w = wrap21(rn - pk);
-          const int p = min(u, w), q = max(u, w);
-          const int pp = jacobi_partner(p, r), pq = jacobi_partner(q, r);
-          const float2 cp = co[p], cq = co[q];
-          const float app = rotated_entry(A, cp, cp, p, pp, p, pp);
-          const float aqq = rotated_entry(A, cq, cq, q, pq, q, pq);
-          const float apq = rotated_entry(A, cp, cq, p, pp, q, pq);
-          float2 np, nq;
-          jacobi_rotation(app, aqq, apq, thr, np, nq);
-          cn[p] = np;
-          cn[q] = nq;
-        }
-      }
-      cur ^= 1;
-      big = fin_bar_or(off_big);
-    }
-    for (int e = tid; e < kD * kD; e += kFinThreads) V[e / kD][e % kD] = Vbuf[cur][e];
-  }
-  fin_bar();
+  // float32 eigenvector estimates: Householder tridiagonalisation, Sturm
+  // multisection and inverse iteration (tridiag.cuh)
+  eig_vectors_f32<kD, kFinThreads>(&Sf[0][0], tw, V, s_mu, FinBar{});
 
   // float64 Rayleigh quotients of the 21 eigenvector estimates.  float64 has a
   // long latency here, so the sums run as three interleaved chains.
-  for (int e = tid; e < kD * kD; e += kFinThreads) V64[e / kD][e % kD] = double(V[e / kD][e % kD]);
+  for (int e = tid; e < kD * kD; e += kFinThreads) V64[e / kD][e % kD] = double(V[e]);
   fin_bar();
   for (int e = tid; e < kD * kD; e += kFinThreads) {
     const int k = e / kD, r = e % kD;
@@ -783,6 +580,7 @@ __device__ __noinline__ void finalize_block(int dtype, const double* __restrict_
         d2 = fma(V64[r + 2][lane], V64[r + 2][lane], d2);
       }
       lam = div_newton(n0 + n1 + n2, d0 + d1 + d2);
+      if (!isfinite(lam)) lam = double(s_mu[lane]);
     }
     // eigenvalues below 1e-9 max(lambda_1, 1) are numerical zeros (a rank-deficient
     // covariance); they are set to exactly 0 so the tail rule never decides on rounding noise

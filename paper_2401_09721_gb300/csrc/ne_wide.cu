@@ -13,26 +13,26 @@
 //                      batch, then float64.  Each block writes its partial
 //                      sums (no atomics, so the totals do not depend on timing).
 //   k_ne_wide_reduce   the partials summed entry by entry in a fixed order.
-//   k_ne_wide_jacobi   one block: Sigma = S2/N - mu mu^T in float64, then a
-//                      cyclic Jacobi in float32 (round-robin order: in round r
-//                      index i pairs with 2r - i mod D) from a Helmert x colour
-//                      warm start, one coefficient step and one update step
-//                      by 2x2 blocks per round.
+//   k_ne_wide_eigvec   one block: Sigma = S2/N - mu mu^T in float64, then
+//                      float32 eigenvector estimates by a Householder
+//                      tridiagonalisation, Sturm multisection and inverse
+//                      iteration (tridiag.cuh).
 //   k_ne_wide_tail     one block per eigenvector: the float64 Rayleigh quotient
 //                      v^T Sigma v / v^T v (second order in the eigenvector
 //                      error); the last block to finish sorts the values, sets
 //                      numerical zeros to 0 and applies the tail rule.
 #include <algorithm>
+#include <atomic>
 
 #include "eigen.cuh"
+#include "tridiag.cuh"
 
 namespace fgbd {
 namespace {
 
 constexpr int kWThreads = 256;        // moments: threads per block
-constexpr int kWJacobiThreads = 512;
+constexpr int kWEigThreads = 256;   // the eigenvector block (255 registers a thread: the reducing warp holds two rows of A a lane)
 constexpr int kWTailThreads = 64;     // D <= 57 eigenvector entries, one per thread
-constexpr int kWMaxSweeps = 30;
 
 template <int W>
 constexpr int patch_dim() {
@@ -349,63 +349,34 @@ __global__ void __launch_bounds__(32 * kReduceWarps) k_ne_wide_reduce(const doub
   }
 }
 
+struct BlockBar {
+  __device__ void operator()() const { __syncthreads(); }
+};
+
 template <int D>
-__device__ __forceinline__ int round_partner(int i, int r) {
-  int p = 2 * r - i;
-  if (p < 0) p += D;
-  if (p >= D) p -= D;
-  return p;
-}
-// v mod D for v in (-D, 2D)
-template <int D>
-__device__ __forceinline__ int wrap_d(int v) {
-  return v < 0 ? v + D : (v >= D ? v - D : v);
+constexpr size_t wide_eig_smem() {
+  return (sizeof(TridiagSmem<D, kWEigThreads>) + 15) / 16 * 16 + size_t(D) * D * 4;
 }
 
-// Entry (i, k) of the Helmert basis of R^T: column 0 is uniform, column k >= 1
-// is (1, ..., 1, -k, 0, ..., 0) / sqrt(k (k + 1)) with k ones.
-__device__ __forceinline__ float helmert(int i, int k, int T) {
-  if (k == 0) return rsqrtf(float(T));
-  const float inv = rsqrtf(float(k * (k + 1)));
-  return i < k ? inv : (i == k ? -float(k) * inv : 0.f);
-}
-
-// One block: the covariance, then the float32 Jacobi.  D is odd, so in round
-// r every pair {i, j} with i + j = 2r (mod D) is rotated and index r rests;
-// each pair meets once per sweep.  Group g of round r is {r} for g = 0 and the
-// pair {r + g, r - g} (mod D) for g >= 1; a round updates A by (group, group)
-// blocks with g <= h (each written with its mirror image, so A stays exactly
-// symmetric: separate roundings of a_ij and a_ji could leave a pair whose
-// a_pq sits above the threshold and a_qp below it unrotated for ever) and V by
-// (row, group).  The start is V0 = H_T (x) Qc (T = D / 3 patch points; H_T
-// their Helmert basis, Qc the eigenvectors of the mean 3x3 colour covariance),
-// which removes about a quarter of the rounds.  A pair is rotated while
-// |a_pq| > 2e-7 ||diag A|| (the float32 resolution of the matrix); the
-// iteration ends at the first round after which no off-diagonal entry is
-// above that, or after kWMaxSweeps sweeps.  Without patches the results are
-// written here (zero).
+// One block: the covariance Sigma = S2/N - mu mu^T in float64 (to S), then
+// float32 eigenvector estimates (tridiag.cuh) to Vout, row-major with the
+// vectors as columns, followed by their D float32 eigenvalues (the fallback of
+// a non-finite Rayleigh quotient).  Without patches the results are written
+// here (zero).
 template <int D>
-__global__ void __launch_bounds__(kWJacobiThreads) k_ne_wide_jacobi(const double* __restrict__ tot,
-                                                                    double* __restrict__ S,
-                                                                    float* __restrict__ Vout,
-                                                                    DevScalars* __restrict__ sc,
-                                                                    double* __restrict__ sigma_out) {
+__global__ void __launch_bounds__(kWEigThreads) k_ne_wide_eigvec(const double* __restrict__ tot,
+                                                                 double* __restrict__ S, float* __restrict__ Vout,
+                                                                 DevScalars* __restrict__ sc,
+                                                                 double* __restrict__ sigma_out) {
   pdl_wait();
-  static_assert(D % 6 == 3, "D = 3 T with T odd: the round-robin schedule needs an odd dimension");
-  constexpr int T = D / 3;
-  constexpr int G = (D + 1) / 2;       // groups of a round: the resting index and (D - 1) / 2 pairs
-  constexpr int NA = G * (G + 1) / 2;  // (group, group) blocks with g <= h
-  constexpr int NV = D * G;            // (row of V, group)
-  __shared__ float Ab[2][D * D];
-  __shared__ float V[D * D];
-  __shared__ float2 co[D];
-  __shared__ uint16_t s_blk[NA];
-  __shared__ float s_qc[3][3];
+  extern __shared__ __align__(16) unsigned char s_dyn[];
+  TridiagSmem<D, kWEigThreads>& tw = *reinterpret_cast<TridiagSmem<D, kWEigThreads>*>(s_dyn);
+  float* Sf = reinterpret_cast<float*>(s_dyn + (sizeof(TridiagSmem<D, kWEigThreads>) + 15) / 16 * 16);
   const int tid = threadIdx.x;
   const double npd = tot[D * D + D];
   if (tid == 0) sc->n_patches = (unsigned long long)npd;
   if (!(npd >= 1.0)) {
-    for (int i = tid; i < D; i += kWJacobiThreads) sc->eig[i] = 0.0;
+    for (int i = tid; i < D; i += kWEigThreads) sc->eig[i] = 0.0;
     if (tid == 0) {
       sc->tau = 0.0;
       sc->sigma_est = 0.0;
@@ -418,8 +389,7 @@ __global__ void __launch_bounds__(kWJacobiThreads) k_ne_wide_jacobi(const double
     return;
   }
   const double inv_n = 1.0 / npd;
-  float* Sf = Ab[0];  // Sigma in float32 until the warm start replaces it
-  for (int e = tid; e < D * D; e += kWJacobiThreads) {
+  for (int e = tid; e < D * D; e += kWEigThreads) {
     const int r = e / D, c = e % D;
     const int rr = min(r, c), cc = max(r, c);
     const double mr = tot[D * D + rr] * inv_n, mc = tot[D * D + cc] * inv_n;
@@ -427,120 +397,8 @@ __global__ void __launch_bounds__(kWJacobiThreads) k_ne_wide_jacobi(const double
     S[e] = v;
     Sf[e] = float(v);
   }
-  for (int t = tid; t < NA; t += kWJacobiThreads) {
-    int b = t, g = 0;
-    while (b >= G - g) {
-      b -= G - g;
-      ++g;
-    }
-    s_blk[t] = uint16_t((g << 8) | (g + b));
-  }
   __syncthreads();
-  if (tid < 9) {
-    const int a = tid / 3, b = tid % 3;
-    float c = 0.f;
-    for (int i = 0; i < T; ++i) c += Sf[(3 * i + a) * D + 3 * i + b];
-    s_qc[a][b] = c * (1.f / float(T));
-  }
-  __syncthreads();
-  if (tid == 0) colour_basis(s_qc);
-  __syncthreads();
-  for (int e = tid; e < D * D; e += kWJacobiThreads) {
-    const int r = e / D, c = e % D;
-    V[e] = helmert(r / 3, c / 3, T) * s_qc[r % 3][c % 3];
-  }
-  __syncthreads();
-  // A0 = V0^T Sigma V0: Sigma V0 into Ab[1], then the upper triangle of V0^T (Sigma V0), mirrored
-  for (int e = tid; e < D * D; e += kWJacobiThreads) {
-    const int r = e / D, c = e % D;
-    float t0 = 0.f, t1 = 0.f, t2 = 0.f;
-#pragma unroll 3
-    for (int k = 0; k < D; k += 3) {
-      t0 = fmaf(Sf[r * D + k], V[k * D + c], t0);
-      t1 = fmaf(Sf[r * D + k + 1], V[(k + 1) * D + c], t1);
-      t2 = fmaf(Sf[r * D + k + 2], V[(k + 2) * D + c], t2);
-    }
-    Ab[1][e] = t0 + t1 + t2;
-  }
-  __syncthreads();
-  for (int e = tid; e < D * D; e += kWJacobiThreads) {
-    const int r = e / D, c = e % D;
-    if (r > c) continue;
-    float t0 = 0.f, t1 = 0.f, t2 = 0.f;
-#pragma unroll 3
-    for (int k = 0; k < D; k += 3) {
-      t0 = fmaf(V[k * D + r], Ab[1][k * D + c], t0);
-      t1 = fmaf(V[(k + 1) * D + r], Ab[1][(k + 1) * D + c], t1);
-      t2 = fmaf(V[(k + 2) * D + r], Ab[1][(k + 2) * D + c], t2);
-    }
-    const float v = t0 + t1 + t2;
-    Ab[0][r * D + c] = v;
-    Ab[0][c * D + r] = v;
-  }
-  __syncthreads();
-  float dsq = 0.f;
-  for (int i = 0; i < D; ++i) dsq = fmaf(Ab[0][i * D + i], Ab[0][i * D + i], dsq);
-  const float thr = 2e-7f * sqrtf(dsq);
-  bool off = false;
-  for (int e = tid; e < D * D; e += kWJacobiThreads) off |= (e / D != e % D) && fabsf(Ab[0][e]) > thr;
-  bool big = __syncthreads_or(off) != 0;
-  int cur = 0;
-  for (int round = 0; big && round < kWMaxSweeps * D; ++round) {
-    const int r = round % D;
-    const float* A = Ab[cur];
-    float* An = Ab[cur ^ 1];
-    if (tid < D) {
-      const int i = tid, pi = round_partner<D>(i, r);
-      float2 c = make_float2(1.f, 0.f);
-      if (pi != i) {
-        const int p = min(i, pi), q = max(i, pi);
-        float2 cp, cq;
-        jacobi_rotation(A[p * D + p], A[q * D + q], A[p * D + q], thr, cp, cq);
-        c = i == p ? cp : cq;
-      }
-      co[i] = c;  // column i of J: alpha_i at row i, beta_i at row pi
-    }
-    __syncthreads();
-    off = false;
-    for (int t = tid; t < NA + NV; t += kWJacobiThreads) {
-      if (t < NA) {
-        // block (g, h): T = A_blk J_h, then J_g^T T; J_g = [[alpha_x0, beta_x1], [beta_x0, alpha_x1]]
-        const int ag = s_blk[t] >> 8, ah = s_blk[t] & 255;
-        const int x0 = wrap_d<D>(r + ag), x1 = wrap_d<D>(r - ag), y0 = wrap_d<D>(r + ah), y1 = wrap_d<D>(r - ah);
-        const float2 cx0 = co[x0], cx1 = co[x1], cy0 = co[y0], cy1 = co[y1];
-        const float a00 = A[x0 * D + y0], a01 = A[x0 * D + y1], a10 = A[x1 * D + y0], a11 = A[x1 * D + y1];
-        const float t00 = fmaf(a00, cy0.x, a01 * cy0.y), t01 = fmaf(a00, cy1.y, a01 * cy1.x);
-        const float t10 = fmaf(a10, cy0.x, a11 * cy0.y), t11 = fmaf(a10, cy1.y, a11 * cy1.x);
-        const float n00 = fmaf(cx0.x, t00, cx0.y * t10), n01 = fmaf(cx0.x, t01, cx0.y * t11);
-        const float n10 = fmaf(cx1.y, t00, cx1.x * t10), n11 = fmaf(cx1.y, t01, cx1.x * t11);
-        An[x0 * D + y0] = n00;
-        An[y0 * D + x0] = n00;
-        An[x1 * D + y1] = n11;
-        An[y1 * D + x1] = n11;
-        An[x0 * D + y1] = n01;
-        An[y1 * D + x0] = n01;
-        off |= (x0 != y0 && fabsf(n00) > thr) || (x1 != y1 && fabsf(n11) > thr) || (x0 != y1 && fabsf(n01) > thr);
-        if (ag != ah) {
-          // off the diagonal the fourth entry is distinct; on it, it is the mirror of n01
-          An[x1 * D + y0] = n10;
-          An[y0 * D + x1] = n10;
-          off |= x1 != y0 && fabsf(n10) > thr;
-        }
-      } else {
-        // row x of V in the columns of group h (the resting column, h = 0, is unchanged)
-        const int v = t - NA, x = v / G, h = v % G;
-        if (h == 0) continue;
-        const int y0 = wrap_d<D>(r + h), y1 = wrap_d<D>(r - h);
-        const float2 c0 = co[y0], c1 = co[y1];
-        const float v0 = V[x * D + y0], v1 = V[x * D + y1];
-        V[x * D + y0] = fmaf(c0.x, v0, c0.y * v1);
-        V[x * D + y1] = fmaf(c1.x, v1, c1.y * v0);
-      }
-    }
-    big = __syncthreads_or(off) != 0;
-    cur ^= 1;
-  }
-  for (int e = tid; e < D * D; e += kWJacobiThreads) Vout[e] = V[e];
+  eig_vectors_f32<D, kWEigThreads>(Sf, tw, Vout, Vout + D * D, BlockBar{});
 }
 
 // Block k: lambda_k = v_k^T Sigma v_k / v_k^T v_k in float64.  The last block
@@ -566,7 +424,7 @@ __global__ void __launch_bounds__(kWTailThreads) k_ne_wide_tail(const double* __
   __shared__ double s_top[2];
   __shared__ int s_m;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  if (!(tot[D * D + D] >= 1.0)) return;  // no patches: the Jacobi launch wrote the results
+  if (!(tot[D * D + D] >= 1.0)) return;  // no patches: the eigenvector launch wrote the results
   const int k = blockIdx.x;
   if (tid < D) s_v[tid] = double(V[tid * D + k]);
   __syncthreads();
@@ -592,7 +450,8 @@ __global__ void __launch_bounds__(kWTailThreads) k_ne_wide_tail(const double* __
   __syncthreads();
   if (tid == 0) {
     const double nn = s_red[0][0] + s_red[1][0], dd = s_red[0][1] + s_red[1][1];
-    lam[k] = dd > 0.0 ? nn / dd : 0.0;
+    const double q = dd > 0.0 ? nn / dd : 0.0;
+    lam[k] = isfinite(q) ? q : double(V[D * D + k]);  // else the float32 multisection value
     __threadfence();
     s_last = atomicAdd(done, 1u) == unsigned(D - 1);
   }
@@ -673,9 +532,16 @@ cudaError_t launch_wide(int stage, int n, int bits, int dtype, const GraphBufs& 
                         : launch_kernel(k_ne_wide_reduce<1>, rgrid, rblock, 0, stream, false,
                                         static_cast<const double*>(w.part), used, D, w.tot);
     }
-    case 2:
-      return launch_kernel(k_ne_wide_jacobi<D>, dim3(1), dim3(kWJacobiThreads), 0, stream, false,
+    case 2: {
+      static std::atomic<unsigned long long> configured{0};  // the shared-memory limit, once per device
+      const cudaError_t e = once_per_device(configured, [] {
+        return cudaFuncSetAttribute(k_ne_wide_eigvec<D>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    int(wide_eig_smem<D>()));
+      });
+      if (e != cudaSuccess) return e;
+      return launch_kernel(k_ne_wide_eigvec<D>, dim3(1), dim3(kWEigThreads), wide_eig_smem<D>(), stream, false,
                            static_cast<const double*>(w.tot), w.S, w.V, sc, sigma_out);
+    }
     case 3:
       return launch_kernel(k_ne_wide_tail<D>, dim3(D), dim3(kWTailThreads), 0, stream, false,
                            static_cast<const double*>(w.tot), static_cast<const double*>(w.S),
