@@ -20,7 +20,13 @@
  *  - Errors are returned as fgbd_status, never thrown or trapped.  Errors
  *    found on the device (a coordinate out of range, a bounded device wait
  *    that gave up) are latched in the context and returned by the next call
- *    that synchronises (fgbd_sync, fgbd_get_stats, fgbd_graph_csr).
+ *    that synchronises (fgbd_sync, fgbd_get_stats, fgbd_graph_export, a call
+ *    given a _host output).
+ *  - The four steps act on the context's working graph, the one built by its
+ *    last fgbd_build_graph (one frame at a time, as in Section 2.1); it is
+ *    kept in the scan orders' own form, not as CSR.  fgbd_graph_export makes
+ *    a standalone CSR copy of it (an fgbd_graph) for callers that want the
+ *    graph itself.
  *  - A context is not thread-safe; use one per stream.  The context owns all
  *    scratch memory, allocated once by fgbd_ctx_create for `capacity` points;
  *    the per-frame calls allocate nothing.
@@ -34,7 +40,7 @@
 extern "C" {
 #endif
 
-#define FGBD_ABI_VERSION 2
+#define FGBD_ABI_VERSION 3
 #define FGBD_PATCH_DIM 21   /* D = 3 colour channels x (1 point + 6 neighbours), Section 2.3, window 1 */
 #define FGBD_MAX_WINDOW 3   /* largest window implemented */
 #define FGBD_PATCH_DIM_MAX 57  /* D = 3 (6 w + 1) at window FGBD_MAX_WINDOW */
@@ -152,12 +158,15 @@ fgbd_status fgbd_build_graph(fgbd_ctx* ctx, const int32_t* xyz, int64_t n, void*
  * covariance, its eigenvalues, and
  * sigma_est = sqrt(tau) with tau the mean of the eigenvalues left by the tail
  * rule.  Also computes each point's patch colour spread for FSLR.
- *   rgb:        colours [n][3] device, dtype FGBD_U8 or FGBD_F32.
- *   sigma_est:  optional device double receiving sigma_est (may be NULL).
+ *   rgb:             colours [n][3] device, dtype FGBD_U8 or FGBD_F32.
+ *   sigma_est:       optional device double receiving sigma_est (may be NULL).
+ *   sigma_est_host:  optional host double receiving sigma_est (may be NULL);
+ *                    if given, the call synchronises `stream` and returns a
+ *                    latched device error like fgbd_sync.
  * With no complete patch sigma_est is 0.  Errors: FGBD_EINVAL, FGBD_ESTATE
  * (no graph), FGBD_ECUDA. */
 fgbd_status fgbd_estimate_noise(fgbd_ctx* ctx, const void* rgb, int32_t dtype, double* sigma_est,
-                                void* stream);
+                                double* sigma_est_host, void* stream);
 
 /* Section 2.4 (FSLR, Eq. 5-6): the integer filter power q minimising
  * |sigma_est^2 - (sum y^2 - sum x_q^2)/N| over the points whose mean patch
@@ -170,9 +179,12 @@ fgbd_status fgbd_estimate_noise(fgbd_ctx* ctx, const void* rgb, int32_t dtype, d
  *               unchanged contents).
  *   sigma_est:  device double to use as sigma_est, or NULL for this context's estimate.
  *   q_out:      optional device int32 receiving q* (may be NULL).
+ *   q_host:     optional host int32 receiving q* (may be NULL); if given, the
+ *               call synchronises `stream` and returns a latched device error
+ *               like fgbd_sync.
  * Errors: FGBD_EINVAL, FGBD_ESTATE (no estimate, or other colours), FGBD_ECUDA. */
 fgbd_status fgbd_select_filter(fgbd_ctx* ctx, const void* rgb, int32_t dtype, const double* sigma_est,
-                               int32_t* q_out, void* stream);
+                               int32_t* q_out, int32_t* q_host, void* stream);
 
 /* Eq. 5: f_out = (D_g^{-1} W_g)^q f_in with W_g = D + W, D_g = 2D, i.e. q steps
  * of x <- x/2 + D^{-1} W x / 2 with W the Gaussian weights of Eq. 4.
@@ -305,14 +317,40 @@ fgbd_status fgbd_get_stats(fgbd_ctx* ctx, fgbd_stats* out_host, void* stream);
 
 /* The graph of the last build as CSR in input order, rows sorted by column,
  * with the Eq. 4 weights w_ij = exp(-|g_i - g_j|^2 / sigma_g^2) (float32; long
- * edges may underflow to 0).  Synchronises `stream`.
+ * edges may underflow to 0), copied into caller buffers.  Synchronises `stream`.
  *   row_ptr:   int64 [n+1] device, or NULL to only query *nnz_host.
  *   col:       int32 [col_capacity] device (ignored if row_ptr is NULL).
  *   w:         float32 [col_capacity] device, or NULL.
  *   nnz_host:  receives the number of stored entries (2 x edges).
  * Errors: FGBD_EINVAL (col_capacity too small), FGBD_ESTATE, FGBD_ECUDA. */
-fgbd_status fgbd_graph_csr(fgbd_ctx* ctx, int64_t* row_ptr, int32_t* col, float* w, int64_t col_capacity,
-                           int64_t* nnz_host, void* stream);
+fgbd_status fgbd_graph_csr_copy(fgbd_ctx* ctx, int64_t* row_ptr, int32_t* col, float* w, int64_t col_capacity,
+                                int64_t* nnz_host, void* stream);
+
+/* A standalone copy of a context's graph (Section 2.2) as symmetric CSR in
+ * input order: row_ptr int64 [n+1], col int32 [nnz] (rows sorted by column),
+ * the Eq. 4 weights w float32 [nnz], and sigma_g.  It owns its device memory
+ * (on the context's device) and outlives the context. */
+typedef struct fgbd_graph fgbd_graph;
+
+/* Export the graph of the context's last build as a new fgbd_graph (device
+ * memory allocated here, about 12 bytes per stored entry plus 8 per point).
+ * Synchronises `stream`; returns a latched device error like fgbd_sync.
+ * Release it with fgbd_graph_free.  Errors: FGBD_EINVAL, FGBD_ESTATE (no
+ * graph), FGBD_ENOMEM, FGBD_ECUDA. */
+fgbd_status fgbd_graph_export(fgbd_ctx* ctx, fgbd_graph** out, void* stream);
+
+/* Borrowed views of an exported graph: device pointers that stay valid until
+ * fgbd_graph_free(g), and host scalars.  Any output pointer may be NULL.
+ *   row_ptr, col, w: device arrays as described at fgbd_graph (NULL when the
+ *                    graph has no points / no entries).
+ *   n_host, nnz_host, sigma_g_host: points, stored entries (2 x edges), the
+ *                    mean edge length sigma_g of Eq. 4.
+ * Errors: FGBD_EINVAL (g is NULL). */
+fgbd_status fgbd_graph_csr(const fgbd_graph* g, const int64_t** row_ptr, const int32_t** col, const float** w,
+                           int64_t* n_host, int64_t* nnz_host, double* sigma_g_host);
+
+/* Free an exported graph and its device memory.  NULL is ignored. */
+void fgbd_graph_free(fgbd_graph* g);
 
 /* The three scan orders of the last build: orders[l][k] is the input index of
  * the k-th point along code l+1 (Eq. 1-3).  orders: int32 [3][n] device. */

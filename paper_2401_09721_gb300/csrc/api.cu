@@ -126,6 +126,18 @@ struct fgbd_ctx {
   int n_timed = 0;
 };
 
+// An exported graph: CSR in input order with the Eq. 4 weights (fgbd_graph_export).
+struct fgbd_graph {
+  int device = 0;
+  int64_t n = 0;
+  int64_t nnz = 0;
+  double sigma_g = 0.0;
+  void* mem = nullptr;
+  int64_t* row_ptr = nullptr;
+  int32_t* col = nullptr;
+  float* w = nullptr;
+};
+
 namespace {
 
 // NVTX range over one API call (header-only NVTX 3: no cost unless a profiler is attached)
@@ -785,19 +797,30 @@ fgbd_status fgbd_build_graph(fgbd_ctx* ctx, const int32_t* xyz, int64_t n, void*
   return do_build(ctx, xyz, n, as_stream(stream));
 }
 
-fgbd_status fgbd_estimate_noise(fgbd_ctx* ctx, const void* rgb, int32_t dtype, double* sigma_est, void* stream) {
+fgbd_status fgbd_estimate_noise(fgbd_ctx* ctx, const void* rgb, int32_t dtype, double* sigma_est,
+                                double* sigma_est_host, void* stream) {
   NvtxRange nvtx_("fgbd_estimate_noise");
   if (!ctx) return FGBD_EINVAL;
   DeviceGuard g(ctx->device);
-  return do_estimate(ctx, rgb, dtype, sigma_est, as_stream(stream));
+  const cudaStream_t st = as_stream(stream);
+  fgbd_status s = do_estimate(ctx, rgb, dtype, sigma_est, st);
+  if (s != FGBD_OK || !sigma_est_host) return s;
+  s = take_device_status(ctx, st);
+  FGBD_CUDA(ctx, cudaMemcpy(sigma_est_host, &ctx->sc->sigma_est, sizeof(double), cudaMemcpyDeviceToHost));
+  return s;
 }
 
 fgbd_status fgbd_select_filter(fgbd_ctx* ctx, const void* rgb, int32_t dtype, const double* sigma_est,
-                               int32_t* q_out, void* stream) {
+                               int32_t* q_out, int32_t* q_host, void* stream) {
   NvtxRange nvtx_("fgbd_select_filter");
   if (!ctx) return FGBD_EINVAL;
   DeviceGuard g(ctx->device);
-  return do_select(ctx, rgb, dtype, sigma_est, q_out, nullptr, FGBD_F32, as_stream(stream));
+  const cudaStream_t st = as_stream(stream);
+  fgbd_status s = do_select(ctx, rgb, dtype, sigma_est, q_out, nullptr, FGBD_F32, st);
+  if (s != FGBD_OK || !q_host) return s;
+  s = take_device_status(ctx, st);
+  FGBD_CUDA(ctx, cudaMemcpy(q_host, &ctx->sc->q_sel, sizeof(int32_t), cudaMemcpyDeviceToHost));
+  return s;
 }
 
 fgbd_status fgbd_denoise(fgbd_ctx* ctx, const void* rgb_in, int32_t in_dtype, int32_t q, void* rgb_out,
@@ -1138,8 +1161,8 @@ fgbd_status fgbd_get_stats(fgbd_ctx* ctx, fgbd_stats* out, void* stream) {
   return s;
 }
 
-fgbd_status fgbd_graph_csr(fgbd_ctx* ctx, int64_t* row_ptr, int32_t* col, float* w, int64_t col_capacity,
-                           int64_t* nnz_host, void* stream) {
+fgbd_status fgbd_graph_csr_copy(fgbd_ctx* ctx, int64_t* row_ptr, int32_t* col, float* w, int64_t col_capacity,
+                                int64_t* nnz_host, void* stream) {
   if (!ctx || !nnz_host) return FGBD_EINVAL;
   DeviceGuard g(ctx->device);
   const cudaStream_t st = as_stream(stream);
@@ -1158,6 +1181,76 @@ fgbd_status fgbd_graph_csr(fgbd_ctx* ctx, int64_t* row_ptr, int32_t* col, float*
               launch_csr_fill(n, ctx->params.bits, ctx->gb, row_ptr, col, w, col_capacity, ctx->sc, st));
   FGBD_CUDA(ctx, cudaStreamSynchronize(st));
   return FGBD_OK;
+}
+
+fgbd_status fgbd_graph_export(fgbd_ctx* ctx, fgbd_graph** out, void* stream) {
+  if (!ctx || !out) return FGBD_EINVAL;
+  *out = nullptr;
+  DeviceGuard g(ctx->device);
+  const cudaStream_t st = as_stream(stream);
+  if (!ctx->has_graph) return FGBD_ESTATE;
+  const fgbd_status s = take_device_status(ctx, st);
+  if (s != FGBD_OK) return s;
+  unsigned long long edges = 0, dist = 0;
+  FGBD_CUDA(ctx, cudaMemcpy(&edges, &ctx->sc->n_edges, sizeof(edges), cudaMemcpyDeviceToHost));
+  FGBD_CUDA(ctx, cudaMemcpy(&dist, &ctx->sc->dist_fx, sizeof(dist), cudaMemcpyDeviceToHost));
+  fgbd_graph* gr = new (std::nothrow) fgbd_graph();
+  if (!gr) return FGBD_ENOMEM;
+  gr->device = ctx->device;
+  gr->n = ctx->n;
+  gr->nnz = int64_t(2 * edges);
+  gr->sigma_g = edges ? double(dist) / double(1ull << kDistShift) / double(edges) : 0.0;
+  const size_t rp_b = align_up(size_t(gr->n + 1) * 8, 256), col_b = align_up(size_t(gr->nnz) * 4, 256);
+  if (cudaMalloc(&gr->mem, rp_b + 2 * col_b) != cudaSuccess) {
+    cudaGetLastError();
+    delete gr;
+    return FGBD_ENOMEM;
+  }
+  char* base = static_cast<char*>(gr->mem);
+  gr->row_ptr = reinterpret_cast<int64_t*>(base);
+  gr->col = reinterpret_cast<int32_t*>(base + rp_b);
+  gr->w = reinterpret_cast<float*>(base + rp_b + col_b);
+  const int n = ctx->n;
+  cudaError_t e = cudaSuccess;
+  {
+    LaunchScope s1(ctx, "csr_degree", st);
+    e = launch_csr_degree(n, ctx->gb, gr->row_ptr, st);
+  }
+  if (e == cudaSuccess) {
+    LaunchScope s2(ctx, "csr_scan", st);
+    e = launch_scan_i64(gr->row_ptr, int64_t(n) + 1, ctx->scan_tmp, st);
+  }
+  if (e == cudaSuccess) {
+    LaunchScope s3(ctx, "csr_fill", st);
+    e = launch_csr_fill(n, ctx->params.bits, ctx->gb, gr->row_ptr, gr->col, gr->w, gr->nnz, ctx->sc, st);
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) {
+    cudaFree(gr->mem);
+    delete gr;
+    return cuda_fail(ctx, e, "fgbd_graph_export");
+  }
+  *out = gr;
+  return FGBD_OK;
+}
+
+fgbd_status fgbd_graph_csr(const fgbd_graph* g, const int64_t** row_ptr, const int32_t** col, const float** w,
+                           int64_t* n_host, int64_t* nnz_host, double* sigma_g_host) {
+  if (!g) return FGBD_EINVAL;
+  if (row_ptr) *row_ptr = g->n > 0 ? g->row_ptr : nullptr;
+  if (col) *col = g->nnz > 0 ? g->col : nullptr;
+  if (w) *w = g->nnz > 0 ? g->w : nullptr;
+  if (n_host) *n_host = g->n;
+  if (nnz_host) *nnz_host = g->nnz;
+  if (sigma_g_host) *sigma_g_host = g->sigma_g;
+  return FGBD_OK;
+}
+
+void fgbd_graph_free(fgbd_graph* g) {
+  if (!g) return;
+  DeviceGuard dg(g->device);
+  cudaFree(g->mem);  // waits for work that uses it
+  delete g;
 }
 
 fgbd_status fgbd_get_orders(fgbd_ctx* ctx, int32_t* orders, void* stream) {

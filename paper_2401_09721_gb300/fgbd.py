@@ -24,7 +24,7 @@ PATCH_DIM = 21        # FGBD_PATCH_DIM (window 1)
 MAX_WINDOW = 3        # FGBD_MAX_WINDOW
 PATCH_DIM_MAX = 57    # FGBD_PATCH_DIM_MAX
 Q_CAP = 256
-ABI_VERSION = 2
+ABI_VERSION = 3
 
 STATUS = {
     0: "FGBD_OK",
@@ -106,8 +106,8 @@ _SIGS = {
     "fgbd_ctx_destroy": (None, [_P]),
     "fgbd_last_error": (ctypes.c_char_p, [_P]),
     "fgbd_build_graph": (ctypes.c_int, [_P, _P, ctypes.c_int64, _P]),
-    "fgbd_estimate_noise": (ctypes.c_int, [_P, _P, ctypes.c_int32, _P, _P]),
-    "fgbd_select_filter": (ctypes.c_int, [_P, _P, ctypes.c_int32, _P, _P, _P]),
+    "fgbd_estimate_noise": (ctypes.c_int, [_P, _P, ctypes.c_int32, _P, ctypes.POINTER(ctypes.c_double), _P]),
+    "fgbd_select_filter": (ctypes.c_int, [_P, _P, ctypes.c_int32, _P, _P, ctypes.POINTER(ctypes.c_int32), _P]),
     "fgbd_denoise": (ctypes.c_int, [_P, _P, ctypes.c_int32, ctypes.c_int32, _P, ctypes.c_int32, _P]),
     "fgbd_run": (ctypes.c_int, [_P, _P, ctypes.c_int64, _P, ctypes.c_int32, _P, ctypes.c_int32, _P]),
     "fgbd_run_reuse": (ctypes.c_int, [_P, _P, ctypes.c_int64, _P, ctypes.c_int32, _P, ctypes.c_int32, _P]),
@@ -121,7 +121,12 @@ _SIGS = {
     "fgbd_filter_backward": (ctypes.c_int, [_P, _P, _P, _P, _P]),
     "fgbd_sync": (ctypes.c_int, [_P, _P]),
     "fgbd_get_stats": (ctypes.c_int, [_P, ctypes.POINTER(Stats), _P]),
-    "fgbd_graph_csr": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64), _P]),
+    "fgbd_graph_csr_copy": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64), _P]),
+    "fgbd_graph_export": (ctypes.c_int, [_P, ctypes.POINTER(_P), _P]),
+    "fgbd_graph_csr": (ctypes.c_int, [_P, ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(_P),
+                                      ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
+                                      ctypes.POINTER(ctypes.c_double)]),
+    "fgbd_graph_free": (None, [_P]),
     "fgbd_get_orders": (ctypes.c_int, [_P, _P, _P]),
     "fgbd_get_fslr": (ctypes.c_int, [_P, _P, _P, _P]),
     "fgbd_set_timing": (ctypes.c_int, [_P, ctypes.c_int32]),
@@ -213,23 +218,31 @@ def fgbd_build_graph(ctx, xyz: torch.Tensor, stream=None) -> None:
     _check(lib().fgbd_build_graph(ctx, _ptr(xyz), xyz.shape[0], _stream(stream)), "fgbd_build_graph", ctx)
 
 
-def fgbd_estimate_noise(ctx, rgb: torch.Tensor, sigma_out: torch.Tensor | None = None, stream=None) -> None:
+def fgbd_estimate_noise(ctx, rgb: torch.Tensor, sigma_out: torch.Tensor | None = None, stream=None,
+                        host: bool = False):
+    """Enqueue the noise estimate; with host=True also synchronise and return sigma_est (float)."""
     _need_cuda(rgb, "rgb")
     if sigma_out is not None and (sigma_out.dtype != torch.float64 or not sigma_out.is_cuda):
         raise TypeError("sigma_out must be a CUDA float64 tensor")
-    _check(lib().fgbd_estimate_noise(ctx, _ptr(rgb), _dtype_code(rgb), _ptr(sigma_out), _stream(stream)),
+    h = ctypes.c_double() if host else None
+    _check(lib().fgbd_estimate_noise(ctx, _ptr(rgb), _dtype_code(rgb), _ptr(sigma_out),
+                                     ctypes.byref(h) if host else None, _stream(stream)),
            "fgbd_estimate_noise", ctx)
+    return h.value if host else None
 
 
 def fgbd_select_filter(ctx, rgb: torch.Tensor, sigma_est: torch.Tensor | None = None,
-                       q_out: torch.Tensor | None = None, stream=None) -> None:
+                       q_out: torch.Tensor | None = None, stream=None, host: bool = False):
+    """Enqueue the q search; with host=True also synchronise and return q* (int)."""
     _need_cuda(rgb, "rgb")
     if sigma_est is not None and (sigma_est.dtype != torch.float64 or not sigma_est.is_cuda):
         raise TypeError("sigma_est must be a CUDA float64 tensor")
     if q_out is not None and (q_out.dtype != torch.int32 or not q_out.is_cuda):
         raise TypeError("q_out must be a CUDA int32 tensor")
+    h = ctypes.c_int32() if host else None
     _check(lib().fgbd_select_filter(ctx, _ptr(rgb), _dtype_code(rgb), _ptr(sigma_est), _ptr(q_out),
-                                    _stream(stream)), "fgbd_select_filter", ctx)
+                                    ctypes.byref(h) if host else None, _stream(stream)), "fgbd_select_filter", ctx)
+    return h.value if host else None
 
 
 def fgbd_denoise(ctx, rgb_in: torch.Tensor | None, q: int, rgb_out: torch.Tensor, stream=None) -> None:
@@ -377,15 +390,63 @@ def fgbd_get_stats(ctx, stream=None) -> dict:
     return s.as_dict()
 
 
-def fgbd_graph_csr(ctx, n: int, device, with_weights: bool = True, stream=None):
+def fgbd_graph_csr_copy(ctx, n: int, device, with_weights: bool = True, stream=None):
     nnz = ctypes.c_int64()
-    _check(lib().fgbd_graph_csr(ctx, None, None, None, 0, ctypes.byref(nnz), _stream(stream)), "fgbd_graph_csr", ctx)
+    _check(lib().fgbd_graph_csr_copy(ctx, None, None, None, 0, ctypes.byref(nnz), _stream(stream)),
+           "fgbd_graph_csr_copy", ctx)
     row_ptr = torch.empty(n + 1, dtype=torch.int64, device=device)
     col = torch.empty(max(nnz.value, 1), dtype=torch.int32, device=device)
     w = torch.empty(max(nnz.value, 1), dtype=torch.float32, device=device) if with_weights else None
-    _check(lib().fgbd_graph_csr(ctx, _ptr(row_ptr), _ptr(col), _ptr(w), col.numel(), ctypes.byref(nnz),
-                                _stream(stream)), "fgbd_graph_csr", ctx)
+    _check(lib().fgbd_graph_csr_copy(ctx, _ptr(row_ptr), _ptr(col), _ptr(w), col.numel(), ctypes.byref(nnz),
+                                     _stream(stream)), "fgbd_graph_csr_copy", ctx)
     return row_ptr, col[: nnz.value], (w[: nnz.value] if w is not None else None)
+
+
+class _DeviceArray:
+    """A borrowed device array, exposed through __cuda_array_interface__ so that
+    torch.as_tensor views it without a copy; it keeps its owner alive."""
+
+    def __init__(self, ptr: int, n: int, typestr: str, owner):
+        self._owner = owner
+        self.__cuda_array_interface__ = {"shape": (n,), "typestr": typestr, "data": (ptr, False), "version": 2}
+
+
+class Graph:
+    """An exported graph (fgbd_graph): CSR in input order, the Eq. 4 weights and
+    sigma_g.  row_ptr, col and w are tensors viewing the library's device
+    memory (no copy); they stay valid while this object (or a view) is alive."""
+
+    def __init__(self, handle, device):
+        self.handle = handle
+        self.device = device
+        rp, col, w = _P(), _P(), _P()
+        n, nnz, sg = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_double()
+        _check(lib().fgbd_graph_csr(handle, ctypes.byref(rp), ctypes.byref(col), ctypes.byref(w), ctypes.byref(n),
+                                    ctypes.byref(nnz), ctypes.byref(sg)), "fgbd_graph_csr")
+        self.n, self.nnz, self.sigma_g = n.value, nnz.value, sg.value
+
+        def view(ptr, count, typestr, dtype):
+            if not ptr.value or count == 0:
+                return torch.empty(count, dtype=dtype, device=device)
+            return torch.as_tensor(_DeviceArray(ptr.value, count, typestr, self), device=device)
+
+        self.row_ptr = view(rp, self.n + 1 if self.n > 0 else 0, "<i8", torch.int64)
+        self.col = view(col, self.nnz, "<i4", torch.int32)
+        self.w = view(w, self.nnz, "<f4", torch.float32)
+
+    def __del__(self):
+        h, self.handle = getattr(self, "handle", None), None
+        if h is not None:
+            try:
+                lib().fgbd_graph_free(h)
+            except Exception:
+                pass
+
+
+def fgbd_graph_export(ctx, device, stream=None) -> Graph:
+    out = _P()
+    _check(lib().fgbd_graph_export(ctx, ctypes.byref(out), _stream(stream)), "fgbd_graph_export", ctx)
+    return Graph(out, device)
 
 
 def fgbd_get_orders(ctx, n: int, device, stream=None) -> torch.Tensor:
@@ -449,11 +510,11 @@ class Context:
         fgbd_build_graph(self.handle, xyz, stream)
         self.n = xyz.shape[0]
 
-    def estimate_noise(self, rgb, sigma_out=None, stream=None):
-        fgbd_estimate_noise(self.handle, rgb, sigma_out, stream)
+    def estimate_noise(self, rgb, sigma_out=None, stream=None, host=False):
+        return fgbd_estimate_noise(self.handle, rgb, sigma_out, stream, host)
 
-    def select_filter(self, rgb, sigma_est=None, q_out=None, stream=None):
-        fgbd_select_filter(self.handle, rgb, sigma_est, q_out, stream)
+    def select_filter(self, rgb, sigma_est=None, q_out=None, stream=None, host=False):
+        return fgbd_select_filter(self.handle, rgb, sigma_est, q_out, stream, host)
 
     def denoise(self, rgb_in, q, out_dtype=torch.float32, out=None, stream=None):
         if out is None:
@@ -507,7 +568,10 @@ class Context:
         return fgbd_get_stats(self.handle, stream)
 
     def graph_csr(self, with_weights=True, stream=None):
-        return fgbd_graph_csr(self.handle, self.n, self.device, with_weights, stream)
+        return fgbd_graph_csr_copy(self.handle, self.n, self.device, with_weights, stream)
+
+    def export_graph(self, stream=None) -> Graph:
+        return fgbd_graph_export(self.handle, self.device, stream)
 
     def orders(self, stream=None):
         return fgbd_get_orders(self.handle, self.n, self.device, stream)

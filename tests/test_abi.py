@@ -57,7 +57,7 @@ def test_only_the_abi_is_exported():
 def test_host_side_checks_without_gpu(so):
     from paper_2401_09721_gb300 import fgbd
     lib = fgbd.lib()
-    assert lib.fgbd_abi_version() == fgbd.ABI_VERSION == 2
+    assert lib.fgbd_abi_version() == fgbd.ABI_VERSION == 3
     p = fgbd.Params()
     assert lib.fgbd_params_default(ctypes.byref(p)) == 0
     assert (p.bits, p.window, p.fslr_factor, p.q_max) == (10, 1, 2.0, 64)
@@ -93,6 +93,13 @@ def test_host_side_checks_without_gpu(so):
     assert lib.fgbd_status_str(0) == b"FGBD_OK"
     assert lib.fgbd_status_str(5).startswith(b"FGBD_ETIMEOUT")
     assert lib.fgbd_debug_set_wait_limit(None, 0) == 1
+    # the graph handle: argument checks before any CUDA call
+    g = ctypes.c_void_p()
+    assert lib.fgbd_graph_export(None, ctypes.byref(g), None) == 1
+    assert lib.fgbd_graph_csr(None, None, None, None, None, None, None) == 1
+    lib.fgbd_graph_free(None)                                               # NULL is ignored
+    assert lib.fgbd_estimate_noise(None, None, 0, None, None, None) == 1
+    assert lib.fgbd_select_filter(None, None, 0, None, None, None, None) == 1
 
 
 def test_binding_structs_match_the_header_layout(tmp_path):
