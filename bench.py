@@ -82,7 +82,9 @@ def generate(fn, items):
     import multiprocessing as mp
     items = list(items)
     workers = max(1, min(len(items), len(os.sched_getaffinity(0))))
-    if workers == 1:
+    # never from inside a pool worker (a script without a __main__ guard would
+    # otherwise spawn pools recursively)
+    if workers == 1 or mp.current_process().name != "MainProcess":
         return [fn(i) for i in items]
     with mp.get_context("spawn").Pool(workers) as pool:
         return pool.map(fn, items, chunksize=1)
@@ -90,17 +92,20 @@ def generate(fn, items):
 
 # ------------------------------------------------------------------ batched path
 
-def measure_batched(fgbd, torch, dev, stream, flush, repeats=3):
-    """16 frames of uneven size (200k..1.2M sphere points at b = 10, sigma ~ U[10, 50]):
-    the same frames through 16 sequential fgbd_run calls, one fgbd_run_batch call,
-    and that call replayed from a CUDA graph.  Device time per pass over the 16
-    frames, L2 flushed before each pass (not timed)."""
-    frames = generate(_batch_frame, range(16))
-    ctxs = [fgbd.Context(fr.n, bits=10) for fr in frames]
+def measure_batched(fgbd, torch, dev, stream, flush, frames, workload, repeats=3):
+    """A batch of frames through (a) one fgbd_run per frame, (b) fgbd_run_batch
+    with every frame on its own stream, (c) fgbd_run_batch segmented (one
+    launch per stage over 16 frames), then (d) fgbd_tune_batch's choice among
+    those (and the block shapes), run directly and replayed from a CUDA graph.
+    Device time per pass over the frames, L2 flushed before each pass (not
+    timed); every output is checked against (a)'s bit for bit."""
+    ctxs = [fgbd.Context(fr.n, bits=fr.bits) for fr in frames]
     xs = [torch.from_numpy(fr.xyz).to(dev) for fr in frames]
     cs = [torch.from_numpy(fr.noisy).to(dev) for fr in frames]
     outs = [torch.empty((fr.n, 3), dtype=torch.uint8, device=dev) for fr in frames]
     total = sum(fr.n for fr in frames)
+    mean = int(total / len(frames))
+    didx = dev.index if dev.index is not None else torch.cuda.current_device()
 
     def plain():
         for c, x, ci, co in zip(ctxs, xs, cs, outs):
@@ -123,29 +128,44 @@ def measure_batched(fgbd, torch, dev, stream, flush, repeats=3):
             ms.append(a.elapsed_time(b))
         return float(np.median(ms))
 
-    res = {"frames": len(frames), "points": total, "sizes": [fr.n for fr in frames],
-           "workload": "16 sphere frames, N ~ U[200k, 1.2M] at b=10, sigma ~ U[10, 50], seeds 1..16"}
+    res = {"frames": len(frames), "points": total, "sizes": [fr.n for fr in frames], "workload": workload}
     res["plain_ms"] = timed(plain)
-    plain_outs = [o.clone() for o in outs]
+    ref = [o.clone() for o in outs]
+    same = True
+    base = fgbd.fgbd_get_batch_shape(didx, mean)
+    for name, sf in (("streams", 0), ("segmented", 16)):
+        fgbd.fgbd_set_batch_shape(didx, mean, dict(base, seg_frames=sf))
+        res[f"{name}_ms"] = timed(batched)
+        same &= all(torch.equal(a, b) for a, b in zip(outs, ref))
+    fgbd.fgbd_set_batch_shape(didx, mean, None)
+    shape, _ = fgbd.Context.tune_batch(ctxs, xs, cs, outs=outs)
+    res["tuned_shape"] = shape
     res["batched_ms"] = timed(batched)
-    res["identical_to_plain"] = all(torch.equal(a, b) for a, b in zip(outs, plain_outs))
+    same &= all(torch.equal(a, b) for a, b in zip(outs, ref))
     try:
         g = torch.cuda.CUDAGraph()
         with torch.cuda.graph(g):
             batched()
         res["graph_ms"] = timed(g.replay)
-        res["graph_identical_to_plain"] = all(torch.equal(a, b) for a, b in zip(outs, plain_outs))
+        same &= all(torch.equal(a, b) for a, b in zip(outs, ref))
     except RuntimeError as e:  # capture refused: report why, keep the other numbers
         res["graph_ms"] = None
         res["graph_error"] = str(e).splitlines()[0][:200]
-    for key in ("plain", "batched", "graph"):
-        ms = res[f"{key}_ms"]
+    res["identical_to_plain"] = bool(same)
+    for key in ("plain", "streams", "segmented", "batched", "graph"):
+        ms = res.get(f"{key}_ms")
         if ms:
             res[f"{key}_frames_per_s"] = len(frames) / (ms / 1e3)
             res[f"{key}_mpoints_per_s"] = total / (ms / 1e3) / 1e6
+    fgbd.fgbd_set_batch_shape(didx, mean, None)
     for c in ctxs:
         c.close()
     return res
+
+
+def _small_batch_frame(f):
+    from paper_2401_09721_gb300 import synth
+    return synth.batch_frame(f, lo=20_000, hi=100_000, seed=501, bits=9)
 
 
 # ------------------------------------------------------------------ differentiable filter
@@ -722,8 +742,12 @@ def run_fgbd(args):
                            "q": qv, "psnr_db": ps}
 
     batched = None
+    batched_small = None
     if not args.no_batch:
-        batched = measure_batched(fgbd, torch, dev, stream, flush)
+        batched = measure_batched(fgbd, torch, dev, stream, flush, generate(_batch_frame, range(16)),
+                                  "16 sphere frames, N ~ U[200k, 1.2M] at b=10, sigma ~ U[10, 50], seeds 1..16")
+        batched_small = measure_batched(fgbd, torch, dev, stream, flush, generate(_small_batch_frame, range(64)),
+                                        "64 sphere frames, N ~ U[20k, 100k] at b=9, sigma ~ U[10, 50], seeds 501..564")
     differentiable = None
     if not args.no_diff:
         differentiable = measure_differentiable(fgbd, torch, dev, stream)
@@ -744,7 +768,8 @@ def run_fgbd(args):
             "gpu_launches": int(launches), "roofline": roofline, "cpu_baseline": cpu,
             "clocks": clocks.summary(), "stages_ms": stages,
             "q_mean": q_mean, "wall_s": wall, "step_ms_min": min(step_ms), "step_ms_max": max(step_ms),
-            "ablations": ablations, "batched": batched, "differentiable": differentiable,
+            "ablations": ablations, "batched": batched, "batched_small": batched_small,
+            "differentiable": differentiable,
             "streaming": streaming,
         }
         print(json.dumps(line), flush=True)

@@ -240,30 +240,76 @@ fgbd_status fgbd_run_reuse(fgbd_ctx* ctx, const int32_t* xyz, int64_t n, const v
                            void* rgb_out, int32_t out_dtype, void* stream);
 
 /* Batched path (no counterpart in the paper, which processes one frame at a
- * time): fgbd_run on `count` frames, frame f with its own context ctxs[f],
- * all enqueued in one call and overlapped on the GPU.  A single 1M-point frame
- * leaves most of the GPU idle in its short, latency-bound kernels; frames run
- * side by side fill it.
+ * time): fgbd_run on `count` frames of any sizes, frame f with its own context
+ * ctxs[f], all enqueued in one call.  A single 1M-point frame leaves most of
+ * the GPU idle in its short, latency-bound kernels; frames run side by side
+ * fill it.
  *   ctxs, xyz, n, rgb_in, in_dtype, rgb_out, out_dtype: host arrays of
  *     `count` entries, the fgbd_run arguments of each frame (device buffers).
  *   count: 0..FGBD_BATCH_MAX; the contexts must be distinct and on one device.
- * Each context runs its frame on a stream of its own, forked from `stream`
- * (everything earlier on `stream` finishes first) and joined back into it
- * (later work on `stream` waits for every frame).  The selection/filter steps,
- * cooperative launches that use the whole GPU, run one frame after another.
- * Results, stats and errors are per context, exactly as after fgbd_run (the
- * outputs are bit-identical).  The call contains no host synchronisation, so
- * it can be captured into a CUDA graph once the contexts have run a frame (the
- * first launches set kernel attributes).  Like fgbd_run, the second call with
- * the same contexts and buffers records a CUDA graph of the whole batch (kept
- * by ctxs[0], up to 4 of them) and later calls launch it.
- * Contexts of any window may share a batch.
+ * Segmented batches: when every frame has at least one point, window 1, the
+ * same ablation switches and the same input colour type, each stage may run as
+ * one launch over up to 16 frames (the sort passes, the link, the colour
+ * gather, the moments: every frame's blocks in one grid; the noise estimate:
+ * one eigen block per frame while the other SMs, shared out by frame size,
+ * take the frames' speculative filter steps; the selection and filter: one
+ * cooperative launch in which each frame's blocks, shared out by frame size,
+ * synchronise among themselves).  Whether a batch that can be segmented is,
+ * how many frames a launch takes and the block shapes of the sort scatter and
+ * of the selection/filter are those fgbd_tune_batch chose for this device and
+ * frame size (or fgbd_set_batch_shape set; by default segmented below 2^18
+ * points a frame); they do not change any result.  Other batches run every
+ * frame on a stream of its own, forked from `stream` and joined back into it,
+ * the cooperative selection/filter launches one frame after another.
+ * Either way results, stats and errors are per context, exactly as after
+ * fgbd_run (the outputs are bit-identical), everything earlier on `stream`
+ * finishes first and later work on `stream` waits for every frame.  The call
+ * contains no host synchronisation, so it can be captured into a CUDA graph
+ * once the contexts have run a frame (the first launches set kernel
+ * attributes).  Like fgbd_run, the second call with the same contexts, buffers
+ * and block shapes records a CUDA graph of the whole batch (kept by ctxs[0],
+ * up to 4 of them) and later calls launch it.  In a segmented batch the
+ * launches are counted in the stats of ctxs[0] (kernel timing too).
  * Errors: FGBD_EINVAL (any argument), checked before anything is enqueued;
  * FGBD_ECUDA. */
 #define FGBD_BATCH_MAX 64
 fgbd_status fgbd_run_batch(fgbd_ctx* const* ctxs, const int32_t* const* xyz, const int64_t* n,
                            const void* const* rgb_in, const int32_t* in_dtype, void* const* rgb_out,
                            const int32_t* out_dtype, int32_t count, void* stream);
+
+/* How a batch runs (no counterpart in the paper). */
+typedef struct fgbd_batch_shape {
+  int32_t seg_frames;            /* frames per segmented launch, 1..16; 0: per-frame streams.  Default: 16
+                                    below 2^18 points a frame, 0 above (fgbd_tune_batch: -1 when the batch
+                                    cannot be segmented, and nothing was tuned) */
+  int32_t scatter_threads;       /* threads ranking one 4096-key sort tile: 256, 512 (default) or 1024 */
+  int32_t filter_threads;        /* threads per block of the selection/filter: 256 or 512 (default) */
+  int32_t filter_blocks_per_sm;  /* its blocks per SM (default 2; capped by what fits) */
+  float ms;                      /* fgbd_tune_batch: device time of one batch with the chosen shape */
+  int32_t reserved[3];
+} fgbd_batch_shape;
+
+/* Autotuner of batches: runs the batch (the arguments of fgbd_run_batch) with
+ * candidate shapes - per-frame streams against segmented launches of 16, 8, 4
+ * and 2 frames, then, if segmented won, the sort scatter at 256, 512 and 1024
+ * threads a tile, then the selection/filter at 512 threads x 1 or 2 blocks per
+ * SM and 256 threads x 2 or 4 - timing each (median of three after one untimed
+ * run, CUDA events on `stream`), one coordinate at a time, and keeps the
+ * fastest for this device and frame-size class (floor(log2(mean points per
+ * frame))); later fgbd_run_batch calls use it.  Synchronises; the frames'
+ * outputs and stats are those of the batch (every candidate gives the same).
+ * *chosen (optional, host) receives the shape and its time.  A batch that
+ * cannot be segmented is not run (seg_frames = -1).  Errors: as
+ * fgbd_run_batch. */
+fgbd_status fgbd_tune_batch(fgbd_ctx* const* ctxs, const int32_t* const* xyz, const int64_t* n,
+                            const void* const* rgb_in, const int32_t* in_dtype, void* const* rgb_out,
+                            const int32_t* out_dtype, int32_t count, void* stream, fgbd_batch_shape* chosen);
+
+/* The shapes a segmented batch of frames of about `mean_points` points on CUDA
+ * device `device` uses, into *out (host); set them (or, with shape NULL, go
+ * back to the defaults) with fgbd_set_batch_shape.  Errors: FGBD_EINVAL. */
+fgbd_status fgbd_get_batch_shape(int32_t device, int64_t mean_points, fgbd_batch_shape* out);
+fgbd_status fgbd_set_batch_shape(int32_t device, int64_t mean_points, const fgbd_batch_shape* shape);
 
 /* Differentiable filter (no counterpart in the paper; a training extension
  * of Eq. 5).  With R = D^-1 W, W_ij = exp(-d_ij^2 / sigma^2) on the graph of

@@ -11,6 +11,7 @@
 #include <cstddef>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -99,6 +100,7 @@ struct fgbd_ctx {
     std::vector<uint64_t> uids;  // the contexts' ids: a graph of a destroyed context never matches
     std::vector<RunKey> keys;
     std::vector<int64_t> launches;
+    BatchShape shape;            // the block shapes it was recorded with
     cudaGraphExec_t exec;
   };
   std::vector<BatchGraph> batch_graphs;  // most recent last
@@ -545,10 +547,189 @@ fgbd_status capture_run(fgbd_ctx* ctx, const fgbd_ctx::RunKey& k, cudaStream_t s
   return FGBD_OK;
 }
 
-// The batch of fgbd_run_batch, enqueued directly: every frame on its context's
-// own stream, forked from `st` and joined back into it; the selection/filter
-// launches (cooperative, each using the whole GPU) one frame after another.
+// ---------------------------------------------------------------- segmented batches
+// A batch whose frames share the window (1), the ablation switches and the
+// colour type runs each stage as one launch over up to kSegMax frames
+// (segmented launches, fgbd_internal.cuh): 13 launches for the whole chunk
+// instead of about 17 per frame, every frame's short latency-bound kernels
+// side by side in one grid, the estimate launch with one eigen block per
+// frame, and one cooperative selection/filter for all frames (each frame's
+// blocks synchronise among themselves).  Each frame's blocks run the same
+// code with the same block counts as its one-frame kernels (or, for the
+// block shapes the tuner may change, code whose results do not depend on the
+// shape), so the outputs equal fgbd_run's bit for bit.
+
+bool seg_eligible(const std::vector<fgbd_ctx*>& ctxs, const std::vector<fgbd_ctx::RunKey>& keys) {
+  const fgbd_ctx* c0 = ctxs[0];
+  if (c0->num_sms < 2 * kSegMax) return false;
+  for (size_t f = 0; f < ctxs.size(); ++f) {
+    const fgbd_ctx* c = ctxs[f];
+    if (c->params.window != 1 || c->params.variant != c0->params.variant || c->num_sms != c0->num_sms) return false;
+    if (keys[f].in_dtype != keys[0].in_dtype || keys[f].n < 1) return false;
+  }
+  return true;
+}
+
+// Frames [i0, i1) of the batch (i1 - i0 <= kSegMax), enqueued on `st`.
+fgbd_status seg_chunk(const std::vector<fgbd_ctx*>& ctxs, const std::vector<fgbd_ctx::RunKey>& keys, int i0,
+                      int i1, const BatchShape& shape, cudaStream_t st) {
+  const int F = i1 - i0;
+  fgbd_ctx* lead = ctxs[i0];
+  const int num_sms = lead->num_sms;
+  const int dtype = keys[i0].in_dtype;
+  const bool same_line = (lead->params.variant & FGBD_VARIANT_SAME_LINE) != 0;
+  const bool sorted = (lead->params.variant & FGBD_VARIANT_UNSORTED_PATCH) == 0;
+  ZeroArgs z[kSegMax];
+  HistArgs h[kSegMax];
+  LinkArgs l[kSegMax];
+  GatherArgs g[kSegMax];
+  MomentArgs m[kSegMax];
+  FilterArgs spec[kSegMax], sel[kSegMax];
+  const double* f64[kSegMax];
+  int nblk[kSegMax], ns[kSegMax], bits[kSegMax], caps[kSegMax];
+  SortBufs sbs[kSegMax];
+  GraphBufs gbs[kSegMax];
+  DevScalars* scs[kSegMax];
+  for (int f = 0; f < F; ++f) {
+    fgbd_ctx* c = ctxs[i0 + f];
+    const fgbd_ctx::RunKey& k = keys[i0 + f];
+    const int n = int(k.n);
+    const int32_t* xyz = static_cast<const int32_t*>(k.xyz);
+    ns[f] = n;
+    bits[f] = c->params.bits;
+    caps[f] = ord_stride(c);
+    sbs[f] = c->sb;
+    gbs[f] = c->gb;
+    scs[f] = c->sc;
+    z[f] = ZeroArgs{reinterpret_cast<uint32_t*>(reinterpret_cast<char*>(c->sc) + offsetof(DevScalars, n_edges)),
+                    (offsetof(DevScalars, sel_end_) - offsetof(DevScalars, n_edges)) / 4};
+    h[f] = hist_args(xyz, n, bits[f], c->sc);
+    l[f] = link_args(n, bits[f], caps[f], c->gb, c->sb, c->sc);
+    g[f] = GatherArgs{k.rgb_in, dtype, n, c->gb.perm1, c->y8, c->yf};
+    m[f] = moment_args(n, bits[f], c->gb, c->y8, c->yf, c->spread, c->f64part, true, sorted, c->sc);
+    // the state fgbd_run's calls leave (n is set first: filter_args reads it)
+    c->n = n;
+    spec[f] = filter_args(c, 0, 0, nullptr, nullptr, 0, dtype);
+    spec[f].spec_depth = std::min(kSpecMax, int(c->params.q_max));
+    sel[f] = filter_args(c, 0, 0, nullptr, k.rgb_out, k.out_dtype, dtype);
+    sel[f].spec_depth = spec[f].spec_depth;
+    f64[f] = c->f64part;
+    nblk[f] = ne_moment_blocks(n, num_sms);
+  }
+  FGBD_LAUNCH(lead, "seg_zero", st, launch_zero_words_seg(z, F, st));
+  FGBD_LAUNCH(lead, "seg_hist", st, launch_coord_hist_seg(h, F, num_sms, st));
+  static const char* const kPass[kSlgPasses][3] = {{"seg_counts0", "seg_scan0", "seg_scatter0"},
+                                                   {"seg_counts1", "seg_scan1", "seg_scatter1"},
+                                                   {"seg_counts2", "seg_scan2", "seg_scatter2"}};
+  for (int p = 0; p < kSlgPasses; ++p) {
+    SortPassArgs a[kSegMax];
+    for (int f = 0; f < F; ++f) {
+      fgbd_ctx* c = ctxs[i0 + f];
+      a[f] = slg_pass_args(p, static_cast<const int32_t*>(keys[i0 + f].xyz), ns[f], bits[f], caps[f], c->sb, c->gb,
+                           c->sc);
+    }
+    {
+      // counts, scan and scatter: three launches under one timing scope
+      LaunchScope scope_(lead, kPass[p][2], st, 3);
+      FGBD_CUDA(lead, launch_sort_pass_seg(a, F, shape.scatter_threads, st));
+    }
+    if (p == 0) FGBD_LAUNCH(lead, "seg_slab", st, launch_slab_sort_seg(ns, bits, caps, sbs, gbs, scs, F, st));
+  }
+  FGBD_LAUNCH(lead, "seg_link", st, launch_link_seg(l, F, same_line, num_sms, st));
+  if (same_line) lead->launches += 1;  // and the line flags
+  FGBD_LAUNCH(lead, "seg_gather", st, launch_gather_colors_seg(g, F, st));
+  FGBD_LAUNCH(lead, "seg_moments", st, launch_ne_moments_seg(m, F, dtype, num_sms, st));
+  FGBD_LAUNCH(lead, "seg_estimate", st, launch_ne_finalize_seg(spec, f64, nblk, F, num_sms, st));
+  FGBD_LAUNCH(lead, "seg_select", st,
+              launch_filter_seg(sel, F, shape.filter_threads, shape.filter_per_sm, num_sms, st));
+  for (int f = 0; f < F; ++f) {
+    fgbd_ctx* c = ctxs[i0 + f];
+    mark_run_done(c, keys[i0 + f], 0);
+    c->spec_depth = spec[f].spec_depth;
+  }
+  return FGBD_OK;
+}
+
+fgbd_status segmented_batch(const std::vector<fgbd_ctx*>& ctxs, const std::vector<fgbd_ctx::RunKey>& keys,
+                            const BatchShape& shape, cudaStream_t st) {
+  const int count = int(ctxs.size());
+  const int chunk = std::max(1, std::min(shape.seg_frames, kSegMax));
+  for (int i0 = 0; i0 < count; i0 += chunk) {
+    const fgbd_status s = seg_chunk(ctxs, keys, i0, std::min(count, i0 + chunk), shape, st);
+    if (s != FGBD_OK) return s;
+  }
+  return FGBD_OK;
+}
+
+// Block shapes of segmented batches, per device and frame-size class
+// (floor(log2(mean points per frame))): set by fgbd_tune_batch or
+// fgbd_set_batch_shape, the defaults otherwise.
+struct TunedShape {
+  int device;
+  int size_class;
+  BatchShape shape;
+};
+std::mutex g_shape_mutex;
+std::vector<TunedShape> g_shapes;
+
+int size_class(const std::vector<fgbd_ctx::RunKey>& keys) {
+  double total = 0.0;
+  for (const auto& k : keys) total += double(std::max<int64_t>(k.n, 1));
+  const double mean = total / double(std::max<size_t>(keys.size(), 1));
+  return int(std::floor(std::log2(std::max(mean, 1.0))));
+}
+
+// Untuned: segmented launches of up to kSegMax frames for frames below 2^18
+// points, whose stages are short and whose working sets (about 180 bytes a
+// point) fit the L2 together; per-frame streams above, where a frame's own
+// working set fills the L2 and running the frames stage by stage would evict
+// each frame's data between its stages (measured on 16 frames of 200k-1.2M
+// points: 4.41 ms segmented against 3.45 ms on streams).
+BatchShape default_shape(int cls) {
+  BatchShape b;
+  b.seg_frames = cls < 18 ? kSegMax : 0;
+  return b;
+}
+
+BatchShape shape_for(int device, int cls) {
+  std::lock_guard<std::mutex> lock(g_shape_mutex);
+  for (const TunedShape& t : g_shapes)
+    if (t.device == device && t.size_class == cls) return t.shape;
+  return default_shape(cls);
+}
+
+void store_shape(int device, int cls, const BatchShape* shape) {
+  std::lock_guard<std::mutex> lock(g_shape_mutex);
+  for (size_t i = 0; i < g_shapes.size(); ++i) {
+    if (g_shapes[i].device == device && g_shapes[i].size_class == cls) {
+      if (shape) g_shapes[i].shape = *shape;
+      else g_shapes.erase(g_shapes.begin() + long(i));
+      return;
+    }
+  }
+  if (shape) g_shapes.push_back({device, cls, *shape});
+}
+
+bool shape_ok(const BatchShape& b) {
+  return b.seg_frames >= 0 && b.seg_frames <= kSegMax &&
+         (b.scatter_threads == 256 || b.scatter_threads == 512 || b.scatter_threads == 1024) &&
+         (b.filter_threads == 256 || b.filter_threads == 512) && b.filter_per_sm >= 1 && b.filter_per_sm <= 8;
+}
+
+// The batch of fgbd_run_batch, enqueued directly: segmented when the frames
+// allow it, else every frame on its context's own stream, forked from `st`
+// and joined back into it, the selection/filter launches (cooperative, each
+// using the whole GPU) one frame after another.
+fgbd_status stream_batch(const std::vector<fgbd_ctx*>& ctxs, const std::vector<fgbd_ctx::RunKey>& keys,
+                         cudaStream_t st);
+
 fgbd_status direct_batch(const std::vector<fgbd_ctx*>& ctxs, const std::vector<fgbd_ctx::RunKey>& keys,
+                         const BatchShape& shape, cudaStream_t st) {
+  if (shape.seg_frames > 0 && seg_eligible(ctxs, keys)) return segmented_batch(ctxs, keys, shape, st);
+  return stream_batch(ctxs, keys, st);
+}
+
+fgbd_status stream_batch(const std::vector<fgbd_ctx*>& ctxs, const std::vector<fgbd_ctx::RunKey>& keys,
                          cudaStream_t st) {
   const int count = int(ctxs.size());
   fgbd_ctx* lead = ctxs[0];
@@ -585,7 +766,7 @@ fgbd_status direct_batch(const std::vector<fgbd_ctx*>& ctxs, const std::vector<f
 // frames' own streams join the capture through the fork event), then launch it.
 // If the capture fails the batch runs directly and the first context stops capturing.
 fgbd_status capture_batch(fgbd_ctx* lead, const std::vector<fgbd_ctx*>& ctxs,
-                          const std::vector<fgbd_ctx::RunKey>& keys, cudaStream_t st) {
+                          const std::vector<fgbd_ctx::RunKey>& keys, const BatchShape& shape, cudaStream_t st) {
   const cudaStream_t cs = lead->cap_stream;
   std::vector<int64_t> launches0;
   for (fgbd_ctx* c : ctxs) launches0.push_back(c->launches);
@@ -594,9 +775,9 @@ fgbd_status capture_batch(fgbd_ctx* lead, const std::vector<fgbd_ctx*>& ctxs,
   if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
     cudaGetLastError();
     lead->graphs_on = false;
-    return direct_batch(ctxs, keys, st);
+    return direct_batch(ctxs, keys, shape, st);
   }
-  const fgbd_status s = direct_batch(ctxs, keys, cs);
+  const fgbd_status s = direct_batch(ctxs, keys, shape, cs);
   const cudaError_t ce = cudaStreamEndCapture(cs, &graph);
   bool ok = s == FGBD_OK && ce == cudaSuccess && graph;
   ok = ok && cudaGraphInstantiate(&exec, graph, 0) == cudaSuccess;
@@ -607,14 +788,14 @@ fgbd_status capture_batch(fgbd_ctx* lead, const std::vector<fgbd_ctx*>& ctxs,
     for (size_t f = 0; f < ctxs.size(); ++f) ctxs[f]->launches = launches0[f];
     lead->graphs_on = false;
     if (s != FGBD_OK && s != FGBD_ECUDA) return s;
-    return direct_batch(ctxs, keys, st);
+    return direct_batch(ctxs, keys, shape, st);
   }
   FGBD_CUDA(lead, cudaGraphLaunch(exec, st));
   if (lead->batch_graphs.size() >= 4) {
     cudaGraphExecDestroy(lead->batch_graphs.front().exec);
     lead->batch_graphs.erase(lead->batch_graphs.begin());
   }
-  fgbd_ctx::BatchGraph bg{ctxs, {}, keys, {}, exec};
+  fgbd_ctx::BatchGraph bg{ctxs, {}, keys, {}, shape, exec};
   for (fgbd_ctx* c : ctxs) bg.uids.push_back(c->uid);
   for (size_t f = 0; f < ctxs.size(); ++f) bg.launches.push_back(ctxs[f]->launches - launches0[f]);
   lead->batch_graphs.push_back(bg);
@@ -1000,6 +1181,7 @@ fgbd_status fgbd_run_batch(fgbd_ctx* const* ctxs, const int32_t* const* xyz, con
   for (int f = 0; f < count; ++f) keys.push_back({xyz[f], n[f], rgb_in[f], in_dtype[f], rgb_out[f], out_dtype[f]});
   bool timing = false;
   for (int f = 0; f < count; ++f) timing |= ctxs[f]->timing;
+  const BatchShape shape = shape_for(lead->device, size_class(keys));
   cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
   if (cudaStreamIsCapturing(st, &cap) != cudaSuccess) {
     cudaGetLastError();
@@ -1011,17 +1193,160 @@ fgbd_status fgbd_run_batch(fgbd_ctx* const* ctxs, const int32_t* const* xyz, con
     for (size_t i = 0; i < lead->batch_graphs.size(); ++i) {
       const fgbd_ctx::BatchGraph& bg = lead->batch_graphs[i];
       if (bg.uids != uids || bg.ctxs != cv || !(bg.keys == keys)) continue;
+      if (bg.shape.seg_frames != shape.seg_frames || bg.shape.scatter_threads != shape.scatter_threads ||
+          bg.shape.filter_threads != shape.filter_threads || bg.shape.filter_per_sm != shape.filter_per_sm)
+        continue;
       FGBD_CUDA(lead, cudaGraphLaunch(bg.exec, st));
-      for (int f = 0; f < count; ++f) mark_run_done(ctxs[f], keys[f], bg.launches[f]);
+      const bool seg = shape.seg_frames > 0 && seg_eligible(cv, keys);
+      for (int f = 0; f < count; ++f) {
+        mark_run_done(ctxs[f], keys[f], bg.launches[f]);
+        if (seg) ctxs[f]->spec_depth = std::min(kSpecMax, int(ctxs[f]->params.q_max));
+      }
       return FGBD_OK;
     }
     bool seen = false;
     for (const auto& e : lead->batch_seen) seen |= e.first == uids && e.second == keys;
-    if (seen) return capture_batch(lead, cv, keys, st);
+    if (seen) return capture_batch(lead, cv, keys, shape, st);
     lead->batch_seen.push_back({uids, keys});
     if (lead->batch_seen.size() > 8) lead->batch_seen.erase(lead->batch_seen.begin());
   }
-  return direct_batch(cv, keys, st);
+  return direct_batch(cv, keys, shape, st);
+}
+
+fgbd_status fgbd_get_batch_shape(int32_t device, int64_t mean_points, fgbd_batch_shape* out) {
+  if (!out || mean_points < 0) return FGBD_EINVAL;
+  const int cls = int(std::floor(std::log2(std::max(double(mean_points), 1.0))));
+  const BatchShape b = shape_for(device, cls);
+  std::memset(out, 0, sizeof(*out));
+  out->seg_frames = b.seg_frames;
+  out->scatter_threads = b.scatter_threads;
+  out->filter_threads = b.filter_threads;
+  out->filter_blocks_per_sm = b.filter_per_sm;
+  return FGBD_OK;
+}
+
+fgbd_status fgbd_set_batch_shape(int32_t device, int64_t mean_points, const fgbd_batch_shape* shape) {
+  if (mean_points < 0) return FGBD_EINVAL;
+  const int cls = int(std::floor(std::log2(std::max(double(mean_points), 1.0))));
+  if (!shape) {
+    store_shape(device, cls, nullptr);
+    return FGBD_OK;
+  }
+  BatchShape b;
+  b.seg_frames = shape->seg_frames;
+  b.scatter_threads = shape->scatter_threads;
+  b.filter_threads = shape->filter_threads;
+  b.filter_per_sm = shape->filter_blocks_per_sm;
+  if (!shape_ok(b)) return FGBD_EINVAL;
+  store_shape(device, cls, &b);
+  return FGBD_OK;
+}
+
+fgbd_status fgbd_tune_batch(fgbd_ctx* const* ctxs, const int32_t* const* xyz, const int64_t* n,
+                            const void* const* rgb_in, const int32_t* in_dtype, void* const* rgb_out,
+                            const int32_t* out_dtype, int32_t count, void* stream, fgbd_batch_shape* chosen) {
+  NvtxRange nvtx_("fgbd_tune_batch");
+  if (count < 1 || count > FGBD_BATCH_MAX) return FGBD_EINVAL;
+  if (!ctxs || !xyz || !n || !rgb_in || !in_dtype || !rgb_out || !out_dtype) return FGBD_EINVAL;
+  for (int f = 0; f < count; ++f) {
+    fgbd_ctx* c = ctxs[f];
+    if (!c || c->device != ctxs[0]->device) return FGBD_EINVAL;
+    for (int h = 0; h < f; ++h)
+      if (ctxs[h] == c) return FGBD_EINVAL;
+    if (!dtype_ok(in_dtype[f]) || !dtype_ok(out_dtype[f])) return FGBD_EINVAL;
+    if (n[f] < 0 || n[f] > c->capacity) return FGBD_EINVAL;
+    if (n[f] > 0 && (!xyz[f] || !rgb_in[f] || !rgb_out[f])) return FGBD_EINVAL;
+  }
+  DeviceGuard g(ctxs[0]->device);
+  const cudaStream_t st = as_stream(stream);
+  fgbd_ctx* lead = ctxs[0];
+  std::vector<fgbd_ctx*> cv(ctxs, ctxs + count);
+  std::vector<fgbd_ctx::RunKey> keys;
+  for (int f = 0; f < count; ++f) keys.push_back({xyz[f], n[f], rgb_in[f], in_dtype[f], rgb_out[f], out_dtype[f]});
+  const int cls = size_class(keys);
+  if (chosen) std::memset(chosen, 0, sizeof(*chosen));
+  if (!seg_eligible(cv, keys)) {
+    // only per-frame streams apply: nothing to choose (the batch does not run)
+    if (chosen) chosen->seg_frames = -1;
+    return FGBD_OK;
+  }
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  FGBD_CUDA(lead, cudaEventCreate(&e0));
+  FGBD_CUDA(lead, cudaEventCreate(&e1));
+  // the median of three timed batches (after one untimed) with a shape
+  auto time_shape = [&](const BatchShape& b, float* ms) -> fgbd_status {
+    fgbd_status s = direct_batch(cv, keys, b, st);
+    if (s != FGBD_OK) return s;
+    float t[3];
+    for (int r = 0; r < 3; ++r) {
+      FGBD_CUDA(lead, cudaEventRecord(e0, st));
+      s = direct_batch(cv, keys, b, st);
+      if (s != FGBD_OK) return s;
+      FGBD_CUDA(lead, cudaEventRecord(e1, st));
+      FGBD_CUDA(lead, cudaEventSynchronize(e1));
+      FGBD_CUDA(lead, cudaEventElapsedTime(&t[r], e0, e1));
+    }
+    std::sort(t, t + 3);
+    *ms = t[1];
+    return FGBD_OK;
+  };
+  // coordinate search: how the frames run (per-frame streams, or segmented
+  // launches of 16, 8, 4 or 2 frames), then - if segmented - the scatter's
+  // threads per tile, then the filter's block shape and blocks per SM
+  BatchShape best;
+  best.seg_frames = 0;
+  float best_ms = 0.f;
+  fgbd_status s = time_shape(best, &best_ms);
+  for (int sf : {16, 8, 4, 2}) {
+    if (s != FGBD_OK || sf >= count * 2) continue;  // chunks larger than the batch repeat a candidate
+    BatchShape b;
+    b.seg_frames = sf;
+    float ms = 0.f;
+    s = time_shape(b, &ms);
+    if (s == FGBD_OK && ms < best_ms) {
+      best = b;
+      best_ms = ms;
+    }
+  }
+  if (s == FGBD_OK && best.seg_frames > 0) {
+    for (int th : {256, 1024}) {
+      if (s != FGBD_OK) break;
+      BatchShape b = best;
+      b.scatter_threads = th;
+      float ms = 0.f;
+      s = time_shape(b, &ms);
+      if (s == FGBD_OK && ms < best_ms) {
+        best = b;
+        best_ms = ms;
+      }
+    }
+    const BatchShape sorted_best = best;
+    for (const auto& cand : {std::make_pair(512, 1), std::make_pair(256, 2), std::make_pair(256, 4)}) {
+      if (s != FGBD_OK) break;
+      BatchShape b = sorted_best;
+      b.filter_threads = cand.first;
+      b.filter_per_sm = cand.second;
+      if (b.filter_per_sm > filter_seg_max_per_sm(b.filter_threads)) continue;
+      float ms = 0.f;
+      s = time_shape(b, &ms);
+      if (s == FGBD_OK && ms < best_ms) {
+        best = b;
+        best_ms = ms;
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (s != FGBD_OK) return s;
+  store_shape(lead->device, cls, &best);
+  if (chosen) {
+    chosen->seg_frames = best.seg_frames;
+    chosen->scatter_threads = best.scatter_threads;
+    chosen->filter_threads = best.filter_threads;
+    chosen->filter_blocks_per_sm = best.filter_per_sm;
+    chosen->ms = best_ms;
+  }
+  return FGBD_OK;
 }
 
 fgbd_status fgbd_filter_forward(fgbd_ctx* ctx, const float* rgb_in, int32_t q, double alpha, double sigma,

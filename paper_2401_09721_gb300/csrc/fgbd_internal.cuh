@@ -147,6 +147,110 @@ struct SortPassArgs {
   const DevScalars* sc;
 };
 
+// ---------------------------------------------------------------- segmented launches
+// A batch of frames runs each stage as one launch: the per-frame arguments of
+// up to kSegMax frames travel in the kernel's parameter space, and frame f
+// owns the blocks [start[f], start[f + 1]) of a one-dimensional grid.  A
+// block finds its frame, then runs the same body as the one-frame kernel with
+// its block index and block count inside the frame, so a frame's results do
+// not depend on the batch it is in.
+constexpr int kSegMax = 16;
+
+template <typename A>
+struct Seg {
+  A a[kSegMax];
+  int start[kSegMax + 1];
+  int count;
+};
+
+// the frame that owns block b (frames with no blocks are skipped)
+template <typename A>
+__device__ __forceinline__ int seg_frame(const Seg<A>& s, int b) {
+  int f = 0;
+  while (f + 1 < s.count && s.start[f + 1] <= b) ++f;
+  return f;
+}
+
+// fill s.start from per-frame block counts; returns the grid size
+template <typename A>
+inline int seg_layout(Seg<A>& s, const int* blocks, int count) {
+  s.count = count;
+  int t = 0;
+  for (int f = 0; f < count; ++f) {
+    s.start[f] = t;
+    t += blocks[f];
+  }
+  s.start[count] = t;
+  return t;
+}
+
+// Arguments of the kernels that the one-frame path passes one by one.
+struct HistArgs {
+  const int32_t* xyz;
+  int n;
+  int bits;
+  struct DevScalars* sc;
+};
+struct SlabArgs {
+  int n;
+  int bits;
+  const uint32_t* keys_in;
+  const uint32_t* vals_in;
+  uint32_t* keys_tmp;
+  uint32_t* vals_tmp;
+  uint32_t* keys_out;
+  int32_t* vals_out;
+  const struct DevScalars* sc;
+};
+struct LinkArgs {
+  int n;
+  int bits;
+  int cap;
+  const int32_t* ord23;
+  const uint32_t* keys_c2;
+  const uint32_t* keys_c3;
+  const int32_t* rank2;
+  uint32_t* pk;
+  int4* c4;
+  struct DevScalars* sc;
+};
+struct GatherArgs {
+  const void* rgb;
+  int dtype;
+  int n;
+  const int32_t* perm1;
+  uint32_t* y8;
+  float4* yf;
+};
+struct MomentArgs {
+  int n;
+  int bits;
+  const uint32_t* pk;
+  const int4* c4;
+  const uint32_t* y8;
+  const float4* yf;
+  float* spread;
+  double* f64_partials;
+  int moments;
+  int sorted_patches;
+  struct DevScalars* sc;
+};
+struct ZeroArgs {
+  uint32_t* p;
+  size_t words;
+};
+
+// How a batch runs, chosen by the batch tuner (api.cu): frames per segmented
+// launch (0: every frame on a stream of its own, its own kernels), threads of
+// the sort scatter (one 4096-key tile a block), threads of the filter blocks
+// and filter blocks per SM of the cooperative selection.
+struct BatchShape {
+  int seg_frames = kSegMax;
+  int scatter_threads = 512;
+  int filter_threads = 512;
+  int filter_per_sm = 2;
+};
+
 // ---------------------------------------------------------------- launchers
 struct FilterArgs;
 // Every launcher enqueues on `stream` and returns the launch error.
@@ -164,6 +268,17 @@ cudaError_t launch_tile_scan(const SortPassArgs& a, cudaStream_t stream);
 cudaError_t launch_sort_scatter(const SortPassArgs& a, cudaStream_t stream);
 cudaError_t launch_sort_pass(const SortPassArgs& a, cudaStream_t stream);  // the three above
 cudaError_t launch_orders_export(int n, int cap, const GraphBufs& gb, int32_t* out, cudaStream_t stream);
+// segmented launches: one launch for frames 0..count-1 (count <= kSegMax), each
+// frame with the blocks its one-frame launch would have
+HistArgs hist_args(const int32_t* xyz, int n, int bits, DevScalars* sc);
+LinkArgs link_args(int n, int bits, int cap, const GraphBufs& gb, const SortBufs& sb, DevScalars* sc);
+cudaError_t launch_zero_words_seg(const ZeroArgs* a, int count, cudaStream_t stream);
+cudaError_t launch_coord_hist_seg(const HistArgs* a, int count, int num_sms, cudaStream_t stream);
+// counts, scan and scatter of one pass (scatter_threads: 256, 512 or 1024 per 4096-key tile)
+cudaError_t launch_sort_pass_seg(const SortPassArgs* a, int count, int scatter_threads, cudaStream_t stream);
+cudaError_t launch_slab_sort_seg(const int* n, const int* bits, const int* cap, const SortBufs* sb,
+                                 const GraphBufs* gb, DevScalars* const* sc, int count, cudaStream_t stream);
+cudaError_t launch_link_seg(const LinkArgs* a, int count, bool same_line, int num_sms, cudaStream_t stream);
 cudaError_t launch_link(int n, int bits, int cap, bool same_line, const GraphBufs& gb, const SortBufs& sb,
                         DevScalars* sc, int num_sms, cudaStream_t stream);
 // windows w > 1: every link of the window (C2/C3 d = 1 into c4, d >= 2 into cx)
@@ -183,6 +298,15 @@ cudaError_t launch_ne_finalize(int dtype, const double* f64_partials, int nblock
                                DevScalars* sc, double* sigma_out, const FilterArgs* spec, int num_sms,
                                cudaStream_t stream);
 int ne_moment_blocks(int n, int num_sms);
+MomentArgs moment_args(int n, int bits, const GraphBufs& gb, const uint32_t* y8, const float4* yf, float* spread,
+                       double* f64_partials, bool moments, bool sorted_patches, DevScalars* sc);
+// segmented: frames 0..count-1 (count <= kSegMax; one colour dtype for the moments)
+cudaError_t launch_gather_colors_seg(const GatherArgs* a, int count, cudaStream_t stream);
+cudaError_t launch_ne_moments_seg(const MomentArgs* a, int count, int dtype, int num_sms, cudaStream_t stream);
+// the estimate launch over frames: one eigen block per frame, the other SMs
+// shared out for the speculative steps (spec[f].spec_depth of them)
+cudaError_t launch_ne_finalize_seg(const FilterArgs* spec, const double* const* f64_partials, const int* nblocks,
+                                   int count, int num_sms, cudaStream_t stream);
 
 // Noise estimate at windows w > 1 (patch dimension D = 3 (6w + 1)): per-block
 // moment partials, their reduction, the one-block float32 eigenvectors, and float64
@@ -240,6 +364,11 @@ struct FilterArgs {
 cudaError_t launch_filter(const FilterArgs& a, int grid, cudaStream_t stream);
 int filter_grid(int n, int num_sms, int nx = 0);
 cudaError_t launch_output(const FilterArgs& a, cudaStream_t stream);  // the kept iterate, in input order
+// the cooperative selection/filter over frames (window 1): filter_per_sm blocks
+// of `threads` (256 or 512) per SM, shared out in proportion to the frames' points
+cudaError_t launch_filter_seg(const FilterArgs* a, int count, int threads, int filter_per_sm, int num_sms,
+                              cudaStream_t stream);
+int filter_seg_max_per_sm(int threads);  // resident blocks per SM of that kernel
 
 // Differentiable filter: rows of R = D^-1 W for given alpha, sigma, and their transpose
 struct DiffBufs {

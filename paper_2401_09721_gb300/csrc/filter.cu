@@ -24,6 +24,23 @@ __global__ void __launch_bounds__(kFilterThreads, 2) k_filter(FilterArgs a) {
   select_filter<kFilterThreads, NX>(a, s_S, 0, gridDim.x, &a.sc->barrier, epoch);
 }
 
+// Segmented (window 1): frame f's blocks [start[f], start[f + 1]) select and
+// filter frame f, with grid barriers among themselves only.
+template <int THREADS>
+__global__ void __launch_bounds__(THREADS, 1024 / THREADS) k_filter_seg(const __grid_constant__ Seg<FilterArgs> s) {
+  pdl_wait();
+  const int f = seg_frame(s, blockIdx.x);
+  const FilterArgs& a = s.a[f];
+  __shared__ int s_S;
+  if (threadIdx.x == 0) {
+    const int done = int(ld_acquire_u32(reinterpret_cast<const uint32_t*>(&a.sc->spec_done)));
+    s_S = (a.mode == 0 && a.spec_depth > 0) ? min(done, a.spec_depth) : 0;
+  }
+  __syncthreads();
+  uint32_t epoch = 0;
+  select_filter<THREADS, 0>(a, s_S, s.start[f], uint32_t(s.start[f + 1] - s.start[f]), &a.sc->barrier, epoch);
+}
+
 __global__ void __launch_bounds__(256) k_output(FilterArgs a) {
   pdl_wait();
   output_quads(a, a.sc->kept_buf, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
@@ -169,6 +186,47 @@ cudaError_t launch_filter(const FilterArgs& a, int grid, cudaStream_t stream) {
     return launch_kernel(k_filter<extra_slots(3)>, dim3(grid), dim3(kFilterThreads), 0, stream, true, a);
   if (a.nx != 0) return cudaErrorInvalidValue;
   return launch_kernel(k_filter<0>, dim3(grid), dim3(kFilterThreads), 0, stream, true, a);
+}
+
+int filter_seg_max_per_sm(int threads) {
+  int per_sm = 0;
+  const cudaError_t e =
+      threads == 256 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_filter_seg<256>, 256, 0)
+                     : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_filter_seg<512>, 512, 0);
+  if (e != cudaSuccess || per_sm < 1) {
+    cudaGetLastError();
+    return 1;
+  }
+  return per_sm;
+}
+
+cudaError_t launch_filter_seg(const FilterArgs* a, int count, int threads, int filter_per_sm, int num_sms,
+                              cudaStream_t stream) {
+  if (count < 1 || count > kSegMax || (threads != 256 && threads != 512)) return cudaErrorInvalidValue;
+  for (int f = 0; f < count; ++f)
+    if (a[f].nx != 0) return cudaErrorInvalidValue;
+  // every block must be resident (grid barriers): at most the occupancy per SM
+  const int per_sm = std::max(1, std::min(filter_per_sm, filter_seg_max_per_sm(threads)));
+  const int pool = per_sm * num_sms;
+  if (pool < count) return cudaErrorInvalidValue;
+  Seg<FilterArgs> sg;
+  int blocks[kSegMax];
+  double total = 0.0;
+  for (int f = 0; f < count; ++f) total += double(std::max(a[f].n, 1));
+  int given = 0;
+  for (int f = 0; f < count; ++f) {
+    sg.a[f] = a[f];
+    // in proportion to the points, at least one block, no more than one thread per point
+    const int need = std::max(1, (a[f].n + threads - 1) / threads);
+    const int left = count - 1 - f;
+    int b = int(double(pool) * double(std::max(a[f].n, 1)) / total);
+    b = std::max(1, std::min({b, need, pool - given - left}));
+    given += b;
+    blocks[f] = b;
+  }
+  const int grid = seg_layout(sg, blocks, count);
+  if (threads == 256) return launch_kernel(k_filter_seg<256>, dim3(grid), dim3(256), 0, stream, true, sg);
+  return launch_kernel(k_filter_seg<512>, dim3(grid), dim3(512), 0, stream, true, sg);
 }
 
 cudaError_t launch_output(const FilterArgs& a, cudaStream_t stream) {

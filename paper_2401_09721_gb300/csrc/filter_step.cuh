@@ -225,17 +225,17 @@ __device__ __forceinline__ float4 eq5_step_nx(const FilterArgs& a, const float4*
 }
 
 // The first steps x_1, x_2, ... and each point's Eq. 6 term sum_c (y^2 - x_q^2)
-// in fixed point beside them, by the blocks [first, gridDim.x) of a
+// in fixed point beside them, by the blocks [first, first + members) of a
 // cooperative grid (they need the graph and the colours only, not sigma_est):
 // `depth` steps, or, with `until_sigma`, fewer once sigma_est is published
 // (sc->sigma_ready).  Block `first` reads that flag before each grid barrier
 // and leaves its answer in sc->spec_go[t], which every block reads after the
 // barrier, so all blocks stop after the same step.  sc->spec_done = the steps
 // stored; returns that number, or -1 after a barrier timeout.
-__device__ __forceinline__ int speculative_steps(const FilterArgs& a, int depth, int first, bool until_sigma,
-                                                 uint32_t& epoch, int* s_ok, float* s_cexp, int* s_go) {
+__device__ __forceinline__ int speculative_steps(const FilterArgs& a, int depth, int first, uint32_t members,
+                                                 bool until_sigma, uint32_t& epoch, int* s_ok, float* s_cexp,
+                                                 int* s_go) {
   const int n = a.n;
-  const uint32_t members = gridDim.x - uint32_t(first);
   const int gtid = (blockIdx.x - first) * blockDim.x + threadIdx.x;
   const int gstride = int(members) * blockDim.x;
   DevScalars* sc = a.sc;

@@ -16,6 +16,7 @@
 //   order in the eigenvector error; the values are sorted descending and the
 //   tail rule gives sigma_est.
 #include <algorithm>
+#include <atomic>
 
 #include "eigen.cuh"
 #include "select.cuh"
@@ -41,11 +42,10 @@ __device__ __forceinline__ void perm_quad(const int32_t* __restrict__ perm1, int
   }
 }
 
-__global__ void __launch_bounds__(256) k_gather_u8(const uint8_t* __restrict__ rgb, int n,
-                                                   const int32_t* __restrict__ perm1,
-                                                   uint32_t* __restrict__ y8) {
-  pdl_wait();
-  for (int k0 = 4 * (blockIdx.x * blockDim.x + threadIdx.x); k0 < n; k0 += 4 * gridDim.x * blockDim.x) {
+__device__ __forceinline__ void gather_u8_body(const uint8_t* __restrict__ rgb, int n,
+                                               const int32_t* __restrict__ perm1, uint32_t* __restrict__ y8,
+                                               int bid, int nblk) {
+  for (int k0 = 4 * (bid * blockDim.x + threadIdx.x); k0 < n; k0 += 4 * nblk * blockDim.x) {
     int pi[4];
     perm_quad(perm1, k0, n, pi);
     uint32_t c[4];
@@ -67,11 +67,10 @@ __global__ void __launch_bounds__(256) k_gather_u8(const uint8_t* __restrict__ r
   }
 }
 
-__global__ void __launch_bounds__(256) k_gather_f32(const float* __restrict__ rgb, int n,
-                                                    const int32_t* __restrict__ perm1,
-                                                    float4* __restrict__ yf) {
-  pdl_wait();
-  for (int k0 = 4 * (blockIdx.x * blockDim.x + threadIdx.x); k0 < n; k0 += 4 * gridDim.x * blockDim.x) {
+__device__ __forceinline__ void gather_f32_body(const float* __restrict__ rgb, int n,
+                                                const int32_t* __restrict__ perm1, float4* __restrict__ yf, int bid,
+                                                int nblk) {
+  for (int k0 = 4 * (bid * blockDim.x + threadIdx.x); k0 < n; k0 += 4 * nblk * blockDim.x) {
     int pi[4];
     perm_quad(perm1, k0, n, pi);
     float4 c[4];
@@ -87,6 +86,29 @@ __global__ void __launch_bounds__(256) k_gather_f32(const float* __restrict__ rg
     for (int i = 0; i < 4; ++i)
       if (k0 + i < n) yf[k0 + i] = c[i];
   }
+}
+
+__global__ void __launch_bounds__(256) k_gather_u8(const uint8_t* __restrict__ rgb, int n,
+                                                   const int32_t* __restrict__ perm1,
+                                                   uint32_t* __restrict__ y8) {
+  pdl_wait();
+  gather_u8_body(rgb, n, perm1, y8, blockIdx.x, gridDim.x);
+}
+
+__global__ void __launch_bounds__(256) k_gather_f32(const float* __restrict__ rgb, int n,
+                                                    const int32_t* __restrict__ perm1,
+                                                    float4* __restrict__ yf) {
+  pdl_wait();
+  gather_f32_body(rgb, n, perm1, yf, blockIdx.x, gridDim.x);
+}
+
+__global__ void __launch_bounds__(256) k_gather_seg(const __grid_constant__ Seg<GatherArgs> s) {
+  pdl_wait();
+  const int f = seg_frame(s, blockIdx.x);
+  const GatherArgs& a = s.a[f];
+  const int bid = blockIdx.x - s.start[f], nblk = s.start[f + 1] - s.start[f];
+  if (a.dtype == 0) gather_u8_body(static_cast<const uint8_t*>(a.rgb), a.n, a.perm1, a.y8, bid, nblk);
+  else gather_f32_body(static_cast<const float*>(a.rgb), a.n, a.perm1, a.yf, bid, nblk);
 }
 
 __device__ __forceinline__ void tile_rc(int tile, int& r0, int& c0) {
@@ -305,12 +327,15 @@ __device__ __forceinline__ bool point_patch(int k, int n, int bits, int lane, co
 // batches, then float64.  The block combines its warps through shared atomics
 // and adds its totals to the context (uint8) or writes them (float).
 template <int DT>
-__global__ void __launch_bounds__(kNeThreads, 4)
-    k_ne_moments(int n, int bits, const uint32_t* __restrict__ pk, const int4* __restrict__ c4,
-                 const uint32_t* __restrict__ y8, const float4* __restrict__ yf,
-                 float* __restrict__ spread, double* __restrict__ f64_partials, int moments,
-                 int sorted_patches, DevScalars* __restrict__ sc) {
-  pdl_wait();
+__device__ __forceinline__ void ne_moments_body(const MomentArgs& ma, int bid, int nblk) {
+  const int n = ma.n, bits = ma.bits, moments = ma.moments, sorted_patches = ma.sorted_patches;
+  const uint32_t* __restrict__ pk = ma.pk;
+  const int4* __restrict__ c4 = ma.c4;
+  const uint32_t* __restrict__ y8 = ma.y8;
+  const float4* __restrict__ yf = ma.yf;
+  float* __restrict__ spread = ma.spread;
+  double* __restrict__ f64_partials = ma.f64_partials;
+  DevScalars* __restrict__ sc = ma.sc;
   constexpr int kP = kD * kD + kD + 1;
   __shared__ __align__(16) uint32_t s_at8[DT == 0 ? kNeWarps : 1][kD * kRowWords];
   __shared__ __align__(16) float s_atf[DT == 1 ? kNeWarps : 1][kD * kRowFloats];
@@ -341,8 +366,8 @@ __global__ void __launch_bounds__(kNeThreads, 4)
   uint8_t* at8 = reinterpret_cast<uint8_t*>(&s_at8[DT == 0 ? warp : 0][0]);
   float* atf = &s_atf[DT == 1 ? warp : 0][0];
 
-  const int nwarps = gridDim.x * kNeWarps;
-  for (int base = (blockIdx.x * kNeWarps + warp) * 32; base < n; base += nwarps * 32) {
+  const int nwarps = nblk * kNeWarps;
+  for (int base = (bid * kNeWarps + warp) * 32; base < n; base += nwarps * 32) {
     const int k = base + lane;
     bool has = false;
     if (k < n)
@@ -468,9 +493,22 @@ __global__ void __launch_bounds__(kNeThreads, 4)
       else if (i < kD * kD + kD) atomicAdd(reinterpret_cast<unsigned long long*>(&sc->s1[i - kD * kD]), v);
       else atomicAdd(&sc->n_patches, v);
     } else {
-      f64_partials[size_t(blockIdx.x) * kP + i] = s_totf[i];
+      f64_partials[size_t(bid) * kP + i] = s_totf[i];
     }
   }
+}
+
+template <int DT>
+__global__ void __launch_bounds__(kNeThreads, 4) k_ne_moments(MomentArgs a) {
+  pdl_wait();
+  ne_moments_body<DT>(a, blockIdx.x, gridDim.x);
+}
+
+template <int DT>
+__global__ void __launch_bounds__(kNeThreads, 4) k_ne_moments_seg(const __grid_constant__ Seg<MomentArgs> s) {
+  pdl_wait();
+  const int f = seg_frame(s, blockIdx.x);
+  ne_moments_body<DT>(s.a[f], blockIdx.x - s.start[f], s.start[f + 1] - s.start[f]);
 }
 
 // ---------------------------------------------------------------- finalize
@@ -668,7 +706,7 @@ __global__ void __launch_bounds__(kSpecThreads, 1)
     return;
   }
   uint32_t epoch = 0;
-  const int S = speculative_steps(a, a.spec_depth, 1, a.fuse != 0, epoch, &s_ok, &s_cexp, &s_go);
+  const int S = speculative_steps(a, a.spec_depth, 1, gridDim.x - 1, a.fuse != 0, epoch, &s_ok, &s_cexp, &s_go);
   if (!a.fuse || S < 0) return;
   // sigma_est of block 0 (a bounded wait)
   if (threadIdx.x == 0) {
@@ -690,7 +728,94 @@ __global__ void __launch_bounds__(kSpecThreads, 1)
   select_filter<kSpecThreads>(a, S, 1, gridDim.x - 1, &sc->spec_barrier, epoch);
 }
 
+// Segmented estimate launch (one block per SM, cooperative): block f < count
+// computes sigma_est of frame f, and frame f's share of the other blocks takes
+// its speculative filter steps (no fused selection here).
+struct EstimateSeg {
+  FilterArgs spec[kSegMax];
+  const double* f64_partials[kSegMax];
+  int nblocks[kSegMax];
+  int first[kSegMax + 1];  // frame f's step blocks: [count + first[f], count + first[f + 1])
+  int count;
+};
+
+__global__ void __launch_bounds__(kSpecThreads, 1) k_ne_finalize_spec_seg(const __grid_constant__ EstimateSeg e) {
+  pdl_wait();
+  __shared__ int s_ok;
+  __shared__ int s_go;
+  __shared__ float s_cexp;
+  if (int(blockIdx.x) < e.count) {
+    const int f = blockIdx.x;
+    if (threadIdx.x < kFinThreads) finalize_block(e.spec[f].dtype, e.f64_partials[f], e.nblocks[f], e.spec[f].sc, nullptr);
+    return;
+  }
+  const int b = int(blockIdx.x) - e.count;
+  int f = 0;
+  while (f + 1 < e.count && e.first[f + 1] <= b) ++f;
+  uint32_t epoch = 0;
+  speculative_steps(e.spec[f], e.spec[f].spec_depth, e.count + e.first[f], uint32_t(e.first[f + 1] - e.first[f]),
+                    false, epoch, &s_ok, &s_cexp, &s_go);
+}
+
 }  // namespace
+
+cudaError_t launch_gather_colors_seg(const GatherArgs* a, int count, cudaStream_t stream) {
+  if (count < 1 || count > kSegMax) return cudaErrorInvalidValue;
+  Seg<GatherArgs> sg;
+  int blocks[kSegMax];
+  for (int f = 0; f < count; ++f) {
+    sg.a[f] = a[f];
+    blocks[f] = a[f].n > 0 ? std::min((a[f].n + 1023) / 1024, 152 * 8) : 0;  // as launch_gather_colors
+  }
+  const int grid = seg_layout(sg, blocks, count);
+  if (grid == 0) return cudaSuccess;
+  return launch_kernel(k_gather_seg, dim3(grid), dim3(256), 0, stream, false, sg);
+}
+
+cudaError_t launch_ne_moments_seg(const MomentArgs* a, int count, int dtype, int num_sms, cudaStream_t stream) {
+  if (count < 1 || count > kSegMax) return cudaErrorInvalidValue;
+  Seg<MomentArgs> sg;
+  int blocks[kSegMax];
+  for (int f = 0; f < count; ++f) {
+    sg.a[f] = a[f];
+    blocks[f] = a[f].n > 0 ? ne_moment_blocks(a[f].n, num_sms) : 0;
+  }
+  const int grid = seg_layout(sg, blocks, count);
+  if (grid == 0) return cudaSuccess;
+  if (dtype == 0) return launch_kernel(k_ne_moments_seg<0>, dim3(grid), dim3(kNeThreads), 0, stream, false, sg);
+  return launch_kernel(k_ne_moments_seg<1>, dim3(grid), dim3(kNeThreads), 0, stream, false, sg);
+}
+
+cudaError_t launch_ne_finalize_seg(const FilterArgs* spec, const double* const* f64_partials, const int* nblocks,
+                                   int count, int num_sms, cudaStream_t stream) {
+  if (count < 1 || count > kSegMax || num_sms < 2 * count) return cudaErrorInvalidValue;
+  static std::atomic<unsigned long long> configured{0};  // the shared-memory limit is set once per device
+  cudaError_t e = once_per_device(configured, [] {
+    return cudaFuncSetAttribute(k_ne_finalize_spec_seg, cudaFuncAttributeMaxDynamicSharedMemorySize, kSpecPadBytes);
+  });
+  if (e != cudaSuccess) return e;
+  EstimateSeg es;
+  es.count = count;
+  // the step blocks in proportion to the frames' points, at least one each
+  const int pool = num_sms - count;
+  double total = 0.0;
+  for (int f = 0; f < count; ++f) total += double(std::max(spec[f].n, 1));
+  int given = 0;
+  es.first[0] = 0;
+  for (int f = 0; f < count; ++f) {
+    es.spec[f] = spec[f];
+    es.f64_partials[f] = f64_partials[f];
+    es.nblocks[f] = nblocks[f];
+    const int left = count - 1 - f;  // frames after this one keep one block each
+    int b = int(double(pool) * double(std::max(spec[f].n, 1)) / total);
+    b = std::max(1, std::min(b, pool - given - left));
+    if (f == count - 1) b = pool - given;
+    given += b;
+    es.first[f + 1] = given;
+  }
+  return launch_kernel(k_ne_finalize_spec_seg, dim3(count + pool), dim3(kSpecThreads), kSpecPadBytes, stream, true,
+                       es);
+}
 
 cudaError_t launch_gather_colors(const void* rgb, int dtype, int n, const int32_t* perm1,
                                  uint32_t* y8, float4* yf, cudaStream_t stream) {
@@ -717,17 +842,20 @@ int ne_moment_blocks(int n, int num_sms) {
   return std::max(1, std::min((n + kNeThreads - 1) / kNeThreads, num_sms * per_sm));
 }
 
+MomentArgs moment_args(int n, int bits, const GraphBufs& gb, const uint32_t* y8, const float4* yf, float* spread,
+                       double* f64_partials, bool moments, bool sorted_patches, DevScalars* sc) {
+  return MomentArgs{n, bits, gb.pk, gb.c4, y8, yf, spread, f64_partials, moments ? 1 : 0, sorted_patches ? 1 : 0, sc};
+}
+
 cudaError_t launch_ne_moments(int n, int bits, int dtype, const GraphBufs& gb, const uint32_t* y8,
                               const float4* yf, float* spread, double* f64_partials,
                               DevScalars* sc, int num_sms, bool moments, bool sorted_patches,
                               cudaStream_t stream) {
   if (n <= 0) return cudaSuccess;
   const int grid = ne_moment_blocks(n, num_sms);
-  if (dtype == 0)
-    return launch_kernel(k_ne_moments<0>, dim3(grid), dim3(kNeThreads), 0, stream, false, n, bits, gb.pk, gb.c4, y8,
-                         yf, spread, f64_partials, moments ? 1 : 0, sorted_patches ? 1 : 0, sc);
-  return launch_kernel(k_ne_moments<1>, dim3(grid), dim3(kNeThreads), 0, stream, false, n, bits, gb.pk, gb.c4, y8, yf,
-                       spread, f64_partials, moments ? 1 : 0, sorted_patches ? 1 : 0, sc);
+  const MomentArgs a = moment_args(n, bits, gb, y8, yf, spread, f64_partials, moments, sorted_patches, sc);
+  if (dtype == 0) return launch_kernel(k_ne_moments<0>, dim3(grid), dim3(kNeThreads), 0, stream, false, a);
+  return launch_kernel(k_ne_moments<1>, dim3(grid), dim3(kNeThreads), 0, stream, false, a);
 }
 
 cudaError_t launch_ne_finalize(int dtype, const double* f64_partials, int nblocks, DevScalars* sc,

@@ -34,43 +34,60 @@
 namespace fgbd {
 namespace {
 
-// The scatter runs 512 threads on a 4096-key tile (8 keys a thread), twice
-// the threads of the counting pass, so that the per-block serial chains
-// (ranking, write-out) are half as long.  Two warps share one 32-bit digit
-// counter word (16 bits each: a warp ranks at most 256 keys).
-constexpr int kScatterThreads = 512;
-constexpr int kScatterWarps = kScatterThreads / 32;         // 16
-constexpr int kScatterKpt = kSortTile / kScatterThreads;     // 8
-constexpr int kPairWords = kScatterWarps / 2;               // counter words per digit
-constexpr int kDigitsPerThread = kMaxRadix / kScatterThreads;  // 2
+// The scatter ranks a 4096-key tile with THREADS threads (the one-frame path
+// runs 512, twice the threads of the counting pass, so that the per-block
+// serial chains - ranking, write-out - are half as long; the batch tuner may
+// pick 256 or 1024).  Two warps share one 32-bit digit counter word (16 bits
+// each: a warp ranks at most 512 keys).
+template <int THREADS>
+struct ScatterShape {
+  static constexpr int kWarps = THREADS / 32;
+  static constexpr int kKpt = kSortTile / THREADS;          // keys per thread
+  static constexpr int kPairWords = kWarps / 2;             // counter words per digit
+  static constexpr int kDigitsPerThread = kMaxRadix / THREADS;
+  static constexpr int kMinBlocks = THREADS >= 1024 ? 1 : 2;
+  static_assert(kSortTile % THREADS == 0 && kMaxRadix % THREADS == 0 && kWarps % 2 == 0 && 32 * kKpt <= 65535,
+                "tile, digits and counter halves must divide evenly");
+};
+constexpr int kScatterThreads = 512;  // the one-frame path
 
-size_t scatter_smem_bytes() {
+size_t scatter_smem_bytes(int threads) {
+  const int warps = threads / 32;
   return sizeof(uint32_t) *
-         (size_t(kPairWords) * kMaxRadix + 2 * size_t(kSortTile) + 2 * size_t(kMaxRadix) + kScatterWarps + 1);
+         (size_t(warps / 2) * kMaxRadix + 2 * size_t(kSortTile) + 2 * size_t(kMaxRadix) + warps + 1);
 }
 
-__global__ void __launch_bounds__(1024) k_coord_hist(const int32_t* __restrict__ xyz, int n, int bits,
-                                                     DevScalars* __restrict__ sc) {
-  pdl_wait();
+__device__ __forceinline__ void coord_hist_body(const HistArgs& a, int bid, int nblk) {
   __shared__ uint32_t h[3][kMaxRadix];
-  const int radix = 1 << bits;
+  const int radix = 1 << a.bits;
   for (int i = threadIdx.x; i < 3 * kMaxRadix; i += blockDim.x) (&h[0][0])[i] = 0;
   __syncthreads();
   const uint32_t m = uint32_t(radix) - 1u;
   bool bad = false;
-  const size_t gstride = size_t(gridDim.x) * blockDim.x;
-  for (size_t i = size_t(blockIdx.x) * blockDim.x + threadIdx.x; i < size_t(n); i += gstride) {
-    const int xi = xyz[3 * i], yi = xyz[3 * i + 1], zi = xyz[3 * i + 2];
+  const size_t gstride = size_t(nblk) * blockDim.x;
+  for (size_t i = size_t(bid) * blockDim.x + threadIdx.x; i < size_t(a.n); i += gstride) {
+    const int xi = a.xyz[3 * i], yi = a.xyz[3 * i + 1], zi = a.xyz[3 * i + 2];
     bad |= (uint32_t(xi) > m) | (uint32_t(yi) > m) | (uint32_t(zi) > m);
     atomicAdd(&h[0][uint32_t(xi) & m], 1u);
     atomicAdd(&h[1][uint32_t(yi) & m], 1u);
     atomicAdd(&h[2][uint32_t(zi) & m], 1u);
   }
-  if (bad) atomicOr(&sc->status, kFlagRange);
+  if (bad) atomicOr(&a.sc->status, kFlagRange);
   __syncthreads();
   for (int c = 0; c < 3; ++c)
     for (int d = threadIdx.x; d < radix; d += blockDim.x)
-      if (h[c][d]) atomicAdd(&sc->chist[c][d], h[c][d]);
+      if (h[c][d]) atomicAdd(&a.sc->chist[c][d], h[c][d]);
+}
+
+__global__ void __launch_bounds__(1024) k_coord_hist(HistArgs a) {
+  pdl_wait();
+  coord_hist_body(a, blockIdx.x, gridDim.x);
+}
+
+__global__ void __launch_bounds__(1024) k_coord_hist_seg(const __grid_constant__ Seg<HistArgs> s) {
+  pdl_wait();
+  const int f = seg_frame(s, blockIdx.x);
+  coord_hist_body(s.a[f], blockIdx.x - s.start[f], s.start[f + 1] - s.start[f]);
 }
 
 // The keys and values of one tile (striped: item j of lane l of warp w is
@@ -99,12 +116,10 @@ __device__ __forceinline__ void load_tile(const SortPassArgs& a, int warp_base, 
 }
 
 // Reduce: digit counts of every tile, counts[digit * tiles + tile].
-__global__ void __launch_bounds__(kSortThreads) k_tile_counts(SortPassArgs a) {
-  pdl_wait();
+__device__ __forceinline__ void tile_counts_body(const SortPassArgs& a, int t) {
   __shared__ uint32_t s_h[kMaxRadix];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int radix = 1 << a.bits;
-  const int t = blockIdx.x;
   for (int d = tid; d < radix; d += kSortThreads) s_h[d] = 0;
   __syncthreads();
   uint32_t key[kSortKpt], val[kSortKpt];
@@ -118,14 +133,24 @@ __global__ void __launch_bounds__(kSortThreads) k_tile_counts(SortPassArgs a) {
   for (int d = tid; d < radix; d += kSortThreads) a.counts[size_t(d) * a.tiles + t] = s_h[d];
 }
 
+__global__ void __launch_bounds__(kSortThreads) k_tile_counts(SortPassArgs a) {
+  pdl_wait();
+  tile_counts_body(a, blockIdx.x);
+}
+
+__global__ void __launch_bounds__(kSortThreads) k_tile_counts_seg(const __grid_constant__ Seg<SortPassArgs> s) {
+  pdl_wait();
+  const int f = seg_frame(s, blockIdx.x);
+  tile_counts_body(s.a[f], blockIdx.x - s.start[f]);
+}
+
 // Scan: one warp per digit row.  counts become offsets: the start of the
 // digit's bucket (total of the smaller digits) plus the counts of the earlier
 // tiles.  Each lane owns a run of up to 8 consecutive tiles per batch.
-__global__ void __launch_bounds__(256) k_tile_scan(SortPassArgs a) {
-  pdl_wait();
+__device__ __forceinline__ void tile_scan_body(const SortPassArgs& a, int bid) {
   const int lane = threadIdx.x & 31;
   const int radix = 1 << a.bits;
-  const int d = blockIdx.x * 8 + (threadIdx.x >> 5);
+  const int d = bid * 8 + (threadIdx.x >> 5);
   if (d >= radix) return;
   // the digit's bucket start: lane l sums the histogram entries 32l..32l+31
   // below d, read as eight independent 16-byte loads
@@ -168,10 +193,24 @@ __global__ void __launch_bounds__(256) k_tile_scan(SortPassArgs a) {
   }
 }
 
+__global__ void __launch_bounds__(256) k_tile_scan(SortPassArgs a) {
+  pdl_wait();
+  tile_scan_body(a, blockIdx.x);
+}
+
+__global__ void __launch_bounds__(256) k_tile_scan_seg(const __grid_constant__ Seg<SortPassArgs> s) {
+  pdl_wait();
+  const int f = seg_frame(s, blockIdx.x);
+  tile_scan_body(s.a[f], blockIdx.x - s.start[f]);
+}
+
 // Scatter: rank each key of the tile among equal digits (stable), then write
 // the tile out in digit runs at the offsets the scan produced.
-__global__ void __launch_bounds__(kScatterThreads, 2) k_sort_scatter(SortPassArgs a) {
-  pdl_wait();
+template <int THREADS>
+__device__ __forceinline__ void sort_scatter_body(const SortPassArgs& a, int t) {
+  using SS = ScatterShape<THREADS>;
+  constexpr int kScatterWarps = SS::kWarps, kScatterKpt = SS::kKpt, kPairWords = SS::kPairWords;
+  constexpr int kDigitsPerThread = SS::kDigitsPerThread;
   extern __shared__ uint32_t smem[];
   uint32_t* s_whist = smem;                             // [kPairWords][radix]: warps 2w, 2w+1 in the low, high half
   uint32_t* s_keys = s_whist + kPairWords * kMaxRadix;  // [kSortTile]
@@ -184,12 +223,11 @@ __global__ void __launch_bounds__(kScatterThreads, 2) k_sort_scatter(SortPassArg
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int bits = a.bits, radix = 1 << bits;
   const uint32_t m = uint32_t(radix) - 1u;
-  const int t = blockIdx.x;
   const int shift = a.shift;
   const int warp_base = t * kSortTile + warp * (32 * kScatterKpt);
-  for (int i = tid; i < kPairWords * radix; i += kScatterThreads) s_whist[i] = 0;
+  for (int i = tid; i < kPairWords * radix; i += THREADS) s_whist[i] = 0;
   // this tile's global start of every digit, known before any key is ranked
-  for (int d = tid; d < radix; d += kScatterThreads) s_gbase[d] = a.counts[size_t(d) * a.tiles + t];
+  for (int d = tid; d < radix; d += THREADS) s_gbase[d] = a.counts[size_t(d) * a.tiles + t];
 
   // the keys and values of this warp's 256 positions (striped, so loads coalesce)
   uint32_t key[kScatterKpt], val[kScatterKpt], rnk[kScatterKpt];
@@ -277,7 +315,7 @@ __global__ void __launch_bounds__(kScatterThreads, 2) k_sort_scatter(SortPassArg
       if (d < radix) s_tstart[d] = start;
       start += tot[i];
     }
-    if (tid == kScatterThreads - 1) *s_count = start;
+    if (tid == THREADS - 1) *s_count = start;
   }
   __syncthreads();
 
@@ -300,7 +338,7 @@ __global__ void __launch_bounds__(kScatterThreads, 2) k_sort_scatter(SortPassArg
   uint32_t* ko = a.keys_out;
   uint32_t* vo = a.vals_out;
   int32_t* ro = a.rank_out;
-  for (uint32_t i = tid; i < cnt; i += kScatterThreads) {
+  for (uint32_t i = tid; i < cnt; i += THREADS) {
     const uint32_t k = s_keys[i], v = s_vals[i];
     const uint32_t dk = (k >> shift) & m;
     const uint32_t g = s_gbase[dk] + (i - s_tstart[dk]);
@@ -309,6 +347,20 @@ __global__ void __launch_bounds__(kScatterThreads, 2) k_sort_scatter(SortPassArg
     if (vo) vo[g] = v;
     if (ro) ro[v] = int32_t(g);
   }
+}
+
+template <int THREADS>
+__global__ void __launch_bounds__(THREADS, ScatterShape<THREADS>::kMinBlocks) k_sort_scatter(SortPassArgs a) {
+  pdl_wait();
+  sort_scatter_body<THREADS>(a, blockIdx.x);
+}
+
+template <int THREADS>
+__global__ void __launch_bounds__(THREADS, ScatterShape<THREADS>::kMinBlocks)
+    k_sort_scatter_seg(const __grid_constant__ Seg<SortPassArgs> s) {
+  pdl_wait();
+  const int f = seg_frame(s, blockIdx.x);
+  sort_scatter_body<THREADS>(s.a[f], blockIdx.x - s.start[f]);
 }
 
 // ---------------------------------------------------------------- slab sort
@@ -391,11 +443,15 @@ __device__ __forceinline__ uint32_t digit_warp_offsets(uint32_t* cnt, int radix,
   return run;
 }
 
-__global__ void __launch_bounds__(kSlabThreads, 4)
-    k_slab_sort(int n, int bits, const uint32_t* __restrict__ keys_in, const uint32_t* __restrict__ vals_in,
-                uint32_t* __restrict__ keys_tmp, uint32_t* __restrict__ vals_tmp, uint32_t* __restrict__ keys_out,
-                int32_t* __restrict__ vals_out, const DevScalars* __restrict__ sc) {
-  pdl_wait();
+__device__ __forceinline__ void slab_sort_body(const SlabArgs& sa, int yv) {
+  const int n = sa.n, bits = sa.bits;
+  const uint32_t* __restrict__ keys_in = sa.keys_in;
+  const uint32_t* __restrict__ vals_in = sa.vals_in;
+  uint32_t* __restrict__ keys_tmp = sa.keys_tmp;
+  uint32_t* __restrict__ vals_tmp = sa.vals_tmp;
+  uint32_t* __restrict__ keys_out = sa.keys_out;
+  int32_t* __restrict__ vals_out = sa.vals_out;
+  const DevScalars* __restrict__ sc = sa.sc;
   extern __shared__ uint32_t smem[];
   uint32_t* cnt = smem;                                   // [kSlabPairWords][radix]
   uint32_t* s_keys = cnt + kSlabPairWords * kMaxRadix;    // [kSlabMax]
@@ -407,7 +463,7 @@ __global__ void __launch_bounds__(kSlabThreads, 4)
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int radix = 1 << bits;
   const uint32_t m = uint32_t(radix) - 1u;
-  const int yv = blockIdx.x;
+  if (yv >= radix) return;
   const uint32_t* hy = sc->chist[1];
   const uint32_t size = hy[yv];
   if (size == 0) return;
@@ -549,7 +605,18 @@ __global__ void __launch_bounds__(kSlabThreads, 4)
   }
 }
 
-// One code's order per grid row (blockIdx.y = code).  Code 0 is the C1 order
+__global__ void __launch_bounds__(kSlabThreads, 4) k_slab_sort(SlabArgs a) {
+  pdl_wait();
+  slab_sort_body(a, blockIdx.x);
+}
+
+__global__ void __launch_bounds__(kSlabThreads, 4) k_slab_sort_seg(const __grid_constant__ Seg<SlabArgs> s) {
+  pdl_wait();
+  const int f = seg_frame(s, blockIdx.x);
+  slab_sort_body(s.a[f], blockIdx.x - s.start[f]);
+}
+
+// One code's order per group of gx blocks (block x of code c).  Code 0 is the C1 order
 // itself; codes 1 and 2 read the sorted ids along C2 and C3 and the packed C1
 // codes in the same order (keys of the C2 pass; keys of the slab sort for C3),
 // so only the C2 rank of a C3 point is a gather.  Each lane takes four
@@ -598,16 +665,16 @@ __device__ __forceinline__ bool same_scan_line(int code, uint32_t a, uint32_t c,
 // Under the same-line variant (same_line) a pair is linked along a code only on
 // one scan line of it (k_c1_line_flags then records the missing C1 links).
 template <bool SAME_LINE>
-__global__ void __launch_bounds__(kLinkThreads, 6) k_link(int n, int bits, int cap,
-                                                       const int32_t* __restrict__ ord23,
-                                                       const uint32_t* __restrict__ keys_c2,
-                                                       const uint32_t* __restrict__ keys_c3,
-                                                       const int32_t* __restrict__ rank2,
-                                                       const uint32_t* __restrict__ pk, int4* __restrict__ c4,
-                                                       DevScalars* __restrict__ sc) {
-  pdl_wait();
+__device__ __forceinline__ void link_body(const LinkArgs& la, int bx, int gx, int code) {
+  const int n = la.n, bits = la.bits, cap = la.cap;
+  const int32_t* __restrict__ ord23 = la.ord23;
+  const uint32_t* __restrict__ keys_c2 = la.keys_c2;
+  const uint32_t* __restrict__ keys_c3 = la.keys_c3;
+  const int32_t* __restrict__ rank2 = la.rank2;
+  const uint32_t* __restrict__ pk = la.pk;
+  int4* __restrict__ c4 = la.c4;
+  DevScalars* __restrict__ sc = la.sc;
   __shared__ unsigned long long s_red[8];
-  const int code = blockIdx.y;
   const int lane = threadIdx.x & 31;
   const int32_t* ord = code == 0 ? nullptr : ord23 + size_t(code - 1) * size_t(cap);
   const uint32_t* keys = code == 0 ? pk : (code == 1 ? keys_c2 : keys_c3);
@@ -615,9 +682,9 @@ __global__ void __launch_bounds__(kLinkThreads, 6) k_link(int n, int bits, int c
   unsigned long long edges = 0;
   float dist_f = 0.f;  // this thread's few edge lengths; converted to fixed point once
   constexpr int kSpan = 32 * kLinkPerLane;
-  const int warps = gridDim.x * (kLinkThreads / 32);
+  const int warps = gx * (kLinkThreads / 32);
   // whole warps step together so the shuffles see every lane
-  for (int base = (blockIdx.x * (kLinkThreads / 32) + (threadIdx.x >> 5)) * kSpan; base < n; base += warps * kSpan) {
+  for (int base = (bx * (kLinkThreads / 32) + (threadIdx.x >> 5)) * kSpan; base < n; base += warps * kSpan) {
     const int r0 = base + kLinkPerLane * lane;
     int kk[kLinkPerLane];
     uint32_t cc[kLinkPerLane];
@@ -699,19 +766,44 @@ __global__ void __launch_bounds__(kLinkThreads, 6) k_link(int n, int bits, int c
   }
 }
 
+template <bool SAME_LINE>
+__global__ void __launch_bounds__(kLinkThreads, 6) k_link(LinkArgs a) {
+  pdl_wait();
+  link_body<SAME_LINE>(a, blockIdx.x, gridDim.x, blockIdx.y);
+}
+
+// segmented: frame f's blocks are three runs of equal length, one per code
+template <bool SAME_LINE>
+__global__ void __launch_bounds__(kLinkThreads, 6) k_link_seg(const __grid_constant__ Seg<LinkArgs> s) {
+  pdl_wait();
+  const int f = seg_frame(s, blockIdx.x);
+  const int local = blockIdx.x - s.start[f], gx = (s.start[f + 1] - s.start[f]) / 3;
+  link_body<SAME_LINE>(s.a[f], local % gx, gx, local / gx);
+}
+
 // Same-line variant: the missing links of every sorted point to its C1
 // neighbours k - 1, k + 1 (not on its C1 scan line) go into the high bits of
 // its packed code, where every kernel that takes k +- 1 as neighbours looks.
 // (A neighbour's word may already carry its own bits when read: the
 // coordinates are decoded through masks, so that does not matter.)
-__global__ void __launch_bounds__(256) k_c1_line_flags(int n, int bits, uint32_t* pk) {
-  pdl_wait();
-  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+__device__ __forceinline__ void c1_line_flags_body(int n, int bits, uint32_t* pk, int bid, int nblk) {
+  for (int k = bid * blockDim.x + threadIdx.x; k < n; k += nblk * blockDim.x) {
     const uint32_t c = pk[k] & kCoordMask;
     const bool prev_ok = k > 0 && same_scan_line(0, c, pk[k - 1], bits);
     const bool next_ok = k + 1 < n && same_scan_line(0, c, pk[k + 1], bits);
     pk[k] = c | (prev_ok ? 0u : kNoPrevLink) | (next_ok ? 0u : kNoNextLink);
   }
+}
+
+__global__ void __launch_bounds__(256) k_c1_line_flags(int n, int bits, uint32_t* pk) {
+  pdl_wait();
+  c1_line_flags_body(n, bits, pk, blockIdx.x, gridDim.x);
+}
+
+__global__ void __launch_bounds__(256) k_c1_line_flags_seg(const __grid_constant__ Seg<LinkArgs> s) {
+  pdl_wait();
+  const int f = seg_frame(s, blockIdx.x);
+  c1_line_flags_body(s.a[f].n, s.a[f].bits, s.a[f].pk, blockIdx.x - s.start[f], s.start[f + 1] - s.start[f]);
 }
 
 // Windows w > 1 (Section 2.2 with w points linked on each side): one thread
@@ -802,11 +894,68 @@ __global__ void __launch_bounds__(256) k_orders_export(int n, int cap, const int
 
 }  // namespace
 
+namespace {
+// blocks of one frame's launch of each kernel (the same in both paths)
+int coord_hist_blocks(int n, int num_sms) { return n <= 0 ? 0 : std::max(1, std::min((n + 1023) / 1024, num_sms)); }
+int link_gx(int n, int num_sms) {
+  // the three codes' blocks together fill the GPU once (6 resident blocks of 256 threads per SM)
+  return std::max(1, std::min((n + kLinkThreads * kLinkPerLane - 1) / (kLinkThreads * kLinkPerLane), num_sms * 2));
+}
+int line_flag_blocks(int n, int num_sms) { return n <= 0 ? 0 : std::min((n + 255) / 256, num_sms * 8); }
+
+template <int THREADS>
+cudaError_t scatter_attr() {
+  // the shared-memory limit is a per-device function attribute: set it once per device
+  static std::atomic<unsigned long long> configured{0};
+  return once_per_device(configured, [] {
+    cudaError_t e = cudaFuncSetAttribute(k_sort_scatter<THREADS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         int(scatter_smem_bytes(THREADS)));
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_sort_scatter_seg<THREADS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               int(scatter_smem_bytes(THREADS)));
+    return e;
+  });
+}
+
+cudaError_t slab_attr() {
+  static std::atomic<unsigned long long> configured{0};  // the shared-memory limit is set once per device
+  return once_per_device(configured, [] {
+    cudaError_t e = cudaFuncSetAttribute(k_slab_sort, cudaFuncAttributeMaxDynamicSharedMemorySize, int(slab_smem_bytes()));
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_slab_sort_seg, cudaFuncAttributeMaxDynamicSharedMemorySize, int(slab_smem_bytes()));
+    return e;
+  });
+}
+
+template <typename A, typename K>
+cudaError_t launch_seg(K kernel, const A* args, const int* blocks, int count, int threads, size_t smem,
+                       cudaStream_t stream) {
+  if (count < 1 || count > kSegMax) return cudaErrorInvalidValue;
+  Seg<A> sg;
+  for (int f = 0; f < count; ++f) sg.a[f] = args[f];
+  const int grid = seg_layout(sg, blocks, count);
+  if (grid == 0) return cudaSuccess;
+  return launch_kernel(kernel, dim3(grid), dim3(threads), smem, stream, false, sg);
+}
+
+SlabArgs slab_args(int n, int bits, int cap, const SortBufs& sb, const GraphBufs& gb, const DevScalars* sc) {
+  // scratch for slabs larger than shared memory: the C2 order and C2 ranks, written later
+  return SlabArgs{n, bits, sb.keys[0], sb.vals[0], reinterpret_cast<uint32_t*>(gb.ord23),
+                  reinterpret_cast<uint32_t*>(gb.rank2), sb.keys[1], gb.ord23 + size_t(cap), sc};
+}
+}  // namespace
+
+HistArgs hist_args(const int32_t* xyz, int n, int bits, DevScalars* sc) { return HistArgs{xyz, n, bits, sc}; }
+
+LinkArgs link_args(int n, int bits, int cap, const GraphBufs& gb, const SortBufs& sb, DevScalars* sc) {
+  return LinkArgs{n, bits, cap, gb.ord23, sb.keys[0], sb.keys[1], gb.rank2, gb.pk, gb.c4, sc};
+}
+
 cudaError_t launch_coord_hist(const int32_t* xyz, int n, int bits, DevScalars* sc, int num_sms, cudaStream_t stream) {
   if (n <= 0) return cudaSuccess;
   // one large block per SM: few blocks keep the global atomics of the final merge few
-  const int grid = std::max(1, std::min((n + 1023) / 1024, num_sms));
-  return launch_kernel(k_coord_hist, dim3(grid), dim3(1024), 0, stream, false, xyz, n, bits, sc);
+  return launch_kernel(k_coord_hist, dim3(coord_hist_blocks(n, num_sms)), dim3(1024), 0, stream, false,
+                       hist_args(xyz, n, bits, sc));
 }
 
 cudaError_t launch_tile_counts(const SortPassArgs& a, cudaStream_t stream) {
@@ -818,13 +967,10 @@ cudaError_t launch_tile_scan(const SortPassArgs& a, cudaStream_t stream) {
 }
 
 cudaError_t launch_sort_scatter(const SortPassArgs& a, cudaStream_t stream) {
-  // the shared-memory limit is a per-device function attribute: set it once per device
-  static std::atomic<unsigned long long> configured{0};
-  const cudaError_t e = once_per_device(configured, [] {
-    return cudaFuncSetAttribute(k_sort_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, int(scatter_smem_bytes()));
-  });
+  const cudaError_t e = scatter_attr<kScatterThreads>();
   if (e != cudaSuccess) return e;
-  return launch_kernel(k_sort_scatter, dim3(a.tiles), dim3(kScatterThreads), scatter_smem_bytes(), stream, false, a);
+  return launch_kernel(k_sort_scatter<kScatterThreads>, dim3(a.tiles), dim3(kScatterThreads),
+                       scatter_smem_bytes(kScatterThreads), stream, false, a);
 }
 
 cudaError_t launch_sort_pass(const SortPassArgs& a, cudaStream_t stream) {
@@ -837,31 +983,82 @@ cudaError_t launch_sort_pass(const SortPassArgs& a, cudaStream_t stream) {
 cudaError_t launch_slab_sort(int n, int bits, int cap, const SortBufs& sb, const GraphBufs& gb,
                              const DevScalars* sc, cudaStream_t stream) {
   if (n <= 0) return cudaSuccess;
-  static std::atomic<unsigned long long> configured{0};  // the shared-memory limit is set once per device
-  const cudaError_t e = once_per_device(configured, [] {
-    return cudaFuncSetAttribute(k_slab_sort, cudaFuncAttributeMaxDynamicSharedMemorySize, int(slab_smem_bytes()));
-  });
+  const cudaError_t e = slab_attr();
   if (e != cudaSuccess) return e;
-  // scratch for slabs larger than shared memory: the C2 order and C2 ranks, written later
-  return launch_kernel(k_slab_sort, dim3(1 << bits), dim3(kSlabThreads), slab_smem_bytes(), stream, false, n, bits,
-                       sb.keys[0], sb.vals[0], reinterpret_cast<uint32_t*>(gb.ord23),
-                       reinterpret_cast<uint32_t*>(gb.rank2), sb.keys[1], gb.ord23 + size_t(cap), sc);
+  return launch_kernel(k_slab_sort, dim3(1 << bits), dim3(kSlabThreads), slab_smem_bytes(), stream, false,
+                       slab_args(n, bits, cap, sb, gb, sc));
 }
 
 cudaError_t launch_link(int n, int bits, int cap, bool same_line, const GraphBufs& gb, const SortBufs& sb,
                         DevScalars* sc, int num_sms, cudaStream_t stream) {
   if (n <= 0) return cudaSuccess;
-  // the three codes' blocks together fill the GPU once (6 resident blocks of 256 threads per SM)
-  const int gx = std::max(1, std::min((n + kLinkThreads * kLinkPerLane - 1) / (kLinkThreads * kLinkPerLane),
-                                      num_sms * 2));
-  if (!same_line)
-    return launch_kernel(k_link<false>, dim3(gx, 3), dim3(kLinkThreads), 0, stream, false, n, bits, cap, gb.ord23,
-                         sb.keys[0], sb.keys[1], gb.rank2, gb.pk, gb.c4, sc);
-  const cudaError_t e = launch_kernel(k_link<true>, dim3(gx, 3), dim3(kLinkThreads), 0, stream, false, n, bits, cap,
-                                      gb.ord23, sb.keys[0], sb.keys[1], gb.rank2, gb.pk, gb.c4, sc);
+  const int gx = link_gx(n, num_sms);
+  const LinkArgs la = link_args(n, bits, cap, gb, sb, sc);
+  if (!same_line) return launch_kernel(k_link<false>, dim3(gx, 3), dim3(kLinkThreads), 0, stream, false, la);
+  const cudaError_t e = launch_kernel(k_link<true>, dim3(gx, 3), dim3(kLinkThreads), 0, stream, false, la);
   if (e != cudaSuccess) return e;
-  return launch_kernel(k_c1_line_flags, dim3(std::min((n + 255) / 256, num_sms * 8)), dim3(256), 0, stream, false, n,
-                       bits, gb.pk);
+  return launch_kernel(k_c1_line_flags, dim3(line_flag_blocks(n, num_sms)), dim3(256), 0, stream, false, n, bits,
+                       gb.pk);
+}
+
+// ---- segmented (one launch over the frames of a batch)
+
+cudaError_t launch_coord_hist_seg(const HistArgs* a, int count, int num_sms, cudaStream_t stream) {
+  int blocks[kSegMax];
+  for (int f = 0; f < count && f < kSegMax; ++f) blocks[f] = coord_hist_blocks(a[f].n, num_sms);
+  return launch_seg(k_coord_hist_seg, a, blocks, count, 1024, 0, stream);
+}
+
+cudaError_t launch_sort_pass_seg(const SortPassArgs* a, int count, int scatter_threads, cudaStream_t stream) {
+  int tiles[kSegMax], scan[kSegMax];
+  for (int f = 0; f < count && f < kSegMax; ++f) {
+    tiles[f] = a[f].n > 0 ? a[f].tiles : 0;
+    scan[f] = a[f].n > 0 ? ((1 << a[f].bits) + 7) / 8 : 0;
+  }
+  cudaError_t e = launch_seg(k_tile_counts_seg, a, tiles, count, kSortThreads, 0, stream);
+  if (e == cudaSuccess) e = launch_seg(k_tile_scan_seg, a, scan, count, 256, 0, stream);
+  if (e != cudaSuccess) return e;
+  switch (scatter_threads) {
+    case 256:
+      e = scatter_attr<256>();
+      return e != cudaSuccess ? e
+                              : launch_seg(k_sort_scatter_seg<256>, a, tiles, count, 256, scatter_smem_bytes(256), stream);
+    case 1024:
+      e = scatter_attr<1024>();
+      return e != cudaSuccess
+                 ? e
+                 : launch_seg(k_sort_scatter_seg<1024>, a, tiles, count, 1024, scatter_smem_bytes(1024), stream);
+    default:
+      e = scatter_attr<512>();
+      return e != cudaSuccess ? e
+                              : launch_seg(k_sort_scatter_seg<512>, a, tiles, count, 512, scatter_smem_bytes(512), stream);
+  }
+}
+
+cudaError_t launch_slab_sort_seg(const int* n, const int* bits, const int* cap, const SortBufs* sb,
+                                 const GraphBufs* gb, DevScalars* const* sc, int count, cudaStream_t stream) {
+  if (count < 1 || count > kSegMax) return cudaErrorInvalidValue;
+  const cudaError_t e = slab_attr();
+  if (e != cudaSuccess) return e;
+  SlabArgs a[kSegMax];
+  int blocks[kSegMax];
+  for (int f = 0; f < count; ++f) {
+    a[f] = slab_args(n[f], bits[f], cap[f], sb[f], gb[f], sc[f]);
+    blocks[f] = n[f] > 0 ? (1 << bits[f]) : 0;
+  }
+  return launch_seg(k_slab_sort_seg, a, blocks, count, kSlabThreads, slab_smem_bytes(), stream);
+}
+
+cudaError_t launch_link_seg(const LinkArgs* a, int count, bool same_line, int num_sms, cudaStream_t stream) {
+  int blocks[kSegMax], flags[kSegMax];
+  for (int f = 0; f < count && f < kSegMax; ++f) {
+    blocks[f] = a[f].n > 0 ? 3 * link_gx(a[f].n, num_sms) : 0;
+    flags[f] = line_flag_blocks(a[f].n, num_sms);
+  }
+  if (!same_line) return launch_seg(k_link_seg<false>, a, blocks, count, kLinkThreads, 0, stream);
+  const cudaError_t e = launch_seg(k_link_seg<true>, a, blocks, count, kLinkThreads, 0, stream);
+  if (e != cudaSuccess) return e;
+  return launch_seg(k_c1_line_flags_seg, a, flags, count, 256, 0, stream);
 }
 
 cudaError_t launch_link_wide(int n, int bits, int cap, int window, bool same_line, const GraphBufs& gb,
@@ -937,7 +1134,20 @@ __global__ void __launch_bounds__(256) k_zero_words(uint32_t* __restrict__ p, si
   for (size_t i = size_t(blockIdx.x) * blockDim.x + threadIdx.x; i < words; i += size_t(gridDim.x) * blockDim.x)
     p[i] = 0u;
 }
+
+__global__ void __launch_bounds__(256) k_zero_words_seg(const __grid_constant__ Seg<ZeroArgs> s) {
+  pdl_wait();
+  const int f = seg_frame(s, blockIdx.x);
+  const size_t b = size_t(blockIdx.x - s.start[f]), nb = size_t(s.start[f + 1] - s.start[f]);
+  for (size_t i = b * blockDim.x + threadIdx.x; i < s.a[f].words; i += nb * blockDim.x) s.a[f].p[i] = 0u;
+}
 }  // namespace
+
+cudaError_t launch_zero_words_seg(const ZeroArgs* a, int count, cudaStream_t stream) {
+  int blocks[kSegMax];
+  for (int f = 0; f < count && f < kSegMax; ++f) blocks[f] = int(std::min<size_t>((a[f].words + 255) / 256, 64));
+  return launch_seg(k_zero_words_seg, a, blocks, count, 256, 0, stream);
+}
 
 cudaError_t launch_zero_words(uint32_t* p, size_t words, cudaStream_t stream) {
   if (words == 0) return cudaSuccess;

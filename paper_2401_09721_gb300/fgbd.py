@@ -65,6 +65,21 @@ VARIANT_SAME_LINE = 4        # FGBD_VARIANT_SAME_LINE
 FLAG_FUSED_SELECT = 1        # FGBD_FLAG_FUSED_SELECT
 
 
+class BatchShape(ctypes.Structure):
+    _fields_ = [
+        ("seg_frames", ctypes.c_int32),
+        ("scatter_threads", ctypes.c_int32),
+        ("filter_threads", ctypes.c_int32),
+        ("filter_blocks_per_sm", ctypes.c_int32),
+        ("ms", ctypes.c_float),
+        ("reserved", ctypes.c_int32 * 3),
+    ]
+
+    def as_dict(self) -> dict:
+        return dict(seg_frames=self.seg_frames, scatter_threads=self.scatter_threads,
+                    filter_threads=self.filter_threads, filter_blocks_per_sm=self.filter_blocks_per_sm, ms=self.ms)
+
+
 class Stats(ctypes.Structure):
     _fields_ = [
         ("n", ctypes.c_int64),
@@ -116,6 +131,11 @@ _SIGS = {
     "fgbd_run_batch": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(ctypes.c_int64),
                                       ctypes.POINTER(_P), ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(_P),
                                       ctypes.POINTER(ctypes.c_int32), ctypes.c_int32, _P]),
+    "fgbd_tune_batch": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(ctypes.c_int64),
+                                       ctypes.POINTER(_P), ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(_P),
+                                       ctypes.POINTER(ctypes.c_int32), ctypes.c_int32, _P, _P]),
+    "fgbd_get_batch_shape": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int64, _P]),
+    "fgbd_set_batch_shape": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int64, _P]),
     "fgbd_filter_forward": (ctypes.c_int, [_P, _P, ctypes.c_int32, ctypes.c_double, ctypes.c_double, ctypes.c_int32,
                                            _P, _P]),
     "fgbd_filter_backward": (ctypes.c_int, [_P, _P, _P, _P, _P]),
@@ -298,8 +318,7 @@ def fgbd_run_host(ctx, xyz: torch.Tensor, rgb_in: torch.Tensor, rgb_out: torch.T
 BATCH_MAX = 64  # FGBD_BATCH_MAX
 
 
-def fgbd_run_batch(ctxs, xyzs, rgbs_in, rgbs_out, stream=None) -> None:
-    """fgbd_run on several frames at once, frame f in context ctxs[f] (handles)."""
+def _batch_args(ctxs, xyzs, rgbs_in, rgbs_out):
     count = len(ctxs)
     if not (len(xyzs) == len(rgbs_in) == len(rgbs_out) == count):
         raise ValueError("one xyz, rgb_in and rgb_out per context")
@@ -310,17 +329,44 @@ def fgbd_run_batch(ctxs, xyzs, rgbs_in, rgbs_out, stream=None) -> None:
         _need_cuda(xyz, "xyz", n)
         _need_cuda(ci, "rgb_in", n)
         _need_cuda(co, "rgb_out", n)
+
     def arr(t, vals):
         return (t * count)(*[v.value if isinstance(v, ctypes.c_void_p) else v for v in vals])
 
-    _check(lib().fgbd_run_batch(arr(_P, ctxs),
-                                arr(_P, [_ptr(x) for x in xyzs]),
-                                arr(ctypes.c_int64, [x.shape[0] for x in xyzs]),
-                                arr(_P, [_ptr(c) for c in rgbs_in]),
-                                arr(ctypes.c_int32, [_dtype_code(c) for c in rgbs_in]),
-                                arr(_P, [_ptr(c) for c in rgbs_out]),
-                                arr(ctypes.c_int32, [_dtype_code(c) for c in rgbs_out]),
-                                count, _stream(stream)), "fgbd_run_batch")
+    return (arr(_P, ctxs), arr(_P, [_ptr(x) for x in xyzs]), arr(ctypes.c_int64, [x.shape[0] for x in xyzs]),
+            arr(_P, [_ptr(c) for c in rgbs_in]), arr(ctypes.c_int32, [_dtype_code(c) for c in rgbs_in]),
+            arr(_P, [_ptr(c) for c in rgbs_out]), arr(ctypes.c_int32, [_dtype_code(c) for c in rgbs_out]), count)
+
+
+def fgbd_run_batch(ctxs, xyzs, rgbs_in, rgbs_out, stream=None) -> None:
+    """fgbd_run on several frames at once, frame f in context ctxs[f] (handles)."""
+    _check(lib().fgbd_run_batch(*_batch_args(ctxs, xyzs, rgbs_in, rgbs_out), _stream(stream)), "fgbd_run_batch")
+
+
+def fgbd_tune_batch(ctxs, xyzs, rgbs_in, rgbs_out, stream=None) -> dict:
+    """Time candidate block shapes on this batch and keep the fastest (see fgbd.h)."""
+    out = BatchShape()
+    _check(lib().fgbd_tune_batch(*_batch_args(ctxs, xyzs, rgbs_in, rgbs_out), _stream(stream), ctypes.byref(out)),
+           "fgbd_tune_batch")
+    return out.as_dict()
+
+
+def fgbd_get_batch_shape(device: int, mean_points: int) -> dict:
+    out = BatchShape()
+    _check(lib().fgbd_get_batch_shape(int(device), int(mean_points), ctypes.byref(out)), "fgbd_get_batch_shape")
+    return out.as_dict()
+
+
+def fgbd_set_batch_shape(device: int, mean_points: int, shape: dict | None) -> None:
+    if shape is None:
+        _check(lib().fgbd_set_batch_shape(int(device), int(mean_points), None), "fgbd_set_batch_shape")
+        return
+    b = BatchShape()
+    b.seg_frames = int(shape.get("seg_frames", 16))
+    b.scatter_threads = int(shape["scatter_threads"])
+    b.filter_threads = int(shape["filter_threads"])
+    b.filter_blocks_per_sm = int(shape["filter_blocks_per_sm"])
+    _check(lib().fgbd_set_batch_shape(int(device), int(mean_points), ctypes.byref(b)), "fgbd_set_batch_shape")
 
 
 def fgbd_filter_forward(ctx, rgb_in: torch.Tensor, q: int, alpha: float, sigma: float, checkpoint: int,
@@ -563,6 +609,16 @@ class Context:
         for c, x in zip(contexts, xyzs):
             c.n = x.shape[0]
         return outs
+
+    @staticmethod
+    def tune_batch(contexts, xyzs, rgbs_in, out_dtype=torch.float32, outs=None, stream=None):
+        """fgbd_tune_batch over Context objects; returns (the chosen shapes, the outputs)."""
+        if outs is None:
+            outs = [torch.empty((x.shape[0], 3), dtype=out_dtype, device=c.device) for c, x in zip(contexts, xyzs)]
+        shape = fgbd_tune_batch([c.handle for c in contexts], xyzs, rgbs_in, outs, stream)
+        for c, x in zip(contexts, xyzs):
+            c.n = x.shape[0]
+        return shape, outs
 
     def stats(self, stream=None) -> dict:
         return fgbd_get_stats(self.handle, stream)

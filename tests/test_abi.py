@@ -98,6 +98,15 @@ def test_host_side_checks_without_gpu(so):
     assert lib.fgbd_graph_export(None, ctypes.byref(g), None) == 1
     assert lib.fgbd_graph_csr(None, None, None, None, None, None, None) == 1
     lib.fgbd_graph_free(None)                                               # NULL is ignored
+    shape = fgbd.BatchShape()
+    assert lib.fgbd_get_batch_shape(0, 1000000, ctypes.byref(shape)) == 0   # the defaults, no GPU needed
+    assert (shape.seg_frames, shape.scatter_threads, shape.filter_threads, shape.filter_blocks_per_sm) == (0, 512, 512, 2)
+    assert lib.fgbd_get_batch_shape(0, 20000, ctypes.byref(shape)) == 0     # small frames: segmented by default
+    assert shape.seg_frames == 16
+    assert lib.fgbd_get_batch_shape(0, -1, ctypes.byref(shape)) == 1
+    shape.scatter_threads = 300
+    assert lib.fgbd_set_batch_shape(0, 1000, ctypes.byref(shape)) == 1      # not a built shape
+    assert lib.fgbd_tune_batch(None, None, None, None, None, None, None, 1, None, None) == 1
     assert lib.fgbd_estimate_noise(None, None, 0, None, None, None) == 1
     assert lib.fgbd_select_filter(None, None, 0, None, None, None, None) == 1
 
@@ -111,7 +120,7 @@ def test_binding_structs_match_the_header_layout(tmp_path):
     cc = shutil.which("gcc") or shutil.which("cc")
     if cc is None:
         pytest.skip("no C compiler")
-    structs = {"fgbd_params": fgbd.Params, "fgbd_stats": fgbd.Stats}
+    structs = {"fgbd_params": fgbd.Params, "fgbd_stats": fgbd.Stats, "fgbd_batch_shape": fgbd.BatchShape}
     lines = ["#include <stddef.h>", "#include <stdio.h>", '#include "fgbd.h"', "int main(void) {"]
     for cname, py in structs.items():
         lines.append(f'  printf("{cname} size %zu\\n", sizeof({cname}));')
