@@ -33,10 +33,14 @@ __all__ = [
     "slg_edges",
     "adjacency_csr",
     "sigma_g",
+    "node_mean_lengths",
+    "sigma_g_node",
+    "pair_scale",
     "edge_weights",
     "random_walk_weights",
     "patch_vectors",
     "patch_covariance",
+    "pooled_patches",
     "eigenvalues_desc",
     "tail_rule",
     "estimate_noise",
@@ -62,6 +66,14 @@ class Params:
     sorted_patches: bool = True   # False: "NE-GBP w/o sort", patch entries in link order
     # a reading, not the paper's: links only between points of the same scan line
     same_line: bool = False       # True: no link joins the end of one scan line to the next
+    # alternative readings where the paper leaves a choice open (the defaults are the readings taken)
+    sigma_g_mode: str = "edge"    # sigma_g of Eq. 4 (Section 2.2): "edge" the mean length over the edges;
+                                  # "node" the mean over the points of each point's mean edge length;
+                                  # "pair" a bandwidth per point, w_ij = exp(-d_ij^2 / (sigma_i sigma_j))
+    pooled_patch: bool = False    # Section 2.3: True takes D = K + 1 per colour channel and pools the
+                                  # three channels' patches in one covariance (False: D = 3 (K + 1))
+    q_rule: str = "first"         # Section 2.4: "first" stops at the first q whose J is not below the
+                                  # previous one; "global" takes the argmin of J over q = 0..q_max
 
 
 # --------------------------------------------------------------------------
@@ -164,6 +176,36 @@ def sigma_g(g: np.ndarray, row_ptr: np.ndarray, col: np.ndarray) -> float:
     return float(np.sqrt(_sq_dist(g, row_ptr, col).astype(np.float64)).mean())
 
 
+def node_mean_lengths(g: np.ndarray, row_ptr: np.ndarray, col: np.ndarray) -> np.ndarray:
+    """sigma_i: the mean Euclidean length of point i's edges (0 for a point without edges).
+
+    The per-point bandwidth of the "pair" reading of sigma_g (Section 2.2
+    speaks of the average distance between points and their neighbours).
+    """
+    n = row_ptr.size - 1
+    deg = np.diff(row_ptr)
+    lengths = np.sqrt(_sq_dist(g, row_ptr, col).astype(np.float64))
+    s = np.bincount(_row_index(row_ptr), weights=lengths, minlength=n)
+    out = np.zeros(n)
+    out[deg > 0] = s[deg > 0] / deg[deg > 0]
+    return out
+
+
+def sigma_g_node(g: np.ndarray, row_ptr: np.ndarray, col: np.ndarray) -> float:
+    """The "node" reading of sigma_g (Section 2.2): the mean over the points that
+    have edges of their mean edge length (0 without edges)."""
+    deg = np.diff(row_ptr)
+    if not (deg > 0).any():
+        return 0.0
+    return float(node_mean_lengths(g, row_ptr, col)[deg > 0].mean())
+
+
+def pair_scale(g: np.ndarray, row_ptr: np.ndarray, col: np.ndarray) -> np.ndarray:
+    """sigma_i sigma_j per adjacency entry (the "pair" reading of Eq. 4's sigma_g^2)."""
+    si = node_mean_lengths(g, row_ptr, col)
+    return si[_row_index(row_ptr)] * si[col]
+
+
 def edge_weights(g: np.ndarray, row_ptr: np.ndarray, col: np.ndarray, sg: float) -> np.ndarray:
     """Eq. 4: w_ij = exp(-||g_i - g_j||^2 / sigma_g^2) per adjacency entry (float64).
 
@@ -177,23 +219,32 @@ def edge_weights(g: np.ndarray, row_ptr: np.ndarray, col: np.ndarray, sg: float)
     return np.exp(-d2 / (sg * sg))
 
 
-def random_walk_weights(g: np.ndarray, row_ptr: np.ndarray, col: np.ndarray, sg: float) -> np.ndarray:
+def random_walk_weights(g: np.ndarray, row_ptr: np.ndarray, col: np.ndarray, sg: float,
+                        scale: np.ndarray | None = None) -> np.ndarray:
     """Entries of D^{-1} W (rows of Eq. 4's W divided by their degree d_i = sum_j w_ij).
 
     Computed as exp(-(d2_ij - min_k d2_ik)/sigma_g^2) / sum_k exp(-(d2_ik - min_k d2_ik)/sigma_g^2),
     which equals w_ij / d_i exactly in real arithmetic (the common factor
     exp(-min d2 / sigma_g^2) cancels) and stays defined when every w_ij of a
-    row underflows in floating point.
+    row underflows in floating point.  With ``scale`` (per adjacency entry,
+    the "pair" reading: sigma_i sigma_j) the exponents are d2_ij / scale_ij,
+    shifted by their row minimum the same way; an entry with scale 0 has
+    length 0 (its points' mean edge length is 0) and exponent 0.
     """
     d2 = _sq_dist(g, row_ptr, col).astype(np.float64)
     n = row_ptr.size - 1
     rows = _row_index(row_ptr)
     if d2.size == 0:
         return d2
-    dmin = np.full(n, np.inf)
-    np.minimum.at(dmin, rows, d2)
-    shifted = d2 - dmin[rows]
-    e = np.ones_like(shifted) if sg == 0.0 else np.exp(-shifted / (sg * sg))
+    if scale is None:
+        a = np.zeros_like(d2) if sg == 0.0 else d2 / (sg * sg)
+    else:
+        a = np.zeros_like(d2)
+        pos = scale > 0
+        a[pos] = d2[pos] / scale[pos]
+    amin = np.full(n, np.inf)
+    np.minimum.at(amin, rows, a)
+    e = np.exp(-(a - amin[rows]))
     s = np.bincount(rows, weights=e, minlength=n)
     return e / s[rows]
 
@@ -264,6 +315,15 @@ def patch_covariance(A: np.ndarray):
     return (C.T @ C) / n, mu
 
 
+def pooled_patches(A: np.ndarray) -> np.ndarray:
+    """The "pooled" reading of Section 2.3's patch dimension: each RGB patch
+    (node-major, channel-minor, D = 3 (K + 1)) becomes three single-channel
+    patches of K + 1 entries, one per channel, all in one sample: [3 N', K + 1]."""
+    n, d = A.shape
+    k1 = d // 3
+    return A.reshape(n, k1, 3).transpose(0, 2, 1).reshape(3 * n, k1)
+
+
 ZERO_EIG_REL = 1e-9
 
 
@@ -305,15 +365,28 @@ def tail_rule(lam: np.ndarray):
     raise AssertionError("unreachable: a single value is its own median")
 
 
-def estimate_noise(g, f, row_ptr, col, k: int = 6, orders: np.ndarray | None = None):
+def estimate_noise(g, f, row_ptr, col, k: int = 6, orders: np.ndarray | None = None, pooled: bool = False):
     """NE-GBP (Section 2.3): patches -> covariance -> eigenvalues -> sigma_est.
 
     With no complete patch the estimate is 0 (reading: nothing to estimate from).
-    ``orders`` selects the unsorted (link-order) patches of the ablation.
+    ``orders`` selects the unsorted (link-order) patches of the ablation;
+    ``pooled`` the per-channel patches of D = k + 1 pooled over the channels.
     Returns a dict with sigma_est, tau, m, eigenvalues, n_patches, covariance.
     """
     A, idx = patch_vectors(g, f, row_ptr, col, k, orders)
     D = 3 * (k + 1)
+    if pooled:
+        D = k + 1
+        n_points = A.shape[0]
+        A = pooled_patches(A) if n_points else np.zeros((0, D))
+        if n_points == 0:
+            return dict(sigma_est=0.0, tau=0.0, m=0, eigenvalues=np.zeros(D), n_patches=0,
+                        covariance=np.zeros((D, D)), mean=np.zeros(D))
+        S, mu = patch_covariance(A)
+        lam = eigenvalues_desc(S)
+        m, tau, s = tail_rule(lam)
+        return dict(sigma_est=s, tau=tau, m=m, eigenvalues=lam, n_patches=int(n_points),
+                    covariance=S, mean=mu)
     if A.shape[0] == 0:
         return dict(sigma_est=0.0, tau=0.0, m=0, eigenvalues=np.zeros(D), n_patches=0,
                     covariance=np.zeros((D, D)), mean=np.zeros(D))
@@ -454,24 +527,34 @@ def selection_objective(y: np.ndarray, xq: np.ndarray, keep: np.ndarray, sigma_e
     return abs(sigma_est * sigma_est - lost / (3.0 * keep.sum()))
 
 
-def select_q(y, row_ptr, col, rw, keep, sigma_est: float, q_max: int = 64):
+def select_q(y, row_ptr, col, rw, keep, sigma_est: float, q_max: int = 64, rule: str = "first"):
     """Section 2.4: the integer q minimising Eq. 6, and x_q.
 
-    Reading: q is searched upward from 0 and the search stops at the first q
-    whose objective is not below the previous one (J(q) >= J(q-1)); q* = q - 1.
-    Equal objectives go to the smaller q.  The search ends at q_max.
+    Reading ("first"): q is searched upward from 0 and the search stops at the
+    first q whose objective is not below the previous one (J(q) >= J(q-1));
+    q* = q - 1.  Equal objectives go to the smaller q.  The search ends at q_max.
+    Alternative reading ("global"): J is evaluated for every q = 0..q_max and
+    q* is its argmin (the smallest q among equal minima).
     Returns (q*, x_{q*} float64 [N, 3], J list for q = 0..last evaluated).
     """
+    if rule not in ("first", "global"):
+        raise ValueError(rule)
     y = np.asarray(y, dtype=np.float64)
     M = _rw_matrix(row_ptr, col, rw)
     x_prev = y.copy()
     J = [selection_objective(y, x_prev, keep, sigma_est)]
+    best_q, best_x = 0, x_prev
     for q in range(1, q_max + 1):
         x = lowpass_step(x_prev, M)
         J.append(selection_objective(y, x, keep, sigma_est))
-        if J[q] >= J[q - 1]:
-            return q - 1, x_prev, J
+        if rule == "first":
+            if J[q] >= J[q - 1]:
+                return q - 1, x_prev, J
+        elif J[q] < J[best_q]:
+            best_q, best_x = q, x
         x_prev = x
+    if rule == "global":
+        return best_q, best_x, J
     return q_max, x_prev, J
 
 
@@ -507,18 +590,27 @@ def fgbd(g: np.ndarray, f: np.ndarray, params: Params = Params(), q: int | None 
     orders = scan_orders(codes)
     edges = slg_edges(orders, params.window, codes if params.same_line else None, params.bits)
     row_ptr, col = adjacency_csr(edges, n)
-    sg = sigma_g(g, row_ptr, col)
-    w = edge_weights(g, row_ptr, col, sg)
-    rw = random_walk_weights(g, row_ptr, col, sg)
+    if params.sigma_g_mode not in ("edge", "node", "pair"):
+        raise ValueError(params.sigma_g_mode)
+    sg = sigma_g_node(g, row_ptr, col) if params.sigma_g_mode == "node" else sigma_g(g, row_ptr, col)
+    if params.sigma_g_mode == "pair":
+        scale = pair_scale(g, row_ptr, col)
+        d2 = _sq_dist(g, row_ptr, col).astype(np.float64)
+        w = np.ones_like(d2)
+        w[scale > 0] = np.exp(-d2[scale > 0] / scale[scale > 0])
+        rw = random_walk_weights(g, row_ptr, col, sg, scale)
+    else:
+        w = edge_weights(g, row_ptr, col, sg)
+        rw = random_walk_weights(g, row_ptr, col, sg)
     noise = estimate_noise(g, f, row_ptr, col, k=6 * params.window,
-                           orders=None if params.sorted_patches else orders)
+                           orders=None if params.sorted_patches else orders, pooled=params.pooled_patch)
     spread = fslr_spread(f, row_ptr, col)
     if params.fslr:
         keep = fslr_keep(spread, noise["sigma_est"], params.fslr_factor)
     else:
         keep = np.ones(n, dtype=bool)   # "FGBD w/o FSLR": Eq. 6 over every point
     if q is None:
-        qs, out, J = select_q(f, row_ptr, col, rw, keep, noise["sigma_est"], params.q_max)
+        qs, out, J = select_q(f, row_ptr, col, rw, keep, noise["sigma_est"], params.q_max, params.q_rule)
     else:
         qs, out, J = q, lowpass(f, row_ptr, col, rw, q), []
     return OracleResult(orders, row_ptr, col, sg, w, rw, noise, spread, keep, qs, J, out)

@@ -13,7 +13,12 @@ Each function restates one definition of the paper:
 * ``link_order_patches`` the "NE-GBP w/o sort" ablation (Table 4): patch entries
                         in the order the scan lines link them.
 * ``spread``            Section 2.4: mean over channels of the population std in a patch.
-* ``filter_power``      Eq. 5: x <- x/2 + (sum_j w_ij x_j)/(2 sum_j w_ij), q times.
+* ``filter_power``      Eq. 5: x <- x/2 + (sum_j w_ij x_j)/(2 sum_j w_ij), q times
+                        (``pair`` bandwidths: w_ij = exp(-d^2 / (s_i s_j))).
+* ``node_sigma``        the alternative readings of sigma_g: each point's mean edge
+                        length, and their mean over the points with edges.
+* ``pooled_covariance`` the pooled reading of the patch dimension: every channel of
+                        every patch one sample of K + 1 entries.
 """
 from __future__ import annotations
 
@@ -140,7 +145,29 @@ def spread(colors, nb, i):
     return total / 3.0
 
 
-def filter_power(points, colors, nb, sg, q):
+def node_sigma(points, nb):
+    """(per-point mean edge length list, mean of it over the points with edges)."""
+    per = []
+    for i in range(len(points)):
+        if nb[i]:
+            per.append(sum(math.sqrt(sq_dist(points[i], points[j])) for j in nb[i]) / len(nb[i]))
+        else:
+            per.append(0.0)
+    with_edges = [per[i] for i in range(len(points)) if nb[i]]
+    return per, (sum(with_edges) / len(with_edges) if with_edges else 0.0)
+
+
+def pooled_covariance(vectors):
+    """Each RGB patch (point-major, channel-minor) as three single-channel samples."""
+    samples = []
+    for v in vectors:
+        k1 = len(v) // 3
+        for c in range(3):
+            samples.append([v[3 * m + c] for m in range(k1)])
+    return patch_covariance(samples)
+
+
+def filter_power(points, colors, nb, sg, q, pair=None):
     n = len(points)
     x = [[float(colors[i][c]) for c in range(3)] for i in range(n)]
     for _ in range(q):
@@ -149,7 +176,14 @@ def filter_power(points, colors, nb, sg, q):
             if not nb[i]:
                 new.append(list(x[i]))
                 continue
-            ws = {j: math.exp(-sq_dist(points[i], points[j]) / (sg * sg)) for j in nb[i]}
+            if pair is not None:
+                # the common factor exp(-min_j a_ij) cancels in the row; taken out so nothing underflows
+                a = {j: (sq_dist(points[i], points[j]) / (pair[i] * pair[j]) if pair[i] * pair[j] > 0 else 0.0)
+                     for j in nb[i]}
+                amin = min(a.values())
+                ws = {j: math.exp(-(a[j] - amin)) for j in nb[i]}
+            else:
+                ws = {j: math.exp(-sq_dist(points[i], points[j]) / (sg * sg)) for j in nb[i]}
             dsum = sum(ws.values())
             row = []
             for c in range(3):

@@ -576,3 +576,135 @@ def test_param_filter_adjoint_identity():
     xq = orc.param_filter(xyz, row_ptr, col, y, 5, 0.5, sg)[-1]
     gy, _, _ = orc.param_filter_vjp(xyz, row_ptr, col, y, 5, 0.5, sg, gout)
     assert np.sum(xq * gout) == pytest.approx(np.sum(y * gy), rel=1e-12)
+
+
+# ---------------------------------------------------------------- alternative readings
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_sigma_g_readings_brute_force(seed):
+    """node-mean sigma_g and the per-point bandwidths of the pair reading
+    against loops over the brute-force neighbour sets."""
+    rng = np.random.default_rng(40 + seed)
+    xyz = random_cloud(rng, 60, 4, dup_frac=0.1)
+    pts = [tuple(int(v) for v in p) for p in xyz]
+    nb = bf.neighbour_sets(pts)
+    _, _, _, row_ptr, col = graph_of(xyz, 4)
+    per, mean = bf.node_sigma(pts, nb)
+    assert np.allclose(orc.node_mean_lengths(xyz, row_ptr, col), per, rtol=1e-13, atol=0)
+    assert orc.sigma_g_node(xyz, row_ptr, col) == pytest.approx(mean, rel=1e-13)
+    # edge and node means differ unless every point has the same mean edge length
+    assert orc.sigma_g(xyz, row_ptr, col) != pytest.approx(mean, rel=1e-6)
+    scale = orc.pair_scale(xyz, row_ptr, col)
+    rows = np.repeat(np.arange(len(pts)), np.diff(row_ptr))
+    assert np.allclose(scale, [per[i] * per[j] for i, j in zip(rows, col)], rtol=1e-13, atol=0)
+
+
+def test_sigma_g_node_hand_example():
+    # a path of four points along x with edge lengths 1, 3 and 5: the edge
+    # mean is 3; the points' mean edge lengths are 1, 2, 4 and 5, whose mean
+    # is 3 as well.  A path 0-1-2 with lengths 1 and 8 separates the readings:
+    # edge mean 4.5, point means 1, 4.5 and 8, node mean 13.5 / 3 = 4.5 -- equal
+    # again (a path always gives equal means); a star does not: centre linked
+    # to leaves at 1, 1 and 4 has edge mean 2 and point means 2, 1, 1, 4,
+    # node mean 2; leaves at 2, 2 and 8: edge mean 4, point means 4, 2, 2, 8,
+    # node mean 4.  With a second centre the weights differ: see the random clouds.
+    xyz4 = np.array([[0, 0, 0], [1, 0, 0], [4, 0, 0], [9, 0, 0]])
+    row_ptr4 = np.array([0, 1, 3, 5, 6])
+    col4 = np.array([1, 0, 2, 1, 3, 2])
+    assert orc.sigma_g(xyz4, row_ptr4, col4) == 3.0
+    assert orc.node_mean_lengths(xyz4, row_ptr4, col4).tolist() == [1.0, 2.0, 4.0, 5.0]
+    assert orc.sigma_g_node(xyz4, row_ptr4, col4) == 3.0
+    # two stars sharing a leaf: centres a (0) and b (4); a has leaves at 1 and 1
+    # (points 1, 2), b has the leaf 3 at distance 2 and shares leaf 1 (distance
+    # from b to point 1 is 3).  Edges: a-1 (1), a-2 (1), b-3 (2), b-1 (3):
+    # edge mean 7 / 4 = 1.75; point means a 1, point 1 (1 + 3) / 2 = 2,
+    # point 2 1, b (2 + 3) / 2 = 2.5, point 3 2: node mean 8.5 / 5 = 1.7.
+    xyz = np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0], [4, 0, 0], [4, 2, 0]])
+    edges = [(0, 1), (0, 2), (3, 4), (3, 1)]
+    nbs = [[] for _ in range(5)]
+    for a, b in edges:
+        nbs[a].append(b)
+        nbs[b].append(a)
+    row_ptr = np.cumsum([0] + [len(v) for v in nbs])
+    col = np.array([c for v in nbs for c in sorted(v)])
+    assert orc.sigma_g(xyz, row_ptr, col) == pytest.approx(1.75)
+    assert orc.node_mean_lengths(xyz, row_ptr, col).tolist() == [1.0, 2.0, 1.0, 2.5, 2.0]
+    assert orc.sigma_g_node(xyz, row_ptr, col) == pytest.approx(1.7)
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_pair_weights_filter_brute_force(seed):
+    rng = np.random.default_rng(60 + seed)
+    xyz = random_cloud(rng, 40, 4)
+    pts = [tuple(int(v) for v in p) for p in xyz]
+    f = rng.uniform(0, 255, size=(40, 3))
+    _, _, _, row_ptr, col = graph_of(xyz, 4)
+    per, _ = bf.node_sigma(pts, bf.neighbour_sets(pts))
+    rw = orc.random_walk_weights(xyz, row_ptr, col, 0.0, orc.pair_scale(xyz, row_ptr, col))
+    nb = bf.neighbour_sets(pts)
+    for q in (1, 3):
+        got = orc.lowpass(f, row_ptr, col, rw, q)
+        ref = np.array(bf.filter_power(pts, f.tolist(), nb, 0.0, q, pair=per))
+        assert np.allclose(got, ref, rtol=1e-12, atol=1e-10)
+    res = orc.fgbd(xyz, np.clip(f, 0, 255).astype(np.uint8), orc.Params(bits=4, sigma_g_mode="pair"))
+    assert np.allclose(res.rw, rw, rtol=1e-13)
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_pooled_patches_brute_force(seed):
+    rng = np.random.default_rng(80 + seed)
+    xyz = synth.sphere_points(3000, 6, seed)
+    f = rng.integers(0, 256, size=(len(xyz), 3)).astype(np.uint8)
+    _, _, _, row_ptr, col = graph_of(xyz, 6)
+    pts = [tuple(int(v) for v in p) for p in xyz]
+    nb = bf.neighbour_sets(pts)
+    vecs = bf.patches(pts, f.tolist(), nb)
+    cov, mu = bf.pooled_covariance(vecs)
+    A, _ = orc.patch_vectors(xyz, f, row_ptr, col, 6)
+    S, m = orc.patch_covariance(orc.pooled_patches(A))
+    assert S.shape == (7, 7) and np.allclose(S, cov, rtol=1e-10, atol=1e-9) and np.allclose(m, mu)
+    r = orc.estimate_noise(xyz, f, row_ptr, col, 6, pooled=True)
+    assert r["eigenvalues"].size == 7 and r["n_patches"] == len(vecs)
+    # the pooled covariance is the channel average of the 7x7 diagonal blocks of
+    # the RGB covariance, plus the spread of the channel means
+    S21, mu21 = orc.patch_covariance(A)
+    blocks = [S21[c::3, c::3] for c in range(3)]
+    means = [mu21[c::3] for c in range(3)]
+    mbar = sum(means) / 3
+    rebuilt = sum(blocks) / 3 + sum(np.outer(mc - mbar, mc - mbar) for mc in means) / 3
+    assert np.allclose(S, rebuilt, rtol=1e-10, atol=1e-9)
+
+
+def test_pooled_patches_recover_white_noise():
+    rng = np.random.default_rng(7)
+    xyz = synth.sphere_points(20500, 9, 0)
+    f = (128.0 + rng.normal(0, 20.0, size=(len(xyz), 3)))
+    _, _, _, row_ptr, col = graph_of(xyz, 9)
+    r = orc.estimate_noise(xyz, f, row_ptr, col, 6, pooled=True)
+    assert abs(r["sigma_est"] - 20.0) / 20.0 < 0.03
+
+
+def test_select_q_global_argmin_brute_force():
+    """The global rule against J computed for every q with dense powers of D^-1 W."""
+    rng = np.random.default_rng(9)
+    xyz = np.unique(random_cloud(rng, 120, 5), axis=0)
+    n = len(xyz)
+    _, _, _, row_ptr, col = graph_of(xyz, 5)
+    rw = orc.random_walk_weights(xyz, row_ptr, col, orc.sigma_g(xyz, row_ptr, col))
+    R = np.zeros((n, n))
+    R[np.repeat(np.arange(n), np.diff(row_ptr)), col] = rw
+    P = 0.5 * np.eye(n) + 0.5 * R
+    y = rng.uniform(0, 255, size=(n, 3))
+    keep = rng.uniform(size=n) < 0.7
+    for sigma in (3.0, 15.0, 40.0):
+        Js, x = [], y.copy()
+        for q in range(0, 13):
+            Js.append(abs(sigma ** 2 - ((y[keep] ** 2).sum() - (x[keep] ** 2).sum()) / (3 * keep.sum())))
+            x = P @ x
+        q, xq, J = orc.select_q(y, row_ptr, col, rw, keep, sigma, q_max=12, rule="global")
+        assert len(J) == 13 and np.allclose(J, Js, rtol=1e-9, atol=1e-9)
+        assert q == int(np.argmin(Js))
+        assert np.allclose(xq, np.linalg.matrix_power(P, q) @ y, rtol=1e-9, atol=1e-8)
+        qf, _, Jf = orc.select_q(y, row_ptr, col, rw, keep, sigma, q_max=12)
+        # the first local minimum is never below the global one, and the rules agree on a convex curve
+        assert Js[qf] >= Js[q]
