@@ -717,7 +717,11 @@ def run_fgbd(args):
     clean_d = torch.from_numpy(clean).to(dev).float()
     for name, variant, window in (("as_published", 0, 1), ("no_fslr", fgbd.VARIANT_NO_FSLR, 1),
                                   ("unsorted_patch", fgbd.VARIANT_UNSORTED_PATCH, 1),
-                                  ("same_line", fgbd.VARIANT_SAME_LINE, 1), ("window2", 0, 2), ("window3", 0, 3)):
+                                  ("same_line", fgbd.VARIANT_SAME_LINE, 1), ("window2", 0, 2), ("window3", 0, 3),
+                                  ("sigma_g_node_mean", fgbd.VARIANT_SIGMA_NODE, 1),
+                                  ("sigma_g_per_point", fgbd.VARIANT_SIGMA_PAIR, 1),
+                                  ("pooled_patch_d7", fgbd.VARIANT_POOLED_PATCH, 1),
+                                  ("q_global_argmin", fgbd.VARIANT_GLOBAL_Q, 1)):
         vctx = fgbd.Context(n, bits=BITS, variant=variant, window=window)
         for k in range(2 * len(cols)):  # every frame's graph is captured before the timed runs
             vctx.run(x, cols[k % len(cols)], out=out)
@@ -737,8 +741,8 @@ def run_fgbd(args):
             ps.append(round(10.0 * math.log10(255.0 ** 2 / max(mse, 1e-12)), 3))
         vctx.close()
         ablations[name] = {"ms_per_step": float(np.mean(ms)), "value": n / (float(np.mean(ms)) / 1e3) / 1e6,
-                           "unit": "Mpoints/s", "window": window, "sigma": list(SIGMAS),
-                           "sigma_est": [round(v, 4) for v in sig],
+                           "unit": "Mpoints/s", "window": window, "variant": int(variant), "sigma": list(SIGMAS),
+                           "sigma_est": [round(v, 4) for v in sig], "sigma_g": round(vst["sigma_g"], 4),
                            "q": qv, "psnr_db": ps}
 
     batched = None

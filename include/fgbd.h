@@ -93,6 +93,25 @@ typedef struct fgbd_params {
  *     scan line is also linked to the first of the next (Section 2.2); this
  *     switch drops those links, to measure what they contribute. */
 #define FGBD_VARIANT_SAME_LINE 4
+/* Alternative readings where the paper leaves a choice open (for comparison
+ * runs; the method as read here is 0):
+ *   FGBD_VARIANT_SIGMA_NODE: sigma_g of Eq. 4 is the mean over the points of
+ *     each point's mean edge length (Section 2.2 speaks of the average distance
+ *     between points and their neighbours) instead of the mean edge length.
+ *   FGBD_VARIANT_SIGMA_PAIR: a bandwidth per point, sigma_i = its mean edge
+ *     length, and w_ij = exp(-d_ij^2 / (sigma_i sigma_j)) (window 1; not with
+ *     the differentiable filter, whose bandwidth is one scalar).
+ *   FGBD_VARIANT_POOLED_PATCH: NE-GBP with patches of D = 6 w + 1 entries per
+ *     colour channel, the three channels pooled in one covariance (Section 2.3
+ *     defines patches of a point and its neighbours; window 1), instead of
+ *     D = 3 (6 w + 1) RGB patches.
+ *   FGBD_VARIANT_GLOBAL_Q: q* is the argmin of Eq. 6 over q = 0..q_max (the
+ *     smaller q among equal values) instead of the first q whose objective does
+ *     not fall; every J(q) up to q_max is evaluated (Section 2.4). */
+#define FGBD_VARIANT_SIGMA_NODE 8
+#define FGBD_VARIANT_SIGMA_PAIR 16
+#define FGBD_VARIANT_POOLED_PATCH 32
+#define FGBD_VARIANT_GLOBAL_Q 64
 
 typedef struct fgbd_stats {
   int64_t n;                                /* points of the last graph */

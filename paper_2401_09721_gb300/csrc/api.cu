@@ -40,6 +40,7 @@ struct fgbd_ctx {
   float* spread = nullptr;
   float4* x0 = nullptr;
   float4* x1 = nullptr;
+  float4* xbest = nullptr;  // the global reading of the q search: the best iterate (else null)
   double* f64part = nullptr;
   int f64_blocks = 0;
   WideNe wne{};  // noise-estimate scratch of windows w > 1 (unused at window 1)
@@ -209,7 +210,11 @@ bool params_ok(const fgbd_params& p) {
   if (p.window < 1) return false;
   if (!(p.fslr_factor > 0.0) || p.fslr_factor > 1e30) return false;
   if (p.q_max < 0 || p.q_max > kQCap) return false;
-  if (p.variant & ~(FGBD_VARIANT_NO_FSLR | FGBD_VARIANT_UNSORTED_PATCH | FGBD_VARIANT_SAME_LINE)) return false;
+  if (p.variant & ~(FGBD_VARIANT_NO_FSLR | FGBD_VARIANT_UNSORTED_PATCH | FGBD_VARIANT_SAME_LINE |
+                    FGBD_VARIANT_SIGMA_NODE | FGBD_VARIANT_SIGMA_PAIR | FGBD_VARIANT_POOLED_PATCH |
+                    FGBD_VARIANT_GLOBAL_Q))
+    return false;
+  if ((p.variant & FGBD_VARIANT_SIGMA_NODE) && (p.variant & FGBD_VARIANT_SIGMA_PAIR)) return false;
   if (p.flags & ~FGBD_FLAG_FUSED_SELECT) return false;
   for (int r : p.reserved)
     if (r != 0) return false;
@@ -270,6 +275,9 @@ FilterArgs filter_args(fgbd_ctx* ctx, int mode, int q_fixed, const double* sigma
   a.cx = ctx->gb.cx;
   a.nx = ctx->gb.nx;
   a.cx_stride = ctx->gb.cx_stride;
+  a.node_sig = (ctx->params.variant & FGBD_VARIANT_SIGMA_PAIR) ? ctx->gb.node_sig : nullptr;
+  a.q_global = (ctx->params.variant & FGBD_VARIANT_GLOBAL_Q) ? 1 : 0;
+  a.xbest = ctx->xbest;
   return a;
 }
 
@@ -391,6 +399,9 @@ fgbd_status do_build(fgbd_ctx* ctx, const int32_t* xyz, int64_t n64, cudaStream_
                   launch_link_wide(n, bits, ord_stride(ctx), ctx->params.window, same_line, ctx->gb, ctx->sb,
                                    ctx->sc, ctx->num_sms, st));
     if (same_line) ctx->launches += 1;  // and k_c1_line_flags
+    if (ctx->params.variant & (FGBD_VARIANT_SIGMA_NODE | FGBD_VARIANT_SIGMA_PAIR))
+      FGBD_LAUNCH(ctx, "slg_node_sigma", st,
+                  launch_node_sigma(n, bits, ctx->gb, ctx->sc, ctx->num_sms, st));
   }
   ctx->has_graph = true;
   return FGBD_OK;
@@ -565,6 +576,10 @@ bool seg_eligible(const std::vector<fgbd_ctx*>& ctxs, const std::vector<fgbd_ctx
   for (size_t f = 0; f < ctxs.size(); ++f) {
     const fgbd_ctx* c = ctxs[f];
     if (c->params.window != 1 || c->params.variant != c0->params.variant || c->num_sms != c0->num_sms) return false;
+    // the readings that add a kernel or a buffer run on streams
+    if (c->params.variant & (FGBD_VARIANT_SIGMA_NODE | FGBD_VARIANT_SIGMA_PAIR | FGBD_VARIANT_POOLED_PATCH |
+                             FGBD_VARIANT_GLOBAL_Q))
+      return false;
     if (keys[f].in_dtype != keys[0].in_dtype || keys[f].n < 1) return false;
   }
   return true;
@@ -840,9 +855,11 @@ fgbd_status fgbd_ctx_create(int64_t capacity, const fgbd_params* params, fgbd_ct
   if (params) p = *params;
   else fgbd_params_default(&p);
   if (!params_ok(p)) return FGBD_EINVAL;
-  // windows 2..3 are built; the unsorted-patch ablation is defined for window 1 only
+  // windows 2..3 are built; the unsorted-patch ablation is defined for window 1 only,
+  // and the pair bandwidths and pooled patches are built for window 1 only
   if (p.window > kMaxWindow) return FGBD_ENOTIMPL;
-  if (p.window > 1 && (p.variant & FGBD_VARIANT_UNSORTED_PATCH)) return FGBD_ENOTIMPL;
+  if (p.window > 1 && (p.variant & (FGBD_VARIANT_UNSORTED_PATCH | FGBD_VARIANT_SIGMA_PAIR | FGBD_VARIANT_POOLED_PATCH)))
+    return FGBD_ENOTIMPL;
   fgbd_ctx* ctx = new (std::nothrow) fgbd_ctx();
   if (!ctx) return FGBD_ENOMEM;
   static std::atomic<uint64_t> next_uid{1};
@@ -898,6 +915,8 @@ fgbd_status fgbd_ctx_create(int64_t capacity, const fgbd_params* params, fgbd_ct
       {reinterpret_cast<void**>(&ctx->f64part), size_t(ctx->f64_blocks) * kP * 8},
       {reinterpret_cast<void**>(&ctx->scan_tmp), ((C + 1 + 1023) / 1024 + 1) * 8},
       {reinterpret_cast<void**>(&ctx->gb.cx), size_t(nx) * align_up(C, 64) * 4},
+      {reinterpret_cast<void**>(&ctx->gb.node_sig), (p.variant & FGBD_VARIANT_SIGMA_PAIR) ? C * 4 : 0},
+      {reinterpret_cast<void**>(&ctx->xbest), (p.variant & FGBD_VARIANT_GLOBAL_Q) ? C * 16 : 0},
       {reinterpret_cast<void**>(&ctx->wne.part), wide ? size_t(w_blocks) * wP * 8 : 0},
       {reinterpret_cast<void**>(&ctx->wne.tot), wide ? wP * 8 : 0},
       {reinterpret_cast<void**>(&ctx->wne.S), wide ? wD * wD * 8 : 0},
@@ -926,6 +945,8 @@ fgbd_status fgbd_ctx_create(int64_t capacity, const fgbd_params* params, fgbd_ct
   ctx->sb.vals[1] = static_cast<uint32_t*>(vals1);
   ctx->gb.nx = nx;
   ctx->gb.cx_stride = int(align_up(C, 64));
+  if (!(p.variant & FGBD_VARIANT_SIGMA_PAIR)) ctx->gb.node_sig = nullptr;
+  if (!(p.variant & FGBD_VARIANT_GLOBAL_Q)) ctx->xbest = nullptr;
   if (!wide) {
     ctx->gb.cx = nullptr;
     ctx->wne = WideNe{};
@@ -935,6 +956,11 @@ fgbd_status fgbd_ctx_create(int64_t capacity, const fgbd_params* params, fgbd_ct
   if (wide) ok = ok && cudaMemset(ctx->wne.done, 0, 4) == cudaSuccess;
   const unsigned long long limit = kWaitLimitNs;
   ok = ok && cudaMemcpy(&ctx->sc->wait_limit_ns, &limit, sizeof(limit), cudaMemcpyHostToDevice) == cudaSuccess;
+  const uint32_t mode = (p.variant & FGBD_VARIANT_SIGMA_NODE) ? kSigmaNode
+                        : (p.variant & FGBD_VARIANT_SIGMA_PAIR) ? kSigmaPair : kSigmaEdge;
+  const uint32_t pooled = (p.variant & FGBD_VARIANT_POOLED_PATCH) ? 1u : 0u;
+  ok = ok && cudaMemcpy(&ctx->sc->sigma_mode, &mode, sizeof(mode), cudaMemcpyHostToDevice) == cudaSuccess;
+  ok = ok && cudaMemcpy(&ctx->sc->pooled_patch, &pooled, sizeof(pooled), cudaMemcpyHostToDevice) == cudaSuccess;
   ok = ok && cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking) == cudaSuccess;
   ok = ok && cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking) == cudaSuccess;
   for (cudaEvent_t* e : {&ctx->ev_fork, &ctx->ev_filter, &ctx->ev_join})
@@ -1354,6 +1380,7 @@ fgbd_status fgbd_filter_forward(fgbd_ctx* ctx, const float* rgb_in, int32_t q, d
   NvtxRange nvtx_("fgbd_filter_forward");
   if (!ctx) return FGBD_EINVAL;
   if (ctx->params.window != 1) return FGBD_ENOTIMPL;  // the adjoint rows hold six neighbours
+  if (ctx->params.variant & FGBD_VARIANT_SIGMA_PAIR) return FGBD_ENOTIMPL;  // its bandwidth is one scalar
   if (!ctx->has_graph) return FGBD_ESTATE;
   if (q < 0 || q > kQCap || checkpoint < 0) return FGBD_EINVAL;
   if (!std::isfinite(alpha) || !std::isfinite(sigma) || sigma < 0.0) return FGBD_EINVAL;
@@ -1466,11 +1493,14 @@ fgbd_status fgbd_get_stats(fgbd_ctx* ctx, fgbd_stats* out, void* stream) {
   out->valid = (ctx->has_graph ? 1 : 0) | (ctx->has_noise ? 2 : 0) | (ctx->has_sel ? 4 : 0);
   if (ctx->has_graph) {
     out->n_edges = int64_t(h.n_edges);
-    out->sigma_g = h.n_edges ? double(h.dist_fx) / double(1ull << kDistShift) / double(h.n_edges) : 0.0;
+    if (h.sigma_mode == kSigmaNode)
+      out->sigma_g = h.node_cnt ? double(h.node_fx) / double(1ull << kDistShift) / double(h.node_cnt) : 0.0;
+    else
+      out->sigma_g = h.n_edges ? double(h.dist_fx) / double(1ull << kDistShift) / double(h.n_edges) : 0.0;
   }
   if (ctx->has_noise) {
     out->n_patches = int64_t(h.n_patches);
-    out->patch_dim = 3 * (6 * ctx->params.window + 1);
+    out->patch_dim = h.pooled_patch ? 6 * ctx->params.window + 1 : 3 * (6 * ctx->params.window + 1);
     for (int i = 0; i < out->patch_dim; ++i) out->eigenvalues[i] = h.eig[i];
     out->m = h.m;
     out->tau = h.tau;
@@ -1525,6 +1555,12 @@ fgbd_status fgbd_graph_export(fgbd_ctx* ctx, fgbd_graph** out, void* stream) {
   gr->n = ctx->n;
   gr->nnz = int64_t(2 * edges);
   gr->sigma_g = edges ? double(dist) / double(1ull << kDistShift) / double(edges) : 0.0;
+  if (ctx->params.variant & FGBD_VARIANT_SIGMA_NODE) {
+    unsigned long long nfx = 0, ncnt = 0;
+    FGBD_CUDA(ctx, cudaMemcpy(&nfx, &ctx->sc->node_fx, sizeof(nfx), cudaMemcpyDeviceToHost));
+    FGBD_CUDA(ctx, cudaMemcpy(&ncnt, &ctx->sc->node_cnt, sizeof(ncnt), cudaMemcpyDeviceToHost));
+    gr->sigma_g = ncnt ? double(nfx) / double(1ull << kDistShift) / double(ncnt) : 0.0;
+  }
   const size_t rp_b = align_up(size_t(gr->n + 1) * 8, 256), col_b = align_up(size_t(gr->nnz) * 4, 256);
   if (cudaMalloc(&gr->mem, rp_b + 2 * col_b) != cudaSuccess) {
     cudaGetLastError();

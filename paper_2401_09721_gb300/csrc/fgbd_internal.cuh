@@ -56,6 +56,8 @@ struct DevScalars {
   unsigned long long n_edges;   // distinct undirected edges E
   unsigned long long dist_fx;   // sum of edge lengths, fixed point 2^-kDistShift
   alignas(16) uint32_t chist[3][kMaxRadix];  // histograms of x, y and z (read as uint4)
+  unsigned long long node_fx;   // node-mean reading: sum over points of their mean edge length (fixed point)
+  unsigned long long node_cnt;  // and the points that have edges
   uint32_t build_end_;
   // ---- noise estimate region
   unsigned long long n_patches;
@@ -83,7 +85,8 @@ struct DevScalars {
   uint32_t sel_end_;
   // ---- results of the selection
   double J[kQCap + 1];
-  int32_t kept_buf;             // where x_q is: 0 / 1 the iterate buffers, 2 + q - 1 a stored step, -1 the input
+  int32_t kept_buf;             // where x_q is: 0 / 1 the iterate buffers, 2 + q - 1 a stored step, -1 the input,
+                                // kKeptBest the copy of the global reading's best iterate
   int32_t q_sel;
   int32_t n_J;
   int32_t sel_valid;
@@ -91,7 +94,14 @@ struct DevScalars {
   uint32_t status;
   // ---- settings (set at context creation)
   unsigned long long wait_limit_ns;  // any device-side wait gives up after this long
+  uint32_t sigma_mode;               // sigma_g of Eq. 4: kSigmaEdge, kSigmaNode or kSigmaPair
+  uint32_t pooled_patch;             // 1: patches of D = 7 pooled over the colour channels (Section 2.3)
 };
+
+// Readings of sigma_g (Section 2.2): the mean length over the edges (the
+// method as read here), the mean over the points of each point's mean edge
+// length, or a bandwidth per point (w_ij = exp(-d_ij^2 / (sigma_i sigma_j))).
+enum : uint32_t { kSigmaEdge = 0u, kSigmaNode = 1u, kSigmaPair = 2u };
 
 // the regions are zeroed as 32-bit words
 static_assert(offsetof(DevScalars, n_edges) % 4 == 0 && offsetof(DevScalars, build_end_) % 4 == 0 &&
@@ -124,6 +134,7 @@ struct GraphBufs {
   int32_t* cx;
   int nx;            // 6 (w - 1)
   int cx_stride;     // row stride of cx, a multiple of 64
+  float* node_sig;   // [cap] each sorted point's mean edge length (the node and pair readings of sigma_g), or null
 };
 
 // number of further neighbour slots at window w
@@ -281,6 +292,9 @@ cudaError_t launch_slab_sort_seg(const int* n, const int* bits, const int* cap, 
 cudaError_t launch_link_seg(const LinkArgs* a, int count, bool same_line, int num_sms, cudaStream_t stream);
 cudaError_t launch_link(int n, int bits, int cap, bool same_line, const GraphBufs& gb, const SortBufs& sb,
                         DevScalars* sc, int num_sms, cudaStream_t stream);
+// each sorted point's mean edge length into gb.node_sig (if set) and, for the
+// node reading of sigma_g, their sum and count into the build scalars
+cudaError_t launch_node_sigma(int n, int bits, const GraphBufs& gb, DevScalars* sc, int num_sms, cudaStream_t stream);
 // windows w > 1: every link of the window (C2/C3 d = 1 into c4, d >= 2 into cx)
 // and the edge sums; then k_c1_line_flags under the same-line variant
 cudaError_t launch_link_wide(int n, int bits, int cap, int window, bool same_line, const GraphBufs& gb,
@@ -360,7 +374,14 @@ struct FilterArgs {
   const int32_t* cx;
   int nx;
   int cx_stride;
+  // the pair reading of sigma_g: each sorted point's mean edge length (null otherwise)
+  const float* node_sig;
+  // the global reading of the q search: argmin of J over 0..q_max; the best
+  // iterate beyond the stored steps is copied to xbest
+  int q_global;
+  float4* xbest;
 };
+constexpr int kKeptBest = 64;  // kept_buf value of the iterate copied to xbest
 cudaError_t launch_filter(const FilterArgs& a, int grid, cudaStream_t stream);
 int filter_grid(int n, int num_sms, int nx = 0);
 cudaError_t launch_output(const FilterArgs& a, cudaStream_t stream);  // the kept iterate, in input order
@@ -496,8 +517,13 @@ __device__ __forceinline__ unsigned long long block_sum_u64(unsigned long long v
   return t;
 }
 
-// sigma_g (Section 2.2) from the build sums
+// sigma_g (Section 2.2) from the build sums: the mean edge length, or under
+// the node reading the mean of the points' mean edge lengths
 __device__ __forceinline__ double sigma_g_of(const DevScalars* sc) {
+  if (sc->sigma_mode == kSigmaNode) {
+    const unsigned long long c = sc->node_cnt;
+    return c ? double(sc->node_fx) * (1.0 / double(1ull << kDistShift)) / double(c) : 0.0;
+  }
   const unsigned long long e = sc->n_edges;
   if (e == 0) return 0.0;
   return double(sc->dist_fx) * (1.0 / double(1ull << kDistShift)) / double(e);

@@ -90,7 +90,14 @@ __global__ void k_csr_fill(int n, int bits, GraphBufs gb, const int64_t* __restr
     float wv[kMaxDegree];
     for (int j = 0; j < cnt; ++j) {
       orig[j] = gb.perm1[nb[j]];
-      wv[j] = expf(-float(sq_dist_c1(gb.pk[k], gb.pk[nb[j]], bits)) * inv2);
+      const float d2 = float(sq_dist_c1(gb.pk[k], gb.pk[nb[j]], bits));
+      if (gb.node_sig && sc->sigma_mode == kSigmaPair) {
+        // the pair reading: w_ij = exp(-d_ij^2 / (sigma_i sigma_j)); 1 where the product is 0
+        const float s = gb.node_sig[k] * gb.node_sig[nb[j]];
+        wv[j] = s > 0.f ? expf(-d2 / s) : 1.f;
+      } else {
+        wv[j] = expf(-d2 * inv2);
+      }
     }
     for (int a = 1; a < cnt; ++a) {  // insertion sort by input index
       const int o = orig[a];

@@ -127,14 +127,40 @@ __device__ __forceinline__ float4 eq5_step(const FilterArgs& a, const float4* __
     dmin = min(dmin, d2[j]);
   }
   float se = 0.f, sr = 0.f, sgc = 0.f, sb = 0.f;
+  if (a.node_sig) {
+    // the pair reading: exponents d2_j / (sigma_k sigma_j), shifted by their minimum
+    const float sk = __ldg(&a.node_sig[k]);
+    float ex[6];
+    float emin = 3.0e38f;
 #pragma unroll
-  for (int j = 0; j < 6; ++j) {
-    if (v[j]) {
-      const float e = exp2f(float(dmin - d2[j]) * cexp);
-      se += e;
-      sr = fmaf(e, xn[j].x, sr);
-      sgc = fmaf(e, xn[j].y, sgc);
-      sb = fmaf(e, xn[j].z, sb);
+    for (int j = 0; j < 6; ++j) {
+      ex[j] = 0.f;
+      if (v[j]) {
+        const float s = sk * __ldg(&a.node_sig[nb[j]]);
+        ex[j] = s > 0.f ? float(d2[j]) / s : 0.f;
+        emin = fminf(emin, ex[j]);
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < 6; ++j) {
+      if (v[j]) {
+        const float e = exp2f((emin - ex[j]) * 1.4426950408889634f);
+        se += e;
+        sr = fmaf(e, xn[j].x, sr);
+        sgc = fmaf(e, xn[j].y, sgc);
+        sb = fmaf(e, xn[j].z, sb);
+      }
+    }
+  } else {
+#pragma unroll
+    for (int j = 0; j < 6; ++j) {
+      if (v[j]) {
+        const float e = exp2f(float(dmin - d2[j]) * cexp);
+        se += e;
+        sr = fmaf(e, xn[j].x, sr);
+        sgc = fmaf(e, xn[j].y, sgc);
+        sb = fmaf(e, xn[j].z, sb);
+      }
     }
   }
   float4 xo = xk;

@@ -522,24 +522,139 @@ struct FinBar {
   __device__ void operator()() const { fin_bar(); }
 };
 
+// The eigenvalues of the D x D covariance S (float64, row-major in shared
+// memory; Sf its float32 copy) as float64 Rayleigh quotients of float32
+// eigenvector estimates (tridiag.cuh), sorted descending, then the tail rule:
+// sigma_est and the eigenvalues into the context's scalars.  Threads
+// 0..kFinThreads-1 of the block.
+template <int D>
+__device__ void eig_tail(const double* __restrict__ S, const float* __restrict__ Sf, DevScalars* __restrict__ sc,
+                         double* __restrict__ sigma_out) {
+  static_assert(D <= 32, "warp 0 holds one eigenvalue a lane");
+  __shared__ float V[D * D];  // eigenvector estimates (columns)
+  __shared__ float s_mu[D];   // their float32 eigenvalues (the fallback of a non-finite quotient)
+  __shared__ TridiagSmem<D, kFinThreads> tw;
+  __shared__ long long s_key[D];
+  __shared__ double s_sorted[D];
+  __shared__ double s_num[D][D];
+  __shared__ double V64[D][D + 1];
+  const int tid = threadIdx.x;
+
+  // float32 eigenvector estimates: Householder tridiagonalisation, Sturm
+  // multisection and inverse iteration (tridiag.cuh)
+  eig_vectors_f32<D, kFinThreads>(Sf, tw, V, s_mu, FinBar{});
+
+  // float64 Rayleigh quotients of the eigenvector estimates.  float64 has a
+  // long latency here, so the sums run as three interleaved chains.
+  for (int e = tid; e < D * D; e += kFinThreads) V64[e / D][e % D] = double(V[e]);
+  fin_bar();
+  for (int e = tid; e < D * D; e += kFinThreads) {
+    const int k = e / D, r = e % D;
+    double w0 = 0.0, w1 = 0.0, w2 = 0.0;
+#pragma unroll
+    for (int c = 0; c < D; c += 3) {
+      w0 = fma(S[r * D + c], V64[c][k], w0);
+      if (c + 1 < D) w1 = fma(S[r * D + c + 1], V64[c + 1][k], w1);
+      if (c + 2 < D) w2 = fma(S[r * D + c + 2], V64[c + 2][k], w2);
+    }
+    s_num[k][r] = (w0 + w1 + w2) * V64[r][k];
+  }
+  fin_bar();
+  // the rest runs in warp 0, lane j < D holding eigenvalue j
+  if (tid < 32) {
+    constexpr unsigned kFull = 0xffffffffu;
+    const int lane = tid;
+    double lam = 0.0;
+    if (lane < D) {
+      double n0 = 0.0, n1 = 0.0, n2 = 0.0, d0 = 0.0, d1 = 0.0, d2 = 0.0;
+#pragma unroll
+      for (int r = 0; r < D; r += 3) {
+        n0 += s_num[lane][r];
+        d0 = fma(V64[r][lane], V64[r][lane], d0);
+        if (r + 1 < D) {
+          n1 += s_num[lane][r + 1];
+          d1 = fma(V64[r + 1][lane], V64[r + 1][lane], d1);
+        }
+        if (r + 2 < D) {
+          n2 += s_num[lane][r + 2];
+          d2 = fma(V64[r + 2][lane], V64[r + 2][lane], d2);
+        }
+      }
+      lam = div_newton(n0 + n1 + n2, d0 + d1 + d2);
+      if (!isfinite(lam)) lam = double(s_mu[lane]);
+    }
+    // eigenvalues below 1e-9 max(lambda_1, 1) are numerical zeros (a rank-deficient
+    // covariance); they are set to exactly 0 so the tail rule never decides on rounding noise
+    double top = lane < D ? lam : -1.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) top = fmax(top, __shfl_xor_sync(kFull, top, o));
+    if (lane < D && fabs(lam) < kZeroEigRel * fmax(top, 1.0)) lam = 0.0;
+    // descending order (ties by index), by counting the larger values
+    // (float64 compares are slow here: the values are compared through
+    // order-preserving 64-bit integer keys of their bit patterns)
+    if (lane < D) s_key[lane] = order_key(lam);
+    __syncwarp();
+    if (lane < D) {
+      const long long mine = order_key(lam);
+      int rank = 0;
+#pragma unroll
+      for (int j = 0; j < D; ++j) {
+        const long long o = s_key[j];
+        rank += (o > mine) || (o == mine && j < lane);
+      }
+      s_sorted[rank] = lam;
+    }
+    __syncwarp();
+    const double sorted = lane < D ? s_sorted[lane] : 0.0;
+    if (lane < D) sc->eig[lane] = sorted;
+    // tail sums lambda_j + ... + lambda_D by a suffix scan (a tail of exact
+    // zeros sums to exactly 0 in any order)
+    double suffix = sorted;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const double t = __shfl_down_sync(kFull, suffix, o);
+      if (lane + o < D) suffix += t;
+    }
+    // tail rule, every m tested at once: the smallest m with
+    // mean(lambda_{m+1..D}) <= median(lambda_{m+1..D}), tested as
+    // sum <= median * count; m = D - 1 always passes
+    bool pass = false;
+    if (lane < D) {
+      const int cnt = D - lane;
+      const double med = (cnt & 1) ? s_sorted[lane + cnt / 2]
+                                   : 0.5 * (s_sorted[lane + cnt / 2 - 1] + s_sorted[lane + cnt / 2]);
+      pass = suffix <= med * double(cnt);
+    }
+    const int m = __ffs(__ballot_sync(kFull, pass)) - 1;
+    const double tail = __shfl_sync(kFull, suffix, m);
+    if (lane == 0) {
+      const double tau = div_newton(tail, double(D - m));
+      const double sg = sqrt(fmax(tau, 0.0));
+      sc->m = m;
+      sc->tau = tau;
+      sc->sigma_est = sg;
+      sc->ne_valid = 1;
+      if (sigma_out) *sigma_out = sg;
+      __threadfence();
+      atomicExch(&sc->sigma_ready, 1u);
+    }
+  }
+}
+
 // sigma_est from the patch moments, by the first kFinThreads threads of one
 // block (its barriers count those threads only, so the rest of a larger block
-// may leave at once)
+// may leave at once).  With sc->pooled_patch, the per-channel patches of
+// D = 7 pooled over the channels (a reading of Section 2.3), built from the
+// same sums: channel c's sums are the entries 3i + c of the RGB moments.
 __device__ __noinline__ void finalize_block(int dtype, const double* __restrict__ f64_partials, int nblocks,
                                             DevScalars* __restrict__ sc, double* __restrict__ sigma_out) {
-  __shared__ double S[kD][kD];
-  __shared__ float Sf[kD][kD];  // Sigma rounded to float32 once, for the float32 work
+  __shared__ double S[kD * kD];
+  __shared__ float Sf[kD * kD];  // Sigma rounded to float32 once, for the float32 work
   __shared__ double s_sum[kD * kD + kD + 1];
-  __shared__ float V[kD * kD];  // eigenvector estimates (columns)
-  __shared__ float s_mu[kD];    // their float32 eigenvalues (the fallback of a non-finite quotient)
-  __shared__ TridiagSmem<kD, kFinThreads> tw;
-  __shared__ long long s_key[kD];
-  __shared__ double s_sorted[kD];
-  __shared__ double s_num[kD][kD];
-  __shared__ double V64[kD][kD + 1];
 
   const int tid = threadIdx.x;
   constexpr int kP = kD * kD + kD + 1;
+  constexpr int kT = kD / 3;  // points of a patch: the pooled dimension
   // gather the moments
   double npd;
   if (dtype == 0) {
@@ -569,113 +684,39 @@ __device__ __noinline__ void finalize_block(int dtype, const double* __restrict_
     }
     return;
   }
-  // Sigma = S2/N - mu mu^T (upper triangle accumulated; mirror it)
-  const double inv_n = 1.0 / npd;
-  for (int e = tid; e < kD * kD; e += kFinThreads) {
-    const int r = e / kD, c = e % kD;
-    const int rr = min(r, c), cc = max(r, c);
-    const double mr = s_sum[kD * kD + rr] * inv_n, mc = s_sum[kD * kD + cc] * inv_n;
-    const double v = s_sum[rr * kD + cc] * inv_n - mr * mc;
-    S[r][c] = v;
-    Sf[r][c] = float(v);
+  if (!sc->pooled_patch) {
+    // Sigma = S2/N - mu mu^T (upper triangle accumulated; mirror it)
+    const double inv_n = 1.0 / npd;
+    for (int e = tid; e < kD * kD; e += kFinThreads) {
+      const int r = e / kD, c = e % kD;
+      const int rr = min(r, c), cc = max(r, c);
+      const double mr = s_sum[kD * kD + rr] * inv_n, mc = s_sum[kD * kD + cc] * inv_n;
+      const double v = s_sum[rr * kD + cc] * inv_n - mr * mc;
+      S[e] = v;
+      Sf[e] = float(v);
+    }
+    fin_bar();
+    eig_tail<kD>(S, Sf, sc, sigma_out);
+    return;
+  }
+  // pooled: 3 N samples of kT entries; mu_i = sum_c s1[3i + c] / 3N,
+  // Sigma_ij = sum_c s2[3i + c][3j + c] / 3N - mu_i mu_j
+  const double inv_3n = 1.0 / (3.0 * npd);
+  for (int e = tid; e < kT * kT; e += kFinThreads) {
+    const int i = e / kT, j = e % kT;
+    const int lo = min(i, j), hi = max(i, j);
+    double s2 = 0.0, mi = 0.0, mj = 0.0;
+    for (int c = 0; c < 3; ++c) {
+      s2 += s_sum[(3 * lo + c) * kD + 3 * hi + c];
+      mi += s_sum[kD * kD + 3 * i + c];
+      mj += s_sum[kD * kD + 3 * j + c];
+    }
+    const double v = s2 * inv_3n - (mi * inv_3n) * (mj * inv_3n);
+    S[e] = v;
+    Sf[e] = float(v);
   }
   fin_bar();
-
-  // float32 eigenvector estimates: Householder tridiagonalisation, Sturm
-  // multisection and inverse iteration (tridiag.cuh)
-  eig_vectors_f32<kD, kFinThreads>(&Sf[0][0], tw, V, s_mu, FinBar{});
-
-  // float64 Rayleigh quotients of the 21 eigenvector estimates.  float64 has a
-  // long latency here, so the sums run as three interleaved chains.
-  for (int e = tid; e < kD * kD; e += kFinThreads) V64[e / kD][e % kD] = double(V[e]);
-  fin_bar();
-  for (int e = tid; e < kD * kD; e += kFinThreads) {
-    const int k = e / kD, r = e % kD;
-    double w0 = 0.0, w1 = 0.0, w2 = 0.0;
-#pragma unroll
-    for (int c = 0; c < kD; c += 3) {
-      w0 = fma(S[r][c], V64[c][k], w0);
-      w1 = fma(S[r][c + 1], V64[c + 1][k], w1);
-      w2 = fma(S[r][c + 2], V64[c + 2][k], w2);
-    }
-    s_num[k][r] = (w0 + w1 + w2) * V64[r][k];
-  }
-  fin_bar();
-  // the rest runs in warp 0, lane j < 21 holding eigenvalue j
-  if (tid < 32) {
-    constexpr unsigned kFull = 0xffffffffu;
-    const int lane = tid;
-    double lam = 0.0;
-    if (lane < kD) {
-      double n0 = 0.0, n1 = 0.0, n2 = 0.0, d0 = 0.0, d1 = 0.0, d2 = 0.0;
-#pragma unroll
-      for (int r = 0; r < kD; r += 3) {
-        n0 += s_num[lane][r];
-        n1 += s_num[lane][r + 1];
-        n2 += s_num[lane][r + 2];
-        d0 = fma(V64[r][lane], V64[r][lane], d0);
-        d1 = fma(V64[r + 1][lane], V64[r + 1][lane], d1);
-        d2 = fma(V64[r + 2][lane], V64[r + 2][lane], d2);
-      }
-      lam = div_newton(n0 + n1 + n2, d0 + d1 + d2);
-      if (!isfinite(lam)) lam = double(s_mu[lane]);
-    }
-    // eigenvalues below 1e-9 max(lambda_1, 1) are numerical zeros (a rank-deficient
-    // covariance); they are set to exactly 0 so the tail rule never decides on rounding noise
-    double top = lane < kD ? lam : -1.0;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) top = fmax(top, __shfl_xor_sync(kFull, top, o));
-    if (lane < kD && fabs(lam) < kZeroEigRel * fmax(top, 1.0)) lam = 0.0;
-    // descending order (ties by index), by counting the larger values
-    // (float64 compares are slow here: the values are compared through
-    // order-preserving 64-bit integer keys of their bit patterns)
-    if (lane < kD) s_key[lane] = order_key(lam);
-    __syncwarp();
-    if (lane < kD) {
-      const long long mine = order_key(lam);
-      int rank = 0;
-#pragma unroll
-      for (int j = 0; j < kD; ++j) {
-        const long long o = s_key[j];
-        rank += (o > mine) || (o == mine && j < lane);
-      }
-      s_sorted[rank] = lam;
-    }
-    __syncwarp();
-    const double sorted = lane < kD ? s_sorted[lane] : 0.0;
-    if (lane < kD) sc->eig[lane] = sorted;
-    // tail sums lambda_j + ... + lambda_21 by a suffix scan (a tail of exact
-    // zeros sums to exactly 0 in any order)
-    double suffix = sorted;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const double t = __shfl_down_sync(kFull, suffix, o);
-      if (lane + o < kD) suffix += t;
-    }
-    // tail rule, every m tested at once: the smallest m with
-    // mean(lambda_{m+1..D}) <= median(lambda_{m+1..D}), tested as
-    // sum <= median * count; m = D - 1 always passes
-    bool pass = false;
-    if (lane < kD) {
-      const int cnt = kD - lane;
-      const double med = (cnt & 1) ? s_sorted[lane + cnt / 2]
-                                   : 0.5 * (s_sorted[lane + cnt / 2 - 1] + s_sorted[lane + cnt / 2]);
-      pass = suffix <= med * double(cnt);
-    }
-    const int m = __ffs(__ballot_sync(kFull, pass)) - 1;
-    const double tail = __shfl_sync(kFull, suffix, m);
-    if (lane == 0) {
-      const double tau = div_newton(tail, double(kD - m));
-      const double sg = sqrt(fmax(tau, 0.0));
-      sc->m = m;
-      sc->tau = tau;
-      sc->sigma_est = sg;
-      sc->ne_valid = 1;
-      if (sigma_out) *sigma_out = sg;
-      __threadfence();
-      atomicExch(&sc->sigma_ready, 1u);
-    }
-  }
+  eig_tail<kT>(S, Sf, sc, sigma_out);
 }
 
 __global__ void __launch_bounds__(kFinThreads) k_ne_finalize(int dtype, const double* __restrict__ f64_partials,

@@ -238,6 +238,7 @@ __device__ __forceinline__ void write_out(const FilterArgs& a, int i, float4 x) 
 // x_q of sorted point k, wherever the kept iterate is (kept_buf)
 __device__ __forceinline__ float4 kept_value(const FilterArgs& a, int kept, int k) {
   if (kept < 0) return x0_of(a, k);
+  if (kept == kKeptBest) return __ldcg(&a.xbest[k]);
   if (kept >= 2) return __ldcg(&a.spec_x[size_t(kept - 2) * size_t(a.cap) + k]);
   return __ldcg(&(kept ? a.xbuf1 : a.xbuf0)[k]);
 }
@@ -523,10 +524,15 @@ __device__ __forceinline__ void select_filter(const FilterArgs& a, int S, int fi
   if (!grid_barrier(bar, &sc->status, members, epoch, &s_ok, sc)) return;
 
   // J(0..S) from the stored terms, by thread 0 of each block (every block
-  // reaches the same values: the sums are exact integers)
-  __shared__ int s_ctl[4];  // keep_all, q_limit, q_final, stop
+  // reaches the same values: the sums are exact integers).  Under the global
+  // reading (a.q_global) the search never stops early and q* is the argmin of
+  // J over 0..q_max (the smaller q among equal values); a new best iterate
+  // beyond the stored steps is copied to xbest while the next step reads it.
+  __shared__ int s_ctl[6];  // keep_all, q_limit, q_final, stop, q_best, copy the last iterate
   __shared__ float s_cexp;
-  double sigma = 0.0, nsel = 1.0, J_prev = 0.0;  // thread 0 only
+  const bool global = select && a.q_global;
+  double sigma = 0.0, nsel = 1.0, J_prev = 0.0, J_best = 0.0;  // thread 0 only
+  int q_best = 0;                                               // thread 0 only
   unsigned long long ysq = 0;
   if (threadIdx.x == 0) {
     s_cexp = step_cexp(sc);
@@ -540,6 +546,7 @@ __device__ __forceinline__ void select_filter(const FilterArgs& a, int S, int fi
       nsel = keep_all ? double(n) : double(nkt);
       ysq = keep_all ? ld_relaxed_u64(&sc->ysq_all) : ld_relaxed_u64(&sc->ysq_keep);
       J_prev = sigma * sigma;  // J(0): nothing filtered yet
+      J_best = J_prev;
       if (gtid == 0) sc->J[0] = J_prev;
       for (int t = 1; t <= min(S, q_limit); ++t) {
         const unsigned long long* src = reinterpret_cast<const unsigned long long*>(
@@ -549,6 +556,14 @@ __device__ __forceinline__ void select_filter(const FilterArgs& a, int S, int fi
         if (gtid == 0) {
           sc->J[t] = J;
           sc->n_J = t + 1;
+        }
+        if (global) {
+          if (J < J_best) {
+            J_best = J;
+            q_best = t;
+          }
+          q_final = t;
+          continue;
         }
         if (J >= J_prev) {
           q_final = t - 1;
@@ -563,6 +578,8 @@ __device__ __forceinline__ void select_filter(const FilterArgs& a, int S, int fi
     s_ctl[1] = q_limit;
     s_ctl[2] = q_final;
     s_ctl[3] = stopped;
+    s_ctl[4] = q_best;
+    s_ctl[5] = 0;
   }
   __syncthreads();
   const float cexp = s_cexp;
@@ -570,6 +587,7 @@ __device__ __forceinline__ void select_filter(const FilterArgs& a, int S, int fi
   const int q_limit = s_ctl[1];
   int q_final = s_ctl[2];
   const bool stopped = s_ctl[3] != 0;
+  bool copy_best = false;  // this step's source is the best iterate so far: copy it to xbest
   for (int t = S + 1; t <= q_limit && !stopped; ++t) {
     const float4* __restrict__ src =
         (S > 0 && t == S + 1) ? a.spec_x + size_t(S - 1) * size_t(a.cap) : ((t & 1) ? a.xbuf0 : a.xbuf1);
@@ -578,6 +596,7 @@ __device__ __forceinline__ void select_filter(const FilterArgs& a, int S, int fi
     for (int k = gtid; k < n; k += gstride) {
       const float4 xo = eq5_step_nx<NX>(a, src, k, n, cexp);
       dst[k] = xo;
+      if (copy_best) a.xbest[k] = __ldcg(&src[k]);
       if (select && (keep_all || __ldcg(a.keep8 + k))) loc += sq3(xo);
     }
     if (select) {
@@ -595,8 +614,19 @@ __device__ __forceinline__ void select_filter(const FilterArgs& a, int S, int fi
           sc->J[t] = J;
           sc->n_J = t + 1;
         }
-        s_ctl[3] = J >= J_prev;
-        if (!(J >= J_prev)) J_prev = J;
+        if (global) {
+          const bool better = J < J_best;
+          if (better) {
+            J_best = J;
+            q_best = t;
+          }
+          s_ctl[3] = 0;
+          s_ctl[4] = q_best;
+          s_ctl[5] = better;
+        } else {
+          s_ctl[3] = J >= J_prev;
+          if (!(J >= J_prev)) J_prev = J;
+        }
       }
       __syncthreads();
       if (s_ctl[3]) {
@@ -604,12 +634,21 @@ __device__ __forceinline__ void select_filter(const FilterArgs& a, int S, int fi
         break;
       }
       q_final = t;
+      copy_best = s_ctl[5] != 0;
     } else {
       q_final = t;
     }
   }
   // where the kept iterate is
-  const int kept = (S > 0 && q_final <= S) ? (q_final == 0 ? -1 : 2 + q_final - 1) : (q_final & 1);
+  int kept = (S > 0 && q_final <= S) ? (q_final == 0 ? -1 : 2 + q_final - 1) : (q_final & 1);
+  if (global) {
+    const int qb = s_ctl[4];
+    if (qb == 0) kept = -1;
+    else if (qb <= S) kept = 2 + qb - 1;
+    else if (qb == q_final) kept = qb & 1;  // the last step: still in its buffer
+    else kept = kKeptBest;                  // copied while step qb + 1 read it
+    q_final = qb;
+  }
   if (gtid == 0) {
     if (!a.q_src) sc->q_sel = q_final;
     sc->kept_buf = kept;

@@ -878,6 +878,41 @@ __global__ void __launch_bounds__(256) k_link_wide(int n, int bits, int cap, int
   }
 }
 
+// Each sorted point's mean edge length (its neighbours from every slot), for
+// the node and pair readings of sigma_g: written to node_sig (if set), and its
+// fixed-point sum over the points that have edges, with their count, added to
+// the build scalars.
+__global__ void __launch_bounds__(256) k_node_sigma(int n, int bits, GraphBufs gb, DevScalars* __restrict__ sc) {
+  pdl_wait();
+  __shared__ unsigned long long s_red[8];
+  unsigned long long sum = 0, cnt = 0;
+  const int slots = 6 + gb.nx;
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+    const uint32_t pkw = gb.pk[k];
+    const int4 s4 = gb.c4[k];
+    float len = 0.f;
+    int deg = 0;
+    for (int j = 0; j < slots; ++j) {
+      const int o = neighbour_of(j, k, n, pkw, s4, gb.cx, gb.cx_stride);
+      if (o < 0) continue;
+      len += sqrtf(float(sq_dist_c1(pkw, gb.pk[o], bits)));
+      deg += 1;
+    }
+    const float mean = deg ? len / float(deg) : 0.f;
+    if (gb.node_sig) gb.node_sig[k] = mean;
+    if (deg) {
+      sum += __float2ull_rn(mean * float(1u << kDistShift));
+      cnt += 1;
+    }
+  }
+  sum = block_sum_u64<256>(sum, s_red);
+  cnt = block_sum_u64<256>(cnt, s_red);
+  if (threadIdx.x == 0) {
+    if (sum) atomicAdd(&sc->node_fx, sum);
+    if (cnt) atomicAdd(&sc->node_cnt, cnt);
+  }
+}
+
 // The three orders in input indices: C1 from perm1, C2 and C3 through perm1.
 __global__ void __launch_bounds__(256) k_orders_export(int n, int cap, const int32_t* __restrict__ perm1,
                                                        const int32_t* __restrict__ ord23, int32_t* __restrict__ out) {
@@ -1072,6 +1107,12 @@ cudaError_t launch_link_wide(int n, int bits, int cap, int window, bool same_lin
   if (e != cudaSuccess || !same_line) return e;
   return launch_kernel(k_c1_line_flags, dim3(std::min((n + 255) / 256, num_sms * 8)), dim3(256), 0, stream, false, n,
                        bits, gb.pk);
+}
+
+cudaError_t launch_node_sigma(int n, int bits, const GraphBufs& gb, DevScalars* sc, int num_sms, cudaStream_t stream) {
+  if (n <= 0) return cudaSuccess;
+  const int grid = std::max(1, std::min((n + 255) / 256, num_sms * 8));
+  return launch_kernel(k_node_sigma, dim3(grid), dim3(256), 0, stream, false, n, bits, gb, sc);
 }
 
 cudaError_t launch_orders_export(int n, int cap, const GraphBufs& gb, int32_t* out, cudaStream_t stream) {

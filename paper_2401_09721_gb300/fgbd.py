@@ -62,6 +62,10 @@ class Params(ctypes.Structure):
 VARIANT_NO_FSLR = 1          # FGBD_VARIANT_NO_FSLR
 VARIANT_UNSORTED_PATCH = 2   # FGBD_VARIANT_UNSORTED_PATCH
 VARIANT_SAME_LINE = 4        # FGBD_VARIANT_SAME_LINE
+VARIANT_SIGMA_NODE = 8       # FGBD_VARIANT_SIGMA_NODE
+VARIANT_SIGMA_PAIR = 16      # FGBD_VARIANT_SIGMA_PAIR
+VARIANT_POOLED_PATCH = 32    # FGBD_VARIANT_POOLED_PATCH
+VARIANT_GLOBAL_Q = 64        # FGBD_VARIANT_GLOBAL_Q
 FLAG_FUSED_SELECT = 1        # FGBD_FLAG_FUSED_SELECT
 
 

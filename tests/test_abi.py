@@ -71,7 +71,9 @@ def test_host_side_checks_without_gpu(so):
     assert lib.fgbd_ctx_create(100, ctypes.byref(bad), ctypes.byref(out)) == 1
     bad.bits, bad.q_max = 10, 257
     assert lib.fgbd_ctx_create(100, ctypes.byref(bad), ctypes.byref(out)) == 1
-    bad.q_max, bad.variant = 64, 8                                          # no such ablation switch
+    bad.q_max, bad.variant = 64, 128                                        # no such ablation switch
+    assert lib.fgbd_ctx_create(100, ctypes.byref(bad), ctypes.byref(out)) == 1
+    bad.variant = fgbd.VARIANT_SIGMA_NODE | fgbd.VARIANT_SIGMA_PAIR         # two readings of one quantity
     assert lib.fgbd_ctx_create(100, ctypes.byref(bad), ctypes.byref(out)) == 1
     bad.variant, bad.reserved[0] = 0, 1                                     # reserved must stay zero
     assert lib.fgbd_ctx_create(100, ctypes.byref(bad), ctypes.byref(out)) == 1
@@ -83,6 +85,9 @@ def test_host_side_checks_without_gpu(so):
     assert lib.fgbd_ctx_create(100, ctypes.byref(bad), ctypes.byref(out)) == 7
     bad.window, bad.variant = 2, fgbd.VARIANT_UNSORTED_PATCH                # link order defined at w = 1 only
     assert lib.fgbd_ctx_create(100, ctypes.byref(bad), ctypes.byref(out)) == 7
+    for v in (fgbd.VARIANT_SIGMA_PAIR, fgbd.VARIANT_POOLED_PATCH):           # built for window 1 only
+        bad.variant = v
+        assert lib.fgbd_ctx_create(100, ctypes.byref(bad), ctypes.byref(out)) == 7
     assert (fgbd.MAX_WINDOW, fgbd.PATCH_DIM_MAX) == (3, 57)
     assert p.flags == 0 and fgbd.FLAG_FUSED_SELECT == 1
     assert p.variant == 0 and fgbd.VARIANT_NO_FSLR == 1 and fgbd.VARIANT_UNSORTED_PATCH == 2
