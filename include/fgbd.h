@@ -371,6 +371,15 @@ fgbd_status fgbd_filter_backward(fgbd_ctx* ctx, const float* grad_out, float* gr
  * Errors: FGBD_EINVAL (ns < 0), FGBD_ECUDA. */
 fgbd_status fgbd_debug_set_wait_limit(fgbd_ctx* ctx, int64_t ns);
 
+/* Testing (not part of the method): q_newton[i] = a[i] / b[i] by the float64
+ * quotient the eigen step of the noise estimate uses (a float32 reciprocal
+ * refined by Newton steps, Section 2.3's tail mean and Rayleigh quotients),
+ * and q_div[i] by CUDA's own division, for n pairs (device arrays of double,
+ * on the current device).  Enqueues on `stream`.  Errors: FGBD_EINVAL,
+ * FGBD_ECUDA. */
+fgbd_status fgbd_debug_div(const double* a, const double* b, double* q_newton, double* q_div, int64_t n,
+                           void* stream);
+
 /* Wait for the context's work on `stream` (and for the output copies of
  * fgbd_run_host) and return any latched device error (FGBD_ERANGE,
  * FGBD_ETIMEOUT), clearing it. */

@@ -1474,6 +1474,17 @@ fgbd_status fgbd_debug_set_wait_limit(fgbd_ctx* ctx, int64_t ns) {
   return FGBD_OK;
 }
 
+fgbd_status fgbd_debug_div(const double* a, const double* b, double* q_newton, double* q_div, int64_t n,
+                           void* stream) {
+  if (n < 0 || (n > 0 && (!a || !b || !q_newton || !q_div))) return FGBD_EINVAL;
+  const cudaError_t e = launch_debug_div(a, b, q_newton, q_div, n, as_stream(stream));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return FGBD_ECUDA;
+  }
+  return FGBD_OK;
+}
+
 fgbd_status fgbd_sync(fgbd_ctx* ctx, void* stream) {
   if (!ctx) return FGBD_EINVAL;
   DeviceGuard g(ctx->device);

@@ -312,6 +312,9 @@ cudaError_t launch_ne_finalize(int dtype, const double* f64_partials, int nblock
                                DevScalars* sc, double* sigma_out, const FilterArgs* spec, int num_sms,
                                cudaStream_t stream);
 int ne_moment_blocks(int n, int num_sms);
+// testing: div_newton and CUDA's division of n operand pairs
+cudaError_t launch_debug_div(const double* a, const double* b, double* q_newton, double* q_div, int64_t n,
+                             cudaStream_t stream);
 MomentArgs moment_args(int n, int bits, const GraphBufs& gb, const uint32_t* y8, const float4* yf, float* spread,
                        double* f64_partials, bool moments, bool sorted_patches, DevScalars* sc);
 // segmented: frames 0..count-1 (count <= kSegMax; one colour dtype for the moments)

@@ -798,7 +798,24 @@ __global__ void __launch_bounds__(kSpecThreads, 1) k_ne_finalize_spec_seg(const 
                     false, epoch, &s_ok, &s_cexp, &s_go);
 }
 
+// testing: the float64 quotient of the eigen step beside CUDA's own division
+__global__ void __launch_bounds__(256) k_debug_div(const double* __restrict__ a, const double* __restrict__ b,
+                                                   double* __restrict__ q_newton, double* __restrict__ q_div,
+                                                   int64_t n) {
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
+    q_newton[i] = div_newton(a[i], b[i]);
+    q_div[i] = a[i] / b[i];
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_debug_div(const double* a, const double* b, double* q_newton, double* q_div, int64_t n,
+                             cudaStream_t stream) {
+  if (n <= 0) return cudaSuccess;
+  const int grid = int(std::min<int64_t>((n + 255) / 256, 152 * 8));
+  return launch_kernel(k_debug_div, dim3(grid), dim3(256), 0, stream, false, a, b, q_newton, q_div, n);
+}
 
 cudaError_t launch_gather_colors_seg(const GatherArgs* a, int count, cudaStream_t stream) {
   if (count < 1 || count > kSegMax) return cudaErrorInvalidValue;

@@ -132,6 +132,7 @@ _SIGS = {
     "fgbd_run_reuse": (ctypes.c_int, [_P, _P, ctypes.c_int64, _P, ctypes.c_int32, _P, ctypes.c_int32, _P]),
     "fgbd_run_host": (ctypes.c_int, [_P, _P, ctypes.c_int64, _P, ctypes.c_int32, _P, ctypes.c_int32, _P]),
     "fgbd_debug_set_wait_limit": (ctypes.c_int, [_P, ctypes.c_int64]),
+    "fgbd_debug_div": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int64, _P]),
     "fgbd_run_batch": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(ctypes.c_int64),
                                       ctypes.POINTER(_P), ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(_P),
                                       ctypes.POINTER(ctypes.c_int32), ctypes.c_int32, _P]),
@@ -644,3 +645,13 @@ class Context:
 
     def timings(self) -> list:
         return fgbd_get_timings(self.handle)
+
+
+def fgbd_debug_div(a: torch.Tensor, b: torch.Tensor, stream=None):
+    """(div_newton(a, b), CUDA's a / b) elementwise on CUDA float64 tensors (testing)."""
+    if a.dtype != torch.float64 or b.dtype != torch.float64 or a.shape != b.shape or not (a.is_cuda and b.is_cuda):
+        raise TypeError("two CUDA float64 tensors of one shape")
+    a, b = a.contiguous(), b.contiguous()
+    qn, qd = torch.empty_like(a), torch.empty_like(a)
+    _check(lib().fgbd_debug_div(_ptr(a), _ptr(b), _ptr(qn), _ptr(qd), a.numel(), _stream(stream)), "fgbd_debug_div")
+    return qn, qd
