@@ -41,6 +41,8 @@ struct fgbd_ctx {
   float4* x0 = nullptr;
   float4* x1 = nullptr;
   float4* xbest = nullptr;  // the global reading of the q search: the best iterate (else null)
+  float4* w4 = nullptr;     // window 1: normalised Eq. 4 weights of the slots (FilterArgs::w4, w2)
+  float2* w2 = nullptr;
   double* f64part = nullptr;
   int f64_blocks = 0;
   WideNe wne{};  // noise-estimate scratch of windows w > 1 (unused at window 1)
@@ -278,6 +280,8 @@ FilterArgs filter_args(fgbd_ctx* ctx, int mode, int q_fixed, const double* sigma
   a.node_sig = (ctx->params.variant & FGBD_VARIANT_SIGMA_PAIR) ? ctx->gb.node_sig : nullptr;
   a.q_global = (ctx->params.variant & FGBD_VARIANT_GLOBAL_Q) ? 1 : 0;
   a.xbest = ctx->xbest;
+  a.w4 = ctx->w4;
+  a.w2 = ctx->w2;
   return a;
 }
 
@@ -917,6 +921,8 @@ fgbd_status fgbd_ctx_create(int64_t capacity, const fgbd_params* params, fgbd_ct
       {reinterpret_cast<void**>(&ctx->gb.cx), size_t(nx) * align_up(C, 64) * 4},
       {reinterpret_cast<void**>(&ctx->gb.node_sig), (p.variant & FGBD_VARIANT_SIGMA_PAIR) ? C * 4 : 0},
       {reinterpret_cast<void**>(&ctx->xbest), (p.variant & FGBD_VARIANT_GLOBAL_Q) ? C * 16 : 0},
+      {reinterpret_cast<void**>(&ctx->w4), wide ? 0 : C * 16},
+      {reinterpret_cast<void**>(&ctx->w2), wide ? 0 : C * 8},
       {reinterpret_cast<void**>(&ctx->wne.part), wide ? size_t(w_blocks) * wP * 8 : 0},
       {reinterpret_cast<void**>(&ctx->wne.tot), wide ? wP * 8 : 0},
       {reinterpret_cast<void**>(&ctx->wne.S), wide ? wD * wD * 8 : 0},
@@ -947,6 +953,10 @@ fgbd_status fgbd_ctx_create(int64_t capacity, const fgbd_params* params, fgbd_ct
   ctx->gb.cx_stride = int(align_up(C, 64));
   if (!(p.variant & FGBD_VARIANT_SIGMA_PAIR)) ctx->gb.node_sig = nullptr;
   if (!(p.variant & FGBD_VARIANT_GLOBAL_Q)) ctx->xbest = nullptr;
+  if (wide) {
+    ctx->w4 = nullptr;
+    ctx->w2 = nullptr;
+  }
   if (!wide) {
     ctx->gb.cx = nullptr;
     ctx->wne = WideNe{};

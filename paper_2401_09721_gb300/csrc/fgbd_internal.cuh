@@ -383,6 +383,11 @@ struct FilterArgs {
   // iterate beyond the stored steps is copied to xbest
   int q_global;
   float4* xbest;
+  // window 1: the Eq. 4 weights of each sorted point's six slots, normalised by
+  // their sum (slots C1 prev, C1 next, C2 prev, C2 next in w4; C3 prev, next in
+  // w2), written by step 1 and read by every later step of the same graph
+  float4* w4;
+  float2* w2;
 };
 constexpr int kKeptBest = 64;  // kept_buf value of the iterate copied to xbest
 cudaError_t launch_filter(const FilterArgs& a, int grid, cudaStream_t stream);

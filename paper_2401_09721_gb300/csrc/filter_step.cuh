@@ -92,23 +92,25 @@ __device__ __forceinline__ float block_cexp(const DevScalars* sc, float* s_cexp)
   return *s_cexp;
 }
 
-// One Eq. 5 step at sorted point k: x_k / 2 + (sum_j e_j x_j) / (2 sum_j e_j)
-// over the neighbours (C1 k - 1, k + 1, the C2/C3 slots) with
-// e_j = exp(-(d2_j - min d2) / sigma_g^2), from the previous iterate `src` (x_0
-// built from the colours when src is null).  Every kernel that takes a step
-// uses this function, so a step gives the same bits in all of them.
-__device__ __forceinline__ float4 eq5_step(const FilterArgs& a, const float4* __restrict__ src, int k, int n,
-                                           float cexp) {
-  const float4 xk = src ? __ldcg(&src[k]) : x0_of(a, k);
-  const uint32_t wk = __float_as_uint(xk.w);  // packed code and the missing-C1-link bits
-  const uint32_t ck = wk & kCoordMask;
-  int nb[6];
-  bool v[6];
+// What a step at sorted point k reads before its neighbours: the point's own
+// previous iterate (x_0 built from the colours when src is null) and its C2/C3
+// slots.
+struct StepHead {
+  float4 xk;
+  int4 s;
+};
+
+__device__ __forceinline__ StepHead step_head(const FilterArgs& a, const float4* __restrict__ src, int k) {
+  return {src ? __ldcg(&src[k]) : x0_of(a, k), a.c4[k]};
+}
+
+// The six window-1 slots of sorted point k (C1 k - 1, k + 1, then the C2/C3
+// slots of c4) and whether each holds a neighbour.
+__device__ __forceinline__ void slots6(int k, int n, uint32_t wk, int4 s, int (&nb)[6], bool (&v)[6]) {
   nb[0] = k - 1;
   v[0] = c1_prev_linked(wk, k);
   nb[1] = k + 1;
   v[1] = c1_next_linked(wk, k, n);
-  const int4 s = a.c4[k];
   nb[2] = s.x;
   nb[3] = s.y;
   nb[4] = s.z;
@@ -117,58 +119,101 @@ __device__ __forceinline__ float4 eq5_step(const FilterArgs& a, const float4* __
   v[3] = in_range(s.y, n);
   v[4] = in_range(s.z, n);
   v[5] = in_range(s.w, n);
+}
+
+// One Eq. 5 step at sorted point k: x_k / 2 + (sum_j w_j x_j) / 2 over the
+// neighbours (C1 k - 1, k + 1, the C2/C3 slots), with the weights of Eq. 4
+// normalised by their sum, w_j = e_j / sum_i e_i, e_j = exp(-(d2_j - min d2) /
+// sigma_g^2) (the pair reading: d2_j / (sigma_k sigma_j) in the exponent), from
+// the previous iterate `src` (x_0 built from the colours when src is null;
+// h = step_head(a, src, k)).  A point without neighbours keeps x_k.
+// The weights depend on the graph and sigma_g only, so they are computed once:
+// kStore (step 1) computes them and, where a.w4 is set, stores them; the later
+// steps of the same graph load them (kStore false with a.w4 set).  Every kernel
+// that takes a window-1 step uses this function, so a step gives the same bits
+// in all of them.
+template <bool kStore>
+__device__ __forceinline__ float4 eq5_step(const FilterArgs& a, const float4* __restrict__ src, int k, int n,
+                                           float cexp, const StepHead& h) {
+  const float4 xk = h.xk;
+  const uint32_t wk = __float_as_uint(xk.w);  // packed code and the missing-C1-link bits
+  int nb[6];
+  bool v[6];
+  slots6(k, n, wk, h.s, nb, v);
   float4 xn[6];
-  int d2[6];
-  int dmin = INT_MAX;
 #pragma unroll
-  for (int j = 0; j < 6; ++j) {
-    xn[j] = v[j] ? (src ? __ldcg(&src[nb[j]]) : x0_of(a, nb[j])) : xk;
-    d2[j] = v[j] ? sq_dist_c1(ck, __float_as_uint(xn[j].w) & kCoordMask, a.bits) : INT_MAX;
-    dmin = min(dmin, d2[j]);
-  }
-  float se = 0.f, sr = 0.f, sgc = 0.f, sb = 0.f;
-  if (a.node_sig) {
-    // the pair reading: exponents d2_j / (sigma_k sigma_j), shifted by their minimum
-    const float sk = __ldg(&a.node_sig[k]);
-    float ex[6];
-    float emin = 3.0e38f;
+  for (int j = 0; j < 6; ++j) xn[j] = v[j] ? (src ? __ldcg(&src[nb[j]]) : x0_of(a, nb[j])) : xk;
+  float w[6];
+  if (kStore || !a.w4) {
+    const uint32_t ck = wk & kCoordMask;
+    int d2[6];
+    int dmin = INT_MAX;
 #pragma unroll
     for (int j = 0; j < 6; ++j) {
-      ex[j] = 0.f;
-      if (v[j]) {
-        const float s = sk * __ldg(&a.node_sig[nb[j]]);
-        ex[j] = s > 0.f ? float(d2[j]) / s : 0.f;
-        emin = fminf(emin, ex[j]);
+      d2[j] = v[j] ? sq_dist_c1(ck, __float_as_uint(xn[j].w) & kCoordMask, a.bits) : INT_MAX;
+      dmin = min(dmin, d2[j]);
+    }
+    float se = 0.f;
+    if (a.node_sig) {
+      // the pair reading: exponents d2_j / (sigma_k sigma_j), shifted by their minimum
+      const float sk = __ldg(&a.node_sig[k]);
+      float ex[6];
+      float emin = 3.0e38f;
+#pragma unroll
+      for (int j = 0; j < 6; ++j) {
+        ex[j] = 0.f;
+        if (v[j]) {
+          const float s = sk * __ldg(&a.node_sig[nb[j]]);
+          ex[j] = s > 0.f ? float(d2[j]) / s : 0.f;
+          emin = fminf(emin, ex[j]);
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < 6; ++j) {
+        w[j] = v[j] ? exp2f((emin - ex[j]) * 1.4426950408889634f) : 0.f;
+        se += w[j];
+      }
+    } else {
+#pragma unroll
+      for (int j = 0; j < 6; ++j) {
+        w[j] = v[j] ? exp2f(float(dmin - d2[j]) * cexp) : 0.f;
+        se += w[j];
       }
     }
+    // se >= 1 when a slot is linked (its nearest neighbour has e = 1)
+    const float inv = se > 0.f ? 1.f / se : 0.f;
 #pragma unroll
-    for (int j = 0; j < 6; ++j) {
-      if (v[j]) {
-        const float e = exp2f((emin - ex[j]) * 1.4426950408889634f);
-        se += e;
-        sr = fmaf(e, xn[j].x, sr);
-        sgc = fmaf(e, xn[j].y, sgc);
-        sb = fmaf(e, xn[j].z, sb);
-      }
+    for (int j = 0; j < 6; ++j) w[j] *= inv;
+    if (kStore && a.w4) {
+      a.w4[k] = make_float4(w[0], w[1], w[2], w[3]);
+      a.w2[k] = make_float2(w[4], w[5]);
     }
   } else {
+    const float4 wa = __ldcg(&a.w4[k]);
+    const float2 wb = __ldcg(&a.w2[k]);
+    w[0] = wa.x;
+    w[1] = wa.y;
+    w[2] = wa.z;
+    w[3] = wa.w;
+    w[4] = wb.x;
+    w[5] = wb.y;
+  }
+  float sr = 0.f, sgc = 0.f, sb = 0.f;
+  bool any = false;
 #pragma unroll
-    for (int j = 0; j < 6; ++j) {
-      if (v[j]) {
-        const float e = exp2f(float(dmin - d2[j]) * cexp);
-        se += e;
-        sr = fmaf(e, xn[j].x, sr);
-        sgc = fmaf(e, xn[j].y, sgc);
-        sb = fmaf(e, xn[j].z, sb);
-      }
+  for (int j = 0; j < 6; ++j) {
+    if (v[j]) {
+      sr = fmaf(w[j], xn[j].x, sr);
+      sgc = fmaf(w[j], xn[j].y, sgc);
+      sb = fmaf(w[j], xn[j].z, sb);
+      any = true;
     }
   }
   float4 xo = xk;
-  if (se > 0.f) {
-    const float inv = 1.f / se;
-    xo.x = 0.5f * xk.x + 0.5f * (sr * inv);
-    xo.y = 0.5f * xk.y + 0.5f * (sgc * inv);
-    xo.z = 0.5f * xk.z + 0.5f * (sb * inv);
+  if (any) {
+    xo.x = 0.5f * xk.x + 0.5f * sr;
+    xo.y = 0.5f * xk.y + 0.5f * sgc;
+    xo.z = 0.5f * xk.z + 0.5f * sb;
   }
   return xo;
 }
@@ -195,11 +240,11 @@ __device__ __forceinline__ void slot_group(const FilterArgs& a, int k, int n, ui
 // accumulates.
 template <int NX>
 __device__ __forceinline__ float4 eq5_step_wide(const FilterArgs& a, const float4* __restrict__ src, int k, int n,
-                                                float cexp) {
-  const float4 xk = src ? __ldcg(&src[k]) : x0_of(a, k);
+                                                float cexp, const StepHead& h) {
+  const float4 xk = h.xk;
   const uint32_t wk = __float_as_uint(xk.w);
   const uint32_t ck = wk & kCoordMask;
-  const int4 s = a.c4[k];
+  const int4 s = h.s;
   int dmin = INT_MAX;
 #pragma unroll 1
   for (int g = 0; g <= NX / 6; ++g) {
@@ -243,11 +288,11 @@ __device__ __forceinline__ float4 eq5_step_wide(const FilterArgs& a, const float
 }
 
 // one Eq. 5 step at window 1 (NX = 0) or wider
-template <int NX>
+template <int NX, bool kStore>
 __device__ __forceinline__ float4 eq5_step_nx(const FilterArgs& a, const float4* __restrict__ src, int k, int n,
-                                              float cexp) {
-  if constexpr (NX == 0) return eq5_step(a, src, k, n, cexp);
-  else return eq5_step_wide<NX>(a, src, k, n, cexp);
+                                              float cexp, const StepHead& h) {
+  if constexpr (NX == 0) return eq5_step<kStore>(a, src, k, n, cexp, h);
+  else return eq5_step_wide<NX>(a, src, k, n, cexp, h);
 }
 
 // The first steps x_1, x_2, ... and each point's Eq. 6 term sum_c (y^2 - x_q^2)
@@ -272,9 +317,10 @@ __device__ __forceinline__ int speculative_steps(const FilterArgs& a, int depth,
     float4* dst = a.spec_x + size_t(t - 1) * size_t(a.cap);
     int32_t* z = a.spec_z + size_t(t - 1) * size_t(a.cap);
     for (int k = gtid; k < n; k += gstride) {
-      const float4 xo = eq5_step(a, src, k, n, cexp);
+      const StepHead h = step_head(a, src, k);
+      const float4 xo = t == 1 ? eq5_step<true>(a, src, k, n, cexp, h) : eq5_step<false>(a, src, k, n, cexp, h);
       dst[k] = xo;
-      z[k] = int32_t((long long)sq3(x0_of(a, k)) - (long long)sq3(xo));
+      z[k] = int32_t((long long)sq3(src ? x0_of(a, k) : h.xk) - (long long)sq3(xo));
     }
     const bool ask = until_sigma && t < depth;
     if (ask && blockIdx.x == first && threadIdx.x == 0) sc->spec_go[t] = ld_acquire_u32(&sc->sigma_ready) ? 0u : 1u;

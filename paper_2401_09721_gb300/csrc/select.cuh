@@ -594,9 +594,11 @@ __device__ __forceinline__ void select_filter(const FilterArgs& a, int S, int fi
     float4* __restrict__ dst = (t & 1) ? a.xbuf1 : a.xbuf0;
     unsigned long long loc = 0;
     for (int k = gtid; k < n; k += gstride) {
-      const float4 xo = eq5_step_nx<NX>(a, src, k, n, cexp);
+      const StepHead h = step_head(a, src, k);
+      const float4 xo =
+          t == 1 ? eq5_step_nx<NX, true>(a, src, k, n, cexp, h) : eq5_step_nx<NX, false>(a, src, k, n, cexp, h);
       dst[k] = xo;
-      if (copy_best) a.xbest[k] = __ldcg(&src[k]);
+      if (copy_best) a.xbest[k] = h.xk;
       if (select && (keep_all || __ldcg(a.keep8 + k))) loc += sq3(xo);
     }
     if (select) {
