@@ -504,12 +504,14 @@ def algorithmic_bytes(name, n, extra_steps=0.0, out_bytes=3):
         return per_point[name] * n
     if name == "ne_finalize":
         # the filter steps stored by the estimate launch (its eigen block moves no bytes):
-        # per step x in 16 (or y 4 + codes 4), c4 16, x out 16, Eq. 6 term 4, y 4
-        return SPEC_STEPS * 56 * n
+        # per step x in 16 (or y 4 + codes 4), c4 16, the six normalised weights 24
+        # (written by step 1, read by the later steps), x out 16, Eq. 6 term 4, y 4
+        return SPEC_STEPS * 80 * n
     if name == "filter_select":
         # keep flags: y 4, spread 4, keep 1; the stored steps' Eq. 6 terms 4 each and keep 1;
-        # ordinary steps beyond the stored ones 48 each; output: rank 4, x 16, colours out
-        return (9 + 4 * SPEC_STEPS + 1 + 48 * extra_steps + 20 + out_bytes) * n
+        # ordinary steps beyond the stored ones 72 each (x in, c4, weights, x out);
+        # output: rank 4, x 16, colours out
+        return (9 + 4 * SPEC_STEPS + 1 + 72 * extra_steps + 20 + out_bytes) * n
     return 0
 
 

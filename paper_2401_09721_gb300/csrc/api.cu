@@ -962,8 +962,10 @@ fgbd_status fgbd_ctx_create(int64_t capacity, const fgbd_params* params, fgbd_ct
     ctx->wne = WideNe{};
   }
   ctx->wne.blocks = wide ? w_blocks : 0;
-  bool ok = cudaMemset(ctx->sc, 0, sizeof(DevScalars)) == cudaSuccess;
-  if (wide) ok = ok && cudaMemset(ctx->wne.done, 0, 4) == cudaSuccess;
+  // all of it zeroed once: every index array then holds indices inside the
+  // context's buffers even before a build has written it (the kernels bound
+  // every index they write by n <= capacity, so this stays true)
+  bool ok = cudaMemset(ctx->mem, 0, total) == cudaSuccess;
   const unsigned long long limit = kWaitLimitNs;
   ok = ok && cudaMemcpy(&ctx->sc->wait_limit_ns, &limit, sizeof(limit), cudaMemcpyHostToDevice) == cudaSuccess;
   const uint32_t mode = (p.variant & FGBD_VARIANT_SIGMA_NODE) ? kSigmaNode
