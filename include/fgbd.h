@@ -380,6 +380,15 @@ fgbd_status fgbd_debug_set_wait_limit(fgbd_ctx* ctx, int64_t ns);
 fgbd_status fgbd_debug_div(const double* a, const double* b, double* q_newton, double* q_div, int64_t n,
                            void* stream);
 
+/* Testing (not part of the method): the patch moments of the context's last
+ * noise estimate with uint8 colours (Section 2.3), as exact integers over the
+ * patches' entries centred on 128: s2[r * D + c] = sum_i a_ir a_ic for
+ * r <= c (entries below the diagonal are 0), s1[r] = sum_i a_ir, *n_patches =
+ * the number of patches; D = fgbd_stats.patch_dim (host arrays of D * D and D
+ * int64).  Synchronises the device.  Errors: FGBD_EINVAL (a null pointer),
+ * FGBD_ESTATE (no estimate with uint8 colours yet), FGBD_ECUDA. */
+fgbd_status fgbd_debug_moments(fgbd_ctx* ctx, int64_t* s2, int64_t* s1, int64_t* n_patches);
+
 /* Wait for the context's work on `stream` (and for the output copies of
  * fgbd_run_host) and return any latched device error (FGBD_ERANGE,
  * FGBD_ETIMEOUT), clearing it. */

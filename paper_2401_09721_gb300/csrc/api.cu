@@ -1486,6 +1486,32 @@ fgbd_status fgbd_debug_set_wait_limit(fgbd_ctx* ctx, int64_t ns) {
   return FGBD_OK;
 }
 
+fgbd_status fgbd_debug_moments(fgbd_ctx* ctx, int64_t* s2, int64_t* s1, int64_t* n_patches) {
+  if (!ctx || !s2 || !s1 || !n_patches) return FGBD_EINVAL;
+  DeviceGuard g(ctx->device);
+  if (!ctx->has_noise || ctx->noise_dtype != FGBD_U8) return FGBD_ESTATE;
+  FGBD_CUDA(ctx, cudaDeviceSynchronize());
+  const int w = ctx->params.window;
+  const int D = 3 * (6 * w + 1);
+  std::vector<double> t(size_t(D) * D + D + 1, 0.0);
+  if (w == 1) {
+    DevScalars h;
+    FGBD_CUDA(ctx, cudaMemcpy(&h, ctx->sc, sizeof(h), cudaMemcpyDeviceToHost));
+    for (int i = 0; i < D * D; ++i) s2[i] = h.s2[i];
+    for (int i = 0; i < D; ++i) s1[i] = h.s1[i];
+    *n_patches = int64_t(h.n_patches);
+  } else {
+    // the reduced totals (exact integers held as doubles)
+    FGBD_CUDA(ctx, cudaMemcpy(t.data(), ctx->wne.tot, t.size() * sizeof(double), cudaMemcpyDeviceToHost));
+    for (int i = 0; i < D * D; ++i) s2[i] = int64_t(t[i]);
+    for (int i = 0; i < D; ++i) s1[i] = int64_t(t[size_t(D) * D + i]);
+    *n_patches = int64_t(t[size_t(D) * D + D]);
+  }
+  for (int r = 0; r < D; ++r)
+    for (int c = 0; c < r; ++c) s2[r * D + c] = 0;
+  return FGBD_OK;
+}
+
 fgbd_status fgbd_debug_div(const double* a, const double* b, double* q_newton, double* q_div, int64_t n,
                            void* stream) {
   if (n < 0 || (n > 0 && (!a || !b || !q_newton || !q_div))) return FGBD_EINVAL;

@@ -19,6 +19,7 @@
 #include <atomic>
 
 #include "eigen.cuh"
+#include "gram_mma.cuh"
 #include "select.cuh"
 #include "tridiag.cuh"
 
@@ -151,7 +152,12 @@ __device__ __forceinline__ void cswap(NbKey<DT>& a, NbKey<DT>& b) {
 }
 
 constexpr int kNeWarps = kNeThreads / 32;
-constexpr int kRowWords = 9;    // 32 int8 patch entries = 8 words, padded: the 21 rows start in distinct banks
+// uint8 colours: the batch's patches as float16, entry-major: rows 0..20 the
+// entries, row 21 the constant 1 of each valid patch, rows 22..31 zero (the
+// second 16-row block of the mma tiles); 32 patches and 8 halves of padding a
+// row (80-byte rows: the eight rows of an ldmatrix tile fall in distinct banks)
+constexpr int kHRow = 40;
+constexpr int kHRows = 32;
 constexpr int kRowFloats = 33;  // 32 float entries, padded likewise
 constexpr int kFirstLanes = 32 - kTiles;  // lanes 28..31 sum the first moments
 
@@ -163,7 +169,7 @@ template <int DT>
 __device__ __forceinline__ bool point_patch(int k, int n, int bits, int lane, const uint32_t* __restrict__ pk,
                                             const int4* __restrict__ c4, const uint32_t* __restrict__ y8,
                                             const float4* __restrict__ yf, float* __restrict__ spread,
-                                            bool moments, bool sorted_patches, uint8_t* at8, float* atf) {
+                                            bool moments, bool sorted_patches, __half* ath, float* atf) {
   int nb[6];
   bool v[6];
   const uint32_t pkk = pk[k];  // packed code, with the same-line variant's missing-C1-link bits
@@ -292,17 +298,16 @@ __device__ __forceinline__ bool point_patch(int k, int n, int bits, int lane, co
     cswap(e[3], e[4]);
   }
   if (DT == 0) {
-    // entry r of the patch, centred on 128: the colour byte with its top bit flipped, read as int8
-    const int stride = kRowWords * 4;
-    at8[0 * stride + lane] = uint8_t((own8 & 255u) ^ 0x80u);
-    at8[1 * stride + lane] = uint8_t(((own8 >> 8) & 255u) ^ 0x80u);
-    at8[2 * stride + lane] = uint8_t(((own8 >> 16) & 255u) ^ 0x80u);
+    // entry r of the patch, centred on 128 (exact in float16)
+    ath[0 * kHRow + lane] = __int2half_rn(int(own8 & 255u) - 128);
+    ath[1 * kHRow + lane] = __int2half_rn(int((own8 >> 8) & 255u) - 128);
+    ath[2 * kHRow + lane] = __int2half_rn(int((own8 >> 16) & 255u) - 128);
 #pragma unroll
     for (int j = 0; j < 6; ++j) {
       const uint32_t c = reinterpret_cast<NbKey<0>&>(e[j]).col;
-      at8[(3 + 3 * j) * stride + lane] = uint8_t((c & 255u) ^ 0x80u);
-      at8[(4 + 3 * j) * stride + lane] = uint8_t(((c >> 8) & 255u) ^ 0x80u);
-      at8[(5 + 3 * j) * stride + lane] = uint8_t(((c >> 16) & 255u) ^ 0x80u);
+      ath[(3 + 3 * j) * kHRow + lane] = __int2half_rn(int(c & 255u) - 128);
+      ath[(4 + 3 * j) * kHRow + lane] = __int2half_rn(int((c >> 8) & 255u) - 128);
+      ath[(5 + 3 * j) * kHRow + lane] = __int2half_rn(int((c >> 16) & 255u) - 128);
     }
   } else {
     atf[0 * kRowFloats + lane] = ownr - 128.f;
@@ -321,11 +326,14 @@ __device__ __forceinline__ bool point_patch(int k, int n, int bits, int lane, co
 
 // Warp-synchronous: each warp takes 32 points at a time, stages their patches
 // transposed in its own shared-memory block and accumulates the moments with
-// __syncwarp only.  Lanes 0..27 own one 3x3 tile of the upper triangle of
-// sum a a^T; lanes 28..31 own rows of sum a.  uint8 colours: exact int32 dp4a
-// sums, moved to int64 every 1024 batches; float colours: fp32 sums over 4
-// batches, then float64.  The block combines its warps through shared atomics
-// and adds its totals to the context (uint8) or writes them (float).
+// __syncwarp only.  uint8 colours: float16 patches and mma.sync on the tensor
+// pipe (gram_mma.cuh): per 16 patches four m16n8k16 products cover the upper
+// triangle of the 22 x 22 Gram matrix of (a, 1), moved to exact int64 sums
+// every kGramFlushPatches patches.  Float colours: lanes 0..27 own one 3x3
+// tile of the upper triangle of sum a a^T, lanes 28..31 rows of sum a, in
+// fp32 over 4 batches, then float64.  The block combines its warps through
+// shared atomics and adds its totals to the context (uint8) or writes them
+// (float).
 template <int DT>
 __device__ __forceinline__ void ne_moments_body(const MomentArgs& ma, int bid, int nblk) {
   const int n = ma.n, bits = ma.bits, moments = ma.moments, sorted_patches = ma.sorted_patches;
@@ -337,7 +345,8 @@ __device__ __forceinline__ void ne_moments_body(const MomentArgs& ma, int bid, i
   double* __restrict__ f64_partials = ma.f64_partials;
   DevScalars* __restrict__ sc = ma.sc;
   constexpr int kP = kD * kD + kD + 1;
-  __shared__ __align__(16) uint32_t s_at8[DT == 0 ? kNeWarps : 1][kD * kRowWords];
+  static_assert(kD + 1 <= kHRows && kHRows == 32, "entries, the constant row and the zero rows fill two 16-row blocks");
+  __shared__ __align__(16) __half s_h[DT == 0 ? kNeWarps : 1][kHRows * kHRow];
   __shared__ __align__(16) float s_atf[DT == 1 ? kNeWarps : 1][kD * kRowFloats];
   __shared__ unsigned long long s_tot8[DT == 0 ? kP : 1];
   __shared__ double s_totf[DT == 1 ? kP : 1];
@@ -348,73 +357,67 @@ __device__ __forceinline__ void ne_moments_body(const MomentArgs& ma, int bid, i
       if (DT == 0) s_tot8[i] = 0ull;
       else s_totf[i] = 0.0;
     }
+    if (DT == 0) {
+      // the warp's staging block: all zero (rows 22..31 stay so)
+      uint32_t* hw = reinterpret_cast<uint32_t*>(&s_h[warp][0]);
+      for (int i = lane; i < kHRows * kHRow / 2; i += 32) hw[i] = 0u;
+    }
   }
   __syncthreads();
   int r0 = 0, c0 = 0, rb = 0, re = 0;
-  if (lane < kTiles) {
-    tile_rc(lane, r0, c0);
-  } else {
-    rb = ((lane - kTiles) * kD) / kFirstLanes;
-    re = ((lane - kTiles + 1) * kD) / kFirstLanes;
+  if (DT == 1) {
+    if (lane < kTiles) {
+      tile_rc(lane, r0, c0);
+    } else {
+      rb = ((lane - kTiles) * kD) / kFirstLanes;
+      re = ((lane - kTiles + 1) * kD) / kFirstLanes;
+    }
   }
-  int acc[9] = {};
-  long long acc64[9] = {};
+  float gc[4][4] = {};  // uint8: the Gram blocks (m0, n0), (m0, n1), (m0, n2), (m1, n2)
   float accf[9] = {};
   double accd[9] = {};
   unsigned long long npatch = 0;
   int since_flush = 0;
-  uint8_t* at8 = reinterpret_cast<uint8_t*>(&s_at8[DT == 0 ? warp : 0][0]);
+  __half* ath = &s_h[DT == 0 ? warp : 0][0];
   float* atf = &s_atf[DT == 1 ? warp : 0][0];
+  const uint32_t hbase = uint32_t(__cvta_generic_to_shared(ath));
 
   const int nwarps = nblk * kNeWarps;
   for (int base = (bid * kNeWarps + warp) * 32; base < n; base += nwarps * 32) {
     const int k = base + lane;
     bool has = false;
     if (k < n)
-      has = point_patch<DT>(k, n, bits, lane, pk, c4, y8, yf, spread, moments != 0, sorted_patches != 0, at8, atf);
+      has = point_patch<DT>(k, n, bits, lane, pk, c4, y8, yf, spread, moments != 0, sorted_patches != 0, ath, atf);
     if (!moments) continue;
-    if (!has) {
+    if (DT == 0) {
+      if (!has) {
 #pragma unroll
-      for (int r = 0; r < kD; ++r) {
-        if (DT == 0) at8[r * kRowWords * 4 + lane] = 0;
-        else atf[r * kRowFloats + lane] = 0.f;
+        for (int r = 0; r < kD; ++r) ath[r * kHRow + lane] = __float2half_rn(0.f);
       }
+      ath[kD * kHRow + lane] = __float2half_rn(has ? 1.f : 0.f);
+    } else if (!has) {
+#pragma unroll
+      for (int r = 0; r < kD; ++r) atf[r * kRowFloats + lane] = 0.f;
     }
     const uint32_t hb = __ballot_sync(0xffffffffu, has);
     npatch += __popc(hb);
     __syncwarp();
     if (DT == 0) {
-      const int* at = reinterpret_cast<const int*>(&s_at8[warp][0]);
-      if (lane < kTiles) {
 #pragma unroll
-        for (int w = 0; w < 8; ++w) {
-          int a[3], b[3];
-#pragma unroll
-          for (int i = 0; i < 3; ++i) {
-            a[i] = at[(r0 + i) * kRowWords + w];
-            b[i] = at[(c0 + i) * kRowWords + w];
-          }
-#pragma unroll
-          for (int i = 0; i < 3; ++i)
-#pragma unroll
-            for (int j = 0; j < 3; ++j) acc[3 * i + j] = __dp4a(a[i], b[j], acc[3 * i + j]);
-        }
-      } else {
-#pragma unroll
-        for (int t = 0; t < 6; ++t) {
-          const int r = rb + t;
-          if (r < re) {
-#pragma unroll
-            for (int w = 0; w < 8; ++w) acc[t] = __dp4a(at[r * kRowWords + w], 0x01010101, acc[t]);
-          }
-        }
+      for (int ks = 0; ks < 2; ++ks) {
+        uint32_t lo[4], hi[4];
+        ldsm_x4(gram_tile_addr(hbase, 0, 16 * ks, kHRow, lane), lo);
+        ldsm_x4(gram_tile_addr(hbase, 16, 16 * ks, kHRow, lane), hi);
+        mma_16816(gc[0], lo, lo[0], lo[2]);
+        mma_16816(gc[1], lo, lo[1], lo[3]);
+        mma_16816(gc[2], lo, hi[0], hi[2]);
+        mma_16816(gc[3], hi, hi[0], hi[2]);
       }
-      if (++since_flush == 1024) {
-#pragma unroll
-        for (int i = 0; i < 9; ++i) {
-          acc64[i] += acc[i];
-          acc[i] = 0;
-        }
+      if (++since_flush == kGramFlushPatches / 32) {
+        gram_flush(gc[0], 0, 0, kD + 1, lane, s_tot8, s_tot8 + kD * kD);
+        gram_flush(gc[1], 0, 1, kD + 1, lane, s_tot8, s_tot8 + kD * kD);
+        gram_flush(gc[2], 0, 2, kD + 1, lane, s_tot8, s_tot8 + kD * kD);
+        gram_flush(gc[3], 1, 2, kD + 1, lane, s_tot8, s_tot8 + kD * kD);
         since_flush = 0;
       }
     } else {
@@ -455,28 +458,25 @@ __device__ __forceinline__ void ne_moments_body(const MomentArgs& ma, int bid, i
     __syncwarp();
   }
   if (!moments) return;
-#pragma unroll
-  for (int i = 0; i < 9; ++i) {
-    acc64[i] += acc[i];
-    accd[i] += double(accf[i]);
-  }
   // combine the warps of the block
-  if (lane < kTiles) {
-#pragma unroll
-    for (int i = 0; i < 3; ++i)
-#pragma unroll
-      for (int j = 0; j < 3; ++j) {
-        const int idx = (r0 + i) * kD + (c0 + j);
-        if (DT == 0) atomicAdd(&s_tot8[idx], (unsigned long long)acc64[3 * i + j]);
-        else atomicAdd(&s_totf[idx], accd[3 * i + j]);
-      }
+  if (DT == 0) {
+    gram_flush(gc[0], 0, 0, kD + 1, lane, s_tot8, s_tot8 + kD * kD);
+    gram_flush(gc[1], 0, 1, kD + 1, lane, s_tot8, s_tot8 + kD * kD);
+    gram_flush(gc[2], 0, 2, kD + 1, lane, s_tot8, s_tot8 + kD * kD);
+    gram_flush(gc[3], 1, 2, kD + 1, lane, s_tot8, s_tot8 + kD * kD);
   } else {
 #pragma unroll
-    for (int t = 0; t < 6; ++t) {
-      const int r = rb + t;
-      if (r < re) {
-        if (DT == 0) atomicAdd(&s_tot8[kD * kD + r], (unsigned long long)acc64[t]);
-        else atomicAdd(&s_totf[kD * kD + r], accd[t]);
+    for (int i = 0; i < 9; ++i) accd[i] += double(accf[i]);
+    if (lane < kTiles) {
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) atomicAdd(&s_totf[(r0 + i) * kD + (c0 + j)], accd[3 * i + j]);
+    } else {
+#pragma unroll
+      for (int t = 0; t < 6; ++t) {
+        const int r = rb + t;
+        if (r < re) atomicAdd(&s_totf[kD * kD + r], accd[t]);
       }
     }
   }

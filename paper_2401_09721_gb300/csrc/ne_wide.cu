@@ -25,6 +25,7 @@
 #include <atomic>
 
 #include "eigen.cuh"
+#include "gram_mma.cuh"
 #include "tridiag.cuh"
 
 namespace fgbd {
@@ -52,8 +53,8 @@ __device__ __forceinline__ void cmp_swap(unsigned long long& ka, int& ia, unsign
 
 // Sorted point k: its FSLR spread over itself and all its neighbours
 // (spread[k]) and, if it has exactly K = 6W neighbours, its patch written to
-// column `col` of the transposed batch block `rows` (row stride `rw` words;
-// uint8: byte entries c ^ 0x80, i.e. c - 128 as int8; float: c - 128).
+// column `col` of the transposed batch block `rows` (row stride `rw`
+// elements; uint8: float16 entries c - 128, exact; float: float c - 128).
 // Returns whether a patch was written.
 template <int W, int DT>
 __device__ __forceinline__ bool wide_patch(int k, int n, int bits, const GraphBufs& gb, const uint32_t* __restrict__ y8,
@@ -140,18 +141,17 @@ __device__ __forceinline__ bool wide_patch(int k, int n, int bits, const GraphBu
     for (int i = round & 1; i + 1 < K; i += 2) cmp_swap(key[i], id[i], key[i + 1], id[i + 1]);
   }
   if (DT == 0) {
-    uint8_t* b = reinterpret_cast<uint8_t*>(rows);
-    const int stride = rw * 4;
+    __half* h = reinterpret_cast<__half*>(rows);
     const uint32_t own = y8[k];
-    b[0 * stride + col] = uint8_t((own & 255u) ^ 0x80u);
-    b[1 * stride + col] = uint8_t(((own >> 8) & 255u) ^ 0x80u);
-    b[2 * stride + col] = uint8_t(((own >> 16) & 255u) ^ 0x80u);
+    h[0 * rw + col] = __int2half_rn(int(own & 255u) - 128);
+    h[1 * rw + col] = __int2half_rn(int((own >> 8) & 255u) - 128);
+    h[2 * rw + col] = __int2half_rn(int((own >> 16) & 255u) - 128);
 #pragma unroll
     for (int j = 0; j < K; ++j) {
       const uint32_t c = y8[id[j]];
-      b[(3 + 3 * j) * stride + col] = uint8_t((c & 255u) ^ 0x80u);
-      b[(4 + 3 * j) * stride + col] = uint8_t(((c >> 8) & 255u) ^ 0x80u);
-      b[(5 + 3 * j) * stride + col] = uint8_t(((c >> 16) & 255u) ^ 0x80u);
+      h[(3 + 3 * j) * rw + col] = __int2half_rn(int(c & 255u) - 128);
+      h[(4 + 3 * j) * rw + col] = __int2half_rn(int((c >> 8) & 255u) - 128);
+      h[(5 + 3 * j) * rw + col] = __int2half_rn(int((c >> 16) & 255u) - 128);
     }
   } else {
     float* f = reinterpret_cast<float*>(rows);
@@ -170,20 +170,117 @@ __device__ __forceinline__ bool wide_patch(int k, int n, int bits, const GraphBu
   return true;
 }
 
-// Per block: batches of B points (B = 256 uint8 / 128 float), one per thread
-// of the first B; partial sums to part[blockIdx.x][D*D + D + 1] (second
-// moments at r*D + c for the computed tiles, first moments at D*D + r, the
-// patch count last; uint8 sums as int64 bit patterns).
-template <int W, int DT>
-__global__ void __launch_bounds__(kWThreads) k_ne_moments_wide(int n, int bits, GraphBufs gb,
-                                                               const uint32_t* __restrict__ y8,
-                                                               const float4* __restrict__ yf,
-                                                               float* __restrict__ spread, double* __restrict__ part) {
+// uint8 colours, per block: batches of B = 256 points, one per thread, staged
+// as float16 entry-major rows (entries, then the constant 1 of each valid
+// patch, then zero rows up to a multiple of 16); the upper triangle of the
+// Gram matrix of (a, 1) is covered by 16 x 8 blocks (mt, nt) with nt >= 2 mt,
+// shared out among the warps, each summed over the batch by mma.sync
+// (gram_mma.cuh) and moved to exact int64 sums in shared memory after every
+// batch.  The block's sums go to part[blockIdx.x][D*D + D + 1] as int64 bit
+// patterns (second moments at r*D + c, r <= c, 0 below the diagonal; first
+// moments at D*D + r; the patch count last).
+constexpr int kWBatch = 256;          // patches of a batch: one per thread
+constexpr int kWHRow = kWBatch + 8;   // halves a staged row (528-byte rows: ldmatrix rows in distinct banks)
+
+template <int W>
+struct WideGram {
+  static constexpr int D = patch_dim<W>();
+  static constexpr int De = D + 1;             // with the constant entry
+  static constexpr int MT = (De + 15) / 16;    // 16-row blocks
+  static constexpr int NTL = (De + 7) / 8;     // 8-column blocks holding entries
+  static constexpr int Tiles = [] {
+    int c = 0;
+    for (int mt = 0; mt < MT; ++mt) c += NTL - 2 * mt > 0 ? NTL - 2 * mt : 0;
+    return c;
+  }();
+  static constexpr int PerWarp = (Tiles + kWThreads / 32 - 1) / (kWThreads / 32);
+  static constexpr size_t RowBytes = size_t(16 * MT) * kWHRow * 2;
+  static constexpr size_t SmemBytes = RowBytes + size_t(D * D + D) * 8;
+  static_assert(kWBatch == kWThreads, "one patch per thread");
+  static_assert(2 * MT >= NTL, "every column block's B operand comes from a row block");
+};
+
+template <int W>
+__global__ void __launch_bounds__(kWThreads) k_ne_moments_wide_tc(int n, int bits, GraphBufs gb,
+                                                                  const uint32_t* __restrict__ y8,
+                                                                  float* __restrict__ spread,
+                                                                  double* __restrict__ part) {
+  pdl_wait();
+  using G = WideGram<W>;
+  constexpr int D = G::D, P = D * D + D + 1;
+  extern __shared__ __align__(16) unsigned char s_dyn[];
+  __half* rows = reinterpret_cast<__half*>(s_dyn);
+  unsigned long long* sums = reinterpret_cast<unsigned long long*>(s_dyn + G::RowBytes);  // s2, then s1
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int i = tid; i < int(G::RowBytes / 4); i += kWThreads) reinterpret_cast<uint32_t*>(rows)[i] = 0u;
+  for (int i = tid; i < D * D + D; i += kWThreads) sums[i] = 0ull;
+  // this warp's blocks of the Gram matrix: tiles warp, warp + 8, ...
+  int tm[G::PerWarp], tn[G::PerWarp];
+#pragma unroll
+  for (int j = 0; j < G::PerWarp; ++j) {
+    int t = warp + j * (kWThreads / 32), mt = 0;
+    tm[j] = -1;
+    tn[j] = 0;
+    if (t >= G::Tiles) continue;
+    while (t >= G::NTL - 2 * mt) {
+      t -= G::NTL - 2 * mt;
+      ++mt;
+    }
+    tm[j] = mt;
+    tn[j] = 2 * mt + t;
+  }
+  __syncthreads();
+  const uint32_t hbase = uint32_t(__cvta_generic_to_shared(rows));
+  unsigned long long npatch = 0;
+  for (int base = blockIdx.x * kWBatch; base < n; base += gridDim.x * kWBatch) {
+    const int k = base + tid;
+    bool has = false;
+    if (k < n) has = wide_patch<W, 0>(k, n, bits, gb, y8, nullptr, spread, tid, reinterpret_cast<uint32_t*>(rows),
+                                      kWHRow);
+    if (!has) {
+#pragma unroll 3
+      for (int r = 0; r < D; ++r) rows[r * kWHRow + tid] = __float2half_rn(0.f);
+    }
+    rows[D * kWHRow + tid] = __float2half_rn(has ? 1.f : 0.f);
+    npatch += (unsigned long long)__syncthreads_count(has);
+#pragma unroll
+    for (int j = 0; j < G::PerWarp; ++j) {
+      if (tm[j] < 0) continue;
+      float c[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll 4
+      for (int ks = 0; ks < kWBatch / 16; ++ks) {
+        uint32_t a[4], b[4];
+        ldsm_x4(gram_tile_addr(hbase, 16 * tm[j], 16 * ks, kWHRow, lane), a);
+        ldsm_x4(gram_tile_addr(hbase, 16 * (tn[j] >> 1), 16 * ks, kWHRow, lane), b);
+        if (tn[j] & 1) mma_16816(c, a, b[1], b[3]);
+        else mma_16816(c, a, b[0], b[2]);
+      }
+      static_assert(kWBatch <= kGramFlushPatches, "one batch per accumulator before the move to int64");
+      gram_flush(c, tm[j], tn[j], G::De, lane, sums, sums + D * D);
+    }
+    __syncthreads();  // the rows are rewritten by the next batch
+  }
+  __syncthreads();
+  long long* out = reinterpret_cast<long long*>(part + size_t(blockIdx.x) * P);
+  for (int i = tid; i < D * D + D; i += kWThreads) out[i] = (long long)sums[i];
+  if (tid == 0) out[D * D + D] = (long long)npatch;
+}
+
+// Float colours, per block: batches of B = 128 points, one per thread of the
+// first B; each thread owns one 3x3 tile (node a, node b >= a) of sum a a^T or
+// the three sums a of one node, in float32 per batch, then float64; partial
+// sums to part[blockIdx.x][D*D + D + 1] (second moments at r*D + c for the
+// computed tiles, first moments at D*D + r, the patch count last).
+template <int W>
+__global__ void __launch_bounds__(kWThreads) k_ne_moments_wide_f32(int n, int bits, GraphBufs gb,
+                                                                   const float4* __restrict__ yf,
+                                                                   float* __restrict__ spread,
+                                                                   double* __restrict__ part) {
   pdl_wait();
   constexpr int T = 6 * W + 1;  // points of a patch
   constexpr int D = 3 * T;
-  constexpr int B = DT == 0 ? 256 : 128;
-  constexpr int RW = DT == 0 ? B / 4 + 1 : B + 1;  // row stride in words, odd: rows start in distinct banks
+  constexpr int B = 128;
+  constexpr int RW = B + 1;                        // row stride in words, odd: rows start in distinct banks
   constexpr int NT = T * (T + 1) / 2;              // tiles (a, b), a <= b
   constexpr int P = D * D + D + 1;
   static_assert(NT + T <= kWThreads && B <= kWThreads, "one tile or one first-moment node per thread");
@@ -203,108 +300,60 @@ __global__ void __launch_bounds__(kWThreads) k_ne_moments_wide(int n, int bits, 
   } else if (tid < NT + T) {
     ta = tid - NT;
   }
-  long long acc64[9] = {};
   double accd[9] = {};
   unsigned long long npatch = 0;
   for (int base = blockIdx.x * B; base < n; base += gridDim.x * B) {
     bool has = false;
     if (tid < B) {
       const int k = base + tid;
-      if (k < n) has = wide_patch<W, DT>(k, n, bits, gb, y8, yf, spread, tid, rows, RW);
+      if (k < n) has = wide_patch<W, 1>(k, n, bits, gb, nullptr, yf, spread, tid, rows, RW);
       if (!has) {
-        if (DT == 0) {
-          uint8_t* b = reinterpret_cast<uint8_t*>(rows);
+        float* f = reinterpret_cast<float*>(rows);
 #pragma unroll 3
-          for (int r = 0; r < D; ++r) b[r * RW * 4 + tid] = 0;
-        } else {
-          float* f = reinterpret_cast<float*>(rows);
-#pragma unroll 3
-          for (int r = 0; r < D; ++r) f[r * RW + tid] = 0.f;
-        }
+        for (int r = 0; r < D; ++r) f[r * RW + tid] = 0.f;
       }
     }
     npatch += (unsigned long long)__syncthreads_count(has);
-    if (DT == 0) {
-      const int* ri = reinterpret_cast<const int*>(rows);
-      if (tb >= 0) {
-        int acc[9] = {};
+    const float* rf = reinterpret_cast<const float*>(rows);
+    if (tb >= 0) {
+      float accf[9] = {};
 #pragma unroll 4
-        for (int w = 0; w < B / 4; ++w) {
-          int a[3], b[3];
+      for (int p = 0; p < B; ++p) {
+        float a[3], b[3];
 #pragma unroll
-          for (int i = 0; i < 3; ++i) {
-            a[i] = ri[(3 * ta + i) * RW + w];
-            b[i] = ri[(3 * tb + i) * RW + w];
-          }
-#pragma unroll
-          for (int i = 0; i < 3; ++i)
-#pragma unroll
-            for (int j = 0; j < 3; ++j) acc[3 * i + j] = __dp4a(a[i], b[j], acc[3 * i + j]);
+        for (int i = 0; i < 3; ++i) {
+          a[i] = rf[(3 * ta + i) * RW + p];
+          b[i] = rf[(3 * tb + i) * RW + p];
         }
 #pragma unroll
-        for (int i = 0; i < 9; ++i) acc64[i] += acc[i];
-      } else if (ta >= 0) {
-        int acc[3] = {};
-#pragma unroll 4
-        for (int w = 0; w < B / 4; ++w)
+        for (int i = 0; i < 3; ++i)
 #pragma unroll
-          for (int i = 0; i < 3; ++i) acc[i] = __dp4a(ri[(3 * ta + i) * RW + w], 0x01010101, acc[i]);
-#pragma unroll
-        for (int i = 0; i < 3; ++i) acc64[i] += acc[i];
+          for (int j = 0; j < 3; ++j) accf[3 * i + j] = fmaf(a[i], b[j], accf[3 * i + j]);
       }
-    } else {
-      const float* rf = reinterpret_cast<const float*>(rows);
-      if (tb >= 0) {
-        float accf[9] = {};
+#pragma unroll
+      for (int i = 0; i < 9; ++i) accd[i] += double(accf[i]);
+    } else if (ta >= 0) {
+      float accf[3] = {};
 #pragma unroll 4
-        for (int p = 0; p < B; ++p) {
-          float a[3], b[3];
+      for (int p = 0; p < B; ++p)
 #pragma unroll
-          for (int i = 0; i < 3; ++i) {
-            a[i] = rf[(3 * ta + i) * RW + p];
-            b[i] = rf[(3 * tb + i) * RW + p];
-          }
+        for (int i = 0; i < 3; ++i) accf[i] += rf[(3 * ta + i) * RW + p];
 #pragma unroll
-          for (int i = 0; i < 3; ++i)
-#pragma unroll
-            for (int j = 0; j < 3; ++j) accf[3 * i + j] = fmaf(a[i], b[j], accf[3 * i + j]);
-        }
-#pragma unroll
-        for (int i = 0; i < 9; ++i) accd[i] += double(accf[i]);
-      } else if (ta >= 0) {
-        float accf[3] = {};
-#pragma unroll 4
-        for (int p = 0; p < B; ++p)
-#pragma unroll
-          for (int i = 0; i < 3; ++i) accf[i] += rf[(3 * ta + i) * RW + p];
-#pragma unroll
-        for (int i = 0; i < 3; ++i) accd[i] += double(accf[i]);
-      }
+      for (int i = 0; i < 3; ++i) accd[i] += double(accf[i]);
     }
     __syncthreads();
   }
   double* out = part + size_t(blockIdx.x) * P;
-  long long* outi = reinterpret_cast<long long*>(out);
   if (tb >= 0) {
 #pragma unroll
     for (int i = 0; i < 3; ++i)
 #pragma unroll
-      for (int j = 0; j < 3; ++j) {
-        const int idx = (3 * ta + i) * D + 3 * tb + j;
-        if (DT == 0) outi[idx] = acc64[3 * i + j];
-        else out[idx] = accd[3 * i + j];
-      }
+      for (int j = 0; j < 3; ++j) out[(3 * ta + i) * D + 3 * tb + j] = accd[3 * i + j];
   } else if (ta >= 0) {
 #pragma unroll
-    for (int i = 0; i < 3; ++i) {
-      if (DT == 0) outi[D * D + 3 * ta + i] = acc64[i];
-      else out[D * D + 3 * ta + i] = accd[i];
-    }
+    for (int i = 0; i < 3; ++i) out[D * D + 3 * ta + i] = accd[i];
   }
-  if (tid == 0) {
-    if (DT == 0) outi[D * D + D] = (long long)npatch;
-    else out[D * D + D] = double(npatch);
-  }
+  if (tid == 0) out[D * D + D] = double(npatch);
 }
 
 // The totals: block (32 entries) x 8 warps; warp w sums the partial rows
@@ -520,10 +569,18 @@ cudaError_t launch_wide(int stage, int n, int bits, int dtype, const GraphBufs& 
   switch (stage) {
     case 0:
       if (n <= 0) return cudaSuccess;
-      return dtype == 0 ? launch_kernel(k_ne_moments_wide<W, 0>, dim3(blocks), dim3(kWThreads), 0, stream, false, n,
-                                        bits, gb, y8, yf, spread, w.part)
-                        : launch_kernel(k_ne_moments_wide<W, 1>, dim3(blocks), dim3(kWThreads), 0, stream, false, n,
-                                        bits, gb, y8, yf, spread, w.part);
+      if (dtype == 0) {
+        static std::atomic<unsigned long long> configured{0};  // the shared-memory limit, once per device
+        const cudaError_t e = once_per_device(configured, [] {
+          return cudaFuncSetAttribute(k_ne_moments_wide_tc<W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      int(WideGram<W>::SmemBytes));
+        });
+        if (e != cudaSuccess) return e;
+        return launch_kernel(k_ne_moments_wide_tc<W>, dim3(blocks), dim3(kWThreads), WideGram<W>::SmemBytes, stream,
+                             false, n, bits, gb, y8, spread, w.part);
+      }
+      return launch_kernel(k_ne_moments_wide_f32<W>, dim3(blocks), dim3(kWThreads), 0, stream, false, n, bits, gb,
+                           yf, spread, w.part);
     case 1: {
       const int used = n > 0 ? blocks : 0;
       const dim3 rgrid((P + 31) / 32), rblock(32 * kReduceWarps);

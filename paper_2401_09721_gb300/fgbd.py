@@ -13,6 +13,7 @@ from __future__ import annotations
 import ctypes
 import os
 
+import numpy as np
 import torch
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -133,6 +134,7 @@ _SIGS = {
     "fgbd_run_host": (ctypes.c_int, [_P, _P, ctypes.c_int64, _P, ctypes.c_int32, _P, ctypes.c_int32, _P]),
     "fgbd_debug_set_wait_limit": (ctypes.c_int, [_P, ctypes.c_int64]),
     "fgbd_debug_div": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int64, _P]),
+    "fgbd_debug_moments": (ctypes.c_int, [_P, _P, _P, _P]),
     "fgbd_run_batch": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(ctypes.c_int64),
                                       ctypes.POINTER(_P), ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(_P),
                                       ctypes.POINTER(ctypes.c_int32), ctypes.c_int32, _P]),
@@ -642,6 +644,16 @@ class Context:
 
     def set_timing(self, enable: bool):
         fgbd_set_timing(self.handle, enable)
+
+    def debug_moments(self):
+        """(s2 [D, D], s1 [D], patch count) of the last uint8 noise estimate, exact int64 (testing)."""
+        D = self.stats()["patch_dim"]
+        s2 = np.zeros((D, D), dtype=np.int64)
+        s1 = np.zeros(D, dtype=np.int64)
+        npat = ctypes.c_int64(0)
+        _check(lib().fgbd_debug_moments(self.handle, s2.ctypes.data, s1.ctypes.data, ctypes.byref(npat)),
+               "fgbd_debug_moments")
+        return s2, s1, int(npat.value)
 
     def timings(self) -> list:
         return fgbd_get_timings(self.handle)

@@ -98,6 +98,7 @@ def test_host_side_checks_without_gpu(so):
     assert lib.fgbd_status_str(0) == b"FGBD_OK"
     assert lib.fgbd_status_str(5).startswith(b"FGBD_ETIMEOUT")
     assert lib.fgbd_debug_set_wait_limit(None, 0) == 1
+    assert lib.fgbd_debug_moments(None, None, None, None) == 1
     # the graph handle: argument checks before any CUDA call
     g = ctypes.c_void_p()
     assert lib.fgbd_graph_export(None, ctypes.byref(g), None) == 1
