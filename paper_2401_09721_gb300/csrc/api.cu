@@ -377,10 +377,10 @@ fgbd_status do_build(fgbd_ctx* ctx, const int32_t* xyz, int64_t n64, cudaStream_
     static const char* const kCounts[kSlgPasses] = {"slg_counts0", "slg_counts1", "slg_counts2"};
     static const char* const kScan[kSlgPasses] = {"slg_scan0", "slg_scan1", "slg_scan2"};
     static const char* const kScatter[kSlgPasses] = {"slg_scatter0", "slg_scatter1", "slg_scatter2"};
-    FGBD_LAUNCH(ctx, "slg_hist", st, launch_coord_hist(xyz, n, bits, ctx->sc, ctx->num_sms, st));
+    FGBD_LAUNCH(ctx, "slg_hist", st, launch_coord_hist(xyz, n, bits, ctx->sc, &ctx->sb, ctx->num_sms, st));
     for (int p = 0; p < kSlgPasses; ++p) {
       const SortPassArgs a = slg_pass_args(p, xyz, n, bits, ord_stride(ctx), ctx->sb, ctx->gb, ctx->sc);
-      FGBD_LAUNCH(ctx, kCounts[p], st, launch_tile_counts(a, st));
+      if (!pass_counted_before(p)) FGBD_LAUNCH(ctx, kCounts[p], st, launch_tile_counts(a, st));
       FGBD_LAUNCH(ctx, kScan[p], st, launch_tile_scan(a, st));
       FGBD_LAUNCH(ctx, kScatter[p], st, launch_sort_scatter(a, st));
       if (p == 0)
@@ -622,7 +622,7 @@ fgbd_status seg_chunk(const std::vector<fgbd_ctx*>& ctxs, const std::vector<fgbd
     scs[f] = c->sc;
     z[f] = ZeroArgs{reinterpret_cast<uint32_t*>(reinterpret_cast<char*>(c->sc) + offsetof(DevScalars, n_edges)),
                     (offsetof(DevScalars, sel_end_) - offsetof(DevScalars, n_edges)) / 4};
-    h[f] = hist_args(xyz, n, bits[f], c->sc);
+    h[f] = hist_args(xyz, n, bits[f], c->sc, c->sb);
     l[f] = link_args(n, bits[f], caps[f], c->gb, c->sb, c->sc);
     g[f] = GatherArgs{k.rgb_in, dtype, n, c->gb.perm1, c->y8, c->yf};
     m[f] = moment_args(n, bits[f], c->gb, c->y8, c->yf, c->spread, c->f64part, true, sorted, c->sc);
@@ -648,8 +648,8 @@ fgbd_status seg_chunk(const std::vector<fgbd_ctx*>& ctxs, const std::vector<fgbd
                            c->sc);
     }
     {
-      // counts, scan and scatter: three launches under one timing scope
-      LaunchScope scope_(lead, kPass[p][2], st, 3);
+      // (counts,) scan and scatter: two or three launches under one timing scope
+      LaunchScope scope_(lead, kPass[p][2], st, pass_counted_before(p) ? 2 : 3);
       FGBD_CUDA(lead, launch_sort_pass_seg(a, F, shape.scatter_threads, st));
     }
     if (p == 0) FGBD_LAUNCH(lead, "seg_slab", st, launch_slab_sort_seg(ns, bits, caps, sbs, gbs, scs, F, st));
@@ -901,7 +901,7 @@ fgbd_status fgbd_ctx_create(int64_t capacity, const fgbd_params* params, fgbd_ct
       {&keys1, C * 4},
       {&vals0, C * 4},
       {&vals1, C * 4},
-      {reinterpret_cast<void**>(&ctx->sb.tile_counts), size_t(kMaxRadix) * tiles * 4},
+      {reinterpret_cast<void**>(&ctx->sb.tile_counts), size_t(kSlgPasses) * kMaxRadix * tiles * 4},
       {reinterpret_cast<void**>(&ctx->gb.perm1), C * 4},
       {reinterpret_cast<void**>(&ctx->gb.rank1), C * 4},
       {reinterpret_cast<void**>(&ctx->gb.pk), C * 4},
@@ -945,6 +945,7 @@ fgbd_status fgbd_ctx_create(int64_t capacity, const fgbd_params* params, fgbd_ct
     *it.ptr = static_cast<char*>(ctx->mem) + off;
     off += it.bytes;
   }
+  ctx->sb.count_stride = kMaxRadix * tiles;
   ctx->sb.keys[0] = static_cast<uint32_t*>(keys0);
   ctx->sb.keys[1] = static_cast<uint32_t*>(keys1);
   ctx->sb.vals[0] = static_cast<uint32_t*>(vals0);

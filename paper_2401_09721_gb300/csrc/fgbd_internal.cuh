@@ -117,7 +117,11 @@ static_assert(offsetof(DevScalars, n_edges) < offsetof(DevScalars, build_end_) &
 struct SortBufs {
   uint32_t* keys[2];     // ping-pong [cap]
   uint32_t* vals[2];     // ping-pong [cap]
-  uint32_t* tile_counts; // [kMaxRadix digits][tiles]: per-tile digit counts, then offsets
+  uint32_t* tile_counts; // [3 passes][kMaxRadix digits][tiles of the capacity]: per-tile digit counts,
+                         // then offsets.  Pass 0's are written by the histogram launch, pass 1's
+                         // added up by the slab sort (zeroed by the histogram launch), pass 2's by
+                         // a counting launch.
+  int count_stride;      // words of one pass's counts: kMaxRadix * tiles of the capacity
 };
 
 // Graph in sorted order.
@@ -154,6 +158,7 @@ struct SortPassArgs {
   uint32_t* vals_out;
   int32_t* rank_out;       // rank_out[value] = output position, or null
   int32_t* pos_out;        // pos_out[input position] = output position, or null
+  int pass;                // 0, 1, 2 (which launch made the tile counts: pass_counted_before)
   uint32_t* counts;
   const DevScalars* sc;
 };
@@ -201,6 +206,8 @@ struct HistArgs {
   int n;
   int bits;
   struct DevScalars* sc;
+  uint32_t* counts0;     // sort pass 0's tile counts (the y digits of each 4096-point input tile), or null
+  uint32_t* counts1;     // pass 1's tile counts, zeroed here (the slab sort adds them up), or null
 };
 struct SlabArgs {
   int n;
@@ -212,6 +219,7 @@ struct SlabArgs {
   uint32_t* keys_out;
   int32_t* vals_out;
   const struct DevScalars* sc;
+  uint32_t* counts1;     // sort pass 1's tile counts: the z digits of the C3 order, added up here (or null)
 };
 struct LinkArgs {
   int n;
@@ -266,7 +274,9 @@ struct BatchShape {
 struct FilterArgs;
 // Every launcher enqueues on `stream` and returns the launch error.
 
-cudaError_t launch_coord_hist(const int32_t* xyz, int n, int bits, DevScalars* sc, int num_sms, cudaStream_t stream);
+// the coordinate histograms; with sb, also sort pass 0's tile counts (and pass 1's zeroed)
+cudaError_t launch_coord_hist(const int32_t* xyz, int n, int bits, DevScalars* sc, const SortBufs* sb, int num_sms,
+                              cudaStream_t stream);
 // pass 0: y-slabs from the input; (the slab sort then gives C3); pass 1: C1 = the C3 order on z;
 // pass 2: C2 = the C1 order on x
 SortPassArgs slg_pass_args(int pass, const int32_t* xyz, int n, int bits, int cap, const SortBufs& sb,
@@ -275,13 +285,15 @@ SortPassArgs slg_pass_args(int pass, const int32_t* xyz, int n, int bits, int ca
 cudaError_t launch_slab_sort(int n, int bits, int cap, const SortBufs& sb, const GraphBufs& gb,
                              const DevScalars* sc, cudaStream_t stream);
 cudaError_t launch_tile_counts(const SortPassArgs& a, cudaStream_t stream);
+// pass p's tile counts are made by the launches before it for p = 0 (histogram) and p = 1 (slab sort)
+constexpr bool pass_counted_before(int pass) { return pass < 2; }
 cudaError_t launch_tile_scan(const SortPassArgs& a, cudaStream_t stream);
 cudaError_t launch_sort_scatter(const SortPassArgs& a, cudaStream_t stream);
 cudaError_t launch_sort_pass(const SortPassArgs& a, cudaStream_t stream);  // the three above
 cudaError_t launch_orders_export(int n, int cap, const GraphBufs& gb, int32_t* out, cudaStream_t stream);
 // segmented launches: one launch for frames 0..count-1 (count <= kSegMax), each
 // frame with the blocks its one-frame launch would have
-HistArgs hist_args(const int32_t* xyz, int n, int bits, DevScalars* sc);
+HistArgs hist_args(const int32_t* xyz, int n, int bits, DevScalars* sc, const SortBufs& sb);
 LinkArgs link_args(int n, int bits, int cap, const GraphBufs& gb, const SortBufs& sb, DevScalars* sc);
 cudaError_t launch_zero_words_seg(const ZeroArgs* a, int count, cudaStream_t stream);
 cudaError_t launch_coord_hist_seg(const HistArgs* a, int count, int num_sms, cudaStream_t stream);

@@ -133,12 +133,24 @@ __device__ __forceinline__ bool wide_patch(int k, int n, int bits, const GraphBu
     key[j] = (d2 << 33) | ((unsigned long long)(dz + 1024) << 22) | ((unsigned long long)(dy + 1024) << 11) |
              (unsigned long long)(dx + 1024);
   }
-  // odd-even transposition sort: K rounds order K elements (keys with their
-  // id are a strict order, so the result is the unique sorted one)
+  // Batcher's odd-even merge sort for K elements (42 comparators at K = 12,
+  // 90 at K = 18, against K (K - 1) / 2 of a transposition sort); the keys
+  // with their id are a strict order, so any sorting network gives the unique
+  // sorted result.  All bounds are compile-time, so the network unrolls into
+  // straight compare-exchanges on registers.
 #pragma unroll
-  for (int round = 0; round < K; ++round) {
+  for (int p = 1; p < K; p <<= 1) {
 #pragma unroll
-    for (int i = round & 1; i + 1 < K; i += 2) cmp_swap(key[i], id[i], key[i + 1], id[i + 1]);
+    for (int kk = p; kk >= 1; kk >>= 1) {
+#pragma unroll
+      for (int j = kk % p; j + kk < K; j += 2 * kk) {
+#pragma unroll
+        for (int i = 0; i < kk && i + j + kk < K; ++i) {
+          if ((i + j) / (2 * p) == (i + j + kk) / (2 * p))
+            cmp_swap(key[i + j], id[i + j], key[i + j + kk], id[i + j + kk]);
+        }
+      }
+    }
   }
   if (DT == 0) {
     __half* h = reinterpret_cast<__half*>(rows);

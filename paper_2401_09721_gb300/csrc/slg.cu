@@ -57,20 +57,39 @@ size_t scatter_smem_bytes(int threads) {
          (size_t(warps / 2) * kMaxRadix + 2 * size_t(kSortTile) + 2 * size_t(kMaxRadix) + warps + 1);
 }
 
+// The three coordinate histograms, one 1024-thread block per SM taking whole
+// 4096-point tiles of the input, merged with global atomics.  The y digits of
+// each tile are also counted on their own: sort pass 0's tile counts (its
+// keys are the input's y digits in input order), so that pass needs no
+// counting launch.  Pass 1's tile counts, which the slab sort adds up, are
+// zeroed here.
 __device__ __forceinline__ void coord_hist_body(const HistArgs& a, int bid, int nblk) {
   __shared__ uint32_t h[3][kMaxRadix];
+  __shared__ uint32_t ht[kMaxRadix];
   const int radix = 1 << a.bits;
+  const int tiles = (a.n + kSortTile - 1) / kSortTile;
   for (int i = threadIdx.x; i < 3 * kMaxRadix; i += blockDim.x) (&h[0][0])[i] = 0;
-  __syncthreads();
+  if (a.counts1) {
+    const size_t words = size_t(radix) * tiles;
+    for (size_t i = size_t(bid) * blockDim.x + threadIdx.x; i < words; i += size_t(nblk) * blockDim.x)
+      a.counts1[i] = 0u;
+  }
   const uint32_t m = uint32_t(radix) - 1u;
   bool bad = false;
-  const size_t gstride = size_t(nblk) * blockDim.x;
-  for (size_t i = size_t(bid) * blockDim.x + threadIdx.x; i < size_t(a.n); i += gstride) {
-    const int xi = a.xyz[3 * i], yi = a.xyz[3 * i + 1], zi = a.xyz[3 * i + 2];
-    bad |= (uint32_t(xi) > m) | (uint32_t(yi) > m) | (uint32_t(zi) > m);
-    atomicAdd(&h[0][uint32_t(xi) & m], 1u);
-    atomicAdd(&h[1][uint32_t(yi) & m], 1u);
-    atomicAdd(&h[2][uint32_t(zi) & m], 1u);
+  for (int t = bid; t < tiles; t += nblk) {
+    for (int d = threadIdx.x; d < radix; d += blockDim.x) ht[d] = 0;
+    __syncthreads();
+    for (int i = t * kSortTile + int(threadIdx.x); i < min(a.n, (t + 1) * kSortTile); i += blockDim.x) {
+      const int xi = a.xyz[3 * size_t(i)], yi = a.xyz[3 * size_t(i) + 1], zi = a.xyz[3 * size_t(i) + 2];
+      bad |= (uint32_t(xi) > m) | (uint32_t(yi) > m) | (uint32_t(zi) > m);
+      atomicAdd(&h[0][uint32_t(xi) & m], 1u);
+      atomicAdd(&h[1][uint32_t(yi) & m], 1u);
+      atomicAdd(&h[2][uint32_t(zi) & m], 1u);
+      atomicAdd(&ht[uint32_t(yi) & m], 1u);
+    }
+    __syncthreads();
+    if (a.counts0)
+      for (int d = threadIdx.x; d < radix; d += blockDim.x) a.counts0[size_t(d) * tiles + t] = ht[d];
   }
   if (bad) atomicOr(&a.sc->status, kFlagRange);
   __syncthreads();
@@ -537,6 +556,24 @@ __device__ __forceinline__ void slab_sort_body(const SlabArgs& sa, int yv) {
       keys_out[start + i] = s_keys[i];
       vals_out[start + i] = int32_t(s_vals[i]);
     }
+    if (sa.counts1) {
+      // sort pass 1's tile counts (z digits of the C3 order): the slab's at
+      // most kSlabMax positions lie in the 4096-key tiles t0 and t0 + 1, counted
+      // in the digit counters (free after the last pass), then added to the totals
+      const uint32_t t0 = start / kSortTile;
+      const int tiles = (n + kSortTile - 1) / kSortTile;
+      static_assert(kSlabMax <= kSortTile && 2 * kMaxRadix <= kSlabPairWords * kMaxRadix,
+                    "a slab spans at most two tiles, counted in the digit counter words");
+      for (int i = tid; i < 2 * radix; i += kSlabThreads) cnt[i] = 0;
+      __syncthreads();
+      for (uint32_t i = tid; i < size; i += kSlabThreads)
+        atomicAdd(&cnt[((start + i) / kSortTile - t0) * radix + ((s_keys[i] >> (2 * bits)) & m)], 1u);
+      __syncthreads();
+      for (int i = tid; i < 2 * radix; i += kSlabThreads) {
+        const uint32_t c = cnt[i], t = t0 + uint32_t(i / radix);
+        if (c && t < uint32_t(tiles)) atomicAdd(&sa.counts1[size_t(i % radix) * tiles + t], c);
+      }
+    }
     return;
   }
 
@@ -594,6 +631,10 @@ __device__ __forceinline__ void slab_sort_body(const SlabArgs& sa, int yv) {
           } else {
             keys_out[g] = key;
             vals_out[g] = int32_t(val);
+            if (sa.counts1)  // sort pass 1's tile counts, one key at a time here
+              atomicAdd(&sa.counts1[size_t((key >> (2 * bits)) & m) * ((n + kSortTile - 1) / kSortTile) +
+                                    g / kSortTile],
+                        1u);
           }
         }
       }
@@ -975,22 +1016,26 @@ cudaError_t launch_seg(K kernel, const A* args, const int* blocks, int count, in
 
 SlabArgs slab_args(int n, int bits, int cap, const SortBufs& sb, const GraphBufs& gb, const DevScalars* sc) {
   // scratch for slabs larger than shared memory: the C2 order and C2 ranks, written later
-  return SlabArgs{n, bits, sb.keys[0], sb.vals[0], reinterpret_cast<uint32_t*>(gb.ord23),
-                  reinterpret_cast<uint32_t*>(gb.rank2), sb.keys[1], gb.ord23 + size_t(cap), sc};
+  return SlabArgs{n,  bits, sb.keys[0], sb.vals[0], reinterpret_cast<uint32_t*>(gb.ord23),
+                  reinterpret_cast<uint32_t*>(gb.rank2), sb.keys[1], gb.ord23 + size_t(cap), sc,
+                  sb.tile_counts + sb.count_stride};
 }
 }  // namespace
 
-HistArgs hist_args(const int32_t* xyz, int n, int bits, DevScalars* sc) { return HistArgs{xyz, n, bits, sc}; }
+HistArgs hist_args(const int32_t* xyz, int n, int bits, DevScalars* sc, const SortBufs& sb) {
+  return HistArgs{xyz, n, bits, sc, sb.tile_counts, sb.tile_counts + sb.count_stride};
+}
 
 LinkArgs link_args(int n, int bits, int cap, const GraphBufs& gb, const SortBufs& sb, DevScalars* sc) {
   return LinkArgs{n, bits, cap, gb.ord23, sb.keys[0], sb.keys[1], gb.rank2, gb.pk, gb.c4, sc};
 }
 
-cudaError_t launch_coord_hist(const int32_t* xyz, int n, int bits, DevScalars* sc, int num_sms, cudaStream_t stream) {
+cudaError_t launch_coord_hist(const int32_t* xyz, int n, int bits, DevScalars* sc, const SortBufs* sb, int num_sms,
+                              cudaStream_t stream) {
   if (n <= 0) return cudaSuccess;
+  const HistArgs h = sb ? hist_args(xyz, n, bits, sc, *sb) : HistArgs{xyz, n, bits, sc, nullptr, nullptr};
   // one large block per SM: few blocks keep the global atomics of the final merge few
-  return launch_kernel(k_coord_hist, dim3(coord_hist_blocks(n, num_sms)), dim3(1024), 0, stream, false,
-                       hist_args(xyz, n, bits, sc));
+  return launch_kernel(k_coord_hist, dim3(coord_hist_blocks(n, num_sms)), dim3(1024), 0, stream, false, h);
 }
 
 cudaError_t launch_tile_counts(const SortPassArgs& a, cudaStream_t stream) {
@@ -1009,7 +1054,7 @@ cudaError_t launch_sort_scatter(const SortPassArgs& a, cudaStream_t stream) {
 }
 
 cudaError_t launch_sort_pass(const SortPassArgs& a, cudaStream_t stream) {
-  cudaError_t e = launch_tile_counts(a, stream);
+  cudaError_t e = pass_counted_before(a.pass) ? cudaSuccess : launch_tile_counts(a, stream);
   if (e == cudaSuccess) e = launch_tile_scan(a, stream);
   if (e == cudaSuccess) e = launch_sort_scatter(a, stream);
   return e;
@@ -1050,7 +1095,9 @@ cudaError_t launch_sort_pass_seg(const SortPassArgs* a, int count, int scatter_t
     tiles[f] = a[f].n > 0 ? a[f].tiles : 0;
     scan[f] = a[f].n > 0 ? ((1 << a[f].bits) + 7) / 8 : 0;
   }
-  cudaError_t e = launch_seg(k_tile_counts_seg, a, tiles, count, kSortThreads, 0, stream);
+  cudaError_t e = count > 0 && pass_counted_before(a[0].pass)
+                      ? cudaSuccess
+                      : launch_seg(k_tile_counts_seg, a, tiles, count, kSortThreads, 0, stream);
   if (e == cudaSuccess) e = launch_seg(k_tile_scan_seg, a, scan, count, 256, 0, stream);
   if (e != cudaSuccess) return e;
   switch (scatter_threads) {
@@ -1127,7 +1174,8 @@ SortPassArgs slg_pass_args(int pass, const int32_t* xyz, int n, int bits, int ca
   a.n = n;
   a.bits = bits;
   a.tiles = (n + kSortTile - 1) / kSortTile;
-  a.counts = sb.tile_counts;
+  a.pass = pass;
+  a.counts = sb.tile_counts + size_t(pass) * sb.count_stride;
   a.sc = sc;
   if (pass == 0) {
     // y-slabs: keys are packed C1 codes, values input indices

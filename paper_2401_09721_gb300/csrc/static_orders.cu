@@ -30,7 +30,7 @@ constexpr size_t kOffKeys1 = align256(kOffKeys0 + kMaxPts * 4);
 constexpr size_t kOffVals0 = align256(kOffKeys1 + kMaxPts * 4);
 constexpr size_t kOffVals1 = align256(kOffVals0 + kMaxPts * 4);
 constexpr size_t kOffTileCounts = align256(kOffVals1 + kMaxPts * 4);
-constexpr size_t kOffPerm1 = align256(kOffTileCounts + size_t(kMaxRadix) * kMaxTiles * 4);
+constexpr size_t kOffPerm1 = align256(kOffTileCounts + size_t(kSlgPasses) * kMaxRadix * kMaxTiles * 4);
 constexpr size_t kOffRank1 = align256(kOffPerm1 + kMaxPts * 4);
 constexpr size_t kOffPk = align256(kOffRank1 + kMaxPts * 4);
 constexpr size_t kOffOrd23 = align256(kOffPk + kMaxPts * 4);
@@ -95,13 +95,14 @@ extern "C" fgbd_status fgbd_scan_orders_static(const int32_t* xyz, int64_t n64, 
     sb.vals[0] = reinterpret_cast<uint32_t*>(base + kOffVals0);
     sb.vals[1] = reinterpret_cast<uint32_t*>(base + kOffVals1);
     sb.tile_counts = reinterpret_cast<uint32_t*>(base + kOffTileCounts);
+    sb.count_stride = int(size_t(kMaxRadix) * kMaxTiles);
     GraphBufs gb{};
     gb.perm1 = reinterpret_cast<int32_t*>(base + kOffPerm1);
     gb.rank1 = reinterpret_cast<int32_t*>(base + kOffRank1);
     gb.pk = reinterpret_cast<uint32_t*>(base + kOffPk);
     gb.ord23 = reinterpret_cast<int32_t*>(base + kOffOrd23);
     gb.rank2 = reinterpret_cast<int32_t*>(base + kOffRank2);
-    if (launch_coord_hist(xyz, n, bits, sc, num_sms, st) != cudaSuccess) {
+    if (launch_coord_hist(xyz, n, bits, sc, &sb, num_sms, st) != cudaSuccess) {
       cudaGetLastError();
       return FGBD_ECUDA;
     }
