@@ -145,9 +145,10 @@ fgbd_status fgbd_params_default(fgbd_params* p);
 
 /* Create a context on the current CUDA device for frames of up to `capacity`
  * points (1 <= capacity < 2^30) and allocate all its device memory (about
- * 180 bytes per point).  `params` may be NULL for the defaults.  On success
- * *out owns the context; release it with fgbd_ctx_destroy.  A window w > 1
- * adds 24 (w - 1) bytes per point and a few MB of noise-estimate scratch.
+ * 205 bytes per point), zeroed once.  `params` may be NULL for the defaults.
+ * On success *out owns the context; release it with fgbd_ctx_destroy.  A
+ * window w > 1 adds 24 (w - 1) bytes per point (less the 24 of the stored
+ * window-1 filter weights) and a few MB of noise-estimate scratch.
  * Errors: FGBD_EINVAL (bad capacity or parameters), FGBD_ENOTIMPL (window
  * above FGBD_MAX_WINDOW, or FGBD_VARIANT_UNSORTED_PATCH with window > 1),
  * FGBD_ENOMEM, FGBD_ECUDA. */
