@@ -100,8 +100,20 @@ struct StepHead {
   int4 s;
 };
 
+// An iterate of an earlier step: through L1 (kL1) where every line this SM
+// could hold was final before the launch first read it - the stored steps of
+// the noise-estimate launch, each writing a slice of its own that is only read
+// after the next grid barrier - else from L2 (ping-pong buffers rewritten
+// within one launch, whose stale L1 lines another SM could still hold).
+template <bool kL1>
+__device__ __forceinline__ float4 ld_iterate(const float4* __restrict__ p) {
+  if constexpr (kL1) return __ldca(p);
+  else return __ldcg(p);
+}
+
+template <bool kL1 = false>
 __device__ __forceinline__ StepHead step_head(const FilterArgs& a, const float4* __restrict__ src, int k) {
-  return {src ? __ldcg(&src[k]) : x0_of(a, k), a.c4[k]};
+  return {src ? ld_iterate<kL1>(&src[k]) : x0_of(a, k), a.c4[k]};
 }
 
 // The six window-1 slots of sorted point k (C1 k - 1, k + 1, then the C2/C3
@@ -132,7 +144,7 @@ __device__ __forceinline__ void slots6(int k, int n, uint32_t wk, int4 s, int (&
 // steps of the same graph load them (kStore false with a.w4 set).  Every kernel
 // that takes a window-1 step uses this function, so a step gives the same bits
 // in all of them.
-template <bool kStore>
+template <bool kStore, bool kL1 = false>
 __device__ __forceinline__ float4 eq5_step(const FilterArgs& a, const float4* __restrict__ src, int k, int n,
                                            float cexp, const StepHead& h) {
   const float4 xk = h.xk;
@@ -142,7 +154,7 @@ __device__ __forceinline__ float4 eq5_step(const FilterArgs& a, const float4* __
   slots6(k, n, wk, h.s, nb, v);
   float4 xn[6];
 #pragma unroll
-  for (int j = 0; j < 6; ++j) xn[j] = v[j] ? (src ? __ldcg(&src[nb[j]]) : x0_of(a, nb[j])) : xk;
+  for (int j = 0; j < 6; ++j) xn[j] = v[j] ? (src ? ld_iterate<kL1>(&src[nb[j]]) : x0_of(a, nb[j])) : xk;
   float w[6];
   if (kStore || !a.w4) {
     const uint32_t ck = wk & kCoordMask;
@@ -317,8 +329,9 @@ __device__ __forceinline__ int speculative_steps(const FilterArgs& a, int depth,
     float4* dst = a.spec_x + size_t(t - 1) * size_t(a.cap);
     int32_t* z = a.spec_z + size_t(t - 1) * size_t(a.cap);
     for (int k = gtid; k < n; k += gstride) {
-      const StepHead h = step_head(a, src, k);
-      const float4 xo = t == 1 ? eq5_step<true>(a, src, k, n, cexp, h) : eq5_step<false>(a, src, k, n, cexp, h);
+      const StepHead h = step_head<true>(a, src, k);
+      const float4 xo =
+          t == 1 ? eq5_step<true, true>(a, src, k, n, cexp, h) : eq5_step<false, true>(a, src, k, n, cexp, h);
       dst[k] = xo;
       z[k] = int32_t((long long)sq3(src ? x0_of(a, k) : h.xk) - (long long)sq3(xo));
     }

@@ -735,6 +735,9 @@ __global__ void __launch_bounds__(kFinThreads) k_ne_finalize(int dtype, const do
 constexpr int kSpecThreads = 1024;
 constexpr int kSpecPadBytes = 100 * 1024;  // shared memory that makes a second block not fit on an SM
 
+// FUSE: the selection and filter follow in the same launch (a.fuse); a kernel
+// of its own, so that the plain launch carries none of their registers.
+template <bool FUSE>
 __global__ void __launch_bounds__(kSpecThreads, 1)
     k_ne_finalize_spec(int dtype, const double* __restrict__ f64_partials, int nblocks, DevScalars* __restrict__ sc,
                        double* __restrict__ sigma_out, FilterArgs a) {
@@ -747,8 +750,8 @@ __global__ void __launch_bounds__(kSpecThreads, 1)
     return;
   }
   uint32_t epoch = 0;
-  const int S = speculative_steps(a, a.spec_depth, 1, gridDim.x - 1, a.fuse != 0, epoch, &s_ok, &s_cexp, &s_go);
-  if (!a.fuse || S < 0) return;
+  const int S = speculative_steps(a, a.spec_depth, 1, gridDim.x - 1, FUSE, epoch, &s_ok, &s_cexp, &s_go);
+  if (!FUSE || S < 0) return;
   // sigma_est of block 0 (a bounded wait)
   if (threadIdx.x == 0) {
     const unsigned long long t0 = global_ns();
@@ -923,11 +926,18 @@ cudaError_t launch_ne_finalize(int dtype, const double* f64_partials, int nblock
                          sc, sigma_out);
   static std::atomic<unsigned long long> configured{0};  // the shared-memory limit is set once per device
   const cudaError_t e = once_per_device(configured, [] {
-    return cudaFuncSetAttribute(k_ne_finalize_spec, cudaFuncAttributeMaxDynamicSharedMemorySize, kSpecPadBytes);
+    cudaError_t r = cudaFuncSetAttribute(k_ne_finalize_spec<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         kSpecPadBytes);
+    if (r == cudaSuccess)
+      r = cudaFuncSetAttribute(k_ne_finalize_spec<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSpecPadBytes);
+    return r;
   });
   if (e != cudaSuccess) return e;
-  return launch_kernel(k_ne_finalize_spec, dim3(num_sms), dim3(kSpecThreads), kSpecPadBytes, stream, true, dtype,
-                       f64_partials, nblocks, sc, sigma_out, *spec);
+  if (spec->fuse)
+    return launch_kernel(k_ne_finalize_spec<true>, dim3(num_sms), dim3(kSpecThreads), kSpecPadBytes, stream, true,
+                         dtype, f64_partials, nblocks, sc, sigma_out, *spec);
+  return launch_kernel(k_ne_finalize_spec<false>, dim3(num_sms), dim3(kSpecThreads), kSpecPadBytes, stream, true,
+                       dtype, f64_partials, nblocks, sc, sigma_out, *spec);
 }
 
 }  // namespace fgbd

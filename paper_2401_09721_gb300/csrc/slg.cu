@@ -57,8 +57,8 @@ size_t scatter_smem_bytes(int threads) {
          (size_t(warps / 2) * kMaxRadix + 2 * size_t(kSortTile) + 2 * size_t(kMaxRadix) + warps + 1);
 }
 
-// The three coordinate histograms, one 1024-thread block per SM taking whole
-// 4096-point tiles of the input, merged with global atomics.  The y digits of
+// The three coordinate histograms, 1024-thread blocks (up to two per SM) taking
+// whole 4096-point tiles of the input, merged with global atomics.  The y digits of
 // each tile are also counted on their own: sort pass 0's tile counts (its
 // keys are the input's y digits in input order), so that pass needs no
 // counting launch.  Pass 1's tile counts, which the slab sort adds up, are
@@ -75,17 +75,36 @@ __device__ __forceinline__ void coord_hist_body(const HistArgs& a, int bid, int 
       a.counts1[i] = 0u;
   }
   const uint32_t m = uint32_t(radix) - 1u;
+  // four consecutive points a thread (a tile is kSortTile = 4 x 1024 points),
+  // read as three 16-byte loads where the array is aligned, all issued before
+  // the first shared-memory atomic
+  static_assert(kSortTile == 4 * 1024, "1024 threads take four points each");
+  const bool vec = (reinterpret_cast<uintptr_t>(a.xyz) & 15u) == 0;
   bool bad = false;
   for (int t = bid; t < tiles; t += nblk) {
     for (int d = threadIdx.x; d < radix; d += blockDim.x) ht[d] = 0;
     __syncthreads();
-    for (int i = t * kSortTile + int(threadIdx.x); i < min(a.n, (t + 1) * kSortTile); i += blockDim.x) {
-      const int xi = a.xyz[3 * size_t(i)], yi = a.xyz[3 * size_t(i) + 1], zi = a.xyz[3 * size_t(i) + 2];
-      bad |= (uint32_t(xi) > m) | (uint32_t(yi) > m) | (uint32_t(zi) > m);
-      atomicAdd(&h[0][uint32_t(xi) & m], 1u);
-      atomicAdd(&h[1][uint32_t(yi) & m], 1u);
-      atomicAdd(&h[2][uint32_t(zi) & m], 1u);
-      atomicAdd(&ht[uint32_t(yi) & m], 1u);
+    const int p0 = t * kSortTile + 4 * int(threadIdx.x);
+    int c[12];
+    if (vec && p0 + 4 <= a.n) {
+      const int4* q = reinterpret_cast<const int4*>(a.xyz + 3 * size_t(p0));
+      const int4 v0 = q[0], v1 = q[1], v2 = q[2];
+      c[0] = v0.x; c[1] = v0.y; c[2] = v0.z; c[3] = v0.w;
+      c[4] = v1.x; c[5] = v1.y; c[6] = v1.z; c[7] = v1.w;
+      c[8] = v2.x; c[9] = v2.y; c[10] = v2.z; c[11] = v2.w;
+    } else {
+#pragma unroll
+      for (int j = 0; j < 12; ++j) c[j] = p0 + j / 3 < a.n ? a.xyz[3 * size_t(p0) + j] : 0;
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      if (p0 + i >= a.n) break;
+      const uint32_t xi = uint32_t(c[3 * i]), yi = uint32_t(c[3 * i + 1]), zi = uint32_t(c[3 * i + 2]);
+      bad |= (xi > m) | (yi > m) | (zi > m);
+      atomicAdd(&h[0][xi & m], 1u);
+      atomicAdd(&h[1][yi & m], 1u);
+      atomicAdd(&h[2][zi & m], 1u);
+      atomicAdd(&ht[yi & m], 1u);
     }
     __syncthreads();
     if (a.counts0)
@@ -98,12 +117,12 @@ __device__ __forceinline__ void coord_hist_body(const HistArgs& a, int bid, int 
       if (h[c][d]) atomicAdd(&a.sc->chist[c][d], h[c][d]);
 }
 
-__global__ void __launch_bounds__(1024) k_coord_hist(HistArgs a) {
+__global__ void __launch_bounds__(1024, 2) k_coord_hist(HistArgs a) {
   pdl_wait();
   coord_hist_body(a, blockIdx.x, gridDim.x);
 }
 
-__global__ void __launch_bounds__(1024) k_coord_hist_seg(const __grid_constant__ Seg<HistArgs> s) {
+__global__ void __launch_bounds__(1024, 2) k_coord_hist_seg(const __grid_constant__ Seg<HistArgs> s) {
   pdl_wait();
   const int f = seg_frame(s, blockIdx.x);
   coord_hist_body(s.a[f], blockIdx.x - s.start[f], s.start[f + 1] - s.start[f]);
@@ -171,6 +190,16 @@ __device__ __forceinline__ void tile_scan_body(const SortPassArgs& a, int bid) {
   const int radix = 1 << a.bits;
   const int d = bid * 8 + (threadIdx.x >> 5);
   if (d >= radix) return;
+  uint32_t* r = a.counts + size_t(d) * a.tiles;
+  constexpr int kRun = 8;
+  // the first run of tile counts, loaded before the histogram so that the two
+  // sets of loads are in flight together
+  uint32_t c[kRun];
+#pragma unroll
+  for (int i = 0; i < kRun; ++i) {
+    const int t = lane * kRun + i;
+    c[i] = t < a.tiles ? r[t] : 0u;
+  }
   // the digit's bucket start: lane l sums the histogram entries 32l..32l+31
   // below d, read as eight independent 16-byte loads
   const uint4* hist4 = reinterpret_cast<const uint4*>(a.sc->chist[a.coord]);
@@ -184,17 +213,17 @@ __device__ __forceinline__ void tile_scan_body(const SortPassArgs& a, int bid) {
     }
   }
   base = warp_sum(base);
-  uint32_t* r = a.counts + size_t(d) * a.tiles;
-  constexpr int kRun = 8;
   for (int t0 = 0; t0 < a.tiles; t0 += 32 * kRun) {
-    uint32_t c[kRun];
+    if (t0 > 0) {
+#pragma unroll
+      for (int i = 0; i < kRun; ++i) {
+        const int t = t0 + lane * kRun + i;
+        c[i] = t < a.tiles ? r[t] : 0u;
+      }
+    }
     uint32_t own = 0;
 #pragma unroll
-    for (int i = 0; i < kRun; ++i) {
-      const int t = t0 + lane * kRun + i;
-      c[i] = t < a.tiles ? r[t] : 0u;
-      own += c[i];
-    }
+    for (int i = 0; i < kRun; ++i) own += c[i];
     uint32_t x = own;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -972,7 +1001,10 @@ __global__ void __launch_bounds__(256) k_orders_export(int n, int cap, const int
 
 namespace {
 // blocks of one frame's launch of each kernel (the same in both paths)
-int coord_hist_blocks(int n, int num_sms) { return n <= 0 ? 0 : std::max(1, std::min((n + 1023) / 1024, num_sms)); }
+// one 4096-point tile a block, up to two resident blocks per SM
+int coord_hist_blocks(int n, int num_sms) {
+  return n <= 0 ? 0 : std::max(1, std::min((n + kSortTile - 1) / kSortTile, 2 * num_sms));
+}
 int link_gx(int n, int num_sms) {
   // the three codes' blocks together fill the GPU once (6 resident blocks of 256 threads per SM)
   return std::max(1, std::min((n + kLinkThreads * kLinkPerLane - 1) / (kLinkThreads * kLinkPerLane), num_sms * 2));
@@ -1034,7 +1066,7 @@ cudaError_t launch_coord_hist(const int32_t* xyz, int n, int bits, DevScalars* s
                               cudaStream_t stream) {
   if (n <= 0) return cudaSuccess;
   const HistArgs h = sb ? hist_args(xyz, n, bits, sc, *sb) : HistArgs{xyz, n, bits, sc, nullptr, nullptr};
-  // one large block per SM: few blocks keep the global atomics of the final merge few
+  // one block a tile, two per SM: every tile of a 1M-point frame in one wave
   return launch_kernel(k_coord_hist, dim3(coord_hist_blocks(n, num_sms)), dim3(1024), 0, stream, false, h);
 }
 
