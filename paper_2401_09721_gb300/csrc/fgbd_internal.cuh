@@ -79,7 +79,7 @@ struct DevScalars {
   unsigned long long ysq_all;
   unsigned long long n_keep;
   unsigned long long sumsq[kQCap + 1];
-  long long spec_keep[kSpecMax + 1];  // over the kept points: sum of y^2 - x_q^2 (fixed point), q = 1..
+  long long spec_keep[kSpecMax + 1];  // over the kept points: sum of x_q^2 (fixed point), stored steps q = 1..
   long long spec_all[kSpecMax + 1];   // the same over every point
   uint32_t barrier;
   uint32_t sel_end_;
@@ -381,7 +381,7 @@ struct FilterArgs {
   // select mode: the first spec_depth steps were stored before sigma_est was known
   int spec_depth;          // 0: none
   float4* spec_x;          // [kSpecMax][cap]: x_1 .. x_S
-  int32_t* spec_z;         // [kSpecMax][cap]: per point sum_c (y^2 - x_q^2), fixed point
+  int32_t* spec_z;         // [kSpecMax][cap]: per point sum_c x_q^2, fixed point
   int cap;                 // row stride of spec_x / spec_z, a multiple of 64
   int fuse;                // noise-estimate launch: select and filter too, once sigma_est is known
   uint8_t* keep8;          // select mode: the FSLR keep flag of every sorted point

@@ -307,8 +307,9 @@ __device__ __forceinline__ float4 eq5_step_nx(const FilterArgs& a, const float4*
   else return eq5_step_wide<NX>(a, src, k, n, cexp, h);
 }
 
-// The first steps x_1, x_2, ... and each point's Eq. 6 term sum_c (y^2 - x_q^2)
-// in fixed point beside them, by the blocks [first, first + members) of a
+// The first steps x_1, x_2, ... and beside them each point's sum_c x_q^2 in
+// fixed point (the selection subtracts these sums from those of y^2 for
+// Eq. 6), by the blocks [first, first + members) of a
 // cooperative grid (they need the graph and the colours only, not sigma_est):
 // `depth` steps, or, with `until_sigma`, fewer once sigma_est is published
 // (sc->sigma_ready).  Block `first` reads that flag before each grid barrier
@@ -333,7 +334,7 @@ __device__ __forceinline__ int speculative_steps(const FilterArgs& a, int depth,
       const float4 xo =
           t == 1 ? eq5_step<true, true>(a, src, k, n, cexp, h) : eq5_step<false, true>(a, src, k, n, cexp, h);
       dst[k] = xo;
-      z[k] = int32_t((long long)sq3(src ? x0_of(a, k) : h.xk) - (long long)sq3(xo));
+      z[k] = int32_t(sq3(xo));
     }
     const bool ask = until_sigma && t < depth;
     if (ask && blockIdx.x == first && threadIdx.x == 0) sc->spec_go[t] = ld_acquire_u32(&sc->sigma_ready) ? 0u : 1u;

@@ -5,14 +5,15 @@
 //
 //   phase 0   the FSLR keep flag of each point (spread <= 2 sigma_est) goes to
 //             keep8; the kept power sum y^2 and the kept count are reduced, and
-//             so are the stored steps' per-point Eq. 6 terms y^2 - x_q^2;
+//             so are the stored steps' per-point power sums x_q^2;
 //             x_0 = y is written unless steps are stored.
 //   J(1..S)   from those sums, by thread 0 of every block (the same values
 //             everywhere: the sums are exact integers).
 //   step t    x_t = x_{t-1}/2 + (sum_j e_j x_{t-1}[j]) / (2 sum_j e_j) with
 //             e_j = exp(-(d2_j - min_j d2_j) / sigma_g^2) (eq5_step): the rows
-//             of D^{-1} W of Eq. 4, computed on the fly from the neighbours'
-//             coordinates (carried in x.w), so no weight array is read.
+//             of D^{-1} W of Eq. 4, normalised once per graph by step 1 (from
+//             the neighbours' coordinates, carried in x.w) and read back by the
+//             later steps.
 //             In select mode the kept power sum x_t^2 is reduced and, after a
 //             grid barrier, J(t) = |sigma^2 - (sum y^2 - sum x_t^2)/(3 N_sel)|;
 //             the search stops at the first t with J(t) >= J(t-1), keeping
@@ -374,7 +375,7 @@ __device__ __forceinline__ void block_sums(unsigned long long (&v)[K], unsigned 
   __syncthreads();
 }
 
-constexpr int kSums = 3 + 2 * kSpecMax;  // kept y^2, all y^2, kept count, then per stored step kept and all terms
+constexpr int kSums = 3 + 2 * kSpecMax;  // kept y^2, all y^2, kept count, then per stored step kept and all x_q^2
 
 // The selection and filter for the blocks [first, first + members) of a
 // cooperative grid of THREADS-thread blocks, from S stored steps (0: none),
@@ -463,7 +464,7 @@ __device__ __forceinline__ void select_filter(const FilterArgs& a, int S, int fi
       }
     }
   }
-  // the stored steps' Eq. 6 terms (a second pass over this thread's own points and keep flags)
+  // the stored steps' power sums (a second pass over this thread's own points and keep flags)
   if (S > 0) {
     for (int k0 = 4 * gtid; k0 < n; k0 += 4 * gstride) {
       const bool full = k0 + 4 <= n;
@@ -551,7 +552,8 @@ __device__ __forceinline__ void select_filter(const FilterArgs& a, int S, int fi
       for (int t = 1; t <= min(S, q_limit); ++t) {
         const unsigned long long* src = reinterpret_cast<const unsigned long long*>(
             keep_all ? &sc->spec_all[t] : &sc->spec_keep[t]);
-        const double lost = double((long long)ld_relaxed_u64(src)) * (1.0 / double(1 << kSqShift));
+        // sum of y^2 - x_t^2 over the points of Eq. 6: exact in two's complement
+        const double lost = double((long long)(ysq - ld_relaxed_u64(src))) * (1.0 / double(1 << kSqShift));
         const double J = fabs(sigma * sigma - lost / (3.0 * nsel));
         if (gtid == 0) {
           sc->J[t] = J;
