@@ -485,8 +485,8 @@ def algorithmic_bytes(name, n, extra_steps=0.0, out_bytes=3):
     """Compulsory DRAM bytes of one launch: the per-point figure of each kernel times n."""
     per_point = {
         "slg_hist": 12,                                   # xyz
-        # digit counts: the keys of the pass (pass 0 reads xyz)
-        "slg_counts0": 12, "slg_counts1": 4, "slg_counts2": 4,
+        # digit counts of pass 2 (passes 0 and 1 are counted by the histogram and the slab sort)
+        "slg_counts2": 4,
         # scatter: keys and values in, keys and values (or the final arrays) out.
         # pass 0 (y-slabs) reads xyz; the slab sort reads the y-ordered pairs and
         # writes the C3 order; pass 1 (C1 on z) writes packed codes, input
@@ -504,9 +504,10 @@ def algorithmic_bytes(name, n, extra_steps=0.0, out_bytes=3):
         return per_point[name] * n
     if name == "ne_finalize":
         # the filter steps stored by the estimate launch (its eigen block moves no bytes):
-        # per step x in 16 (or y 4 + codes 4), c4 16, the six normalised weights 24
-        # (written by step 1, read by the later steps), x out 16, Eq. 6 term 4, y 4
-        return SPEC_STEPS * 80 * n
+        # step 1 reads x_0 (y 4 + codes 4) and c4 16, writes the six normalised weights 24,
+        # x_1 16 and its power sum 4; each later step reads x 16, c4 16 and the weights 24,
+        # writes x 16 and its power sum 4
+        return (68 + 76 * (SPEC_STEPS - 1)) * n
     if name == "filter_select":
         # keep flags: y 4, spread 4, keep 1; the stored steps' Eq. 6 terms 4 each and keep 1;
         # ordinary steps beyond the stored ones 72 each (x in, c4, weights, x out);

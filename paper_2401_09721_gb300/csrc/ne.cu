@@ -7,8 +7,9 @@
 //   exactly 6 neighbours contributes the patch a_i = [f_i, f_n1, ..., f_n6],
 //   neighbours in increasing distance (ties by offset (dz, dy, dx), then
 //   index), to the first and second moments sum a and sum a a^T.  uint8
-//   colours are centred on 128 and kept as int8, so the moments are exact
-//   integer sums (dp4a over 4 patches per instruction, int64 accumulation).
+//   colours are centred on 128 (exact in float16), so the moments are exact
+//   integer sums: mma.sync products with float32 partial sums, moved to int64
+//   before they can lose a bit (gram_mma.cuh).
 // k_ne_finalize: one block.  Sigma = S2/N - mu mu^T in float64; float32
 //   eigenvector estimates from a Householder tridiagonalisation, Sturm
 //   multisection and inverse iteration (tridiag.cuh); each eigenvalue is then
@@ -141,15 +142,6 @@ struct NbKey<1> {
   float r, g, b;
 };
 
-template <int DT>
-__device__ __forceinline__ void cswap(NbKey<DT>& a, NbKey<DT>& b) {
-  const bool sw = (b.key < a.key) || (b.key == a.key && b.idx < a.idx);
-  if (sw) {
-    const NbKey<DT> t = a;
-    a = b;
-    b = t;
-  }
-}
 
 constexpr int kNeWarps = kNeThreads / 32;
 // uint8 colours: the batch's patches as float16, entry-major: rows 0..20 the
@@ -279,23 +271,23 @@ __device__ __forceinline__ bool point_patch(int k, int n, int bits, int lane, co
     e[j].key = (d2 << 33) | ((unsigned long long)(dz + 1024) << 22) | ((unsigned long long)(dy + 1024) << 11) |
                (unsigned long long)(dx + 1024);
   }
-  // a sorting network for 6 elements with 12 comparators in 5 layers (the
-  // keys with their index are a strict order, so the result is the unique
-  // sorted one).  Without it (the "w/o sort" ablation) the entries stay in
-  // link order: C1 prev, C1 next, C2 prev, C2 next, C3 prev, C3 next.
+  // the place of each neighbour in the patch: its rank in the strict order
+  // (key, index), from the 15 pairwise comparisons, so the colours are written
+  // straight to their rows (the unique sorted order).  Without sorting (the
+  // "w/o sort" ablation) the entries stay in link order: C1 prev, C1 next,
+  // C2 prev, C2 next, C3 prev, C3 next.
+  int rk[6] = {0, 1, 2, 3, 4, 5};
   if (sorted_patches) {
-    cswap(e[0], e[5]);
-    cswap(e[1], e[3]);
-    cswap(e[2], e[4]);
-    cswap(e[1], e[2]);
-    cswap(e[3], e[4]);
-    cswap(e[0], e[3]);
-    cswap(e[2], e[5]);
-    cswap(e[0], e[1]);
-    cswap(e[2], e[3]);
-    cswap(e[4], e[5]);
-    cswap(e[1], e[2]);
-    cswap(e[3], e[4]);
+#pragma unroll
+    for (int j = 0; j < 6; ++j) rk[j] = 0;
+#pragma unroll
+    for (int i = 0; i < 6; ++i)
+#pragma unroll
+      for (int j = i + 1; j < 6; ++j) {
+        const bool j_first = (e[j].key < e[i].key) || (e[j].key == e[i].key && e[j].idx < e[i].idx);
+        rk[i] += j_first;
+        rk[j] += !j_first;
+      }
   }
   if (DT == 0) {
     // entry r of the patch, centred on 128 (exact in float16)
@@ -305,9 +297,10 @@ __device__ __forceinline__ bool point_patch(int k, int n, int bits, int lane, co
 #pragma unroll
     for (int j = 0; j < 6; ++j) {
       const uint32_t c = reinterpret_cast<NbKey<0>&>(e[j]).col;
-      ath[(3 + 3 * j) * kHRow + lane] = __int2half_rn(int(c & 255u) - 128);
-      ath[(4 + 3 * j) * kHRow + lane] = __int2half_rn(int((c >> 8) & 255u) - 128);
-      ath[(5 + 3 * j) * kHRow + lane] = __int2half_rn(int((c >> 16) & 255u) - 128);
+      __half* row = ath + (3 + 3 * rk[j]) * kHRow + lane;
+      row[0] = __int2half_rn(int(c & 255u) - 128);
+      row[kHRow] = __int2half_rn(int((c >> 8) & 255u) - 128);
+      row[2 * kHRow] = __int2half_rn(int((c >> 16) & 255u) - 128);
     }
   } else {
     atf[0 * kRowFloats + lane] = ownr - 128.f;
@@ -316,9 +309,10 @@ __device__ __forceinline__ bool point_patch(int k, int n, int bits, int lane, co
 #pragma unroll
     for (int j = 0; j < 6; ++j) {
       const NbKey<1>& f = reinterpret_cast<NbKey<1>&>(e[j]);
-      atf[(3 + 3 * j) * kRowFloats + lane] = f.r - 128.f;
-      atf[(4 + 3 * j) * kRowFloats + lane] = f.g - 128.f;
-      atf[(5 + 3 * j) * kRowFloats + lane] = f.b - 128.f;
+      float* row = atf + (3 + 3 * rk[j]) * kRowFloats + lane;
+      row[0] = f.r - 128.f;
+      row[kRowFloats] = f.g - 128.f;
+      row[2 * kRowFloats] = f.b - 128.f;
     }
   }
   return true;

@@ -525,15 +525,48 @@ __device__ __forceinline__ void slab_sort_body(const SlabArgs& sa, int yv) {
   const int half = 16 * (warp & 1);
 
   if (size <= uint32_t(kSlabMax)) {
+    // the slab's z and x extents: each pass ranks the coordinate minus its
+    // smallest value in the slab, with as many digit bits as the extent needs
+    // (the order is the same; the digit counters and ballots are fewer)
+    __shared__ uint32_t s_ext[4][kSlabWarps];
+    uint32_t zlo = m, zhi = 0, xlo = m, xhi = 0;
     for (uint32_t i = tid; i < size; i += kSlabThreads) {
-      s_keys[i] = keys_in[start + i];
+      const uint32_t key = keys_in[start + i];
+      s_keys[i] = key;
       s_vals[i] = vals_in[start + i];
+      const uint32_t z = (key >> (2 * bits)) & m, x = key & m;
+      zlo = min(zlo, z);
+      zhi = max(zhi, z);
+      xlo = min(xlo, x);
+      xhi = max(xhi, x);
+    }
+    zlo = __reduce_min_sync(0xffffffffu, zlo);
+    zhi = __reduce_max_sync(0xffffffffu, zhi);
+    xlo = __reduce_min_sync(0xffffffffu, xlo);
+    xhi = __reduce_max_sync(0xffffffffu, xhi);
+    if (lane == 0) {
+      s_ext[0][warp] = zlo;
+      s_ext[1][warp] = zhi;
+      s_ext[2][warp] = xlo;
+      s_ext[3][warp] = xhi;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int w = 0; w < kSlabWarps; ++w) {
+      zlo = min(zlo, s_ext[0][w]);
+      zhi = max(zhi, s_ext[1][w]);
+      xlo = min(xlo, s_ext[2][w]);
+      xhi = max(xhi, s_ext[3][w]);
     }
     const int chunk = int((size + 32 * kSlabWarps - 1) / (32 * kSlabWarps)) * 32;  // positions per warp
     const int rounds = chunk / 32;                                                 // <= kSlabKpt
     for (int pass = 0; pass < 2; ++pass) {
       const int shift = pass == 0 ? 2 * bits : 0;  // z, then x
-      for (int i = tid; i < kSlabPairWords * radix; i += kSlabThreads) cnt[i] = 0;
+      const uint32_t lo = pass == 0 ? zlo : xlo, ext = (pass == 0 ? zhi : xhi) - lo;
+      const int dbits = max(1, 32 - __clz(int(ext)));  // digit bits of this pass (<= bits)
+      const int pradix = 1 << dbits;
+      uint32_t* pw = cnt + (warp >> 1) * pradix;       // this warp pair's counters
+      for (int i = tid; i < kSlabPairWords * pradix; i += kSlabThreads) cnt[i] = 0;
       __syncthreads();
       uint32_t k[kSlabKpt], v[kSlabKpt], rk[kSlabKpt];
 #pragma unroll
@@ -546,7 +579,7 @@ __device__ __forceinline__ void slab_sort_body(const SlabArgs& sa, int yv) {
             k[j] = s_keys[pos];
             v[j] = s_vals[pos];
           }
-          rk[j] = warp_rank(valid, (k[j] >> shift) & m, bits, wh, half, lane);
+          rk[j] = warp_rank(valid, ((k[j] >> shift) & m) - lo, dbits, pw, half, lane);
           __syncwarp();
         }
       }
@@ -555,13 +588,13 @@ __device__ __forceinline__ void slab_sort_body(const SlabArgs& sa, int yv) {
       uint32_t tot[kSlabDigits], own = 0;
 #pragma unroll
       for (int i = 0; i < kSlabDigits; ++i) {
-        tot[i] = digit_warp_offsets(cnt, radix, kSlabDigits * tid + i);
+        tot[i] = digit_warp_offsets(cnt, pradix, kSlabDigits * tid + i);
         own += tot[i];
       }
       uint32_t ts = slab_block_scan(own, s_warp, nullptr);
 #pragma unroll
       for (int i = 0; i < kSlabDigits; ++i) {
-        if (kSlabDigits * tid + i < radix) s_start[kSlabDigits * tid + i] = ts;
+        if (kSlabDigits * tid + i < pradix) s_start[kSlabDigits * tid + i] = ts;
         ts += tot[i];
       }
       __syncthreads();
@@ -570,8 +603,8 @@ __device__ __forceinline__ void slab_sort_body(const SlabArgs& sa, int yv) {
         if (j < rounds) {
           const uint32_t pos = uint32_t(warp * chunk + j * 32 + lane);
           if (pos < size) {
-            const uint32_t d = (k[j] >> shift) & m;
-            const uint32_t lp = s_start[d] + ((wh[d] >> half) & 0xffffu) + rk[j];
+            const uint32_t d = ((k[j] >> shift) & m) - lo;
+            const uint32_t lp = s_start[d] + ((pw[d] >> half) & 0xffffu) + rk[j];
             if (lp < size) {
               s_keys[lp] = k[j];
               s_vals[lp] = v[j];
@@ -593,14 +626,16 @@ __device__ __forceinline__ void slab_sort_body(const SlabArgs& sa, int yv) {
       const int tiles = (n + kSortTile - 1) / kSortTile;
       static_assert(kSlabMax <= kSortTile && 2 * kMaxRadix <= kSlabPairWords * kMaxRadix,
                     "a slab spans at most two tiles, counted in the digit counter words");
-      for (int i = tid; i < 2 * radix; i += kSlabThreads) cnt[i] = 0;
+      // (z digits zlo .. zhi only)
+      const int zr = int(zhi - zlo) + 1;
+      for (int i = tid; i < 2 * zr; i += kSlabThreads) cnt[i] = 0;
       __syncthreads();
       for (uint32_t i = tid; i < size; i += kSlabThreads)
-        atomicAdd(&cnt[((start + i) / kSortTile - t0) * radix + ((s_keys[i] >> (2 * bits)) & m)], 1u);
+        atomicAdd(&cnt[((start + i) / kSortTile - t0) * zr + (((s_keys[i] >> (2 * bits)) & m) - zlo)], 1u);
       __syncthreads();
-      for (int i = tid; i < 2 * radix; i += kSlabThreads) {
-        const uint32_t c = cnt[i], t = t0 + uint32_t(i / radix);
-        if (c && t < uint32_t(tiles)) atomicAdd(&sa.counts1[size_t(i % radix) * tiles + t], c);
+      for (int i = tid; i < 2 * zr; i += kSlabThreads) {
+        const uint32_t c = cnt[i], t = t0 + uint32_t(i / zr);
+        if (c && t < uint32_t(tiles)) atomicAdd(&sa.counts1[size_t(zlo + uint32_t(i % zr)) * tiles + t], c);
       }
     }
     return;
