@@ -453,14 +453,17 @@ fgbd_status do_estimate(fgbd_ctx* ctx, const void* rgb, int32_t dtype, double* s
       FGBD_LAUNCH(ctx, "gather_colors", st,
                   launch_gather_colors(rgb, dtype, n, ctx->gb.perm1, ctx->y8, ctx->yf, st));
     nblocks = ne_moment_blocks(n, ctx->num_sms);
+    // (with x_0 of the filter steps into ctx->x0, which step 1 then reads as one 16-byte load a point)
     FGBD_LAUNCH(ctx, "ne_moments", st,
                 launch_ne_moments(n, ctx->params.bits, dtype, ctx->gb, ctx->y8, ctx->yf, ctx->spread, ctx->f64part,
                                   ctx->sc, ctx->num_sms, true,
-                                  (ctx->params.variant & FGBD_VARIANT_UNSORTED_PATCH) == 0, st));
+                                  (ctx->params.variant & FGBD_VARIANT_UNSORTED_PATCH) == 0, st,
+                                  speculate ? ctx->x0 : nullptr));
   }
   // the same launch stores the first filter steps of these colours on the other SMs
   FilterArgs spec = filter_args(ctx, 0, 0, nullptr, fuse ? fuse_out : nullptr, fuse ? fuse_out_dtype : 0, dtype);
   spec.spec_depth = speculate ? std::min(kSpecMax, int(ctx->params.q_max)) : 0;
+  spec.x0 = speculate && n > 0 ? ctx->x0 : nullptr;
   ctx->spec_depth = n > 0 && ctx->num_sms >= 2 ? spec.spec_depth : 0;
   const bool fused = fuse && ctx->spec_depth > 0;
   spec.fuse = fused ? 1 : 0;

@@ -253,6 +253,7 @@ struct MomentArgs {
   int moments;
   int sorted_patches;
   struct DevScalars* sc;
+  float4* x0;  // if set: also x_0 of the filter steps, (r, g, b, packed code) per sorted point
 };
 struct ZeroArgs {
   uint32_t* p;
@@ -314,10 +315,11 @@ cudaError_t launch_link_wide(int n, int bits, int cap, int window, bool same_lin
 
 cudaError_t launch_gather_colors(const void* rgb, int dtype, int n, const int32_t* perm1,
                                  uint32_t* y8, float4* yf, cudaStream_t stream);
+// x0: if set, the launch also writes x_0 of the filter steps (colours and packed code)
 cudaError_t launch_ne_moments(int n, int bits, int dtype, const GraphBufs& gb, const uint32_t* y8,
                               const float4* yf, float* spread, double* f64_partials,
                               DevScalars* sc, int num_sms, bool moments, bool sorted_patches,
-                              cudaStream_t stream);
+                              cudaStream_t stream, float4* x0 = nullptr);
 // spec: if not null (and spec->spec_depth > 0), the same launch also takes the
 // first spec_depth filter steps on the other SMs (one block per SM)
 cudaError_t launch_ne_finalize(int dtype, const double* f64_partials, int nblocks,
@@ -380,6 +382,7 @@ struct FilterArgs {
   DevScalars* sc;
   // select mode: the first spec_depth steps were stored before sigma_est was known
   int spec_depth;          // 0: none
+  const float4* x0;        // x_0 as the moments launch wrote it (r, g, b, packed code), or null: from y8/yf, pk
   float4* spec_x;          // [kSpecMax][cap]: x_1 .. x_S
   int32_t* spec_z;         // [kSpecMax][cap]: per point sum_c x_q^2, fixed point
   int cap;                 // row stride of spec_x / spec_z, a multiple of 64

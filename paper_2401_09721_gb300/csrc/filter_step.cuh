@@ -326,7 +326,7 @@ __device__ __forceinline__ int speculative_steps(const FilterArgs& a, int depth,
   const float cexp = block_cexp(sc, s_cexp);
   int stored = depth;
   for (int t = 1; t <= depth; ++t) {
-    const float4* src = t == 1 ? nullptr : a.spec_x + size_t(t - 2) * size_t(a.cap);
+    const float4* src = t == 1 ? a.x0 : a.spec_x + size_t(t - 2) * size_t(a.cap);
     float4* dst = a.spec_x + size_t(t - 1) * size_t(a.cap);
     int32_t* z = a.spec_z + size_t(t - 1) * size_t(a.cap);
     for (int k = gtid; k < n; k += gstride) {

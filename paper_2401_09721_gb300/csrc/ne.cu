@@ -161,7 +161,8 @@ template <int DT>
 __device__ __forceinline__ bool point_patch(int k, int n, int bits, int lane, const uint32_t* __restrict__ pk,
                                             const int4* __restrict__ c4, const uint32_t* __restrict__ y8,
                                             const float4* __restrict__ yf, float* __restrict__ spread,
-                                            bool moments, bool sorted_patches, __half* ath, float* atf) {
+                                            float4* __restrict__ x0, bool moments, bool sorted_patches, __half* ath,
+                                            float* atf) {
   int nb[6];
   bool v[6];
   const uint32_t pkk = pk[k];  // packed code, with the same-line variant's missing-C1-link bits
@@ -204,6 +205,9 @@ __device__ __forceinline__ bool point_patch(int k, int n, int bits, int lane, co
   float ownr = 0.f, owng = 0.f, ownb = 0.f;
   if (DT == 0) {
     own8 = y8[k];
+    if (x0)
+      x0[k] = make_float4(float(own8 & 255u), float((own8 >> 8) & 255u), float((own8 >> 16) & 255u),
+                          __uint_as_float(pkk));
     int sr = int(own8 & 255u), sg = int((own8 >> 8) & 255u), sb = int((own8 >> 16) & 255u);
     int qr = sr * sr, qg = sg * sg, qb = sb * sb;
 #pragma unroll
@@ -231,6 +235,7 @@ __device__ __forceinline__ bool point_patch(int k, int n, int bits, int lane, co
     ownr = o.x;
     owng = o.y;
     ownb = o.z;
+    if (x0) x0[k] = make_float4(ownr, owng, ownb, __uint_as_float(pkk));
     float mr = ownr, mg = owng, mb = ownb;
 #pragma unroll
     for (int j = 0; j < 6; ++j) {
@@ -381,7 +386,8 @@ __device__ __forceinline__ void ne_moments_body(const MomentArgs& ma, int bid, i
     const int k = base + lane;
     bool has = false;
     if (k < n)
-      has = point_patch<DT>(k, n, bits, lane, pk, c4, y8, yf, spread, moments != 0, sorted_patches != 0, ath, atf);
+      has = point_patch<DT>(k, n, bits, lane, pk, c4, y8, yf, spread, ma.x0, moments != 0, sorted_patches != 0, ath,
+                            atf);
     if (!moments) continue;
     if (DT == 0) {
       if (!has) {
@@ -899,16 +905,18 @@ int ne_moment_blocks(int n, int num_sms) {
 
 MomentArgs moment_args(int n, int bits, const GraphBufs& gb, const uint32_t* y8, const float4* yf, float* spread,
                        double* f64_partials, bool moments, bool sorted_patches, DevScalars* sc) {
-  return MomentArgs{n, bits, gb.pk, gb.c4, y8, yf, spread, f64_partials, moments ? 1 : 0, sorted_patches ? 1 : 0, sc};
+  return MomentArgs{n,  bits,         gb.pk, gb.c4, y8, yf, spread, f64_partials, moments ? 1 : 0, sorted_patches ? 1 : 0,
+                    sc, nullptr};
 }
 
 cudaError_t launch_ne_moments(int n, int bits, int dtype, const GraphBufs& gb, const uint32_t* y8,
                               const float4* yf, float* spread, double* f64_partials,
                               DevScalars* sc, int num_sms, bool moments, bool sorted_patches,
-                              cudaStream_t stream) {
+                              cudaStream_t stream, float4* x0) {
   if (n <= 0) return cudaSuccess;
   const int grid = ne_moment_blocks(n, num_sms);
-  const MomentArgs a = moment_args(n, bits, gb, y8, yf, spread, f64_partials, moments, sorted_patches, sc);
+  MomentArgs a = moment_args(n, bits, gb, y8, yf, spread, f64_partials, moments, sorted_patches, sc);
+  a.x0 = x0;
   if (dtype == 0) return launch_kernel(k_ne_moments<0>, dim3(grid), dim3(kNeThreads), 0, stream, false, a);
   return launch_kernel(k_ne_moments<1>, dim3(grid), dim3(kNeThreads), 0, stream, false, a);
 }
