@@ -329,8 +329,13 @@ __device__ __forceinline__ int speculative_steps(const FilterArgs& a, int depth,
     const float4* src = t == 1 ? a.x0 : a.spec_x + size_t(t - 2) * size_t(a.cap);
     float4* dst = a.spec_x + size_t(t - 1) * size_t(a.cap);
     int32_t* z = a.spec_z + size_t(t - 1) * size_t(a.cap);
+    // each point's own iterate and slots are loaded one trip ahead, so that
+    // only the neighbour loads wait on the point before them
+    StepHead next{};
+    if (gtid < n) next = step_head<true>(a, src, gtid);
     for (int k = gtid; k < n; k += gstride) {
-      const StepHead h = step_head<true>(a, src, k);
+      const StepHead h = next;
+      if (k + gstride < n) next = step_head<true>(a, src, k + gstride);
       const float4 xo =
           t == 1 ? eq5_step<true, true>(a, src, k, n, cexp, h) : eq5_step<false, true>(a, src, k, n, cexp, h);
       dst[k] = xo;

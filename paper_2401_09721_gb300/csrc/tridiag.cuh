@@ -7,8 +7,10 @@
 // eigenvalues far inside the noise estimate's tolerance.  The vectors come
 // from the textbook route for a small dense symmetric matrix, in float32:
 //   1. Householder reduction to tridiagonal form T = Q^T A Q (D - 2
-//      reflections H_k = I - u_k u_k^T / h_k), by one warp holding the rows of
-//      A in registers;
+//      reflections H_k = I - u_k u_k^T / h_k), the rows of A in registers:
+//      for D <= 32 spread over the block's warps (lane j holds column j), so
+//      the products of each step are warp reductions side by side; for
+//      larger D in one warp;
 //   2. the eigenvalues of T by Sturm-count multisection (every participating
 //      thread counts at its own point, so each pass narrows every bracket at
 //      once; no iteration depends on convergence);
@@ -92,132 +94,227 @@ __device__ void eig_vectors_f32(const float* __restrict__ As, TridiagSmem<D, NT>
   const int lane = tid & 31;
   constexpr unsigned kFull = 0xffffffffu;
 
-  // ---- 1. Householder reduction, warp 0; lane l holds rows l, l + 32
-  if (tid < 32) {
-    float a[R][D];
-    float scale = 0.f;
+  // ---- 1. Householder reduction.  D <= 32: every warp of the block holds
+  // rows of A (row i in warp i mod W, lane j its column j), so each step's
+  // products are warp reductions running side by side, with two barriers a
+  // step; D > 32: warp 0 alone, a row of A a lane (two for D > 32).
+  if constexpr (D <= 32) {
+    constexpr int W = (NT / 32) < D ? (NT / 32) : D;  // warps holding rows
+    constexpr int RPW = (D + W - 1) / W;              // rows a warp holds
+    const int warp = tid >> 5;
+    float a[RPW];
 #pragma unroll
-    for (int r = 0; r < R; ++r) {
-      const int row = r * 32 + lane;
-#pragma unroll
-      for (int j = 0; j < D; ++j) a[r][j] = row < D ? As[row * D + j] : 0.f;
-#pragma unroll
-      for (int j = 0; j < D; ++j)
-        if (row == j) scale = fmaxf(scale, fabsf(a[r][j]));
+    for (int r = 0; r < RPW; ++r) {
+      const int row = warp + r * W;
+      a[r] = (warp < W && row < D && lane < D) ? As[row * D + lane] : 0.f;
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) scale = fmaxf(scale, __shfl_xor_sync(kFull, scale, o));
+    float scale = 0.f;
+    for (int j = 0; j < D; ++j) scale = fmaxf(scale, fabsf(As[j * D + j]));
     const float skip = 1e-12f * scale;  // a column below this size is taken as already reduced
 #pragma unroll 1
     for (int k = 0; k + 2 < D; ++k) {
-      // column k of A, below the diagonal, read as row k (A is symmetric):
-      // its owner lane publishes the row and |x|^2
+      // the owner of row k (= column k below the diagonal, A being symmetric)
+      // forms u = x - alpha e_1 with alpha = -sign(x_0) |x|, so |u|^2 = 2 h
+      if (warp == k % W) {
+        float ak = 0.f;
 #pragma unroll
-      for (int r = 0; r < R; ++r) {
-        if (r * 32 + lane == k) {
-          float t0 = 0.f, t1 = 0.f;
+        for (int r = 0; r < RPW; ++r)
+          if (r == k / W) ak = a[r];
+        const float v = lane > k && lane < D ? ak : 0.f;
+        float xs = v * v;
 #pragma unroll
-          for (int j = 0; j < D; ++j) {
-            w.rk[j] = a[r][j];
-            const float v = j > k ? a[r][j] : 0.f;
-            if (j & 1) t1 = fmaf(v, v, t1);
-            else t0 = fmaf(v, v, t0);
-          }
-          w.rk[D] = t0 + t1;
+        for (int o = 16; o > 0; o >>= 1) xs += __shfl_xor_sync(kFull, xs, o);
+        const float x0 = __shfl_sync(kFull, v, k + 1);
+        const float nx = sqrtf(xs);
+        const bool reflect = nx > skip && xs > 0.f;  // warp-uniform
+        const float alpha = x0 > 0.f ? -nx : nx;
+        const float h = reflect ? fmaf(-x0, alpha, xs) : 0.f;
+        const float u = !reflect ? 0.f : (lane == k + 1 ? x0 - alpha : v);
+        if (lane < D) {
+          w.U[k][lane] = u;
+          w.su[lane] = u;
         }
+        if (lane == 0) w.h[k] = h;
       }
-      __syncwarp();
-      float xv[R];
+      bar();
+      const float h = w.h[k];
+      if (!(h > 0.f)) continue;  // the same for every thread
+      const float uj = lane < D ? w.su[lane] : 0.f;
+      const float ih = __frcp_rn(h);
+      // p_i = (A u)_i / h for this warp's rows
+      float p[RPW];
 #pragma unroll
-      for (int r = 0; r < R; ++r) {
-        const int row = r * 32 + lane;
-        xv[r] = (row > k && row < D) ? w.rk[row] : 0.f;
+      for (int r = 0; r < RPW; ++r) {
+        float t = a[r] * uj;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(kFull, t, o);
+        p[r] = t * ih;
+        const int row = warp + r * W;
+        if (lane == 0 && warp < W && row < D) w.sq[row] = p[r];
       }
-      const float xs = w.rk[D];
-      const float x0 = w.rk[k + 1];
-      const float nx = sqrtf(xs);
-      const bool reflect = nx > skip && xs > 0.f;  // warp-uniform
-      // u = x - alpha e_1 with alpha = -sign(x_0) |x|, so |u|^2 = 2 (|x|^2 + |x_0| |x|)
-      const float alpha = x0 > 0.f ? -nx : nx;
-      const float h = reflect ? fmaf(-x0, alpha, xs) : 0.f;
-      float u[R];
+      bar();
+      // K = u^T p / (2 h), q = p - K u, A <- A - u q^T - q u^T
+      const float pj = lane < D ? w.sq[lane] : 0.f;
+      float up = uj * pj;
 #pragma unroll
-      for (int r = 0; r < R; ++r) {
-        const int row = r * 32 + lane;
-        u[r] = !reflect ? 0.f : (row == k + 1 ? x0 - alpha : (row > k + 1 ? xv[r] : 0.f));
-        if (row < D) {
-          w.U[k][row] = u[r];
-          w.su[row] = u[r];
-        }
+      for (int o = 16; o > 0; o >>= 1) up += __shfl_xor_sync(kFull, up, o);
+      const float K = 0.5f * up * ih;
+      const float qj = fmaf(-K, uj, pj);
+#pragma unroll
+      for (int r = 0; r < RPW; ++r) {
+        const int row = warp + r * W;
+        const float ui = __shfl_sync(kFull, uj, row & 31);
+        const float qi = fmaf(-K, ui, p[r]);
+        a[r] = fmaf(-ui, qj, fmaf(-qi, uj, a[r]));
       }
-      if (lane == 0) w.h[k] = h;
-      __syncwarp();
-      if (reflect) {
-        // p = A u / h, K = u^T p / (2 h), q = p - K u, A <- A - u q^T - q u^T
-        const float ih = __frcp_rn(h);
-        float p[R];
-#pragma unroll
-        for (int r = 0; r < R; ++r) {
-          const int row = r * 32 + lane;
-          float s0 = 0.f, s1 = 0.f, s2 = 0.f;
-#pragma unroll
-          for (int j = 0; j < D; j += 3) {
-            s0 = fmaf(a[r][j], w.su[j], s0);
-            if (j + 1 < D) s1 = fmaf(a[r][j + 1], w.su[j + 1], s1);
-            if (j + 2 < D) s2 = fmaf(a[r][j + 2], w.su[j + 2], s2);
-          }
-          p[r] = (s0 + s1 + s2) * ih;
-          if (row < D) w.sq[row] = p[r];
-        }
-        __syncwarp();
-        // u^T p, summed by every lane from the broadcast copies (no shuffle chain)
-        float up0 = 0.f, up1 = 0.f, up2 = 0.f;
-#pragma unroll
-        for (int j = 0; j < D; j += 3) {
-          up0 = fmaf(w.su[j], w.sq[j], up0);
-          if (j + 1 < D) up1 = fmaf(w.su[j + 1], w.sq[j + 1], up1);
-          if (j + 2 < D) up2 = fmaf(w.su[j + 2], w.sq[j + 2], up2);
-        }
-        const float up = up0 + up1 + up2;
-        __syncwarp();
-        const float K = 0.5f * up * ih;
-        float q[R];
-#pragma unroll
-        for (int r = 0; r < R; ++r) {
-          const int row = r * 32 + lane;
-          q[r] = fmaf(-K, u[r], p[r]);
-          if (row < D) w.sq[row] = q[r];
-        }
-        __syncwarp();
-#pragma unroll
-        for (int r = 0; r < R; ++r) {
-#pragma unroll
-          for (int j = 0; j < D; ++j) a[r][j] = fmaf(-u[r], w.sq[j], fmaf(-q[r], w.su[j], a[r][j]));
-        }
-      }
-      __syncwarp();
     }
-    // T: diagonal and first off-diagonal
+    // T: diagonal and first off-diagonal, from the owners of the rows
 #pragma unroll
-    for (int r = 0; r < R; ++r) {
-      const int row = r * 32 + lane;
-#pragma unroll
-      for (int j = 0; j < D; ++j) {
-        if (row == j) {
-          w.d[j] = a[r][j];
-          if (j + 1 < D) {
-            w.e[j] = a[r][j + 1];
-            w.e2[j] = a[r][j + 1] * a[r][j + 1];
-          }
+    for (int r = 0; r < RPW; ++r) {
+      const int row = warp + r * W;
+      const float nxt = __shfl_down_sync(kFull, a[r], 1);  // the entry right of lane's
+      if (warp < W && row < D && lane == row) {
+        w.d[row] = a[r];
+        if (row + 1 < D) {
+          w.e[row] = nxt;
+          w.e2[row] = nxt * nxt;
         }
       }
     }
-    if (lane == 0) {
+    if (tid == 0) {
       w.e[D - 1] = 0.f;
       w.e2[D - 1] = 0.f;
       w.scale = scale;
     }
-    __syncwarp();
+    bar();
+  }
+  if (tid < 32) {
+    if constexpr (D > 32) {
+      float a[R][D];
+      float scale = 0.f;
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        const int row = r * 32 + lane;
+#pragma unroll
+        for (int j = 0; j < D; ++j) a[r][j] = row < D ? As[row * D + j] : 0.f;
+#pragma unroll
+        for (int j = 0; j < D; ++j)
+          if (row == j) scale = fmaxf(scale, fabsf(a[r][j]));
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) scale = fmaxf(scale, __shfl_xor_sync(kFull, scale, o));
+      const float skip = 1e-12f * scale;  // a column below this size is taken as already reduced
+#pragma unroll 1
+      for (int k = 0; k + 2 < D; ++k) {
+        // column k of A, below the diagonal, read as row k (A is symmetric):
+        // its owner lane publishes the row and |x|^2
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+          if (r * 32 + lane == k) {
+            float t0 = 0.f, t1 = 0.f;
+#pragma unroll
+            for (int j = 0; j < D; ++j) {
+              w.rk[j] = a[r][j];
+              const float v = j > k ? a[r][j] : 0.f;
+              if (j & 1) t1 = fmaf(v, v, t1);
+              else t0 = fmaf(v, v, t0);
+            }
+            w.rk[D] = t0 + t1;
+          }
+        }
+        __syncwarp();
+        float xv[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+          const int row = r * 32 + lane;
+          xv[r] = (row > k && row < D) ? w.rk[row] : 0.f;
+        }
+        const float xs = w.rk[D];
+        const float x0 = w.rk[k + 1];
+        const float nx = sqrtf(xs);
+        const bool reflect = nx > skip && xs > 0.f;  // warp-uniform
+        // u = x - alpha e_1 with alpha = -sign(x_0) |x|, so |u|^2 = 2 (|x|^2 + |x_0| |x|)
+        const float alpha = x0 > 0.f ? -nx : nx;
+        const float h = reflect ? fmaf(-x0, alpha, xs) : 0.f;
+        float u[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+          const int row = r * 32 + lane;
+          u[r] = !reflect ? 0.f : (row == k + 1 ? x0 - alpha : (row > k + 1 ? xv[r] : 0.f));
+          if (row < D) {
+            w.U[k][row] = u[r];
+            w.su[row] = u[r];
+          }
+        }
+        if (lane == 0) w.h[k] = h;
+        __syncwarp();
+        if (reflect) {
+          // p = A u / h, K = u^T p / (2 h), q = p - K u, A <- A - u q^T - q u^T
+          const float ih = __frcp_rn(h);
+          float p[R];
+#pragma unroll
+          for (int r = 0; r < R; ++r) {
+            const int row = r * 32 + lane;
+            float s0 = 0.f, s1 = 0.f, s2 = 0.f;
+#pragma unroll
+            for (int j = 0; j < D; j += 3) {
+              s0 = fmaf(a[r][j], w.su[j], s0);
+              if (j + 1 < D) s1 = fmaf(a[r][j + 1], w.su[j + 1], s1);
+              if (j + 2 < D) s2 = fmaf(a[r][j + 2], w.su[j + 2], s2);
+            }
+            p[r] = (s0 + s1 + s2) * ih;
+            if (row < D) w.sq[row] = p[r];
+          }
+          __syncwarp();
+          // u^T p, summed by every lane from the broadcast copies (no shuffle chain)
+          float up0 = 0.f, up1 = 0.f, up2 = 0.f;
+#pragma unroll
+          for (int j = 0; j < D; j += 3) {
+            up0 = fmaf(w.su[j], w.sq[j], up0);
+            if (j + 1 < D) up1 = fmaf(w.su[j + 1], w.sq[j + 1], up1);
+            if (j + 2 < D) up2 = fmaf(w.su[j + 2], w.sq[j + 2], up2);
+          }
+          const float up = up0 + up1 + up2;
+          __syncwarp();
+          const float K = 0.5f * up * ih;
+          float q[R];
+#pragma unroll
+          for (int r = 0; r < R; ++r) {
+            const int row = r * 32 + lane;
+            q[r] = fmaf(-K, u[r], p[r]);
+            if (row < D) w.sq[row] = q[r];
+          }
+          __syncwarp();
+#pragma unroll
+          for (int r = 0; r < R; ++r) {
+#pragma unroll
+            for (int j = 0; j < D; ++j) a[r][j] = fmaf(-u[r], w.sq[j], fmaf(-q[r], w.su[j], a[r][j]));
+          }
+        }
+        __syncwarp();
+      }
+      // T: diagonal and first off-diagonal
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        const int row = r * 32 + lane;
+#pragma unroll
+        for (int j = 0; j < D; ++j) {
+          if (row == j) {
+            w.d[j] = a[r][j];
+            if (j + 1 < D) {
+              w.e[j] = a[r][j + 1];
+              w.e2[j] = a[r][j + 1] * a[r][j + 1];
+            }
+          }
+        }
+      }
+      if (lane == 0) {
+        w.e[D - 1] = 0.f;
+        w.e2[D - 1] = 0.f;
+        w.scale = scale;
+      }
+      __syncwarp();
+    }
     // Gershgorin interval of T
     float glo = 3.0e38f, ghi = -3.0e38f;
     for (int i = lane; i < D; i += 32) {
