@@ -58,6 +58,8 @@ struct DevScalars {
   alignas(16) uint32_t chist[3][kMaxRadix];  // histograms of x, y and z (read as uint4)
   unsigned long long node_fx;   // node-mean reading: sum over points of their mean edge length (fixed point)
   unsigned long long node_cnt;  // and the points that have edges
+  float cexp;                   // the Eq. 4 exponent scale log2(e) / sigma_g^2 of this graph, once cexp_ready
+  uint32_t cexp_ready;          // set by the first moments launch on this graph
   uint32_t build_end_;
   // ---- noise estimate region
   unsigned long long n_patches;

@@ -84,10 +84,16 @@ __device__ __forceinline__ float step_cexp(const DevScalars* sc) {
   return sg > 0.0 ? float(1.4426950408889634 / (sg * sg)) : 0.f;
 }
 
-// The same, computed once per block by thread 0 and shared: float64 work is
-// slow on this GPU, and every thread computing it costs microseconds.
+// The same as the moments launch left it for this graph, or computed here:
+// float64 work is slow on this GPU (dependent float64 operations cost hundreds
+// of cycles), so it is done once where it is off the critical path.
+__device__ __forceinline__ float graph_cexp(const DevScalars* sc) {
+  return sc->cexp_ready ? sc->cexp : step_cexp(sc);
+}
+
+// The same, read or computed once per block by thread 0 and shared.
 __device__ __forceinline__ float block_cexp(const DevScalars* sc, float* s_cexp) {
-  if (threadIdx.x == 0) *s_cexp = step_cexp(sc);
+  if (threadIdx.x == 0) *s_cexp = graph_cexp(sc);
   __syncthreads();
   return *s_cexp;
 }

@@ -362,6 +362,13 @@ __device__ __forceinline__ void ne_moments_body(const MomentArgs& ma, int bid, i
       for (int i = lane; i < kHRows * kHRow / 2; i += 32) hw[i] = 0u;
     }
   }
+  // the graph's Eq. 4 exponent scale, once, for the filter steps that follow
+  // (float64 work, here off their critical path)
+  if (bid == 0 && threadIdx.x == 0 && !sc->cexp_ready) {
+    sc->cexp = step_cexp(sc);
+    __threadfence();
+    sc->cexp_ready = 1u;
+  }
   __syncthreads();
   int r0 = 0, c0 = 0, rb = 0, re = 0;
   if (DT == 1) {

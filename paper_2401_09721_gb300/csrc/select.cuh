@@ -533,10 +533,14 @@ __device__ __forceinline__ void select_filter(const FilterArgs& a, int S, int fi
   __shared__ float s_cexp;
   const bool global = select && a.q_global;
   double sigma = 0.0, nsel = 1.0, J_prev = 0.0, J_best = 0.0;  // thread 0 only
+  // J(t) = |sigma^2 - lost_t / (3 N_sel)| with lost_t the exact fixed-point sum of
+  // y^2 - x_t^2: sigma^2 and 2^-kSqShift / (3 N_sel) are formed once, so each J
+  // is one fused multiply-add (float64 operations have a long latency here)
+  double sig2 = 0.0, inv3n = 0.0;  // thread 0 only
   int q_best = 0;                                               // thread 0 only
   unsigned long long ysq = 0;
   if (threadIdx.x == 0) {
-    s_cexp = step_cexp(sc);
+    s_cexp = graph_cexp(sc);
     const int q_fixed = a.q_src ? min(max(*a.q_src, 0), kQCap) : a.q_fixed;
     const int q_limit = n == 0 ? 0 : (select ? a.q_max : q_fixed);
     int keep_all = 0, q_final = 0, stopped = 0;
@@ -546,15 +550,17 @@ __device__ __forceinline__ void select_filter(const FilterArgs& a, int S, int fi
       keep_all = nkt == 0;  // no point left: every point is used
       nsel = keep_all ? double(n) : double(nkt);
       ysq = keep_all ? ld_relaxed_u64(&sc->ysq_all) : ld_relaxed_u64(&sc->ysq_keep);
-      J_prev = sigma * sigma;  // J(0): nothing filtered yet
+      sig2 = sigma * sigma;
+      inv3n = (1.0 / double(1 << kSqShift)) / (3.0 * nsel);
+      J_prev = sig2;  // J(0): nothing filtered yet
       J_best = J_prev;
       if (gtid == 0) sc->J[0] = J_prev;
       for (int t = 1; t <= min(S, q_limit); ++t) {
         const unsigned long long* src = reinterpret_cast<const unsigned long long*>(
             keep_all ? &sc->spec_all[t] : &sc->spec_keep[t]);
         // sum of y^2 - x_t^2 over the points of Eq. 6: exact in two's complement
-        const double lost = double((long long)(ysq - ld_relaxed_u64(src))) * (1.0 / double(1 << kSqShift));
-        const double J = fabs(sigma * sigma - lost / (3.0 * nsel));
+        const double lost = double((long long)(ysq - ld_relaxed_u64(src)));
+        const double J = fabs(fma(-lost, inv3n, sig2));
         if (gtid == 0) {
           sc->J[t] = J;
           sc->n_J = t + 1;
@@ -612,8 +618,8 @@ __device__ __forceinline__ void select_filter(const FilterArgs& a, int S, int fi
     if (select) {
       if (threadIdx.x == 0) {
         const unsigned long long ss = ld_relaxed_u64(&sc->sumsq[t]);
-        const double lost = double((long long)(ysq - ss)) * (1.0 / double(1 << kSqShift));
-        const double J = fabs(sigma * sigma - lost / (3.0 * nsel));
+        const double lost = double((long long)(ysq - ss));
+        const double J = fabs(fma(-lost, inv3n, sig2));
         if (gtid == 0) {
           sc->J[t] = J;
           sc->n_J = t + 1;
