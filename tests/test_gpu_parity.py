@@ -421,6 +421,27 @@ def test_fixed_power_filter(F, q):
     assert np.abs(out - ref).max() <= COLOR_TOL
 
 
+def test_fixed_power_filter_on_a_new_graph_after_an_estimate(F):
+    """The Eq. 4 exponent scale that the moments launch leaves for a graph must not
+    outlive it: a full run on one cloud, then a fixed-q denoise on another cloud
+    (no noise estimate of its own) in the same context."""
+    xa = synth.torso_points(20000, 8, 11)
+    ca = synth.add_noise_u8(synth.piecewise_colors(xa, 8, 11), 20.0, 11)
+    xb = synth.sphere_points(15000, 8, 12)
+    cb = synth.add_noise_u8(synth.piecewise_colors(xb, 8, 12), 30.0, 12)
+    codes = orc.scan_line_codes(xb, 8)
+    row_ptr, col = orc.adjacency_csr(orc.slg_edges(orc.scan_orders(codes)), len(xb))
+    sg_b = orc.sigma_g(xb, row_ptr, col)
+    ref = orc.lowpass(cb, row_ptr, col, orc.random_walk_weights(xb, row_ptr, col, sg_b), 3)
+    ctx = F.Context(len(xa), bits=8)
+    ctx.run(torch.from_numpy(xa).cuda(), torch.from_numpy(ca).cuda())
+    sg_a = ctx.stats()["sigma_g"]
+    assert abs(sg_a - sg_b) > 1e-3 * sg_b  # the two graphs have different scales
+    ctx.build_graph(torch.from_numpy(xb).cuda())
+    out = ctx.denoise(torch.from_numpy(cb).cuda(), 3).cpu().numpy()
+    assert np.abs(out - ref).max() <= COLOR_TOL
+
+
 def test_external_sigma_and_q_out(F):
     xyz = synth.torso_points(20000, 8, 6)
     rgb = synth.add_noise_u8(synth.piecewise_colors(xyz, 8, 6), 30.0, 6)
