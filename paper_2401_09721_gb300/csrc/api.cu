@@ -977,6 +977,7 @@ fgbd_status fgbd_ctx_create(int64_t capacity, const fgbd_params* params, fgbd_ct
   const uint32_t pooled = (p.variant & FGBD_VARIANT_POOLED_PATCH) ? 1u : 0u;
   ok = ok && cudaMemcpy(&ctx->sc->sigma_mode, &mode, sizeof(mode), cudaMemcpyHostToDevice) == cudaSuccess;
   ok = ok && cudaMemcpy(&ctx->sc->pooled_patch, &pooled, sizeof(pooled), cudaMemcpyHostToDevice) == cudaSuccess;
+  ok = ok && cudaMemcpy(&ctx->sc->fslr_factor, &p.fslr_factor, sizeof(double), cudaMemcpyHostToDevice) == cudaSuccess;
   ok = ok && cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking) == cudaSuccess;
   ok = ok && cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking) == cudaSuccess;
   for (cudaEvent_t* e : {&ctx->ev_fork, &ctx->ev_filter, &ctx->ev_join})

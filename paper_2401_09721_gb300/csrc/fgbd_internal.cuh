@@ -69,6 +69,8 @@ struct DevScalars {
   int32_t spec_done;            // filter steps stored by the noise-estimate kernel
   uint32_t sigma_ready;         // set (release) once sigma_est of this estimate is written
   uint32_t spec_go[kSpecMax + 1];  // after stored step t: 1 to take another before selecting
+  float fslr_thr[4];            // the FSLR threshold of this sigma_est as the selection uses it (once fslr_ready)
+  uint32_t fslr_ready;          // set by the eigen step with sigma_est
   uint32_t ne_end_;
   // ---- results of the noise estimate
   double eig[kDMax];            // descending (the first D = 3 (6w + 1) are used)
@@ -98,6 +100,7 @@ struct DevScalars {
   unsigned long long wait_limit_ns;  // any device-side wait gives up after this long
   uint32_t sigma_mode;               // sigma_g of Eq. 4: kSigmaEdge, kSigmaNode or kSigmaPair
   uint32_t pooled_patch;             // 1: patches of D = 7 pooled over the colour channels (Section 2.3)
+  double fslr_factor;                // the FSLR threshold factor (2 in Section 2.4)
 };
 
 // Readings of sigma_g (Section 2.2): the mean length over the edges (the

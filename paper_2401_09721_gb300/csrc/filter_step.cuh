@@ -78,6 +78,18 @@ __device__ __forceinline__ unsigned long long sq3(float4 x) {
   return (unsigned long long)(sq_fixed(x.x) + sq_fixed(x.y) + sq_fixed(x.z));
 }
 
+// The FSLR threshold factor * sigma as the selection uses it: a float32 band
+// [t[0], t[1]] outside which float32 decides, and the threshold as a
+// float-float pair (t[2], t[3]).
+__device__ __forceinline__ void fslr_band(double factor, double sigma, int dtype, float* t) {
+  const double thr = factor * sigma;
+  const double band = dtype == 0 ? 2e-6 : 5e-5;
+  t[0] = float(thr * (1.0 - band));
+  t[1] = float(thr * (1.0 + band));
+  t[2] = float(thr);
+  t[3] = float(thr - double(t[2]));
+}
+
 // The Eq. 4 exponent scale log2(e) / sigma_g^2
 __device__ __forceinline__ float step_cexp(const DevScalars* sc) {
   const double sg = sigma_g_of(sc);

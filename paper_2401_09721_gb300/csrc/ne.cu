@@ -536,7 +536,7 @@ struct FinBar {
 // 0..kFinThreads-1 of the block.
 template <int D>
 __device__ void eig_tail(const double* __restrict__ S, const float* __restrict__ Sf, DevScalars* __restrict__ sc,
-                         double* __restrict__ sigma_out) {
+                         double* __restrict__ sigma_out, int dtype) {
   static_assert(D <= 32, "warp 0 holds one eigenvalue a lane");
   __shared__ float V[D * D];  // eigenvector estimates (columns)
   __shared__ float s_mu[D];   // their float32 eigenvalues (the fallback of a non-finite quotient)
@@ -641,6 +641,10 @@ __device__ void eig_tail(const double* __restrict__ S, const float* __restrict__
       sc->tau = tau;
       sc->sigma_est = sg;
       sc->ne_valid = 1;
+      // the selection's FSLR threshold of this sigma_est, formed here where it
+      // is off the critical path (float64)
+      fslr_band(sc->fslr_factor, sg, dtype, sc->fslr_thr);
+      sc->fslr_ready = 1u;
       if (sigma_out) *sigma_out = sg;
       __threadfence();
       atomicExch(&sc->sigma_ready, 1u);
@@ -703,7 +707,7 @@ __device__ __noinline__ void finalize_block(int dtype, const double* __restrict_
       Sf[e] = float(v);
     }
     fin_bar();
-    eig_tail<kD>(S, Sf, sc, sigma_out);
+    eig_tail<kD>(S, Sf, sc, sigma_out, dtype);
     return;
   }
   // pooled: 3 N samples of kT entries; mu_i = sum_c s1[3i + c] / 3N,
@@ -723,7 +727,7 @@ __device__ __noinline__ void finalize_block(int dtype, const double* __restrict_
     Sf[e] = float(v);
   }
   fin_bar();
-  eig_tail<kT>(S, Sf, sc, sigma_out);
+  eig_tail<kT>(S, Sf, sc, sigma_out, dtype);
 }
 
 __global__ void __launch_bounds__(kFinThreads) k_ne_finalize(int dtype, const double* __restrict__ f64_partials,

@@ -395,12 +395,13 @@ __device__ __forceinline__ void select_filter(const FilterArgs& a, int S, int fi
   // as a float32 band [t_lo, t_hi] (outside it float32 decides) and as float-float.
   __shared__ float s_thr[4];
   if (threadIdx.x == 0 && select) {
-    const double thr = a.fslr_factor * __ldcg(a.sigma_src);
-    const double band = a.dtype == 0 ? 2e-6 : 5e-5;
-    s_thr[0] = float(thr * (1.0 - band));
-    s_thr[1] = float(thr * (1.0 + band));
-    s_thr[2] = float(thr);
-    s_thr[3] = float(thr - double(s_thr[2]));
+    if (a.sigma_src == &sc->sigma_est && sc->fslr_ready) {
+      // as the eigen step formed them with sigma_est (fslr_band, the same arithmetic)
+#pragma unroll
+      for (int i = 0; i < 4; ++i) s_thr[i] = sc->fslr_thr[i];
+    } else {
+      fslr_band(a.fslr_factor, __ldcg(a.sigma_src), a.dtype, s_thr);
+    }
   }
   __syncthreads();
   float t_lo = 0.f, t_hi = 0.f;
@@ -540,26 +541,41 @@ __device__ __forceinline__ void select_filter(const FilterArgs& a, int S, int fi
   int q_best = 0;                                               // thread 0 only
   unsigned long long ysq = 0;
   if (threadIdx.x == 0) {
-    s_cexp = graph_cexp(sc);
+    // every scalar this thread reads, loaded together (one round trip to L2)
+    const uint32_t c_ready = sc->cexp_ready;
+    const float c_val = sc->cexp;
+    unsigned long long nkt = 0, ysk = 0, ysa = 0, sk[kSpecMax] = {}, sa[kSpecMax] = {};
+    if (select) {
+      sigma = __ldcg(a.sigma_src);
+      nkt = ld_relaxed_u64(&sc->n_keep);
+      ysk = ld_relaxed_u64(&sc->ysq_keep);
+      ysa = ld_relaxed_u64(&sc->ysq_all);
+#pragma unroll
+      for (int q = 0; q < kSpecMax; ++q) {
+        if (q < S) {
+          sk[q] = ld_relaxed_u64(reinterpret_cast<const unsigned long long*>(&sc->spec_keep[q + 1]));
+          sa[q] = ld_relaxed_u64(reinterpret_cast<const unsigned long long*>(&sc->spec_all[q + 1]));
+        }
+      }
+    }
+    s_cexp = c_ready ? c_val : step_cexp(sc);
     const int q_fixed = a.q_src ? min(max(*a.q_src, 0), kQCap) : a.q_fixed;
     const int q_limit = n == 0 ? 0 : (select ? a.q_max : q_fixed);
     int keep_all = 0, q_final = 0, stopped = 0;
     if (select) {
-      sigma = __ldcg(a.sigma_src);
-      const unsigned long long nkt = ld_relaxed_u64(&sc->n_keep);
       keep_all = nkt == 0;  // no point left: every point is used
       nsel = keep_all ? double(n) : double(nkt);
-      ysq = keep_all ? ld_relaxed_u64(&sc->ysq_all) : ld_relaxed_u64(&sc->ysq_keep);
+      ysq = keep_all ? ysa : ysk;
       sig2 = sigma * sigma;
       inv3n = (1.0 / double(1 << kSqShift)) / (3.0 * nsel);
       J_prev = sig2;  // J(0): nothing filtered yet
       J_best = J_prev;
       if (gtid == 0) sc->J[0] = J_prev;
-      for (int t = 1; t <= min(S, q_limit); ++t) {
-        const unsigned long long* src = reinterpret_cast<const unsigned long long*>(
-            keep_all ? &sc->spec_all[t] : &sc->spec_keep[t]);
+#pragma unroll
+      for (int t = 1; t <= kSpecMax; ++t) {
+        if (t > min(S, q_limit)) break;
         // sum of y^2 - x_t^2 over the points of Eq. 6: exact in two's complement
-        const double lost = double((long long)(ysq - ld_relaxed_u64(src)));
+        const double lost = double((long long)(ysq - (keep_all ? sa[t - 1] : sk[t - 1])));
         const double J = fabs(fma(-lost, inv3n, sig2));
         if (gtid == 0) {
           sc->J[t] = J;
