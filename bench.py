@@ -498,16 +498,17 @@ def algorithmic_bytes(name, n, extra_steps=0.0, out_bytes=3):
         # points; the neighbour slots out
         "slg_link": 4 + 8 + 12 + 16,
         "gather_colors": 11,
-        "ne_moments": 28,
+        # moments: codes 4, slots 16, colours 4, the spread out 4; x_0 of the filter steps out 16
+        "ne_moments": 28 + 16,
     }
     if name in per_point:
         return per_point[name] * n
     if name == "ne_finalize":
         # the filter steps stored by the estimate launch (its eigen block moves no bytes):
-        # step 1 reads x_0 (y 4 + codes 4) and c4 16, writes the six normalised weights 24,
-        # x_1 16 and its power sum 4; each later step reads x 16, c4 16 and the weights 24,
-        # writes x 16 and its power sum 4
-        return (68 + 76 * (SPEC_STEPS - 1)) * n
+        # step 1 reads x_0 16 (written by the moments launch) and c4 16, writes the six
+        # normalised weights 24, x_1 16 and its power sum 4; each later step reads x 16, c4 16
+        # and the weights 24, writes x 16 and its power sum 4
+        return 76 * SPEC_STEPS * n
     if name == "filter_select":
         # keep flags: y 4, spread 4, keep 1; the stored steps' Eq. 6 terms 4 each and keep 1;
         # ordinary steps beyond the stored ones 72 each (x in, c4, weights, x out);
