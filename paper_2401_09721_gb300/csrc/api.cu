@@ -568,8 +568,8 @@ fgbd_status capture_run(fgbd_ctx* ctx, const fgbd_ctx::RunKey& k, cudaStream_t s
 // ---------------------------------------------------------------- segmented batches
 // A batch whose frames share the window (1), the ablation switches and the
 // colour type runs each stage as one launch over up to kSegMax frames
-// (segmented launches, fgbd_internal.cuh): 13 launches for the whole chunk
-// instead of about 17 per frame, every frame's short latency-bound kernels
+// (segmented launches, fgbd_internal.cuh): 15 launches for the whole chunk
+// instead of 15 per frame, every frame's short latency-bound kernels
 // side by side in one grid, the estimate launch with one eigen block per
 // frame, and one cooperative selection/filter for all frames (each frame's
 // blocks synchronise among themselves).  Each frame's blocks run the same
